@@ -1,0 +1,209 @@
+/*
+ * gblu -- sparse LU re-factorization with pivot check and sparse triangular
+ * solves for circuit-simulation matrices, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is CKTSO's numerical path (arXiv 2411.14082):
+ *   - factorization with pivoting (Section II-A, Algorithm 1), here in CSC
+ *     form: left-looking column updates, threshold partial row pivoting;
+ *   - fast re-factorization on the previous pattern and pivot order with a
+ *     pivot check (Section IV-B, Algorithms 3 and 4), and, when a pivot fails
+ *     the check, a restart that recomputes with pivoting the unfinished
+ *     columns and their ancestors in the column elimination tree
+ *     (Section IV-C and IV-D, Algorithm 5);
+ *   - forward and back substitution (Section II-C, Algorithm 2, and the
+ *     structure-adaptive parallel solve of Section V).
+ * Ordering and symbolic analysis run on the host; all numerical work runs in
+ * this library's CUDA kernels.  There is no CPU fallback.
+ *
+ * Conventions shared by every call
+ *   - Matrices are CSC: Ap[n+1] (Ap[0] = 0, non-decreasing), Ai[nnz] row
+ *     indices in [0, n), no duplicate row inside a column (rows inside a
+ *     column may be unsorted), Ax[nnz] values (float64).  Indices are int32.
+ *   - "_dev" pointers are device memory of the handle's device; other
+ *     pointers are host memory.  The caller owns every pointer it passes;
+ *     the library never frees caller memory and keeps no caller pointer after
+ *     a call returns.  The handle owns its internal device buffers.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Kernels are queued on it; calls that must read a device result
+ *     (documented below) synchronize that stream.
+ *   - Return codes: GBLU_OK (0), GBLU_REPIVOTED (1, success after a restart
+ *     with pivoting), or a negative GBLU_ERR_* code.  No call prints, aborts,
+ *     or falls back to the CPU.  gblu_last_error() gives a one-line message.
+ */
+#ifndef GBLU_H
+#define GBLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBLU_OK 0
+#define GBLU_REPIVOTED 1
+#define GBLU_ERR_INVALID_INPUT (-1)  /* bad n, pointers, CSC pattern, duplicates, Q */
+#define GBLU_ERR_SINGULAR (-2)       /* a column has no nonzero pivot candidate     */
+#define GBLU_ERR_NOT_ANALYZED (-3)   /* call order violated                         */
+#define GBLU_ERR_NOMEM (-4)          /* device or host allocation failed            */
+#define GBLU_ERR_DEVICE_TIMEOUT (-5) /* a bounded device wait ran out               */
+#define GBLU_ERR_CUDA (-6)           /* a CUDA runtime call failed                  */
+#define GBLU_ERR_NOT_FACTORIZED (-7) /* refactorize/solve before a factorization    */
+#define GBLU_ERR_INTERNAL (-8)       /* a structural invariant check failed         */
+
+/* Scheduling of the re-factorization (Section III-B dual-mode scheduling). */
+#define GBLU_SCHED_AUTO 0     /* level-synchronous front, sync-free tail      */
+#define GBLU_SCHED_LEVEL 1    /* every level a separate launch (cluster mode) */
+#define GBLU_SCHED_SYNCFREE 2 /* one launch, ready flags (pipeline mode)      */
+
+typedef struct gblu_ctx *gblu_handle;
+
+typedef struct {
+    double pivot_tol;    /* eps of the pivot rule |x(k)| >= eps*max|x(L rows)|
+                            (Section II-A; the paper gives no value), default 1e-3 */
+    int sched_mode;      /* GBLU_SCHED_*, default AUTO                            */
+    int solve_mode;      /* GBLU_SCHED_*, same meaning for the triangular solves  */
+    double alpha;        /* dividing level = first level with fewer than
+                            alpha * resident warps columns (Section IV-B uses
+                            alpha = 2 per thread), default 2.0                    */
+    long long spin_limit;/* iterations of every device wait before it gives up
+                            with GBLU_ERR_DEVICE_TIMEOUT, default 1<<24           */
+} gblu_opts;
+
+/* Fill *o with the defaults above. */
+void gblu_default_opts(gblu_opts *o);
+
+/* One-line description of the last error of this thread (never NULL). */
+const char *gblu_last_error(void);
+
+/* Create a handle on CUDA device `device`; o may be NULL for defaults.
+ * Returns GBLU_ERR_CUDA if the device cannot be used. */
+int gblu_create(gblu_handle *h, int device, const gblu_opts *o);
+
+/* Release every device buffer of the handle (synchronizes the device). */
+void gblu_destroy(gblu_handle h);
+
+/*
+ * Pre-processing for one sparsity pattern (Section III-A): validates the CSC
+ * pattern, takes the column order Q (Q[k] = original column eliminated at
+ * step k; rows use the same symmetric order as the preferred pivots), or
+ * computes a minimum-degree order on A+A^T when Q is NULL, and builds the
+ * column elimination tree of A(:,Q) (the dependency upper bound of
+ * Section II-B used to choose restart columns).  Host-only work.  Ap, Ai,
+ * Q are host arrays and are copied.  Any previous factorization of the
+ * handle is discarded.
+ */
+int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
+                 const int32_t *Q);
+
+/*
+ * Factorization with pivoting (Section II-A, Algorithm 1 in CSC form,
+ * scheduled over the column elimination tree): every step prefers its
+ * diagonal row Q[k] and keeps it unless |x(Q[k])| < pivot_tol * max|other
+ * candidates| or x(Q[k]) == 0, else takes the largest candidate (ties: the
+ * row first in Q).  Ax_dev: device float64[nnz] in the slot order of the
+ * analyze call's Ai.  Builds the factors and, on the host, the fixed-pattern
+ * schedule for refactorize and solve.  Synchronizes `stream`.
+ * Returns GBLU_OK or GBLU_ERR_SINGULAR (factors then invalid).
+ */
+int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
+
+/*
+ * Fast re-factorization with pivot check (Section IV, Algorithms 3-5):
+ * recomputes the factors of new values on the previous pattern and pivot
+ * order, checking every pivot.  If a pivot fails, the unfinished columns and
+ * their elimination-tree ancestors are recomputed with pivoting (preferring
+ * the previous pivots) and the schedule is rebuilt; the call then returns
+ * GBLU_REPIVOTED.  The result equals a factorization with pivoting that
+ * prefers the previous pivot sequence.  Synchronizes `stream` once (to read
+ * the 4-byte check status).  *repivoted (optional, host) is set to 1 if a
+ * restart happened, else 0.
+ */
+int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream,
+                     int32_t *repivoted);
+
+/*
+ * Solve A x = b with the current factors: y = L^-1 P b, z = U^-1 y,
+ * x(Q) = z (Algorithm 2 and the parallel solve of Section V).  b_dev and
+ * x_dev are device float64[n]; they may alias.  Asynchronous on `stream`.
+ */
+int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream);
+
+/*
+ * Relative residual of a solution, computed on the device in float64:
+ * out_dev[0] = ||b - A x||_inf / (||A||_inf * ||x||_inf), out_dev[1] =
+ * ||b - A x||_inf, out_dev[2] = ||A||_inf, out_dev[3] = ||x||_inf.
+ * Ax_dev uses the analyze slot order.  Asynchronous on `stream`.
+ * (A measurement aid; not part of the paper's method.)
+ */
+int gblu_residual(gblu_handle h, const double *Ax_dev, const double *b_dev,
+                  const double *x_dev, double *out_dev, void *stream);
+
+/*
+ * One Newton-Raphson linear step from HOST buffers: copies Ax_host (nnz
+ * values, analyze slot order) and b_host (n) to handle-owned device staging
+ * buffers, re-factorizes with pivot check (as gblu_refactorize), solves, and
+ * copies the solution to x_host (n).  Host buffers may be pageable; pinned
+ * buffers make the copies asynchronous.  Synchronizes `stream` before
+ * returning.  Returns what gblu_refactorize returns (GBLU_OK or
+ * GBLU_REPIVOTED) or an error.
+ */
+int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host,
+                   double *x_host, void *stream, int32_t *repivoted);
+
+/* Sizes and counters of the current factorization (host struct). */
+typedef struct {
+    int32_t n;
+    int64_t nnz_a;
+    int64_t nnz_l;        /* strict lower entries                            */
+    int64_t nnz_u;        /* upper entries incl. diagonal                    */
+    double flops;         /* refactor flops: sum over updates 2*nnz(L(:,j))   */
+    int32_t n_levels;     /* levels of the column dependency graph (EGraph)  */
+    int32_t div_level;    /* first level scheduled sync-free                 */
+    int32_t n_solve_levels_l, n_solve_levels_u;
+    int32_t etree_height;
+    int64_t n_refactor;   /* refactorize calls                               */
+    int64_t n_repivot;    /* refactorize calls that restarted with pivoting  */
+    int64_t n_restart_cols; /* columns recomputed by the last restart        */
+    int32_t last_first_bad; /* first failing column of the last check, -1    */
+    int64_t device_bytes; /* device memory held by the handle                */
+    int64_t kernel_launches; /* kernels this handle has launched so far      */
+} gblu_stats;
+
+int gblu_get_stats(gblu_handle h, gblu_stats *s);
+
+/*
+ * Copy the current factors to host arrays (for verification): column k of
+ * L (strict lower) and U (upper, diagonal last) in step numbering with rows
+ * sorted, piv[k] = original row pivotal at step k, q[k] = original column
+ * of step k.  Array sizes: Lp/Up n+1, Li/Lx nnz_l, Ui/Ux nnz_u, piv/q n.
+ * Any pointer may be NULL to skip it.  Synchronizes the device.
+ */
+int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx,
+                        int64_t *Up, int32_t *Ui, double *Ux, int32_t *piv,
+                        int32_t *q);
+
+/*
+ * Host-only helpers (no device work), exposed so that the symbolic layer can
+ * be checked on machines without a GPU.
+ */
+/* Minimum-degree column order of the pattern of A + A^T: perm[k] = column
+ * eliminated at step k. */
+int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Column elimination tree of A(:,Q) (elimination tree of (A Q)^T (A Q)),
+ * parent[k] = parent step of step k or -1 (Section II-B "ETree"). */
+int gblu_column_etree(int32_t n, const int32_t *Ap, const int32_t *Ai,
+                      const int32_t *Q, int32_t *parent);
+/* Restart set of Section IV-C: every step that is not finished (finished[k]
+ * == 0) together with all its ancestors in `parent`; out[k] = 1 for members.
+ * Returns the number of members. */
+int64_t gblu_restart_set(int32_t n, const int32_t *parent, const uint8_t *finished,
+                         uint8_t *out);
+/* Levels of a column dependency DAG given as CSC of U (rows < column are the
+ * dependencies; the diagonal is ignored): level[k] = 1 + max level of its
+ * dependencies (Section II-B levelization).  Returns the number of levels. */
+int32_t gblu_levels(int32_t n, const int64_t *Up, const int32_t *Ui, int32_t *level);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLU_H */

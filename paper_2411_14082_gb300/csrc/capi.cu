@@ -1,0 +1,784 @@
+// C-ABI entry points of libgblu: handle management, analyze, factorize,
+// checked re-factorization with restart, solve, residual, stats and export.
+// The orchestration runs on the host; every numerical step runs in the
+// kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gblu_internal.h"
+
+using namespace gblu;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? GBLU_ERR_NOMEM : GBLU_ERR_CUDA, \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                        \
+    } while (0)
+
+#define CK(call)                                   \
+    do {                                           \
+        int r_ = (call);                           \
+        if (r_ != 0) return r_;                    \
+    } while (0)
+
+#define KL(call)                                                                        \
+    do {                                                                                \
+        h->launches++;                                                                  \
+        int e_ = (call);                                                                \
+        if (e_ != 0)                                                                    \
+            return fail(GBLU_ERR_CUDA, "kernel launch %s failed: %s", #call,            \
+                        cudaGetErrorString((cudaError_t)e_));                            \
+    } while (0)
+
+// Device buffer with capacity tracking.
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t cap = 0;  // elements
+};
+
+}  // namespace
+
+struct gblu_ctx {
+    int device = 0;
+    gblu_opts opts{};
+    int sm_count = 0;
+    int smem_cap = 1024;
+    int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0;
+    bool analyzed = false, factorized = false;
+    Pattern P;
+    Structure S;
+    Schedule W;
+    int32_t epoch = 0, solve_epoch = 0, tail_epoch = 0;
+    int64_t n_refactor = 0, n_repivot = 0, n_restart_cols = 0;
+    int64_t launches = 0;
+    int32_t last_first_bad = -1;
+    size_t device_bytes = 0;
+    DevCtl *hctl = nullptr;  // pinned mirror
+    DevCtl *ctl = nullptr;
+    // pattern / order
+    DBuf<int32_t> Ap, Ai, Q, qinv, clo, Acol, Aslot;
+    DBuf<int64_t> Arp;
+    // factor structure and values: rows/vals hold the canonical columns
+    // followed by the restart pool
+    DBuf<int64_t> LUp;
+    DBuf<int32_t> LUi, nU, rows, finish, level_cols, amap, piv, pinv;
+    DBuf<double> vals;
+    // solves
+    DBuf<int64_t> Lrp, Urp;
+    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, lflag, uflag;
+    DBuf<double> y, partial, stage_ax, stage_b, stage_x;
+    // restart (tail factorization)
+    DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist;
+    DBuf<int64_t> cbeg;
+    DBuf<double> sx;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int ensure(gblu_ctx *h, DBuf<T> &b, size_t count)
+{
+    if (count == 0) count = 1;
+    if (b.cap >= count) return GBLU_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        h->device_bytes -= b.cap * sizeof(T);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc((void **)&b.p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GBLU_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    b.cap = count;
+    h->device_bytes += count * sizeof(T);
+    return GBLU_OK;
+}
+
+template <class T>
+void release(gblu_ctx *h, DBuf<T> &b)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        h->device_bytes -= b.cap * sizeof(T);
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <class T>
+int upload(gblu_ctx *h, DBuf<T> &b, const std::vector<T> &v, cudaStream_t st)
+{
+    CK(ensure(h, b, v.size()));
+    if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return GBLU_OK;
+}
+
+int read_ctl(gblu_ctx *h, cudaStream_t st)
+{
+    CU(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return GBLU_OK;
+}
+
+int status_code(gblu_ctx *h)
+{
+    const int s = h->hctl->status;
+    if (s == 0) return GBLU_OK;
+    if (s == GBLU_ERR_DEVICE_TIMEOUT)
+        return fail(s, "device wait timed out (site %d, column %d)", h->hctl->where, h->hctl->where_k);
+    if (s == GBLU_ERR_SINGULAR) return fail(s, "singular: no nonzero pivot candidate at step %d", h->hctl->where_k);
+    if (s == GBLU_ERR_INTERNAL) return fail(s, "internal structure check failed on the device");
+    return fail(s, "device status %d", s);
+}
+
+// Install a factor structure: schedule on the host, arrays on the device.
+// values (optional) are the factor values in canonical order.
+int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st)
+{
+    h->S = std::move(S);
+    const int resident_warps = h->ref_blocks_per_sm * h->sm_count * kRefWarpsPerBlock;
+    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->W);
+    for (int32_t v : h->W.amap)
+        if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
+    const int32_t n = h->S.n;
+    const size_t nnz = (size_t)h->S.nnz();
+    CK(upload(h, h->LUp, h->S.LUp, st));
+    CK(upload(h, h->LUi, h->S.LUi, st));
+    CK(upload(h, h->nU, h->S.nU, st));
+    CK(upload(h, h->piv, h->S.piv, st));
+    CK(upload(h, h->pinv, h->S.pinv, st));
+    CK(upload(h, h->level_cols, h->W.level_cols, st));
+    CK(upload(h, h->amap, h->W.amap, st));
+    CK(ensure(h, h->finish, n));
+    CK(ensure(h, h->lflag, n));
+    CK(ensure(h, h->uflag, n));
+    CK(ensure(h, h->y, n));
+    // canonical rows/vals; the pool is sized at restart time
+    if (h->rows.cap < nnz || h->vals.cap < nnz) {
+        CK(ensure(h, h->rows, nnz));
+        CK(ensure(h, h->vals, nnz));
+    }
+    CU(cudaMemcpyAsync(h->rows.p, h->W.LUi_orig.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (values)
+        CU(cudaMemcpyAsync(h->vals.p, values->data(), nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(upload(h, h->Lrp, h->W.Lrp, st));
+    CK(upload(h, h->Urp, h->W.Urp, st));
+    CK(upload(h, h->Lcol, h->W.Lcol, st));
+    CK(upload(h, h->Lslot, h->W.Lslot, st));
+    CK(upload(h, h->Ucol, h->W.Urow_col, st));
+    CK(upload(h, h->Uslot, h->W.Uslot, st));
+    CK(upload(h, h->Udiag, h->W.Udiag, st));
+    CK(upload(h, h->lsv_rows, h->W.lsv_rows, st));
+    CK(upload(h, h->usv_rows, h->W.usv_rows, st));
+    // host vectors are uploaded asynchronously: keep them alive until done
+    CU(cudaStreamSynchronize(st));
+    return GBLU_OK;
+}
+
+// Checked re-factorization on the installed structure (Algorithms 3 and 4).
+// *interrupted = 1 if a pivot failed the check.
+int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+{
+    const int32_t n = h->S.n;
+    h->epoch++;
+    KL(launch_begin_refactor(h->ctl, st));
+    RefactorArgs a{};
+    a.Ap = h->Ap.p;
+    a.Q = h->Q.p;
+    a.amap = h->amap.p;
+    a.Ax = Ax;
+    a.LUp = h->LUp.p;
+    a.LUi = h->LUi.p;
+    a.nU = h->nU.p;
+    a.LUx = h->vals.p;
+    a.finish = h->finish.p;
+    a.eps = h->opts.pivot_tol;
+    a.spin_limit = h->opts.spin_limit;
+    a.ctl = h->ctl;
+    const std::vector<int32_t> &lp = h->W.level_ptr;
+    int32_t div = h->W.div_level;
+    if (h->opts.sched_mode == GBLU_SCHED_LEVEL) div = h->W.n_levels;
+    if (h->opts.sched_mode == GBLU_SCHED_SYNCFREE) div = 0;
+    for (int32_t l = 0; l < div; l++) {
+        a.cols = h->level_cols.p + lp[l];
+        a.ncols = lp[l + 1] - lp[l];
+        KL(launch_refactor_level(a, h->smem_cap, h->epoch, st));
+    }
+    if (div < h->W.n_levels) {
+        a.cols = h->level_cols.p + lp[div];
+        a.ncols = n - lp[div];
+        KL(launch_refactor_syncfree(a, h->smem_cap, h->ref_grid, h->epoch, st));
+    }
+    CK(read_ctl(h, st));
+    CK(status_code(h));
+    *interrupted = h->hctl->interrupted;
+    h->last_first_bad = h->hctl->interrupted ? h->hctl->first_bad : -1;
+    return GBLU_OK;
+}
+
+// Restart (Section IV-C/D): recompute with pivoting every unfinished column
+// and its column-elimination-tree ancestors, then rebuild the structure.
+int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
+{
+    const Pattern &P = h->P;
+    const int32_t n = P.n;
+    const Structure &S = h->S;
+    const int64_t nnz = S.nnz();
+    // ---- which columns finished in this refactorization?
+    std::vector<int32_t> fin(n);
+    CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::vector<uint8_t> finished(n), rmask(n);
+    for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
+    const int64_t nR = gblu_restart_set(n, P.cetree.data(), finished.data(), rmask.data());
+    std::vector<int32_t> seq, rm(n);
+    seq.reserve(nR);
+    int64_t restart_len = 0;
+    for (int32_t k = 0; k < n; k++) {
+        rm[k] = rmask[k];
+        if (rmask[k]) {
+            seq.push_back(k);
+            restart_len += S.LUp[k + 1] - S.LUp[k];
+        }
+    }
+    // canonical descriptors for the columns that keep their values
+    std::vector<int64_t> cbeg(n);
+    std::vector<int32_t> cnu(n), cnl(n);
+    for (int32_t k = 0; k < n; k++) {
+        cbeg[k] = S.LUp[k];
+        cnu[k] = S.nU[k];
+        cnl[k] = (int32_t)(S.LUp[k + 1] - S.LUp[k]) - S.nU[k];
+    }
+    CK(upload(h, h->seq, seq, st));
+    CK(upload(h, h->restart, rm, st));
+    CK(upload(h, h->cbeg, cbeg, st));
+    CK(upload(h, h->cnu, cnu, st));
+    CK(upload(h, h->cnl, cnl, st));
+    CK(ensure(h, h->done, n));
+    CK(ensure(h, h->tpiv, n));
+    CK(ensure(h, h->tpinv, n));
+    // scratch: one dense work vector per CTA
+    int slots = std::min<int64_t>((int64_t)nR, (int64_t)h->sm_count * 2);
+    const size_t per_slot = (size_t)n * (sizeof(double) + 2 * sizeof(int32_t));
+    const size_t budget = (size_t)4 << 30;
+    slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)slots, budget / per_slot));
+    CK(ensure(h, h->sx, (size_t)slots * n));
+    CK(ensure(h, h->smark, (size_t)slots * n));
+    CK(ensure(h, h->slist, (size_t)slots * n));
+    // pool after the canonical columns
+    size_t pool = (size_t)std::max<int64_t>(2 * restart_len, (int64_t)P.Ai.size()) + (size_t)n;
+    for (int attempt = 0; attempt < 8; attempt++) {
+        const size_t need = (size_t)nnz + pool;
+        if (h->rows.cap < need || h->vals.cap < need) {
+            // grow, keeping the canonical region
+            DBuf<int32_t> nr;
+            DBuf<double> nv;
+            CK(ensure(h, nr, need));
+            CK(ensure(h, nv, need));
+            CU(cudaMemcpyAsync(nr.p, h->rows.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpyAsync(nv.p, h->vals.p, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            CU(cudaStreamSynchronize(st));
+            release(h, h->rows);
+            release(h, h->vals);
+            h->rows = nr;
+            h->vals = nv;
+        }
+        h->tail_epoch++;
+        KL(launch_begin_tail(h->ctl, (unsigned long long)nnz, st));
+        KL(launch_tail_init(n, h->restart.p, h->piv.p, h->tpinv.p, h->tpiv.p, h->done.p, h->tail_epoch, st));
+        CU(cudaMemsetAsync(h->smark.p, 0, (size_t)slots * n * sizeof(int32_t), st));
+        TailArgs t{};
+        t.n = n;
+        t.Ap = h->Ap.p;
+        t.Ai = h->Ai.p;
+        t.Q = h->Q.p;
+        t.qinv = h->qinv.p;
+        t.Ax = Ax;
+        t.seq = h->seq.p;
+        t.nseq = (int32_t)nR;
+        t.prefer = h->piv.p;
+        t.clo = h->clo.p;
+        t.pinv = h->tpinv.p;
+        t.piv = h->tpiv.p;
+        t.done = h->done.p;
+        t.cbeg = h->cbeg.p;
+        t.cnu = h->cnu.p;
+        t.cnl = h->cnl.p;
+        t.rows = h->rows.p;
+        t.vals = h->vals.p;
+        t.pool_base = (unsigned long long)nnz;
+        t.pool_end = (unsigned long long)(nnz + pool);
+        t.sx = h->sx.p;
+        t.smark = h->smark.p;
+        t.slist = h->slist.p;
+        t.eps = h->opts.pivot_tol;
+        t.spin_limit = h->opts.spin_limit;
+        t.ctl = h->ctl;
+        KL(launch_tail(t, slots, h->tail_epoch, st));
+        CK(read_ctl(h, st));
+        if (h->hctl->status == GBLU_INTERNAL_POOL_FULL) {
+            pool *= 2;
+            continue;
+        }
+        CK(status_code(h));
+        break;
+    }
+    if (h->hctl->status != 0) return fail(GBLU_ERR_NOMEM, "restart pool could not be sized");
+    const unsigned long long top = h->hctl->pool_top;
+    // ---- download and repack into the new canonical structure
+    std::vector<int32_t> tpiv(n), rows(top);
+    std::vector<double> vals(top);
+    CU(cudaMemcpyAsync(tpiv.data(), h->tpiv.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(cbeg.data(), h->cbeg.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(cnu.data(), h->cnu.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(cnl.data(), h->cnl.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    if (top) {
+        CU(cudaMemcpyAsync(rows.data(), h->rows.p, sizeof(int32_t) * top, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(vals.data(), h->vals.p, sizeof(double) * top, cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    std::vector<int32_t> pinv_new(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        if (tpiv[k] < 0 || tpiv[k] >= n || pinv_new[tpiv[k]] >= 0)
+            return fail(GBLU_ERR_INTERNAL, "restart produced an invalid pivot sequence");
+        pinv_new[tpiv[k]] = k;
+    }
+    Structure S2;
+    S2.n = n;
+    S2.piv = tpiv;
+    S2.pinv = pinv_new;
+    S2.LUp.assign(n + 1, 0);
+    S2.nU.assign(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        S2.nU[k] = cnu[k];
+        S2.LUp[k + 1] = S2.LUp[k] + cnu[k] + cnl[k];
+    }
+    if (S2.LUp[n] > INT32_MAX) return fail(GBLU_ERR_NOMEM, "factor too large (> 2^31 entries)");
+    S2.LUi.assign(S2.LUp[n], 0);
+    std::vector<double> V2(S2.LUp[n]);
+    std::vector<std::pair<int32_t, double>> tmp;
+    for (int32_t k = 0; k < n; k++) {
+        const int64_t b = cbeg[k];
+        int64_t o = S2.LUp[k];
+        // U part: step ids, unchanged numbering for kept columns
+        tmp.clear();
+        for (int64_t e = b; e < b + cnu[k]; e++)
+            tmp.push_back({rmask[k] ? rows[e] : S.LUi[e], vals[e]});
+        std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
+        for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
+        // L part: original rows (pool) or old step ids (kept) -> new step ids
+        tmp.clear();
+        for (int64_t e = b + cnu[k]; e < b + cnu[k] + cnl[k]; e++) {
+            const int32_t orig = rmask[k] ? rows[e] : S.piv[S.LUi[e]];
+            tmp.push_back({pinv_new[orig], vals[e]});
+        }
+        std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
+        for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
+        if (S2.LUi[S2.LUp[k] + S2.nU[k] - 1] != k)
+            return fail(GBLU_ERR_INTERNAL, "restart: diagonal misplaced in column %d", k);
+    }
+    h->n_restart_cols = nR;
+    CK(install_structure(h, std::move(S2), &V2, st));
+    return GBLU_OK;
+}
+
+int check_handle(gblu_ctx *h)
+{
+    if (!h) return fail(GBLU_ERR_INVALID_INPUT, "null handle");
+    if (!h->analyzed) return fail(GBLU_ERR_NOT_ANALYZED, "gblu_analyze has not been called");
+    return GBLU_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void gblu_default_opts(gblu_opts *o)
+{
+    if (!o) return;
+    o->pivot_tol = 1e-3;
+    o->sched_mode = GBLU_SCHED_AUTO;
+    o->solve_mode = GBLU_SCHED_AUTO;
+    o->alpha = 2.0;
+    o->spin_limit = 1LL << 24;
+}
+
+const char *gblu_last_error(void) { return g_err.c_str(); }
+
+int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
+{
+    if (!out) return fail(GBLU_ERR_INVALID_INPUT, "null output pointer");
+    *out = nullptr;
+    gblu_ctx *h = new (std::nothrow) gblu_ctx();
+    if (!h) return fail(GBLU_ERR_NOMEM, "host allocation failed");
+    gblu_default_opts(&h->opts);
+    if (o) h->opts = *o;
+    if (!(h->opts.pivot_tol >= 0.0 && h->opts.pivot_tol <= 1.0) || h->opts.spin_limit <= 0 ||
+        h->opts.sched_mode < 0 || h->opts.sched_mode > 2 || h->opts.solve_mode < 0 ||
+        h->opts.solve_mode > 2 || !(h->opts.alpha >= 0.0)) {
+        delete h;
+        return fail(GBLU_ERR_INVALID_INPUT, "invalid options");
+    }
+    h->device = device;
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete h;
+        return fail(GBLU_ERR_CUDA, "cannot use CUDA device %d", device);
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hctl, sizeof(DevCtl));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->ctl, sizeof(DevCtl));
+    if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(DevCtl));
+    int r = 0;
+    if (e == cudaSuccess) r = refactor_max_resident_blocks(h->smem_cap, &h->ref_blocks_per_sm);
+    if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
+    if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
+        const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
+        if (h->hctl) cudaFreeHost(h->hctl);
+        if (h->ctl) cudaFree(h->ctl);
+        delete h;
+        cudaGetLastError();
+        return fail(GBLU_ERR_CUDA, "device setup failed: %s", msg);
+    }
+    h->ref_grid = h->ref_blocks_per_sm * h->sm_count;
+    h->res_blocks = h->sm_count * 4;
+    *out = h;
+    return GBLU_OK;
+}
+
+void gblu_destroy(gblu_handle h)
+{
+    if (!h) return;
+    {
+        DeviceGuard g(h->device);
+        cudaDeviceSynchronize();
+        release(h, h->Ap); release(h, h->Ai); release(h, h->Q); release(h, h->qinv);
+        release(h, h->clo); release(h, h->Acol); release(h, h->Aslot); release(h, h->Arp);
+        release(h, h->LUp); release(h, h->LUi); release(h, h->nU); release(h, h->rows);
+        release(h, h->finish); release(h, h->level_cols); release(h, h->amap);
+        release(h, h->piv); release(h, h->pinv); release(h, h->vals);
+        release(h, h->Lrp); release(h, h->Urp); release(h, h->Lcol); release(h, h->Lslot);
+        release(h, h->Ucol); release(h, h->Uslot); release(h, h->Udiag);
+        release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->lflag);
+        release(h, h->uflag); release(h, h->y); release(h, h->partial);
+        release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
+        release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
+        release(h, h->tpinv); release(h, h->cnu); release(h, h->cnl); release(h, h->smark);
+        release(h, h->slist); release(h, h->cbeg); release(h, h->sx);
+        if (h->ctl) cudaFree(h->ctl);
+        if (h->hctl) cudaFreeHost(h->hctl);
+    }
+    delete h;
+}
+
+int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)
+{
+    if (!h) return fail(GBLU_ERR_INVALID_INPUT, "null handle");
+    std::string err;
+    int rc = validate_pattern(n, Ap, Ai, err);
+    if (rc != GBLU_OK) return fail(rc, "invalid pattern: %s", err.c_str());
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GBLU_ERR_CUDA, "cannot use CUDA device %d", h->device);
+    h->analyzed = false;
+    h->factorized = false;
+    Pattern &P = h->P;
+    P = Pattern();
+    P.n = n;
+    P.Ap.assign(Ap, Ap + n + 1);
+    P.Ai.assign(Ai, Ai + Ap[n]);
+    P.Q.assign(n, 0);
+    if (Q) {
+        std::vector<uint8_t> seen(n, 0);
+        for (int32_t k = 0; k < n; k++) {
+            if (Q[k] < 0 || Q[k] >= n || seen[Q[k]]) return fail(GBLU_ERR_INVALID_INPUT, "Q is not a permutation");
+            seen[Q[k]] = 1;
+            P.Q[k] = Q[k];
+        }
+    } else {
+        mindeg_order(n, Ap, Ai, P.Q.data());
+    }
+    P.qinv.assign(n, 0);
+    for (int32_t k = 0; k < n; k++) P.qinv[P.Q[k]] = k;
+    column_etree(P, P.cetree);
+    P.clo.resize(n);
+    std::vector<int32_t> depth(n, 0);
+    for (int32_t k = 0; k < n; k++) P.clo[k] = k;
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = P.cetree[k];
+        if (p >= 0) P.clo[p] = std::min(P.clo[p], P.clo[k]);
+    }
+    P.cetree_height = 0;
+    for (int32_t k = n - 1; k >= 0; k--) {
+        const int32_t p = P.cetree[k];
+        depth[k] = p >= 0 ? depth[p] + 1 : 1;
+        P.cetree_height = std::max(P.cetree_height, depth[k]);
+    }
+    // row-wise copy of A for the residual
+    P.Arp.assign(n + 1, 0);
+    for (int32_t p = 0; p < Ap[n]; p++) P.Arp[Ai[p] + 1]++;
+    for (int32_t i = 0; i < n; i++) P.Arp[i + 1] += P.Arp[i];
+    P.Acol.assign(Ap[n], 0);
+    P.Aslot.assign(Ap[n], 0);
+    {
+        std::vector<int64_t> pos(P.Arp.begin(), P.Arp.end() - 1);
+        for (int32_t c = 0; c < n; c++)
+            for (int32_t p = Ap[c]; p < Ap[c + 1]; p++) {
+                P.Acol[pos[Ai[p]]] = c;
+                P.Aslot[pos[Ai[p]]++] = p;
+            }
+    }
+    cudaStream_t st = 0;
+    CK(upload(h, h->Ap, P.Ap, st));
+    CK(upload(h, h->Ai, P.Ai, st));
+    CK(upload(h, h->Q, P.Q, st));
+    CK(upload(h, h->qinv, P.qinv, st));
+    CK(upload(h, h->clo, P.clo, st));
+    CK(upload(h, h->Arp, P.Arp, st));
+    CK(upload(h, h->Acol, P.Acol, st));
+    CK(upload(h, h->Aslot, P.Aslot, st));
+    CK(ensure(h, h->partial, (size_t)3 * h->res_blocks));
+    CU(cudaStreamSynchronize(st));
+    h->analyzed = true;
+    return GBLU_OK;
+}
+
+int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
+{
+    CK(check_handle(h));
+    if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->factorized = false;
+    Structure S;
+    std::string err;
+    int rc = guess_structure(h->P, S, err);
+    if (rc != GBLU_OK) return fail(rc, "%s", err.c_str());
+    CK(install_structure(h, std::move(S), nullptr, st));
+    int interrupted = 0;
+    CK(run_refactor(h, Ax_dev, st, &interrupted));
+    if (interrupted) CK(run_restart(h, Ax_dev, st));
+    h->factorized = true;
+    return GBLU_OK;
+}
+
+int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t *repivoted)
+{
+    CK(check_handle(h));
+    if (repivoted) *repivoted = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int interrupted = 0;
+    h->n_refactor++;
+    int rc = run_refactor(h, Ax_dev, st, &interrupted);
+    if (rc != GBLU_OK) {
+        h->factorized = false;
+        return rc;
+    }
+    if (!interrupted) return GBLU_OK;
+    h->n_repivot++;
+    rc = run_restart(h, Ax_dev, st);
+    if (rc != GBLU_OK) {
+        h->factorized = false;
+        return rc;
+    }
+    if (repivoted) *repivoted = 1;
+    return GBLU_REPIVOTED;
+}
+
+int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
+{
+    CK(check_handle(h));
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
+    if (!b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = h->S.n;
+    h->solve_epoch++;
+    KL(launch_begin_solve(h->ctl, st));
+    SolveArgs a{};
+    a.n = n;
+    a.LUx = h->vals.p;
+    a.Lrp = h->Lrp.p;
+    a.Urp = h->Urp.p;
+    a.Lcol = h->Lcol.p;
+    a.Lslot = h->Lslot.p;
+    a.Ucol = h->Ucol.p;
+    a.Uslot = h->Uslot.p;
+    a.Udiag = h->Udiag.p;
+    a.piv = h->piv.p;
+    a.Q = h->Q.p;
+    a.b = b_dev;
+    a.y = h->y.p;
+    a.x = x_dev;
+    a.lflag = h->lflag.p;
+    a.uflag = h->uflag.p;
+    a.spin_limit = h->opts.spin_limit;
+    a.ctl = h->ctl;
+    const Schedule &W = h->W;
+    for (int pass = 0; pass < 2; pass++) {
+        const bool lower = pass == 0;
+        const std::vector<int32_t> &ptr = lower ? W.lsv_ptr : W.usv_ptr;
+        const int32_t nlev = lower ? W.lsv_levels : W.usv_levels;
+        int32_t div = lower ? W.lsv_div : W.usv_div;
+        if (h->opts.solve_mode == GBLU_SCHED_LEVEL) div = nlev;
+        if (h->opts.solve_mode == GBLU_SCHED_SYNCFREE) div = 0;
+        int32_t *rows = lower ? h->lsv_rows.p : h->usv_rows.p;
+        for (int32_t l = 0; l < div; l++) {
+            a.rows = rows + ptr[l];
+            a.nrows = ptr[l + 1] - ptr[l];
+            KL(lower ? launch_lsolve(a, true, 0, h->solve_epoch, st)
+                     : launch_usolve(a, true, 0, h->solve_epoch, st));
+        }
+        if (div < nlev) {
+            KL(launch_flag_rows(rows, ptr[div], lower ? h->lflag.p : h->uflag.p, h->solve_epoch, st));
+            a.rows = rows + ptr[div];
+            a.nrows = n - ptr[div];
+            KL(lower ? launch_lsolve(a, false, h->solve_grid, h->solve_epoch, st)
+                     : launch_usolve(a, false, h->solve_grid, h->solve_epoch, st));
+        }
+    }
+    return GBLU_OK;
+}
+
+int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host, double *x_host,
+                   void *stream, int32_t *repivoted)
+{
+    CK(check_handle(h));
+    if (repivoted) *repivoted = 0;
+    if (!Ax_host || !b_host || !x_host) return fail(GBLU_ERR_INVALID_INPUT, "null host pointer");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nnz = h->P.Ai.size(), n = (size_t)h->P.n;
+    CK(ensure(h, h->stage_ax, nnz));
+    CK(ensure(h, h->stage_b, n));
+    CK(ensure(h, h->stage_x, n));
+    CU(cudaMemcpyAsync(h->stage_ax.p, Ax_host, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(h->stage_b.p, b_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    const int rc = gblu_refactorize(h, h->stage_ax.p, stream, repivoted);
+    if (rc < 0) return rc;
+    CK(gblu_solve(h, h->stage_b.p, h->stage_x.p, stream));
+    CU(cudaMemcpyAsync(x_host, h->stage_x.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int gblu_residual(gblu_handle h, const double *Ax_dev, const double *b_dev, const double *x_dev,
+                  double *out_dev, void *stream)
+{
+    CK(check_handle(h));
+    if (!Ax_dev || !b_dev || !x_dev || !out_dev) return fail(GBLU_ERR_INVALID_INPUT, "null pointer");
+    DeviceGuard g(h->device);
+    KL(launch_residual(h->P.n, h->Arp.p, h->Acol.p, h->Aslot.p, Ax_dev, b_dev, x_dev, out_dev,
+                       h->partial.p, h->res_blocks, (cudaStream_t)stream));
+    h->launches++;  // the residual is two kernels
+    return GBLU_OK;
+}
+
+int gblu_get_stats(gblu_handle h, gblu_stats *s)
+{
+    if (!h || !s) return fail(GBLU_ERR_INVALID_INPUT, "null pointer");
+    std::memset(s, 0, sizeof(*s));
+    s->n = h->P.n;
+    s->nnz_a = (int64_t)h->P.Ai.size();
+    s->etree_height = h->P.cetree_height;
+    s->n_refactor = h->n_refactor;
+    s->n_repivot = h->n_repivot;
+    s->n_restart_cols = h->n_restart_cols;
+    s->last_first_bad = h->last_first_bad;
+    s->device_bytes = (int64_t)h->device_bytes;
+    s->kernel_launches = h->launches;
+    if (h->factorized) {
+        int64_t nu = 0;
+        for (int32_t v : h->S.nU) nu += v;
+        s->nnz_u = nu;
+        s->nnz_l = h->S.nnz() - nu;
+        s->flops = h->W.flops;
+        s->n_levels = h->W.n_levels;
+        s->div_level = h->W.div_level;
+        s->n_solve_levels_l = h->W.lsv_levels;
+        s->n_solve_levels_u = h->W.usv_levels;
+    }
+    return GBLU_OK;
+}
+
+int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx, int64_t *Up,
+                        int32_t *Ui, double *Ux, int32_t *piv, int32_t *q)
+{
+    CK(check_handle(h));
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
+    DeviceGuard g(h->device);
+    const Structure &S = h->S;
+    const int32_t n = S.n;
+    std::vector<double> v(S.nnz());
+    CU(cudaDeviceSynchronize());
+    if (!v.empty()) CU(cudaMemcpy(v.data(), h->vals.p, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    int64_t lo = 0, uo = 0;
+    if (Lp) Lp[0] = 0;
+    if (Up) Up[0] = 0;
+    for (int32_t k = 0; k < n; k++) {
+        for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++) {
+            if (e - S.LUp[k] < S.nU[k]) {
+                if (Ui) Ui[uo] = S.LUi[e];
+                if (Ux) Ux[uo] = v[e];
+                uo++;
+            } else {
+                if (Li) Li[lo] = S.LUi[e];
+                if (Lx) Lx[lo] = v[e];
+                lo++;
+            }
+        }
+        if (Lp) Lp[k + 1] = lo;
+        if (Up) Up[k + 1] = uo;
+    }
+    if (piv) std::memcpy(piv, S.piv.data(), sizeof(int32_t) * n);
+    if (q) std::memcpy(q, h->P.Q.data(), sizeof(int32_t) * n);
+    return GBLU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations shared by the host symbolic code (symbolic.cpp),
+// the kernels (kernels.cu) and the entry points (capi.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gblu.h"
+
+namespace gblu {
+
+// ---------------------------------------------------------------- host side
+// Validated copy of the input pattern.
+struct Pattern {
+    int32_t n = 0;
+    std::vector<int32_t> Ap, Ai;  // caller slot order
+    std::vector<int32_t> Q, qinv; // column order and its inverse
+    std::vector<int32_t> cetree;  // column elimination tree of A(:,Q), by step
+    std::vector<int32_t> clo;     // smallest step in the cetree subtree of each step
+    int32_t cetree_height = 0;
+    // row-wise copy of A for the residual: Arp[n+1], Acol[nnz], Aslot[nnz]
+    std::vector<int64_t> Arp;
+    std::vector<int32_t> Acol, Aslot;
+};
+
+// Fixed-pattern factor structure in step numbering (CSC, per column: the U
+// rows ascending with the diagonal last, then the L rows ascending).
+struct Structure {
+    int32_t n = 0;
+    std::vector<int64_t> LUp;  // n+1
+    std::vector<int32_t> LUi;  // step numbers
+    std::vector<int32_t> nU;   // U entries of each column incl. the diagonal
+    std::vector<int32_t> piv;  // original row pivotal at each step
+    std::vector<int32_t> pinv;
+    int64_t nnz() const { return LUp.empty() ? 0 : LUp.back(); }
+};
+
+// Everything derived from a Structure that the kernels use.
+struct Schedule {
+    // refactor: EGraph levels (Section II-B) and dual-mode split
+    std::vector<int32_t> level_ptr;   // n_levels+1
+    std::vector<int32_t> level_cols;  // columns sorted by level
+    int32_t n_levels = 0;
+    int32_t div_level = 0;            // levels [div_level, n_levels) run sync-free
+    std::vector<int32_t> amap;        // A slot -> position inside its column
+    std::vector<int32_t> LUi_orig;    // L entries: original row ids (U: step ids)
+    double flops = 0;
+    // solves: row-wise (CSR) copies, slots into the factor value array
+    std::vector<int64_t> Lrp, Urp;        // n+1
+    std::vector<int32_t> Lcol, Urow_col;  // column (step) of each entry
+    std::vector<int32_t> Lslot, Uslot;    // slot in LUx
+    std::vector<int32_t> Udiag;           // slot of U(i,i)
+    std::vector<int32_t> lsv_ptr, lsv_rows; int32_t lsv_levels = 0, lsv_div = 0;
+    std::vector<int32_t> usv_ptr, usv_rows; int32_t usv_levels = 0, usv_div = 0;
+};
+
+int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
+void column_etree(const Pattern &P, std::vector<int32_t> &parent);
+void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+// guessed structure: pattern of the Cholesky factor of (A + A^T)(Q,Q) with
+// diagonal pivots piv = Q
+int guess_structure(const Pattern &P, Structure &S, std::string &err);
+void build_schedule(const Pattern &P, const Structure &S, double alpha,
+                    int resident_warps, Schedule &W);
+int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
+                  const int32_t *nU_or_null, std::vector<int32_t> &level);
+
+// ---------------------------------------------------------------- device side
+// Control block in device memory (one per handle).
+struct DevCtl {
+    int32_t epoch;        // refactor epoch stored in finish[] on completion
+    int32_t ticket;       // sync-free ticket counter
+    int32_t interrupted;  // a pivot failed the check (Algorithms 3/4)
+    int32_t first_bad;    // smallest failing column
+    int32_t status;       // first error code (GBLU_ERR_*), 0 = none
+    int32_t solve_epoch;  // epoch of the solve ready flags
+    int32_t ticket_l, ticket_u;
+    int32_t tail_epoch;   // epoch of the tail factorization done flags
+    int32_t tail_ticket;
+    int32_t abort_tail;   // singular / overflow seen by the tail kernel
+    int32_t pad;
+    unsigned long long pool_top;  // next free slot of the tail pool
+    int32_t where;        // diagnostic: which wait timed out
+    int32_t where_k;
+};
+
+#define GBLU_INTERNAL_POOL_FULL (-100)
+
+struct RefactorArgs {
+    const int32_t *Ap, *Q, *amap;   // A pattern (column pointers), order, slot map
+    const double *Ax;               // new values (caller slot order)
+    const int64_t *LUp;
+    const int32_t *LUi, *nU;
+    double *LUx;
+    int32_t *finish;
+    const int32_t *cols;            // level_cols (level mode) or sequence (sync-free)
+    int32_t ncols;
+    double eps;
+    long long spin_limit;
+    DevCtl *ctl;
+};
+
+struct TailArgs {
+    int32_t n;
+    const int32_t *Ap, *Ai, *Q, *qinv;
+    const double *Ax;
+    const int32_t *seq;             // restart steps, ascending
+    int32_t nseq;
+    const int32_t *prefer;          // preferred original row per step
+    const int32_t *clo;             // cetree subtree lower bound per step
+    int32_t *pinv;                  // original row -> step (-1 = not pivotal)
+    int32_t *piv;                   // step -> original row
+    int32_t *done;                  // == tail_epoch when the step is final
+    // per-step column storage: entries [beg, beg+nu) are U (step ids, diagonal
+    // last) and [beg+nu, beg+nu+nl) are L (original row ids)
+    int64_t *cbeg;
+    int32_t *cnu, *cnl;
+    int32_t *rows;                  // canonical region: LUi_orig; pool after it
+    double *vals;                   // canonical region: LUx; pool after it
+    unsigned long long pool_base, pool_end;
+    // per-CTA scratch
+    double *sx;
+    int32_t *smark, *slist;
+    double eps;
+    long long spin_limit;
+    DevCtl *ctl;
+};
+
+struct SolveArgs {
+    int32_t n;
+    const double *LUx;
+    const int64_t *Lrp, *Urp;
+    const int32_t *Lcol, *Lslot, *Ucol, *Uslot, *Udiag;
+    const int32_t *piv, *Q;
+    const double *b;
+    double *y, *x;
+    int32_t *lflag, *uflag;
+    const int32_t *rows;            // level-mode row list
+    int32_t nrows;
+    long long spin_limit;
+    DevCtl *ctl;
+};
+
+// kernel launchers (kernels.cu); each returns a cudaError_t as int
+int launch_begin_refactor(DevCtl *ctl, void *stream);
+int launch_refactor_level(const RefactorArgs &a, int smem_cap, int epoch, void *stream);
+int launch_refactor_syncfree(const RefactorArgs &a, int smem_cap, int grid, int epoch, void *stream);
+int refactor_max_resident_blocks(int smem_cap, int *blocks_per_sm);
+int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
+int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
+                     int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
+int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
+int launch_begin_solve(DevCtl *ctl, void *stream);
+int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream);
+int launch_usolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream);
+int launch_flag_rows(const int32_t *rows, int nrows, int32_t *flag, int epoch, void *stream);
+int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
+                    const int32_t *Aslot, const double *Ax, const double *b,
+                    const double *x, double *out, double *partial, int nblocks,
+                    void *stream);
+int solve_syncfree_grid(int *grid);
+
+constexpr int kRefWarpsPerBlock = 4;
+constexpr int kTailThreads = 256;
+constexpr int kSolveWarpsPerBlock = 8;
+
+}  // namespace gblu

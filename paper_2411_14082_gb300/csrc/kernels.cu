@@ -1,0 +1,789 @@
+// Device kernels of the sparse LU path (sm_103a).
+//
+//  * refactor_*      fast re-factorization with pivot check (Section IV-B,
+//                    Algorithms 3 and 4): one warp per column, left-looking
+//                    updates into a work vector staged in shared memory;
+//                    level-synchronous launches (cluster mode) or one
+//                    persistent launch with ready flags (pipeline mode).
+//  * tail_kernel     factorization with threshold pivoting of a set of
+//                    columns (Section IV-D, Algorithm 5 and Algorithm 1):
+//                    one CTA per column, columns taken in increasing order
+//                    by an atomic ticket, waiting on ready flags of earlier
+//                    columns.
+//  * lsolve/usolve   triangular solves (Algorithm 2, Section V): one warp
+//                    per row on row-wise copies, level launches or ready
+//                    flags.
+//  * residual        ||b - A x||_inf / (||A||_inf ||x||_inf) in float64.
+//
+// Every wait is bounded by spin_limit iterations; on expiry the kernel
+// records GBLU_ERR_DEVICE_TIMEOUT in the control block and returns.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "gblu_internal.h"
+
+namespace gblu {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int32_t *p)
+{
+    return *(const volatile int32_t *)p;
+}
+
+__device__ __forceinline__ void set_status(DevCtl *ctl, int code)
+{
+    atomicCAS(&ctl->status, 0, code);
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// One column of the checked re-factorization, computed by one warp.
+//
+// Column k's pattern (sorted step numbers: U rows, diagonal k, L rows) is
+// the work vector's index set.  x = A(:,Q[k]) is scattered through amap;
+// then for every dependency j (U rows above the diagonal, ascending, which is
+// a topological order) x(rows of L(:,j)) -= x(j) * L(:,j).  The slot of an
+// L(:,j) row inside column k is found by binary search in the sorted
+// pattern, narrowed by the previous chunk's slot (rows and slots are both
+// strictly increasing).  Then the pivot check and the stores.
+//
+// Returns true when the warp has to stop (timeout or error in kWait mode).
+template <bool kWait>
+__device__ bool refactor_column(const RefactorArgs &a, int k, double *xs, int32_t *rs,
+                                int cap, int lane, int epoch)
+{
+    const int64_t beg = __ldg(a.LUp + k);
+    const int len = (int)(__ldg(a.LUp + k + 1) - beg);
+    const int nU = __ldg(a.nU + k);
+    const bool in_smem = len <= cap;
+    double *x = in_smem ? xs : a.LUx + beg;
+    const int32_t *rows = in_smem ? rs : a.LUi + beg;
+    for (int i = lane; i < len; i += 32) {
+        if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
+        x[i] = 0.0;
+    }
+    __syncwarp();
+    {
+        const int c = __ldg(a.Q + k);
+        const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
+        for (int e = ab + lane; e < ae; e += 32) {
+            const int s = __ldg(a.amap + e);
+            if (s >= 0 && s < len) x[s] = __ldg(a.Ax + e);
+            else set_status(a.ctl, GBLU_ERR_INTERNAL);
+        }
+    }
+    __syncwarp();
+
+    int ready = 0;  // dependencies [0, ready) are known to be finished
+    for (int t = 0; t < nU - 1; ++t) {
+        const int j = rows[t];
+        if (kWait && t >= ready) {
+            const int tt = t + lane;
+            bool ok = true;
+            if (tt < nU - 1) ok = ld_acquire(a.finish + rows[tt]) == epoch;
+            const unsigned m = __ballot_sync(kFull, ok);
+            int run = (m == kFull) ? 32 : __ffs(~m) - 1;
+            if (run == 0) {
+                long long it = 0;
+                for (;;) {
+                    if (ld_acquire(a.finish + j) == epoch) break;
+                    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return true;
+                    if (++it > a.spin_limit) {
+                        if (lane == 0) {
+                            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                            a.ctl->where = 1;
+                            a.ctl->where_k = k;
+                        }
+                        return true;
+                    }
+                    __nanosleep(64);
+                }
+                run = 1;
+            }
+            ready = t + run;
+            __syncwarp();
+        }
+        const double xj = x[t];
+        const int64_t lb = __ldg(a.LUp + j) + __ldg(a.nU + j);
+        const int64_t le = __ldg(a.LUp + j + 1);
+        int bslot = t, brow = j;
+        for (int64_t e0 = lb; e0 < le; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const bool act = e < le;
+            int r = INT_MAX, s = 0;
+            double v = 0.0;
+            bool bad = false;
+            if (act) {
+                r = __ldg(a.LUi + e);
+                v = __ldcg(a.LUx + e);
+                int lo = bslot + 1 + lane;
+                int hi = bslot + (r - brow);
+                if (hi > len - 1) hi = len - 1;
+                if (lo > hi) {
+                    bad = true;
+                } else {
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (rows[mid] < r) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    s = lo;
+                    bad = rows[s] != r;
+                }
+            }
+            if (__any_sync(kFull, bad)) {  // pattern inconsistent: never index with it
+                if (lane == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
+                return true;
+            }
+            if (act) x[s] = fma(-xj, v, x[s]);
+            const int last = (le - e0 >= 32) ? 31 : (int)(le - e0 - 1);
+            bslot = __shfl_sync(kFull, s, last);
+            brow = __shfl_sync(kFull, r, last);
+        }
+        __syncwarp();
+    }
+
+    // ---- pivot check (Algorithm 3 line 8 / Algorithm 4 line 10) ----
+    const double d = x[nU - 1];
+    double m = 0.0;
+    for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
+    m = warp_max(m);
+    const bool pass = (d != 0.0) && (fabs(d) >= a.eps * m);
+    if (!pass) {
+        if (lane == 0) {
+            atomicExch(&a.ctl->interrupted, 1);
+            atomicMin(&a.ctl->first_bad, k);
+        }
+        return false;
+    }
+    // ---- store U(:,k) and L(:,k) = x / pivot ----
+    if (in_smem) {
+        for (int i = lane; i < len; i += 32) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] / d;
+    } else {
+        for (int i = nU + lane; i < len; i += 32) x[i] = x[i] / d;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(a.finish + k, epoch);
+    return false;
+}
+
+__global__ void begin_refactor_kernel(DevCtl *ctl)
+{
+    ctl->ticket = 0;
+    ctl->interrupted = 0;
+    ctl->first_bad = INT_MAX;
+    ctl->status = 0;
+    ctl->where = 0;
+    ctl->where_k = -1;
+}
+
+__global__ void __launch_bounds__(kRefWarpsPerBlock * 32)
+refactor_level_kernel(RefactorArgs a, int cap, int epoch)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *xs = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)kRefWarpsPerBlock * cap * sizeof(double)) +
+                  (size_t)warp * cap;
+    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return;
+    const int idx = blockIdx.x * kRefWarpsPerBlock + warp;
+    if (idx >= a.ncols) return;
+    refactor_column<false>(a, __ldg(a.cols + idx), xs, rs, cap, lane, epoch);
+}
+
+__global__ void __launch_bounds__(kRefWarpsPerBlock * 32)
+refactor_syncfree_kernel(RefactorArgs a, int cap, int epoch)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *xs = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)kRefWarpsPerBlock * cap * sizeof(double)) +
+                  (size_t)warp * cap;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctl->ticket, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.ncols) break;
+        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) break;
+        if (refactor_column<true>(a, __ldg(a.cols + t), xs, rs, cap, lane, epoch)) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Factorization with threshold pivoting of the columns in a.seq (ascending),
+// one CTA per column, columns handed out by an atomic ticket.
+//
+// Column k: scatter A(:,Q[k]) into a dense work vector x (original row ids)
+// with a stamp array for the structure; then sweep the earlier steps j of
+// k's column-elimination subtree range [clo[k], k) in increasing order.
+// Step j is a dependency iff its pivot row is already in the structure;
+// applying it, x(rows of L(:,j)) -= x(piv[j]) * L(:,j), may add rows and so
+// create later dependencies, which the ascending sweep meets afterwards.  A
+// step that is not finished yet is waited for (its pivot decides whether it
+// is a dependency).  Then threshold pivoting with the preferred row, exactly
+// as the oracle defines it, and the column is appended to the pool.
+__device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
+                            int32_t *list, int epoch)
+{
+    __shared__ int s_cnt, s_found, s_mode, s_stop;
+    __shared__ double r_m[kTailThreads / 32], r_ba[kTailThreads / 32];
+    __shared__ int r_bq[kTailThreads / 32], r_br[kTailThreads / 32];
+    __shared__ int r_nu[kTailThreads / 32], r_nc[kTailThreads / 32], r_pc[kTailThreads / 32];
+    __shared__ int s_piv, s_nu, s_nc;
+    __shared__ unsigned long long s_off;
+    __shared__ int s_u, s_l;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int stamp = k + 1;
+    if (tid == 0) { s_cnt = 0; s_stop = 0; }
+    __syncthreads();
+    {
+        const int c = __ldg(a.Q + k);
+        for (int e = __ldg(a.Ap + c) + tid; e < __ldg(a.Ap + c + 1); e += kTailThreads) {
+            const int r = __ldg(a.Ai + e);
+            x[r] = __ldg(a.Ax + e);
+            mark[r] = stamp;
+            list[atomicAdd(&s_cnt, 1)] = r;
+        }
+    }
+    __syncthreads();
+    int j = __ldg(a.clo + k);
+    while (j < k) {
+        if (warp == 0) {
+            int found = k, mode = 0;
+            for (int base = j; base < k; base += 32) {
+                const int jj = base + lane;
+                bool notready = false, dep = false;
+                if (jj < k) {
+                    if (ld_acquire(a.done + jj) != epoch) notready = true;
+                    else dep = mark[__ldcg(a.piv + jj)] == stamp;
+                }
+                const unsigned nr = __ballot_sync(kFull, notready);
+                const unsigned dp = __ballot_sync(kFull, dep);
+                const unsigned any = nr | dp;
+                if (any) {
+                    const int l = __ffs(any) - 1;
+                    found = base + l;
+                    mode = ((nr >> l) & 1u) ? 2 : 1;
+                    break;
+                }
+            }
+            if (lane == 0) { s_found = found; s_mode = mode; }
+        }
+        __syncthreads();
+        const int found = s_found, mode = s_mode;
+        if (found >= k) break;
+        if (mode == 2) {
+            if (tid == 0) {
+                long long it = 0;
+                while (ld_acquire(a.done + found) != epoch) {
+                    if (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status)) { s_stop = 1; break; }
+                    if (++it > a.spin_limit) {
+                        set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                        a.ctl->where = 2;
+                        a.ctl->where_k = k;
+                        atomicExch(&a.ctl->abort_tail, 1);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __syncthreads();
+            if (s_stop) return true;
+            j = found;
+            continue;
+        }
+        // apply dependency `found`
+        {
+            const int jd = found;
+            const int pr = __ldcg(a.piv + jd);
+            const double xj = x[pr];
+            const int64_t b = __ldcg(a.cbeg + jd) + __ldcg(a.cnu + jd);
+            const int64_t e_end = b + __ldcg(a.cnl + jd);
+            for (int64_t e = b + tid; e < e_end; e += kTailThreads) {
+                const int r = __ldcg(a.rows + e);
+                const double v = __ldcg(a.vals + e);
+                if (mark[r] != stamp) {
+                    mark[r] = stamp;
+                    x[r] = 0.0;
+                    list[atomicAdd(&s_cnt, 1)] = r;
+                }
+                x[r] = fma(-xj, v, x[r]);
+            }
+        }
+        __syncthreads();
+        j = found + 1;
+    }
+
+    // ---- threshold pivoting (Algorithm 5 lines 14-15, preferred row) ----
+    const int cnt = s_cnt;
+    const int pref = __ldg(a.prefer + k);
+    double m = 0.0, ba = 0.0;
+    int bq = INT_MAX, br = -1, nu = 0, nc = 0, pc = 0;
+    for (int i = tid; i < cnt; i += kTailThreads) {
+        const int r = list[i];
+        if (__ldcg(a.pinv + r) >= 0) { nu++; continue; }
+        nc++;
+        const double av = fabs(x[r]);
+        if (r == pref) pc = 1;
+        else m = fmax(m, av);
+        const int q = __ldg(a.qinv + r);
+        if (av > 0.0 && (br < 0 || av > ba || (av == ba && q < bq))) { ba = av; bq = q; br = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(kFull, m, o));
+        const double oa = __shfl_xor_sync(kFull, ba, o);
+        const int oq = __shfl_xor_sync(kFull, bq, o), orr = __shfl_xor_sync(kFull, br, o);
+        if (orr >= 0 && (br < 0 || oa > ba || (oa == ba && oq < bq))) { ba = oa; bq = oq; br = orr; }
+        nu += __shfl_xor_sync(kFull, nu, o);
+        nc += __shfl_xor_sync(kFull, nc, o);
+        pc |= __shfl_xor_sync(kFull, pc, o);
+    }
+    if (lane == 0) { r_m[warp] = m; r_ba[warp] = ba; r_bq[warp] = bq; r_br[warp] = br; r_nu[warp] = nu; r_nc[warp] = nc; r_pc[warp] = pc; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < kTailThreads / 32; w++) {
+            m = fmax(m, r_m[w]);
+            if (r_br[w] >= 0 && (br < 0 || r_ba[w] > ba || (r_ba[w] == ba && r_bq[w] < bq))) {
+                ba = r_ba[w]; bq = r_bq[w]; br = r_br[w];
+            }
+            nu += r_nu[w];
+            nc += r_nc[w];
+            pc |= r_pc[w];
+        }
+        int piv = -1;
+        if (pc) {
+            const double xp = x[pref];
+            if (xp != 0.0 && fabs(xp) >= a.eps * m) piv = pref;
+        }
+        if (piv < 0) piv = br;
+        s_stop = 0;
+        if (piv < 0) {
+            set_status(a.ctl, GBLU_ERR_SINGULAR);
+            a.ctl->where_k = k;
+            atomicExch(&a.ctl->abort_tail, 1);
+            s_stop = 1;
+        } else {
+            const unsigned long long total = (unsigned long long)nu + (unsigned long long)nc;
+            const unsigned long long off = atomicAdd(&a.ctl->pool_top, total);
+            if (off + total > a.pool_end) {
+                set_status(a.ctl, GBLU_INTERNAL_POOL_FULL);
+                atomicExch(&a.ctl->abort_tail, 1);
+                s_stop = 1;
+            }
+            s_off = off;
+        }
+        s_piv = piv;
+        s_nu = nu;
+        s_nc = nc;
+        s_u = 0;
+        s_l = 0;
+    }
+    __syncthreads();
+    if (s_stop) return true;
+    const int piv = s_piv;
+    const unsigned long long off = s_off;
+    const int nuc = s_nu;
+    const double d = x[piv];
+    for (int i = tid; i < cnt; i += kTailThreads) {
+        const int r = list[i];
+        const int pj = __ldcg(a.pinv + r);
+        if (pj >= 0) {
+            const int p = atomicAdd(&s_u, 1);
+            a.rows[off + p] = pj;
+            a.vals[off + p] = x[r];
+        } else if (r != piv) {
+            const int p = atomicAdd(&s_l, 1);
+            a.rows[off + nuc + 1 + p] = r;
+            a.vals[off + nuc + 1 + p] = x[r] / d;
+        }
+    }
+    if (tid == 0) {
+        a.rows[off + nuc] = k;
+        a.vals[off + nuc] = d;
+        a.cbeg[k] = (int64_t)off;
+        a.cnu[k] = nuc + 1;
+        a.cnl[k] = s_nc - 1;
+        a.pinv[piv] = k;
+        a.piv[k] = piv;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(a.done + k, epoch);
+    return false;
+}
+
+__global__ void begin_tail_kernel(DevCtl *ctl, unsigned long long pool_base)
+{
+    ctl->tail_ticket = 0;
+    ctl->abort_tail = 0;
+    ctl->status = 0;
+    ctl->pool_top = pool_base;
+    ctl->where = 0;
+    ctl->where_k = -1;
+}
+
+__global__ void tail_init_kernel(int32_t n, const int32_t *restart, const int32_t *piv_old,
+                                 int32_t *pinv, int32_t *piv, int32_t *done, int epoch)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const bool rs = restart[k] != 0;
+        pinv[piv_old[k]] = rs ? -1 : k;
+        piv[k] = rs ? -1 : piv_old[k];
+        done[k] = rs ? 0 : epoch;
+    }
+}
+
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoch)
+{
+    __shared__ int s_t, s_quit;
+    double *x = a.sx + (size_t)blockIdx.x * a.n;
+    int32_t *mark = a.smark + (size_t)blockIdx.x * a.n;
+    int32_t *list = a.slist + (size_t)blockIdx.x * a.n;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_t = atomicAdd(&a.ctl->tail_ticket, 1);
+            s_quit = ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status);
+        }
+        __syncthreads();
+        const int t = s_t, quit = s_quit;
+        __syncthreads();
+        if (t >= a.nseq || quit) break;
+        if (tail_column(a, __ldg(a.seq + t), x, mark, list, epoch)) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves on row-wise copies (Algorithm 2): one warp per row; the
+// lanes split the row, the dot product is reduced in a fixed tree so that
+// the result does not depend on the schedule.
+__global__ void begin_solve_kernel(DevCtl *ctl)
+{
+    ctl->ticket_l = 0;
+    ctl->ticket_u = 0;
+}
+
+template <bool kWait>
+__device__ bool lsolve_row(const SolveArgs &a, int i, int lane, int epoch)
+{
+    double s = 0.0;
+    const int64_t rb = __ldg(a.Lrp + i), re = __ldg(a.Lrp + i + 1);
+    for (int64_t e = rb + lane; e < re; e += 32) {
+        const int j = __ldg(a.Lcol + e);
+        if (kWait) {
+            long long it = 0;
+            while (ld_acquire(a.lflag + j) != epoch) {
+                if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
+                    set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                    a.ctl->where = 3;
+                    a.ctl->where_k = i;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), __ldcg(a.y + j), s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        a.y[i] = __ldg(a.b + __ldg(a.piv + i)) - s;
+        if (kWait) {
+            __threadfence();
+            st_release(a.lflag + i, epoch);
+        }
+    }
+    return kWait && ld_volatile(&a.ctl->status) != 0;
+}
+
+template <bool kWait>
+__device__ bool usolve_row(const SolveArgs &a, int i, int lane, int epoch)
+{
+    double s = 0.0;
+    const int64_t rb = __ldg(a.Urp + i), re = __ldg(a.Urp + i + 1);
+    for (int64_t e = rb + lane; e < re; e += 32) {
+        const int j = __ldg(a.Ucol + e);
+        if (kWait) {
+            long long it = 0;
+            while (ld_acquire(a.uflag + j) != epoch) {
+                if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
+                    set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                    a.ctl->where = 4;
+                    a.ctl->where_k = i;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), __ldcg(a.y + j), s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        const double z = (__ldcg(a.y + i) - s) / __ldg(a.LUx + __ldg(a.Udiag + i));
+        a.y[i] = z;
+        a.x[__ldg(a.Q + i)] = z;
+        if (kWait) {
+            __threadfence();
+            st_release(a.uflag + i, epoch);
+        }
+    }
+    return kWait && ld_volatile(&a.ctl->status) != 0;
+}
+
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+lsolve_level_kernel(SolveArgs a)
+{
+    const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= a.nrows) return;
+    lsolve_row<false>(a, __ldg(a.rows + w), threadIdx.x & 31, 0);
+}
+
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+usolve_level_kernel(SolveArgs a)
+{
+    const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= a.nrows) return;
+    usolve_row<false>(a, __ldg(a.rows + w), threadIdx.x & 31, 0);
+}
+
+// Sync-free: the rows a.rows[0..nrows) are in a topological order; rows not
+// in the list are already final and flagged by the level kernels (flags are
+// set for them by flag_rows_kernel).
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+lsolve_syncfree_kernel(SolveArgs a, int epoch)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctl->ticket_l, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.nrows) break;
+        if (lsolve_row<true>(a, __ldg(a.rows + t), lane, epoch)) break;
+    }
+}
+
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+usolve_syncfree_kernel(SolveArgs a, int epoch)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctl->ticket_u, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.nrows) break;
+        if (usolve_row<true>(a, __ldg(a.rows + t), lane, epoch)) break;
+    }
+}
+
+__global__ void flag_rows_kernel(const int32_t *rows, int nrows, int32_t *flag, int epoch)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x)
+        flag[rows[i]] = epoch;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void residual_kernel(int32_t n, const int64_t *Arp, const int32_t *Acol,
+                                const int32_t *Aslot, const double *Ax, const double *b,
+                                const double *x, double *partial)
+{
+    __shared__ double sr[8], sa[8], sx[8];
+    double rmax = 0.0, amax = 0.0, xmax = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+        double s = 0.0, as = 0.0;
+        for (int64_t e = Arp[i] + lane; e < Arp[i + 1]; e += 32) {
+            const double v = Ax[Aslot[e]];
+            s = fma(v, x[Acol[e]], s);
+            as += fabs(v);
+        }
+        s = warp_sum(s);
+        as = warp_sum(as);
+        rmax = fmax(rmax, fabs(b[i] - s));
+        amax = fmax(amax, as);
+        xmax = fmax(xmax, fabs(x[i]));
+    }
+    if (lane == 0) { sr[warp] = rmax; sa[warp] = amax; sx[warp] = xmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) { rmax = fmax(rmax, sr[w]); amax = fmax(amax, sa[w]); xmax = fmax(xmax, sx[w]); }
+        partial[3 * blockIdx.x + 0] = rmax;
+        partial[3 * blockIdx.x + 1] = amax;
+        partial[3 * blockIdx.x + 2] = xmax;
+    }
+}
+
+__global__ void residual_final_kernel(const double *partial, int nblocks, double *out)
+{
+    double r = 0.0, a = 0.0, x = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 32) {
+        r = fmax(r, partial[3 * i]);
+        a = fmax(a, partial[3 * i + 1]);
+        x = fmax(x, partial[3 * i + 2]);
+    }
+    r = warp_max(r);
+    a = warp_max(a);
+    x = warp_max(x);
+    if (threadIdx.x == 0) {
+        out[0] = (a > 0.0 && x > 0.0) ? r / (a * x) : r;
+        out[1] = r;
+        out[2] = a;
+        out[3] = x;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+static size_t refactor_smem(int cap)
+{
+    return (size_t)kRefWarpsPerBlock * cap * (sizeof(double) + sizeof(int32_t));
+}
+
+int launch_begin_refactor(DevCtl *ctl, void *stream)
+{
+    begin_refactor_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
+    return (int)cudaGetLastError();
+}
+
+int refactor_max_resident_blocks(int smem_cap, int *blocks_per_sm)
+{
+    const size_t sm = refactor_smem(smem_cap);
+    cudaError_t e = cudaFuncSetAttribute(refactor_syncfree_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(refactor_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, refactor_syncfree_kernel, kRefWarpsPerBlock * 32, sm);
+}
+
+int launch_refactor_level(const RefactorArgs &a, int smem_cap, int epoch, void *stream)
+{
+    if (a.ncols <= 0) return 0;
+    const int grid = (a.ncols + kRefWarpsPerBlock - 1) / kRefWarpsPerBlock;
+    refactor_level_kernel<<<grid, kRefWarpsPerBlock * 32, refactor_smem(smem_cap), (cudaStream_t)stream>>>(
+        a, smem_cap, epoch);
+    return (int)cudaGetLastError();
+}
+
+int launch_refactor_syncfree(const RefactorArgs &a, int smem_cap, int grid, int epoch, void *stream)
+{
+    if (a.ncols <= 0) return 0;
+    refactor_syncfree_kernel<<<grid, kRefWarpsPerBlock * 32, refactor_smem(smem_cap), (cudaStream_t)stream>>>(
+        a, smem_cap, epoch);
+    return (int)cudaGetLastError();
+}
+
+int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream)
+{
+    begin_tail_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, pool_base);
+    return (int)cudaGetLastError();
+}
+
+int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
+                     int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream)
+{
+    const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    tail_init_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, restart_mask, piv_old, pinv, piv, done, epoch);
+    return (int)cudaGetLastError();
+}
+
+int launch_tail(const TailArgs &a, int grid, int epoch, void *stream)
+{
+    if (a.nseq <= 0) return 0;
+    tail_kernel<<<grid, kTailThreads, 0, (cudaStream_t)stream>>>(a, epoch);
+    return (int)cudaGetLastError();
+}
+
+int launch_begin_solve(DevCtl *ctl, void *stream)
+{
+    begin_solve_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
+    return (int)cudaGetLastError();
+}
+
+int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream)
+{
+    if (a.nrows <= 0) return 0;
+    if (level_mode) {
+        const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+        lsolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+    } else {
+        lsolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a, epoch);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_usolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream)
+{
+    if (a.nrows <= 0) return 0;
+    if (level_mode) {
+        const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+        usolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+    } else {
+        usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a, epoch);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_flag_rows(const int32_t *rows, int nrows, int32_t *flag, int epoch, void *stream)
+{
+    if (nrows <= 0) return 0;
+    const int grid = (nrows + 255) / 256 < 4096 ? (nrows + 255) / 256 : 4096;
+    flag_rows_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(rows, nrows, flag, epoch);
+    return (int)cudaGetLastError();
+}
+
+int solve_syncfree_grid(int *grid)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lsolve_syncfree_kernel,
+                                                                  kSolveWarpsPerBlock * 32, 0);
+    if (e != cudaSuccess) return (int)e;
+    int per2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, usolve_syncfree_kernel,
+                                                      kSolveWarpsPerBlock * 32, 0);
+    if (e != cudaSuccess) return (int)e;
+    *grid = sms * (per < per2 ? per : per2);
+    return 0;
+}
+
+int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol, const int32_t *Aslot,
+                    const double *Ax, const double *b, const double *x, double *out,
+                    double *partial, int nblocks, void *stream)
+{
+    residual_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(n, Arp, Acol, Aslot, Ax, b, x, partial);
+    residual_final_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nblocks, out);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace gblu

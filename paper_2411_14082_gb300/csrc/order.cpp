@@ -1,0 +1,104 @@
+// Minimum-degree fill-reducing ordering on the pattern of A + A^T
+// (pre-processing, Section III-A; the paper uses approximate minimum degree).
+//
+// Quotient-graph elimination: eliminating variable p turns it into an
+// element whose variable set Lp is the union of p's variable neighbours and
+// of the variable sets of p's element neighbours; those elements are
+// absorbed.  The degree of every variable i in Lp is then bounded by
+//     |A_i| + (|Lp| - 1) + sum over other elements e of i of |L_e \ Lp|,
+// the approximate external degree of Amestoy, Davis and Duff (1996).
+// Elements contained in Lp are absorbed as well.  Ties go to the lower
+// index, so the order is deterministic.
+#include <algorithm>
+#include <set>
+#include <vector>
+
+#include "gblu_internal.h"
+
+namespace gblu {
+
+void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    std::vector<std::vector<int32_t>> A(n), E(n), Lel(n);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = Ap[c]; p < Ap[c + 1]; p++) {
+            const int32_t r = Ai[p];
+            if (r == c) continue;
+            A[r].push_back(c);
+            A[c].push_back(r);
+        }
+    for (int32_t i = 0; i < n; i++) {
+        std::sort(A[i].begin(), A[i].end());
+        A[i].erase(std::unique(A[i].begin(), A[i].end()), A[i].end());
+    }
+    std::vector<char> elim(n, 0), alive(n, 0);
+    std::vector<int32_t> deg(n), mark(n, -1), wmark(n, -1);
+    std::vector<int64_t> w(n, 0);
+    std::set<std::pair<int32_t, int32_t>> pq;
+    for (int32_t i = 0; i < n; i++) {
+        deg[i] = (int32_t)A[i].size();
+        pq.insert({deg[i], i});
+    }
+    std::vector<int32_t> Lp;
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = pq.begin()->second;
+        pq.erase(pq.begin());
+        perm[k] = p;
+        elim[p] = 1;
+        // ---- element p: Lp = variables adjacent to p directly or via elements
+        Lp.clear();
+        mark[p] = k;
+        for (int32_t v : A[p])
+            if (!elim[v] && mark[v] != k) { mark[v] = k; Lp.push_back(v); }
+        for (int32_t e : E[p]) {
+            if (!alive[e]) continue;
+            for (int32_t v : Lel[e])
+                if (!elim[v] && mark[v] != k) { mark[v] = k; Lp.push_back(v); }
+            alive[e] = 0;  // absorbed into p
+            std::vector<int32_t>().swap(Lel[e]);
+        }
+        std::vector<int32_t>().swap(A[p]);
+        std::vector<int32_t>().swap(E[p]);
+        Lel[p] = Lp;
+        alive[p] = 1;
+        // ---- |L_e \ Lp| for the other elements next to Lp
+        for (int32_t i : Lp)
+            for (int32_t e : E[i]) {
+                if (!alive[e] || e == p) continue;
+                if (wmark[e] != k) { wmark[e] = k; w[e] = (int64_t)Lel[e].size(); }
+                w[e]--;
+            }
+        // ---- update the variables of Lp
+        const int32_t remaining = n - k - 1;
+        for (int32_t i : Lp) {
+            std::vector<int32_t> &Ei = E[i];
+            size_t o = 0;
+            int64_t ext = 0;
+            for (int32_t e : Ei) {
+                if (!alive[e] || e == p) continue;
+                if (wmark[e] == k && w[e] <= 0) {  // e inside Lp: absorb
+                    alive[e] = 0;
+                    std::vector<int32_t>().swap(Lel[e]);
+                    continue;
+                }
+                Ei[o++] = e;
+                ext += (wmark[e] == k) ? w[e] : (int64_t)Lel[e].size();
+            }
+            Ei.resize(o);
+            Ei.push_back(p);
+            std::vector<int32_t> &Ai_ = A[i];
+            size_t q = 0;
+            for (int32_t v : Ai_)
+                if (!elim[v] && mark[v] != k && v != i) Ai_[q++] = v;
+            Ai_.resize(q);
+            int64_t d = (int64_t)Ai_.size() + (int64_t)Lp.size() - 1 + ext;
+            if (d > remaining - 1) d = remaining - 1;
+            if (d < 0) d = 0;
+            pq.erase({deg[i], i});
+            deg[i] = (int32_t)d;
+            pq.insert({deg[i], i});
+        }
+    }
+}
+
+}  // namespace gblu

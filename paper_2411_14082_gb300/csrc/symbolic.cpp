@@ -1,0 +1,331 @@
+// Host-side symbolic work: input validation, elimination trees, the guessed
+// factor structure, the fixed-pattern schedules and the repack after a
+// restart.  No device code and no CUDA calls in this file.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "gblu_internal.h"
+
+namespace gblu {
+
+int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err)
+{
+    if (n < 1) { err = "n must be >= 1"; return GBLU_ERR_INVALID_INPUT; }
+    if (!Ap || !Ai) { err = "null pattern pointer"; return GBLU_ERR_INVALID_INPUT; }
+    if (Ap[0] != 0) { err = "Ap[0] != 0"; return GBLU_ERR_INVALID_INPUT; }
+    for (int32_t c = 0; c < n; c++)
+        if (Ap[c + 1] < Ap[c]) { err = "Ap not non-decreasing at column " + std::to_string(c); return GBLU_ERR_INVALID_INPUT; }
+    std::vector<int32_t> seen(n, -1);
+    for (int32_t c = 0; c < n; c++) {
+        for (int32_t p = Ap[c]; p < Ap[c + 1]; p++) {
+            int32_t r = Ai[p];
+            if (r < 0 || r >= n) { err = "row index out of range in column " + std::to_string(c); return GBLU_ERR_INVALID_INPUT; }
+            if (seen[r] == c) { err = "duplicate entry (" + std::to_string(r) + "," + std::to_string(c) + ")"; return GBLU_ERR_INVALID_INPUT; }
+            seen[r] = c;
+        }
+    }
+    return GBLU_OK;
+}
+
+// Column elimination tree of B = A(:,Q): the elimination tree of B^T B,
+// computed without forming B^T B (Section II-B: the ETree "is built from
+// A^T A without explicitly forming A^T A").  For every row, the columns
+// that contain it are linked through the most recent such column; union
+// with path compression (Liu's algorithm).
+void column_etree(const Pattern &P, std::vector<int32_t> &parent)
+{
+    const int32_t n = P.n;
+    parent.assign(n, -1);
+    std::vector<int32_t> anc(n, -1), prev(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t c = P.Q[k];
+        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+            int32_t i = prev[P.Ai[p]];
+            while (i != -1 && i < k) {
+                int32_t next = anc[i];
+                anc[i] = k;
+                if (next == -1) { parent[i] = k; break; }
+                i = next;
+            }
+            prev[P.Ai[p]] = k;
+        }
+    }
+}
+
+// Levels of a dependency DAG given column-wise: dependencies of column k are
+// the rows j < k of its U part.  Returns the number of levels.
+int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
+                  const int32_t *nU, std::vector<int32_t> &level)
+{
+    level.assign(n, 0);
+    int32_t nl = 0;
+    for (int32_t k = 0; k < n; k++) {
+        int32_t lv = 0;
+        const int64_t end = nU ? Up[k] + nU[k] : Up[k + 1];
+        for (int64_t e = Up[k]; e < end; e++) {
+            const int32_t j = Ui[e];
+            if (j < k && level[j] + 1 > lv) lv = level[j] + 1;
+        }
+        level[k] = lv;
+        if (lv + 1 > nl) nl = lv + 1;
+    }
+    return nl;
+}
+
+// Guessed structure for a first factorization: diagonal pivots piv = Q and
+// the pattern of the Cholesky factor of S = (A + A^T)(Q,Q), which contains
+// the LU pattern of A(Q,Q) without pivoting.  Row structures of L come from
+// the elimination tree of S by walking up from every off-diagonal entry of
+// row k until a node already visited for row k ("row subtree").  The
+// diagonal is always part of the pattern, even where A has no entry; such a
+// column then fails the pivot check and is recomputed with pivoting.
+int guess_structure(const Pattern &P, Structure &S, std::string &err)
+{
+    const int32_t n = P.n;
+    // symmetric adjacency of S, lower part per row (j < i) and upper per column
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+            int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+            if (i == j) continue;
+            cnt[std::max(i, j) + 1]++;  // entry (max, min): row max, column min
+        }
+    for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    std::vector<int32_t> lowadj(cnt[n]);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int32_t c = 0; c < n; c++)
+            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+                int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+                if (i == j) continue;
+                lowadj[pos[std::max(i, j)]++] = std::min(i, j);
+            }
+    }
+    // elimination tree of S (Liu, path compression)
+    std::vector<int32_t> parent(n, -1), anc(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
+            int32_t i = lowadj[e];
+            while (i != -1 && i < k) {
+                int32_t next = anc[i];
+                anc[i] = k;
+                if (next == -1) parent[i] = k;
+                i = next;
+            }
+        }
+    }
+    // row structures of L (strict lower) by row subtrees
+    std::vector<int32_t> mark(n, -1);
+    std::vector<int64_t> rptr(n + 1, 0);
+    std::vector<int32_t> rows;  // concatenated row structures
+    rows.reserve((size_t)cnt[n] * 4 + n);
+    std::vector<int32_t> colcnt(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        mark[k] = k;
+        const size_t start = rows.size();
+        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
+            for (int32_t j = lowadj[e]; j != -1 && mark[j] != k; j = parent[j]) {
+                mark[j] = k;
+                rows.push_back(j);
+            }
+        }
+        std::sort(rows.begin() + start, rows.end());
+        for (size_t e = start; e < rows.size(); e++) colcnt[rows[e]]++;
+        rptr[k + 1] = (int64_t)rows.size();
+    }
+    const int64_t nnzL = (int64_t)rows.size();
+    // canonical columns: U rows of column k = row structure of k, diagonal,
+    // then L rows of column k = rows i whose structure contains k
+    S.n = n;
+    S.LUp.assign(n + 1, 0);
+    S.nU.assign(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        S.nU[k] = (int32_t)(rptr[k + 1] - rptr[k]) + 1;
+        S.LUp[k + 1] = S.LUp[k] + S.nU[k] + colcnt[k];
+    }
+    if (S.LUp[n] > INT32_MAX) { err = "factor too large (> 2^31 entries)"; return GBLU_ERR_NOMEM; }
+    S.LUi.assign(S.LUp[n], 0);
+    std::vector<int64_t> lpos(n);
+    for (int32_t k = 0; k < n; k++) {
+        int64_t o = S.LUp[k];
+        for (int64_t e = rptr[k]; e < rptr[k + 1]; e++) S.LUi[o++] = rows[e];
+        S.LUi[o++] = k;
+        lpos[k] = o;
+    }
+    for (int32_t i = 0; i < n; i++)
+        for (int64_t e = rptr[i]; e < rptr[i + 1]; e++) S.LUi[lpos[rows[e]]++] = i;
+    S.piv = P.Q;
+    S.pinv = P.qinv;
+    (void)nnzL;
+    return GBLU_OK;
+}
+
+void build_schedule(const Pattern &P, const Structure &S, double alpha,
+                    int resident_warps, Schedule &W)
+{
+    const int32_t n = S.n;
+    // ---- EGraph levels and the dividing level (Section III-B) ----
+    std::vector<int32_t> level;
+    W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level);
+    W.level_ptr.assign(W.n_levels + 1, 0);
+    for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
+    for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
+    W.level_cols.assign(n, 0);
+    {
+        std::vector<int32_t> pos(W.level_ptr.begin(), W.level_ptr.end() - 1);
+        for (int32_t k = 0; k < n; k++) W.level_cols[pos[level[k]]++] = k;
+    }
+    const double thr = alpha * (double)resident_warps;
+    W.div_level = W.n_levels;
+    for (int32_t l = 0; l < W.n_levels; l++)
+        if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
+    // ---- flops of one refactorization ----
+    double fl = 0;
+    for (int32_t k = 0; k < n; k++)
+        for (int64_t e = S.LUp[k]; e < S.LUp[k] + S.nU[k] - 1; e++) {
+            const int32_t j = S.LUi[e];
+            fl += 2.0 * (double)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
+        }
+    W.flops = fl;
+    // ---- A slot -> position in its column (columns are sorted) ----
+    const int64_t nnzA = (int64_t)P.Ai.size();
+    W.amap.assign(nnzA, -1);
+    for (int32_t c = 0; c < n; c++) {
+        const int32_t k = P.qinv[c];
+        const int32_t *col = S.LUi.data() + S.LUp[k];
+        const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
+        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+            const int32_t s = S.pinv[P.Ai[p]];
+            const int32_t *it = std::lower_bound(col, col + len, s);
+            W.amap[p] = (it != col + len && *it == s) ? (int32_t)(it - col) : -1;
+        }
+    }
+    // ---- original row ids of L entries (used by the restart kernel) ----
+    W.LUi_orig.assign(S.LUi.size(), 0);
+    for (int32_t k = 0; k < n; k++)
+        for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
+            W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
+    // ---- row-wise copies for the solves ----
+    W.Lrp.assign(n + 1, 0);
+    W.Urp.assign(n + 1, 0);
+    W.Udiag.assign(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        const int64_t d = S.LUp[k] + S.nU[k] - 1;
+        W.Udiag[k] = (int32_t)d;
+        for (int64_t e = S.LUp[k]; e < d; e++) W.Urp[S.LUi[e] + 1]++;
+        for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) W.Lrp[S.LUi[e] + 1]++;
+    }
+    for (int32_t i = 0; i < n; i++) { W.Lrp[i + 1] += W.Lrp[i]; W.Urp[i + 1] += W.Urp[i]; }
+    W.Lcol.assign(W.Lrp[n], 0);
+    W.Lslot.assign(W.Lrp[n], 0);
+    W.Urow_col.assign(W.Urp[n], 0);
+    W.Uslot.assign(W.Urp[n], 0);
+    {
+        std::vector<int64_t> lp(W.Lrp.begin(), W.Lrp.end() - 1), up(W.Urp.begin(), W.Urp.end() - 1);
+        for (int32_t k = 0; k < n; k++) {
+            const int64_t d = S.LUp[k] + S.nU[k] - 1;
+            for (int64_t e = S.LUp[k]; e < d; e++) {
+                const int32_t i = S.LUi[e];
+                W.Urow_col[up[i]] = k;
+                W.Uslot[up[i]++] = (int32_t)e;
+            }
+            for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) {
+                const int32_t i = S.LUi[e];
+                W.Lcol[lp[i]] = k;
+                W.Lslot[lp[i]++] = (int32_t)e;
+            }
+        }
+    }
+    // ---- solve levels: L rows forward, U rows backward ----
+    auto levelize = [&](bool lower, std::vector<int32_t> &ptr, std::vector<int32_t> &rowsv,
+                        int32_t &nlev, int32_t &div) {
+        std::vector<int32_t> lv(n, 0);
+        nlev = 0;
+        for (int32_t t = 0; t < n; t++) {
+            const int32_t i = lower ? t : n - 1 - t;
+            int32_t v = 0;
+            const std::vector<int64_t> &rp = lower ? W.Lrp : W.Urp;
+            const std::vector<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
+            for (int64_t e = rp[i]; e < rp[i + 1]; e++) v = std::max(v, lv[cc[e]] + 1);
+            lv[i] = v;
+            nlev = std::max(nlev, v + 1);
+        }
+        ptr.assign(nlev + 1, 0);
+        for (int32_t i = 0; i < n; i++) ptr[lv[i] + 1]++;
+        for (int32_t l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
+        rowsv.assign(n, 0);
+        std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
+        for (int32_t t = 0; t < n; t++) {
+            const int32_t i = lower ? t : n - 1 - t;
+            rowsv[pos[lv[i]]++] = i;
+        }
+        div = nlev;
+        for (int32_t l = 0; l < nlev; l++)
+            if ((double)(ptr[l + 1] - ptr[l]) < thr) { div = l; break; }
+    };
+    levelize(true, W.lsv_ptr, W.lsv_rows, W.lsv_levels, W.lsv_div);
+    levelize(false, W.usv_ptr, W.usv_rows, W.usv_levels, W.usv_div);
+}
+
+}  // namespace gblu
+
+// ------------------------------------------------------------ host-only C ABI
+using namespace gblu;
+
+extern "C" int gblu_column_etree(int32_t n, const int32_t *Ap, const int32_t *Ai,
+                                 const int32_t *Q, int32_t *parent)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !parent) return GBLU_ERR_INVALID_INPUT;
+    Pattern P;
+    P.n = n;
+    P.Ap.assign(Ap, Ap + n + 1);
+    P.Ai.assign(Ai, Ai + Ap[n]);
+    P.Q.resize(n);
+    std::vector<int32_t> seen(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        int32_t c = Q ? Q[k] : k;
+        if (c < 0 || c >= n || seen[c]) return GBLU_ERR_INVALID_INPUT;
+        seen[c] = 1;
+        P.Q[k] = c;
+    }
+    std::vector<int32_t> par;
+    column_etree(P, par);
+    std::memcpy(parent, par.data(), sizeof(int32_t) * n);
+    return GBLU_OK;
+}
+
+extern "C" int64_t gblu_restart_set(int32_t n, const int32_t *parent, const uint8_t *finished,
+                                    uint8_t *out)
+{
+    if (n < 1 || !parent || !finished || !out) return GBLU_ERR_INVALID_INPUT;
+    std::memset(out, 0, (size_t)n);
+    int64_t cnt = 0;
+    // Section IV-C: every unfinished node and all of its ancestors
+    for (int32_t k = 0; k < n; k++) {
+        if (finished[k]) continue;
+        for (int32_t j = k; j != -1 && !out[j]; j = parent[j]) {
+            out[j] = 1;
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+extern "C" int32_t gblu_levels(int32_t n, const int64_t *Up, const int32_t *Ui, int32_t *level)
+{
+    if (n < 1 || !Up || !Ui || !level) return GBLU_ERR_INVALID_INPUT;
+    std::vector<int32_t> lv;
+    int32_t nl = levels_of(n, Up, Ui, nullptr, lv);
+    std::memcpy(level, lv.data(), sizeof(int32_t) * n);
+    return nl;
+}
+
+extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm) return GBLU_ERR_INVALID_INPUT;
+    mindeg_order(n, Ap, Ai, perm);
+    return GBLU_OK;
+}

@@ -1,0 +1,274 @@
+"""Python binding of libgblu (the C ABI declared in include/gblu.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  Device arrays are torch tensors (float64, contiguous, on the
+handle's device); the stream defaults to torch's current stream.  There is
+no CPU fallback: if the library cannot be loaded or the device cannot be
+used, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+REPIVOTED = 1
+ERR_INVALID_INPUT = -1
+ERR_SINGULAR = -2
+ERR_NOT_ANALYZED = -3
+ERR_NOMEM = -4
+ERR_DEVICE_TIMEOUT = -5
+ERR_CUDA = -6
+ERR_NOT_FACTORIZED = -7
+ERR_INTERNAL = -8
+
+SCHED = {"auto": 0, "level": 1, "syncfree": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTED = [
+    "gblu_default_opts", "gblu_last_error", "gblu_create", "gblu_destroy", "gblu_analyze",
+    "gblu_factorize", "gblu_refactorize", "gblu_solve", "gblu_residual", "gblu_get_stats",
+    "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
+    "gblu_levels", "gblu_step_host",
+]
+
+
+class GbluError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gblu error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("pivot_tol", ctypes.c_double), ("sched_mode", ctypes.c_int),
+                ("solve_mode", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("spin_limit", ctypes.c_longlong)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz_a", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
+                ("nnz_u", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("n_levels", ctypes.c_int32), ("div_level", ctypes.c_int32),
+                ("n_solve_levels_l", ctypes.c_int32), ("n_solve_levels_u", ctypes.c_int32),
+                ("etree_height", ctypes.c_int32), ("n_refactor", ctypes.c_int64),
+                ("n_repivot", ctypes.c_int64), ("n_restart_cols", ctypes.c_int64),
+                ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgblu.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise OSError(f"libgblu not built: {path}")
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.gblu_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        lib.gblu_default_opts.restype = None
+        lib.gblu_last_error.argtypes = []
+        lib.gblu_last_error.restype = ctypes.c_char_p
+        lib.gblu_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(Opts)]
+        lib.gblu_destroy.argtypes = [P]
+        lib.gblu_destroy.restype = None
+        lib.gblu_analyze.argtypes = [P, I32, P, P, P]
+        lib.gblu_factorize.argtypes = [P, P, P]
+        lib.gblu_refactorize.argtypes = [P, P, P, ctypes.POINTER(I32)]
+        lib.gblu_solve.argtypes = [P, P, P, P]
+        lib.gblu_residual.argtypes = [P, P, P, P, P, P]
+        lib.gblu_step_host.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
+        lib.gblu_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        lib.gblu_export_factors.argtypes = [P] * 9
+        lib.gblu_order_mindeg.argtypes = [I32, P, P, P]
+        lib.gblu_column_etree.argtypes = [I32, P, P, P, P]
+        lib.gblu_restart_set.argtypes = [I32, P, P, P]
+        lib.gblu_restart_set.restype = I64
+        lib.gblu_levels.argtypes = [I32, P, P, P]
+        lib.gblu_levels.restype = I32
+        for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
+                  "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
+                  "gblu_order_mindeg", "gblu_column_etree"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(code):
+    if code < 0:
+        raise GbluError(code, load().gblu_last_error().decode())
+    return code
+
+
+def _dev_ptr(t, device, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 torch tensor")
+    if t.device.index != device:
+        raise ValueError(f"tensor on cuda:{t.device.index}, handle on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Solver:
+    """One handle: analyze a pattern once, then factorize / refactorize / solve."""
+
+    def __init__(self, device=0, pivot_tol=1e-3, sched_mode="auto", solve_mode="auto",
+                 alpha=2.0, spin_limit=1 << 24):
+        lib = load()
+        o = Opts()
+        lib.gblu_default_opts(ctypes.byref(o))
+        o.pivot_tol = pivot_tol
+        o.sched_mode = SCHED[sched_mode]
+        o.solve_mode = SCHED[solve_mode]
+        o.alpha = alpha
+        o.spin_limit = spin_limit
+        h = ctypes.c_void_p()
+        _check(lib.gblu_create(ctypes.byref(h), int(device), ctypes.byref(o)))
+        self._h = h
+        self.device = int(device)
+        self.n = None
+        self.nnz = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gblu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def analyze(self, n, Ap, Ai, Q=None):
+        Ap, Ai = _i32(Ap), _i32(Ai)
+        q = None if Q is None else _i32(Q)
+        _check(load().gblu_analyze(self._h, int(n), _np_ptr(Ap), _np_ptr(Ai),
+                                   None if q is None else _np_ptr(q)))
+        self.n, self.nnz = int(n), int(Ap[-1])
+
+    def factorize(self, Ax, stream=None):
+        return _check(load().gblu_factorize(self._h, _dev_ptr(Ax, self.device, self.nnz),
+                                            _stream(stream)))
+
+    def refactorize(self, Ax, stream=None):
+        rep = ctypes.c_int32(0)
+        rc = _check(load().gblu_refactorize(self._h, _dev_ptr(Ax, self.device, self.nnz),
+                                            _stream(stream), ctypes.byref(rep)))
+        return rc, bool(rep.value)
+
+    def solve(self, b, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        _check(load().gblu_solve(self._h, _dev_ptr(b, self.device, self.n),
+                                 _dev_ptr(x, self.device, self.n), _stream(stream)))
+        return x
+
+    def step_host(self, Ax, b, x, stream=None):
+        """Refactorize + solve from host numpy float64 arrays (x is written)."""
+        for a, m in ((Ax, self.nnz), (b, self.n), (x, self.n)):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                    and a.size == m):
+                raise ValueError("expected contiguous float64 numpy arrays of the right size")
+        rep = ctypes.c_int32(0)
+        rc = _check(load().gblu_step_host(self._h, _np_ptr(Ax), _np_ptr(b), _np_ptr(x),
+                                          _stream(stream), ctypes.byref(rep)))
+        return rc, bool(rep.value)
+
+    def residual(self, Ax, b, x, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(4, dtype=torch.float64, device=b.device)
+        _check(load().gblu_residual(self._h, _dev_ptr(Ax, self.device, self.nnz),
+                                    _dev_ptr(b, self.device, self.n),
+                                    _dev_ptr(x, self.device, self.n),
+                                    _dev_ptr(out, self.device, 4), _stream(stream)))
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().gblu_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def export_factors(self) -> dict:
+        st = self.stats()
+        n, nl, nu = st["n"], st["nnz_l"], st["nnz_u"]
+        out = dict(Lp=np.empty(n + 1, np.int64), Li=np.empty(max(nl, 1), np.int32),
+                   Lx=np.empty(max(nl, 1), np.float64), Up=np.empty(n + 1, np.int64),
+                   Ui=np.empty(max(nu, 1), np.int32), Ux=np.empty(max(nu, 1), np.float64),
+                   piv=np.empty(n, np.int32), q=np.empty(n, np.int32))
+        _check(load().gblu_export_factors(self._h, *[_np_ptr(out[k]) for k in
+                                                     ("Lp", "Li", "Lx", "Up", "Ui", "Ux", "piv", "q")]))
+        for k, m in (("Li", nl), ("Lx", nl), ("Ui", nu), ("Ux", nu)):
+            out[k] = out[k][:m]
+        return out
+
+
+# ---------------------------------------------------------------- host-only helpers
+def order_mindeg(n, Ap, Ai):
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    perm = np.empty(n, np.int32)
+    _check(load().gblu_order_mindeg(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
+    return perm
+
+
+def column_etree(n, Ap, Ai, Q=None):
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    q = None if Q is None else _i32(Q)
+    parent = np.empty(n, np.int32)
+    _check(load().gblu_column_etree(int(n), _np_ptr(Ap), _np_ptr(Ai),
+                                    None if q is None else _np_ptr(q), _np_ptr(parent)))
+    return parent
+
+
+def restart_set(parent, finished):
+    parent = _i32(parent)
+    fin = np.ascontiguousarray(finished, dtype=np.uint8)
+    out = np.empty(len(parent), np.uint8)
+    cnt = load().gblu_restart_set(len(parent), _np_ptr(parent), _np_ptr(fin), _np_ptr(out))
+    _check(int(cnt) if cnt < 0 else 0)
+    return out.astype(bool)
+
+
+def levels(n, Up, Ui):
+    Up = np.ascontiguousarray(Up, dtype=np.int64)
+    Ui = _i32(Ui)
+    lv = np.empty(n, np.int32)
+    nl = load().gblu_levels(int(n), _np_ptr(Up), _np_ptr(Ui), _np_ptr(lv))
+    _check(int(nl) if nl < 0 else 0)
+    return lv, int(nl)

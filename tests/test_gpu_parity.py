@@ -1,0 +1,275 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (FP64): factor entries to 1e-10 relative to the column's
+inf-norm, identical pivot sequences, relative residual
+||b - A x||_inf / (||A||_inf ||x||_inf) <= 1e-12 for every solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2411_14082_gb300 import gblu, inputs
+from tests.factor_compare import compare_factors
+from tests.golden_io import dense_lu, load
+
+pytestmark = pytest.mark.gpu
+
+DEV = 0
+RTOL = 1e-10
+RESID = 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(f"cuda:{DEV}")
+
+
+def solve_and_check(s, n, Ap, Ai, Ax, Axd, rng):
+    b = inputs.rhs(n, rng)
+    x = s.solve(dev(b))
+    res = s.residual(Axd, dev(b), x).cpu().numpy()
+    xh = x.cpu().numpy()
+    assert res[0] <= RESID, f"device residual {res[0]:.3e}"
+    assert O.residual(n, Ap, Ai, Ax, xh, b) <= RESID
+    return xh, b
+
+
+@pytest.mark.parametrize("name", ["mna_vsource_3x3.txt", "refactor_fail_col2_4x4.txt",
+                                  "restart_recompute_3x3.txt"])
+def test_golden_examples_on_gpu(name):
+    g = load(name)
+    n = g["n"]
+    s = gblu.Solver(DEV, pivot_tol=g["eps"])
+    s.analyze(n, g["Ap"], g["Ai"], g["Q"])
+    if "Ax0" in g:
+        s.factorize(dev(g["Ax0"]))
+        assert np.array_equal(s.export_factors()["piv"], g["prefer"])
+        rc, rep = s.refactorize(dev(g["Ax"]))
+        assert rc == gblu.REPIVOTED and rep
+    else:
+        s.factorize(dev(g["Ax"]))
+    f = s.export_factors()
+    np.testing.assert_array_equal(f["piv"], g["piv"])
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for k in range(n):
+        L[f["Li"][f["Lp"][k]:f["Lp"][k + 1]], k] = f["Lx"][f["Lp"][k]:f["Lp"][k + 1]]
+        U[f["Ui"][f["Up"][k]:f["Up"][k + 1]], k] = f["Ux"][f["Up"][k]:f["Up"][k + 1]]
+    Lg, Ug = dense_lu(g)
+    np.testing.assert_allclose(L, Lg, rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(U, Ug, rtol=1e-15, atol=1e-15)
+    if "x" in g:
+        x = s.solve(dev(g["b"])).cpu().numpy()
+        np.testing.assert_allclose(x, g["x"], rtol=1e-15)
+    if name == "restart_recompute_3x3.txt":
+        st = s.stats()
+        assert st["n_restart_cols"] == len(g["restart_set"]) and st["last_first_bad"] == 0
+
+
+@pytest.mark.parametrize("sched", ["auto", "level", "syncfree"])
+def test_random_small_matrices_factorize_and_refactorize(sched):
+    rng = np.random.default_rng(42)
+    for trial in range(40):
+        n = int(rng.integers(1, 80))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.02, 0.3), rng,
+                                             zero_diag_frac=rng.uniform(0, 0.3), dominance=1.0)
+        Q = rng.permutation(n).astype(np.int32)
+        lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+        s = gblu.Solver(DEV, sched_mode=sched, solve_mode=sched)
+        s.analyze(n, Ap, Ai, Q)
+        if lu.status == O.ERR_SINGULAR:
+            with pytest.raises(gblu.GbluError) as ei:
+                s.factorize(dev(Ax))
+            assert ei.value.code == gblu.ERR_SINGULAR
+            continue
+        Axd = dev(Ax)
+        s.factorize(Axd)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+        for it in range(3):
+            Ax2 = inputs.perturb_entries(Ax, rng, frac=0.3, sigma=1.0)
+            lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+            Axd2 = dev(Ax2)
+            if lu2.status != O.OK:
+                with pytest.raises(gblu.GbluError):
+                    s.refactorize(Axd2)
+                break
+            rc, rep = s.refactorize(Axd2)
+            assert rep == (lu2.n_rejected > 0)
+            compare_factors(s.export_factors(), lu2, RTOL)
+            solve_and_check(s, n, Ap, Ai, Ax2, Axd2, rng)
+            lu = lu2
+
+
+def test_small_mna_workload_sequence():
+    """n = 2,020 MNA grid with voltage sources: 1 factorize, then 10
+    refactorizations with 5% of the element conductances perturbed
+    (log-normal, sigma 0.3), each followed by a solve."""
+    ckt = inputs.workload_small()
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(inputs.BASE_SEED)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    Axd = dev(Ax)
+    s.factorize(Axd)
+    compare_factors(s.export_factors(), lu, RTOL)
+    solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    for it in range(10):
+        ckt = inputs.perturb_elements(ckt, rng)
+        Ax = ckt.values()
+        Axd = dev(Ax)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        s.refactorize(Axd)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    # the raw-entry perturbation fires the pivot check more often
+    for it in range(5):
+        Ax = inputs.perturb_entries(ckt.values(), rng, frac=0.05, sigma=0.3)
+        Axd = dev(Ax)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        s.refactorize(Axd)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+
+
+def mesh_small(seed=7):
+    return inputs.rc_mesh3d(40, 40, 4, seed=seed, n_fet=100)
+
+
+def test_schedules_give_bitwise_identical_results():
+    ckt = mesh_small()
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    b = dev(inputs.rhs(n, np.random.default_rng(1)))
+    outs = []
+    for mode in ("auto", "level", "syncfree"):
+        s = gblu.Solver(DEV, sched_mode=mode, solve_mode=mode)
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(dev(Ax))
+        Ax2 = inputs.redraw_transistors(ckt, np.random.default_rng(3)).values()
+        s.refactorize(dev(Ax2))
+        f = s.export_factors()
+        outs.append((f["Lx"], f["Ux"], s.solve(b).cpu().numpy()))
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
+
+
+def test_forced_repivot_protocol_matches_oracle():
+    """Section VI-A general case: a run is forced to re-pivot at a random
+    column (here: that column's diagonal entry of A is scaled by 1e-12)."""
+    ckt = mesh_small(seed=11)
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(5)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    s.factorize(dev(Ax))
+    compare_factors(s.export_factors(), lu, RTOL)
+    diag_slot = {}
+    for c in range(n):
+        for p in range(Ap[c], Ap[c + 1]):
+            if Ai[p] == c:
+                diag_slot[c] = p
+    for trial in range(6):
+        k = int(rng.integers(0, n))
+        Ax2 = inputs.redraw_transistors(ckt, rng).values()
+        Ax2[diag_slot[int(Q[k])]] *= 1e-12
+        lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+        assert lu2.n_rejected > 0
+        Axd2 = dev(Ax2)
+        rc, rep = s.refactorize(Axd2)
+        assert rc == gblu.REPIVOTED and rep
+        st = s.stats()
+        assert st["last_first_bad"] <= k
+        compare_factors(s.export_factors(), lu2, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax2, Axd2, rng)
+        lu = lu2
+
+
+def test_dense_block_uses_long_column_path():
+    """Columns longer than the shared-memory work vector (1,024 entries)
+    are updated in place in global memory."""
+    rng = np.random.default_rng(3)
+    n = 1200
+    A = rng.normal(size=(n, n))
+    A[np.arange(n), np.arange(n)] += 40.0
+    _, Ap, Ai, Ax = inputs.dense_to_csc(A, np.ones((n, n), bool))
+    Q = np.arange(n, dtype=np.int32)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    Axd = dev(Ax)
+    s.factorize(Axd)
+    compare_factors(s.export_factors(), lu, RTOL)
+    solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    # and through the pivoting tail: flip the first diagonal
+    Ax2 = Ax.copy()
+    Ax2[0] = 1e-9
+    lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+    s.refactorize(dev(Ax2))
+    compare_factors(s.export_factors(), lu2, RTOL)
+
+
+def test_edge_cases():
+    # n = 1
+    s = gblu.Solver(DEV)
+    s.analyze(1, np.array([0, 1]), np.array([0]), None)
+    s.factorize(dev([4.0]))
+    assert s.solve(dev([2.0])).cpu().item() == 0.5
+    # structurally singular (empty column)
+    s = gblu.Solver(DEV)
+    s.analyze(2, np.array([0, 2, 2]), np.array([0, 1]), np.array([0, 1]))
+    with pytest.raises(gblu.GbluError) as ei:
+        s.factorize(dev([1.0, 2.0]))
+    assert ei.value.code == gblu.ERR_SINGULAR
+    # numerically singular
+    s = gblu.Solver(DEV)
+    s.analyze(2, np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([0, 1]))
+    with pytest.raises(gblu.GbluError):
+        s.factorize(dev([1.0, 2.0, 2.0, 4.0]))
+    # invalid input
+    s = gblu.Solver(DEV)
+    with pytest.raises(gblu.GbluError) as ei:
+        s.analyze(2, np.array([0, 2, 2]), np.array([1, 1]))
+    assert ei.value.code == gblu.ERR_INVALID_INPUT
+    with pytest.raises(gblu.GbluError) as ei:
+        s.solve(dev([1.0, 2.0]))
+    assert ei.value.code == gblu.ERR_NOT_ANALYZED
+
+
+def test_bounded_wait_returns_timeout_and_context_survives():
+    """Every device wait has an iteration limit: with a limit of one
+    iteration the sync-free kernels give up on the first unfinished
+    predecessor and the call returns GBLU_ERR_DEVICE_TIMEOUT; the context
+    stays usable."""
+    ckt = mesh_small(seed=2)
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    s = gblu.Solver(DEV, sched_mode="syncfree", spin_limit=1)
+    s.analyze(n, Ap, Ai, Q)
+    with pytest.raises(gblu.GbluError) as ei:
+        s.factorize(dev(Ax))
+    assert ei.value.code == gblu.ERR_DEVICE_TIMEOUT
+    torch.cuda.synchronize()
+    s2 = gblu.Solver(DEV)
+    s2.analyze(n, Ap, Ai, Q)
+    Axd = dev(Ax)
+    s2.factorize(Axd)
+    solve_and_check(s2, n, Ap, Ai, Ax, Axd, np.random.default_rng(0))
+
+
+def test_library_ordering_when_no_q_given():
+    ckt = inputs.workload_small()
+    n, Ap, Ai, Ax = ckt.csc()
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, None)
+    Axd = dev(Ax)
+    s.factorize(Axd)
+    f = s.export_factors()
+    lu = O.factorize(n, Ap, Ai, Ax, gblu.order_mindeg(n, Ap, Ai), 1e-3)
+    compare_factors(f, lu, RTOL)
+    solve_and_check(s, n, Ap, Ai, Ax, Axd, np.random.default_rng(0))

@@ -1,0 +1,154 @@
+"""CPU checks of the library's host-side logic and of its C ABI.
+
+No device work: the library is loaded (libcudart is linked but no GPU is
+needed for these calls), every symbol declared in include/gblu.h must be
+exported, and the host-only helpers (column elimination tree, restart set,
+levels, minimum-degree order) are checked against brute force.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2411_14082_gb300 import gblu, inputs
+from tests.golden_io import load as load_golden
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gblu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gblu_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = gblu.load()
+    names = header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/gblu.h but not exported"
+    assert set(names) == set(gblu.EXPORTED)
+
+
+def dense_pattern(n, Ap, Ai):
+    S = np.zeros((n, n), dtype=bool)
+    for c in range(n):
+        S[Ai[Ap[c]:Ap[c + 1]], c] = True
+    return S
+
+
+def brute_etree_of(M):
+    """Elimination tree of a symmetric boolean pattern M by symbolic Cholesky:
+    parent(j) = first row below the diagonal of column j of the factor."""
+    n = len(M)
+    L = np.tril(M | M.T).copy()
+    np.fill_diagonal(L, True)
+    for k in range(n):   # fill rule: L(a, b) |= L(a, k) & L(b, k) for k < b < a
+        rows = np.nonzero(L[k + 1:, k])[0] + k + 1
+        for a in rows:
+            for b in rows:
+                if a > b:
+                    L[a, b] = True
+    parent = np.full(n, -1)
+    for j in range(n):
+        below = np.nonzero(L[j + 1:, j])[0]
+        if len(below):
+            parent[j] = below[0] + j + 1
+    return parent
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_column_etree_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 14))
+    _, Ap, Ai, _ = inputs.random_sparse(n, rng.uniform(0.1, 0.5), rng, zero_diag_frac=0.3)
+    Q = rng.permutation(n).astype(np.int32)
+    S = dense_pattern(n, Ap, Ai)[:, Q].astype(int)
+    AtA = (S.T @ S) > 0
+    np.testing.assert_array_equal(gblu.column_etree(n, Ap, Ai, Q), brute_etree_of(AtA))
+
+
+def test_restart_set_golden_and_brute_force():
+    g = load_golden("restart_recompute_3x3.txt")
+    parent = gblu.column_etree(g["n"], g["Ap"], g["Ai"], g["Q"])
+    np.testing.assert_array_equal(parent, g["etree_parent"])
+    finished = np.array([0, 1, 1], dtype=np.uint8)   # column 0 failed, 1 and 2 finished
+    rs = gblu.restart_set(parent, finished)
+    np.testing.assert_array_equal(np.nonzero(rs)[0], g["restart_set"])
+    rng = np.random.default_rng(0)
+    for trial in range(200):
+        n = int(rng.integers(1, 30))
+        parent = np.array([rng.integers(k + 1, n + 1) if k < n - 1 else n for k in range(n)])
+        parent = np.where(parent >= n, -1, parent).astype(np.int32)
+        finished = (rng.random(n) < 0.7).astype(np.uint8)
+        expect = np.zeros(n, bool)
+        for k in range(n):
+            if not finished[k]:
+                j = k
+                while j != -1:
+                    expect[j] = True
+                    j = parent[j]
+        np.testing.assert_array_equal(gblu.restart_set(parent, finished), expect)
+
+
+def test_levels_are_longest_path():
+    rng = np.random.default_rng(1)
+    for trial in range(50):
+        n = int(rng.integers(1, 40))
+        Up = [0]
+        Ui = []
+        deps = []
+        for k in range(n):
+            d = sorted(set(rng.integers(0, k, size=int(rng.integers(0, 4))).tolist())) if k else []
+            deps.append(d)
+            Ui += d + [k]
+            Up.append(len(Ui))
+        lv, nl = gblu.levels(n, np.array(Up), np.array(Ui))
+        expect = np.zeros(n, int)
+        for k in range(n):
+            expect[k] = max([expect[j] + 1 for j in deps[k]], default=0)
+        np.testing.assert_array_equal(lv, expect)
+        assert nl == expect.max() + 1
+
+
+def symbolic_fill(n, Ap, Ai, Q):
+    """nnz(L+U) of A(Q,Q)+A(Q,Q)^T with diagonal pivots (brute force)."""
+    S = dense_pattern(n, Ap, Ai)
+    S = S | S.T
+    S = S[np.ix_(Q, Q)]
+    np.fill_diagonal(S, True)
+    for k in range(n):
+        rows = np.nonzero(S[k + 1:, k])[0] + k + 1
+        S[np.ix_(rows, rows)] = True
+    return int(S.sum())
+
+
+def test_mindeg_is_permutation_and_reduces_fill():
+    ckt = inputs.mna_grid2d(12, 12, n_vsrc=3)
+    n, Ap, Ai, _ = ckt.csc()
+    perm = gblu.order_mindeg(n, Ap, Ai)
+    assert sorted(perm.tolist()) == list(range(n))
+    fill_md = symbolic_fill(n, Ap, Ai, perm)
+    fill_nat = symbolic_fill(n, Ap, Ai, np.arange(n))
+    assert fill_md < 0.8 * fill_nat
+
+
+def test_mindeg_on_arrow_matrix_orders_hub_last():
+    n = 30
+    A = np.eye(n)
+    A[0, :] = 1
+    A[:, 0] = 1
+    _, Ap, Ai, _ = inputs.dense_to_csc(A)
+    perm = gblu.order_mindeg(n, Ap, Ai)
+    assert perm[-1] == 0 or perm[-2] == 0   # the dense hub is eliminated (nearly) last
+
+
+def test_invalid_patterns_rejected_on_host():
+    with pytest.raises(gblu.GbluError):
+        gblu.column_etree(2, np.array([0, 1, 2]), np.array([0, 5]))   # row out of range
+    with pytest.raises(gblu.GbluError):
+        gblu.column_etree(2, np.array([0, 2, 2]), np.array([1, 1]))   # duplicate
+    with pytest.raises(gblu.GbluError):
+        gblu.order_mindeg(2, np.array([1, 1, 2]), np.array([0, 1]))   # Ap[0] != 0
