@@ -96,13 +96,15 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
                  const int32_t *Q);
 
 /*
- * Factorization with pivoting (Section II-A, Algorithm 1 in CSC form,
- * scheduled over the column elimination tree): every step prefers its
- * diagonal row Q[k] and keeps it unless |x(Q[k])| < pivot_tol * max|other
- * candidates| or x(Q[k]) == 0, else takes the largest candidate (ties: the
- * row first in Q).  Ax_dev: device float64[nnz] in the slot order of the
- * analyze call's Ai.  Builds the factors and, on the host, the fixed-pattern
- * schedule for refactorize and solve.  Synchronizes `stream`.
+ * Factorization with pivoting (Section II-A, Algorithm 1 in CSC form, run as
+ * the pipelined factorization of Section IV-D over all columns: columns are
+ * taken in increasing order, and each waits only for earlier columns of its
+ * column-elimination subtree).  Every step prefers its diagonal row Q[k] and
+ * keeps it unless |x(Q[k])| < pivot_tol * max|other candidates| or
+ * x(Q[k]) == 0, else takes the largest candidate (ties: the row first in Q).
+ * Ax_dev: device float64[nnz] in the slot order of the analyze call's Ai.
+ * Builds the factors and, on the host, the fixed-pattern schedule for
+ * refactorize and solve.  Synchronizes `stream`.
  * Returns GBLU_OK or GBLU_ERR_SINGULAR (factors then invalid).
  */
 int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);

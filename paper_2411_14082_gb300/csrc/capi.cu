@@ -95,7 +95,7 @@ struct gblu_ctx {
     DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, lflag, uflag;
     DBuf<double> y, partial, stage_ax, stage_b, stage_x;
     // restart (tail factorization)
-    DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist;
+    DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
     DBuf<double> sx;
 };
@@ -196,13 +196,19 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(ensure(h, h->lflag, n));
     CK(ensure(h, h->uflag, n));
     CK(ensure(h, h->y, n));
+    // ready flags hold epochs (> 0); recycled device memory may hold any
+    // value, so they start from zero
+    CU(cudaMemsetAsync(h->finish.p, 0, sizeof(int32_t) * n, st));
+    CU(cudaMemsetAsync(h->lflag.p, 0, sizeof(int32_t) * n, st));
+    CU(cudaMemsetAsync(h->uflag.p, 0, sizeof(int32_t) * n, st));
     // canonical rows/vals; the pool is sized at restart time
     if (h->rows.cap < nnz || h->vals.cap < nnz) {
         CK(ensure(h, h->rows, nnz));
         CK(ensure(h, h->vals, nnz));
     }
-    CU(cudaMemcpyAsync(h->rows.p, h->W.LUi_orig.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    if (values)
+    if (nnz > 0)
+        CU(cudaMemcpyAsync(h->rows.p, h->W.LUi_orig.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (values && nnz > 0)
         CU(cudaMemcpyAsync(h->vals.p, values->data(), nnz * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(upload(h, h->Lrp, h->W.Lrp, st));
     CK(upload(h, h->Urp, h->W.Urp, st));
@@ -259,21 +265,18 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     return GBLU_OK;
 }
 
-// Restart (Section IV-C/D): recompute with pivoting every unfinished column
-// and its column-elimination-tree ancestors, then rebuild the structure.
-int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
+// Factorization with threshold pivoting of the steps in rmask (Algorithm 5;
+// Algorithm 1 when rmask holds every step); the other steps keep their
+// current columns.  Rebuilds the structure and the schedule afterwards.
+int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<uint8_t> &rmask,
+             size_t pool_hint)
 {
     const Pattern &P = h->P;
     const int32_t n = P.n;
     const Structure &S = h->S;
     const int64_t nnz = S.nnz();
-    // ---- which columns finished in this refactorization?
-    std::vector<int32_t> fin(n);
-    CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    std::vector<uint8_t> finished(n), rmask(n);
-    for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
-    const int64_t nR = gblu_restart_set(n, P.cetree.data(), finished.data(), rmask.data());
+    int64_t nR = 0;
+    for (uint8_t v : rmask) nR += v != 0;
     std::vector<int32_t> seq, rm(n);
     seq.reserve(nR);
     int64_t restart_len = 0;
@@ -308,8 +311,10 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
     CK(ensure(h, h->sx, (size_t)slots * n));
     CK(ensure(h, h->smark, (size_t)slots * n));
     CK(ensure(h, h->slist, (size_t)slots * n));
+    CK(ensure(h, h->sclass, (size_t)slots * n));
     // pool after the canonical columns
-    size_t pool = (size_t)std::max<int64_t>(2 * restart_len, (int64_t)P.Ai.size()) + (size_t)n;
+    size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>(2 * restart_len, (int64_t)P.Ai.size())) +
+                  (size_t)n;
     for (int attempt = 0; attempt < 8; attempt++) {
         const size_t need = (size_t)nnz + pool;
         if (h->rows.cap < need || h->vals.cap < need) {
@@ -318,8 +323,10 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
             DBuf<double> nv;
             CK(ensure(h, nr, need));
             CK(ensure(h, nv, need));
-            CU(cudaMemcpyAsync(nr.p, h->rows.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-            CU(cudaMemcpyAsync(nv.p, h->vals.p, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            if (nnz > 0) {
+                CU(cudaMemcpyAsync(nr.p, h->rows.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CU(cudaMemcpyAsync(nv.p, h->vals.p, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
             CU(cudaStreamSynchronize(st));
             release(h, h->rows);
             release(h, h->vals);
@@ -354,6 +361,7 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
         t.sx = h->sx.p;
         t.smark = h->smark.p;
         t.slist = h->slist.p;
+        t.sclass = h->sclass.p;
         t.eps = h->opts.pivot_tol;
         t.spin_limit = h->opts.spin_limit;
         t.ctl = h->ctl;
@@ -423,6 +431,21 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
     h->n_restart_cols = nR;
     CK(install_structure(h, std::move(S2), &V2, st));
     return GBLU_OK;
+}
+
+// Restart (Section IV-C): every column that did not finish in this
+// re-factorization, and all of its column-elimination-tree ancestors, is
+// recomputed with pivoting.
+int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
+{
+    const int32_t n = h->P.n;
+    std::vector<int32_t> fin(n);
+    CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::vector<uint8_t> finished(n), rmask(n);
+    for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
+    gblu_restart_set(n, h->P.cetree.data(), finished.data(), rmask.data());
+    return run_tail(h, Ax, st, rmask, 0);
 }
 
 int check_handle(gblu_ctx *h)
@@ -508,7 +531,7 @@ void gblu_destroy(gblu_handle h)
         release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
         release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
         release(h, h->tpinv); release(h, h->cnu); release(h, h->cnl); release(h, h->smark);
-        release(h, h->slist); release(h, h->cbeg); release(h, h->sx);
+        release(h, h->slist); release(h, h->sclass); release(h, h->cbeg); release(h, h->sx);
         if (h->ctl) cudaFree(h->ctl);
         if (h->hctl) cudaFreeHost(h->hctl);
     }
@@ -593,14 +616,22 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     h->factorized = false;
+    // no kept columns: an empty structure whose preferred pivots are the
+    // diagonal rows Q[k]; every step is computed with pivoting
+    const int32_t n = h->P.n;
     Structure S;
-    std::string err;
-    int rc = guess_structure(h->P, S, err);
-    if (rc != GBLU_OK) return fail(rc, "%s", err.c_str());
-    CK(install_structure(h, std::move(S), nullptr, st));
-    int interrupted = 0;
-    CK(run_refactor(h, Ax_dev, st, &interrupted));
-    if (interrupted) CK(run_restart(h, Ax_dev, st));
+    S.n = n;
+    S.LUp.assign(n + 1, 0);
+    S.nU.assign(n, 0);
+    S.LUi.clear();
+    S.piv = h->P.Q;
+    S.pinv = h->P.qinv;
+    h->S = std::move(S);
+    CK(upload(h, h->piv, h->S.piv, st));
+    CU(cudaStreamSynchronize(st));
+    const size_t hint = (size_t)(1.25 * (double)(2 * symmetric_fill(h->P) + n));
+    std::vector<uint8_t> all(n, 1);
+    CK(run_tail(h, Ax_dev, st, all, hint));
     h->factorized = true;
     return GBLU_OK;
 }

@@ -58,9 +58,10 @@ struct Schedule {
 int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
 void column_etree(const Pattern &P, std::vector<int32_t> &parent);
 void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
-// guessed structure: pattern of the Cholesky factor of (A + A^T)(Q,Q) with
-// diagonal pivots piv = Q
-int guess_structure(const Pattern &P, Structure &S, std::string &err);
+// nnz of the Cholesky factor of (A + A^T)(Q,Q) (strict lower part), the
+// size of the LU factors when every diagonal pivot is kept on a structurally
+// symmetric matrix; used to size the first factorization's pool
+int64_t symmetric_fill(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, Schedule &W);
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
@@ -121,7 +122,7 @@ struct TailArgs {
     unsigned long long pool_base, pool_end;
     // per-CTA scratch
     double *sx;
-    int32_t *smark, *slist;
+    int32_t *smark, *slist, *sclass;
     double eps;
     long long spin_limit;
     DevCtl *ctl;

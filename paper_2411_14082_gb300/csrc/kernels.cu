@@ -252,7 +252,7 @@ refactor_syncfree_kernel(RefactorArgs a, int cap, int epoch)
 // is a dependency).  Then threshold pivoting with the preferred row, exactly
 // as the oracle defines it, and the column is appended to the pool.
 __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
-                            int32_t *list, int epoch)
+                            int32_t *list, int32_t *cls, int epoch)
 {
     __shared__ int s_cnt, s_found, s_mode, s_stop;
     __shared__ double r_m[kTailThreads / 32], r_ba[kTailThreads / 32];
@@ -345,13 +345,23 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
     }
 
     // ---- threshold pivoting (Algorithm 5 lines 14-15, preferred row) ----
+    // Every row is classified once (pivotal at step cls[i] >= 0, or a
+    // candidate); counting and storing both use that classification.  A
+    // pivotal row must belong to a step of k's elimination subtree.
     const int cnt = s_cnt;
     const int pref = __ldg(a.prefer + k);
+    const int lo_k = __ldg(a.clo + k);
     double m = 0.0, ba = 0.0;
-    int bq = INT_MAX, br = -1, nu = 0, nc = 0, pc = 0;
+    int bq = INT_MAX, br = -1, nu = 0, nc = 0, pc = 0, badrow = 0;
     for (int i = tid; i < cnt; i += kTailThreads) {
         const int r = list[i];
-        if (__ldcg(a.pinv + r) >= 0) { nu++; continue; }
+        const int pj = __ldcg(a.pinv + r);
+        cls[i] = pj;
+        if (pj >= 0) {
+            if (pj < lo_k || pj >= k) badrow = 1;
+            nu++;
+            continue;
+        }
         nc++;
         const double av = fabs(x[r]);
         if (r == pref) pc = 1;
@@ -367,8 +377,9 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         nu += __shfl_xor_sync(kFull, nu, o);
         nc += __shfl_xor_sync(kFull, nc, o);
         pc |= __shfl_xor_sync(kFull, pc, o);
+        badrow |= __shfl_xor_sync(kFull, badrow, o);
     }
-    if (lane == 0) { r_m[warp] = m; r_ba[warp] = ba; r_bq[warp] = bq; r_br[warp] = br; r_nu[warp] = nu; r_nc[warp] = nc; r_pc[warp] = pc; }
+    if (lane == 0) { r_m[warp] = m; r_ba[warp] = ba; r_bq[warp] = bq; r_br[warp] = br; r_nu[warp] = nu; r_nc[warp] = nc; r_pc[warp] = pc | (badrow << 1); }
     __syncthreads();
     if (tid == 0) {
         for (int w = 1; w < kTailThreads / 32; w++) {
@@ -380,6 +391,8 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
             nc += r_nc[w];
             pc |= r_pc[w];
         }
+        badrow = (pc >> 1) | badrow;
+        pc &= 1;
         int piv = -1;
         if (pc) {
             const double xp = x[pref];
@@ -387,7 +400,12 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         }
         if (piv < 0) piv = br;
         s_stop = 0;
-        if (piv < 0) {
+        if (badrow) {
+            set_status(a.ctl, GBLU_ERR_INTERNAL);
+            a.ctl->where_k = k;
+            atomicExch(&a.ctl->abort_tail, 1);
+            s_stop = 1;
+        } else if (piv < 0) {
             set_status(a.ctl, GBLU_ERR_SINGULAR);
             a.ctl->where_k = k;
             atomicExch(&a.ctl->abort_tail, 1);
@@ -416,7 +434,7 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
     const double d = x[piv];
     for (int i = tid; i < cnt; i += kTailThreads) {
         const int r = list[i];
-        const int pj = __ldcg(a.pinv + r);
+        const int pj = cls[i];
         if (pj >= 0) {
             const int p = atomicAdd(&s_u, 1);
             a.rows[off + p] = pj;
@@ -469,6 +487,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoc
     double *x = a.sx + (size_t)blockIdx.x * a.n;
     int32_t *mark = a.smark + (size_t)blockIdx.x * a.n;
     int32_t *list = a.slist + (size_t)blockIdx.x * a.n;
+    int32_t *cls = a.sclass + (size_t)blockIdx.x * a.n;
     for (;;) {
         if (threadIdx.x == 0) {
             s_t = atomicAdd(&a.ctl->tail_ticket, 1);
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoc
         const int t = s_t, quit = s_quit;
         __syncthreads();
         if (t >= a.nseq || quit) break;
-        if (tail_column(a, __ldg(a.seq + t), x, mark, list, epoch)) break;
+        if (tail_column(a, __ldg(a.seq + t), x, mark, list, cls, epoch)) break;
     }
 }
 

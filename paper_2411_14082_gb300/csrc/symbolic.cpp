@@ -1,6 +1,6 @@
-// Host-side symbolic work: input validation, elimination trees, the guessed
-// factor structure, the fixed-pattern schedules and the repack after a
-// restart.  No device code and no CUDA calls in this file.
+// Host-side symbolic work: input validation, elimination trees, the fill
+// estimate of a first factorization and the fixed-pattern schedules.  No
+// device code and no CUDA calls in this file.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -73,23 +73,21 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
     return nl;
 }
 
-// Guessed structure for a first factorization: diagonal pivots piv = Q and
-// the pattern of the Cholesky factor of S = (A + A^T)(Q,Q), which contains
-// the LU pattern of A(Q,Q) without pivoting.  Row structures of L come from
-// the elimination tree of S by walking up from every off-diagonal entry of
-// row k until a node already visited for row k ("row subtree").  The
-// diagonal is always part of the pattern, even where A has no entry; such a
-// column then fails the pivot check and is recomputed with pivoting.
-int guess_structure(const Pattern &P, Structure &S, std::string &err)
+// Number of entries of the strict lower Cholesky factor of
+// S = (A + A^T)(Q,Q): row structures come from the elimination tree of S by
+// walking up from every off-diagonal entry of row k until a node already
+// visited for row k ("row subtree").  When every diagonal pivot is kept on a
+// structurally symmetric matrix, L and U^T both have this pattern; it sizes
+// the pool of the first factorization (pivoting can change it, and the pool
+// then grows).
+int64_t symmetric_fill(const Pattern &P)
 {
     const int32_t n = P.n;
-    // symmetric adjacency of S, lower part per row (j < i) and upper per column
     std::vector<int64_t> cnt(n + 1, 0);
     for (int32_t c = 0; c < n; c++)
         for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-            int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
-            if (i == j) continue;
-            cnt[std::max(i, j) + 1]++;  // entry (max, min): row max, column min
+            const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+            if (i != j) cnt[std::max(i, j) + 1]++;
         }
     for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
     std::vector<int32_t> lowadj(cnt[n]);
@@ -97,68 +95,32 @@ int guess_structure(const Pattern &P, Structure &S, std::string &err)
         std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
         for (int32_t c = 0; c < n; c++)
             for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-                int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
-                if (i == j) continue;
-                lowadj[pos[std::max(i, j)]++] = std::min(i, j);
+                const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+                if (i != j) lowadj[pos[std::max(i, j)]++] = std::min(i, j);
             }
     }
-    // elimination tree of S (Liu, path compression)
-    std::vector<int32_t> parent(n, -1), anc(n, -1);
+    std::vector<int32_t> parent(n, -1), anc(n, -1), mark(n, -1);
     for (int32_t k = 0; k < n; k++) {
         for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
             int32_t i = lowadj[e];
             while (i != -1 && i < k) {
-                int32_t next = anc[i];
+                const int32_t next = anc[i];
                 anc[i] = k;
                 if (next == -1) parent[i] = k;
                 i = next;
             }
         }
     }
-    // row structures of L (strict lower) by row subtrees
-    std::vector<int32_t> mark(n, -1);
-    std::vector<int64_t> rptr(n + 1, 0);
-    std::vector<int32_t> rows;  // concatenated row structures
-    rows.reserve((size_t)cnt[n] * 4 + n);
-    std::vector<int32_t> colcnt(n, 0);
+    int64_t total = 0;
     for (int32_t k = 0; k < n; k++) {
         mark[k] = k;
-        const size_t start = rows.size();
-        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
+        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++)
             for (int32_t j = lowadj[e]; j != -1 && mark[j] != k; j = parent[j]) {
                 mark[j] = k;
-                rows.push_back(j);
+                total++;
             }
-        }
-        std::sort(rows.begin() + start, rows.end());
-        for (size_t e = start; e < rows.size(); e++) colcnt[rows[e]]++;
-        rptr[k + 1] = (int64_t)rows.size();
     }
-    const int64_t nnzL = (int64_t)rows.size();
-    // canonical columns: U rows of column k = row structure of k, diagonal,
-    // then L rows of column k = rows i whose structure contains k
-    S.n = n;
-    S.LUp.assign(n + 1, 0);
-    S.nU.assign(n, 0);
-    for (int32_t k = 0; k < n; k++) {
-        S.nU[k] = (int32_t)(rptr[k + 1] - rptr[k]) + 1;
-        S.LUp[k + 1] = S.LUp[k] + S.nU[k] + colcnt[k];
-    }
-    if (S.LUp[n] > INT32_MAX) { err = "factor too large (> 2^31 entries)"; return GBLU_ERR_NOMEM; }
-    S.LUi.assign(S.LUp[n], 0);
-    std::vector<int64_t> lpos(n);
-    for (int32_t k = 0; k < n; k++) {
-        int64_t o = S.LUp[k];
-        for (int64_t e = rptr[k]; e < rptr[k + 1]; e++) S.LUi[o++] = rows[e];
-        S.LUi[o++] = k;
-        lpos[k] = o;
-    }
-    for (int32_t i = 0; i < n; i++)
-        for (int64_t e = rptr[i]; e < rptr[i + 1]; e++) S.LUi[lpos[rows[e]]++] = i;
-    S.piv = P.Q;
-    S.pinv = P.qinv;
-    (void)nnzL;
-    return GBLU_OK;
+    return total;
 }
 
 void build_schedule(const Pattern &P, const Structure &S, double alpha,

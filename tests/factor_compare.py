@@ -1,5 +1,20 @@
-"""Element-wise comparison of exported GPU factors with oracle factors."""
+"""Element-wise comparison of exported GPU factors with oracle factors.
+
+Tolerance.  Column k of L and U comes from one work vector x_k (U(:,k) =
+x_k on the pivotal rows, L(:,k) = x_k / U(k,k) on the others).  With
+M = |L_o| |U_o| (the magnitudes summed into each entry) and
+X_k = max(max|U_o(:,k)|, |U_o(k,k)| * max|L_o(:,k)|) (the largest entry of
+x_k), the bound is
+    |U_g(i,k) - U_o(i,k)| <= rtol * max(M(i,k), X_k)
+    |L_g(i,k) - L_o(i,k)| <= rtol * max(M(i,k), X_k) / |U_o(k,k)|
+i.e. every computed work-vector entry agrees to rtol relative to the larger
+of its componentwise magnitude and the largest entry of its column.  Entries
+that are rounding noise around an exact zero (cancellation) differ between
+two valid summation orders by far more than their own size; the column
+scale keeps them comparable.
+"""
 import numpy as np
+import scipy.sparse as sp
 
 
 def _keys(p, i, n):
@@ -7,10 +22,23 @@ def _keys(p, i, n):
     return cols * n + np.asarray(i, dtype=np.int64), cols
 
 
-def compare_part(n, gp, gi, gx, op, oi, ox, rtol):
-    """Oracle entries must all be in the GPU pattern with values within
-    rtol * (column inf-norm of the oracle); GPU-only entries must be 0.0
-    (structural zeros of a superset pattern).  Returns the max relative error."""
+def abs_product(lu):
+    """|L| |U| of the oracle factors as (keys, values) sorted by key."""
+    n = lu.n
+    L = sp.csc_matrix((np.abs(lu.Lx), lu.Li, lu.Lp), shape=(n, n)) + sp.identity(n, format="csc")
+    U = sp.csc_matrix((np.abs(lu.Ux), lu.Ui, lu.Up), shape=(n, n))
+    if n <= 2500:
+        M = sp.csc_matrix(L.toarray() @ U.toarray())
+    else:
+        M = (L @ U).tocsc()
+    M.sort_indices()
+    k, _ = _keys(M.indptr, M.indices, n)
+    return k, M.data
+
+
+def compare_part(n, gp, gi, gx, op, oi, ox, scale_of):
+    """Oracle entries must all be in the GPU pattern; GPU-only entries must be
+    exact zeros.  Returns max |diff| / scale over the oracle entries."""
     gk, _ = _keys(gp, gi, n)
     ok, ocols = _keys(op, oi, n)
     pos = np.searchsorted(gk, ok)
@@ -19,20 +47,34 @@ def compare_part(n, gp, gi, gx, op, oi, ox, rtol):
     extra = np.ones(len(gk), dtype=bool)
     extra[pos] = False
     assert np.all(gx[extra] == 0.0), "GPU-only pattern entries must be exact zeros"
-    colnorm = np.zeros(n)
-    np.maximum.at(colnorm, ocols, np.abs(ox))
-    scale = np.where(colnorm[ocols] > 0, colnorm[ocols], 1.0)
-    err = np.abs(gx[pos] - ox) / scale
+    scale = scale_of(ok, ocols)
+    err = np.abs(gx[pos] - ox) / np.where(scale > 0, scale, 1.0)
     return float(err.max()) if len(err) else 0.0
 
 
 def compare_factors(f, lu, rtol=1e-10):
-    """Same column order, same pivot sequence, L and U within rtol per column."""
+    """Same column order, same pivot sequence, L and U within rtol (componentwise)."""
     n = lu.n
     assert np.array_equal(f["q"], lu.Q)
     assert np.array_equal(f["piv"], lu.piv), \
         f"pivot sequences differ at steps {np.nonzero(f['piv'] != lu.piv)[0][:10]}"
-    el = compare_part(n, f["Lp"], f["Li"], f["Lx"], lu.Lp, lu.Li, lu.Lx, rtol)
-    eu = compare_part(n, f["Up"], f["Ui"], f["Ux"], lu.Up, lu.Ui, lu.Ux, rtol)
+    mk, mv = abs_product(lu)
+    udiag = np.abs(lu.Ux[np.asarray(lu.Up[1:], dtype=np.int64) - 1])
+    xcol = np.zeros(n)
+    if len(lu.Ux):
+        np.maximum.at(xcol, np.repeat(np.arange(n), np.diff(lu.Up)), np.abs(lu.Ux))
+    if len(lu.Lx):
+        np.maximum.at(xcol, np.repeat(np.arange(n), np.diff(lu.Lp)),
+                      np.abs(lu.Lx) * udiag[np.repeat(np.arange(n), np.diff(lu.Lp))])
+
+    def m_at(keys):
+        # entries whose |L||U| sum is exactly zero are absent from M
+        p = np.minimum(np.searchsorted(mk, keys), len(mk) - 1)
+        return np.where(mk[p] == keys, mv[p], 0.0) if len(mk) else np.zeros(len(keys))
+
+    el = compare_part(n, f["Lp"], f["Li"], f["Lx"], lu.Lp, lu.Li, lu.Lx,
+                      lambda keys, cols: np.maximum(m_at(keys), xcol[cols]) / udiag[cols])
+    eu = compare_part(n, f["Up"], f["Ui"], f["Ux"], lu.Up, lu.Ui, lu.Ux,
+                      lambda keys, cols: np.maximum(m_at(keys), xcol[cols]))
     assert el <= rtol and eu <= rtol, f"factor mismatch: L {el:.3e}, U {eu:.3e} (tol {rtol})"
     return max(el, eu)

@@ -66,14 +66,25 @@ def test_golden_examples_on_gpu(name):
         assert st["n_restart_cols"] == len(g["restart_set"]) and st["last_first_bad"] == 0
 
 
+def well_conditioned(n, Ap, Ai, Ax, limit=1e12):
+    """Pivot choices among rounding noise are arbitrary: compare only
+    matrices whose condition number is far from 1/eps_machine."""
+    A = np.zeros((n, n))
+    for c in range(n):
+        A[Ai[Ap[c]:Ap[c + 1]], c] = Ax[Ap[c]:Ap[c + 1]]
+    return np.linalg.cond(A) < limit
+
+
 @pytest.mark.parametrize("sched", ["auto", "level", "syncfree"])
 def test_random_small_matrices_factorize_and_refactorize(sched):
     rng = np.random.default_rng(42)
-    for trial in range(40):
+    for trial in range(60):
         n = int(rng.integers(1, 80))
         _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.02, 0.3), rng,
                                              zero_diag_frac=rng.uniform(0, 0.3), dominance=1.0)
         Q = rng.permutation(n).astype(np.int32)
+        if not well_conditioned(n, Ap, Ai, Ax):
+            continue
         lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
         s = gblu.Solver(DEV, sched_mode=sched, solve_mode=sched)
         s.analyze(n, Ap, Ai, Q)
@@ -88,6 +99,8 @@ def test_random_small_matrices_factorize_and_refactorize(sched):
         solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
         for it in range(3):
             Ax2 = inputs.perturb_entries(Ax, rng, frac=0.3, sigma=1.0)
+            if not well_conditioned(n, Ap, Ai, Ax2):
+                break
             lu2 = O.refactorize(lu, Ap, Ai, Ax2)
             Axd2 = dev(Ax2)
             if lu2.status != O.OK:
@@ -158,8 +171,10 @@ def test_schedules_give_bitwise_identical_results():
 
 
 def test_forced_repivot_protocol_matches_oracle():
-    """Section VI-A general case: a run is forced to re-pivot at a random
-    column (here: that column's diagonal entry of A is scaled by 1e-12)."""
+    """Section VI-A general case: runs forced to re-pivot at a random column.
+    The pivot entry of A for step k is shifted so that the updated pivot
+    x(k) becomes 1e-9 of its value, far below pivot_tol times the largest
+    entry of L(:,k), so the check must fail at step k (or earlier)."""
     ckt = mesh_small(seed=11)
     n, Ap, Ai, Ax = ckt.csc()
     Q = inputs.grid_nd_order(ckt)
@@ -169,25 +184,38 @@ def test_forced_repivot_protocol_matches_oracle():
     lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
     s.factorize(dev(Ax))
     compare_factors(s.export_factors(), lu, RTOL)
-    diag_slot = {}
-    for c in range(n):
-        for p in range(Ap[c], Ap[c + 1]):
-            if Ai[p] == c:
-                diag_slot[c] = p
-    for trial in range(6):
-        k = int(rng.integers(0, n))
+
+    def slot(r, c):
+        rows = Ai[Ap[c]:Ap[c + 1]]
+        hit = np.nonzero(rows == r)[0]
+        return Ap[c] + hit[0] if len(hit) else None
+
+    done = 0
+    while done < 6:
         Ax2 = inputs.redraw_transistors(ckt, rng).values()
-        Ax2[diag_slot[int(Q[k])]] *= 1e-12
+        ref = O.refactorize(lu, Ap, Ai, Ax2)
+        k = int(rng.integers(0, n))
+        p = slot(lu.piv[k], Q[k])
+        if ref.n_rejected or p is None or ref.Lp[k + 1] == ref.Lp[k]:
+            continue
+        Ax2[p] -= ref.Ux[ref.Up[k + 1] - 1] * (1.0 - 1e-9)
         lu2 = O.refactorize(lu, Ap, Ai, Ax2)
         assert lu2.n_rejected > 0
         Axd2 = dev(Ax2)
         rc, rep = s.refactorize(Axd2)
         assert rc == gblu.REPIVOTED and rep
         st = s.stats()
-        assert st["last_first_bad"] <= k
+        assert 0 <= st["last_first_bad"] <= k
         compare_factors(s.export_factors(), lu2, RTOL)
         solve_and_check(s, n, Ap, Ai, Ax2, Axd2, rng)
-        lu = lu2
+        # the next plain refactorization runs on the new pattern
+        Ax3 = inputs.redraw_transistors(ckt, rng).values()
+        lu3 = O.refactorize(lu2, Ap, Ai, Ax3)
+        rc, rep = s.refactorize(dev(Ax3))
+        assert rep == (lu3.n_rejected > 0)
+        compare_factors(s.export_factors(), lu3, RTOL)
+        lu = lu3
+        done += 1
 
 
 def test_dense_block_uses_long_column_path():
@@ -249,11 +277,20 @@ def test_bounded_wait_returns_timeout_and_context_survives():
     ckt = mesh_small(seed=2)
     n, Ap, Ai, Ax = ckt.csc()
     Q = inputs.grid_nd_order(ckt)
-    s = gblu.Solver(DEV, sched_mode="syncfree", spin_limit=1)
+    s = gblu.Solver(DEV, sched_mode="syncfree", solve_mode="syncfree", spin_limit=1)
     s.analyze(n, Ap, Ai, Q)
-    with pytest.raises(gblu.GbluError) as ei:
-        s.factorize(dev(Ax))
-    assert ei.value.code == gblu.ERR_DEVICE_TIMEOUT
+    codes = []
+    for attempt in range(4):   # a wait must occur at least once; it then gives up
+        try:
+            if attempt == 0 or not codes:
+                s.factorize(dev(Ax))
+            s.refactorize(dev(Ax))
+            s.solve(dev(np.ones(n)))
+            torch.cuda.synchronize()
+        except gblu.GbluError as e:
+            codes.append(e.code)
+            break
+    assert codes == [gblu.ERR_DEVICE_TIMEOUT]
     torch.cuda.synchronize()
     s2 = gblu.Solver(DEV)
     s2.analyze(n, Ap, Ai, Q)
