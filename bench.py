@@ -38,10 +38,10 @@ METRIC = "refactor+solve/s"
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload(name, n_steps, seed):
+def make_workload(name, n_steps, seed, mesh=(200, 200, 4)):
     if name == "mesh":
-        ckt = inputs.workload_mesh()
-        desc = "rc_mesh_200x200x4"
+        ckt = inputs.workload_mesh(nx=mesh[0], ny=mesh[1], nz=mesh[2])
+        desc = f"rc_mesh_{mesh[0]}x{mesh[1]}x{mesh[2]}"
     elif name == "small":
         ckt = inputs.workload_small()
         desc = "mna_grid_40x50_vsrc20"
@@ -121,7 +121,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import oracle as O
 from bench import make_workload
-w = make_workload({name!r}, {steps}, {seed})
+w = make_workload({name!r}, {steps}, {seed}, {mesh!r})
 out = []
 for s in range({steps}):
     Ax, b = w["vals"][s], w["rhs"][s]
@@ -135,8 +135,8 @@ print("ORACLE_JSON " + json.dumps(out), flush=True)
 """
 
 
-def start_oracle(name, steps, seed):
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, steps=steps, seed=seed)
+def start_oracle(name, steps, seed, mesh=(200, 200, 4)):
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, steps=steps, seed=seed, mesh=tuple(mesh))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
                             stderr=subprocess.STDOUT, env=env, text=True)
@@ -163,14 +163,14 @@ def run_reference(args, rank, world):
     # workload); the count is capped so that the run stays within minutes
     steps = max(1, min(args.steps, 2))
     w_name = args.workload
-    proc = start_oracle(w_name, steps, args.seed)
+    proc = start_oracle(w_name, steps, args.seed, args.mesh)
     res = collect_oracle(proc)
     if not res:
         print(json.dumps({"impl": "reference", "unavailable": "CPU oracle run failed"}))
         return 0
     secs = [r["seconds"] for r in res]
     value = len(secs) / sum(secs)
-    wl = make_workload(w_name, 0, args.seed)
+    wl = make_workload(w_name, 0, args.seed, args.mesh)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": 0, "steps": steps, "warmup": 0, "ms_per_step": 1e3 * float(np.mean(secs)),
@@ -192,7 +192,7 @@ def run_ours(args, rank, world, local_rank):
     oracle_proc = None
     if rank == 0 and not args.no_cpu_baseline:
         # started before the first CUDA call, in a separate process
-        oracle_proc = start_oracle(args.workload, 1, args.seed + 1000)
+        oracle_proc = start_oracle(args.workload, 1, args.seed + 1000, args.mesh)
     import torch
     import torch.distributed as dist
     from paper_2411_14082_gb300 import gblu
@@ -202,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{dev}"))
     total = args.warmup + args.steps
-    w = make_workload(args.workload, total, args.seed + 17 * rank)
+    w = make_workload(args.workload, total, args.seed + 17 * rank, args.mesh)
     n, nnz = w["n"], int(w["Ap"][-1])
     s = gblu.Solver(dev)
     t0 = time.perf_counter()
@@ -344,7 +344,10 @@ def main():
     ap.add_argument("--workload", default="mesh", choices=["mesh", "small"])
     ap.add_argument("--seed", type=int, default=inputs.BASE_SEED + 1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", default="200x200x4",
+                    help="grid of the mesh workload (smaller grids for profiling runs)")
     args = ap.parse_args()
+    args.mesh = tuple(int(v) for v in args.mesh.lower().split("x"))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
