@@ -152,6 +152,37 @@ int gblu_residual(gblu_handle h, const double *Ax_dev, const double *b_dev,
 int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host,
                    double *x_host, void *stream, int32_t *repivoted);
 
+/*
+ * Allocation-free solve for callers that cannot allocate device memory (a
+ * simulator that runs on its own fixed device pool, code running while a
+ * CUDA graph is being captured, builds that forbid allocation after
+ * start-up).  The paper has no counterpart; this is an interface
+ * convenience.  It solves A x = b from factors the caller keeps in its own
+ * device buffers, with the same sync-free row solves as gblu_solve, and
+ * allocates nothing: its scratch (intermediate vector, ready flags,
+ * tickets) is one file-scope device array of 8 MB that every GPU loading
+ * the library holds until the process exits.
+ *   Factors, row-wise (CSR) in step numbering, all device arrays:
+ *   Lrp[n+1]/Lcol/Lval = strict lower part of L (unit diagonal implied),
+ *   Urp[n+1]/Ucol/Uval = strict upper part of U, Udiag[n] = U(k,k),
+ *   piv[n] = original row of step k, q[n] = original column of step k
+ *   (gblu_export_factors gives the same factors column-wise).
+ *   b_dev[n] -> x_dev[n] (must not alias); status_dev (optional device
+ *   int32) receives 0 or GBLU_ERR_DEVICE_TIMEOUT when the solve finishes.
+ * n must be <= GBLU_NOALLOC_MAX_N; larger n returns GBLU_ERR_INVALID_INPUT
+ * with a message.  Asynchronous on `stream`.  Every call shares the scratch
+ * array (it keeps the last call's contents; each call clears its flags
+ * first): calls that overlap on the GPU race, so serialize them.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make it before any stream capture.
+ */
+#define GBLU_NOALLOC_MAX_N 524288
+int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lcol,
+                               const double *Lval, const int64_t *Urp, const int32_t *Ucol,
+                               const double *Uval, const double *Udiag, const int32_t *piv,
+                               const int32_t *q, const double *b_dev, double *x_dev,
+                               int32_t *status_dev, void *stream);
+
 /* Sizes and counters of the current factorization (host struct). */
 typedef struct {
     int32_t n;

@@ -65,6 +65,12 @@ struct DBuf {
 
 }  // namespace
 
+int gblu::record_error(int code, const char *msg)
+{
+    g_err = msg;
+    return code;
+}
+
 struct gblu_ctx {
     int device = 0;
     gblu_opts opts{};

@@ -55,6 +55,9 @@ struct Schedule {
     std::vector<int32_t> usv_ptr, usv_rows; int32_t usv_levels = 0, usv_div = 0;
 };
 
+// record a one-line message for gblu_last_error() and return code
+int record_error(int code, const char *msg);
+
 int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
 void column_etree(const Pattern &P, std::vector<int32_t> &parent);
 void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);

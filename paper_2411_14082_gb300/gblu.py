@@ -36,8 +36,10 @@ EXPORTED = [
     "gblu_default_opts", "gblu_last_error", "gblu_create", "gblu_destroy", "gblu_analyze",
     "gblu_factorize", "gblu_refactorize", "gblu_solve", "gblu_residual", "gblu_get_stats",
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
-    "gblu_levels", "gblu_step_host",
+    "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc",
 ]
+
+NOALLOC_MAX_N = 524288
 
 
 class GbluError(RuntimeError):
@@ -99,6 +101,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_column_etree.argtypes = [I32, P, P, P, P]
         lib.gblu_restart_set.argtypes = [I32, P, P, P]
         lib.gblu_restart_set.restype = I64
+        lib.gblu_solve_factors_noalloc.argtypes = [I32] + [P] * 13
+        lib.gblu_solve_factors_noalloc.restype = ctypes.c_int
         lib.gblu_levels.argtypes = [I32, P, P, P]
         lib.gblu_levels.restype = I32
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
@@ -237,6 +241,23 @@ class Solver:
         for k, m in (("Li", nl), ("Lx", nl), ("Ui", nu), ("Ux", nu)):
             out[k] = out[k][:m]
         return out
+
+
+def solve_factors_noalloc(n, Lrp, Lcol, Lval, Urp, Ucol, Uval, Udiag, piv, q, b, x,
+                          status=None, stream=None):
+    """Allocation-free solve from caller-held row-wise factors (all CUDA tensors:
+    Lrp/Urp int64, Lcol/Ucol/piv/q int32, values float64)."""
+    import torch
+    ptrs = []
+    for t, dt in ((Lrp, torch.int64), (Lcol, torch.int32), (Lval, torch.float64),
+                  (Urp, torch.int64), (Ucol, torch.int32), (Uval, torch.float64),
+                  (Udiag, torch.float64), (piv, torch.int32), (q, torch.int32),
+                  (b, torch.float64), (x, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA {dt} tensor")
+        ptrs.append(ctypes.c_void_p(t.data_ptr()))
+    st = None if status is None else ctypes.c_void_p(status.data_ptr())
+    return _check(load().gblu_solve_factors_noalloc(int(n), *ptrs, st, _stream(stream)))
 
 
 # ---------------------------------------------------------------- host-only helpers
