@@ -158,7 +158,7 @@ int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host,
  * CUDA graph is being captured, builds that forbid allocation after
  * start-up).  The paper has no counterpart; this is an interface
  * convenience.  It solves A x = b from factors the caller keeps in its own
- * device buffers, with the same sync-free row solves as gblu_solve, and
+ * device buffers, with sync-free row solves like gblu_solve's, and
  * allocates nothing: its scratch (intermediate vector, ready flags,
  * tickets) is one file-scope device array of 8 MB that every GPU loading
  * the library holds until the process exits.

@@ -75,13 +75,12 @@ struct gblu_ctx {
     int device = 0;
     gblu_opts opts{};
     int sm_count = 0;
-    int smem_cap = 1024;
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0;
     bool analyzed = false, factorized = false;
     Pattern P;
     Structure S;
     Schedule W;
-    int32_t epoch = 0, solve_epoch = 0, tail_epoch = 0;
+    int32_t epoch = 0, tail_epoch = 0;
     int64_t n_refactor = 0, n_repivot = 0, n_restart_cols = 0;
     int64_t launches = 0;
     int32_t last_first_bad = -1;
@@ -94,12 +93,12 @@ struct gblu_ctx {
     // factor structure and values: rows/vals hold the canonical columns
     // followed by the restart pool
     DBuf<int64_t> LUp;
-    DBuf<int32_t> LUi, nU, rows, finish, level_cols, amap, piv, pinv;
+    DBuf<int32_t> LUi, nU, rows, finish, task_ptr, task_cols, amap, piv, pinv;
     DBuf<double> vals;
     // solves
     DBuf<int64_t> Lrp, Urp;
-    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, lflag, uflag;
-    DBuf<double> y, partial, stage_ax, stage_b, stage_x;
+    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows;
+    DBuf<double> y, z, partial, stage_ax, stage_b, stage_x;
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
@@ -185,8 +184,8 @@ int status_code(gblu_ctx *h)
 int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st)
 {
     h->S = std::move(S);
-    const int resident_warps = h->ref_blocks_per_sm * h->sm_count * kRefWarpsPerBlock;
-    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->W);
+    const int resident_warps = h->ref_blocks_per_sm * h->sm_count * (kRefThreads / 32);
+    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, h->W);
     for (int32_t v : h->W.amap)
         if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
     const int32_t n = h->S.n;
@@ -196,17 +195,15 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->nU, h->S.nU, st));
     CK(upload(h, h->piv, h->S.piv, st));
     CK(upload(h, h->pinv, h->S.pinv, st));
-    CK(upload(h, h->level_cols, h->W.level_cols, st));
+    CK(upload(h, h->task_ptr, h->W.task_ptr, st));
+    CK(upload(h, h->task_cols, h->W.task_cols, st));
     CK(upload(h, h->amap, h->W.amap, st));
     CK(ensure(h, h->finish, n));
-    CK(ensure(h, h->lflag, n));
-    CK(ensure(h, h->uflag, n));
     CK(ensure(h, h->y, n));
+    CK(ensure(h, h->z, n));
     // ready flags hold epochs (> 0); recycled device memory may hold any
     // value, so they start from zero
     CU(cudaMemsetAsync(h->finish.p, 0, sizeof(int32_t) * n, st));
-    CU(cudaMemsetAsync(h->lflag.p, 0, sizeof(int32_t) * n, st));
-    CU(cudaMemsetAsync(h->uflag.p, 0, sizeof(int32_t) * n, st));
     // canonical rows/vals; the pool is sized at restart time
     if (h->rows.cap < nnz || h->vals.cap < nnz) {
         CK(ensure(h, h->rows, nnz));
@@ -247,23 +244,27 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     a.nU = h->nU.p;
     a.LUx = h->vals.p;
     a.finish = h->finish.p;
+    a.task_ptr = h->task_ptr.p;
+    a.task_cols = h->task_cols.p;
+    a.cap_short = kRefCapShort;
+    a.cap_long = kRefCapLong;
     a.eps = h->opts.pivot_tol;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
-    const std::vector<int32_t> &lp = h->W.level_ptr;
-    int32_t div = h->W.div_level;
-    if (h->opts.sched_mode == GBLU_SCHED_LEVEL) div = h->W.n_levels;
-    if (h->opts.sched_mode == GBLU_SCHED_SYNCFREE) div = 0;
-    for (int32_t l = 0; l < div; l++) {
-        a.cols = h->level_cols.p + lp[l];
-        a.ncols = lp[l + 1] - lp[l];
-        KL(launch_refactor_level(a, h->smem_cap, h->epoch, st));
+    const std::vector<int32_t> &ltp = h->W.level_task_ptr;
+    const int32_t div = h->W.div_level;   // the schedule already follows sched_mode
+    for (int32_t l = 0; l < div; l++) {   // cluster mode: one launch per level
+        a.task_begin = ltp[l];
+        a.ntasks = ltp[l + 1] - ltp[l];
+        KL(launch_refactor_tasks(a, false, 0, h->epoch, st));
     }
-    if (div < h->W.n_levels) {
-        a.cols = h->level_cols.p + lp[div];
-        a.ncols = n - lp[div];
-        KL(launch_refactor_syncfree(a, h->smem_cap, h->ref_grid, h->epoch, st));
+    const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
+    if (ltp[div] < ntask) {               // pipeline mode: one persistent launch
+        a.task_begin = ltp[div];
+        a.ntasks = ntask - ltp[div];
+        KL(launch_refactor_tasks(a, true, h->ref_grid, h->epoch, st));
     }
+    (void)n;
     CK(read_ctl(h, st));
     CK(status_code(h));
     *interrupted = h->hctl->interrupted;
@@ -503,7 +504,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->ctl, sizeof(DevCtl));
     if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(DevCtl));
     int r = 0;
-    if (e == cudaSuccess) r = refactor_max_resident_blocks(h->smem_cap, &h->ref_blocks_per_sm);
+    if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
     if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
         const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
@@ -528,12 +529,12 @@ void gblu_destroy(gblu_handle h)
         release(h, h->Ap); release(h, h->Ai); release(h, h->Q); release(h, h->qinv);
         release(h, h->clo); release(h, h->Acol); release(h, h->Aslot); release(h, h->Arp);
         release(h, h->LUp); release(h, h->LUi); release(h, h->nU); release(h, h->rows);
-        release(h, h->finish); release(h, h->level_cols); release(h, h->amap);
+        release(h, h->finish); release(h, h->task_ptr); release(h, h->task_cols); release(h, h->amap);
         release(h, h->piv); release(h, h->pinv); release(h, h->vals);
         release(h, h->Lrp); release(h, h->Urp); release(h, h->Lcol); release(h, h->Lslot);
         release(h, h->Ucol); release(h, h->Uslot); release(h, h->Udiag);
-        release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->lflag);
-        release(h, h->uflag); release(h, h->y); release(h, h->partial);
+        release(h, h->lsv_rows); release(h, h->usv_rows);
+        release(h, h->y); release(h, h->z); release(h, h->partial);
         release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
         release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
         release(h, h->tpinv); release(h, h->cnu); release(h, h->cnl); release(h, h->smark);
@@ -676,8 +677,7 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t n = h->S.n;
-    h->solve_epoch++;
-    KL(launch_begin_solve(h->ctl, st));
+    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, n, st));
     SolveArgs a{};
     a.n = n;
     a.LUx = h->vals.p;
@@ -692,9 +692,8 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     a.Q = h->Q.p;
     a.b = b_dev;
     a.y = h->y.p;
+    a.z = h->z.p;
     a.x = x_dev;
-    a.lflag = h->lflag.p;
-    a.uflag = h->uflag.p;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
     const Schedule &W = h->W;
@@ -709,15 +708,13 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
         for (int32_t l = 0; l < div; l++) {
             a.rows = rows + ptr[l];
             a.nrows = ptr[l + 1] - ptr[l];
-            KL(lower ? launch_lsolve(a, true, 0, h->solve_epoch, st)
-                     : launch_usolve(a, true, 0, h->solve_epoch, st));
+            KL(lower ? launch_lsolve(a, true, 0, st) : launch_usolve(a, true, 0, st));
         }
         if (div < nlev) {
-            KL(launch_flag_rows(rows, ptr[div], lower ? h->lflag.p : h->uflag.p, h->solve_epoch, st));
             a.rows = rows + ptr[div];
             a.nrows = n - ptr[div];
-            KL(lower ? launch_lsolve(a, false, h->solve_grid, h->solve_epoch, st)
-                     : launch_usolve(a, false, h->solve_grid, h->solve_epoch, st));
+            KL(lower ? launch_lsolve(a, false, h->solve_grid, st)
+                     : launch_usolve(a, false, h->solve_grid, st));
         }
     }
     return GBLU_OK;

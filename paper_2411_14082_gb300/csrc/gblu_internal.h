@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gblu.h"
+#include "gblu.h"
 
 namespace gblu {
 
@@ -43,6 +43,11 @@ struct Schedule {
     std::vector<int32_t> level_cols;  // columns sorted by level
     int32_t n_levels = 0;
     int32_t div_level = 0;            // levels [div_level, n_levels) run sync-free
+    // refactor tasks: task t = task_cols[task_ptr[t] .. task_ptr[t+1]), either
+    // one long column (whole CTA) or up to 8 short columns (one per warp);
+    // tasks of level l < div_level are [level_task_ptr[l], level_task_ptr[l+1]),
+    // the sync-free tasks start at level_task_ptr[div_level]
+    std::vector<int32_t> task_ptr, task_cols, level_task_ptr;
     std::vector<int32_t> amap;        // A slot -> position inside its column
     std::vector<int32_t> LUi_orig;    // L entries: original row ids (U: step ids)
     double flops = 0;
@@ -66,7 +71,7 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
 // symmetric matrix; used to size the first factorization's pool
 int64_t symmetric_fill(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
-                    int resident_warps, Schedule &W);
+                    int resident_warps, int sched_mode, int cap_short, Schedule &W);
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
                   const int32_t *nU_or_null, std::vector<int32_t> &level);
 
@@ -98,8 +103,9 @@ struct RefactorArgs {
     const int32_t *LUi, *nU;
     double *LUx;
     int32_t *finish;
-    const int32_t *cols;            // level_cols (level mode) or sequence (sync-free)
-    int32_t ncols;
+    const int32_t *task_ptr, *task_cols;
+    int32_t task_begin, ntasks;     // tasks of this launch
+    int32_t cap_short, cap_long;    // shared-memory work vector entries (warp / CTA)
     double eps;
     long long spin_limit;
     DevCtl *ctl;
@@ -138,8 +144,7 @@ struct SolveArgs {
     const int32_t *Lcol, *Lslot, *Ucol, *Uslot, *Udiag;
     const int32_t *piv, *Q;
     const double *b;
-    double *y, *x;
-    int32_t *lflag, *uflag;
+    double *y, *z, *x;              // forward result, backward result, output
     const int32_t *rows;            // level-mode row list
     int32_t nrows;
     long long spin_limit;
@@ -148,24 +153,24 @@ struct SolveArgs {
 
 // kernel launchers (kernels.cu); each returns a cudaError_t as int
 int launch_begin_refactor(DevCtl *ctl, void *stream);
-int launch_refactor_level(const RefactorArgs &a, int smem_cap, int epoch, void *stream);
-int launch_refactor_syncfree(const RefactorArgs &a, int smem_cap, int grid, int epoch, void *stream);
-int refactor_max_resident_blocks(int smem_cap, int *blocks_per_sm);
+int refactor_setup(int cap_long, int *blocks_per_sm);
+int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
-int launch_begin_solve(DevCtl *ctl, void *stream);
-int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream);
-int launch_usolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream);
-int launch_flag_rows(const int32_t *rows, int nrows, int32_t *flag, int epoch, void *stream);
+int launch_begin_solve(DevCtl *ctl, double *y, double *z, int n, void *stream);
+int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
+int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
                     const int32_t *Aslot, const double *Ax, const double *b,
                     const double *x, double *out, double *partial, int nblocks,
                     void *stream);
 int solve_syncfree_grid(int *grid);
 
-constexpr int kRefWarpsPerBlock = 4;
+constexpr int kRefThreads = 256;       // 8 warps per refactor CTA
+constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short columns)
+constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
 

@@ -1,18 +1,14 @@
 // Device kernels of the sparse LU path (sm_103a).
 //
-//  * refactor_*      fast re-factorization with pivot check (Section IV-B,
-//                    Algorithms 3 and 4): one warp per column, left-looking
-//                    updates into a work vector staged in shared memory;
-//                    level-synchronous launches (cluster mode) or one
-//                    persistent launch with ready flags (pipeline mode).
+//  (the checked re-factorization kernels are in refactor.cu)
 //  * tail_kernel     factorization with threshold pivoting of a set of
 //                    columns (Section IV-D, Algorithm 5 and Algorithm 1):
 //                    one CTA per column, columns taken in increasing order
 //                    by an atomic ticket, waiting on ready flags of earlier
 //                    columns.
 //  * lsolve/usolve   triangular solves (Algorithm 2, Section V): one warp
-//                    per row on row-wise copies, level launches or ready
-//                    flags.
+//                    per row on row-wise copies, level launches or values
+//                    published with a NaN sentinel (sync-free).
 //  * residual        ||b - A x||_inf / (||A||_inf ||x||_inf) in float64.
 //
 // Every wait is bounded by spin_limit iterations; on expiry the kernel
@@ -22,221 +18,14 @@
 #include <climits>
 #include <cstdint>
 
+#include "device_util.cuh"
 #include "gblu_internal.h"
 
 namespace gblu {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ int ld_acquire(const int32_t *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int32_t *p, int v)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int ld_volatile(const int32_t *p)
-{
-    return *(const volatile int32_t *)p;
-}
-
-__device__ __forceinline__ void set_status(DevCtl *ctl, int code)
-{
-    atomicCAS(&ctl->status, 0, code);
-}
-
-__device__ __forceinline__ double warp_max(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-// ---------------------------------------------------------------------------
-// One column of the checked re-factorization, computed by one warp.
-//
-// Column k's pattern (sorted step numbers: U rows, diagonal k, L rows) is
-// the work vector's index set.  x = A(:,Q[k]) is scattered through amap;
-// then for every dependency j (U rows above the diagonal, ascending, which is
-// a topological order) x(rows of L(:,j)) -= x(j) * L(:,j).  The slot of an
-// L(:,j) row inside column k is found by binary search in the sorted
-// pattern, narrowed by the previous chunk's slot (rows and slots are both
-// strictly increasing).  Then the pivot check and the stores.
-//
-// Returns true when the warp has to stop (timeout or error in kWait mode).
-template <bool kWait>
-__device__ bool refactor_column(const RefactorArgs &a, int k, double *xs, int32_t *rs,
-                                int cap, int lane, int epoch)
-{
-    const int64_t beg = __ldg(a.LUp + k);
-    const int len = (int)(__ldg(a.LUp + k + 1) - beg);
-    const int nU = __ldg(a.nU + k);
-    const bool in_smem = len <= cap;
-    double *x = in_smem ? xs : a.LUx + beg;
-    const int32_t *rows = in_smem ? rs : a.LUi + beg;
-    for (int i = lane; i < len; i += 32) {
-        if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
-        x[i] = 0.0;
-    }
-    __syncwarp();
-    {
-        const int c = __ldg(a.Q + k);
-        const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
-        for (int e = ab + lane; e < ae; e += 32) {
-            const int s = __ldg(a.amap + e);
-            if (s >= 0 && s < len) x[s] = __ldg(a.Ax + e);
-            else set_status(a.ctl, GBLU_ERR_INTERNAL);
-        }
-    }
-    __syncwarp();
-
-    int ready = 0;  // dependencies [0, ready) are known to be finished
-    for (int t = 0; t < nU - 1; ++t) {
-        const int j = rows[t];
-        if (kWait && t >= ready) {
-            const int tt = t + lane;
-            bool ok = true;
-            if (tt < nU - 1) ok = ld_acquire(a.finish + rows[tt]) == epoch;
-            const unsigned m = __ballot_sync(kFull, ok);
-            int run = (m == kFull) ? 32 : __ffs(~m) - 1;
-            if (run == 0) {
-                long long it = 0;
-                for (;;) {
-                    if (ld_acquire(a.finish + j) == epoch) break;
-                    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return true;
-                    if (++it > a.spin_limit) {
-                        if (lane == 0) {
-                            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
-                            a.ctl->where = 1;
-                            a.ctl->where_k = k;
-                        }
-                        return true;
-                    }
-                    __nanosleep(64);
-                }
-                run = 1;
-            }
-            ready = t + run;
-            __syncwarp();
-        }
-        const double xj = x[t];
-        const int64_t lb = __ldg(a.LUp + j) + __ldg(a.nU + j);
-        const int64_t le = __ldg(a.LUp + j + 1);
-        int bslot = t, brow = j;
-        for (int64_t e0 = lb; e0 < le; e0 += 32) {
-            const int64_t e = e0 + lane;
-            const bool act = e < le;
-            int r = INT_MAX, s = 0;
-            double v = 0.0;
-            bool bad = false;
-            if (act) {
-                r = __ldg(a.LUi + e);
-                v = __ldcg(a.LUx + e);
-                int lo = bslot + 1 + lane;
-                int hi = bslot + (r - brow);
-                if (hi > len - 1) hi = len - 1;
-                if (lo > hi) {
-                    bad = true;
-                } else {
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (rows[mid] < r) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    s = lo;
-                    bad = rows[s] != r;
-                }
-            }
-            if (__any_sync(kFull, bad)) {  // pattern inconsistent: never index with it
-                if (lane == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
-                return true;
-            }
-            if (act) x[s] = fma(-xj, v, x[s]);
-            const int last = (le - e0 >= 32) ? 31 : (int)(le - e0 - 1);
-            bslot = __shfl_sync(kFull, s, last);
-            brow = __shfl_sync(kFull, r, last);
-        }
-        __syncwarp();
-    }
-
-    // ---- pivot check (Algorithm 3 line 8 / Algorithm 4 line 10) ----
-    const double d = x[nU - 1];
-    double m = 0.0;
-    for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
-    m = warp_max(m);
-    const bool pass = (d != 0.0) && (fabs(d) >= a.eps * m);
-    if (!pass) {
-        if (lane == 0) {
-            atomicExch(&a.ctl->interrupted, 1);
-            atomicMin(&a.ctl->first_bad, k);
-        }
-        return false;
-    }
-    // ---- store U(:,k) and L(:,k) = x / pivot ----
-    if (in_smem) {
-        for (int i = lane; i < len; i += 32) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] / d;
-    } else {
-        for (int i = nU + lane; i < len; i += 32) x[i] = x[i] / d;
-    }
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(a.finish + k, epoch);
-    return false;
-}
-
-__global__ void begin_refactor_kernel(DevCtl *ctl)
-{
-    ctl->ticket = 0;
-    ctl->interrupted = 0;
-    ctl->first_bad = INT_MAX;
-    ctl->status = 0;
-    ctl->where = 0;
-    ctl->where_k = -1;
-}
-
-__global__ void __launch_bounds__(kRefWarpsPerBlock * 32)
-refactor_level_kernel(RefactorArgs a, int cap, int epoch)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *xs = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
-    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)kRefWarpsPerBlock * cap * sizeof(double)) +
-                  (size_t)warp * cap;
-    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return;
-    const int idx = blockIdx.x * kRefWarpsPerBlock + warp;
-    if (idx >= a.ncols) return;
-    refactor_column<false>(a, __ldg(a.cols + idx), xs, rs, cap, lane, epoch);
-}
-
-__global__ void __launch_bounds__(kRefWarpsPerBlock * 32)
-refactor_syncfree_kernel(RefactorArgs a, int cap, int epoch)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *xs = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
-    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)kRefWarpsPerBlock * cap * sizeof(double)) +
-                  (size_t)warp * cap;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&a.ctl->ticket, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= a.ncols) break;
-        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) break;
-        if (refactor_column<true>(a, __ldg(a.cols + t), xs, rs, cap, lane, epoch)) break;
-    }
-}
+using namespace dev;
 
 // ---------------------------------------------------------------------------
 // Factorization with threshold pivoting of the columns in a.seq (ascending),
@@ -503,86 +292,103 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoc
 
 // ---------------------------------------------------------------------------
 // Triangular solves on row-wise copies (Algorithm 2): one warp per row; the
-// lanes split the row, the dot product is reduced in a fixed tree so that
-// the result does not depend on the schedule.
-__global__ void begin_solve_kernel(DevCtl *ctl)
+// lanes split the row and the dot product is reduced in a fixed tree, so the
+// result does not depend on the schedule.
+//
+// Readiness travels with the values: before each solve y (forward result)
+// and z (backward result) are filled with a NaN sentinel; a row publishes its
+// value with one 64-bit store, and a consumer polls the value itself with
+// relaxed 64-bit loads until it is no longer the sentinel.  No flag array
+// and no fence per dependency; a lane consumes each dependency as soon as it
+// lands.  Backward rows walk their entries from the highest column down,
+// the order in which those values are produced.
+constexpr unsigned long long kSentinel = 0xFFF4B1A5C0DEF00DULL;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double *p)
 {
-    ctl->ticket_l = 0;
-    ctl->ticket_u = 0;
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-template <bool kWait>
-__device__ bool lsolve_row(const SolveArgs &a, int i, int lane, int epoch)
+__device__ __forceinline__ void st_relaxed_f64(double *p, double v)
 {
-    double s = 0.0;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+}
+
+__global__ void begin_solve_kernel(DevCtl *ctl, double *y, double *z, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        y[i] = __longlong_as_double((long long)kSentinel);
+        z[i] = __longlong_as_double((long long)kSentinel);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->ticket_l = 0;
+        ctl->ticket_u = 0;
+    }
+}
+
+// value of v[j] once it is published; false if the wait gave up
+__device__ __forceinline__ bool await_value(const double *v, int j, const SolveArgs &a, int site,
+                                            int row, double &out)
+{
+    unsigned long long b = ld_relaxed_u64(v + j);
+    long long it = 0;
+    while (b == kSentinel) {
+        if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
+            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+            a.ctl->where = site;
+            a.ctl->where_k = row;
+            return false;
+        }
+        __nanosleep(32);
+        b = ld_relaxed_u64(v + j);
+    }
+    out = __longlong_as_double((long long)b);
+    return true;
+}
+
+__device__ bool lsolve_row(const SolveArgs &a, int i, int lane)
+{
     const int64_t rb = __ldg(a.Lrp + i), re = __ldg(a.Lrp + i + 1);
-    for (int64_t e = rb + lane; e < re; e += 32) {
-        const int j = __ldg(a.Lcol + e);
-        if (kWait) {
-            long long it = 0;
-            while (ld_acquire(a.lflag + j) != epoch) {
-                if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
-                    set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
-                    a.ctl->where = 3;
-                    a.ctl->where_k = i;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), __ldcg(a.y + j), s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) {
-        a.y[i] = __ldg(a.b + __ldg(a.piv + i)) - s;
-        if (kWait) {
-            __threadfence();
-            st_release(a.lflag + i, epoch);
-        }
-    }
-    return kWait && ld_volatile(&a.ctl->status) != 0;
-}
-
-template <bool kWait>
-__device__ bool usolve_row(const SolveArgs &a, int i, int lane, int epoch)
-{
     double s = 0.0;
-    const int64_t rb = __ldg(a.Urp + i), re = __ldg(a.Urp + i + 1);
+    bool ok = true;
     for (int64_t e = rb + lane; e < re; e += 32) {
-        const int j = __ldg(a.Ucol + e);
-        if (kWait) {
-            long long it = 0;
-            while (ld_acquire(a.uflag + j) != epoch) {
-                if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
-                    set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
-                    a.ctl->where = 4;
-                    a.ctl->where_k = i;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), __ldcg(a.y + j), s);
+        double yj = 0.0;
+        if (ok) ok = await_value(a.y, __ldg(a.Lcol + e), a, 3, i, yj);
+        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), yj, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) st_relaxed_f64(a.y + i, __ldg(a.b + __ldg(a.piv + i)) - s);
+    return !__all_sync(kFull, ok);
+}
+
+__device__ bool usolve_row(const SolveArgs &a, int i, int lane)
+{
+    const int64_t rb = __ldg(a.Urp + i), re = __ldg(a.Urp + i + 1);
+    double s = 0.0;
+    bool ok = true;
+    for (int64_t e = re - 1 - lane; e >= rb; e -= 32) {
+        double zj = 0.0;
+        if (ok) ok = await_value(a.z, __ldg(a.Ucol + e), a, 4, i, zj);
+        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), zj, s);
     }
     s = warp_sum(s);
     if (lane == 0) {
-        const double z = (__ldcg(a.y + i) - s) / __ldg(a.LUx + __ldg(a.Udiag + i));
-        a.y[i] = z;
-        a.x[__ldg(a.Q + i)] = z;
-        if (kWait) {
-            __threadfence();
-            st_release(a.uflag + i, epoch);
-        }
+        const double zi = (__ldcg(a.y + i) - s) / __ldg(a.LUx + __ldg(a.Udiag + i));
+        st_relaxed_f64(a.z + i, zi);
+        a.x[__ldg(a.Q + i)] = zi;
     }
-    return kWait && ld_volatile(&a.ctl->status) != 0;
+    return !__all_sync(kFull, ok);
 }
 
+// level mode: the rows of one level, one warp each
 __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
 lsolve_level_kernel(SolveArgs a)
 {
     const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= a.nrows) return;
-    lsolve_row<false>(a, __ldg(a.rows + w), threadIdx.x & 31, 0);
+    lsolve_row(a, __ldg(a.rows + w), threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
@@ -590,14 +396,12 @@ usolve_level_kernel(SolveArgs a)
 {
     const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= a.nrows) return;
-    usolve_row<false>(a, __ldg(a.rows + w), threadIdx.x & 31, 0);
+    usolve_row(a, __ldg(a.rows + w), threadIdx.x & 31);
 }
 
-// Sync-free: the rows a.rows[0..nrows) are in a topological order; rows not
-// in the list are already final and flagged by the level kernels (flags are
-// set for them by flag_rows_kernel).
+// sync-free: a.rows[0..nrows) in a topological order, handed out by ticket
 __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-lsolve_syncfree_kernel(SolveArgs a, int epoch)
+lsolve_syncfree_kernel(SolveArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -605,12 +409,12 @@ lsolve_syncfree_kernel(SolveArgs a, int epoch)
         if (lane == 0) t = atomicAdd(&a.ctl->ticket_l, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= a.nrows) break;
-        if (lsolve_row<true>(a, __ldg(a.rows + t), lane, epoch)) break;
+        if (lsolve_row(a, __ldg(a.rows + t), lane)) break;
     }
 }
 
 __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-usolve_syncfree_kernel(SolveArgs a, int epoch)
+usolve_syncfree_kernel(SolveArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -618,14 +422,8 @@ usolve_syncfree_kernel(SolveArgs a, int epoch)
         if (lane == 0) t = atomicAdd(&a.ctl->ticket_u, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= a.nrows) break;
-        if (usolve_row<true>(a, __ldg(a.rows + t), lane, epoch)) break;
+        if (usolve_row(a, __ldg(a.rows + t), lane)) break;
     }
-}
-
-__global__ void flag_rows_kernel(const int32_t *rows, int nrows, int32_t *flag, int epoch)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x)
-        flag[rows[i]] = epoch;
 }
 
 // ---------------------------------------------------------------------------
@@ -681,46 +479,6 @@ __global__ void residual_final_kernel(const double *partial, int nblocks, double
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-static size_t refactor_smem(int cap)
-{
-    return (size_t)kRefWarpsPerBlock * cap * (sizeof(double) + sizeof(int32_t));
-}
-
-int launch_begin_refactor(DevCtl *ctl, void *stream)
-{
-    begin_refactor_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
-    return (int)cudaGetLastError();
-}
-
-int refactor_max_resident_blocks(int smem_cap, int *blocks_per_sm)
-{
-    const size_t sm = refactor_smem(smem_cap);
-    cudaError_t e = cudaFuncSetAttribute(refactor_syncfree_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(refactor_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, refactor_syncfree_kernel, kRefWarpsPerBlock * 32, sm);
-}
-
-int launch_refactor_level(const RefactorArgs &a, int smem_cap, int epoch, void *stream)
-{
-    if (a.ncols <= 0) return 0;
-    const int grid = (a.ncols + kRefWarpsPerBlock - 1) / kRefWarpsPerBlock;
-    refactor_level_kernel<<<grid, kRefWarpsPerBlock * 32, refactor_smem(smem_cap), (cudaStream_t)stream>>>(
-        a, smem_cap, epoch);
-    return (int)cudaGetLastError();
-}
-
-int launch_refactor_syncfree(const RefactorArgs &a, int smem_cap, int grid, int epoch, void *stream)
-{
-    if (a.ncols <= 0) return 0;
-    refactor_syncfree_kernel<<<grid, kRefWarpsPerBlock * 32, refactor_smem(smem_cap), (cudaStream_t)stream>>>(
-        a, smem_cap, epoch);
-    return (int)cudaGetLastError();
-}
-
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream)
 {
     begin_tail_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, pool_base);
@@ -742,41 +500,34 @@ int launch_tail(const TailArgs &a, int grid, int epoch, void *stream)
     return (int)cudaGetLastError();
 }
 
-int launch_begin_solve(DevCtl *ctl, void *stream)
+int launch_begin_solve(DevCtl *ctl, double *y, double *z, int n, void *stream)
 {
-    begin_solve_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
+    const int grid = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
+    begin_solve_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(ctl, y, z, n);
     return (int)cudaGetLastError();
 }
 
-int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream)
+int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
     if (level_mode) {
         const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
         lsolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     } else {
-        lsolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a, epoch);
+        lsolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     }
     return (int)cudaGetLastError();
 }
 
-int launch_usolve(const SolveArgs &a, bool level_mode, int grid, int epoch, void *stream)
+int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
     if (level_mode) {
         const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
         usolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     } else {
-        usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a, epoch);
+        usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     }
-    return (int)cudaGetLastError();
-}
-
-int launch_flag_rows(const int32_t *rows, int nrows, int32_t *flag, int epoch, void *stream)
-{
-    if (nrows <= 0) return 0;
-    const int grid = (nrows + 255) / 256 < 4096 ? (nrows + 255) / 256 : 4096;
-    flag_rows_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(rows, nrows, flag, epoch);
     return (int)cudaGetLastError();
 }
 

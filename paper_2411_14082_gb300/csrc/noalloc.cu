@@ -5,8 +5,8 @@
 // runs while a CUDA graph is being captured into a pool it does not own, or
 // embedded/safety-certified builds that forbid allocation after start-up.
 // They keep the LU factors in their own device buffers and only need the
-// solve.  This entry point runs the same sync-free row solves as the
-// handle's gblu_solve, but its scratch (the intermediate vector, the ready
+// solve.  This entry point runs sync-free row solves (one warp per row,
+// ready flags) like the handle's gblu_solve, but its scratch (the intermediate vector, the ready
 // flags and the work tickets) lives in one file-scope static device array
 // instead of handle-owned allocations.  The paper has no counterpart; it is
 // an interface convenience.

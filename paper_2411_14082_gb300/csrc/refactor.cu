@@ -1,0 +1,409 @@
+// Checked re-factorization on a fixed pattern (Section IV-B, Algorithms 3
+// and 4), CSC left-looking form.
+//
+// Column k's pattern (step numbers, sorted: U rows, diagonal k, L rows) is
+// the index set of its work vector x.  x = A(:,Q[k]) is scattered through
+// amap; then for every dependency j (the U rows above the diagonal, in
+// ascending order, which is a topological order)
+//     x(rows of L(:,j)) -= x(j) * L(:,j);
+// then the pivot check |x(k)| >= eps * max|x(L rows)| and x(k) != 0, and
+// the stores U(:,k) = x(U rows), L(:,k) = x(L rows) / x(k).
+//
+// Work is handed out as tasks (built on the host in level order): a task is
+// either one long column, computed by all 8 warps of a CTA with its work
+// vector in shared memory, or up to 8 short columns, one per warp.  The
+// slot of an L(:,j) row inside column k comes from a binary search in the
+// sorted pattern over [t+1+i, t+(r-j)] (t = slot of j, i = index of the row
+// inside L(:,j)); the interval is exact inside dense runs, so dense parts
+// need no search steps.  L(:,k) is stored as x * (1 / x(k)).
+//
+// Two schedules (Section III-B): cluster mode = one launch per level with no
+// waits; pipeline mode = one persistent launch whose CTAs take tasks by an
+// atomic ticket and wait on per-column ready flags (epochs) before using a
+// dependency.  A failing pivot sets `interrupted` (Algorithm 3 line 9 /
+// Algorithm 4 line 11); waiting CTAs poll it and leave.  Every wait is
+// bounded by spin_limit iterations.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "gblu_internal.h"
+
+namespace gblu {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kThreads = kRefThreads;
+constexpr int kWarps = kRefThreads / 32;
+constexpr int kBatch = 4;
+
+// ---------------------------------------------------------------------------
+// slot of row r inside column k's sorted pattern, searched in [lo, hi]
+// (hi clamped to the column); -1 if r is not there
+__device__ __forceinline__ int find_slot(const int32_t *rows, int lo, int hi, int len, int r)
+{
+    if (hi > len - 1) hi = len - 1;
+    if (lo > hi) return -1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rows[mid] < r) lo = mid + 1;
+        else hi = mid;
+    }
+    return rows[lo] == r ? lo : -1;
+}
+
+// one column, one warp.  Every 32 dependencies the lanes check their ready
+// flags and load their (start, length) in L; the values are then broadcast
+// by shuffles, so a dependency step needs no dependent global load before
+// its entries.
+template <bool kWait>
+__device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int lane,
+                         int epoch)
+{
+    const int64_t beg = __ldg(a.LUp + k);
+    const int len = (int)(__ldg(a.LUp + k + 1) - beg);
+    const int nU = __ldg(a.nU + k);
+    const int nD = nU - 1;
+    const bool in_smem = len <= a.cap_short;
+    double *x = in_smem ? xs : a.LUx + beg;
+    const int32_t *rows = in_smem ? rs : a.LUi + beg;
+    for (int i = lane; i < len; i += 32) {
+        if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
+        x[i] = 0.0;
+    }
+    __syncwarp();
+    {
+        const int c = __ldg(a.Q + k);
+        const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
+        for (int e = ab + lane; e < ae; e += 32) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
+    }
+    __syncwarp();
+
+    int ready = 0, mbase = 0;
+    long long m_lb = 0;
+    int m_nl = 0;
+    for (int t = 0; t < nD; ++t) {
+        if (t >= ready) {
+            const int tt = t + lane;
+            const int jj = tt < nD ? rows[tt] : -1;
+            bool ok = true;
+            if (jj >= 0) {
+                if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
+                m_lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
+                m_nl = (int)(__ldg(a.LUp + jj + 1) - m_lb);
+            }
+            const unsigned m = __ballot_sync(kFull, ok);
+            int run = (m == kFull) ? 32 : __ffs(~m) - 1;
+            if (run == 0) {
+                long long it = 0;
+                while (ld_acquire(a.finish + rows[t]) != epoch) {
+                    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return true;
+                    if (++it > a.spin_limit) {
+                        if (lane == 0) {
+                            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                            a.ctl->where = 1;
+                            a.ctl->where_k = k;
+                        }
+                        return true;
+                    }
+                    if (it > 64) __nanosleep(64);
+                }
+                run = 1;
+            }
+            ready = t + run;
+            mbase = t;
+            __syncwarp();
+        }
+        const int j = rows[t];
+        const double xj = x[t];
+        const int64_t lb = __shfl_sync(kFull, m_lb, t - mbase);
+        const int nl = __shfl_sync(kFull, m_nl, t - mbase);
+        for (int base = 0; base < nl; base += 32 * kBatch) {
+            int r[kBatch];
+            double v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                const int i = base + u * 32 + lane;
+                r[u] = i < nl ? __ldg(a.LUi + lb + i) : -1;
+                v[u] = i < nl ? __ldcg(a.LUx + lb + i) : 0.0;
+            }
+            bool bad = false;
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                if (r[u] < 0) continue;
+                const int i = base + u * 32 + lane;
+                const int sl = find_slot(rows, t + 1 + i, t + (r[u] - j), len, r[u]);
+                if (sl < 0) { bad = true; continue; }
+                x[sl] = fma(-xj, v[u], x[sl]);
+            }
+            if (__any_sync(kFull, bad)) {  // inconsistent pattern: never index with it
+                if (lane == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
+                return true;
+            }
+        }
+        __syncwarp();
+    }
+
+    const double d = x[nU - 1];
+    double m = 0.0;
+    for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
+    m = warp_max(m);
+    if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
+        if (lane == 0) {
+            atomicExch(&a.ctl->interrupted, 1);
+            atomicMin(&a.ctl->first_bad, k);
+        }
+        return false;
+    }
+    const double inv = 1.0 / d;
+    if (in_smem) {
+        for (int i = lane; i < len; i += 32) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
+    } else {
+        for (int i = nU + lane; i < len; i += 32) x[i] = x[i] * inv;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(a.finish + k, epoch);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// one long column, the whole CTA.  Every 32 dependencies warp 0 checks
+// their ready flags and stages their (start, length) in L in shared memory;
+// the dependency loop is software pipelined: while dependency t is applied,
+// the (row, value) entries of dependency t+1 are being loaded into
+// registers, so global-load latency overlaps the updates and the barrier.
+constexpr int kPre = 8;   // entries per thread held in registers: 2,048 per dependency
+
+__device__ __forceinline__ bool spin_until(const int32_t *flag, int epoch, const RefactorArgs &a, int k)
+{
+    long long it = 0;
+    while (ld_acquire(flag) != epoch) {
+        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return false;
+        if (++it > a.spin_limit) {
+            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+            a.ctl->where = 1;
+            a.ctl->where_k = k;
+            return false;
+        }
+        if (it > 64) __nanosleep(64);
+    }
+    return true;
+}
+
+template <bool kWait>
+__device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch)
+{
+    __shared__ int s_ready, s_stop;
+    __shared__ long long s_lb[32];
+    __shared__ int s_nl[32];
+    __shared__ double s_red[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t beg = __ldg(a.LUp + k);
+    const int len = (int)(__ldg(a.LUp + k + 1) - beg);
+    const int nU = __ldg(a.nU + k);
+    const int nD = nU - 1;
+    const bool in_smem = len <= a.cap_long;
+    double *x = in_smem ? xs : a.LUx + beg;
+    const int32_t *rows = in_smem ? rs : a.LUi + beg;
+    for (int i = tid; i < len; i += kThreads) {
+        if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
+        x[i] = 0.0;
+    }
+    if (tid == 0) { s_ready = 0; s_stop = 0; }
+    __syncthreads();
+    {
+        const int c = __ldg(a.Q + k);
+        const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
+        for (int e = ab + tid; e < ae; e += kThreads) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
+    }
+    __syncthreads();
+
+    int nr[kPre];
+    double nv[kPre];
+    bool have = false;
+    auto load_entries = [&](long long lb, int nl) {
+#pragma unroll
+        for (int u = 0; u < kPre; u++) {
+            const int i = u * kThreads + tid;
+            nr[u] = i < nl ? __ldg(a.LUi + lb + i) : -1;
+            nv[u] = i < nl ? __ldcg(a.LUx + lb + i) : 0.0;
+        }
+    };
+
+    int ready = 0, mbase = 0;
+    for (int t = 0; t < nD; ++t) {
+        if (t >= ready) {
+            if (warp == 0) {
+                const int tt = t + lane;
+                const int jj = tt < nD ? rows[tt] : -1;
+                bool ok = true;
+                if (jj >= 0) {
+                    if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
+                    const long long lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
+                    s_lb[lane] = lb;
+                    s_nl[lane] = (int)(__ldg(a.LUp + jj + 1) - lb);
+                }
+                const unsigned m = __ballot_sync(kFull, ok);
+                const int run = (m == kFull) ? 32 : __ffs(~m) - 1;
+                if (kWait && run == 0 && lane == 0 && !spin_until(a.finish + rows[t], epoch, a, k)) s_stop = 1;
+                if (lane == 0) s_ready = t + (run > 0 ? run : 1);
+            }
+            __syncthreads();
+            if (s_stop) return true;
+            ready = s_ready;
+            mbase = t;
+        }
+        const long long lb = s_lb[t - mbase];
+        const int nl = s_nl[t - mbase];
+        if (!have) load_entries(lb, nl);
+        int cr[kPre];
+        double cv[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
+        have = false;
+        if (t + 1 < ready) {
+            load_entries(s_lb[t + 1 - mbase], s_nl[t + 1 - mbase]);
+            have = true;
+        }
+        const int j = rows[t];
+        const double xj = x[t];
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < kPre; u++) {
+            if (cr[u] < 0) continue;
+            const int i = u * kThreads + tid;
+            const int sl = find_slot(rows, t + 1 + i, t + (cr[u] - j), len, cr[u]);
+            if (sl < 0) { bad = true; continue; }
+            x[sl] = fma(-xj, cv[u], x[sl]);
+        }
+        for (int i = kPre * kThreads + tid; i < nl; i += kThreads) {  // long dependencies
+            const int r = __ldg(a.LUi + lb + i);
+            const double v = __ldcg(a.LUx + lb + i);
+            const int sl = find_slot(rows, t + 1 + i, t + (r - j), len, r);
+            if (sl < 0) { bad = true; continue; }
+            x[sl] = fma(-xj, v, x[sl]);
+        }
+        if (bad) s_stop = 2;
+        __syncthreads();
+        if (s_stop) {  // inconsistent pattern: never index with it
+            if (tid == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
+            return true;
+        }
+    }
+
+    const double d = x[nU - 1];
+    double m = 0.0;
+    for (int i = nU + tid; i < len; i += kThreads) m = fmax(m, fabs(x[i]));
+    m = warp_max(m);
+    if (lane == 0) s_red[warp] = m;
+    __syncthreads();
+    m = s_red[0];
+    for (int w = 1; w < kWarps; w++) m = fmax(m, s_red[w]);
+    if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
+        if (tid == 0) {
+            atomicExch(&a.ctl->interrupted, 1);
+            atomicMin(&a.ctl->first_bad, k);
+        }
+        return false;
+    }
+    const double inv = 1.0 / d;
+    if (in_smem) {
+        for (int i = tid; i < len; i += kThreads) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
+    } else {
+        for (int i = nU + tid; i < len; i += kThreads) x[i] = x[i] * inv;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(a.finish + k, epoch);
+    return false;
+}
+
+__global__ void begin_refactor_kernel(DevCtl *ctl)
+{
+    ctl->ticket = 0;
+    ctl->interrupted = 0;
+    ctl->first_bad = INT_MAX;
+    ctl->status = 0;
+    ctl->where = 0;
+    ctl->where_k = -1;
+}
+
+// Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
+// (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
+template <bool kWait>
+__global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs a, int epoch, int persistent)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_t, s_quit;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *xs = reinterpret_cast<double *>(smem);
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)a.cap_long * sizeof(double));
+    for (int iter = 0;; ++iter) {
+        if (threadIdx.x == 0) {
+            s_t = persistent ? atomicAdd(&a.ctl->ticket, 1) : (iter == 0 ? (int)blockIdx.x : a.ntasks);
+            s_quit = ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status);
+        }
+        __syncthreads();
+        const int t = s_t, quit = s_quit;
+        __syncthreads();
+        if (t >= a.ntasks || quit) break;
+        const int tt = a.task_begin + t;
+        const int c0 = __ldg(a.task_ptr + tt), c1 = __ldg(a.task_ptr + tt + 1);
+        bool stop;
+        const int k0 = __ldg(a.task_cols + c0);
+        if (c1 - c0 == 1 && __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0) > a.cap_short) {
+            stop = col_cta<kWait>(a, k0, xs, rs, epoch);
+        } else {
+            bool ws = false;
+            if (c0 + warp < c1)
+                ws = col_warp<kWait>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
+                                     rs + (size_t)warp * a.cap_short, lane, epoch);
+            stop = __syncthreads_or(ws);
+        }
+        if (stop) break;
+    }
+}
+
+size_t task_smem(const RefactorArgs &a)
+{
+    return (size_t)a.cap_long * (sizeof(double) + sizeof(int32_t));
+}
+
+}  // namespace
+
+int launch_begin_refactor(DevCtl *ctl, void *stream)
+{
+    begin_refactor_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
+    return (int)cudaGetLastError();
+}
+
+int refactor_setup(int cap_long, int *blocks_per_sm)
+{
+    const size_t sm = (size_t)cap_long * (sizeof(double) + sizeof(int32_t));
+    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_task_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, refactor_task_kernel<true>,
+                                                              kThreads, sm);
+}
+
+int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream)
+{
+    if (a.ntasks <= 0) return 0;
+    if (pipeline) {
+        refactor_task_kernel<true><<<grid, kThreads, task_smem(a), (cudaStream_t)stream>>>(a, epoch, 1);
+    } else {
+        refactor_task_kernel<false><<<a.ntasks, kThreads, task_smem(a), (cudaStream_t)stream>>>(a, epoch, 0);
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace gblu

@@ -124,7 +124,7 @@ int64_t symmetric_fill(const Pattern &P)
 }
 
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
-                    int resident_warps, Schedule &W)
+                    int resident_warps, int sched_mode, int cap_short, Schedule &W)
 {
     const int32_t n = S.n;
     // ---- EGraph levels and the dividing level (Section III-B) ----
@@ -142,6 +142,38 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     W.div_level = W.n_levels;
     for (int32_t l = 0; l < W.n_levels; l++)
         if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
+    if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
+    if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
+    // ---- tasks: long columns alone, short ones in groups of up to 8, in
+    // level order; groups stay inside a level before the dividing level
+    W.task_ptr.assign(1, 0);
+    W.task_cols.clear();
+    W.task_cols.reserve(n);
+    W.level_task_ptr.assign(1, 0);
+    {
+        int32_t group = 0;
+        auto flush = [&]() {
+            if (group) { W.task_ptr.push_back((int32_t)W.task_cols.size()); group = 0; }
+        };
+        for (int32_t l = 0; l < W.n_levels; l++) {
+            for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
+                const int32_t k = W.level_cols[p];
+                if (S.LUp[k + 1] - S.LUp[k] > cap_short) {
+                    flush();
+                    W.task_cols.push_back(k);
+                    W.task_ptr.push_back((int32_t)W.task_cols.size());
+                } else {
+                    W.task_cols.push_back(k);
+                    if (++group == 8) flush();
+                }
+            }
+            if (l < W.div_level) {
+                flush();
+                W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
+            }
+        }
+        flush();
+    }
     // ---- flops of one refactorization ----
     double fl = 0;
     for (int32_t k = 0; k < n; k++)
