@@ -67,6 +67,18 @@ typedef struct {
                             alpha = 2 per thread), default 2.0                    */
     long long spin_limit;/* iterations of every device wait before it gives up
                             with GBLU_ERR_DEVICE_TIMEOUT, default 1<<24           */
+    /* structure-adaptive solve (Section V-A): the trailing block L(P0:n,P0:n)
+       (and U likewise) is split off when it holds at least solve_dense_frac
+       of the factor's entries and at least solve_dense_min entries; it is cut
+       into solve_slices trapezoid slices of equal entry counts (the paper's
+       rule: 0.7, 300000, 8).  solve_dense_density > 0 retunes the rule for
+       the GPU: P0 is then the start of the longest trailing block whose
+       entry density stays at least that value (solve_dense_frac ignored);
+       default 0.5.  solve_slices = 0 disables the split.                     */
+    double solve_dense_frac;
+    long long solve_dense_min;
+    int solve_slices;
+    double solve_dense_density;
 } gblu_opts;
 
 /* Fill *o with the defaults above. */
@@ -192,7 +204,9 @@ typedef struct {
     double flops;         /* refactor flops: sum over updates 2*nnz(L(:,j))   */
     int32_t n_levels;     /* levels of the column dependency graph (EGraph)  */
     int32_t div_level;    /* first level scheduled sync-free                 */
-    int32_t n_solve_levels_l, n_solve_levels_u;
+    int32_t n_solve_levels_l, n_solve_levels_u;  /* levels of the sparse blocks     */
+    int32_t solve_p0_l, solve_p0_u;  /* first row of the trailing dense block (n: none) */
+    int32_t solve_slices_l, solve_slices_u;
     int32_t etree_height;
     int64_t n_refactor;   /* refactorize calls                               */
     int64_t n_repivot;    /* refactorize calls that restarted with pivoting  */

@@ -97,7 +97,8 @@ struct gblu_ctx {
     DBuf<double> vals;
     // solves
     DBuf<int64_t> Lrp, Urp;
-    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows;
+    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, ltcnt, utstart;
+    DBuf<int64_t> lsplit, usplit;
     DBuf<double> y, z, partial, stage_ax, stage_b, stage_x;
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
@@ -185,7 +186,13 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
 {
     h->S = std::move(S);
     const int resident_warps = h->ref_blocks_per_sm * h->sm_count * (kRefThreads / 32);
-    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, h->W);
+    SolveSplit sp;
+    sp.density = h->opts.solve_dense_density;
+    sp.frac = h->opts.solve_dense_frac;
+    sp.min_entries = h->opts.solve_dense_min;
+    sp.slices = h->opts.solve_slices;
+    sp.max_piece = kMaxPieceRows;
+    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, sp, h->W);
     for (int32_t v : h->W.amap)
         if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
     const int32_t n = h->S.n;
@@ -222,6 +229,10 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->Udiag, h->W.Udiag, st));
     CK(upload(h, h->lsv_rows, h->W.lsv_rows, st));
     CK(upload(h, h->usv_rows, h->W.usv_rows, st));
+    CK(upload(h, h->lsplit, h->W.lsplit, st));
+    CK(upload(h, h->ltcnt, h->W.ltcnt, st));
+    CK(upload(h, h->usplit, h->W.usplit, st));
+    CK(upload(h, h->utstart, h->W.utstart, st));
     // host vectors are uploaded asynchronously: keep them alive until done
     CU(cudaStreamSynchronize(st));
     return GBLU_OK;
@@ -475,6 +486,10 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_mode = GBLU_SCHED_AUTO;
     o->alpha = 2.0;
     o->spin_limit = 1LL << 24;
+    o->solve_dense_frac = 0.7;
+    o->solve_dense_min = 300000;
+    o->solve_slices = 8;
+    o->solve_dense_density = 0.5;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -489,7 +504,9 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (o) h->opts = *o;
     if (!(h->opts.pivot_tol >= 0.0 && h->opts.pivot_tol <= 1.0) || h->opts.spin_limit <= 0 ||
         h->opts.sched_mode < 0 || h->opts.sched_mode > 2 || h->opts.solve_mode < 0 ||
-        h->opts.solve_mode > 2 || !(h->opts.alpha >= 0.0)) {
+        h->opts.solve_mode > 2 || !(h->opts.alpha >= 0.0) || !(h->opts.solve_dense_frac >= 0.0) ||
+        h->opts.solve_dense_frac > 1.0 || h->opts.solve_slices < 0 ||
+        !(h->opts.solve_dense_density >= 0.0) || h->opts.solve_dense_density > 1.0) {
         delete h;
         return fail(GBLU_ERR_INVALID_INPUT, "invalid options");
     }
@@ -506,6 +523,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     int r = 0;
     if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
+    if (e == cudaSuccess && r == 0) r = dense_piece_setup(kMaxPieceRows);
     if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
         const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
         if (h->hctl) cudaFreeHost(h->hctl);
@@ -533,7 +551,8 @@ void gblu_destroy(gblu_handle h)
         release(h, h->piv); release(h, h->pinv); release(h, h->vals);
         release(h, h->Lrp); release(h, h->Urp); release(h, h->Lcol); release(h, h->Lslot);
         release(h, h->Ucol); release(h, h->Uslot); release(h, h->Udiag);
-        release(h, h->lsv_rows); release(h, h->usv_rows);
+        release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->ltcnt);
+        release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
         release(h, h->y); release(h, h->z); release(h, h->partial);
         release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
         release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
@@ -697,10 +716,12 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
     const Schedule &W = h->W;
-    for (int pass = 0; pass < 2; pass++) {
-        const bool lower = pass == 0;
+    // sparse block rows [0, nrows): levels before the dividing level one
+    // launch each, the rest one sync-free launch
+    auto sparse = [&](bool lower) -> int {
         const std::vector<int32_t> &ptr = lower ? W.lsv_ptr : W.usv_ptr;
         const int32_t nlev = lower ? W.lsv_levels : W.usv_levels;
+        const int32_t nrows = lower ? W.lp0 : W.up0;
         int32_t div = lower ? W.lsv_div : W.usv_div;
         if (h->opts.solve_mode == GBLU_SCHED_LEVEL) div = nlev;
         if (h->opts.solve_mode == GBLU_SCHED_SYNCFREE) div = 0;
@@ -712,11 +733,26 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
         }
         if (div < nlev) {
             a.rows = rows + ptr[div];
-            a.nrows = n - ptr[div];
+            a.nrows = nrows - ptr[div];
             KL(lower ? launch_lsolve(a, false, h->solve_grid, st)
                      : launch_usolve(a, false, h->solve_grid, st));
         }
+        return GBLU_OK;
+    };
+    // forward: sparse block, then the trapezoid slices in order
+    CK(sparse(true));
+    for (size_t q = 0; q + 1 < W.lcut.size(); q++) {
+        KL(launch_dense_piece(a, true, W.lp0, W.lcut[q], W.lcut[q + 1], h->lsplit.p, h->ltcnt.p,
+                              h->LUp.p, h->LUi.p, h->nU.p, st));
+        h->launches++;  // rectangular part + triangular piece
     }
+    // backward: the slices from the last one, then the sparse block
+    for (size_t q = W.ucut.size(); q-- > 1;) {
+        KL(launch_dense_piece(a, false, W.up0, W.ucut[q - 1], W.ucut[q], h->usplit.p, h->utstart.p,
+                              h->LUp.p, h->LUi.p, h->nU.p, st));
+        h->launches++;
+    }
+    CK(sparse(false));
     return GBLU_OK;
 }
 
@@ -777,6 +813,10 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
         s->div_level = h->W.div_level;
         s->n_solve_levels_l = h->W.lsv_levels;
         s->n_solve_levels_u = h->W.usv_levels;
+        s->solve_p0_l = h->W.lp0;
+        s->solve_p0_u = h->W.up0;
+        s->solve_slices_l = h->W.lcut.empty() ? 0 : (int32_t)h->W.lcut.size() - 1;
+        s->solve_slices_u = h->W.ucut.empty() ? 0 : (int32_t)h->W.ucut.size() - 1;
     }
     return GBLU_OK;
 }

@@ -58,6 +58,26 @@ struct Schedule {
     std::vector<int32_t> Udiag;           // slot of U(i,i)
     std::vector<int32_t> lsv_ptr, lsv_rows; int32_t lsv_levels = 0, lsv_div = 0;
     std::vector<int32_t> usv_ptr, usv_rows; int32_t usv_levels = 0, usv_div = 0;
+    // structure-adaptive solve (Section V): rows [p0, n) form the trailing
+    // block, cut at slice boundaries cut[0] = p0 < ... < cut[m] = n.
+    // Forward: the rectangular part of row i (p0 <= i) is its CSR entries
+    // [Lrp[i], lsplit[i - p0]) (columns before the row's slice), the
+    // triangular piece of column j is its first ltcnt[j - p0] L entries.
+    // Backward: the rectangular part of row i is [usplit[i - p0], Urp[i+1])
+    // (columns after the row's slice), the triangular piece of column j is
+    // its U entries from utstart[j - p0] to the diagonal.
+    int32_t lp0 = 0, up0 = 0;
+    std::vector<int32_t> lcut, ucut;
+    std::vector<int64_t> lsplit, usplit;
+    std::vector<int32_t> ltcnt, utstart;
+};
+
+struct SolveSplit {
+    double density = 0.0;   // > 0: longest trailing block at least this dense
+    double frac = 0.7;
+    long long min_entries = 300000;
+    int slices = 8;
+    int max_piece = 8192;   // rows of one triangular piece (shared memory)
 };
 
 // record a one-line message for gblu_last_error() and return code
@@ -71,7 +91,8 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
 // symmetric matrix; used to size the first factorization's pool
 int64_t symmetric_fill(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
-                    int resident_warps, int sched_mode, int cap_short, Schedule &W);
+                    int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
+                    Schedule &W);
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
                   const int32_t *nU_or_null, std::vector<int32_t> &level);
 
@@ -167,11 +188,17 @@ int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
                     const double *x, double *out, double *partial, int nblocks,
                     void *stream);
 int solve_syncfree_grid(int *grid);
+// one trapezoid slice of the trailing block: rectangular part, then triangular piece
+int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,
+                       const int64_t *split, const int32_t *tri, const int64_t *LUp,
+                       const int32_t *LUi, const int32_t *nU, void *stream);
+int dense_piece_setup(int max_rows);
 
 constexpr int kRefThreads = 256;       // 8 warps per refactor CTA
 constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short columns)
 constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
+constexpr int kMaxPieceRows = 4096;    // rows of one triangular piece (80 KB shared memory)
 
 }  // namespace gblu

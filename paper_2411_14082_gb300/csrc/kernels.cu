@@ -427,6 +427,154 @@ usolve_syncfree_kernel(SolveArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Trailing block of the structure-adaptive solve (Section V-B, Algorithm 6):
+// for every trapezoid slice, the rectangular part (columns outside the
+// slice, already final) is a parallel sparse matrix-vector product, then the
+// triangular piece is solved by one CTA, column by column, with the piece's
+// part of the vector in shared memory.
+struct DenseArgs {
+    int32_t p0, r0, r1;                 // trailing block start, piece rows [r0, r1)
+    const int64_t *split;               // per row of the block (see Schedule)
+    const int32_t *tri;                 // per column: ltcnt (forward) / utstart (backward)
+    const int64_t *LUp;
+    const int32_t *LUi, *nU;
+};
+
+// forward rectangular part: y[i] = b[piv[i]] - L(i, columns before the slice) y
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+lsolve_rect_kernel(SolveArgs a, DenseArgs d)
+{
+    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
+    if (i >= d.r1) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t rb = __ldg(a.Lrp + i), re = __ldg(d.split + (i - d.p0));
+    double s = 0.0;
+    for (int64_t e = rb + lane; e < re; e += 32)
+        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), __ldcg(a.y + __ldg(a.Lcol + e)), s);
+    s = warp_sum(s);
+    if (lane == 0) a.y[i] = __ldg(a.b + __ldg(a.piv + i)) - s;
+}
+
+// backward rectangular part: z[i] = y[i] - U(i, columns after the slice) z
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+usolve_rect_kernel(SolveArgs a, DenseArgs d)
+{
+    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
+    if (i >= d.r1) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t rb = __ldg(d.split + (i - d.p0)), re = __ldg(a.Urp + i + 1);
+    double s = 0.0;
+    for (int64_t e = re - 1 - lane; e >= rb; e -= 32)
+        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), __ldcg(a.z + __ldg(a.Ucol + e)), s);
+    s = warp_sum(s);
+    if (lane == 0) a.z[i] = __ldcg(a.y + i) - s;
+}
+
+constexpr int kTriThreads = 256;
+constexpr int kTriPre = 4;   // piece entries per thread prefetched for the next column
+
+// forward triangular piece [r0, r1): columns in increasing order; the first
+// tri[j] L entries of column j are its rows inside the piece
+__global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, DenseArgs d)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = d.r1 - d.r0, tid = threadIdx.x;
+    double *ys = reinterpret_cast<double *>(smem);
+    long long *sb = reinterpret_cast<long long *>(ys + m);
+    int *sc = reinterpret_cast<int *>(sb + m);
+    for (int q = tid; q < m; q += kTriThreads) {
+        const int j = d.r0 + q;
+        ys[q] = __ldcg(a.y + j);
+        sb[q] = __ldg(d.LUp + j) + __ldg(d.nU + j);
+        sc[q] = __ldg(d.tri + (j - d.p0));
+    }
+    __syncthreads();
+    int nr[kTriPre];
+    double nv[kTriPre];
+    auto load = [&](int q) {
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++) {
+            const int p = u * kTriThreads + tid;
+            nr[u] = p < sc[q] ? __ldg(d.LUi + sb[q] + p) : -1;
+            nv[u] = p < sc[q] ? __ldg(a.LUx + sb[q] + p) : 0.0;
+        }
+    };
+    if (m > 0) load(0);
+    for (int q = 0; q < m; q++) {
+        int cr[kTriPre];
+        double cv[kTriPre];
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
+        if (q + 1 < m) load(q + 1);
+        const double yj = ys[q];
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++)
+            if (cr[u] >= 0) ys[cr[u] - d.r0] = fma(-cv[u], yj, ys[cr[u] - d.r0]);
+        for (int p = kTriPre * kTriThreads + tid; p < sc[q]; p += kTriThreads) {
+            const int r = __ldg(d.LUi + sb[q] + p);
+            ys[r - d.r0] = fma(-__ldg(a.LUx + sb[q] + p), yj, ys[r - d.r0]);
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < m; q += kTriThreads) a.y[d.r0 + q] = ys[q];
+}
+
+// backward triangular piece [r0, r1): columns in decreasing order; the U
+// entries of column j from position tri[j] to the diagonal are its rows
+// inside the piece
+__global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, DenseArgs d)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = d.r1 - d.r0, tid = threadIdx.x;
+    double *zs = reinterpret_cast<double *>(smem);
+    long long *sb = reinterpret_cast<long long *>(zs + m);
+    int *sc = reinterpret_cast<int *>(sb + m);
+    for (int q = tid; q < m; q += kTriThreads) {
+        const int j = d.r0 + q;
+        zs[q] = __ldcg(a.z + j);
+        const long long b = __ldg(d.LUp + j) + __ldg(d.tri + (j - d.p0));
+        sb[q] = b;
+        sc[q] = (int)(__ldg(d.LUp + j) + __ldg(d.nU + j) - 1 - b);
+    }
+    __syncthreads();
+    int nr[kTriPre];
+    double nv[kTriPre];
+    auto load = [&](int q) {
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++) {
+            const int p = u * kTriThreads + tid;
+            nr[u] = p < sc[q] ? __ldg(d.LUi + sb[q] + p) : -1;
+            nv[u] = p < sc[q] ? __ldg(a.LUx + sb[q] + p) : 0.0;
+        }
+    };
+    if (m > 0) load(m - 1);
+    for (int q = m - 1; q >= 0; q--) {
+        int cr[kTriPre];
+        double cv[kTriPre];
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
+        if (q > 0) load(q - 1);
+        const int j = d.r0 + q;
+        const double zj = zs[q] / __ldg(a.LUx + __ldg(a.Udiag + j));
+        __syncthreads();   // every thread has read zs[q]
+        if (tid == 0) zs[q] = zj;
+#pragma unroll
+        for (int u = 0; u < kTriPre; u++)
+            if (cr[u] >= 0) zs[cr[u] - d.r0] = fma(-cv[u], zj, zs[cr[u] - d.r0]);
+        for (int p = kTriPre * kTriThreads + tid; p < sc[q]; p += kTriThreads) {
+            const int r = __ldg(d.LUi + sb[q] + p);
+            zs[r - d.r0] = fma(-__ldg(a.LUx + sb[q] + p), zj, zs[r - d.r0]);
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < m; q += kTriThreads) {
+        const int j = d.r0 + q;
+        a.z[j] = zs[q];
+        a.x[__ldg(a.Q + j)] = zs[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
 __global__ void residual_kernel(int32_t n, const int64_t *Arp, const int32_t *Acol,
                                 const int32_t *Aslot, const double *Ax, const double *b,
                                 const double *x, double *partial)
@@ -529,6 +677,39 @@ int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
         usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     }
     return (int)cudaGetLastError();
+}
+
+size_t tri_smem(int rows)
+{
+    return (size_t)rows * (sizeof(double) + sizeof(long long) + sizeof(int));
+}
+
+int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,
+                       const int64_t *split, const int32_t *tri, const int64_t *LUp,
+                       const int32_t *LUi, const int32_t *nU, void *stream)
+{
+    if (r1 <= r0) return 0;
+    DenseArgs d{p0, r0, r1, split, tri, LUp, LUi, nU};
+    const int g = (r1 - r0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+    const size_t sm = tri_smem(r1 - r0);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (lower) {
+        lsolve_rect_kernel<<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+        lsolve_tri_kernel<<<1, kTriThreads, sm, st>>>(a, d);
+    } else {
+        usolve_rect_kernel<<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+        usolve_tri_kernel<<<1, kTriThreads, sm, st>>>(a, d);
+    }
+    return (int)cudaGetLastError();
+}
+
+int dense_piece_setup(int max_rows)
+{
+    const int sm = (int)tri_smem(max_rows);
+    cudaError_t e = cudaFuncSetAttribute(lsolve_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(usolve_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return (int)e;
 }
 
 int solve_syncfree_grid(int *grid)

@@ -123,8 +123,61 @@ int64_t symmetric_fill(const Pattern &P)
     return total;
 }
 
+// Partition point and trapezoid slices of one triangular factor (Section
+// V-A).  count_from[p] = entries of the trailing block [p, n) (suffix sums of
+// the per-column (lower) or per-row (upper) strict counts); rowlen[i] = all
+// entries of row i of the factor.  Paper's rule (density == 0): scan down
+// from n-1 and stop at the first position whose trailing block holds at
+// least frac * total and min_entries entries (the smallest such block).
+// GPU rule (density > 0): P0 = the start of the longest trailing block whose
+// entry density count_from[p] / ((n-p)(n-p-1)/2) is at least `density`,
+// kept if it holds min_entries entries.  The rows [P0, n) are cut into
+// `slices` pieces of equal entry counts (at most max_piece rows each).
+// Returns n when no block qualifies.
+static int32_t dense_split(int32_t n, const std::vector<int64_t> &count_from, const std::vector<int64_t> &rowlen,
+                           const SolveSplit &sp, std::vector<int32_t> &cut)
+{
+    cut.clear();
+    const int64_t total = count_from.empty() ? 0 : count_from[0];
+    if (sp.slices <= 0 || total <= 0) return n;
+    int32_t p0 = n;
+    if (sp.density > 0.0) {
+        for (int32_t p = n - 2; p >= 0; p--) {
+            const double m = (double)(n - p);
+            if ((double)count_from[p] < sp.density * m * (m - 1.0) / 2.0) break;
+            p0 = p;
+        }
+        if (p0 < n && count_from[p0] < sp.min_entries) p0 = n;
+    } else {
+        for (int32_t p = n - 1; p >= 0; p--) {
+            if ((double)count_from[p] >= sp.frac * (double)total && count_from[p] >= sp.min_entries) {
+                p0 = p;
+                break;
+            }
+        }
+    }
+    if (p0 >= n) return n;
+    int64_t tot = 0;
+    for (int32_t i = p0; i < n; i++) tot += rowlen[i];
+    const double per = (double)tot / sp.slices;
+    cut.push_back(p0);
+    int64_t acc = 0;
+    int32_t start = p0;
+    for (int32_t i = p0; i < n; i++) {
+        acc += rowlen[i];
+        if (i + 1 < n && ((double)acc >= per || i + 1 - start >= sp.max_piece)) {
+            cut.push_back(i + 1);
+            acc = 0;
+            start = i + 1;
+        }
+    }
+    cut.push_back(n);
+    return p0;
+}
+
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
-                    int resident_warps, int sched_mode, int cap_short, Schedule &W)
+                    int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
+                    Schedule &W)
 {
     const int32_t n = S.n;
     // ---- EGraph levels and the dividing level (Section III-B) ----
@@ -231,38 +284,96 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             }
         }
     }
-    // ---- solve levels: L rows forward, U rows backward ----
-    auto levelize = [&](bool lower, std::vector<int32_t> &ptr, std::vector<int32_t> &rowsv,
+    // ---- structure-adaptive split of both triangular factors (Section V) ----
+    {
+        std::vector<int64_t> cf(n + 1, 0), rl(n, 0);
+        for (int32_t j = n - 1; j >= 0; j--)
+            cf[j] = cf[j + 1] + (S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
+        for (int32_t i = 0; i < n; i++) rl[i] = W.Lrp[i + 1] - W.Lrp[i];
+        W.lp0 = dense_split(n, cf, rl, split, W.lcut);
+        std::vector<int64_t> cu(n + 1, 0), ru(n, 0);
+        for (int32_t i = n - 1; i >= 0; i--) cu[i] = cu[i + 1] + (W.Urp[i + 1] - W.Urp[i]);
+        for (int32_t i = 0; i < n; i++) ru[i] = W.Urp[i + 1] - W.Urp[i];
+        W.up0 = dense_split(n, cu, ru, split, W.ucut);
+    }
+    W.lsplit.clear();
+    W.ltcnt.clear();
+    if (W.lp0 < n) {
+        W.lsplit.resize(n - W.lp0);
+        W.ltcnt.resize(n - W.lp0);
+        size_t piece = 0;
+        for (int32_t i = W.lp0; i < n; i++) {
+            while (i >= W.lcut[piece + 1]) piece++;
+            const int32_t lo = W.lcut[piece];
+            const int32_t *c = W.Lcol.data() + W.Lrp[i];
+            const int32_t len = (int32_t)(W.Lrp[i + 1] - W.Lrp[i]);
+            W.lsplit[i - W.lp0] = W.Lrp[i] + (std::lower_bound(c, c + len, lo) - c);
+        }
+        piece = 0;
+        for (int32_t j = W.lp0; j < n; j++) {
+            while (j >= W.lcut[piece + 1]) piece++;
+            const int32_t hi = W.lcut[piece + 1];
+            const int32_t *r = S.LUi.data() + S.LUp[j] + S.nU[j];
+            const int32_t len = (int32_t)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
+            W.ltcnt[j - W.lp0] = (int32_t)(std::lower_bound(r, r + len, hi) - r);
+        }
+    }
+    W.usplit.clear();
+    W.utstart.clear();
+    if (W.up0 < n) {
+        W.usplit.resize(n - W.up0);
+        W.utstart.resize(n - W.up0);
+        size_t piece = 0;
+        for (int32_t i = W.up0; i < n; i++) {
+            while (i >= W.ucut[piece + 1]) piece++;
+            const int32_t hi = W.ucut[piece + 1];
+            const int32_t *c = W.Urow_col.data() + W.Urp[i];
+            const int32_t len = (int32_t)(W.Urp[i + 1] - W.Urp[i]);
+            W.usplit[i - W.up0] = W.Urp[i] + (std::lower_bound(c, c + len, hi) - c);
+        }
+        piece = 0;
+        for (int32_t j = W.up0; j < n; j++) {
+            while (j >= W.ucut[piece + 1]) piece++;
+            const int32_t lo = W.ucut[piece];
+            const int32_t *r = S.LUi.data() + S.LUp[j];
+            const int32_t len = S.nU[j] - 1;
+            W.utstart[j - W.up0] = (int32_t)(std::lower_bound(r, r + len, lo) - r);
+        }
+    }
+    // ---- solve levels of the sparse blocks: L rows forward, U rows backward ----
+    auto levelize = [&](bool lower, int32_t nrows, std::vector<int32_t> &ptr, std::vector<int32_t> &rowsv,
                         int32_t &nlev, int32_t &div) {
         std::vector<int32_t> lv(n, 0);
         nlev = 0;
-        for (int32_t t = 0; t < n; t++) {
-            const int32_t i = lower ? t : n - 1 - t;
+        for (int32_t t = 0; t < nrows; t++) {
+            const int32_t i = lower ? t : nrows - 1 - t;
             int32_t v = 0;
             const std::vector<int64_t> &rp = lower ? W.Lrp : W.Urp;
             const std::vector<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
-            for (int64_t e = rp[i]; e < rp[i + 1]; e++) v = std::max(v, lv[cc[e]] + 1);
+            for (int64_t e = rp[i]; e < rp[i + 1]; e++)
+                if (cc[e] < nrows) v = std::max(v, lv[cc[e]] + 1);
             lv[i] = v;
             nlev = std::max(nlev, v + 1);
         }
         ptr.assign(nlev + 1, 0);
-        for (int32_t i = 0; i < n; i++) ptr[lv[i] + 1]++;
+        for (int32_t i = 0; i < nrows; i++) ptr[lv[i] + 1]++;
         for (int32_t l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
-        rowsv.assign(n, 0);
+        rowsv.assign(nrows, 0);
         std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
-        for (int32_t t = 0; t < n; t++) {
-            const int32_t i = lower ? t : n - 1 - t;
+        for (int32_t t = 0; t < nrows; t++) {
+            const int32_t i = lower ? t : nrows - 1 - t;
             rowsv[pos[lv[i]]++] = i;
         }
         div = nlev;
         for (int32_t l = 0; l < nlev; l++)
             if ((double)(ptr[l + 1] - ptr[l]) < thr) { div = l; break; }
     };
-    levelize(true, W.lsv_ptr, W.lsv_rows, W.lsv_levels, W.lsv_div);
-    levelize(false, W.usv_ptr, W.usv_rows, W.usv_levels, W.usv_div);
+    levelize(true, W.lp0, W.lsv_ptr, W.lsv_rows, W.lsv_levels, W.lsv_div);
+    levelize(false, W.up0, W.usv_ptr, W.usv_rows, W.usv_levels, W.usv_div);
 }
 
 }  // namespace gblu
+
 
 // ------------------------------------------------------------ host-only C ABI
 using namespace gblu;

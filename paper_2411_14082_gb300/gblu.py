@@ -51,7 +51,9 @@ class GbluError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("pivot_tol", ctypes.c_double), ("sched_mode", ctypes.c_int),
                 ("solve_mode", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("spin_limit", ctypes.c_longlong)]
+                ("spin_limit", ctypes.c_longlong), ("solve_dense_frac", ctypes.c_double),
+                ("solve_dense_min", ctypes.c_longlong), ("solve_slices", ctypes.c_int),
+                ("solve_dense_density", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -59,6 +61,8 @@ class Stats(ctypes.Structure):
                 ("nnz_u", ctypes.c_int64), ("flops", ctypes.c_double),
                 ("n_levels", ctypes.c_int32), ("div_level", ctypes.c_int32),
                 ("n_solve_levels_l", ctypes.c_int32), ("n_solve_levels_u", ctypes.c_int32),
+                ("solve_p0_l", ctypes.c_int32), ("solve_p0_u", ctypes.c_int32),
+                ("solve_slices_l", ctypes.c_int32), ("solve_slices_u", ctypes.c_int32),
                 ("etree_height", ctypes.c_int32), ("n_refactor", ctypes.c_int64),
                 ("n_repivot", ctypes.c_int64), ("n_restart_cols", ctypes.c_int64),
                 ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
@@ -151,7 +155,8 @@ class Solver:
     """One handle: analyze a pattern once, then factorize / refactorize / solve."""
 
     def __init__(self, device=0, pivot_tol=1e-3, sched_mode="auto", solve_mode="auto",
-                 alpha=2.0, spin_limit=1 << 24):
+                 alpha=2.0, spin_limit=1 << 24, solve_dense_frac=None, solve_dense_min=None,
+                 solve_slices=None, solve_dense_density=None):
         lib = load()
         o = Opts()
         lib.gblu_default_opts(ctypes.byref(o))
@@ -160,6 +165,14 @@ class Solver:
         o.solve_mode = SCHED[solve_mode]
         o.alpha = alpha
         o.spin_limit = spin_limit
+        if solve_dense_frac is not None:
+            o.solve_dense_frac = solve_dense_frac
+        if solve_dense_min is not None:
+            o.solve_dense_min = solve_dense_min
+        if solve_slices is not None:
+            o.solve_slices = solve_slices
+        if solve_dense_density is not None:
+            o.solve_dense_density = solve_dense_density
         h = ctypes.c_void_p()
         _check(lib.gblu_create(ctypes.byref(h), int(device), ctypes.byref(o)))
         self._h = h

@@ -310,3 +310,62 @@ def test_library_ordering_when_no_q_given():
     lu = O.factorize(n, Ap, Ai, Ax, gblu.order_mindeg(n, Ap, Ai), 1e-3)
     compare_factors(f, lu, RTOL)
     solve_and_check(s, n, Ap, Ai, Ax, Axd, np.random.default_rng(0))
+
+
+@pytest.mark.parametrize("slices", [1, 3, 8])
+def test_structure_adaptive_solve(slices):
+    """Section V: trailing block L(P0:n, P0:n) split off by the 70% rule
+    (the entry minimum lowered so that a test-sized mesh qualifies), cut into
+    trapezoid slices; the solution must match the oracle's residual bound,
+    agree with the unsplit solve, and be identical across schedules."""
+    ckt = mesh_small(seed=4)
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(8)
+    b = inputs.rhs(n, rng)
+    Axd = dev(Ax)
+    ref = gblu.Solver(DEV, solve_slices=0)
+    ref.analyze(n, Ap, Ai, Q)
+    ref.factorize(Axd)
+    assert ref.stats()["solve_p0_l"] == n
+    x_ref = ref.solve(dev(b)).cpu().numpy()
+    outs = []
+    for mode in ("auto", "level", "syncfree"):
+        s = gblu.Solver(DEV, sched_mode=mode, solve_mode=mode, solve_dense_min=1000,
+                        solve_slices=slices, solve_dense_density=0.0)
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(Axd)
+        st = s.stats()
+        f = s.export_factors()
+        # P0: the largest position whose trailing block holds >= 70% of nnz(L)
+        counts = np.diff(f["Lp"])
+        suffix = np.cumsum(counts[::-1])[::-1]
+        ok = np.nonzero((suffix >= 0.7 * counts.sum()) & (suffix >= 1000))[0]
+        assert st["solve_p0_l"] == ok.max()
+        assert 1 <= st["solve_slices_l"] <= slices + 1 and st["solve_p0_u"] < n
+        x = s.solve(dev(b))
+        res = s.residual(Axd, dev(b), x).cpu().numpy()[0]
+        assert res <= RESID
+        xh = x.cpu().numpy()
+        np.testing.assert_allclose(xh, x_ref, rtol=1e-9, atol=1e-12 * np.abs(x_ref).max())
+        assert O.residual(n, Ap, Ai, Ax, xh, b) <= RESID
+        outs.append(xh)
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    # GPU rule: the longest trailing block that is at least half dense
+    s = gblu.Solver(DEV, solve_dense_min=100, solve_slices=slices, solve_dense_density=0.5)
+    s.analyze(n, Ap, Ai, Q)
+    s.factorize(Axd)
+    f = s.export_factors()
+    counts = np.diff(f["Lp"])
+    suffix = np.cumsum(counts[::-1])[::-1]
+    m = n - np.arange(n, dtype=float)
+    dense = suffix[:-1] >= 0.5 * m[:-1] * (m[:-1] - 1) / 2
+    p0 = n
+    for p in range(n - 2, -1, -1):
+        if not dense[p]:
+            break
+        p0 = p
+    assert s.stats()["solve_p0_l"] == (p0 if p0 < n and suffix[p0] >= 100 else n)
+    x = s.solve(dev(b)).cpu().numpy()
+    np.testing.assert_allclose(x, x_ref, rtol=1e-9, atol=1e-12 * np.abs(x_ref).max())
