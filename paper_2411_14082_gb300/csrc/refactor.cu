@@ -10,8 +10,10 @@
 // the stores U(:,k) = x(U rows), L(:,k) = x(L rows) / x(k).
 //
 // Work is handed out as tasks (built on the host in level order): a task is
-// either one long column, computed by all 8 warps of a CTA with its work
-// vector in shared memory, or up to 8 short columns, one per warp.  The
+// one long column (all 8 warps of a CTA, work vector of up to 8,192 entries
+// in shared memory), two medium columns (4 warps and up to 4,096 entries
+// each, synchronized by named barriers), or up to 8 short columns (one per
+// warp).  The
 // slot of an L(:,j) row inside column k comes from a binary search in the
 // sorted pattern over [t+1+i, t+(r-j)] (t = slot of j, i = index of the row
 // inside L(:,j)); the interval is exact inside dense runs, so dense parts
@@ -195,33 +197,50 @@ __device__ __forceinline__ bool spin_until(const int32_t *flag, int epoch, const
     return true;
 }
 
-template <bool kWait>
-__device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch)
+// group barrier: the whole CTA (NW == 8) or one half (named barrier 1 + g)
+template <int NW>
+__device__ __forceinline__ void group_sync(int g)
 {
-    __shared__ int s_ready, s_stop;
-    __shared__ long long s_lb[32];
-    __shared__ int s_nl[32];
-    __shared__ double s_red[kWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (NW == kWarps) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(NW * 32) : "memory");
+}
+
+// One column computed by a group of NW warps (the whole CTA, or one half for
+// a pair of medium columns) with its work vector of up to cap entries in
+// shared memory.  g selects the group's barrier and shared scalars.
+template <bool kWait, int NW>
+__device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap)
+{
+    __shared__ int s_ready_[2], s_stop_[2];
+    __shared__ long long s_lb_[2][32];
+    __shared__ int s_nl_[2][32];
+    __shared__ double s_red_[2][kWarps];
+    int &s_ready = s_ready_[g];
+    int &s_stop = s_stop_[g];
+    long long *s_lb = s_lb_[g];
+    int *s_nl = s_nl_[g];
+    double *s_red = s_red_[g];
+    constexpr int kT = NW * 32;
+    const int tid = threadIdx.x - g * kT, lane = tid & 31, warp = tid >> 5;
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
     const int nU = __ldg(a.nU + k);
     const int nD = nU - 1;
-    const bool in_smem = len <= a.cap_long;
+    const bool in_smem = len <= cap;
     double *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : a.LUi + beg;
-    for (int i = tid; i < len; i += kThreads) {
+    for (int i = tid; i < len; i += kT) {
         if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
         x[i] = 0.0;
     }
     if (tid == 0) { s_ready = 0; s_stop = 0; }
-    __syncthreads();
+    group_sync<NW>(g);
     {
         const int c = __ldg(a.Q + k);
         const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
-        for (int e = ab + tid; e < ae; e += kThreads) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
+        for (int e = ab + tid; e < ae; e += kT) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
     }
-    __syncthreads();
+    group_sync<NW>(g);
 
     int nr[kPre];
     double nv[kPre];
@@ -229,7 +248,7 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     auto load_entries = [&](long long lb, int nl) {
 #pragma unroll
         for (int u = 0; u < kPre; u++) {
-            const int i = u * kThreads + tid;
+            const int i = u * kT + tid;
             nr[u] = i < nl ? __ldg(a.LUi + lb + i) : -1;
             nv[u] = i < nl ? __ldcg(a.LUx + lb + i) : 0.0;
         }
@@ -253,7 +272,7 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
                 if (kWait && run == 0 && lane == 0 && !spin_until(a.finish + rows[t], epoch, a, k)) s_stop = 1;
                 if (lane == 0) s_ready = t + (run > 0 ? run : 1);
             }
-            __syncthreads();
+            group_sync<NW>(g);
             if (s_stop) return true;
             ready = s_ready;
             mbase = t;
@@ -276,12 +295,12 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
 #pragma unroll
         for (int u = 0; u < kPre; u++) {
             if (cr[u] < 0) continue;
-            const int i = u * kThreads + tid;
+            const int i = u * kT + tid;
             const int sl = find_slot(rows, t + 1 + i, t + (cr[u] - j), len, cr[u]);
             if (sl < 0) { bad = true; continue; }
             x[sl] = fma(-xj, cv[u], x[sl]);
         }
-        for (int i = kPre * kThreads + tid; i < nl; i += kThreads) {  // long dependencies
+        for (int i = kPre * kT + tid; i < nl; i += kT) {  // long dependencies
             const int r = __ldg(a.LUi + lb + i);
             const double v = __ldcg(a.LUx + lb + i);
             const int sl = find_slot(rows, t + 1 + i, t + (r - j), len, r);
@@ -289,7 +308,7 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
             x[sl] = fma(-xj, v, x[sl]);
         }
         if (bad) s_stop = 2;
-        __syncthreads();
+        group_sync<NW>(g);
         if (s_stop) {  // inconsistent pattern: never index with it
             if (tid == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
             return true;
@@ -298,12 +317,12 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
 
     const double d = x[nU - 1];
     double m = 0.0;
-    for (int i = nU + tid; i < len; i += kThreads) m = fmax(m, fabs(x[i]));
+    for (int i = nU + tid; i < len; i += kT) m = fmax(m, fabs(x[i]));
     m = warp_max(m);
     if (lane == 0) s_red[warp] = m;
-    __syncthreads();
+    group_sync<NW>(g);
     m = s_red[0];
-    for (int w = 1; w < kWarps; w++) m = fmax(m, s_red[w]);
+    for (int w = 1; w < NW; w++) m = fmax(m, s_red[w]);
     if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
         if (tid == 0) {
             atomicExch(&a.ctl->interrupted, 1);
@@ -313,12 +332,12 @@ __device__ bool col_cta(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     }
     const double inv = 1.0 / d;
     if (in_smem) {
-        for (int i = tid; i < len; i += kThreads) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
+        for (int i = tid; i < len; i += kT) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
     } else {
-        for (int i = nU + tid; i < len; i += kThreads) x[i] = x[i] * inv;
+        for (int i = nU + tid; i < len; i += kT) x[i] = x[i] * inv;
     }
     __threadfence();
-    __syncthreads();
+    group_sync<NW>(g);
     if (tid == 0) st_release(a.finish + k, epoch);
     return false;
 }
@@ -356,8 +375,15 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
         const int c0 = __ldg(a.task_ptr + tt), c1 = __ldg(a.task_ptr + tt + 1);
         bool stop;
         const int k0 = __ldg(a.task_cols + c0);
-        if (c1 - c0 == 1 && __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0) > a.cap_short) {
-            stop = col_cta<kWait>(a, k0, xs, rs, epoch);
+        const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
+        if (c1 - c0 == 1 && len0 > a.cap_short) {          // one long column: whole CTA
+            stop = col_grp<kWait, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long);
+        } else if (c1 - c0 == 2 && len0 > a.cap_short) {   // two medium columns: a half each
+            const int g = warp / (kWarps / 2);
+            const int half = a.cap_long / 2;
+            const bool hs = col_grp<kWait, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
+                                                       rs + (size_t)g * half, epoch, g, half);
+            stop = __syncthreads_or(hs);
         } else {
             bool ws = false;
             if (c0 + warp < c1)

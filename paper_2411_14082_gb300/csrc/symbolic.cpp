@@ -197,35 +197,54 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
     if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
     if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
-    // ---- tasks: long columns alone, short ones in groups of up to 8, in
-    // level order; groups stay inside a level before the dividing level
+    // ---- tasks, in level order: long columns alone, medium columns in pairs,
+    // short ones in groups of up to 8.  A pending item is only merged with
+    // the column that immediately follows it, so a task never comes before
+    // a task holding one of its dependencies.  Groups stay inside a level
+    // before the dividing level.
     W.task_ptr.assign(1, 0);
     W.task_cols.clear();
     W.task_cols.reserve(n);
     W.level_task_ptr.assign(1, 0);
     {
-        int32_t group = 0;
-        auto flush = [&]() {
-            if (group) { W.task_ptr.push_back((int32_t)W.task_cols.size()); group = 0; }
+        const int64_t half = kRefCapLong / 2;   // medium: up to half the CTA's entries
+        int32_t group = 0;      // short columns pending
+        bool pend_med = false;  // one medium column pending
+        auto close = [&]() {
+            if (group || pend_med) W.task_ptr.push_back((int32_t)W.task_cols.size());
+            group = 0;
+            pend_med = false;
         };
         for (int32_t l = 0; l < W.n_levels; l++) {
             for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
                 const int32_t k = W.level_cols[p];
-                if (S.LUp[k + 1] - S.LUp[k] > cap_short) {
-                    flush();
+                const int64_t len = S.LUp[k + 1] - S.LUp[k];
+                if (len > half) {
+                    close();
                     W.task_cols.push_back(k);
                     W.task_ptr.push_back((int32_t)W.task_cols.size());
+                } else if (len > cap_short) {
+                    if (pend_med) {
+                        W.task_cols.push_back(k);
+                        W.task_ptr.push_back((int32_t)W.task_cols.size());
+                        pend_med = false;
+                    } else {
+                        close();
+                        W.task_cols.push_back(k);
+                        pend_med = true;
+                    }
                 } else {
+                    if (pend_med) close();
                     W.task_cols.push_back(k);
-                    if (++group == 8) flush();
+                    if (++group == 8) close();
                 }
             }
             if (l < W.div_level) {
-                flush();
+                close();
                 W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
             }
         }
-        flush();
+        close();
     }
     // ---- flops of one refactorization ----
     double fl = 0;

@@ -245,15 +245,17 @@ def bordered_grid(nx=141, ny=141, n_rails=50, density=0.05,
     """2D grid plus dense-ish power/ground rails (bordered block diagonal).
 
     Each of the ``n_rails`` extra nodes connects to ``density`` of the grid
-    nodes with log-normal conductances.
+    nodes (one fraction for all rails, or one per rail) with log-normal
+    conductances.
     """
     rng = np.random.default_rng(seed)
     n_grid = nx * ny
     ex, ey, _ = _grid_edges(nx, ny, 1)
     a = [ex[0], ey[0]]
     b = [ex[1], ey[1]]
-    per = int(round(density * n_grid))
+    dens = np.broadcast_to(np.asarray(density, dtype=np.float64), (n_rails,))
     for r in range(n_rails):
+        per = max(1, int(round(dens[r] * n_grid)))
         tgt = rng.choice(n_grid, size=per, replace=False)
         a.append(np.full(per, n_grid + r))
         b.append(tgt)

@@ -242,6 +242,59 @@ def test_dense_block_uses_long_column_path():
     compare_factors(s.export_factors(), lu2, RTOL)
 
 
+def rails_grid():
+    """130x130 grid with 8 rails of growing coverage: its factor columns
+    span every task kind of the refactorization kernel (short columns one
+    per warp, medium columns in pairs, long columns in shared memory, and
+    columns beyond the shared-memory capacity updated in global memory)."""
+    return inputs.bordered_grid(130, 130, n_rails=8,
+                                density=[0.0005, 0.002, 0.004, 0.01, 0.02, 0.05, 0.1, 0.3])
+
+
+@pytest.mark.parametrize("sched", ["auto", "level", "syncfree"])
+def test_every_column_task_kind(sched):
+    ckt = rails_grid()
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(17)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    ln = np.diff(lu.Lp) + np.diff(lu.Up)
+    kinds = [(ln <= 1024).sum(), ((ln > 1024) & (ln <= 4096)).sum(),
+             ((ln > 4096) & (ln <= 8192)).sum(), (ln > 8192).sum()]
+    assert min(kinds) >= 2, kinds
+    s = gblu.Solver(DEV, sched_mode=sched, solve_mode=sched)
+    s.analyze(n, Ap, Ai, Q)
+    s.factorize(dev(Ax))
+    compare_factors(s.export_factors(), lu, RTOL)
+    for it in range(3):
+        ckt = inputs.perturb_elements(ckt, rng, frac=0.2)
+        Ax = ckt.values()
+        Axd = dev(Ax)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        rc, rep = s.refactorize(Axd)
+        assert rep == (lu.n_rejected > 0)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    # force a restart at the first rail: every longer column is recomputed
+    k = n - 8
+    c = Q[k]
+    rows = Ai[Ap[c]:Ap[c + 1]]
+    p = Ap[c] + np.nonzero(rows == lu.piv[k])[0][0]
+    Ax2 = Ax.copy()
+    Ax2[p] -= lu.Ux[lu.Up[k + 1] - 1] * (1.0 - 1e-9)
+    lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+    assert lu2.n_rejected > 0
+    Axd2 = dev(Ax2)
+    rc, rep = s.refactorize(Axd2)
+    assert rc == gblu.REPIVOTED and rep
+    compare_factors(s.export_factors(), lu2, RTOL)
+    solve_and_check(s, n, Ap, Ai, Ax2, Axd2, rng)
+    lu3 = O.refactorize(lu2, Ap, Ai, Ax)
+    rc, rep = s.refactorize(Axd)
+    assert rep == (lu3.n_rejected > 0)
+    compare_factors(s.export_factors(), lu3, RTOL)
+
+
 def test_edge_cases():
     # n = 1
     s = gblu.Solver(DEV)
