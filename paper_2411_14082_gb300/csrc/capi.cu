@@ -94,6 +94,7 @@ struct gblu_ctx {
     // followed by the restart pool
     DBuf<int64_t> LUp;
     DBuf<int32_t> LUi, nU, rows, finish, task_ptr, task_cols, amap, piv, pinv;
+    DBuf<uint8_t> chain;
     DBuf<double> vals;
     // solves
     DBuf<int64_t> Lrp, Urp;
@@ -200,6 +201,7 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->LUp, h->S.LUp, st));
     CK(upload(h, h->LUi, h->S.LUi, st));
     CK(upload(h, h->nU, h->S.nU, st));
+    CK(upload(h, h->chain, h->W.chain, st));
     CK(upload(h, h->piv, h->S.piv, st));
     CK(upload(h, h->pinv, h->S.pinv, st));
     CK(upload(h, h->task_ptr, h->W.task_ptr, st));
@@ -253,6 +255,7 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     a.LUp = h->LUp.p;
     a.LUi = h->LUi.p;
     a.nU = h->nU.p;
+    a.chain = h->chain.p;
     a.LUx = h->vals.p;
     a.finish = h->finish.p;
     a.task_ptr = h->task_ptr.p;
@@ -546,7 +549,7 @@ void gblu_destroy(gblu_handle h)
         cudaDeviceSynchronize();
         release(h, h->Ap); release(h, h->Ai); release(h, h->Q); release(h, h->qinv);
         release(h, h->clo); release(h, h->Acol); release(h, h->Aslot); release(h, h->Arp);
-        release(h, h->LUp); release(h, h->LUi); release(h, h->nU); release(h, h->rows);
+        release(h, h->LUp); release(h, h->LUi); release(h, h->nU); release(h, h->rows); release(h, h->chain);
         release(h, h->finish); release(h, h->task_ptr); release(h, h->task_cols); release(h, h->amap);
         release(h, h->piv); release(h, h->pinv); release(h, h->vals);
         release(h, h->Lrp); release(h, h->Urp); release(h, h->Lcol); release(h, h->Lslot);

@@ -50,6 +50,9 @@ struct Schedule {
     std::vector<int32_t> task_ptr, task_cols, level_task_ptr;
     std::vector<int32_t> amap;        // A slot -> position inside its column
     std::vector<int32_t> LUi_orig;    // L entries: original row ids (U: step ids)
+    // chain[j] = 1 iff L(:,j) = {j+1} followed by the rows of L(:,j+1), i.e.
+    // j and j+1 are consecutive columns of one supernode of L
+    std::vector<uint8_t> chain;
     double flops = 0;
     // solves: row-wise (CSR) copies, slots into the factor value array
     std::vector<int64_t> Lrp, Urp;        // n+1
@@ -122,6 +125,7 @@ struct RefactorArgs {
     const double *Ax;               // new values (caller slot order)
     const int64_t *LUp;
     const int32_t *LUi, *nU;
+    const uint8_t *chain;           // supernode links of L (Schedule::chain)
     double *LUx;
     int32_t *finish;
     const int32_t *task_ptr, *task_cols;

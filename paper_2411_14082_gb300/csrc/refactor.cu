@@ -174,12 +174,31 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
 }
 
 // ---------------------------------------------------------------------------
-// one long column, the whole CTA.  Every 32 dependencies warp 0 checks
-// their ready flags and stages their (start, length) in L in shared memory;
-// the dependency loop is software pipelined: while dependency t is applied,
-// the (row, value) entries of dependency t+1 are being loaded into
-// registers, so global-load latency overlaps the updates and the barrier.
-constexpr int kPre = 8;   // entries per thread held in registers: 2,048 per dependency
+// One column computed by a group of NW warps: the whole CTA, or one half of
+// it for a pair of medium columns (work vector of up to cap entries in
+// shared memory; longer columns are updated in place in global memory).
+//
+// Dependencies are applied in runs j, j+1, ..., j+w-1 (w <= 32) of
+// consecutive columns of one supernode of L (chain[j+d] set for d < w-1):
+// then L(:,j+d) = {j+d+1, ..., j+w-1} followed by R, the rows of L(:,j+w-1),
+// so the run updates x in two parts:
+//   triangle  - x(j+q) for q < w: the unit lower triangular solve of the
+//               run's diagonal block, by one warp (lane q holds x(j+q)), the
+//               block staged in shared memory;
+//   rectangle - every row r of R: x(r) -= L(r, j+d) * x(j+d) for d = 0..w-1,
+//               one thread per row, the slot of r searched once per run.
+// Every update is one fused multiply-add applied in ascending dependency
+// order, exactly as when the dependencies are applied one at a time, so the
+// result does not depend on how the dependencies fall into runs.
+//
+// Every 32 dependencies warp 0 checks their ready flags and stages their
+// (start, length) in L and their supernode links in shared memory.
+constexpr int kMaxRun = 32;
+constexpr int kTri = kMaxRun * (kMaxRun - 1) / 2;   // strictly lower triangle
+constexpr int kRows = 4;                            // rows of R per thread per pass
+
+// offset of column d of the staged triangle (column d holds kMaxRun-1-d rows)
+__device__ __forceinline__ int tri_off(int d) { return d * (kMaxRun - 1) - d * (d - 1) / 2; }
 
 __device__ __forceinline__ bool spin_until(const int32_t *flag, int epoch, const RefactorArgs &a, int k)
 {
@@ -205,21 +224,27 @@ __device__ __forceinline__ void group_sync(int g)
     else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(NW * 32) : "memory");
 }
 
-// One column computed by a group of NW warps (the whole CTA, or one half for
-// a pair of medium columns) with its work vector of up to cap entries in
-// shared memory.  g selects the group's barrier and shared scalars.
+// shared state of one group (declared once per CTA, for up to two groups)
+struct GroupShared {
+    long long lb[32];    // staged dependencies: start of L(:,j) in LUx
+    int nl[32];          // and its length
+    double red[kWarps];
+    double tri[kTri];    // the run's triangle, column d at tri_off(d)
+    int ready, stop;
+    unsigned cont;
+};
+
 template <bool kWait, int NW>
-__device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap)
+__device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap,
+                        GroupShared &sh)
 {
-    __shared__ int s_ready_[2], s_stop_[2];
-    __shared__ long long s_lb_[2][32];
-    __shared__ int s_nl_[2][32];
-    __shared__ double s_red_[2][kWarps];
-    int &s_ready = s_ready_[g];
-    int &s_stop = s_stop_[g];
-    long long *s_lb = s_lb_[g];
-    int *s_nl = s_nl_[g];
-    double *s_red = s_red_[g];
+    int &s_ready = sh.ready;
+    int &s_stop = sh.stop;
+    unsigned &s_cont = sh.cont;
+    long long *s_lb = sh.lb;
+    int *s_nl = sh.nl;
+    double *s_red = sh.red;
+    double *s_tri = sh.tri;
     constexpr int kT = NW * 32;
     const int tid = threadIdx.x - g * kT, lane = tid & 31, warp = tid >> 5;
     const int64_t beg = __ldg(a.LUp + k);
@@ -242,77 +267,96 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     }
     group_sync<NW>(g);
 
-    int nr[kPre];
-    double nv[kPre];
-    bool have = false;
-    auto load_entries = [&](long long lb, int nl) {
-#pragma unroll
-        for (int u = 0; u < kPre; u++) {
-            const int i = u * kT + tid;
-            nr[u] = i < nl ? __ldg(a.LUi + lb + i) : -1;
-            nv[u] = i < nl ? __ldcg(a.LUx + lb + i) : 0.0;
-        }
-    };
-
     int ready = 0, mbase = 0;
-    for (int t = 0; t < nD; ++t) {
+    unsigned cont = 0;   // bit q: dependency mbase+q continues the run of mbase+q-1
+    for (int t = 0; t < nD;) {
         if (t >= ready) {
             if (warp == 0) {
                 const int tt = t + lane;
                 const int jj = tt < nD ? rows[tt] : -1;
                 bool ok = true;
+                int ch = 0;
                 if (jj >= 0) {
                     if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
                     const long long lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
                     s_lb[lane] = lb;
                     s_nl[lane] = (int)(__ldg(a.LUp + jj + 1) - lb);
+                    ch = __ldg(a.chain + jj);
                 }
+                const int jp = __shfl_up_sync(kFull, jj, 1);
+                const int cp = __shfl_up_sync(kFull, ch, 1);
+                const unsigned cm = __ballot_sync(kFull, lane > 0 && jj >= 0 && jj == jp + 1 && cp != 0);
                 const unsigned m = __ballot_sync(kFull, ok);
                 const int run = (m == kFull) ? 32 : __ffs(~m) - 1;
                 if (kWait && run == 0 && lane == 0 && !spin_until(a.finish + rows[t], epoch, a, k)) s_stop = 1;
-                if (lane == 0) s_ready = t + (run > 0 ? run : 1);
+                if (lane == 0) {
+                    s_ready = t + (run > 0 ? run : 1);
+                    s_cont = cm;
+                }
             }
             group_sync<NW>(g);
             if (s_stop) return true;
             ready = s_ready;
+            cont = s_cont;
             mbase = t;
         }
-        const long long lb = s_lb[t - mbase];
-        const int nl = s_nl[t - mbase];
-        if (!have) load_entries(lb, nl);
-        int cr[kPre];
-        double cv[kPre];
+        const int q0 = t - mbase;
+        int w = 1;
+        while (t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
+        if (w > 1) {   // triangle of the run
+            for (int d = warp; d < w - 1; d += NW)
+                if (lane < w - 1 - d) s_tri[tri_off(d) + lane] = __ldcg(a.LUx + s_lb[q0 + d] + lane);
+            group_sync<NW>(g);
+            if (warp == 0) {
+                double v = lane < w ? x[t + lane] : 0.0;
+                for (int d = 0; d < w - 1; ++d) {
+                    const double m = __shfl_sync(kFull, v, d);
+                    if (lane > d && lane < w) v = fma(-s_tri[tri_off(d) + lane - d - 1], m, v);
+                }
+                if (lane < w) x[t + lane] = v;
+            }
+            group_sync<NW>(g);
+        }
+        {   // rectangle: rows of R = L(:, j+w-1), multipliers x(t .. t+w-1)
+            const int tl = t + w - 1;
+            const int jl = rows[tl];
+            const long long lbl = s_lb[q0 + w - 1];
+            const int nR = s_nl[q0 + w - 1];
+            bool bad = false;
+            for (int r0 = 0; r0 < nR; r0 += kRows * kT) {
+                int sl[kRows];
+                double v[kRows];
 #pragma unroll
-        for (int u = 0; u < kPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
-        have = false;
-        if (t + 1 < ready) {
-            load_entries(s_lb[t + 1 - mbase], s_nl[t + 1 - mbase]);
-            have = true;
-        }
-        const int j = rows[t];
-        const double xj = x[t];
-        bool bad = false;
+                for (int u = 0; u < kRows; u++) {
+                    const int r = r0 + u * kT + tid;
+                    sl[u] = -1;
+                    if (r < nR) {
+                        const int row = __ldg(a.LUi + lbl + r);
+                        sl[u] = find_slot(rows, tl + 1 + r, tl + (row - jl), len, row);
+                        if (sl[u] < 0) bad = true;
+                    }
+                    v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
+                }
+#pragma unroll 4
+                for (int d = 0; d < w; d++) {
+                    const double m = x[t + d];
+                    const double *lv = a.LUx + s_lb[q0 + d] + (w - 1 - d) + r0 + tid;
 #pragma unroll
-        for (int u = 0; u < kPre; u++) {
-            if (cr[u] < 0) continue;
-            const int i = u * kT + tid;
-            const int sl = find_slot(rows, t + 1 + i, t + (cr[u] - j), len, cr[u]);
-            if (sl < 0) { bad = true; continue; }
-            x[sl] = fma(-xj, cv[u], x[sl]);
+                    for (int u = 0; u < kRows; u++)
+                        if (sl[u] >= 0) v[u] = fma(-m, __ldcg(lv + u * kT), v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; u++)
+                    if (sl[u] >= 0) x[sl[u]] = v[u];
+            }
+            if (bad) s_stop = 2;
         }
-        for (int i = kPre * kT + tid; i < nl; i += kT) {  // long dependencies
-            const int r = __ldg(a.LUi + lb + i);
-            const double v = __ldcg(a.LUx + lb + i);
-            const int sl = find_slot(rows, t + 1 + i, t + (r - j), len, r);
-            if (sl < 0) { bad = true; continue; }
-            x[sl] = fma(-xj, v, x[sl]);
-        }
-        if (bad) s_stop = 2;
         group_sync<NW>(g);
         if (s_stop) {  // inconsistent pattern: never index with it
             if (tid == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
             return true;
         }
+        t += w;
     }
 
     const double d = x[nU - 1];
@@ -359,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_quit;
+    __shared__ GroupShared s_grp[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *xs = reinterpret_cast<double *>(smem);
     int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)a.cap_long * sizeof(double));
@@ -377,12 +422,12 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
         const int k0 = __ldg(a.task_cols + c0);
         const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
         if (c1 - c0 == 1 && len0 > a.cap_short) {          // one long column: whole CTA
-            stop = col_grp<kWait, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long);
+            stop = col_grp<kWait, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
         } else if (c1 - c0 == 2 && len0 > a.cap_short) {   // two medium columns: a half each
             const int g = warp / (kWarps / 2);
             const int half = a.cap_long / 2;
             const bool hs = col_grp<kWait, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
-                                                       rs + (size_t)g * half, epoch, g, half);
+                                                       rs + (size_t)g * half, epoch, g, half, s_grp[g]);
             stop = __syncthreads_or(hs);
         } else {
             bool ws = false;

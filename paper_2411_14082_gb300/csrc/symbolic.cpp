@@ -272,6 +272,14 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     for (int32_t k = 0; k < n; k++)
         for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
             W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
+    // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
+    W.chain.assign(n, 0);
+    for (int32_t j = 0; j + 1 < n; j++) {
+        const int64_t a = S.LUp[j] + S.nU[j], ae = S.LUp[j + 1];
+        const int64_t b = S.LUp[j + 1] + S.nU[j + 1], be = S.LUp[j + 2];
+        if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
+        W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
+    }
     // ---- row-wise copies for the solves ----
     W.Lrp.assign(n + 1, 0);
     W.Urp.assign(n + 1, 0);
