@@ -50,6 +50,7 @@ __device__ __forceinline__ int find_slot(const int32_t *rows, int lo, int hi, in
 {
     if (hi > len - 1) hi = len - 1;
     if (lo > hi) return -1;
+    if (rows[lo] == r) return lo;   // the lower bound is exact inside dense stretches
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (rows[mid] < r) lo = mid + 1;
@@ -58,10 +59,15 @@ __device__ __forceinline__ int find_slot(const int32_t *rows, int lo, int hi, in
     return rows[lo] == r ? lo : -1;
 }
 
-// one column, one warp.  Every 32 dependencies the lanes check their ready
-// flags and load their (start, length) in L; the values are then broadcast
-// by shuffles, so a dependency step needs no dependent global load before
-// its entries.
+// one column, one warp.  Dependencies are applied in runs of consecutive
+// columns of one supernode of L, as in the group kernel below (there with
+// the full description), here with runs of at most kWarpRun columns and the
+// run's triangle held in registers (lane q holds row q of it).  Every 32
+// dependencies the lanes check their ready flags and load their (start,
+// length) in L and their supernode links; the values are then broadcast by
+// shuffles.
+constexpr int kWarpRun = 8;
+
 template <bool kWait>
 __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int lane,
                          int epoch)
@@ -88,16 +94,22 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
     int ready = 0, mbase = 0;
     long long m_lb = 0;
     int m_nl = 0;
-    for (int t = 0; t < nD; ++t) {
+    unsigned cont = 0;   // bit q: dependency mbase+q continues the run of mbase+q-1
+    for (int t = 0; t < nD;) {
         if (t >= ready) {
             const int tt = t + lane;
             const int jj = tt < nD ? rows[tt] : -1;
             bool ok = true;
+            int ch = 0;
             if (jj >= 0) {
                 if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
                 m_lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
                 m_nl = (int)(__ldg(a.LUp + jj + 1) - m_lb);
+                ch = __ldg(a.chain + jj);
             }
+            const int jp = __shfl_up_sync(kFull, jj, 1);
+            const int cp = __shfl_up_sync(kFull, ch, 1);
+            cont = __ballot_sync(kFull, lane > 0 && jj >= 0 && jj == jp + 1 && cp != 0);
             const unsigned m = __ballot_sync(kFull, ok);
             int run = (m == kFull) ? 32 : __ffs(~m) - 1;
             if (run == 0) {
@@ -120,27 +132,58 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             mbase = t;
             __syncwarp();
         }
-        const int j = rows[t];
-        const double xj = x[t];
-        const int64_t lb = __shfl_sync(kFull, m_lb, t - mbase);
-        const int nl = __shfl_sync(kFull, m_nl, t - mbase);
-        for (int base = 0; base < nl; base += 32 * kBatch) {
-            int r[kBatch];
-            double v[kBatch];
+        const int q0 = t - mbase;
+        int w = 1;
+        while (w < kWarpRun && t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
+        if (w > 1) {   // triangle: lane q < w holds x(j+q)
+            double tv[kWarpRun - 1];
 #pragma unroll
-            for (int u = 0; u < kBatch; u++) {
-                const int i = base + u * 32 + lane;
-                r[u] = i < nl ? __ldg(a.LUi + lb + i) : -1;
-                v[u] = i < nl ? __ldcg(a.LUx + lb + i) : 0.0;
+            for (int d = 0; d < kWarpRun - 1; d++) {
+                const long long lbd = __shfl_sync(kFull, m_lb, (q0 + d) & 31);
+                tv[d] = (d < w - 1 && lane > d && lane < w) ? __ldcg(a.LUx + lbd + (lane - d - 1)) : 0.0;
             }
-            bool bad = false;
+            double v = lane < w ? x[t + lane] : 0.0;
 #pragma unroll
-            for (int u = 0; u < kBatch; u++) {
-                if (r[u] < 0) continue;
-                const int i = base + u * 32 + lane;
-                const int sl = find_slot(rows, t + 1 + i, t + (r[u] - j), len, r[u]);
-                if (sl < 0) { bad = true; continue; }
-                x[sl] = fma(-xj, v[u], x[sl]);
+            for (int d = 0; d < kWarpRun - 1; d++) {
+                if (d < w - 1) {
+                    const double mv = __shfl_sync(kFull, v, d);
+                    if (lane > d && lane < w) v = fma(-tv[d], mv, v);
+                }
+            }
+            if (lane < w) x[t + lane] = v;
+            __syncwarp();
+        }
+        {   // rectangle: rows of R = L(:, j+w-1), multipliers x(t .. t+w-1)
+            const int tl = t + w - 1;
+            const int jl = rows[tl];
+            const long long lbl = __shfl_sync(kFull, m_lb, q0 + w - 1);
+            const int nR = __shfl_sync(kFull, m_nl, q0 + w - 1);
+            bool bad = false;
+            for (int r0 = 0; r0 < nR; r0 += 32 * kBatch) {
+                int sl[kBatch];
+                double v[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; u++) {
+                    const int r = r0 + u * 32 + lane;
+                    sl[u] = -1;
+                    if (r < nR) {
+                        const int row = __ldg(a.LUi + lbl + r);
+                        sl[u] = find_slot(rows, tl + 1 + r, tl + (row - jl), len, row);
+                        if (sl[u] < 0) bad = true;
+                    }
+                    v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
+                }
+                for (int d = 0; d < w; d++) {
+                    const double mv = x[t + d];
+                    const long long lbd = __shfl_sync(kFull, m_lb, q0 + d);
+                    const double *lv = a.LUx + lbd + (w - 1 - d) + r0 + lane;
+#pragma unroll
+                    for (int u = 0; u < kBatch; u++)
+                        if (sl[u] >= 0) v[u] = fma(-mv, __ldcg(lv + u * 32), v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; u++)
+                    if (sl[u] >= 0) x[sl[u]] = v[u];
             }
             if (__any_sync(kFull, bad)) {  // inconsistent pattern: never index with it
                 if (lane == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
@@ -148,6 +191,7 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             }
         }
         __syncwarp();
+        t += w;
     }
 
     const double d = x[nU - 1];
