@@ -102,10 +102,11 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             bool ok = true;
             int ch = 0;
             if (jj >= 0) {
-                if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
+                // structure first: an acquire load holds back the loads after it
                 m_lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
                 m_nl = (int)(__ldg(a.LUp + jj + 1) - m_lb);
                 ch = __ldg(a.chain + jj);
+                if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
             }
             const int jp = __shfl_up_sync(kFull, jj, 1);
             const int cp = __shfl_up_sync(kFull, ch, 1);
@@ -135,6 +136,10 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
         const int q0 = t - mbase;
         int w = 1;
         while (w < kWarpRun && t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
+        if (w < kWarpRun && t > mbase && t + w == mbase + 32 && t + w < nD) {
+            ready = t;   // the run reaches the end of the staged window: stage from its start
+            continue;
+        }
         if (w > 1) {   // triangle: lane q < w holds x(j+q)
             double tv[kWarpRun - 1];
 #pragma unroll
@@ -321,11 +326,13 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
                 bool ok = true;
                 int ch = 0;
                 if (jj >= 0) {
-                    if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
+                    // structure first: an acquire load holds back the loads after it
                     const long long lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
-                    s_lb[lane] = lb;
-                    s_nl[lane] = (int)(__ldg(a.LUp + jj + 1) - lb);
+                    const int nlj = (int)(__ldg(a.LUp + jj + 1) - lb);
                     ch = __ldg(a.chain + jj);
+                    if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
+                    s_lb[lane] = lb;
+                    s_nl[lane] = nlj;
                 }
                 const int jp = __shfl_up_sync(kFull, jj, 1);
                 const int cp = __shfl_up_sync(kFull, ch, 1);
@@ -347,6 +354,10 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
         const int q0 = t - mbase;
         int w = 1;
         while (t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
+        if (t > mbase && t + w == mbase + 32 && t + w < nD) {
+            ready = t;   // the run reaches the end of the staged window: stage from its start
+            continue;
+        }
         if (w > 1) {   // triangle of the run
             for (int d = warp; d < w - 1; d += NW)
                 if (lane < w - 1 - d) s_tri[tri_off(d) + lane] = __ldcg(a.LUx + s_lb[q0 + d] + lane);
