@@ -203,6 +203,6 @@ constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short co
 constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
-constexpr int kMaxPieceRows = 4096;    // rows of one triangular piece (80 KB shared memory)
+constexpr int kMaxPieceRows = 4096;    // rows of one triangular piece (216 KB shared memory)
 
 }  // namespace gblu

@@ -471,7 +471,61 @@ usolve_rect_kernel(SolveArgs a, DenseArgs d)
 }
 
 constexpr int kTriThreads = 256;
-constexpr int kTriPre = 4;   // piece entries per thread prefetched for the next column
+constexpr int kTriStages = 6;      // columns in flight: the current one and 5 ahead
+constexpr int kTriRing = 1024;     // entries of one column staged per stage (4 per thread)
+
+// asynchronous global -> shared copies (cp.async); each thread later reads
+// only the slots it copied itself, so its own wait_group is enough
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_newest() { asm volatile("cp.async.wait_group %0;" ::"n"(kTriStages - 1) : "memory"); }
+
+// shared memory of a triangular piece of m rows: a ring of kTriStages
+// staged columns (values, rows), then per row: the vector, the start and
+// count of its column's piece entries, its diagonal and its result
+struct TriSmem {
+    double *rv, *vec, *diag, *out;
+    long long *sb;
+    int32_t *ri, *sc;
+};
+__device__ __forceinline__ TriSmem tri_layout(unsigned char *smem, int m)
+{
+    TriSmem t;
+    t.rv = reinterpret_cast<double *>(smem);
+    t.vec = t.rv + kTriStages * kTriRing;
+    t.diag = t.vec + m;
+    t.out = t.diag + m;
+    t.sb = reinterpret_cast<long long *>(t.out + m);
+    t.ri = reinterpret_cast<int32_t *>(t.sb + m);
+    t.sc = t.ri + kTriStages * kTriRing;
+    return t;
+}
+
+// stage column q's first min(count, kTriRing) piece entries into ring slot
+// `stage` (thread tid copies entries tid, tid + kTriThreads, ...); always
+// commits one group so that group counting stays uniform
+__device__ __forceinline__ void tri_issue(const TriSmem &t, const SolveArgs &a, const DenseArgs &d,
+                                          int q, int stage, bool valid, int tid)
+{
+    if (valid) {
+        const long long b = t.sb[q];
+        const int c = min(t.sc[q], kTriRing);
+        for (int p = tid; p < c; p += kTriThreads) {
+            cp_async8(t.rv + stage * kTriRing + p, a.LUx + b + p);
+            cp_async4(t.ri + stage * kTriRing + p, d.LUi + b + p);
+        }
+    }
+    cp_commit();
+}
 
 // forward triangular piece [r0, r1): columns in increasing order; the first
 // tri[j] L entries of column j are its rows inside the piece
@@ -479,44 +533,33 @@ __global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, De
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int m = d.r1 - d.r0, tid = threadIdx.x;
-    double *ys = reinterpret_cast<double *>(smem);
-    long long *sb = reinterpret_cast<long long *>(ys + m);
-    int *sc = reinterpret_cast<int *>(sb + m);
+    const TriSmem t = tri_layout(smem, m);
     for (int q = tid; q < m; q += kTriThreads) {
         const int j = d.r0 + q;
-        ys[q] = __ldcg(a.y + j);
-        sb[q] = __ldg(d.LUp + j) + __ldg(d.nU + j);
-        sc[q] = __ldg(d.tri + (j - d.p0));
+        t.vec[q] = __ldcg(a.y + j);
+        t.sb[q] = __ldg(d.LUp + j) + __ldg(d.nU + j);
+        t.sc[q] = __ldg(d.tri + (j - d.p0));
     }
     __syncthreads();
-    int nr[kTriPre];
-    double nv[kTriPre];
-    auto load = [&](int q) {
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++) {
-            const int p = u * kTriThreads + tid;
-            nr[u] = p < sc[q] ? __ldg(d.LUi + sb[q] + p) : -1;
-            nv[u] = p < sc[q] ? __ldg(a.LUx + sb[q] + p) : 0.0;
-        }
-    };
-    if (m > 0) load(0);
+    for (int q = 0; q < kTriStages - 1; q++) tri_issue(t, a, d, q, q % kTriStages, q < m, tid);
     for (int q = 0; q < m; q++) {
-        int cr[kTriPre];
-        double cv[kTriPre];
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
-        if (q + 1 < m) load(q + 1);
-        const double yj = ys[q];
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++)
-            if (cr[u] >= 0) ys[cr[u] - d.r0] = fma(-cv[u], yj, ys[cr[u] - d.r0]);
-        for (int p = kTriPre * kTriThreads + tid; p < sc[q]; p += kTriThreads) {
-            const int r = __ldg(d.LUi + sb[q] + p);
-            ys[r - d.r0] = fma(-__ldg(a.LUx + sb[q] + p), yj, ys[r - d.r0]);
+        const int qa = q + kTriStages - 1;
+        tri_issue(t, a, d, qa, qa % kTriStages, qa < m, tid);
+        cp_wait_all_but_newest();
+        const int s = q % kTriStages;
+        const double yj = t.vec[q];
+        const int c = t.sc[q];
+        for (int p = tid; p < min(c, kTriRing); p += kTriThreads) {
+            const int r = t.ri[s * kTriRing + p] - d.r0;
+            t.vec[r] = fma(-t.rv[s * kTriRing + p], yj, t.vec[r]);
+        }
+        for (int p = kTriRing + tid; p < c; p += kTriThreads) {   // longer columns
+            const int r = __ldg(d.LUi + t.sb[q] + p) - d.r0;
+            t.vec[r] = fma(-__ldg(a.LUx + t.sb[q] + p), yj, t.vec[r]);
         }
         __syncthreads();
     }
-    for (int q = tid; q < m; q += kTriThreads) a.y[d.r0 + q] = ys[q];
+    for (int q = tid; q < m; q += kTriThreads) a.y[d.r0 + q] = t.vec[q];
 }
 
 // backward triangular piece [r0, r1): columns in decreasing order; the U
@@ -526,51 +569,42 @@ __global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, De
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int m = d.r1 - d.r0, tid = threadIdx.x;
-    double *zs = reinterpret_cast<double *>(smem);
-    long long *sb = reinterpret_cast<long long *>(zs + m);
-    int *sc = reinterpret_cast<int *>(sb + m);
+    const TriSmem t = tri_layout(smem, m);
     for (int q = tid; q < m; q += kTriThreads) {
         const int j = d.r0 + q;
-        zs[q] = __ldcg(a.z + j);
+        t.vec[q] = __ldcg(a.z + j);
         const long long b = __ldg(d.LUp + j) + __ldg(d.tri + (j - d.p0));
-        sb[q] = b;
-        sc[q] = (int)(__ldg(d.LUp + j) + __ldg(d.nU + j) - 1 - b);
+        t.sb[q] = b;
+        t.sc[q] = (int)(__ldg(d.LUp + j) + __ldg(d.nU + j) - 1 - b);
+        t.diag[q] = __ldg(a.LUx + __ldg(a.Udiag + j));
     }
     __syncthreads();
-    int nr[kTriPre];
-    double nv[kTriPre];
-    auto load = [&](int q) {
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++) {
-            const int p = u * kTriThreads + tid;
-            nr[u] = p < sc[q] ? __ldg(d.LUi + sb[q] + p) : -1;
-            nv[u] = p < sc[q] ? __ldg(a.LUx + sb[q] + p) : 0.0;
+    // step i handles column q = m - 1 - i
+    for (int i = 0; i < kTriStages - 1; i++) tri_issue(t, a, d, m - 1 - i, i % kTriStages, i < m, tid);
+    for (int i = 0; i < m; i++) {
+        const int ia = i + kTriStages - 1;
+        tri_issue(t, a, d, m - 1 - ia, ia % kTriStages, ia < m, tid);
+        cp_wait_all_but_newest();
+        const int q = m - 1 - i, s = i % kTriStages;
+        // every thread divides; the piece entries of column q are rows above
+        // q, so nobody writes vec[q] in this step
+        const double zj = t.vec[q] / t.diag[q];
+        if (tid == 0) t.out[q] = zj;
+        const int c = t.sc[q];
+        for (int p = tid; p < min(c, kTriRing); p += kTriThreads) {
+            const int r = t.ri[s * kTriRing + p] - d.r0;
+            t.vec[r] = fma(-t.rv[s * kTriRing + p], zj, t.vec[r]);
         }
-    };
-    if (m > 0) load(m - 1);
-    for (int q = m - 1; q >= 0; q--) {
-        int cr[kTriPre];
-        double cv[kTriPre];
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++) { cr[u] = nr[u]; cv[u] = nv[u]; }
-        if (q > 0) load(q - 1);
-        const int j = d.r0 + q;
-        const double zj = zs[q] / __ldg(a.LUx + __ldg(a.Udiag + j));
-        __syncthreads();   // every thread has read zs[q]
-        if (tid == 0) zs[q] = zj;
-#pragma unroll
-        for (int u = 0; u < kTriPre; u++)
-            if (cr[u] >= 0) zs[cr[u] - d.r0] = fma(-cv[u], zj, zs[cr[u] - d.r0]);
-        for (int p = kTriPre * kTriThreads + tid; p < sc[q]; p += kTriThreads) {
-            const int r = __ldg(d.LUi + sb[q] + p);
-            zs[r - d.r0] = fma(-__ldg(a.LUx + sb[q] + p), zj, zs[r - d.r0]);
+        for (int p = kTriRing + tid; p < c; p += kTriThreads) {   // longer columns
+            const int r = __ldg(d.LUi + t.sb[q] + p) - d.r0;
+            t.vec[r] = fma(-__ldg(a.LUx + t.sb[q] + p), zj, t.vec[r]);
         }
         __syncthreads();
     }
     for (int q = tid; q < m; q += kTriThreads) {
         const int j = d.r0 + q;
-        a.z[j] = zs[q];
-        a.x[__ldg(a.Q + j)] = zs[q];
+        a.z[j] = t.out[q];
+        a.x[__ldg(a.Q + j)] = t.out[q];
     }
 }
 
@@ -681,7 +715,8 @@ int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 
 size_t tri_smem(int rows)
 {
-    return (size_t)rows * (sizeof(double) + sizeof(long long) + sizeof(int));
+    return (size_t)kTriStages * kTriRing * (sizeof(double) + sizeof(int32_t)) +
+           (size_t)rows * (3 * sizeof(double) + sizeof(long long) + sizeof(int32_t));
 }
 
 int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,
