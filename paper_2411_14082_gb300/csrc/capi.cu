@@ -98,9 +98,10 @@ struct gblu_ctx {
     DBuf<double> vals;
     // solves
     DBuf<int64_t> Lrp, Urp;
-    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, ltcnt, utstart;
+    DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, lbs, ubs, lrb, urb, lsv_tick, usv_tick,
+        ltcnt, utstart;
     DBuf<int64_t> lsplit, usplit;
-    DBuf<double> y, z, partial, stage_ax, stage_b, stage_x;
+    DBuf<double> y, z, ext_l, ext_u, partial, stage_ax, stage_b, stage_x;
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
@@ -210,6 +211,8 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(ensure(h, h->finish, n));
     CK(ensure(h, h->y, n));
     CK(ensure(h, h->z, n));
+    CK(ensure(h, h->ext_l, n));
+    CK(ensure(h, h->ext_u, n));
     // ready flags hold epochs (> 0); recycled device memory may hold any
     // value, so they start from zero
     CU(cudaMemsetAsync(h->finish.p, 0, sizeof(int32_t) * n, st));
@@ -231,6 +234,12 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->Udiag, h->W.Udiag, st));
     CK(upload(h, h->lsv_rows, h->W.lsv_rows, st));
     CK(upload(h, h->usv_rows, h->W.usv_rows, st));
+    CK(upload(h, h->lbs, h->W.lbs, st));
+    CK(upload(h, h->ubs, h->W.ubs, st));
+    CK(upload(h, h->lrb, h->W.lrb, st));
+    CK(upload(h, h->urb, h->W.urb, st));
+    CK(upload(h, h->lsv_tick, h->W.lsv_tick, st));
+    CK(upload(h, h->usv_tick, h->W.usv_tick, st));
     CK(upload(h, h->lsplit, h->W.lsplit, st));
     CK(upload(h, h->ltcnt, h->W.ltcnt, st));
     CK(upload(h, h->usplit, h->W.usplit, st));
@@ -554,7 +563,10 @@ void gblu_destroy(gblu_handle h)
         release(h, h->piv); release(h, h->pinv); release(h, h->vals);
         release(h, h->Lrp); release(h, h->Urp); release(h, h->Lcol); release(h, h->Lslot);
         release(h, h->Ucol); release(h, h->Uslot); release(h, h->Udiag);
-        release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->ltcnt);
+        release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->lbs); release(h, h->ubs);
+        release(h, h->lrb); release(h, h->urb); release(h, h->lsv_tick); release(h, h->usv_tick);
+        release(h, h->ext_l); release(h, h->ext_u);
+        release(h, h->ltcnt);
         release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
         release(h, h->y); release(h, h->z); release(h, h->partial);
         release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
@@ -699,7 +711,7 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t n = h->S.n;
-    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, n, st));
+    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n, st));
     SolveArgs a{};
     a.n = n;
     a.LUx = h->vals.p;
@@ -719,24 +731,32 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
     const Schedule &W = h->W;
-    // sparse block rows [0, nrows): levels before the dividing level one
-    // launch each, the rest one sync-free launch
+    // sparse part (rows [0, lp0) / [0, up0)) in row blocks: block levels
+    // before the dividing level one launch each, the rest one sync-free launch
     auto sparse = [&](bool lower) -> int {
-        const std::vector<int32_t> &ptr = lower ? W.lsv_ptr : W.usv_ptr;
+        const std::vector<int32_t> &ptr = lower ? W.lsv_ptr : W.usv_ptr;     // blocks per level
+        const std::vector<int32_t> &tptr = lower ? W.lsv_tptr : W.usv_tptr;  // rows per level
         const int32_t nlev = lower ? W.lsv_levels : W.usv_levels;
-        const int32_t nrows = lower ? W.lp0 : W.up0;
+        const int32_t nrows = (int32_t)(lower ? W.lsv_tick.size() : W.usv_tick.size());
         int32_t div = lower ? W.lsv_div : W.usv_div;
         if (h->opts.solve_mode == GBLU_SCHED_LEVEL) div = nlev;
         if (h->opts.solve_mode == GBLU_SCHED_SYNCFREE) div = 0;
-        int32_t *rows = lower ? h->lsv_rows.p : h->usv_rows.p;
-        for (int32_t l = 0; l < div; l++) {
-            a.rows = rows + ptr[l];
-            a.nrows = ptr[l + 1] - ptr[l];
+        int32_t *blocks = lower ? h->lsv_rows.p : h->usv_rows.p;
+        int32_t *tick = lower ? h->lsv_tick.p : h->usv_tick.p;
+        a.bs = lower ? h->lbs.p : h->ubs.p;
+        a.rb = lower ? h->lrb.p : h->urb.p;
+        a.ext = lower ? h->ext_l.p : h->ext_u.p;
+        for (int32_t l = 0; l < div; l++) {   // outside sums of the level's rows, then its blocks
+            a.rows = tick + tptr[l];
+            a.nrows = tptr[l + 1] - tptr[l];
             KL(lower ? launch_lsolve(a, true, 0, st) : launch_usolve(a, true, 0, st));
+            a.rows = blocks + ptr[l];
+            a.nrows = ptr[l + 1] - ptr[l];
+            KL(launch_solve_finish(a, lower, st));
         }
         if (div < nlev) {
-            a.rows = rows + ptr[div];
-            a.nrows = nrows - ptr[div];
+            a.rows = tick + tptr[div];
+            a.nrows = nrows - tptr[div];
             KL(lower ? launch_lsolve(a, false, h->solve_grid, st)
                      : launch_usolve(a, false, h->solve_grid, st));
         }

@@ -59,8 +59,17 @@ struct Schedule {
     std::vector<int32_t> Lcol, Urow_col;  // column (step) of each entry
     std::vector<int32_t> Lslot, Uslot;    // slot in LUx
     std::vector<int32_t> Udiag;           // slot of U(i,i)
-    std::vector<int32_t> lsv_ptr, lsv_rows; int32_t lsv_levels = 0, lsv_div = 0;
-    std::vector<int32_t> usv_ptr, usv_rows; int32_t usv_levels = 0, usv_div = 0;
+    // sparse part of each solve (rows [0, lp0) forward, [0, up0) backward),
+    // solved in row blocks: block b is rows [lbs[b], lbs[b+1]), at most
+    // kSolveBlockRows consecutive rows whose diagonal block is dense (rows of
+    // one supernode of L forward, of U backward); lrb[i] is the block of row
+    // i.  lsv_rows holds the block ids level by level (lsv_ptr), lsv_tick the
+    // rows in the same order (lsv_tptr; inside a block ascending forward,
+    // descending backward, so the row that finishes a block comes last);
+    // lsv_div is the first sync-free level
+    std::vector<int32_t> lbs, ubs, lrb, urb;
+    std::vector<int32_t> lsv_ptr, lsv_rows, lsv_tptr, lsv_tick; int32_t lsv_levels = 0, lsv_div = 0;
+    std::vector<int32_t> usv_ptr, usv_rows, usv_tptr, usv_tick; int32_t usv_levels = 0, usv_div = 0;
     // structure-adaptive solve (Section V): rows [p0, n) form the trailing
     // block, cut at slice boundaries cut[0] = p0 < ... < cut[m] = n.
     // Forward: the rectangular part of row i (p0 <= i) is its CSR entries
@@ -170,8 +179,11 @@ struct SolveArgs {
     const int32_t *piv, *Q;
     const double *b;
     double *y, *z, *x;              // forward result, backward result, output
-    const int32_t *rows;            // level-mode row list
-    int32_t nrows;
+    const int32_t *bs;              // row blocks: block b is rows [bs[b], bs[b+1])
+    const int32_t *rb;              // block of each row
+    double *ext;                    // per row: its sum over entries outside its block
+    const int32_t *rows;            // rows in ticket order, or block ids (level finish)
+    int32_t nrows;                  // number of entries of rows
     long long spin_limit;
     DevCtl *ctl;
 };
@@ -184,7 +196,8 @@ int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
-int launch_begin_solve(DevCtl *ctl, double *y, double *z, int n, void *stream);
+int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream);
+int launch_solve_finish(const SolveArgs &a, bool lower, void *stream);
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
 int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
@@ -203,6 +216,8 @@ constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short co
 constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
+constexpr int kSolveBlockRows = 32;   // rows of one block of the sparse solves
+constexpr int kSolveBlockThreads = 256;
 constexpr int kMaxPieceRows = 4096;    // rows of one triangular piece (216 KB shared memory)
 
 }  // namespace gblu

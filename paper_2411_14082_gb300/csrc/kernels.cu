@@ -316,11 +316,14 @@ __device__ __forceinline__ void st_relaxed_f64(double *p, double v)
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
 }
 
-__global__ void begin_solve_kernel(DevCtl *ctl, double *y, double *z, int n)
+__global__ void begin_solve_kernel(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n)
 {
+    const double sent = __longlong_as_double((long long)kSentinel);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        y[i] = __longlong_as_double((long long)kSentinel);
-        z[i] = __longlong_as_double((long long)kSentinel);
+        y[i] = sent;
+        z[i] = sent;
+        el[i] = sent;
+        eu[i] = sent;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->ticket_l = 0;
@@ -348,60 +351,145 @@ __device__ __forceinline__ bool await_value(const double *v, int j, const SolveA
     return true;
 }
 
-__device__ bool lsolve_row(const SolveArgs &a, int i, int lane)
+// ---------------------------------------------------------------------------
+// Sparse part of the two solves (Algorithm 2), by row blocks: a block is at
+// most 32 consecutive rows f..l-1 whose diagonal block is dense (the rows of
+// one supernode of L forward, of U backward).  One warp per row sums the
+// row's entries outside its block (lanes over entries, waiting for each
+// needed value to be published) and publishes that sum; the row that comes
+// last in its block (the last row forward, the first backward) then gathers
+// the block's sums and solves the dense diagonal block with shuffles, lane q
+// holding row f+q, and publishes the block's values.  The chain of dependent
+// steps is a chain of blocks, not of rows.  Values are published by
+// overwriting a sentinel.  The arithmetic does not depend on when inputs
+// arrive, so level launches (sums, then block finishes) and the sync-free
+// launch give identical bits.
+constexpr int kBR = kSolveBlockRows;
+
+// forward: sum over the entries of row i outside its block (all but its last q)
+__device__ __forceinline__ bool lrow_ext(const SolveArgs &a, int i, int q, int lane, bool wait, double &s)
 {
-    const int64_t rb = __ldg(a.Lrp + i), re = __ldg(a.Lrp + i + 1);
-    double s = 0.0;
+    const int64_t rb = __ldg(a.Lrp + i), re = __ldg(a.Lrp + i + 1) - q;
+    double acc = 0.0;
     bool ok = true;
     for (int64_t e = rb + lane; e < re; e += 32) {
+        const int j = __ldg(a.Lcol + e);
         double yj = 0.0;
-        if (ok) ok = await_value(a.y, __ldg(a.Lcol + e), a, 3, i, yj);
-        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), yj, s);
+        if (!wait) yj = __ldcg(a.y + j);
+        else if (ok) ok = await_value(a.y, j, a, 3, i, yj);
+        acc = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), yj, acc);
     }
-    s = warp_sum(s);
-    if (lane == 0) st_relaxed_f64(a.y + i, __ldg(a.b + __ldg(a.piv + i)) - s);
-    return !__all_sync(kFull, ok);
+    s = warp_sum(acc);
+    return __all_sync(kFull, ok);
 }
 
-__device__ bool usolve_row(const SolveArgs &a, int i, int lane)
+// forward block finish: lane p < w holds e = the outside sum of row f+p
+__device__ __forceinline__ void lblock_finish(const SolveArgs &a, int f, int w, int lane, double e)
 {
-    const int64_t rb = __ldg(a.Urp + i), re = __ldg(a.Urp + i + 1);
-    double s = 0.0;
+    // row f+p's last p entries are L(f+p, f .. f+p-1)
+    const int64_t rend = lane < w ? __ldg(a.Lrp + f + lane + 1) - lane : 0;
+    double tv[kBR - 1];
+#pragma unroll
+    for (int d = 0; d < kBR - 1; d++)
+        tv[d] = (d < lane && lane < w) ? __ldg(a.LUx + __ldg(a.Lslot + rend + d)) : 0.0;
+    double v = lane < w ? __ldg(a.b + __ldg(a.piv + f + lane)) - e : 0.0;
+#pragma unroll
+    for (int d = 0; d < kBR - 1; d++) {
+        if (d < w - 1) {
+            const double yd = __shfl_sync(kFull, v, d);
+            if (lane > d && lane < w) v = fma(-tv[d], yd, v);
+        }
+    }
+    if (lane < w) st_relaxed_f64(a.y + f + lane, v);
+}
+
+// backward: sum over the entries of row i outside its block (all but its
+// first w-1-q), from the last column down
+__device__ __forceinline__ bool urow_ext(const SolveArgs &a, int i, int q, int w, int lane, bool wait,
+                                         double &s)
+{
+    const int64_t rb = __ldg(a.Urp + i) + (w - 1 - q), re = __ldg(a.Urp + i + 1);
+    double acc = 0.0;
     bool ok = true;
     for (int64_t e = re - 1 - lane; e >= rb; e -= 32) {
+        const int j = __ldg(a.Ucol + e);
         double zj = 0.0;
-        if (ok) ok = await_value(a.z, __ldg(a.Ucol + e), a, 4, i, zj);
-        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), zj, s);
+        if (!wait) zj = __ldcg(a.z + j);
+        else if (ok) ok = await_value(a.z, j, a, 4, i, zj);
+        acc = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), zj, acc);
     }
-    s = warp_sum(s);
-    if (lane == 0) {
-        const double zi = (__ldcg(a.y + i) - s) / __ldg(a.LUx + __ldg(a.Udiag + i));
-        st_relaxed_f64(a.z + i, zi);
-        a.x[__ldg(a.Q + i)] = zi;
+    s = warp_sum(acc);
+    return __all_sync(kFull, ok);
+}
+
+// backward block finish: lane p < w holds e = the outside sum of row f+p
+__device__ __forceinline__ void ublock_finish(const SolveArgs &a, int f, int w, int lane, double e)
+{
+    // row f+p's first w-1-p entries are U(f+p, f+p+1 .. f+w-1)
+    const int64_t rbeg = lane < w ? __ldg(a.Urp + f + lane) - lane - 1 : 0;
+    double tu[kBR];
+#pragma unroll
+    for (int d = 0; d < kBR; d++)
+        tu[d] = (lane < d && d < w) ? __ldg(a.LUx + __ldg(a.Uslot + rbeg + d)) : 0.0;
+    const double dg = lane < w ? __ldg(a.LUx + __ldg(a.Udiag + f + lane)) : 1.0;
+    double v = lane < w ? __ldcg(a.y + f + lane) - e : 0.0, zl = 0.0;
+#pragma unroll
+    for (int d = kBR - 1; d >= 0; d--) {
+        if (d < w) {
+            const double zd = __shfl_sync(kFull, v, d) / __shfl_sync(kFull, dg, d);
+            if (lane == d) zl = zd;
+            if (lane < d) v = fma(-tu[d], zd, v);
+        }
     }
-    return !__all_sync(kFull, ok);
+    if (lane < w) {
+        st_relaxed_f64(a.z + f + lane, zl);
+        a.x[__ldg(a.Q + f + lane)] = zl;
+    }
 }
 
-// level mode: the rows of one level, one warp each
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-lsolve_level_kernel(SolveArgs a)
+// level mode, first launch of a level: every row of the level stores its
+// outside sum (its inputs are final: earlier launches)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_level_kernel(SolveArgs a)
 {
-    const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= a.nrows) return;
-    lsolve_row(a, __ldg(a.rows + w), threadIdx.x & 31);
+    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= a.nrows) return;
+    const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+    double s;
+    lrow_ext(a, i, i - __ldg(a.bs + b), lane, false, s);
+    if (lane == 0) a.ext[i] = s;
 }
 
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-usolve_level_kernel(SolveArgs a)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_level_kernel(SolveArgs a)
 {
-    const int w = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= a.nrows) return;
-    usolve_row(a, __ldg(a.rows + w), threadIdx.x & 31);
+    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= a.nrows) return;
+    const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+    const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
+    double s;
+    urow_ext(a, i, i - f, w, lane, false, s);
+    if (lane == 0) a.ext[i] = s;
 }
 
-// sync-free: a.rows[0..nrows) in a topological order, handed out by ticket
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-lsolve_syncfree_kernel(SolveArgs a)
+// level mode, second launch of a level: one warp per block (a.rows = block ids)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_finish_kernel(SolveArgs a)
+{
+    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= a.nrows) return;
+    const int b = __ldg(a.rows + t), f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
+    lblock_finish(a, f, w, lane, lane < w ? __ldcg(a.ext + f + lane) : 0.0);
+}
+
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_finish_kernel(SolveArgs a)
+{
+    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= a.nrows) return;
+    const int b = __ldg(a.rows + t), f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
+    ublock_finish(a, f, w, lane, lane < w ? __ldcg(a.ext + f + lane) : 0.0);
+}
+
+// sync-free: a.rows[0..nrows) = rows in a topological order (blocks by
+// level, the finishing row of each block last), handed out by ticket
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_syncfree_kernel(SolveArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -409,12 +497,23 @@ lsolve_syncfree_kernel(SolveArgs a)
         if (lane == 0) t = atomicAdd(&a.ctl->ticket_l, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= a.nrows) break;
-        if (lsolve_row(a, __ldg(a.rows + t), lane)) break;
+        const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+        const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
+        double s;
+        if (!lrow_ext(a, i, q, lane, true, s)) break;
+        if (q < w - 1) {
+            if (lane == 0) st_relaxed_f64(a.ext + i, s);
+            continue;
+        }
+        double e = s;   // the last row finishes the block
+        bool ok = true;
+        if (lane < w - 1) ok = await_value(a.ext, f + lane, a, 5, f + lane, e);
+        if (!__all_sync(kFull, ok)) break;
+        lblock_finish(a, f, w, lane, e);
     }
 }
 
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-usolve_syncfree_kernel(SolveArgs a)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_syncfree_kernel(SolveArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -422,7 +521,19 @@ usolve_syncfree_kernel(SolveArgs a)
         if (lane == 0) t = atomicAdd(&a.ctl->ticket_u, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= a.nrows) break;
-        if (usolve_row(a, __ldg(a.rows + t), lane)) break;
+        const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+        const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
+        double s;
+        if (!urow_ext(a, i, q, w, lane, true, s)) break;
+        if (q > 0) {
+            if (lane == 0) st_relaxed_f64(a.ext + i, s);
+            continue;
+        }
+        double e = s;   // the first row finishes the block
+        bool ok = true;
+        if (lane >= 1 && lane < w) ok = await_value(a.ext, f + lane, a, 6, f + lane, e);
+        if (!__all_sync(kFull, ok)) break;
+        ublock_finish(a, f, w, lane, e);
     }
 }
 
@@ -682,18 +793,19 @@ int launch_tail(const TailArgs &a, int grid, int epoch, void *stream)
     return (int)cudaGetLastError();
 }
 
-int launch_begin_solve(DevCtl *ctl, double *y, double *z, int n, void *stream)
+int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream)
 {
-    const int grid = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
-    begin_solve_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(ctl, y, z, n);
+    int grid = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
+    if (grid < 1) grid = 1;
+    begin_solve_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(ctl, y, z, el, eu, n);
     return (int)cudaGetLastError();
 }
 
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
+    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
     if (level_mode) {
-        const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
         lsolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     } else {
         lsolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
@@ -701,11 +813,20 @@ int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
     return (int)cudaGetLastError();
 }
 
+int launch_solve_finish(const SolveArgs &a, bool lower, void *stream)
+{
+    if (a.nrows <= 0) return 0;
+    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+    if (lower) lsolve_finish_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+    else usolve_finish_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
 int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
+    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
     if (level_mode) {
-        const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
         usolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
     } else {
         usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);

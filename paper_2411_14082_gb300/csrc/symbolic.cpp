@@ -367,36 +367,85 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             W.utstart[j - W.up0] = (int32_t)(std::lower_bound(r, r + len, lo) - r);
         }
     }
-    // ---- solve levels of the sparse blocks: L rows forward, U rows backward ----
-    auto levelize = [&](bool lower, int32_t nrows, std::vector<int32_t> &ptr, std::vector<int32_t> &rowsv,
-                        int32_t &nlev, int32_t &div) {
-        std::vector<int32_t> lv(n, 0);
+    // ---- row blocks of the sparse solves and their levels ----
+    // forward: rows i-1 and i share a block when L(:,i-1) = {i} + L(:,i)
+    // (then row f+q holds L(f+q, f..f+q-1) as its last q entries);
+    // backward: when U(i-1,:) = {i} + U(i,:) off the diagonal (then row f+q
+    // holds U(f+q, f+q+1..l-1) as its first l-1-f-q entries)
+    auto blocks = [&](int32_t nrows, bool lower, std::vector<int32_t> &bs) {
+        bs.assign(1, 0);
+        for (int32_t i = 1; i < nrows; i++) {
+            bool link;
+            if (lower) {
+                link = W.chain[i - 1] != 0;
+            } else {
+                const int64_t a0 = W.Urp[i - 1], a1 = W.Urp[i], b1 = W.Urp[i + 1];
+                link = (a1 - a0 == b1 - a1 + 1) && W.Urow_col[a0] == i &&
+                       std::equal(W.Urow_col.begin() + a0 + 1, W.Urow_col.begin() + a1, W.Urow_col.begin() + a1);
+            }
+            if (!link || i - bs.back() >= kSolveBlockRows) bs.push_back(i);
+        }
+        if (nrows > 0) bs.push_back(nrows);
+    };
+    blocks(W.lp0, true, W.lbs);
+    blocks(W.up0, false, W.ubs);
+    // levels of the blocks: forward over ascending blocks, backward over
+    // descending ones; a block waits for the blocks of its rows' entries
+    // outside it (entries in the dense part are final before)
+    auto levelize = [&](bool lower, const std::vector<int32_t> &bs, std::vector<int32_t> &ptr,
+                        std::vector<int32_t> &ids, std::vector<int32_t> &tptr, std::vector<int32_t> &tick,
+                        std::vector<int32_t> &rbk, int32_t &nlev, int32_t &div) {
+        const int32_t nb = bs.empty() ? 0 : (int32_t)bs.size() - 1;
+        const int32_t nrows = nb ? bs[nb] : 0;
+        std::vector<int32_t> blk(nrows), lv(nb, 0);
+        for (int32_t b = 0; b < nb; b++)
+            for (int32_t i = bs[b]; i < bs[b + 1]; i++) blk[i] = b;
         nlev = 0;
-        for (int32_t t = 0; t < nrows; t++) {
-            const int32_t i = lower ? t : nrows - 1 - t;
+        for (int32_t t = 0; t < nb; t++) {
+            const int32_t b = lower ? t : nb - 1 - t;
             int32_t v = 0;
-            const std::vector<int64_t> &rp = lower ? W.Lrp : W.Urp;
-            const std::vector<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
-            for (int64_t e = rp[i]; e < rp[i + 1]; e++)
-                if (cc[e] < nrows) v = std::max(v, lv[cc[e]] + 1);
-            lv[i] = v;
+            for (int32_t i = bs[b]; i < bs[b + 1]; i++) {
+                const std::vector<int64_t> &rp = lower ? W.Lrp : W.Urp;
+                const std::vector<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
+                for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+                    const int32_t j = cc[e];
+                    if (j < nrows && blk[j] != b) v = std::max(v, lv[blk[j]] + 1);
+                }
+            }
+            lv[b] = v;
             nlev = std::max(nlev, v + 1);
         }
         ptr.assign(nlev + 1, 0);
-        for (int32_t i = 0; i < nrows; i++) ptr[lv[i] + 1]++;
+        for (int32_t b = 0; b < nb; b++) ptr[lv[b] + 1]++;
         for (int32_t l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
-        rowsv.assign(nrows, 0);
+        ids.assign(nb, 0);
         std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
-        for (int32_t t = 0; t < nrows; t++) {
-            const int32_t i = lower ? t : nrows - 1 - t;
-            rowsv[pos[lv[i]]++] = i;
+        for (int32_t t = 0; t < nb; t++) {
+            const int32_t b = lower ? t : nb - 1 - t;
+            ids[pos[lv[b]]++] = b;
         }
+        tptr.assign(nlev + 1, 0);
+        tick.clear();
+        tick.reserve(nrows);
+        for (int32_t l = 0; l < nlev; l++) {
+            for (int32_t p = ptr[l]; p < ptr[l + 1]; p++) {
+                const int32_t b = ids[p];
+                if (lower)
+                    for (int32_t i = bs[b]; i < bs[b + 1]; i++) tick.push_back(i);
+                else
+                    for (int32_t i = bs[b + 1] - 1; i >= bs[b]; i--) tick.push_back(i);
+            }
+            tptr[l + 1] = (int32_t)tick.size();
+        }
+        rbk = blk;
+        // a level is run as its own launches while it has at least as many
+        // rows as the threshold
         div = nlev;
         for (int32_t l = 0; l < nlev; l++)
-            if ((double)(ptr[l + 1] - ptr[l]) < thr) { div = l; break; }
+            if ((double)(tptr[l + 1] - tptr[l]) < thr) { div = l; break; }
     };
-    levelize(true, W.lp0, W.lsv_ptr, W.lsv_rows, W.lsv_levels, W.lsv_div);
-    levelize(false, W.up0, W.usv_ptr, W.usv_rows, W.usv_levels, W.usv_div);
+    levelize(true, W.lbs, W.lsv_ptr, W.lsv_rows, W.lsv_tptr, W.lsv_tick, W.lrb, W.lsv_levels, W.lsv_div);
+    levelize(false, W.ubs, W.usv_ptr, W.usv_rows, W.usv_tptr, W.usv_tick, W.urb, W.usv_levels, W.usv_div);
 }
 
 }  // namespace gblu
