@@ -59,6 +59,38 @@ __device__ __forceinline__ int find_slot(const int32_t *rows, int lo, int hi, in
     return rows[lo] == r ? lo : -1;
 }
 
+// the slots of K rows at once, each searched in its own [lo, hi] (as
+// find_slot); the K bisections advance together so that their shared-memory
+// loads overlap.  key < 0 marks an unused entry (slot -1).
+template <int K>
+__device__ __forceinline__ void find_slots(const int32_t *rows, const int (&lo0)[K], const int (&hi0)[K],
+                                           int len, const int (&key)[K], int (&slot)[K])
+{
+    int lo[K], hi[K];
+#pragma unroll
+    for (int u = 0; u < K; u++) {
+        lo[u] = lo0[u];
+        hi[u] = min(hi0[u], len - 1);
+        if (key[u] < 0 || lo[u] > hi[u]) { lo[u] = 0; hi[u] = -1; }          // nothing to search
+        else if (rows[lo[u]] == key[u]) hi[u] = lo[u];                      // exact lower bound
+    }
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < K; u++) {
+            if (lo[u] < hi[u]) {
+                more = true;
+                const int mid = (lo[u] + hi[u]) >> 1;
+                if (rows[mid] < key[u]) lo[u] = mid + 1;
+                else hi[u] = mid;
+            }
+        }
+        if (!more) break;
+    }
+#pragma unroll
+    for (int u = 0; u < K; u++) slot[u] = (lo[u] == hi[u] && rows[lo[u]] == key[u]) ? lo[u] : -1;
+}
+
 // one column, one warp.  Dependencies are applied in runs of consecutive
 // columns of one supernode of L, as in the group kernel below (there with
 // the full description), here with runs of at most kWarpRun columns and the
@@ -232,38 +264,25 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
 // then L(:,j+d) = {j+d+1, ..., j+w-1} followed by R, the rows of L(:,j+w-1),
 // so the run updates x in two parts:
 //   triangle  - x(j+q) for q < w: the unit lower triangular solve of the
-//               run's diagonal block, by one warp (lane q holds x(j+q)), the
-//               block staged in shared memory;
+//               run's diagonal block (lane q of one warp holds x(j+q));
 //   rectangle - every row r of R: x(r) -= L(r, j+d) * x(j+d) for d = 0..w-1,
 //               one thread per row, the slot of r searched once per run.
 // Every update is one fused multiply-add applied in ascending dependency
 // order, exactly as when the dependencies are applied one at a time, so the
 // result does not depend on how the dependencies fall into runs.
 //
-// Every 32 dependencies warp 0 checks their ready flags and stages their
-// (start, length) in L and their supernode links in shared memory.
+// The warps are specialised.  While the workers (warps 1..NW-1) apply run i
+// to the rows of R whose slots lie beyond the next 32 slots, the leader
+// (warp 0) applies run i to the rows in those 32 slots (they hold every row
+// of run i+1), checks the ready flags of the next dependencies (staging 32
+// at a time in registers, waiting if needed), solves the triangle of run
+// i+1 and publishes its descriptor; one barrier per run.
 constexpr int kMaxRun = 32;
 constexpr int kTri = kMaxRun * (kMaxRun - 1) / 2;   // strictly lower triangle
 constexpr int kRows = 4;                            // rows of R per thread per pass
 
 // offset of column d of the staged triangle (column d holds kMaxRun-1-d rows)
 __device__ __forceinline__ int tri_off(int d) { return d * (kMaxRun - 1) - d * (d - 1) / 2; }
-
-__device__ __forceinline__ bool spin_until(const int32_t *flag, int epoch, const RefactorArgs &a, int k)
-{
-    long long it = 0;
-    while (ld_acquire(flag) != epoch) {
-        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return false;
-        if (++it > a.spin_limit) {
-            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
-            a.ctl->where = 1;
-            a.ctl->where_k = k;
-            return false;
-        }
-        if (it > 64) __nanosleep(64);
-    }
-    return true;
-}
 
 // group barrier: the whole CTA (NW == 8) or one half (named barrier 1 + g)
 template <int NW>
@@ -273,28 +292,27 @@ __device__ __forceinline__ void group_sync(int g)
     else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(NW * 32) : "memory");
 }
 
+// a run as published by the leader
+struct RunDesc {
+    long long base[kMaxRun];   // value of R entry r for dependency d: LUx[base[d] + r]
+    long long lbl;             // start of R's rows in LUi
+    int t, w, jl, nR, done;
+};
+
 // shared state of one group (declared once per CTA, for up to two groups)
 struct GroupShared {
-    long long lb[32];    // staged dependencies: start of L(:,j) in LUx
-    int nl[32];          // and its length
+    RunDesc run[2];            // double buffered by run parity
     double red[kWarps];
-    double tri[kTri];    // the run's triangle, column d at tri_off(d)
-    int ready, stop;
-    unsigned cont;
+    double tri[kTri];          // the leader's staged triangle, column d at tri_off(d)
+    int stop;
 };
 
 template <bool kWait, int NW>
 __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap,
                         GroupShared &sh)
 {
-    int &s_ready = sh.ready;
-    int &s_stop = sh.stop;
-    unsigned &s_cont = sh.cont;
-    long long *s_lb = sh.lb;
-    int *s_nl = sh.nl;
-    double *s_red = sh.red;
-    double *s_tri = sh.tri;
-    constexpr int kT = NW * 32;
+    static_assert(NW >= 2, "a group needs a leader and workers");
+    constexpr int kT = NW * 32, kTw = (NW - 1) * 32;
     const int tid = threadIdx.x - g * kT, lane = tid & 31, warp = tid >> 5;
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
@@ -307,7 +325,11 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
         if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
         x[i] = 0.0;
     }
-    if (tid == 0) { s_ready = 0; s_stop = 0; }
+    if (tid == 0) {
+        sh.stop = 0;
+        sh.run[0].done = 0;
+        sh.run[1].done = 0;
+    }
     group_sync<NW>(g);
     {
         const int c = __ldg(a.Q + k);
@@ -316,112 +338,192 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     }
     group_sync<NW>(g);
 
+    // ---- leader state: the staged window of dependencies [mbase, mbase+32),
+    // lane q holding dependency mbase+q; [mbase, ready) are ready
     int ready = 0, mbase = 0;
+    long long m_lb = 0;
+    int m_nl = 0;
     unsigned cont = 0;   // bit q: dependency mbase+q continues the run of mbase+q-1
-    for (int t = 0; t < nD;) {
-        if (t >= ready) {
-            if (warp == 0) {
+
+    // leader: find the run starting at dependency t (waiting for it to be
+    // ready), solve its triangle and publish it as run[p]; false = stop
+    auto lead_next = [&](int t, int p) -> bool {
+        int w = 1;
+        for (;;) {
+            if (t >= ready) {
                 const int tt = t + lane;
                 const int jj = tt < nD ? rows[tt] : -1;
                 bool ok = true;
                 int ch = 0;
                 if (jj >= 0) {
                     // structure first: an acquire load holds back the loads after it
-                    const long long lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
-                    const int nlj = (int)(__ldg(a.LUp + jj + 1) - lb);
+                    m_lb = __ldg(a.LUp + jj) + __ldg(a.nU + jj);
+                    m_nl = (int)(__ldg(a.LUp + jj + 1) - m_lb);
                     ch = __ldg(a.chain + jj);
                     if (kWait) ok = ld_acquire(a.finish + jj) == epoch;
-                    s_lb[lane] = lb;
-                    s_nl[lane] = nlj;
                 }
                 const int jp = __shfl_up_sync(kFull, jj, 1);
                 const int cp = __shfl_up_sync(kFull, ch, 1);
-                const unsigned cm = __ballot_sync(kFull, lane > 0 && jj >= 0 && jj == jp + 1 && cp != 0);
+                cont = __ballot_sync(kFull, lane > 0 && jj >= 0 && jj == jp + 1 && cp != 0);
                 const unsigned m = __ballot_sync(kFull, ok);
-                const int run = (m == kFull) ? 32 : __ffs(~m) - 1;
-                if (kWait && run == 0 && lane == 0 && !spin_until(a.finish + rows[t], epoch, a, k)) s_stop = 1;
-                if (lane == 0) {
-                    s_ready = t + (run > 0 ? run : 1);
-                    s_cont = cm;
+                int run = (m == kFull) ? 32 : __ffs(~m) - 1;
+                if (kWait && run == 0) {
+                    long long it = 0;
+                    while (ld_acquire(a.finish + rows[t]) != epoch) {
+                        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return false;
+                        if (++it > a.spin_limit) {
+                            if (lane == 0) {
+                                set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                                a.ctl->where = 1;
+                                a.ctl->where_k = k;
+                            }
+                            return false;
+                        }
+                        if (it > 64) __nanosleep(64);
+                    }
+                    run = 1;
                 }
+                ready = t + run;
+                mbase = t;
             }
-            group_sync<NW>(g);
-            if (s_stop) return true;
-            ready = s_ready;
-            cont = s_cont;
-            mbase = t;
+            const int q0 = t - mbase;
+            w = 1;
+            while (t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
+            if (t > mbase && t + w == mbase + 32 && t + w < nD) {
+                ready = t;   // the run reaches the end of the staged window: stage from its start
+                continue;
+            }
+            break;
         }
         const int q0 = t - mbase;
-        int w = 1;
-        while (t + w < ready && ((cont >> (q0 + w)) & 1u)) ++w;
-        if (t > mbase && t + w == mbase + 32 && t + w < nD) {
-            ready = t;   // the run reaches the end of the staged window: stage from its start
-            continue;
-        }
-        if (w > 1) {   // triangle of the run
-            for (int d = warp; d < w - 1; d += NW)
-                if (lane < w - 1 - d) s_tri[tri_off(d) + lane] = __ldcg(a.LUx + s_lb[q0 + d] + lane);
-            group_sync<NW>(g);
-            if (warp == 0) {
-                double v = lane < w ? x[t + lane] : 0.0;
-                for (int d = 0; d < w - 1; ++d) {
-                    const double m = __shfl_sync(kFull, v, d);
-                    if (lane > d && lane < w) v = fma(-s_tri[tri_off(d) + lane - d - 1], m, v);
+        const long long lbq = __shfl_sync(kFull, m_lb, (q0 + lane) & 31);   // lane d: dependency t+d
+        if (w > 1) {   // triangle: column d of the run gives its first w-1-d L entries
+            for (int d0 = 0; d0 < w - 1; d0 += 8) {   // eight loads in flight
+                double tv[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const long long lbd = __shfl_sync(kFull, lbq, (d0 + u) & 31);
+                    tv[u] = (d0 + u < w - 1 && lane < w - 1 - (d0 + u)) ? __ldcg(a.LUx + lbd + lane) : 0.0;
                 }
-                if (lane < w) x[t + lane] = v;
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (d0 + u < w - 1 && lane < w - 1 - (d0 + u)) sh.tri[tri_off(d0 + u) + lane] = tv[u];
             }
-            group_sync<NW>(g);
+            __syncwarp();
+            double v = lane < w ? x[t + lane] : 0.0;
+            for (int d = 0; d < w - 1; ++d) {
+                const double mv = __shfl_sync(kFull, v, d);
+                if (lane > d && lane < w) v = fma(-sh.tri[tri_off(d) + lane - d - 1], mv, v);
+            }
+            if (lane < w) x[t + lane] = v;
         }
-        {   // rectangle: rows of R = L(:, j+w-1), multipliers x(t .. t+w-1)
-            const int tl = t + w - 1;
-            const int jl = rows[tl];
-            const long long lbl = s_lb[q0 + w - 1];
-            const int nR = s_nl[q0 + w - 1];
-            bool bad = false;
-            for (int r0 = 0; r0 < nR; r0 += kRows * kT) {
-                int sl[kRows];
+        RunDesc &r = sh.run[p];
+        if (lane < w) r.base[lane] = lbq + (w - 1 - lane);
+        const long long lbl = __shfl_sync(kFull, lbq, w - 1);
+        const int nRl = __shfl_sync(kFull, m_nl, (q0 + w - 1) & 31);
+        if (lane == 0) {
+            r.t = t;
+            r.w = w;
+            r.jl = rows[t + w - 1];
+            r.lbl = lbl;
+            r.nR = nRl;
+            r.done = 0;
+        }
+        return true;
+    };
+
+    if (warp == 0) {
+        if (nD == 0) {
+            if (lane == 0) sh.run[0].done = 1;
+        } else if (!lead_next(0, 0) && lane == 0) {
+            sh.stop = 1;
+        }
+    }
+    group_sync<NW>(g);
+
+    for (int i = 0;; ++i) {
+        if (sh.stop == 2) {  // inconsistent pattern: never index with it
+            if (tid == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
+            return true;
+        }
+        if (sh.stop) return true;
+        const RunDesc &r = sh.run[i & 1];
+        if (r.done) break;
+        const int t = r.t, w = r.w, nR = r.nR, jl = r.jl;
+        const long long lbl = r.lbl;
+        const int tl = t + w - 1, hend = t + w + kMaxRun;   // the leader's slots: [t+w, hend)
+        bool bad = false;
+        if (warp == 0) {
+            if (lane < nR) {   // only the first 32 entries of R can fall in the leader's slots
+                const int row = __ldg(a.LUi + lbl + lane);
+                const int sl = find_slot(rows, tl + 1 + lane, tl + (row - jl), len, row);
+                if (sl < 0) {
+                    bad = true;
+                } else if (sl < hend) {
+                    double v = x[sl];
+                    for (int d0 = 0; d0 < w; d0 += 8) {   // eight loads in flight
+                        double lv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            lv[u] = d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : 0.0;
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            if (d0 + u < w) v = fma(-x[t + d0 + u], lv[u], v);
+                    }
+                    x[sl] = v;
+                }
+            }
+            __syncwarp();
+            const int tn = t + w;
+            if (tn >= nD) {
+                if (lane == 0) sh.run[(i + 1) & 1].done = 1;
+            } else if (!lead_next(tn, (i + 1) & 1) && lane == 0) {
+                sh.stop = 1;
+            }
+        } else {
+            const int wt = tid - 32;
+            for (int r0 = 0; r0 < nR; r0 += kRows * kTw) {
+                int sl[kRows], key[kRows], lo[kRows], hi[kRows];
                 double v[kRows];
 #pragma unroll
                 for (int u = 0; u < kRows; u++) {
-                    const int r = r0 + u * kT + tid;
-                    sl[u] = -1;
-                    if (r < nR) {
-                        const int row = __ldg(a.LUi + lbl + r);
-                        sl[u] = find_slot(rows, tl + 1 + r, tl + (row - jl), len, row);
-                        if (sl[u] < 0) bad = true;
-                    }
+                    const int rr = r0 + u * kTw + wt;
+                    key[u] = rr < nR ? __ldg(a.LUi + lbl + rr) : -1;
+                    lo[u] = tl + 1 + rr;
+                    hi[u] = tl + (key[u] - jl);
+                }
+                find_slots<kRows>(rows, lo, hi, len, key, sl);
+#pragma unroll
+                for (int u = 0; u < kRows; u++) {
+                    if (key[u] >= 0 && sl[u] < 0) bad = true;
+                    if (sl[u] >= 0 && sl[u] < hend) sl[u] = -1;   // the leader's
                     v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
                 }
 #pragma unroll 4
                 for (int d = 0; d < w; d++) {
                     const double m = x[t + d];
-                    const double *lv = a.LUx + s_lb[q0 + d] + (w - 1 - d) + r0 + tid;
+                    const double *lv = a.LUx + r.base[d] + r0 + wt;
 #pragma unroll
                     for (int u = 0; u < kRows; u++)
-                        if (sl[u] >= 0) v[u] = fma(-m, __ldcg(lv + u * kT), v[u]);
+                        if (sl[u] >= 0) v[u] = fma(-m, __ldcg(lv + u * kTw), v[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < kRows; u++)
                     if (sl[u] >= 0) x[sl[u]] = v[u];
             }
-            if (bad) s_stop = 2;
         }
+        if (bad) sh.stop = 2;
         group_sync<NW>(g);
-        if (s_stop) {  // inconsistent pattern: never index with it
-            if (tid == 0) set_status(a.ctl, GBLU_ERR_INTERNAL);
-            return true;
-        }
-        t += w;
     }
 
     const double d = x[nU - 1];
     double m = 0.0;
     for (int i = nU + tid; i < len; i += kT) m = fmax(m, fabs(x[i]));
     m = warp_max(m);
-    if (lane == 0) s_red[warp] = m;
+    if (lane == 0) sh.red[warp] = m;
     group_sync<NW>(g);
-    m = s_red[0];
-    for (int w = 1; w < NW; w++) m = fmax(m, s_red[w]);
+    m = sh.red[0];
+    for (int w = 1; w < NW; w++) m = fmax(m, sh.red[w]);
     if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
         if (tid == 0) {
             atomicExch(&a.ctl->interrupted, 1);
