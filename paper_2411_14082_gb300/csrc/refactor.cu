@@ -197,17 +197,19 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             const int nR = __shfl_sync(kFull, m_nl, q0 + w - 1);
             bool bad = false;
             for (int r0 = 0; r0 < nR; r0 += 32 * kBatch) {
-                int sl[kBatch];
+                int sl[kBatch], key[kBatch], lo[kBatch], hi[kBatch];
                 double v[kBatch];
 #pragma unroll
                 for (int u = 0; u < kBatch; u++) {
                     const int r = r0 + u * 32 + lane;
-                    sl[u] = -1;
-                    if (r < nR) {
-                        const int row = __ldg(a.LUi + lbl + r);
-                        sl[u] = find_slot(rows, tl + 1 + r, tl + (row - jl), len, row);
-                        if (sl[u] < 0) bad = true;
-                    }
+                    key[u] = r < nR ? __ldg(a.LUi + lbl + r) : -1;
+                    lo[u] = tl + 1 + r;
+                    hi[u] = tl + (key[u] - jl);
+                }
+                find_slots<kBatch>(rows, lo, hi, len, key, sl);
+#pragma unroll
+                for (int u = 0; u < kBatch; u++) {
+                    if (key[u] >= 0 && sl[u] < 0) bad = true;
                     v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
                 }
                 for (int d = 0; d < w; d++) {
