@@ -50,7 +50,7 @@ extern "C" {
 #define GBLU_ERR_NOT_FACTORIZED (-7) /* refactorize/solve before a factorization    */
 #define GBLU_ERR_INTERNAL (-8)       /* a structural invariant check failed         */
 
-/* Scheduling of the re-factorization (Section III-B dual-mode scheduling). */
+/* Scheduling of the re-factorization (Section IV-B: cluster and pipeline modes). */
 #define GBLU_SCHED_AUTO 0     /* level-synchronous front, sync-free tail      */
 #define GBLU_SCHED_LEVEL 1    /* every level a separate launch (cluster mode) */
 #define GBLU_SCHED_SYNCFREE 2 /* one launch, ready flags (pipeline mode)      */

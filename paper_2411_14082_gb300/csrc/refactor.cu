@@ -19,7 +19,7 @@
 // inside L(:,j)); the interval is exact inside dense runs, so dense parts
 // need no search steps.  L(:,k) is stored as x * (1 / x(k)).
 //
-// Two schedules (Section III-B): cluster mode = one launch per level with no
+// Two schedules (Section IV-B): cluster mode = one launch per level with no
 // waits; pipeline mode = one persistent launch whose CTAs take tasks by an
 // atomic ticket and wait on per-column ready flags (epochs) before using a
 // dependency.  A failing pivot sets `interrupted` (Algorithm 3 line 9 /

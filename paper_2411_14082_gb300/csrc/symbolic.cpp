@@ -180,7 +180,7 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     Schedule &W)
 {
     const int32_t n = S.n;
-    // ---- EGraph levels and the dividing level (Section III-B) ----
+    // ---- EGraph levels and the dividing level (Section IV-B) ----
     std::vector<int32_t> level;
     W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level);
     W.level_ptr.assign(W.n_levels + 1, 0);
