@@ -79,7 +79,20 @@ typedef struct {
     long long solve_dense_min;
     int solve_slices;
     double solve_dense_density;
+    /* dense tail of the re-factorization: when the last m columns of the
+       factor form a structurally dense block (every column k >= n-m holds
+       every row >= n-m) and m >= dense_min_rows, the re-factorization applies
+       the sparse dependencies of those columns in the column kernels and
+       then factors the block as a dense matrix (blocked right-looking, the
+       same pivot check per column, no row interchanges); at most
+       GBLU_DENSE_MAX_ROWS rows are taken.  0 disables it (the default: on
+       the 200x200x4 mesh its one-SM panels cost more than the column
+       kernels do on the same block).                                        */
+    int dense_min_rows;
 } gblu_opts;
+
+/* largest dense tail block of the re-factorization (shared-memory panel) */
+#define GBLU_DENSE_MAX_ROWS 3456
 
 /* Fill *o with the defaults above. */
 void gblu_default_opts(gblu_opts *o);
@@ -214,6 +227,7 @@ typedef struct {
     int32_t last_first_bad; /* first failing column of the last check, -1    */
     int64_t device_bytes; /* device memory held by the handle                */
     int64_t kernel_launches; /* kernels this handle has launched so far      */
+    int32_t dense_rows;   /* rows of the dense tail block (0: none)          */
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

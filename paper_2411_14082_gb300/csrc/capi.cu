@@ -102,6 +102,9 @@ struct gblu_ctx {
         ltcnt, utstart;
     DBuf<int64_t> lsplit, usplit;
     DBuf<double> y, z, ext_l, ext_u, partial, stage_ax, stage_b, stage_x;
+    // dense tail of the re-factorization: the block and its column offsets
+    DBuf<double> dense;
+    DBuf<int32_t> dense_s0;
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
@@ -194,7 +197,8 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     sp.min_entries = h->opts.solve_dense_min;
     sp.slices = h->opts.solve_slices;
     sp.max_piece = kMaxPieceRows;
-    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, sp, h->W);
+    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, sp,
+                   h->opts.dense_min_rows, h->W);
     for (int32_t v : h->W.amap)
         if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
     const int32_t n = h->S.n;
@@ -203,6 +207,8 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->LUi, h->S.LUi, st));
     CK(upload(h, h->nU, h->S.nU, st));
     CK(upload(h, h->chain, h->W.chain, st));
+    CK(upload(h, h->dense_s0, h->W.dense_s0, st));
+    if (h->W.dense_m > 0) CK(ensure(h, h->dense, (size_t)h->W.dense_m * h->W.dense_m));
     CK(upload(h, h->piv, h->S.piv, st));
     CK(upload(h, h->pinv, h->S.pinv, st));
     CK(upload(h, h->task_ptr, h->W.task_ptr, st));
@@ -265,6 +271,10 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     a.LUi = h->LUi.p;
     a.nU = h->nU.p;
     a.chain = h->chain.p;
+    a.dense_p = h->W.dense_m > 0 ? h->W.dense_p : INT_MAX;   // INT_MAX: no dense tail
+    a.dense_s0 = h->dense_s0.p;
+    a.S = h->dense.p;
+    a.dense_ld = h->W.dense_m;
     a.LUx = h->vals.p;
     a.finish = h->finish.p;
     a.task_ptr = h->task_ptr.p;
@@ -286,6 +296,24 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
         a.task_begin = ltp[div];
         a.ntasks = ntask - ltp[div];
         KL(launch_refactor_tasks(a, true, h->ref_grid, h->epoch, st));
+    }
+    if (h->W.dense_m > 0) {   // the dense tail: blocked LU of the block, then scatter
+        DenseArgs2 d{};
+        d.S = h->dense.p;
+        d.ld = h->W.dense_m;
+        d.m = h->W.dense_m;
+        d.p = h->W.dense_p;
+        d.eps = h->opts.pivot_tol;
+        d.ctl = h->ctl;
+        d.LUp = h->LUp.p;
+        d.s0 = h->dense_s0.p;
+        d.LUx = h->vals.p;
+        d.finish = h->finish.p;
+        d.epoch = h->epoch;
+        long long nl = 0;
+        const int e = launch_dense_lu(d, st, &nl);
+        h->launches += nl;
+        if (e != 0) return fail(GBLU_ERR_CUDA, "dense tail launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
     (void)n;
     CK(read_ctl(h, st));
@@ -502,6 +530,7 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_dense_min = 300000;
     o->solve_slices = 8;
     o->solve_dense_density = 0.5;
+    o->dense_min_rows = 0;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -518,7 +547,8 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
         h->opts.sched_mode < 0 || h->opts.sched_mode > 2 || h->opts.solve_mode < 0 ||
         h->opts.solve_mode > 2 || !(h->opts.alpha >= 0.0) || !(h->opts.solve_dense_frac >= 0.0) ||
         h->opts.solve_dense_frac > 1.0 || h->opts.solve_slices < 0 ||
-        !(h->opts.solve_dense_density >= 0.0) || h->opts.solve_dense_density > 1.0) {
+        !(h->opts.solve_dense_density >= 0.0) || h->opts.solve_dense_density > 1.0 ||
+        h->opts.dense_min_rows < 0) {
         delete h;
         return fail(GBLU_ERR_INVALID_INPUT, "invalid options");
     }
@@ -536,6 +566,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
     if (e == cudaSuccess && r == 0) r = dense_piece_setup(kMaxPieceRows);
+    if (e == cudaSuccess && r == 0) r = dense_setup(GBLU_DENSE_MAX_ROWS);
     if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
         const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
         if (h->hctl) cudaFreeHost(h->hctl);
@@ -565,7 +596,7 @@ void gblu_destroy(gblu_handle h)
         release(h, h->Ucol); release(h, h->Uslot); release(h, h->Udiag);
         release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->lbs); release(h, h->ubs);
         release(h, h->lrb); release(h, h->urb); release(h, h->lsv_tick); release(h, h->usv_tick);
-        release(h, h->ext_l); release(h, h->ext_u);
+        release(h, h->ext_l); release(h, h->ext_u); release(h, h->dense); release(h, h->dense_s0);
         release(h, h->ltcnt);
         release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
         release(h, h->y); release(h, h->z); release(h, h->partial);
@@ -826,6 +857,7 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->last_first_bad = h->last_first_bad;
     s->device_bytes = (int64_t)h->device_bytes;
     s->kernel_launches = h->launches;
+    s->dense_rows = h->W.dense_m;
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

@@ -79,6 +79,11 @@ struct Schedule {
     // (columns after the row's slice), the triangular piece of column j is
     // its U entries from utstart[j - p0] to the diagonal.
     int32_t lp0 = 0, up0 = 0;
+    // dense tail of the re-factorization: columns [dense_p, n) form a
+    // structurally dense block of dense_m = n - dense_p rows (0: none);
+    // dense_s0[c] = slot of row dense_p inside column dense_p + c
+    int32_t dense_p = 0, dense_m = 0;
+    std::vector<int32_t> dense_s0;
     std::vector<int32_t> lcut, ucut;
     std::vector<int64_t> lsplit, usplit;
     std::vector<int32_t> ltcnt, utstart;
@@ -104,9 +109,11 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
 int64_t symmetric_fill(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
-                    Schedule &W);
+                    int dense_min_rows, Schedule &W);
+// levels of the column dependency graph; with cut < n, the dependencies of
+// columns k >= cut on columns >= cut are left out
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
-                  const int32_t *nU_or_null, std::vector<int32_t> &level);
+                  const int32_t *nU, std::vector<int32_t> &level, int32_t cut = INT32_MAX);
 
 // ---------------------------------------------------------------- device side
 // Control block in device memory (one per handle).
@@ -135,6 +142,12 @@ struct RefactorArgs {
     const int64_t *LUp;
     const int32_t *LUi, *nU;
     const uint8_t *chain;           // supernode links of L (Schedule::chain)
+    // dense tail: columns k >= dense_p apply only their dependencies < dense_p
+    // and leave rows >= dense_p in column k - dense_p of S (leading dim dense_ld)
+    int32_t dense_p;
+    const int32_t *dense_s0;
+    double *S;
+    int64_t dense_ld;
     double *LUx;
     int32_t *finish;
     const int32_t *task_ptr, *task_cols;
@@ -196,6 +209,23 @@ int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
+// dense tail of the re-factorization (dense.cu)
+struct DenseArgs2 {
+    double *S;                      // m x m, column-major, leading dimension ld
+    int64_t ld;
+    int32_t m, p;                   // block rows, first column of the block
+    double eps;
+    DevCtl *ctl;
+    const int64_t *LUp;
+    const int32_t *s0;              // slot of row p inside column p + c
+    double *LUx;
+    int32_t *finish;
+    int epoch;
+};
+constexpr int kDenseNb = 8;         // panel width
+int dense_setup(int max_rows);
+int launch_dense_lu(const DenseArgs2 &d, void *stream, long long *launches);
+
 int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream);
 int launch_solve_finish(const SolveArgs &a, bool lower, void *stream);
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream);

@@ -100,14 +100,17 @@ __device__ __forceinline__ void find_slots(const int32_t *rows, const int (&lo0)
 // shuffles.
 constexpr int kWarpRun = 8;
 
-template <bool kWait>
+template <bool kWait, bool kDense>
 __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int lane,
                          int epoch)
 {
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
     const int nU = __ldg(a.nU + k);
-    const int nD = nU - 1;
+    // with a dense tail, a column of the block applies only its dependencies
+    // before the block (its first dense_s0 rows); the block does the rest
+    const bool dcol = kDense && k >= a.dense_p;
+    const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
     const bool in_smem = len <= a.cap_short;
     double *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : a.LUi + beg;
@@ -233,6 +236,13 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
         t += w;
     }
 
+    if (dcol) {   // U above the block is final; rows >= dense_p go to the block
+        double *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
+        if (in_smem)
+            for (int i = lane; i < nD; i += 32) a.LUx[beg + i] = xs[i];
+        for (int i = nD + lane; i < len; i += 32) Sc[i - nD] = x[i];
+        return false;
+    }
     const double d = x[nU - 1];
     double m = 0.0;
     for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
@@ -309,7 +319,7 @@ struct GroupShared {
     int stop;
 };
 
-template <bool kWait, int NW>
+template <bool kWait, bool kDense, int NW>
 __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap,
                         GroupShared &sh)
 {
@@ -319,7 +329,10 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
     const int nU = __ldg(a.nU + k);
-    const int nD = nU - 1;
+    // with a dense tail, a column of the block applies only its dependencies
+    // before the block (its first dense_s0 rows); the block does the rest
+    const bool dcol = kDense && k >= a.dense_p;
+    const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
     const bool in_smem = len <= cap;
     double *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : a.LUi + beg;
@@ -518,6 +531,13 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
         group_sync<NW>(g);
     }
 
+    if (dcol) {   // U above the block is final; rows >= dense_p go to the block
+        double *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
+        if (in_smem)
+            for (int i = tid; i < nD; i += kT) a.LUx[beg + i] = xs[i];
+        for (int i = nD + tid; i < len; i += kT) Sc[i - nD] = x[i];
+        return false;
+    }
     const double d = x[nU - 1];
     double m = 0.0;
     for (int i = nU + tid; i < len; i += kT) m = fmax(m, fabs(x[i]));
@@ -557,7 +577,7 @@ __global__ void begin_refactor_kernel(DevCtl *ctl)
 
 // Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
 // (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
-template <bool kWait>
+template <bool kWait, bool kDense>
 __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs a, int epoch, int persistent)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -581,17 +601,17 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
         const int k0 = __ldg(a.task_cols + c0);
         const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
         if (c1 - c0 == 1 && len0 > a.cap_short) {          // one long column: whole CTA
-            stop = col_grp<kWait, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
+            stop = col_grp<kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
         } else if (c1 - c0 == 2 && len0 > a.cap_short) {   // two medium columns: a half each
             const int g = warp / (kWarps / 2);
             const int half = a.cap_long / 2;
-            const bool hs = col_grp<kWait, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
+            const bool hs = col_grp<kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
                                                        rs + (size_t)g * half, epoch, g, half, s_grp[g]);
             stop = __syncthreads_or(hs);
         } else {
             bool ws = false;
             if (c0 + warp < c1)
-                ws = col_warp<kWait>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
+                ws = col_warp<kWait, kDense>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
                                      rs + (size_t)warp * a.cap_short, lane, epoch);
             stop = __syncthreads_or(ws);
         }
@@ -615,23 +635,37 @@ int launch_begin_refactor(DevCtl *ctl, void *stream)
 int refactor_setup(int cap_long, int *blocks_per_sm)
 {
     const size_t sm = (size_t)cap_long * (sizeof(double) + sizeof(int32_t));
-    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<true>,
+    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<false>,
+        e = cudaFuncSetAttribute(refactor_task_kernel<false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_task_kernel<true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_task_kernel<false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, refactor_task_kernel<true>,
-                                                              kThreads, sm);
+    int b1 = 0, b2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<true, false>, kThreads, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<true, true>, kThreads, sm);
+    *blocks_per_sm = b1 < b2 ? b1 : b2;
+    return (int)e;
 }
 
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream)
 {
     if (a.ntasks <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dense = a.dense_p < INT_MAX;   // a dense tail is in use
     if (pipeline) {
-        refactor_task_kernel<true><<<grid, kThreads, task_smem(a), (cudaStream_t)stream>>>(a, epoch, 1);
+        if (dense) refactor_task_kernel<true, true><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        else refactor_task_kernel<true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
     } else {
-        refactor_task_kernel<false><<<a.ntasks, kThreads, task_smem(a), (cudaStream_t)stream>>>(a, epoch, 0);
+        if (dense) refactor_task_kernel<false, true><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        else refactor_task_kernel<false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
     }
     return (int)cudaGetLastError();
 }

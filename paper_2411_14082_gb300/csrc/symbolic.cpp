@@ -56,7 +56,7 @@ void column_etree(const Pattern &P, std::vector<int32_t> &parent)
 // Levels of a dependency DAG given column-wise: dependencies of column k are
 // the rows j < k of its U part.  Returns the number of levels.
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
-                  const int32_t *nU, std::vector<int32_t> &level)
+                  const int32_t *nU, std::vector<int32_t> &level, int32_t cut)
 {
     level.assign(n, 0);
     int32_t nl = 0;
@@ -65,6 +65,7 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
         const int64_t end = nU ? Up[k] + nU[k] : Up[k + 1];
         for (int64_t e = Up[k]; e < end; e++) {
             const int32_t j = Ui[e];
+            if (k >= cut && j >= cut) continue;
             if (j < k && level[j] + 1 > lv) lv = level[j] + 1;
         }
         level[k] = lv;
@@ -177,12 +178,47 @@ static int32_t dense_split(int32_t n, const std::vector<int64_t> &count_from, co
 
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
-                    Schedule &W)
+                    int dense_min_rows, Schedule &W)
 {
     const int32_t n = S.n;
-    // ---- EGraph levels and the dividing level (Section IV-B) ----
+    // ---- dense tail: the longest trailing block [p, n) in which every
+    // column holds every row >= p (low[k] = first row of the unbroken run of
+    // rows that ends at n-1 in column k) ----
+    W.dense_p = n;
+    W.dense_m = 0;
+    W.dense_s0.clear();
+    if (dense_min_rows > 0 && n > 0) {
+        int32_t pd = n, mx = 0;
+        for (int32_t p = n - 1; p >= 0; p--) {
+            const int64_t b = S.LUp[p], e = S.LUp[p + 1];
+            int32_t low = n;
+            if (e > b && S.LUi[e - 1] == n - 1) {
+                int64_t q = e - 1;
+                while (q > b && S.LUi[q - 1] == S.LUi[q] - 1) q--;
+                low = S.LUi[q];
+            }
+            mx = std::max(mx, low);
+            if (mx > p) break;
+            pd = p;
+        }
+        int32_t m = n - pd;
+        if (m > GBLU_DENSE_MAX_ROWS) { m = GBLU_DENSE_MAX_ROWS; pd = n - m; }
+        if (m >= dense_min_rows) {
+            W.dense_p = pd;
+            W.dense_m = m;
+            W.dense_s0.resize(m);
+            for (int32_t c = 0; c < m; c++) {
+                const int32_t k = pd + c;
+                const int32_t *r = S.LUi.data() + S.LUp[k];
+                const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
+                W.dense_s0[c] = (int32_t)(std::lower_bound(r, r + len, pd) - r);
+            }
+        }
+    }
+    // ---- EGraph levels and the dividing level (Section IV-B); columns of
+    // the dense tail wait only for their dependencies before it ----
     std::vector<int32_t> level;
-    W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level);
+    W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
     W.level_ptr.assign(W.n_levels + 1, 0);
     for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
     for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];

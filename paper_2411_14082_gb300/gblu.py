@@ -53,7 +53,7 @@ class Opts(ctypes.Structure):
                 ("solve_mode", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("spin_limit", ctypes.c_longlong), ("solve_dense_frac", ctypes.c_double),
                 ("solve_dense_min", ctypes.c_longlong), ("solve_slices", ctypes.c_int),
-                ("solve_dense_density", ctypes.c_double)]
+                ("solve_dense_density", ctypes.c_double), ("dense_min_rows", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("etree_height", ctypes.c_int32), ("n_refactor", ctypes.c_int64),
                 ("n_repivot", ctypes.c_int64), ("n_restart_cols", ctypes.c_int64),
                 ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -156,7 +156,7 @@ class Solver:
 
     def __init__(self, device=0, pivot_tol=1e-3, sched_mode="auto", solve_mode="auto",
                  alpha=2.0, spin_limit=1 << 24, solve_dense_frac=None, solve_dense_min=None,
-                 solve_slices=None, solve_dense_density=None):
+                 solve_slices=None, solve_dense_density=None, dense_min_rows=None):
         lib = load()
         o = Opts()
         lib.gblu_default_opts(ctypes.byref(o))
@@ -173,6 +173,8 @@ class Solver:
             o.solve_slices = solve_slices
         if solve_dense_density is not None:
             o.solve_dense_density = solve_dense_density
+        if dense_min_rows is not None:
+            o.dense_min_rows = dense_min_rows
         h = ctypes.c_void_p()
         _check(lib.gblu_create(ctypes.byref(h), int(device), ctypes.byref(o)))
         self._h = h

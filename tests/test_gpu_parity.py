@@ -295,6 +295,54 @@ def test_every_column_task_kind(sched):
     compare_factors(s.export_factors(), lu3, RTOL)
 
 
+def test_dense_tail_block():
+    """The trailing dense block factored as a dense matrix (dense tail) agrees
+    with the oracle and with the column kernels alone, and a pivot that fails
+    inside the block restarts exactly like one that fails in a sparse column."""
+    ckt = mesh_small(seed=13)
+    n, Ap, Ai, Ax = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(23)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    sd = gblu.Solver(DEV, dense_min_rows=128)
+    sc = gblu.Solver(DEV, dense_min_rows=0)
+    for s in (sd, sc):
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(dev(Ax))
+    assert sd.stats()["dense_rows"] >= 128 and sc.stats()["dense_rows"] == 0
+    m = sd.stats()["dense_rows"]
+    for it in range(3):
+        Ax = inputs.redraw_transistors(ckt, rng).values()
+        Axd = dev(Ax)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        for s in (sd, sc):
+            rc, rep = s.refactorize(Axd)
+            assert rep == (lu.n_rejected > 0)
+            compare_factors(s.export_factors(), lu, RTOL)
+            solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    # force the check to fail at a column inside the block
+    k = n - m + m // 3
+    c = Q[k]
+    rows = Ai[Ap[c]:Ap[c + 1]]
+    hit = np.nonzero(rows == lu.piv[k])[0]
+    assert len(hit)
+    Ax2 = Ax.copy()
+    Ax2[Ap[c] + hit[0]] -= lu.Ux[lu.Up[k + 1] - 1] * (1.0 - 1e-9)
+    lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+    assert lu2.n_rejected > 0
+    Axd2 = dev(Ax2)
+    rc, rep = sd.refactorize(Axd2)
+    assert rc == gblu.REPIVOTED and rep
+    assert n - m <= sd.stats()["last_first_bad"] <= k
+    compare_factors(sd.export_factors(), lu2, RTOL)
+    solve_and_check(sd, n, Ap, Ai, Ax2, Axd2, rng)
+    # and back to a normal step on the repacked structure
+    lu3 = O.refactorize(lu2, Ap, Ai, Ax)
+    rc, rep = sd.refactorize(dev(Ax))
+    assert rep == (lu3.n_rejected > 0)
+    compare_factors(sd.export_factors(), lu3, RTOL)
+
+
 def test_edge_cases():
     # n = 1
     s = gblu.Solver(DEV)
