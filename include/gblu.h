@@ -156,6 +156,42 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream,
 int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream);
 
 /*
+ * Batch of value sets on the installed structure (many same-pattern systems,
+ * e.g. the Newton iterations of independent simulations of one circuit): the
+ * checked re-factorization of Algorithms 3 and 4 for every set, in one
+ * persistent launch that reads the structure once.  The paper works on one
+ * matrix at a time; batching is this library's extension.
+ *   Ax_dev   device float64, set s at Ax_dev + s*ax_stride, each in the CSC
+ *            slot order of gblu_analyze (ax_stride >= nnz(A));
+ *   LUx_dev  device float64, set s at LUx_dev + s*lu_stride (lu_stride >=
+ *            nnz_l + nnz_u of gblu_get_stats): receives the set's factor
+ *            values in the handle's internal layout; read them back only
+ *            through gblu_solve_batch.  Caller-owned.
+ *   failed   optional host int32[nsets]: 1 if a pivot of that set failed
+ *            the check, else 0.  A failed set is not restarted (a restart
+ *            changes the set's pattern): its values are not valid, and it
+ *            must be factorized on a handle of its own.  Other sets are not
+ *            affected.
+ *   n_failed optional host: number of failed sets.
+ * The handle's own factors are not touched.  Synchronizes `stream` once.
+ * Errors: GBLU_ERR_INVALID_INPUT (nsets < 1, null buffer, small stride),
+ * GBLU_ERR_NOT_FACTORIZED, GBLU_ERR_DEVICE_TIMEOUT.
+ */
+int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
+                           double *LUx_dev, int64_t lu_stride, int32_t *failed, int32_t *n_failed,
+                           void *stream);
+
+/*
+ * Solve A_s x_s = b_s for every set of a batch whose factor values came from
+ * gblu_refactorize_batch (sets that failed give meaningless x).  b and x are
+ * device float64, set s at b_dev + s*b_stride, x_dev + s*x_stride (strides
+ * >= n; b and x may alias).  Asynchronous on `stream`.
+ */
+int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_t lu_stride,
+                     const double *b_dev, int64_t b_stride, double *x_dev, int64_t x_stride,
+                     void *stream);
+
+/*
  * Relative residual of a solution, computed on the device in float64:
  * out_dev[0] = ||b - A x||_inf / (||A||_inf * ||x||_inf), out_dev[1] =
  * ||b - A x||_inf, out_dev[2] = ||A||_inf, out_dev[3] = ||x||_inf.

@@ -105,6 +105,13 @@ struct gblu_ctx {
     // dense tail of the re-factorization: the block and its column offsets
     DBuf<double> dense;
     DBuf<int32_t> dense_s0;
+    // batches of value sets: ready flags and control blocks per set, the
+    // argument blocks, the ticket
+    DBuf<int32_t> bfinish, bticket;
+    DBuf<DevCtl> bctl;
+    DBuf<RefactorArgs> bargs;
+    std::vector<RefactorArgs> bargs_host;
+    std::vector<DevCtl> bctl_host;
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
@@ -257,11 +264,9 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
 
 // Checked re-factorization on the installed structure (Algorithms 3 and 4).
 // *interrupted = 1 if a pivot failed the check.
-int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+// argument block of the column kernels for the installed structure
+RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
 {
-    const int32_t n = h->S.n;
-    h->epoch++;
-    KL(launch_begin_refactor(h->ctl, st));
     RefactorArgs a{};
     a.Ap = h->Ap.p;
     a.Q = h->Q.p;
@@ -284,6 +289,15 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     a.eps = h->opts.pivot_tol;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
+    return a;
+}
+
+int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+{
+    const int32_t n = h->S.n;
+    h->epoch++;
+    KL(launch_begin_refactor(h->ctl, st));
+    RefactorArgs a = refactor_args(h, Ax);
     const std::vector<int32_t> &ltp = h->W.level_task_ptr;
     const int32_t div = h->W.div_level;   // the schedule already follows sched_mode
     for (int32_t l = 0; l < div; l++) {   // cluster mode: one launch per level
@@ -597,6 +611,7 @@ void gblu_destroy(gblu_handle h)
         release(h, h->lsv_rows); release(h, h->usv_rows); release(h, h->lbs); release(h, h->ubs);
         release(h, h->lrb); release(h, h->urb); release(h, h->lsv_tick); release(h, h->usv_tick);
         release(h, h->ext_l); release(h, h->ext_u); release(h, h->dense); release(h, h->dense_s0);
+        release(h, h->bfinish); release(h, h->bticket); release(h, h->bctl); release(h, h->bargs);
         release(h, h->ltcnt);
         release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
         release(h, h->y); release(h, h->z); release(h, h->partial);
@@ -734,18 +749,14 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
     return GBLU_REPIVOTED;
 }
 
-int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
+// both triangular solves with the factor values LUx (the installed structure)
+static int solve_values(gblu_ctx *h, const double *LUx, const double *b_dev, double *x_dev, cudaStream_t st)
 {
-    CK(check_handle(h));
-    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
-    if (!b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
-    DeviceGuard g(h->device);
-    cudaStream_t st = (cudaStream_t)stream;
     const int32_t n = h->S.n;
     KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n, st));
     SolveArgs a{};
     a.n = n;
-    a.LUx = h->vals.p;
+    a.LUx = LUx;
     a.Lrp = h->Lrp.p;
     a.Urp = h->Urp.p;
     a.Lcol = h->Lcol.p;
@@ -807,6 +818,94 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
         h->launches++;
     }
     CK(sparse(false));
+    return GBLU_OK;
+}
+
+int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
+{
+    CK(check_handle(h));
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
+    if (!b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
+    DeviceGuard g(h->device);
+    return solve_values(h, h->vals.p, b_dev, x_dev, (cudaStream_t)stream);
+}
+
+int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
+                           double *LUx_dev, int64_t lu_stride, int32_t *failed, int32_t *n_failed,
+                           void *stream)
+{
+    CK(check_handle(h));
+    if (n_failed) *n_failed = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    const int64_t nnz_a = (int64_t)h->P.Ai.size(), nnz = h->S.nnz();
+    if (nsets < 1 || !Ax_dev || !LUx_dev || ax_stride < nnz_a || lu_stride < nnz)
+        return fail(GBLU_ERR_INVALID_INPUT, "batch: nsets >= 1, non-null buffers, strides >= %lld and %lld",
+                    (long long)nnz_a, (long long)nnz);
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = h->S.n;
+    const size_t fcap = h->bfinish.cap;
+    CK(ensure(h, h->bfinish, (size_t)nsets * n));
+    if (h->bfinish.cap != fcap)   // fresh flags: epochs start above zero
+        CU(cudaMemsetAsync(h->bfinish.p, 0, h->bfinish.cap * sizeof(int32_t), st));
+    CK(ensure(h, h->bctl, (size_t)nsets));
+    CK(ensure(h, h->bargs, (size_t)nsets));
+    CK(ensure(h, h->bticket, 1));
+    h->epoch++;
+    h->n_refactor += nsets;
+    const RefactorArgs base = refactor_args(h, nullptr);
+    h->bargs_host.assign(nsets, base);
+    for (int32_t s = 0; s < nsets; s++) {
+        RefactorArgs &as = h->bargs_host[s];
+        as.Ax = Ax_dev + s * ax_stride;
+        as.LUx = LUx_dev + s * lu_stride;
+        as.finish = h->bfinish.p + (size_t)s * n;
+        as.ctl = h->bctl.p + s;
+        as.dense_p = INT_MAX;   // the dense tail is not used in batches
+    }
+    CU(cudaMemcpyAsync(h->bargs.p, h->bargs_host.data(), sizeof(RefactorArgs) * nsets, cudaMemcpyHostToDevice, st));
+    KL(launch_begin_batch(h->bctl.p, nsets, h->bticket.p, st));
+    RefactorArgs a0 = base;
+    const std::vector<int32_t> &ltp = h->W.level_task_ptr;
+    const int32_t div = h->W.div_level;
+    for (int32_t l = 0; l < div; l++) {   // cluster mode
+        a0.task_begin = ltp[l];
+        a0.ntasks = ltp[l + 1] - ltp[l];
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, false, 0, h->epoch, h->bticket.p, st));
+    }
+    const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
+    if (ltp[div] < ntask) {               // pipeline mode
+        a0.task_begin = ltp[div];
+        a0.ntasks = ntask - ltp[div];
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->ref_grid, h->epoch, h->bticket.p, st));
+    }
+    h->bctl_host.resize(nsets);
+    CU(cudaMemcpyAsync(h->bctl_host.data(), h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    int32_t nf = 0;
+    for (int32_t s = 0; s < nsets; s++) {
+        const DevCtl &c = h->bctl_host[s];
+        if (c.status != 0) return fail(c.status, "batch set %d: device status %d (wait %d at column %d)", s,
+                                       c.status, c.where, c.where_k);
+        if (failed) failed[s] = c.interrupted ? 1 : 0;
+        nf += c.interrupted ? 1 : 0;
+    }
+    if (n_failed) *n_failed = nf;
+    return GBLU_OK;
+}
+
+int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_t lu_stride,
+                     const double *b_dev, int64_t b_stride, double *x_dev, int64_t x_stride, void *stream)
+{
+    CK(check_handle(h));
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
+    const int32_t n = h->S.n;
+    if (nsets < 1 || !LUx_dev || !b_dev || !x_dev || lu_stride < h->S.nnz() || b_stride < n || x_stride < n)
+        return fail(GBLU_ERR_INVALID_INPUT, "batch solve: nsets >= 1, non-null buffers, strides too small");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int32_t s = 0; s < nsets; s++)
+        CK(solve_values(h, LUx_dev + s * lu_stride, b_dev + s * b_stride, x_dev + s * x_stride, st));
     return GBLU_OK;
 }
 

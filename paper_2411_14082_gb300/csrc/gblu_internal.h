@@ -205,6 +205,10 @@ struct SolveArgs {
 int launch_begin_refactor(DevCtl *ctl, void *stream);
 int refactor_setup(int cap_long, int *blocks_per_sm);
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream);
+// batch of value sets on one structure (sets_dev: one argument block per set)
+int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
+int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
+                          int grid, int epoch, int32_t *ticket, void *stream);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);

@@ -333,11 +333,17 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     // before the block (its first dense_s0 rows); the block does the rest
     const bool dcol = kDense && k >= a.dense_p;
     const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
+    // up to cap entries: work vector and rows in shared memory; up to 2*cap:
+    // the rows alone (slot searches stay in shared memory), the work vector
+    // in place in global memory; longer: both in global memory
     const bool in_smem = len <= cap;
+    const bool rows_smem = !in_smem && len <= 2 * cap;
+    int32_t *rsw = reinterpret_cast<int32_t *>(xs);   // rows over the work-vector area
     double *x = in_smem ? xs : a.LUx + beg;
-    const int32_t *rows = in_smem ? rs : a.LUi + beg;
+    const int32_t *rows = in_smem ? rs : (rows_smem ? rsw : a.LUi + beg);
     for (int i = tid; i < len; i += kT) {
         if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
+        else if (rows_smem) rsw[i] = __ldg(a.LUi + beg + i);
         x[i] = 0.0;
     }
     if (tid == 0) {
@@ -575,6 +581,32 @@ __global__ void begin_refactor_kernel(DevCtl *ctl)
     ctl->where_k = -1;
 }
 
+// One task of the schedule: one long column (whole CTA), two medium
+// columns (a half each) or up to 8 short ones (a warp each); true = stop.
+template <bool kWait, bool kDense>
+__device__ __forceinline__ bool run_task(const RefactorArgs &a, int tt, double *xs, int32_t *rs, int epoch,
+                                         GroupShared *s_grp)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = __ldg(a.task_ptr + tt), c1 = __ldg(a.task_ptr + tt + 1);
+    const int k0 = __ldg(a.task_cols + c0);
+    const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
+    if (c1 - c0 == 1 && len0 > a.cap_short)            // one long column: whole CTA
+        return col_grp<kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
+    if (c1 - c0 == 2 && len0 > a.cap_short) {          // two medium columns: a half each
+        const int g = warp / (kWarps / 2);
+        const int half = a.cap_long / 2;
+        const bool hs = col_grp<kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
+                                                          rs + (size_t)g * half, epoch, g, half, s_grp[g]);
+        return __syncthreads_or(hs);
+    }
+    bool ws = false;
+    if (c0 + warp < c1)
+        ws = col_warp<kWait, kDense>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
+                                     rs + (size_t)warp * a.cap_short, lane, epoch);
+    return __syncthreads_or(ws);
+}
+
 // Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
 // (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
 template <bool kWait, bool kDense>
@@ -583,7 +615,6 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_quit;
     __shared__ GroupShared s_grp[2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *xs = reinterpret_cast<double *>(smem);
     int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)a.cap_long * sizeof(double));
     for (int iter = 0;; ++iter) {
@@ -595,28 +626,60 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
         const int t = s_t, quit = s_quit;
         __syncthreads();
         if (t >= a.ntasks || quit) break;
-        const int tt = a.task_begin + t;
-        const int c0 = __ldg(a.task_ptr + tt), c1 = __ldg(a.task_ptr + tt + 1);
-        bool stop;
-        const int k0 = __ldg(a.task_cols + c0);
-        const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
-        if (c1 - c0 == 1 && len0 > a.cap_short) {          // one long column: whole CTA
-            stop = col_grp<kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
-        } else if (c1 - c0 == 2 && len0 > a.cap_short) {   // two medium columns: a half each
-            const int g = warp / (kWarps / 2);
-            const int half = a.cap_long / 2;
-            const bool hs = col_grp<kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
-                                                       rs + (size_t)g * half, epoch, g, half, s_grp[g]);
-            stop = __syncthreads_or(hs);
-        } else {
-            bool ws = false;
-            if (c0 + warp < c1)
-                ws = col_warp<kWait, kDense>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
-                                     rs + (size_t)warp * a.cap_short, lane, epoch);
-            stop = __syncthreads_or(ws);
-        }
-        if (stop) break;
+        if (run_task<kWait, kDense>(a, a.task_begin + t, xs, rs, epoch, s_grp)) break;
     }
+}
+
+// Batch of value sets on one structure: sets[s] is the argument block of
+// set s (its A values, factor values, ready flags and control block; the
+// structure fields are shared).  Ticket t is task task_begin + t / nsets of
+// set t % nsets, so every set meets its tasks in a topological order.  A set
+// whose check failed (or whose wait gave up) is skipped from then on; the
+// other sets go on.
+template <bool kWait>
+__global__ void __launch_bounds__(kThreads, 2)
+refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
+                      int32_t *ticket)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_t, s_skip;
+    __shared__ GroupShared s_grp[2];
+    double *xs = reinterpret_cast<double *>(smem);
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)sets[0].cap_long * sizeof(double));
+    const long long total = (long long)ntasks * nsets;
+    for (int iter = 0;; ++iter) {
+        if (threadIdx.x == 0) {
+            const long long t = persistent ? (long long)atomicAdd(ticket, 1) : (iter == 0 ? (long long)blockIdx.x : total);
+            s_t = t < total ? (int)t : -1;
+            s_skip = 0;
+            if (t < total) {
+                const DevCtl *c = sets[(int)(t % nsets)].ctl;
+                s_skip = ld_volatile(&c->interrupted) || ld_volatile(&c->status);
+            }
+        }
+        __syncthreads();
+        const int t = s_t, skip = s_skip;
+        __syncthreads();
+        if (t < 0) break;
+        if (skip) continue;
+        // a local copy: stores through the work vector cannot alias it, so its
+        // fields stay in registers instead of being reloaded from memory
+        const RefactorArgs as = sets[t % nsets];
+        run_task<kWait, false>(as, task_begin + t / nsets, xs, rs, epoch, s_grp);
+    }
+}
+
+__global__ void begin_batch_kernel(DevCtl *ctl, int nsets, int32_t *ticket)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsets; s += gridDim.x * blockDim.x) {
+        ctl[s].ticket = 0;
+        ctl[s].interrupted = 0;
+        ctl[s].first_bad = INT_MAX;
+        ctl[s].status = 0;
+        ctl[s].where = 0;
+        ctl[s].where_k = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
 }
 
 size_t task_smem(const RefactorArgs &a)
@@ -646,6 +709,10 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(refactor_task_kernel<false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     int b1 = 0, b2 = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<true, false>, kThreads, sm);
@@ -653,6 +720,30 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<true, true>, kThreads, sm);
     *blocks_per_sm = b1 < b2 ? b1 : b2;
     return (int)e;
+}
+
+int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream)
+{
+    const int g = (nsets + 255) / 256;
+    begin_batch_kernel<<<g < 1 ? 1 : g, 256, 0, (cudaStream_t)stream>>>(ctl, nsets, ticket);
+    return (int)cudaGetLastError();
+}
+
+int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
+                          int grid, int epoch, int32_t *ticket, void *stream)
+{
+    if (a0.ntasks <= 0 || nsets <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pipeline) {
+        refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, a0.task_begin,
+                                                                           a0.ntasks, epoch, 1, ticket);
+    } else {
+        const long long blocks = (long long)a0.ntasks * nsets;
+        if (blocks > INT_MAX) return (int)cudaErrorInvalidValue;
+        refactor_batch_kernel<false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
+            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket);
+    }
+    return (int)cudaGetLastError();
 }
 
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream)

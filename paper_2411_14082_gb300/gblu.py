@@ -36,7 +36,8 @@ EXPORTED = [
     "gblu_default_opts", "gblu_last_error", "gblu_create", "gblu_destroy", "gblu_analyze",
     "gblu_factorize", "gblu_refactorize", "gblu_solve", "gblu_residual", "gblu_get_stats",
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
-    "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc",
+    "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
+    "gblu_solve_batch",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -109,9 +110,11 @@ def load(build_if_missing: bool = True):
         lib.gblu_solve_factors_noalloc.restype = ctypes.c_int
         lib.gblu_levels.argtypes = [I32, P, P, P]
         lib.gblu_levels.restype = I32
+        lib.gblu_refactorize_batch.argtypes = [P, I32, P, I64, P, I64, P, ctypes.POINTER(I32), P]
+        lib.gblu_solve_batch.argtypes = [P, I32, P, I64, P, I64, P, I64, P]
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
-                  "gblu_order_mindeg", "gblu_column_etree"):
+                  "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -216,6 +219,46 @@ class Solver:
             x = torch.empty_like(b)
         _check(load().gblu_solve(self._h, _dev_ptr(b, self.device, self.n),
                                  _dev_ptr(x, self.device, self.n), _stream(stream)))
+        return x
+
+    def refactorize_batch(self, Ax, LUx=None, stream=None):
+        """Checked re-factorization of a batch of value sets on this structure.
+
+        Ax: CUDA float64 tensor [nsets, nnz(A)].  Returns (LUx, failed): LUx
+        [nsets, nnz(L+U)] holds each set's factor values (pass it to
+        solve_batch), failed is a numpy int32 [nsets] (1: a pivot failed the
+        check; that set needs a handle of its own)."""
+        import torch
+        if Ax.dim() != 2 or Ax.shape[1] != self.nnz:
+            raise ValueError("Ax must be [nsets, nnz(A)]")
+        _dev_ptr(Ax, self.device)
+        nsets = Ax.shape[0]
+        st = self.stats()
+        nlu = st["nnz_l"] + st["nnz_u"]
+        if LUx is None:
+            LUx = torch.empty((nsets, nlu), dtype=torch.float64, device=Ax.device)
+        if LUx.dim() != 2 or LUx.shape[0] != nsets or LUx.shape[1] != nlu:
+            raise ValueError("LUx must be [nsets, nnz(L+U)]")
+        _dev_ptr(LUx, self.device)
+        failed = np.zeros(nsets, np.int32)
+        nf = ctypes.c_int32(0)
+        _check(load().gblu_refactorize_batch(self._h, nsets, ctypes.c_void_p(Ax.data_ptr()), self.nnz,
+                                             ctypes.c_void_p(LUx.data_ptr()), nlu, _np_ptr(failed),
+                                             ctypes.byref(nf), _stream(stream)))
+        return LUx, failed
+
+    def solve_batch(self, LUx, b, x=None, stream=None):
+        """Solve every set of a batch: LUx [nsets, nnz(L+U)], b [nsets, n]."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        for t in (LUx, b, x):
+            _dev_ptr(t, self.device)
+        if b.dim() != 2 or b.shape[1] != self.n or b.shape != x.shape or LUx.shape[0] != b.shape[0]:
+            raise ValueError("b and x must be [nsets, n] and match LUx")
+        _check(load().gblu_solve_batch(self._h, b.shape[0], ctypes.c_void_p(LUx.data_ptr()), LUx.shape[1],
+                                       ctypes.c_void_p(b.data_ptr()), self.n, ctypes.c_void_p(x.data_ptr()),
+                                       self.n, _stream(stream)))
         return x
 
     def step_host(self, Ax, b, x, stream=None):
