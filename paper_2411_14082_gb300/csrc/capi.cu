@@ -749,14 +749,29 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
     return GBLU_REPIVOTED;
 }
 
-// both triangular solves with the factor values LUx (the installed structure)
-static int solve_values(gblu_ctx *h, const double *LUx, const double *b_dev, double *x_dev, cudaStream_t st)
+// both triangular solves of nsets systems on the installed structure: set s
+// with factor values LUx + s*lu_stride, right-hand side b_dev + s*b_stride,
+// solution x_dev + s*x_stride
+static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const double *b_dev, int64_t b_stride,
+                        double *x_dev, int64_t x_stride, int32_t nsets, cudaStream_t st)
 {
     const int32_t n = h->S.n;
-    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n, st));
+    if (nsets > 1) {   // per-set intermediate vectors
+        if ((int64_t)n * nsets > INT_MAX) return fail(GBLU_ERR_INVALID_INPUT, "batch too large");
+        CK(ensure(h, h->y, (size_t)n * nsets));
+        CK(ensure(h, h->z, (size_t)n * nsets));
+        CK(ensure(h, h->ext_l, (size_t)n * nsets));
+        CK(ensure(h, h->ext_u, (size_t)n * nsets));
+    }
+    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n * nsets, st));
     SolveArgs a{};
     a.n = n;
     a.LUx = LUx;
+    a.nsets = nsets;
+    a.lu_stride = lu_stride;
+    a.b_stride = b_stride;
+    a.x_stride = x_stride;
+    a.v_stride = n;
     a.Lrp = h->Lrp.p;
     a.Urp = h->Urp.p;
     a.Lcol = h->Lcol.p;
@@ -827,7 +842,7 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
     if (!b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
     DeviceGuard g(h->device);
-    return solve_values(h, h->vals.p, b_dev, x_dev, (cudaStream_t)stream);
+    return solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, (cudaStream_t)stream);
 }
 
 int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
@@ -904,9 +919,7 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
         return fail(GBLU_ERR_INVALID_INPUT, "batch solve: nsets >= 1, non-null buffers, strides too small");
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
-    for (int32_t s = 0; s < nsets; s++)
-        CK(solve_values(h, LUx_dev + s * lu_stride, b_dev + s * b_stride, x_dev + s * x_stride, st));
-    return GBLU_OK;
+    return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, st);
 }
 
 int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host, double *x_host,

@@ -197,6 +197,10 @@ struct SolveArgs {
     double *ext;                    // per row: its sum over entries outside its block
     const int32_t *rows;            // rows in ticket order, or block ids (level finish)
     int32_t nrows;                  // number of entries of rows
+    // batches (nsets > 1): set s reads LUx + s*lu_stride, b + s*b_stride and
+    // writes x + s*x_stride; y, z and ext are per set at s*v_stride
+    int32_t nsets;
+    int64_t lu_stride, b_stride, x_stride, v_stride;
     long long spin_limit;
     DevCtl *ctl;
 };

@@ -447,22 +447,33 @@ __device__ __forceinline__ void ublock_finish(const SolveArgs &a, int f, int w, 
     }
 }
 
+// Batches (gblu_solve_batch): the same kernels over nsets right-hand sides
+// and factor value sets; set s reads its values at LUx + s*lu_stride and
+// its vectors at b + s*b_stride, x + s*x_stride, y/z/ext + s*v_stride.
+__device__ __forceinline__ SolveArgs set_view(const SolveArgs &a, int s)
+{
+    SolveArgs v = a;
+    v.LUx = a.LUx + (int64_t)s * a.lu_stride;
+    v.b = a.b + (int64_t)s * a.b_stride;
+    v.x = a.x + (int64_t)s * a.x_stride;
+    v.y = a.y + (int64_t)s * a.v_stride;
+    v.z = a.z + (int64_t)s * a.v_stride;
+    v.ext = a.ext + (int64_t)s * a.v_stride;
+    return v;
+}
+
 // level mode, first launch of a level: every row of the level stores its
 // outside sum (its inputs are final: earlier launches)
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_level_kernel(SolveArgs a)
+__device__ __forceinline__ void lsolve_level_row(const SolveArgs &a, int t, int lane)
 {
-    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (t >= a.nrows) return;
     const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
     double s;
     lrow_ext(a, i, i - __ldg(a.bs + b), lane, false, s);
     if (lane == 0) a.ext[i] = s;
 }
 
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_level_kernel(SolveArgs a)
+__device__ __forceinline__ void usolve_level_row(const SolveArgs &a, int t, int lane)
 {
-    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (t >= a.nrows) return;
     const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
     const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
     double s;
@@ -471,71 +482,92 @@ __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_level_kernel(
 }
 
 // level mode, second launch of a level: one warp per block (a.rows = block ids)
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_finish_kernel(SolveArgs a)
+__device__ __forceinline__ void lsolve_finish_block(const SolveArgs &a, int t, int lane)
 {
-    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (t >= a.nrows) return;
     const int b = __ldg(a.rows + t), f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
     lblock_finish(a, f, w, lane, lane < w ? __ldcg(a.ext + f + lane) : 0.0);
 }
 
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_finish_kernel(SolveArgs a)
+__device__ __forceinline__ void usolve_finish_block(const SolveArgs &a, int t, int lane)
 {
-    const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (t >= a.nrows) return;
     const int b = __ldg(a.rows + t), f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f;
     ublock_finish(a, f, w, lane, lane < w ? __ldcg(a.ext + f + lane) : 0.0);
 }
 
-// sync-free: a.rows[0..nrows) = rows in a topological order (blocks by
-// level, the finishing row of each block last), handed out by ticket
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_syncfree_kernel(SolveArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&a.ctl->ticket_l, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= a.nrows) break;
-        const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
-        const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
-        double s;
-        if (!lrow_ext(a, i, q, lane, true, s)) break;
-        if (q < w - 1) {
-            if (lane == 0) st_relaxed_f64(a.ext + i, s);
-            continue;
-        }
-        double e = s;   // the last row finishes the block
-        bool ok = true;
-        if (lane < w - 1) ok = await_value(a.ext, f + lane, a, 5, f + lane, e);
-        if (!__all_sync(kFull, ok)) break;
-        lblock_finish(a, f, w, lane, e);
+// kernels of the level launches; a batch puts the set in blockIdx.y
+#define GBLU_WARP_KERNEL(name, body)                                                             \
+    template <bool kBatch>                                                                      \
+    __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) name(SolveArgs a)               \
+    {                                                                                           \
+        const int t = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31; \
+        if (t >= a.nrows) return;                                                               \
+        if (kBatch) body(set_view(a, blockIdx.y), t, lane);                                     \
+        else body(a, t, lane);                                                                  \
     }
+GBLU_WARP_KERNEL(lsolve_level_kernel, lsolve_level_row)
+GBLU_WARP_KERNEL(usolve_level_kernel, usolve_level_row)
+GBLU_WARP_KERNEL(lsolve_finish_kernel, lsolve_finish_block)
+GBLU_WARP_KERNEL(usolve_finish_kernel, usolve_finish_block)
+#undef GBLU_WARP_KERNEL
+
+// sync-free: a.rows[0..nrows) = rows in a topological order (blocks by
+// level, the finishing row of each block last), handed out by ticket; in a
+// batch ticket t is row ticket t / nsets of set t % nsets.  true = stop.
+__device__ __forceinline__ bool lsolve_sf_row(const SolveArgs &a, int t, int lane)
+{
+    const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+    const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
+    double s;
+    if (!lrow_ext(a, i, q, lane, true, s)) return true;
+    if (q < w - 1) {
+        if (lane == 0) st_relaxed_f64(a.ext + i, s);
+        return false;
+    }
+    double e = s;   // the last row finishes the block
+    bool ok = true;
+    if (lane < w - 1) ok = await_value(a.ext, f + lane, a, 5, f + lane, e);
+    if (!__all_sync(kFull, ok)) return true;
+    lblock_finish(a, f, w, lane, e);
+    return false;
 }
 
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_syncfree_kernel(SolveArgs a)
+__device__ __forceinline__ bool usolve_sf_row(const SolveArgs &a, int t, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&a.ctl->ticket_u, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= a.nrows) break;
-        const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
-        const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
-        double s;
-        if (!urow_ext(a, i, q, w, lane, true, s)) break;
-        if (q > 0) {
-            if (lane == 0) st_relaxed_f64(a.ext + i, s);
-            continue;
-        }
-        double e = s;   // the first row finishes the block
-        bool ok = true;
-        if (lane >= 1 && lane < w) ok = await_value(a.ext, f + lane, a, 6, f + lane, e);
-        if (!__all_sync(kFull, ok)) break;
-        ublock_finish(a, f, w, lane, e);
+    const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
+    const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
+    double s;
+    if (!urow_ext(a, i, q, w, lane, true, s)) return true;
+    if (q > 0) {
+        if (lane == 0) st_relaxed_f64(a.ext + i, s);
+        return false;
     }
+    double e = s;   // the first row finishes the block
+    bool ok = true;
+    if (lane >= 1 && lane < w) ok = await_value(a.ext, f + lane, a, 6, f + lane, e);
+    if (!__all_sync(kFull, ok)) return true;
+    ublock_finish(a, f, w, lane, e);
+    return false;
 }
+
+#define GBLU_SYNCFREE_KERNEL(name, body, tick)                                                   \
+    template <bool kBatch>                                                                      \
+    __global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) name(SolveArgs a)               \
+    {                                                                                           \
+        const int lane = threadIdx.x & 31;                                                      \
+        const int total = kBatch ? a.nrows * a.nsets : a.nrows;                                 \
+        for (;;) {                                                                              \
+            int t = 0;                                                                          \
+            if (lane == 0) t = atomicAdd(&a.ctl->tick, 1);                                      \
+            t = __shfl_sync(kFull, t, 0);                                                       \
+            if (t >= total) break;                                                              \
+            const bool stop = kBatch ? body(set_view(a, t % a.nsets), t / a.nsets, lane)        \
+                                     : body(a, t, lane);                                        \
+            if (stop) break;                                                                    \
+        }                                                                                       \
+    }
+GBLU_SYNCFREE_KERNEL(lsolve_syncfree_kernel, lsolve_sf_row, ticket_l)
+GBLU_SYNCFREE_KERNEL(usolve_syncfree_kernel, usolve_sf_row, ticket_u)
+#undef GBLU_SYNCFREE_KERNEL
 
 // ---------------------------------------------------------------------------
 // Trailing block of the structure-adaptive solve (Section V-B, Algorithm 6):
@@ -552,12 +584,8 @@ struct DenseArgs {
 };
 
 // forward rectangular part: y[i] = b[piv[i]] - L(i, columns before the slice) y
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-lsolve_rect_kernel(SolveArgs a, DenseArgs d)
+__device__ __forceinline__ void lsolve_rect(const SolveArgs &a, const DenseArgs &d, int i, int lane)
 {
-    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
-    if (i >= d.r1) return;
-    const int lane = threadIdx.x & 31;
     const int64_t rb = __ldg(a.Lrp + i), re = __ldg(d.split + (i - d.p0));
     double s = 0.0;
     for (int64_t e = rb + lane; e < re; e += 32)
@@ -566,19 +594,33 @@ lsolve_rect_kernel(SolveArgs a, DenseArgs d)
     if (lane == 0) a.y[i] = __ldg(a.b + __ldg(a.piv + i)) - s;
 }
 
-// backward rectangular part: z[i] = y[i] - U(i, columns after the slice) z
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
-usolve_rect_kernel(SolveArgs a, DenseArgs d)
+template <bool kBatch>
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_rect_kernel(SolveArgs a, DenseArgs d)
 {
     const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
     if (i >= d.r1) return;
-    const int lane = threadIdx.x & 31;
+    if (kBatch) lsolve_rect(set_view(a, blockIdx.y), d, i, threadIdx.x & 31);
+    else lsolve_rect(a, d, i, threadIdx.x & 31);
+}
+
+// backward rectangular part: z[i] = y[i] - U(i, columns after the slice) z
+__device__ __forceinline__ void usolve_rect(const SolveArgs &a, const DenseArgs &d, int i, int lane)
+{
     const int64_t rb = __ldg(d.split + (i - d.p0)), re = __ldg(a.Urp + i + 1);
     double s = 0.0;
     for (int64_t e = re - 1 - lane; e >= rb; e -= 32)
         s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), __ldcg(a.z + __ldg(a.Ucol + e)), s);
     s = warp_sum(s);
     if (lane == 0) a.z[i] = __ldcg(a.y + i) - s;
+}
+
+template <bool kBatch>
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_rect_kernel(SolveArgs a, DenseArgs d)
+{
+    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
+    if (i >= d.r1) return;
+    if (kBatch) usolve_rect(set_view(a, blockIdx.y), d, i, threadIdx.x & 31);
+    else usolve_rect(a, d, i, threadIdx.x & 31);
 }
 
 constexpr int kTriThreads = 256;
@@ -640,7 +682,7 @@ __device__ __forceinline__ void tri_issue(const TriSmem &t, const SolveArgs &a, 
 
 // forward triangular piece [r0, r1): columns in increasing order; the first
 // tri[j] L entries of column j are its rows inside the piece
-__global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, DenseArgs d)
+__device__ __forceinline__ void lsolve_tri(const SolveArgs &a, const DenseArgs &d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int m = d.r1 - d.r0, tid = threadIdx.x;
@@ -676,7 +718,7 @@ __global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, De
 // backward triangular piece [r0, r1): columns in decreasing order; the U
 // entries of column j from position tri[j] to the diagonal are its rows
 // inside the piece
-__global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, DenseArgs d)
+__device__ __forceinline__ void usolve_tri(const SolveArgs &a, const DenseArgs &d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int m = d.r1 - d.r0, tid = threadIdx.x;
@@ -717,6 +759,21 @@ __global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, De
         a.z[j] = t.out[q];
         a.x[__ldg(a.Q + j)] = t.out[q];
     }
+}
+
+// one CTA per piece; a batch runs one CTA per set (blockIdx.x)
+template <bool kBatch>
+__global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, DenseArgs d)
+{
+    if (kBatch) lsolve_tri(set_view(a, blockIdx.x), d);
+    else lsolve_tri(a, d);
+}
+
+template <bool kBatch>
+__global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, DenseArgs d)
+{
+    if (kBatch) usolve_tri(set_view(a, blockIdx.x), d);
+    else usolve_tri(a, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -801,14 +858,20 @@ int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu
     return (int)cudaGetLastError();
 }
 
+// a.nsets > 1: a batch (set in blockIdx.y of the level launches, in the
+// ticket of the sync-free launch)
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
-    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+    const bool batch = a.nsets > 1;
+    const dim3 g((a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, batch ? a.nsets : 1);
+    cudaStream_t st = (cudaStream_t)stream;
     if (level_mode) {
-        lsolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+        if (batch) lsolve_level_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else lsolve_level_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
     } else {
-        lsolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+        if (batch) lsolve_syncfree_kernel<true><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else lsolve_syncfree_kernel<false><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(a);
     }
     return (int)cudaGetLastError();
 }
@@ -816,20 +879,31 @@ int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 int launch_solve_finish(const SolveArgs &a, bool lower, void *stream)
 {
     if (a.nrows <= 0) return 0;
-    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
-    if (lower) lsolve_finish_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
-    else usolve_finish_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+    const bool batch = a.nsets > 1;
+    const dim3 g((a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, batch ? a.nsets : 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (lower) {
+        if (batch) lsolve_finish_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else lsolve_finish_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+    } else {
+        if (batch) usolve_finish_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else usolve_finish_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+    }
     return (int)cudaGetLastError();
 }
 
 int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
 {
     if (a.nrows <= 0) return 0;
-    const int g = (a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+    const bool batch = a.nsets > 1;
+    const dim3 g((a.nrows + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, batch ? a.nsets : 1);
+    cudaStream_t st = (cudaStream_t)stream;
     if (level_mode) {
-        usolve_level_kernel<<<g, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+        if (batch) usolve_level_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else usolve_level_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
     } else {
-        usolve_syncfree_kernel<<<grid, kSolveWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(a);
+        if (batch) usolve_syncfree_kernel<true><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(a);
+        else usolve_syncfree_kernel<false><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(a);
     }
     return (int)cudaGetLastError();
 }
@@ -846,15 +920,27 @@ int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, i
 {
     if (r1 <= r0) return 0;
     DenseArgs d{p0, r0, r1, split, tri, LUp, LUi, nU};
-    const int g = (r1 - r0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock;
+    const bool batch = a.nsets > 1;
+    const dim3 g((r1 - r0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, batch ? a.nsets : 1);
+    const int gt = batch ? a.nsets : 1;
     const size_t sm = tri_smem(r1 - r0);
     cudaStream_t st = (cudaStream_t)stream;
     if (lower) {
-        lsolve_rect_kernel<<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-        lsolve_tri_kernel<<<1, kTriThreads, sm, st>>>(a, d);
+        if (batch) {
+            lsolve_rect_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+            lsolve_tri_kernel<true><<<gt, kTriThreads, sm, st>>>(a, d);
+        } else {
+            lsolve_rect_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+            lsolve_tri_kernel<false><<<gt, kTriThreads, sm, st>>>(a, d);
+        }
     } else {
-        usolve_rect_kernel<<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-        usolve_tri_kernel<<<1, kTriThreads, sm, st>>>(a, d);
+        if (batch) {
+            usolve_rect_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+            usolve_tri_kernel<true><<<gt, kTriThreads, sm, st>>>(a, d);
+        } else {
+            usolve_rect_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
+            usolve_tri_kernel<false><<<gt, kTriThreads, sm, st>>>(a, d);
+        }
     }
     return (int)cudaGetLastError();
 }
@@ -862,9 +948,13 @@ int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, i
 int dense_piece_setup(int max_rows)
 {
     const int sm = (int)tri_smem(max_rows);
-    cudaError_t e = cudaFuncSetAttribute(lsolve_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaFuncSetAttribute(lsolve_tri_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(usolve_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaFuncSetAttribute(usolve_tri_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lsolve_tri_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(usolve_tri_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return (int)e;
 }
 
@@ -873,14 +963,22 @@ int solve_syncfree_grid(int *grid)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lsolve_syncfree_kernel,
+    int p[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[0], lsolve_syncfree_kernel<false>,
                                                                   kSolveWarpsPerBlock * 32, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[1], usolve_syncfree_kernel<false>,
+                                                          kSolveWarpsPerBlock * 32, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[2], lsolve_syncfree_kernel<true>,
+                                                          kSolveWarpsPerBlock * 32, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[3], usolve_syncfree_kernel<true>,
+                                                          kSolveWarpsPerBlock * 32, 0);
     if (e != cudaSuccess) return (int)e;
-    int per2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, usolve_syncfree_kernel,
-                                                      kSolveWarpsPerBlock * 32, 0);
-    if (e != cudaSuccess) return (int)e;
-    *grid = sms * (per < per2 ? per : per2);
+    per = p[0];
+    for (int i = 1; i < 4; i++) per = p[i] < per ? p[i] : per;
+    *grid = sms * per;
     return 0;
 }
 
