@@ -38,10 +38,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate of the profiling recipe (non-tensor 
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4": {"refactor_cu_sha256": "36f0c9e51fd6d1f967f2cff7b9a411a5633278fb859c3837e5a73ebf128f70f8",
-                          "bytes": 15.54e9 + 446.2e6},
-    "rc_mesh_120x120x4": {"refactor_cu_sha256": "36f0c9e51fd6d1f967f2cff7b9a411a5633278fb859c3837e5a73ebf128f70f8",
-                          "bytes": 135.4e6 + 82.7e6},
+    "rc_mesh_200x200x4": {"refactor_cu_sha256": "77213f434fa919a3edd95131e1d894033e4e8d95ae293e3ff1c4df6571ba9a7e",
+                          "bytes": 15.99e9 + 445.3e6},
+    "rc_mesh_120x120x4": {"refactor_cu_sha256": "77213f434fa919a3edd95131e1d894033e4e8d95ae293e3ff1c4df6571ba9a7e",
+                          "bytes": 135.9e6 + 82.8e6},
 }
 
 
