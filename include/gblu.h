@@ -192,6 +192,33 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
                      void *stream);
 
 /*
+ * Mixed precision (this library's extension; the paper factors in double).
+ *
+ * gblu_refactorize_f32: the checked re-factorization of Algorithms 3 and 4
+ * computed in single precision (A values are rounded once when scattered;
+ * the pivot check compares single-precision values) into a separate factor
+ * array of the handle.  The handle's double-precision factors are not
+ * touched.  *check_failed (optional, host) = 1 if a pivot failed the check:
+ * those factors are then not used, and gblu_solve_refined falls back to
+ * double precision.  Synchronizes `stream` once.
+ *
+ * gblu_solve_refined: solves A x = b for the A values Ax_dev (the CSC slot
+ * order of gblu_analyze) by iterative refinement on the single-precision
+ * factors of the last gblu_refactorize_f32: x = solve(b), then while the
+ * backward error ||b - A x||inf / (||A||inf ||x||inf), computed in double, is
+ * above tol: x += solve(b - A x).  The solves run in double on the widened
+ * factors.  If the error does not halve in an iteration, max_iter corrections
+ * are used up, or the factors failed the check, it re-factorizes in double
+ * precision (gblu_refactorize, with its restart) and solves directly:
+ * *iters (optional, host) is then -1, else the number of corrections.
+ * *berr (optional, host) = the final backward error.  x_dev must not alias
+ * b_dev.  Synchronizes `stream` once per iteration.
+ */
+int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed);
+int gblu_solve_refined(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, double tol,
+                       int32_t max_iter, void *stream, int32_t *iters, double *berr);
+
+/*
  * Relative residual of a solution, computed on the device in float64:
  * out_dev[0] = ||b - A x||_inf / (||A||_inf * ||x||_inf), out_dev[1] =
  * ||b - A x||_inf, out_dev[2] = ||A||_inf, out_dev[3] = ||x||_inf.

@@ -76,6 +76,8 @@ struct gblu_ctx {
     gblu_opts opts{};
     int sm_count = 0;
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0;
+    int ref32_blocks_per_sm = 0, ref32_grid = 0;
+    bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
     bool analyzed = false, factorized = false;
     Pattern P;
     Structure S;
@@ -110,6 +112,11 @@ struct gblu_ctx {
     DBuf<int32_t> bfinish, bticket;
     DBuf<DevCtl> bctl;
     DBuf<RefactorArgs> bargs;
+    // mixed precision: single-precision factors, their widened copy, the
+    // residual and correction vectors, and the residual norms (host mirror)
+    DBuf<float> vals32;
+    DBuf<double> vals_w, ir_r, ir_d, ir_out;
+    double *ir_host = nullptr;
     std::vector<RefactorArgs> bargs_host;
     std::vector<DevCtl> bctl_host;
     // restart (tail factorization)
@@ -197,6 +204,7 @@ int status_code(gblu_ctx *h)
 int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st)
 {
     h->S = std::move(S);
+    h->f32_valid = false;
     const int resident_warps = h->ref_blocks_per_sm * h->sm_count * (kRefThreads / 32);
     SolveSplit sp;
     sp.density = h->opts.solve_dense_density;
@@ -578,6 +586,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(DevCtl));
     int r = 0;
     if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
+    if (e == cudaSuccess && r == 0) r = refactor_setup_f32(kRefCapLong, &h->ref32_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
     if (e == cudaSuccess && r == 0) r = dense_piece_setup(kMaxPieceRows);
     if (e == cudaSuccess && r == 0) r = dense_setup(GBLU_DENSE_MAX_ROWS);
@@ -590,6 +599,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
         return fail(GBLU_ERR_CUDA, "device setup failed: %s", msg);
     }
     h->ref_grid = h->ref_blocks_per_sm * h->sm_count;
+    h->ref32_grid = h->ref32_blocks_per_sm * h->sm_count;
     h->res_blocks = h->sm_count * 4;
     *out = h;
     return GBLU_OK;
@@ -612,6 +622,8 @@ void gblu_destroy(gblu_handle h)
         release(h, h->lrb); release(h, h->urb); release(h, h->lsv_tick); release(h, h->usv_tick);
         release(h, h->ext_l); release(h, h->ext_u); release(h, h->dense); release(h, h->dense_s0);
         release(h, h->bfinish); release(h, h->bticket); release(h, h->bctl); release(h, h->bargs);
+        release(h, h->vals32); release(h, h->vals_w); release(h, h->ir_r); release(h, h->ir_d); release(h, h->ir_out);
+        if (h->ir_host) cudaFreeHost(h->ir_host);
         release(h, h->ltcnt);
         release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
         release(h, h->y); release(h, h->z); release(h, h->partial);
@@ -920,6 +932,114 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, st);
+}
+
+int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed)
+{
+    CK(check_handle(h));
+    if (check_failed) *check_failed = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(ensure(h, h->vals32, (size_t)h->S.nnz()));
+    h->epoch++;
+    h->n_refactor++;
+    KL(launch_begin_refactor(h->ctl, st));
+    const RefactorArgs d = refactor_args(h, Ax_dev);
+    RefactorArgsT<float> a{};
+    a.Ap = d.Ap; a.Q = d.Q; a.amap = d.amap; a.Ax = d.Ax; a.LUp = d.LUp; a.LUi = d.LUi; a.nU = d.nU;
+    a.chain = d.chain; a.dense_p = INT_MAX; a.dense_s0 = nullptr; a.S = nullptr; a.dense_ld = 0;
+    a.LUx = h->vals32.p; a.finish = d.finish; a.task_ptr = d.task_ptr; a.task_cols = d.task_cols;
+    a.cap_short = d.cap_short; a.cap_long = d.cap_long; a.eps = d.eps; a.spin_limit = d.spin_limit;
+    a.ctl = d.ctl;
+    const std::vector<int32_t> &ltp = h->W.level_task_ptr;
+    const int32_t div = h->W.div_level;
+    for (int32_t l = 0; l < div; l++) {
+        a.task_begin = ltp[l];
+        a.ntasks = ltp[l + 1] - ltp[l];
+        KL(launch_refactor_tasks_f32(a, false, 0, h->epoch, st));
+    }
+    const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
+    if (ltp[div] < ntask) {
+        a.task_begin = ltp[div];
+        a.ntasks = ntask - ltp[div];
+        KL(launch_refactor_tasks_f32(a, true, h->ref32_grid, h->epoch, st));
+    }
+    CK(read_ctl(h, st));
+    CK(status_code(h));
+    h->f32_valid = !h->hctl->interrupted;
+    h->f32_widened = false;
+    h->last_first_bad = h->hctl->interrupted ? h->hctl->first_bad : -1;
+    if (check_failed) *check_failed = h->hctl->interrupted ? 1 : 0;
+    return GBLU_OK;
+}
+
+int gblu_solve_refined(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, double tol,
+                       int32_t max_iter, void *stream, int32_t *iters, double *berr)
+{
+    CK(check_handle(h));
+    if (iters) *iters = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    if (!Ax_dev || !b_dev || !x_dev || !(tol >= 0.0) || max_iter < 0)
+        return fail(GBLU_ERR_INVALID_INPUT, "null vector, negative tolerance or iteration limit");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = h->S.n;
+    const size_t nnz = (size_t)h->S.nnz();
+    CK(ensure(h, h->ir_r, (size_t)n));
+    CK(ensure(h, h->ir_d, (size_t)n));
+    CK(ensure(h, h->ir_out, 4));
+    if (!h->ir_host) CU(cudaMallocHost((void **)&h->ir_host, 4 * sizeof(double)));
+    // backward error ||b - A x||inf / (||A||inf ||x||inf); r = b - A x kept in ir_r
+    auto residual = [&](const double *x, double *out_host) -> int {
+        KL(launch_residual(h->P.n, h->Arp.p, h->Acol.p, h->Aslot.p, Ax_dev, b_dev, x, h->ir_out.p,
+                           h->partial.p, h->res_blocks, st, h->ir_r.p));
+        CU(cudaMemcpyAsync(h->ir_host, h->ir_out.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        *out_host = h->ir_host[0];
+        return GBLU_OK;
+    };
+    double e = 0.0;
+    int32_t it = 0;
+    bool converged = false;
+    if (h->f32_valid) {
+        if (!h->f32_widened) {
+            CK(ensure(h, h->vals_w, nnz));
+            KL(launch_widen(h->vals32.p, h->vals_w.p, (int64_t)nnz, st));
+            h->f32_widened = true;
+        }
+        CK(solve_values(h, h->vals_w.p, 0, b_dev, 0, x_dev, 0, 1, st));
+        CK(residual(x_dev, &e));
+        double prev = e;
+        while (!(e <= tol) && it < max_iter) {
+            CK(solve_values(h, h->vals_w.p, 0, h->ir_r.p, 0, h->ir_d.p, 0, 1, st));   // A d = r
+            KL(launch_axpy(x_dev, h->ir_d.p, n, st));
+            it++;
+            CK(residual(x_dev, &e));
+            if (!(e <= 0.5 * prev)) break;   // refinement stalls
+            prev = e;
+        }
+        converged = e <= tol;
+    }
+    if (!converged) {   // the FP64 re-factorization (with its restart) and solve
+        int interrupted = 0;
+        int rc = run_refactor(h, Ax_dev, st, &interrupted);
+        if (rc == GBLU_OK && interrupted) {
+            h->n_repivot++;
+            rc = run_restart(h, Ax_dev, st);
+        }
+        if (rc != GBLU_OK) {
+            h->factorized = false;
+            return rc;
+        }
+        CK(solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, st));
+        CK(residual(x_dev, &e));
+        it = -1;
+    }
+    if (iters) *iters = it;
+    if (berr) *berr = e;
+    return GBLU_OK;
 }
 
 int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host, double *x_host,

@@ -136,7 +136,10 @@ struct DevCtl {
 
 #define GBLU_INTERNAL_POOL_FULL (-100)
 
-struct RefactorArgs {
+// R: the value type of the factors being computed (double; float for the
+// single-precision factorization of the mixed-precision solve)
+template <typename R>
+struct RefactorArgsT {
     const int32_t *Ap, *Q, *amap;   // A pattern (column pointers), order, slot map
     const double *Ax;               // new values (caller slot order)
     const int64_t *LUp;
@@ -146,9 +149,9 @@ struct RefactorArgs {
     // and leave rows >= dense_p in column k - dense_p of S (leading dim dense_ld)
     int32_t dense_p;
     const int32_t *dense_s0;
-    double *S;
+    R *S;
     int64_t dense_ld;
-    double *LUx;
+    R *LUx;
     int32_t *finish;
     const int32_t *task_ptr, *task_cols;
     int32_t task_begin, ntasks;     // tasks of this launch
@@ -157,6 +160,7 @@ struct RefactorArgs {
     long long spin_limit;
     DevCtl *ctl;
 };
+using RefactorArgs = RefactorArgsT<double>;
 
 struct TailArgs {
     int32_t n;
@@ -208,7 +212,10 @@ struct SolveArgs {
 // kernel launchers (kernels.cu); each returns a cudaError_t as int
 int launch_begin_refactor(DevCtl *ctl, void *stream);
 int refactor_setup(int cap_long, int *blocks_per_sm);
+int refactor_setup_f32(int cap_long, int *blocks_per_sm);
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream);
+// the same tasks with single-precision factor values (no dense tail)
+int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int grid, int epoch, void *stream);
 // batch of value sets on one structure (sets_dev: one argument block per set)
 int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
@@ -234,6 +241,8 @@ constexpr int kDenseNb = 8;         // panel width
 int dense_setup(int max_rows);
 int launch_dense_lu(const DenseArgs2 &d, void *stream, long long *launches);
 
+int launch_widen(const float *src, double *dst, int64_t n, void *stream);
+int launch_axpy(double *x, const double *d, int32_t n, void *stream);
 int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream);
 int launch_solve_finish(const SolveArgs &a, bool lower, void *stream);
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
@@ -241,7 +250,7 @@ int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
                     const int32_t *Aslot, const double *Ax, const double *b,
                     const double *x, double *out, double *partial, int nblocks,
-                    void *stream);
+                    void *stream, double *rvec = nullptr);
 int solve_syncfree_grid(int *grid);
 // one trapezoid slice of the trailing block: rectangular part, then triangular piece
 int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,

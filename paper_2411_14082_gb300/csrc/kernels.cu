@@ -777,9 +777,10 @@ __global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, De
 }
 
 // ---------------------------------------------------------------------------
+// rvec (optional): receives r = b - A x
 __global__ void residual_kernel(int32_t n, const int64_t *Arp, const int32_t *Acol,
                                 const int32_t *Aslot, const double *Ax, const double *b,
-                                const double *x, double *partial)
+                                const double *x, double *partial, double *rvec)
 {
     __shared__ double sr[8], sa[8], sx[8];
     double rmax = 0.0, amax = 0.0, xmax = 0.0;
@@ -793,6 +794,7 @@ __global__ void residual_kernel(int32_t n, const int64_t *Arp, const int32_t *Ac
         }
         s = warp_sum(s);
         as = warp_sum(as);
+        if (rvec && lane == 0) rvec[i] = b[i] - s;
         rmax = fmax(rmax, fabs(b[i] - s));
         amax = fmax(amax, as);
         xmax = fmax(xmax, fabs(x[i]));
@@ -824,6 +826,19 @@ __global__ void residual_final_kernel(const double *partial, int nblocks, double
         out[2] = a;
         out[3] = x;
     }
+}
+
+// mixed precision: single-precision factor values widened for the FP64
+// solves of iterative refinement, and the correction step x += d
+__global__ void widen_kernel(const float *src, double *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+__global__ void axpy_kernel(double *x, const double *d, int32_t n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += d[i];
 }
 
 }  // namespace
@@ -984,10 +999,26 @@ int solve_syncfree_grid(int *grid)
 
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol, const int32_t *Aslot,
                     const double *Ax, const double *b, const double *x, double *out,
-                    double *partial, int nblocks, void *stream)
+                    double *partial, int nblocks, void *stream, double *rvec)
 {
-    residual_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(n, Arp, Acol, Aslot, Ax, b, x, partial);
+    residual_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(n, Arp, Acol, Aslot, Ax, b, x, partial, rvec);
     residual_final_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nblocks, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_widen(const float *src, double *dst, int64_t n, void *stream)
+{
+    if (n <= 0) return 0;
+    const int64_t g = (n + 255) / 256;
+    widen_kernel<<<(unsigned)(g < 4096 ? g : 4096), 256, 0, (cudaStream_t)stream>>>(src, dst, n);
+    return (int)cudaGetLastError();
+}
+
+int launch_axpy(double *x, const double *d, int32_t n, void *stream)
+{
+    if (n <= 0) return 0;
+    const int g = (n + 255) / 256;
+    axpy_kernel<<<g < 4096 ? g : 4096, 256, 0, (cudaStream_t)stream>>>(x, d, n);
     return (int)cudaGetLastError();
 }
 

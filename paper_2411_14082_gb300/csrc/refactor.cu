@@ -100,8 +100,8 @@ __device__ __forceinline__ void find_slots(const int32_t *rows, const int (&lo0)
 // shuffles.
 constexpr int kWarpRun = 8;
 
-template <bool kWait, bool kDense>
-__device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int lane,
+template <typename R, bool kWait, bool kDense>
+__device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, int lane,
                          int epoch)
 {
     const int64_t beg = __ldg(a.LUp + k);
@@ -112,7 +112,7 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
     const bool dcol = kDense && k >= a.dense_p;
     const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
     const bool in_smem = len <= a.cap_short;
-    double *x = in_smem ? xs : a.LUx + beg;
+    R *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : a.LUi + beg;
     for (int i = lane; i < len; i += 32) {
         if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
@@ -122,7 +122,7 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
     {
         const int c = __ldg(a.Q + k);
         const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
-        for (int e = ab + lane; e < ae; e += 32) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
+        for (int e = ab + lane; e < ae; e += 32) x[__ldg(a.amap + e)] = (R)__ldg(a.Ax + e);
     }
     __syncwarp();
 
@@ -176,17 +176,17 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             continue;
         }
         if (w > 1) {   // triangle: lane q < w holds x(j+q)
-            double tv[kWarpRun - 1];
+            R tv[kWarpRun - 1];
 #pragma unroll
             for (int d = 0; d < kWarpRun - 1; d++) {
                 const long long lbd = __shfl_sync(kFull, m_lb, (q0 + d) & 31);
-                tv[d] = (d < w - 1 && lane > d && lane < w) ? __ldcg(a.LUx + lbd + (lane - d - 1)) : 0.0;
+                tv[d] = (d < w - 1 && lane > d && lane < w) ? __ldcg(a.LUx + lbd + (lane - d - 1)) : R(0);
             }
-            double v = lane < w ? x[t + lane] : 0.0;
+            R v = lane < w ? x[t + lane] : R(0);
 #pragma unroll
             for (int d = 0; d < kWarpRun - 1; d++) {
                 if (d < w - 1) {
-                    const double mv = __shfl_sync(kFull, v, d);
+                    const R mv = __shfl_sync(kFull, v, d);
                     if (lane > d && lane < w) v = fma(-tv[d], mv, v);
                 }
             }
@@ -201,7 +201,7 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
             bool bad = false;
             for (int r0 = 0; r0 < nR; r0 += 32 * kBatch) {
                 int sl[kBatch], key[kBatch], lo[kBatch], hi[kBatch];
-                double v[kBatch];
+                R v[kBatch];
 #pragma unroll
                 for (int u = 0; u < kBatch; u++) {
                     const int r = r0 + u * 32 + lane;
@@ -213,12 +213,12 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
 #pragma unroll
                 for (int u = 0; u < kBatch; u++) {
                     if (key[u] >= 0 && sl[u] < 0) bad = true;
-                    v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
+                    v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
                 for (int d = 0; d < w; d++) {
-                    const double mv = x[t + d];
+                    const R mv = x[t + d];
                     const long long lbd = __shfl_sync(kFull, m_lb, q0 + d);
-                    const double *lv = a.LUx + lbd + (w - 1 - d) + r0 + lane;
+                    const R *lv = a.LUx + lbd + (w - 1 - d) + r0 + lane;
 #pragma unroll
                     for (int u = 0; u < kBatch; u++)
                         if (sl[u] >= 0) v[u] = fma(-mv, __ldcg(lv + u * 32), v[u]);
@@ -237,24 +237,24 @@ __device__ bool col_warp(const RefactorArgs &a, int k, double *xs, int32_t *rs, 
     }
 
     if (dcol) {   // U above the block is final; rows >= dense_p go to the block
-        double *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
+        R *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
         if (in_smem)
             for (int i = lane; i < nD; i += 32) a.LUx[beg + i] = xs[i];
         for (int i = nD + lane; i < len; i += 32) Sc[i - nD] = x[i];
         return false;
     }
-    const double d = x[nU - 1];
-    double m = 0.0;
+    const R d = x[nU - 1];
+    R m = R(0);
     for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
     m = warp_max(m);
-    if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
+    if (!((d != R(0)) && (fabs(d) >= a.eps * m))) {
         if (lane == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
         }
         return false;
     }
-    const double inv = 1.0 / d;
+    const R inv = R(1) / d;
     if (in_smem) {
         for (int i = lane; i < len; i += 32) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
     } else {
@@ -312,16 +312,17 @@ struct RunDesc {
 };
 
 // shared state of one group (declared once per CTA, for up to two groups)
+template <typename R>
 struct GroupShared {
     RunDesc run[2];            // double buffered by run parity
-    double red[kWarps];
-    double tri[kTri];          // the leader's staged triangle, column d at tri_off(d)
+    R red[kWarps];
+    R tri[kTri];               // the leader's staged triangle, column d at tri_off(d)
     int stop;
 };
 
-template <bool kWait, bool kDense, int NW>
-__device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, int epoch, int g, int cap,
-                        GroupShared &sh)
+template <typename R, bool kWait, bool kDense, int NW>
+__device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, int epoch, int g, int cap,
+                        GroupShared<R> &sh)
 {
     static_assert(NW >= 2, "a group needs a leader and workers");
     constexpr int kT = NW * 32, kTw = (NW - 1) * 32;
@@ -333,13 +334,14 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     // before the block (its first dense_s0 rows); the block does the rest
     const bool dcol = kDense && k >= a.dense_p;
     const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
-    // up to cap entries: work vector and rows in shared memory; up to 2*cap:
-    // the rows alone (slot searches stay in shared memory), the work vector
-    // in place in global memory; longer: both in global memory
+    // up to cap entries: work vector and rows in shared memory; up to as many
+    // rows as the work-vector area holds (2*cap in double precision): the
+    // rows alone (slot searches stay in shared memory), the work vector in
+    // place in global memory; longer: both in global memory
     const bool in_smem = len <= cap;
-    const bool rows_smem = !in_smem && len <= 2 * cap;
+    const bool rows_smem = !in_smem && len <= cap * (int)(sizeof(R) / sizeof(int32_t));
     int32_t *rsw = reinterpret_cast<int32_t *>(xs);   // rows over the work-vector area
-    double *x = in_smem ? xs : a.LUx + beg;
+    R *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : (rows_smem ? rsw : a.LUi + beg);
     for (int i = tid; i < len; i += kT) {
         if (in_smem) rs[i] = __ldg(a.LUi + beg + i);
@@ -355,7 +357,7 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     {
         const int c = __ldg(a.Q + k);
         const int ab = __ldg(a.Ap + c), ae = __ldg(a.Ap + c + 1);
-        for (int e = ab + tid; e < ae; e += kT) x[__ldg(a.amap + e)] = __ldg(a.Ax + e);
+        for (int e = ab + tid; e < ae; e += kT) x[__ldg(a.amap + e)] = (R)__ldg(a.Ax + e);
     }
     group_sync<NW>(g);
 
@@ -420,20 +422,20 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
         const long long lbq = __shfl_sync(kFull, m_lb, (q0 + lane) & 31);   // lane d: dependency t+d
         if (w > 1) {   // triangle: column d of the run gives its first w-1-d L entries
             for (int d0 = 0; d0 < w - 1; d0 += 8) {   // eight loads in flight
-                double tv[8];
+                R tv[8];
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const long long lbd = __shfl_sync(kFull, lbq, (d0 + u) & 31);
-                    tv[u] = (d0 + u < w - 1 && lane < w - 1 - (d0 + u)) ? __ldcg(a.LUx + lbd + lane) : 0.0;
+                    tv[u] = (d0 + u < w - 1 && lane < w - 1 - (d0 + u)) ? __ldcg(a.LUx + lbd + lane) : R(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 8; u++)
                     if (d0 + u < w - 1 && lane < w - 1 - (d0 + u)) sh.tri[tri_off(d0 + u) + lane] = tv[u];
             }
             __syncwarp();
-            double v = lane < w ? x[t + lane] : 0.0;
+            R v = lane < w ? x[t + lane] : R(0);
             for (int d = 0; d < w - 1; ++d) {
-                const double mv = __shfl_sync(kFull, v, d);
+                const R mv = __shfl_sync(kFull, v, d);
                 if (lane > d && lane < w) v = fma(-sh.tri[tri_off(d) + lane - d - 1], mv, v);
             }
             if (lane < w) x[t + lane] = v;
@@ -481,12 +483,12 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
                 if (sl < 0) {
                     bad = true;
                 } else if (sl < hend) {
-                    double v = x[sl];
+                    R v = x[sl];
                     for (int d0 = 0; d0 < w; d0 += 8) {   // eight loads in flight
-                        double lv[8];
+                        R lv[8];
 #pragma unroll
                         for (int u = 0; u < 8; u++)
-                            lv[u] = d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : 0.0;
+                            lv[u] = d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : R(0);
 #pragma unroll
                         for (int u = 0; u < 8; u++)
                             if (d0 + u < w) v = fma(-x[t + d0 + u], lv[u], v);
@@ -505,7 +507,7 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
             const int wt = tid - 32;
             for (int r0 = 0; r0 < nR; r0 += kRows * kTw) {
                 int sl[kRows], key[kRows], lo[kRows], hi[kRows];
-                double v[kRows];
+                R v[kRows];
 #pragma unroll
                 for (int u = 0; u < kRows; u++) {
                     const int rr = r0 + u * kTw + wt;
@@ -518,12 +520,12 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
                 for (int u = 0; u < kRows; u++) {
                     if (key[u] >= 0 && sl[u] < 0) bad = true;
                     if (sl[u] >= 0 && sl[u] < hend) sl[u] = -1;   // the leader's
-                    v[u] = sl[u] >= 0 ? x[sl[u]] : 0.0;
+                    v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
 #pragma unroll 4
                 for (int d = 0; d < w; d++) {
-                    const double m = x[t + d];
-                    const double *lv = a.LUx + r.base[d] + r0 + wt;
+                    const R m = x[t + d];
+                    const R *lv = a.LUx + r.base[d] + r0 + wt;
 #pragma unroll
                     for (int u = 0; u < kRows; u++)
                         if (sl[u] >= 0) v[u] = fma(-m, __ldcg(lv + u * kTw), v[u]);
@@ -538,28 +540,28 @@ __device__ bool col_grp(const RefactorArgs &a, int k, double *xs, int32_t *rs, i
     }
 
     if (dcol) {   // U above the block is final; rows >= dense_p go to the block
-        double *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
+        R *Sc = a.S + (int64_t)(k - a.dense_p) * a.dense_ld;
         if (in_smem)
             for (int i = tid; i < nD; i += kT) a.LUx[beg + i] = xs[i];
         for (int i = nD + tid; i < len; i += kT) Sc[i - nD] = x[i];
         return false;
     }
-    const double d = x[nU - 1];
-    double m = 0.0;
+    const R d = x[nU - 1];
+    R m = R(0);
     for (int i = nU + tid; i < len; i += kT) m = fmax(m, fabs(x[i]));
     m = warp_max(m);
     if (lane == 0) sh.red[warp] = m;
     group_sync<NW>(g);
     m = sh.red[0];
     for (int w = 1; w < NW; w++) m = fmax(m, sh.red[w]);
-    if (!((d != 0.0) && (fabs(d) >= a.eps * m))) {
+    if (!((d != R(0)) && (fabs(d) >= a.eps * m))) {
         if (tid == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
         }
         return false;
     }
-    const double inv = 1.0 / d;
+    const R inv = R(1) / d;
     if (in_smem) {
         for (int i = tid; i < len; i += kT) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
     } else {
@@ -583,40 +585,40 @@ __global__ void begin_refactor_kernel(DevCtl *ctl)
 
 // One task of the schedule: one long column (whole CTA), two medium
 // columns (a half each) or up to 8 short ones (a warp each); true = stop.
-template <bool kWait, bool kDense>
-__device__ __forceinline__ bool run_task(const RefactorArgs &a, int tt, double *xs, int32_t *rs, int epoch,
-                                         GroupShared *s_grp)
+template <typename R, bool kWait, bool kDense>
+__device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *xs, int32_t *rs, int epoch,
+                                         GroupShared<R> *s_grp)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = __ldg(a.task_ptr + tt), c1 = __ldg(a.task_ptr + tt + 1);
     const int k0 = __ldg(a.task_cols + c0);
     const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
     if (c1 - c0 == 1 && len0 > a.cap_short)            // one long column: whole CTA
-        return col_grp<kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
+        return col_grp<R, kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
     if (c1 - c0 == 2 && len0 > a.cap_short) {          // two medium columns: a half each
         const int g = warp / (kWarps / 2);
         const int half = a.cap_long / 2;
-        const bool hs = col_grp<kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
+        const bool hs = col_grp<R, kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
                                                           rs + (size_t)g * half, epoch, g, half, s_grp[g]);
         return __syncthreads_or(hs);
     }
     bool ws = false;
     if (c0 + warp < c1)
-        ws = col_warp<kWait, kDense>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
+        ws = col_warp<R, kWait, kDense>(a, __ldg(a.task_cols + c0 + warp), xs + (size_t)warp * a.cap_short,
                                      rs + (size_t)warp * a.cap_short, lane, epoch);
     return __syncthreads_or(ws);
 }
 
 // Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
 // (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
-template <bool kWait, bool kDense>
-__global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs a, int epoch, int persistent)
+template <typename R, bool kWait, bool kDense>
+__global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgsT<R> a, int epoch, int persistent)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_quit;
-    __shared__ GroupShared s_grp[2];
-    double *xs = reinterpret_cast<double *>(smem);
-    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)a.cap_long * sizeof(double));
+    __shared__ GroupShared<R> s_grp[2];
+    R *xs = reinterpret_cast<R *>(smem);
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)a.cap_long * sizeof(R));
     for (int iter = 0;; ++iter) {
         if (threadIdx.x == 0) {
             s_t = persistent ? atomicAdd(&a.ctl->ticket, 1) : (iter == 0 ? (int)blockIdx.x : a.ntasks);
@@ -626,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
         const int t = s_t, quit = s_quit;
         __syncthreads();
         if (t >= a.ntasks || quit) break;
-        if (run_task<kWait, kDense>(a, a.task_begin + t, xs, rs, epoch, s_grp)) break;
+        if (run_task<R, kWait, kDense>(a, a.task_begin + t, xs, rs, epoch, s_grp)) break;
     }
 }
 
@@ -643,7 +645,7 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_skip;
-    __shared__ GroupShared s_grp[2];
+    __shared__ GroupShared<double> s_grp[2];
     double *xs = reinterpret_cast<double *>(smem);
     int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)sets[0].cap_long * sizeof(double));
     const long long total = (long long)ntasks * nsets;
@@ -665,7 +667,7 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
         // a local copy: stores through the work vector cannot alias it, so its
         // fields stay in registers instead of being reloaded from memory
         const RefactorArgs as = sets[t % nsets];
-        run_task<kWait, false>(as, task_begin + t / nsets, xs, rs, epoch, s_grp);
+        run_task<double, kWait, false>(as, task_begin + t / nsets, xs, rs, epoch, s_grp);
     }
 }
 
@@ -682,9 +684,10 @@ __global__ void begin_batch_kernel(DevCtl *ctl, int nsets, int32_t *ticket)
     if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
 }
 
-size_t task_smem(const RefactorArgs &a)
+template <typename R>
+size_t task_smem(const RefactorArgsT<R> &a)
 {
-    return (size_t)a.cap_long * (sizeof(double) + sizeof(int32_t));
+    return (size_t)a.cap_long * (sizeof(R) + sizeof(int32_t));
 }
 
 }  // namespace
@@ -698,16 +701,16 @@ int launch_begin_refactor(DevCtl *ctl, void *stream)
 int refactor_setup(int cap_long, int *blocks_per_sm)
 {
     const size_t sm = (size_t)cap_long * (sizeof(double) + sizeof(int32_t));
-    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<true, false>,
+    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<double, true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<false, false>,
+        e = cudaFuncSetAttribute(refactor_task_kernel<double, false, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<true, true>,
+        e = cudaFuncSetAttribute(refactor_task_kernel<double, true, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<false, true>,
+        e = cudaFuncSetAttribute(refactor_task_kernel<double, false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(refactor_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -715,9 +718,9 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
         e = cudaFuncSetAttribute(refactor_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     int b1 = 0, b2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<true, false>, kThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<double, true, false>, kThreads, sm);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<true, true>, kThreads, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<double, true, true>, kThreads, sm);
     *blocks_per_sm = b1 < b2 ? b1 : b2;
     return (int)e;
 }
@@ -746,17 +749,39 @@ int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
     return (int)cudaGetLastError();
 }
 
+int refactor_setup_f32(int cap_long, int *blocks_per_sm)
+{
+    const size_t sm = (size_t)cap_long * (sizeof(float) + sizeof(int32_t));
+    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<float, true, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(refactor_task_kernel<float, false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, refactor_task_kernel<float, true, false>,
+                                                              kThreads, sm);
+}
+
+int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int grid, int epoch, void *stream)
+{
+    if (a.ntasks <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pipeline) refactor_task_kernel<float, true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+    else refactor_task_kernel<float, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+    return (int)cudaGetLastError();
+}
+
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream)
 {
     if (a.ntasks <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
     const bool dense = a.dense_p < INT_MAX;   // a dense tail is in use
     if (pipeline) {
-        if (dense) refactor_task_kernel<true, true><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
-        else refactor_task_kernel<true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        if (dense) refactor_task_kernel<double, true, true><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        else refactor_task_kernel<double, true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
     } else {
-        if (dense) refactor_task_kernel<false, true><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
-        else refactor_task_kernel<false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        if (dense) refactor_task_kernel<double, false, true><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        else refactor_task_kernel<double, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
     }
     return (int)cudaGetLastError();
 }

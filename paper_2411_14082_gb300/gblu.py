@@ -37,7 +37,7 @@ EXPORTED = [
     "gblu_factorize", "gblu_refactorize", "gblu_solve", "gblu_residual", "gblu_get_stats",
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
-    "gblu_solve_batch",
+    "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -112,9 +112,13 @@ def load(build_if_missing: bool = True):
         lib.gblu_levels.restype = I32
         lib.gblu_refactorize_batch.argtypes = [P, I32, P, I64, P, I64, P, ctypes.POINTER(I32), P]
         lib.gblu_solve_batch.argtypes = [P, I32, P, I64, P, I64, P, I64, P]
+        lib.gblu_refactorize_f32.argtypes = [P, P, P, ctypes.POINTER(I32)]
+        lib.gblu_solve_refined.argtypes = [P, P, P, P, ctypes.c_double, I32, P, ctypes.POINTER(I32),
+                                           ctypes.POINTER(ctypes.c_double)]
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
-                  "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch"):
+                  "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
+                  "gblu_refactorize_f32", "gblu_solve_refined"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -260,6 +264,28 @@ class Solver:
                                        ctypes.c_void_p(b.data_ptr()), self.n, ctypes.c_void_p(x.data_ptr()),
                                        self.n, _stream(stream)))
         return x
+
+    def refactorize_f32(self, Ax, stream=None):
+        """Single-precision checked re-factorization; returns True if a pivot failed."""
+        failed = ctypes.c_int32(0)
+        _check(load().gblu_refactorize_f32(self._h, _dev_ptr(Ax, self.device, self.nnz), _stream(stream),
+                                           ctypes.byref(failed)))
+        return bool(failed.value)
+
+    def solve_refined(self, Ax, b, x=None, tol=1e-12, max_iter=10, stream=None):
+        """Iterative refinement on the single-precision factors (double fallback).
+
+        Returns (x, iters, berr); iters == -1 means the double fallback ran."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        it = ctypes.c_int32(0)
+        be = ctypes.c_double(0.0)
+        _check(load().gblu_solve_refined(self._h, _dev_ptr(Ax, self.device, self.nnz),
+                                         _dev_ptr(b, self.device, self.n), _dev_ptr(x, self.device, self.n),
+                                         float(tol), int(max_iter), _stream(stream), ctypes.byref(it),
+                                         ctypes.byref(be)))
+        return x, it.value, be.value
 
     def step_host(self, Ax, b, x, stream=None):
         """Refactorize + solve from host numpy float64 arrays (x is written)."""
