@@ -38,10 +38,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate of the profiling recipe (non-tensor 
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4": {"refactor_cu_sha256": "77213f434fa919a3edd95131e1d894033e4e8d95ae293e3ff1c4df6571ba9a7e",
-                          "bytes": 15.99e9 + 445.3e6},
-    "rc_mesh_120x120x4": {"refactor_cu_sha256": "77213f434fa919a3edd95131e1d894033e4e8d95ae293e3ff1c4df6571ba9a7e",
-                          "bytes": 135.9e6 + 82.8e6},
+    "rc_mesh_200x200x4": {"refactor_cu_sha256": "e6b9749761d2774e4e59eaaecf484b43d1dbca9969cb0904f1b34d9b6914f93b",
+                          "bytes": 16.366e9 + 444.4e6},
+    "rc_mesh_120x120x4": {"refactor_cu_sha256": "e6b9749761d2774e4e59eaaecf484b43d1dbca9969cb0904f1b34d9b6914f93b",
+                          "bytes": 135.0e6 + 82.4e6},
 }
 
 
@@ -405,6 +405,16 @@ def run_ours(args, rank, world, local_rank):
     t_ref = [ev_r[i][0].elapsed_time(ev_r[i][1]) / 1e3 for i in range(args.warmup, total)]
     t_sol = [ev_s[i][0].elapsed_time(ev_s[i][1]) / 1e3 for i in range(args.warmup, total)]
     resid = res[args.warmup:, 0].max().item()
+    fwd = None
+    if mixed:
+        # forward error of each refined result against the double-precision
+        # path on the same values (untimed)
+        fwd = 0.0
+        x64 = torch.empty_like(xs[0])
+        for i in range(args.warmup, total):
+            s.refactorize(vals[i])
+            s.solve(rhs[i], x64)
+            fwd = max(fwd, ((xs[i] - x64).abs().max() / x64.abs().max()).item())
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     hv = [torch.from_numpy(v).pin_memory().numpy() for v in w["vals"][args.warmup:]]
@@ -467,7 +477,8 @@ def run_ours(args, rank, world, local_rank):
         line["dtype"] = "f32 factors, f64 refinement"
         line["config"]["precision"] = "mixed"
         line["refinement"] = {"iters_mean": float(np.mean(t_iter)), "iters_max": int(max(t_iter)),
-                              "fallbacks": int(sum(1 for v in t_iter if v < 0))}
+                              "fallbacks": int(sum(1 for v in t_iter if v < 0)),
+                              "max_fwd_err_vs_f64": fwd}
         line["roofline"]["kernel"] = "refactor_f32 (single-precision checked re-factorization)"
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         line["roofline"]["peak"] = fp32_peak
