@@ -311,6 +311,109 @@ def run_batch(args, rank, world, local_rank):
     return 0
 
 
+def run_serve(args, rank, world, local_rank):
+    """Serving workload: closed-loop clients submit solve requests of three
+    circuits to one gblu server (resident patterns, continuous batching per
+    pattern, patterns overlapping on the device).  A step is one request per
+    client; the metric is completed requests per second (host wall clock)."""
+    import threading
+    import torch
+    from paper_2411_14082_gb300 import gblu
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    V = 8   # distinct value sets per pattern, reused cyclically
+    specs = [("rc_mesh_200x200x4", inputs.workload_mesh(), 4, "transistors"),
+             ("rc_mesh_120x120x4", inputs.workload_mesh(nx=120, ny=120, nz=4), 8, "transistors"),
+             ("mna_grid_40x50_vsrc20", inputs.workload_small(), 16, "elements")]
+    rng = np.random.default_rng(args.seed + 17 * rank)
+    pats = []
+    for name, ckt, clients, kind in specs:
+        n, Ap, Ai, Ax0 = ckt.csc()
+        Q = inputs.grid_nd_order(ckt)
+        vals, rhs = [], []
+        for _ in range(V):
+            ckt = inputs.redraw_transistors(ckt, rng) if kind == "transistors" else inputs.perturb_elements(ckt, rng)
+            vals.append(torch.from_numpy(ckt.values()).pin_memory().numpy())
+            rhs.append(torch.from_numpy(inputs.rhs(n, rng)).pin_memory().numpy())
+        pats.append(dict(name=name, n=n, Ap=Ap, Ai=Ai, Ax0=Ax0, Q=Q, clients=clients, vals=vals, rhs=rhs))
+    srv = gblu.Server(dev, hbm_budget=args.serve_budget_gb << 30, max_batch=args.serve_max_batch)
+    t0 = time.perf_counter()
+    for p in pats:
+        p["id"], p["slots"] = srv.add_pattern(p["n"], p["Ap"], p["Ai"], p["Q"], p["Ax0"])
+        p["footprint"] = srv.pattern_info(p["id"])["footprint_bytes"]
+    t_admit = time.perf_counter() - t0
+    lat = {p["name"]: [] for p in pats}
+    bsz = {p["name"]: [] for p in pats}
+    worst = [0.0]
+    bad = []
+    lock = threading.Lock()
+    start = threading.Barrier(sum(p["clients"] for p in pats) + 1)
+
+    def client(p, c):
+        x = torch.empty(p["n"], dtype=torch.float64).pin_memory().numpy()
+        mine, sizes, wb = [], [], 0.0
+        for i in range(args.warmup + args.steps):
+            if i == args.warmup:
+                start.wait()
+            j = (c + i) % V
+            _, r = srv.wait(srv.submit(p["id"], p["vals"][j], p["rhs"][j], x), timeout=600.0)
+            if r["status"] < 0:
+                bad.append(r["status"])
+            if i >= args.warmup:
+                mine.append(r["latency_s"])
+                sizes.append(r["batch_size"])
+                wb = max(wb, r["berr"])
+        with lock:
+            lat[p["name"]].extend(mine)
+            bsz[p["name"]].extend(sizes)
+            worst[0] = max(worst[0], wb)
+
+    threads = [threading.Thread(target=client, args=(p, c)) for p in pats for c in range(p["clients"])]
+    for t in threads:
+        t.start()
+    clocks = ClockSampler()
+    start.wait()
+    clocks.start()
+    t0 = time.perf_counter()
+    for t in threads:
+        t.join()
+    elapsed = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    done = sum(len(v) for v in lat.values())
+    allv = np.concatenate([np.array(v) for v in lat.values()])
+    per = {}
+    for p in pats:
+        a = np.array(lat[p["name"]])
+        per[p["name"]] = {"n": p["n"], "clients": p["clients"], "slots": p["slots"],
+                          "footprint_gb": p["footprint"] / 1e9, "requests": len(a),
+                          "requests_per_s": len(a) / elapsed,
+                          "latency_ms_p50": 1e3 * float(np.percentile(a, 50)),
+                          "latency_ms_p99": 1e3 * float(np.percentile(a, 99)),
+                          "mean_batch": float(np.mean(bsz[p["name"]]))}
+    line = {
+        "metric": "served requests/s", "value": world * done / elapsed, "unit": "requests/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve_3_circuits", "patterns": [p["name"] for p in pats],
+                   "clients": sum(p["clients"] for p in pats), "max_batch": args.serve_max_batch,
+                   "hbm_budget_gb": args.serve_budget_gb, "timing": "host wall clock, closed-loop clients",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "latency_ms_p50": 1e3 * float(np.percentile(allv, 50)),
+        "latency_ms_p99": 1e3 * float(np.percentile(allv, 99)),
+        "per_pattern": per, "max_rel_residual": worst[0], "residual_ok": bool(worst[0] <= 1e-12),
+        "errors": len(bad), "server": {k: st[k] for k in ("batches", "repivots", "max_batch_seen",
+                                                           "reserved_bytes")},
+        "admission_s": t_admit, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     oracle_proc = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -505,7 +608,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mesh", choices=["mesh", "small", "batch"])
+    ap.add_argument("--workload", default="mesh", choices=["mesh", "small", "batch", "serve"])
+    ap.add_argument("--serve-budget-gb", type=int, default=64, help="device memory budget of the serve workload")
+    ap.add_argument("--serve-max-batch", type=int, default=16)
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
                     help="mixed: single-precision refactor + refinement in double")
     ap.add_argument("--sets", type=int, default=256, help="value sets per step of the batch workload")
@@ -524,6 +629,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args, rank, world, local_rank)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

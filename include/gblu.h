@@ -49,6 +49,7 @@ extern "C" {
 #define GBLU_ERR_CUDA (-6)           /* a CUDA runtime call failed                  */
 #define GBLU_ERR_NOT_FACTORIZED (-7) /* refactorize/solve before a factorization    */
 #define GBLU_ERR_INTERNAL (-8)       /* a structural invariant check failed         */
+#define GBLU_ERR_BUSY (-9)           /* a server request has not finished yet       */
 
 /* Scheduling of the re-factorization (Section IV-B: cluster and pipeline modes). */
 #define GBLU_SCHED_AUTO 0     /* level-synchronous front, sync-free tail      */
@@ -270,6 +271,72 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
                                const double *Uval, const double *Udiag, const int32_t *piv,
                                const int32_t *q, const double *b_dev, double *x_dev,
                                int32_t *status_dev, void *stream);
+
+/*
+ * Solve server (this library's extension; the paper solves one matrix at a
+ * time).  A server on one device keeps one handle resident per registered
+ * pattern and answers requests "solve A x = b for these values of pattern
+ * p".  Per pattern a worker thread with its own stream takes the queued
+ * requests, up to the pattern's slot count, and runs them as one batch
+ * (gblu_refactorize_batch + gblu_solve_batch); requests that arrive while a
+ * batch runs go into the next one.  Patterns overlap on the device.  A
+ * request whose pivot check fails is redone with gblu_refactorize (restart
+ * with pivoting, Section IV-C), and the pattern keeps the new pivot
+ * sequence.  Each result is bit-for-bit the result of the same request run
+ * alone on a handle in the same pivot state.
+ *
+ * gblu_server_create: budget = device bytes the server may hold in total;
+ *   max_batch = most requests per batch; o = options of the handles (NULL:
+ *   defaults).
+ * gblu_server_add_pattern: analyze (Q may be NULL, as in gblu_analyze) and
+ *   factorize with pivoting on the first values Ax0_host (host, nnz(A), slot
+ *   order of Ai); then admits the pattern only if its footprint (handle:
+ *   structure, factors, workspace; plus batch buffers) fits in what is left
+ *   of the budget.  *slots = the largest batch that fits (<= max_batch).
+ *   Returns GBLU_ERR_NOMEM when even one slot does not fit, or the error of
+ *   the analysis or factorization.  Synchronizes the device.
+ * gblu_server_submit: queues a request.  Ax_host (nnz(A), slot order),
+ *   b_host (n) and x_host (n) are host arrays owned by the caller and must
+ *   stay valid until the request is waited for; x_host receives the
+ *   solution.  Pinned host memory makes the copies asynchronous.
+ * gblu_server_wait: waits up to timeout_s seconds (0: poll).  Returns
+ *   GBLU_OK and fills *res (then the request id is released), or
+ *   GBLU_ERR_BUSY if it has not finished.  res->status is the request's own
+ *   outcome: GBLU_OK, GBLU_REPIVOTED or an error code.
+ * gblu_server_destroy: finishes every queued request, stops the workers and
+ *   frees all device memory of the server.
+ * Errors of these calls are described by gblu_server_last_error().
+ */
+typedef struct gblu_server_s *gblu_server;
+
+typedef struct {
+    int32_t status;      /* GBLU_OK, GBLU_REPIVOTED or an error code              */
+    int32_t repivoted;   /* 1 if its check failed and it was redone with pivoting */
+    int32_t batch_size;  /* requests in the batch it ran in                       */
+    int32_t pattern;
+    double berr;         /* ||b - A x||inf / (||A||inf ||x||inf); -1 on error     */
+    double queue_s;      /* submit -> start of its batch (host clock)             */
+    double latency_s;    /* submit -> solution in x_host (host clock)             */
+} gblu_request_result;
+
+typedef struct {
+    int64_t budget_bytes, reserved_bytes;
+    int32_t n_patterns;
+    int32_t max_batch_seen;
+    int64_t submitted, completed, batches, repivots;
+} gblu_server_stats;
+
+const char *gblu_server_last_error(void);
+int gblu_server_create(gblu_server *s, int device, int64_t hbm_budget_bytes, int32_t max_batch,
+                       const gblu_opts *o);
+int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                            const double *Ax0_host, int32_t *pattern, int32_t *slots);
+int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes);
+int gblu_server_submit(gblu_server s, int32_t pattern, const double *Ax_host, const double *b_host,
+                       double *x_host, int64_t *request);
+int gblu_server_wait(gblu_server s, int64_t request, double timeout_s, gblu_request_result *res);
+int gblu_server_get_stats(gblu_server s, gblu_server_stats *st);
+void gblu_server_destroy(gblu_server s);
 
 /* Sizes and counters of the current factorization (host struct). */
 typedef struct {

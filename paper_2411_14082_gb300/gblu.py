@@ -26,6 +26,7 @@ ERR_DEVICE_TIMEOUT = -5
 ERR_CUDA = -6
 ERR_NOT_FACTORIZED = -7
 ERR_INTERNAL = -8
+ERR_BUSY = -9
 
 SCHED = {"auto": 0, "level": 1, "syncfree": 2}
 
@@ -38,6 +39,8 @@ EXPORTED = [
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined",
+    "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
+    "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -68,6 +71,19 @@ class Stats(ctypes.Structure):
                 ("n_repivot", ctypes.c_int64), ("n_restart_cols", ctypes.c_int64),
                 ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("repivoted", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("pattern", ctypes.c_int32), ("berr", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
+                ("n_patterns", ctypes.c_int32), ("max_batch_seen", ctypes.c_int32),
+                ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("repivots", ctypes.c_int64)]
 
 
 def library_path() -> str:
@@ -115,6 +131,19 @@ def load(build_if_missing: bool = True):
         lib.gblu_refactorize_f32.argtypes = [P, P, P, ctypes.POINTER(I32)]
         lib.gblu_solve_refined.argtypes = [P, P, P, P, ctypes.c_double, I32, P, ctypes.POINTER(I32),
                                            ctypes.POINTER(ctypes.c_double)]
+        lib.gblu_server_last_error.argtypes = []
+        lib.gblu_server_last_error.restype = ctypes.c_char_p
+        lib.gblu_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, I64, I32, ctypes.POINTER(Opts)]
+        lib.gblu_server_add_pattern.argtypes = [P, I32, P, P, P, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        lib.gblu_server_pattern_info.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)]
+        lib.gblu_server_submit.argtypes = [P, I32, P, P, P, ctypes.POINTER(I64)]
+        lib.gblu_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(RequestResult)]
+        lib.gblu_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.gblu_server_destroy.argtypes = [P]
+        lib.gblu_server_destroy.restype = None
+        for f in ("gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
+                  "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats"):
+            getattr(lib, f).restype = ctypes.c_int
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
@@ -377,3 +406,90 @@ def levels(n, Up, Ui):
     nl = load().gblu_levels(int(n), _np_ptr(Up), _np_ptr(Ui), _np_ptr(lv))
     _check(int(nl) if nl < 0 else 0)
     return lv, int(nl)
+
+
+def _check_server(code):
+    if code < 0:
+        raise GbluError(code, load().gblu_server_last_error().decode())
+    return code
+
+
+class Server:
+    """Solve server on one device (gblu_server_*): patterns stay resident,
+    concurrent requests of one pattern are batched, patterns overlap.
+
+    Requests take host numpy arrays; the server keeps references to them
+    until the request is waited for."""
+
+    def __init__(self, device=0, hbm_budget=16 << 30, max_batch=64, pivot_tol=1e-3):
+        lib = load()
+        o = Opts()
+        lib.gblu_default_opts(ctypes.byref(o))
+        o.pivot_tol = pivot_tol
+        s = ctypes.c_void_p()
+        _check_server(lib.gblu_server_create(ctypes.byref(s), int(device), int(hbm_budget), int(max_batch),
+                                             ctypes.byref(o)))
+        self._s = s
+        self.device = int(device)
+        self._pat = {}      # pattern id -> (n, nnz)
+        self._live = {}     # request id -> (Ax, b, x) kept alive
+
+    def add_pattern(self, n, Ap, Ai, Q, Ax0):
+        """Register a pattern with its first values; returns (pattern id, slots)."""
+        Ap, Ai = _i32(Ap), _i32(Ai)
+        q = None if Q is None else _i32(Q)
+        Ax0 = np.ascontiguousarray(Ax0, dtype=np.float64)
+        pid, slots = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check_server(load().gblu_server_add_pattern(self._s, int(n), _np_ptr(Ap), _np_ptr(Ai),
+                                                     None if q is None else _np_ptr(q), _np_ptr(Ax0),
+                                                     ctypes.byref(pid), ctypes.byref(slots)))
+        self._pat[pid.value] = (int(n), int(Ap[-1]))
+        return pid.value, slots.value
+
+    def pattern_info(self, pattern):
+        slots, fp = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check_server(load().gblu_server_pattern_info(self._s, int(pattern), ctypes.byref(slots),
+                                                      ctypes.byref(fp)))
+        return {"slots": slots.value, "footprint_bytes": fp.value}
+
+    def submit(self, pattern, Ax, b, x=None):
+        """Queue a request; returns its id.  x (host float64[n]) receives the solution."""
+        n, nnz = self._pat[pattern]
+        Ax = np.ascontiguousarray(Ax, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if Ax.size != nnz or b.size != n:
+            raise ValueError(f"expected {nnz} values and {n} right-hand-side entries")
+        if x is None:
+            x = np.empty(n, np.float64)
+        if x.dtype != np.float64 or not x.flags.c_contiguous or x.size != n:
+            raise ValueError("x must be a contiguous float64 array of n entries")
+        rid = ctypes.c_int64(0)
+        _check_server(load().gblu_server_submit(self._s, int(pattern), _np_ptr(Ax), _np_ptr(b), _np_ptr(x),
+                                                ctypes.byref(rid)))
+        self._live[rid.value] = (Ax, b, x)
+        return rid.value
+
+    def wait(self, request, timeout=60.0):
+        """Wait for a request; returns (x, result dict).  Raises GbluError
+        (code ERR_BUSY) if it has not finished within the timeout."""
+        r = RequestResult()
+        _check_server(load().gblu_server_wait(self._s, int(request), float(timeout), ctypes.byref(r)))
+        _, _, x = self._live.pop(request)
+        return x, {f: getattr(r, f) for f, _ in RequestResult._fields_}
+
+    def stats(self):
+        st = ServerStats()
+        _check_server(load().gblu_server_get_stats(self._s, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().gblu_server_destroy(self._s)
+            self._s = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

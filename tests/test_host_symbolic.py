@@ -152,3 +152,16 @@ def test_invalid_patterns_rejected_on_host():
         gblu.column_etree(2, np.array([0, 2, 2]), np.array([1, 1]))   # duplicate
     with pytest.raises(gblu.GbluError):
         gblu.order_mindeg(2, np.array([1, 1, 2]), np.array([0, 1]))   # Ap[0] != 0
+
+
+def test_server_argument_errors_without_a_device():
+    """Host-side argument checks of the solve server (no device needed)."""
+    import ctypes
+    lib = gblu.load()
+    s = ctypes.c_void_p()
+    assert lib.gblu_server_create(ctypes.byref(s), 0, 0, 4, None) == gblu.ERR_INVALID_INPUT
+    assert lib.gblu_server_create(ctypes.byref(s), 0, 1 << 30, 0, None) == gblu.ERR_INVALID_INPUT
+    assert lib.gblu_server_create(ctypes.byref(s), 999, 1 << 30, 4, None) == gblu.ERR_CUDA
+    assert b"not available" in lib.gblu_server_last_error()
+    assert lib.gblu_server_submit(None, 0, None, None, None, None) == gblu.ERR_INVALID_INPUT
+    lib.gblu_server_destroy(None)
