@@ -150,6 +150,18 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream,
                      int32_t *repivoted);
 
 /*
+ * gblu_refactorize with the pivot check of step force_col treated as failed
+ * whatever its value (force_col = -1: none), so that the restart runs from
+ * that step: the protocol of the paper's general-case evaluation (Section
+ * VI-A), where selected runs re-pivot at a random row.  With unchanged
+ * values the restart keeps the previous pivots.  A step inside the dense
+ * tail block (dense_min_rows > 0) is not forced.  Returns as
+ * gblu_refactorize; GBLU_ERR_INVALID_INPUT if force_col is outside [-1, n).
+ */
+int gblu_refactorize_forced(gblu_handle h, const double *Ax_dev, void *stream, int32_t force_col,
+                            int32_t *repivoted);
+
+/*
  * Solve A x = b with the current factors: y = L^-1 P b, z = U^-1 y,
  * x(Q) = z (Algorithm 2 and the parallel solve of Section V).  b_dev and
  * x_dev are device float64[n]; they may alias.  Asynchronous on `stream`.
@@ -358,6 +370,10 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle                */
     int64_t kernel_launches; /* kernels this handle has launched so far      */
     int32_t dense_rows;   /* rows of the dense tail block (0: none)          */
+    /* last factorization with pivoting (first factorization or restart),
+     * host wall clock: tail kernel, download and repack of the factors,
+     * schedule rebuild, upload of the new structure */
+    double tail_kernel_ms, tail_repack_ms, tail_schedule_ms, tail_upload_ms;
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

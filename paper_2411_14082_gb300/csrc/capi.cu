@@ -2,6 +2,7 @@
 // checked re-factorization with restart, solve, residual, stats and export.
 // The orchestration runs on the host; every numerical step runs in the
 // kernels of kernels.cu.
+#include <chrono>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,6 +79,8 @@ struct gblu_ctx {
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0;
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
+    int32_t force_col = -1;                        // forced check failure of the next refactorization
+    double t_tail[4] = {0, 0, 0, 0};               // last tail run: kernel, repack, schedule, upload (ms)
     bool analyzed = false, factorized = false;
     Pattern P;
     Structure S;
@@ -122,6 +125,8 @@ struct gblu_ctx {
     // restart (tail factorization)
     DBuf<int32_t> seq, restart, done, tpiv, tpinv, cnu, cnl, smark, slist, sclass;
     DBuf<int64_t> cbeg;
+    DBuf<int32_t> sflag;
+    DBuf<unsigned> sbits;
     DBuf<double> sx;
 };
 
@@ -212,8 +217,11 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     sp.min_entries = h->opts.solve_dense_min;
     sp.slices = h->opts.solve_slices;
     sp.max_piece = kMaxPieceRows;
+    const auto t_s = std::chrono::steady_clock::now();
     build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, sp,
                    h->opts.dense_min_rows, h->W);
+    const auto t_u = std::chrono::steady_clock::now();
+    h->t_tail[2] = std::chrono::duration<double, std::milli>(t_u - t_s).count();
     for (int32_t v : h->W.amap)
         if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
     const int32_t n = h->S.n;
@@ -267,6 +275,7 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->utstart, h->W.utstart, st));
     // host vectors are uploaded asynchronously: keep them alive until done
     CU(cudaStreamSynchronize(st));
+    h->t_tail[3] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_u).count();
     return GBLU_OK;
 }
 
@@ -295,6 +304,7 @@ RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
     a.cap_short = kRefCapShort;
     a.cap_long = kRefCapLong;
     a.eps = h->opts.pivot_tol;
+    a.force_col = h->force_col;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
     return a;
@@ -349,7 +359,7 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
 // Algorithm 1 when rmask holds every step); the other steps keep their
 // current columns.  Rebuilds the structure and the schedule afterwards.
 int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<uint8_t> &rmask,
-             size_t pool_hint)
+             size_t pool_hint, bool keep_if_same = false)
 {
     const Pattern &P = h->P;
     const int32_t n = P.n;
@@ -392,9 +402,18 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     CK(ensure(h, h->smark, (size_t)slots * n));
     CK(ensure(h, h->slist, (size_t)slots * n));
     CK(ensure(h, h->sclass, (size_t)slots * n));
+    const bool bits_smem = n <= kTailSmemBits;
+    const size_t words = ((size_t)n + 31) / 32;
+    if (!bits_smem) CK(ensure(h, h->sbits, (size_t)slots * words));
     // pool after the canonical columns
     size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>(2 * restart_len, (int64_t)P.Ai.size())) +
                   (size_t)n;
+    using TClock = std::chrono::steady_clock;
+    auto ms_since = [](TClock::time_point t) {
+        return std::chrono::duration<double, std::milli>(TClock::now() - t).count();
+    };
+    CU(cudaStreamSynchronize(st));
+    const TClock::time_point t_k = TClock::now();
     for (int attempt = 0; attempt < 8; attempt++) {
         const size_t need = (size_t)nnz + pool;
         if (h->rows.cap < need || h->vals.cap < need) {
@@ -417,6 +436,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         KL(launch_begin_tail(h->ctl, (unsigned long long)nnz, st));
         KL(launch_tail_init(n, h->restart.p, h->piv.p, h->tpinv.p, h->tpiv.p, h->done.p, h->tail_epoch, st));
         CU(cudaMemsetAsync(h->smark.p, 0, (size_t)slots * n * sizeof(int32_t), st));
+        if (!bits_smem) CU(cudaMemsetAsync(h->sbits.p, 0, (size_t)slots * words * sizeof(unsigned), st));
         TailArgs t{};
         t.n = n;
         t.Ap = h->Ap.p;
@@ -442,6 +462,8 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         t.smark = h->smark.p;
         t.slist = h->slist.p;
         t.sclass = h->sclass.p;
+        t.sbits = bits_smem ? nullptr : h->sbits.p;
+        t.bits_in_smem = bits_smem ? 1 : 0;
         t.eps = h->opts.pivot_tol;
         t.spin_limit = h->opts.spin_limit;
         t.ctl = h->ctl;
@@ -455,6 +477,30 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         break;
     }
     if (h->hctl->status != 0) return fail(GBLU_ERR_NOMEM, "restart pool could not be sized");
+    h->t_tail[0] = ms_since(t_k);
+    const TClock::time_point t_r = TClock::now();
+    if (keep_if_same && (int32_t)S.piv.size() == n) {
+        // every pivot kept: the structure and schedule stay; only the values
+        // of the recomputed columns move from the pool to their slots
+        std::vector<int32_t> tp(n);
+        CU(cudaMemcpyAsync(tp.data(), h->tpiv.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (tp == S.piv) {
+            CK(ensure(h, h->sflag, 1));
+            CU(cudaMemsetAsync(h->sflag.p, 0, sizeof(int32_t), st));
+            KL(launch_pool_scatter(h->seq.p, (int32_t)nR, h->cbeg.p, h->cnu.p, h->cnl.p, h->rows.p, h->LUp.p,
+                                   h->LUi.p, h->pinv.p, n, h->vals.p, h->sflag.p, st));
+            int32_t bad = 0;
+            CU(cudaMemcpyAsync(&bad, h->sflag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            if (!bad) {
+                h->n_restart_cols = nR;
+                h->t_tail[1] = ms_since(t_r);
+                h->t_tail[2] = h->t_tail[3] = 0.0;
+                return GBLU_OK;
+            }
+        }
+    }
     const unsigned long long top = h->hctl->pool_top;
     // ---- download and repack into the new canonical structure
     std::vector<int32_t> tpiv(n), rows(top);
@@ -509,6 +555,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
             return fail(GBLU_ERR_INTERNAL, "restart: diagonal misplaced in column %d", k);
     }
     h->n_restart_cols = nR;
+    h->t_tail[1] = ms_since(t_r);
     CK(install_structure(h, std::move(S2), &V2, st));
     return GBLU_OK;
 }
@@ -525,7 +572,7 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
     std::vector<uint8_t> finished(n), rmask(n);
     for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
     gblu_restart_set(n, h->P.cetree.data(), finished.data(), rmask.data());
-    return run_tail(h, Ax, st, rmask, 0);
+    return run_tail(h, Ax, st, rmask, 0, true);
 }
 
 int check_handle(gblu_ctx *h)
@@ -590,6 +637,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
     if (e == cudaSuccess && r == 0) r = dense_piece_setup(kMaxPieceRows);
     if (e == cudaSuccess && r == 0) r = dense_setup(GBLU_DENSE_MAX_ROWS);
+    if (e == cudaSuccess && r == 0) r = tail_setup();
     if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
         const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
         if (h->hctl) cudaFreeHost(h->hctl);
@@ -733,6 +781,19 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     CK(run_tail(h, Ax_dev, st, all, hint));
     h->factorized = true;
     return GBLU_OK;
+}
+
+int gblu_refactorize_forced(gblu_handle h, const double *Ax_dev, void *stream, int32_t force_col,
+                            int32_t *repivoted)
+{
+    CK(check_handle(h));
+    if (repivoted) *repivoted = 0;
+    if (force_col < -1 || force_col >= h->P.n)
+        return fail(GBLU_ERR_INVALID_INPUT, "force_col %d outside [-1, n)", force_col);
+    h->force_col = force_col;
+    const int rc = gblu_refactorize(h, Ax_dev, stream, repivoted);
+    h->force_col = -1;
+    return rc;
 }
 
 int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t *repivoted)
@@ -1090,6 +1151,10 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->device_bytes = (int64_t)h->device_bytes;
     s->kernel_launches = h->launches;
     s->dense_rows = h->W.dense_m;
+    s->tail_kernel_ms = h->t_tail[0];
+    s->tail_repack_ms = h->t_tail[1];
+    s->tail_schedule_ms = h->t_tail[2];
+    s->tail_upload_ms = h->t_tail[3];
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

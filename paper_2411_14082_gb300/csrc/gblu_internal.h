@@ -128,7 +128,7 @@ struct DevCtl {
     int32_t tail_epoch;   // epoch of the tail factorization done flags
     int32_t tail_ticket;
     int32_t abort_tail;   // singular / overflow seen by the tail kernel
-    int32_t pad;
+    int32_t tail_frontier; // every step below it is final in this tail run
     unsigned long long pool_top;  // next free slot of the tail pool
     int32_t where;        // diagnostic: which wait timed out
     int32_t where_k;
@@ -157,6 +157,7 @@ struct RefactorArgsT {
     int32_t task_begin, ntasks;     // tasks of this launch
     int32_t cap_short, cap_long;    // shared-memory work vector entries (warp / CTA)
     double eps;
+    int32_t force_col = -1;         // evaluation aid: this column's check fails
     long long spin_limit;
     DevCtl *ctl;
 };
@@ -183,6 +184,8 @@ struct TailArgs {
     // per-CTA scratch
     double *sx;
     int32_t *smark, *slist, *sclass;
+    unsigned *sbits;                // per-CTA step bitmap when it does not fit in shared memory
+    int32_t bits_in_smem;           // 1: the bitmap is the kernel's dynamic shared memory
     double eps;
     long long spin_limit;
     DevCtl *ctl;
@@ -224,6 +227,11 @@ int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
+int tail_setup();
+constexpr int32_t kTailSmemBits = 1 << 19;   // steps whose bitmap fits in shared memory
+int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, const int32_t *cnu,
+                        const int32_t *cnl, const int32_t *prow, const int64_t *LUp, const int32_t *LUi,
+                        const int32_t *pinv, int32_t n, double *vals, int32_t *bad, void *stream);
 // dense tail of the re-factorization (dense.cu)
 struct DenseArgs2 {
     double *S;                      // m x m, column-major, leading dimension ld

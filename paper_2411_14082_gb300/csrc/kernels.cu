@@ -41,7 +41,7 @@ using namespace dev;
 // is a dependency).  Then threshold pivoting with the preferred row, exactly
 // as the oracle defines it, and the column is appended to the pool.
 __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
-                            int32_t *list, int32_t *cls, int epoch)
+                            int32_t *list, int32_t *cls, unsigned *bm, int epoch)
 {
     __shared__ int s_cnt, s_found, s_mode, s_stop;
     __shared__ double r_m[kTailThreads / 32], r_ba[kTailThreads / 32];
@@ -64,7 +64,89 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         }
     }
     __syncthreads();
+    // x(rows of L(:,jd)) -= x(piv[jd]) * L(:,jd); rows new to the structure
+    // whose step is final and below `fk` are entered in the step bitmap
+    auto apply_dep = [&](int jd, int fk) {
+        const int pr = __ldcg(a.piv + jd);
+        const double xj = x[pr];
+        const int64_t b = __ldcg(a.cbeg + jd) + __ldcg(a.cnu + jd);
+        const int64_t e_end = b + __ldcg(a.cnl + jd);
+        for (int64_t e = b + tid; e < e_end; e += kTailThreads) {
+            const int r = __ldcg(a.rows + e);
+            const double v = __ldcg(a.vals + e);
+            if (mark[r] != stamp) {
+                mark[r] = stamp;
+                x[r] = 0.0;
+                list[atomicAdd(&s_cnt, 1)] = r;
+                const int sr = __ldcg(a.pinv + r);
+                if (sr > jd && sr < fk) atomicOr(bm + (sr >> 5), 1u << (sr & 31));
+            }
+            x[r] = fma(-xj, v, x[r]);
+        }
+    };
     int j = __ldg(a.clo + k);
+    // ---- steps below the done frontier: every such step is final, so the
+    // dependencies among them are the steps of the rows in the structure
+    // (row -> step map), taken in ascending order from a bitmap
+    if (warp == 0) {
+        int f = ld_acquire(&a.ctl->tail_frontier);
+        for (long long it = 0; f < k && it < a.n; it++) {
+            const int jj = f + lane;
+            const bool ok = jj < a.n && ld_acquire(a.done + jj) == epoch;
+            const unsigned bb = __ballot_sync(kFull, ok);
+            if (bb == kFull) {
+                f += 32;
+                continue;
+            }
+            f += __ffs(~bb) - 1;
+            break;
+        }
+        if (lane == 0) {
+            __threadfence();
+            atomicMax(&a.ctl->tail_frontier, f);
+            s_found = f;
+        }
+    }
+    __syncthreads();
+    const int fk = min(s_found, k);
+    if (fk > j) {
+        for (int i = tid; i < s_cnt; i += kTailThreads) {
+            const int sr = __ldcg(a.pinv + list[i]);
+            if (sr >= j && sr < fk) atomicOr(bm + (sr >> 5), 1u << (sr & 31));
+        }
+        __syncthreads();
+        int cur = j;
+        for (;;) {
+            if (warp == 0) {
+                int found = fk;
+                for (int wb = cur >> 5; wb * 32 < fk; wb += 32) {
+                    const int w = wb + lane;
+                    unsigned v = w * 32 < fk ? *(const volatile unsigned *)(bm + w) : 0u;
+                    if (w == (cur >> 5)) v &= ~0u << (cur & 31);
+                    const unsigned nz = __ballot_sync(kFull, v != 0u);
+                    if (nz) {
+                        const int l = __ffs(nz) - 1;
+                        const unsigned vv = __shfl_sync(kFull, v, l);
+                        found = min((wb + l) * 32 + __ffs(vv) - 1, fk);
+                        break;
+                    }
+                }
+                if (lane == 0) {
+                    s_found = found;
+                    if (found < fk) atomicAnd(bm + (found >> 5), ~(1u << (found & 31)));
+                }
+            }
+            __syncthreads();
+            const int jd = s_found;
+            if (jd >= fk) break;
+            apply_dep(jd, fk);
+            __syncthreads();
+            cur = jd + 1;
+        }
+        j = fk;
+    }
+    // ---- steps at or above the frontier, in increasing order: wait for an
+    // unfinished one (its pivot decides whether it is a dependency)
     while (j < k) {
         if (warp == 0) {
             int found = k, mode = 0;
@@ -111,24 +193,7 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
             j = found;
             continue;
         }
-        // apply dependency `found`
-        {
-            const int jd = found;
-            const int pr = __ldcg(a.piv + jd);
-            const double xj = x[pr];
-            const int64_t b = __ldcg(a.cbeg + jd) + __ldcg(a.cnu + jd);
-            const int64_t e_end = b + __ldcg(a.cnl + jd);
-            for (int64_t e = b + tid; e < e_end; e += kTailThreads) {
-                const int r = __ldcg(a.rows + e);
-                const double v = __ldcg(a.vals + e);
-                if (mark[r] != stamp) {
-                    mark[r] = stamp;
-                    x[r] = 0.0;
-                    list[atomicAdd(&s_cnt, 1)] = r;
-                }
-                x[r] = fma(-xj, v, x[r]);
-            }
-        }
+        apply_dep(found, 0);
         __syncthreads();
         j = found + 1;
     }
@@ -252,6 +317,7 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
 __global__ void begin_tail_kernel(DevCtl *ctl, unsigned long long pool_base)
 {
     ctl->tail_ticket = 0;
+    ctl->tail_frontier = 0;
     ctl->abort_tail = 0;
     ctl->status = 0;
     ctl->pool_top = pool_base;
@@ -272,11 +338,16 @@ __global__ void tail_init_kernel(int32_t n, const int32_t *restart, const int32_
 
 __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoch)
 {
+    extern __shared__ unsigned s_bits[];
     __shared__ int s_t, s_quit;
     double *x = a.sx + (size_t)blockIdx.x * a.n;
     int32_t *mark = a.smark + (size_t)blockIdx.x * a.n;
     int32_t *list = a.slist + (size_t)blockIdx.x * a.n;
     int32_t *cls = a.sclass + (size_t)blockIdx.x * a.n;
+    const int words = (a.n + 31) >> 5;
+    unsigned *bm = a.bits_in_smem ? s_bits : a.sbits + (size_t)blockIdx.x * words;
+    if (a.bits_in_smem)   // the global bitmap is cleared by the host
+        for (int w = threadIdx.x; w < words; w += kTailThreads) s_bits[w] = 0u;
     for (;;) {
         if (threadIdx.x == 0) {
             s_t = atomicAdd(&a.ctl->tail_ticket, 1);
@@ -286,7 +357,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoc
         const int t = s_t, quit = s_quit;
         __syncthreads();
         if (t >= a.nseq || quit) break;
-        if (tail_column(a, __ldg(a.seq + t), x, mark, list, cls, epoch)) break;
+        if (tail_column(a, __ldg(a.seq + t), x, mark, list, cls, bm, epoch)) break;
     }
 }
 
@@ -843,7 +914,58 @@ __global__ void axpy_kernel(double *x, const double *d, int32_t n)
 
 }  // namespace
 
+// After a restart that kept every pivot, the factor structure is the old
+// one (the pattern is fixed by the pattern of A and the pivot order), so the
+// recomputed columns only move their values from the pool into their
+// canonical slots.  One warp per restarted step k: the pool holds U entries
+// as step ids and L entries as original rows; each goes to the slot of its
+// step in the sorted canonical column.  Any mismatch sets *bad (the caller
+// then rebuilds the structure instead).
+__global__ void pool_scatter_kernel(const int32_t *seq, int32_t nseq, const int64_t *cbeg, const int32_t *cnu,
+                                    const int32_t *cnl, const int32_t *prow, const int64_t *LUp,
+                                    const int32_t *LUi, const int32_t *pinv, int32_t n, double *vals, int32_t *bad)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = w; t < nseq; t += nw) {
+        const int k = __ldg(seq + t);
+        const int64_t b = cbeg[k];
+        const int nu = cnu[k], nl = cnl[k];
+        const int64_t lo = __ldg(LUp + k);
+        const int len = (int)(__ldg(LUp + k + 1) - lo);
+        if (nu + nl != len) {
+            if (lane == 0) atomicExch(bad, 1);
+            continue;
+        }
+        for (int e = lane; e < len; e += 32) {
+            const int r = prow[b + e];
+            const int s = e < nu ? r : ((unsigned)r < (unsigned)n ? __ldg(pinv + r) : -1);
+            int a = 0, z = len;   // first slot with LUi >= s
+            while (a < z) {
+                const int m = (a + z) >> 1;
+                if (__ldg(LUi + lo + m) < s) a = m + 1;
+                else z = m;
+            }
+            if (s < 0 || a >= len || __ldg(LUi + lo + a) != s) atomicExch(bad, 1);
+            else vals[lo + a] = vals[b + e];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
+int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, const int32_t *cnu,
+                        const int32_t *cnl, const int32_t *prow, const int64_t *LUp, const int32_t *LUi,
+                        const int32_t *pinv, int32_t n, double *vals, int32_t *bad, void *stream)
+{
+    if (nseq <= 0) return 0;
+    int grid = (nseq + 7) / 8;
+    if (grid > 4096) grid = 4096;
+    pool_scatter_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(seq, nseq, cbeg, cnu, cnl, prow, LUp, LUi, pinv, n,
+                                                                 vals, bad);
+    return (int)cudaGetLastError();
+}
+
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream)
 {
     begin_tail_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, pool_base);
@@ -858,10 +980,17 @@ int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_
     return (int)cudaGetLastError();
 }
 
+int tail_setup()
+{
+    return (int)cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kTailSmemBits / 8));
+}
+
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream)
 {
     if (a.nseq <= 0) return 0;
-    tail_kernel<<<grid, kTailThreads, 0, (cudaStream_t)stream>>>(a, epoch);
+    const size_t smem = a.bits_in_smem ? (size_t)((a.n + 31) >> 5) * sizeof(unsigned) : 0;
+    tail_kernel<<<grid, kTailThreads, smem, (cudaStream_t)stream>>>(a, epoch);
     return (int)cudaGetLastError();
 }
 

@@ -247,7 +247,7 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
     R m = R(0);
     for (int i = nU + lane; i < len; i += 32) m = fmax(m, fabs(x[i]));
     m = warp_max(m);
-    if (!((d != R(0)) && (fabs(d) >= a.eps * m))) {
+    if (!((d != R(0)) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
         if (lane == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
@@ -554,7 +554,7 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
     group_sync<NW>(g);
     m = sh.red[0];
     for (int w = 1; w < NW; w++) m = fmax(m, sh.red[w]);
-    if (!((d != R(0)) && (fabs(d) >= a.eps * m))) {
+    if (!((d != R(0)) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
         if (tid == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);

@@ -38,7 +38,7 @@ EXPORTED = [
     "gblu_factorize", "gblu_refactorize", "gblu_solve", "gblu_residual", "gblu_get_stats",
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
-    "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined",
+    "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -70,7 +70,9 @@ class Stats(ctypes.Structure):
                 ("etree_height", ctypes.c_int32), ("n_refactor", ctypes.c_int64),
                 ("n_repivot", ctypes.c_int64), ("n_restart_cols", ctypes.c_int64),
                 ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32),
+                ("tail_kernel_ms", ctypes.c_double), ("tail_repack_ms", ctypes.c_double),
+                ("tail_schedule_ms", ctypes.c_double), ("tail_upload_ms", ctypes.c_double)]
 
 
 class RequestResult(ctypes.Structure):
@@ -113,6 +115,7 @@ def load(build_if_missing: bool = True):
         lib.gblu_analyze.argtypes = [P, I32, P, P, P]
         lib.gblu_factorize.argtypes = [P, P, P]
         lib.gblu_refactorize.argtypes = [P, P, P, ctypes.POINTER(I32)]
+        lib.gblu_refactorize_forced.argtypes = [P, P, P, I32, ctypes.POINTER(I32)]
         lib.gblu_solve.argtypes = [P, P, P, P]
         lib.gblu_residual.argtypes = [P, P, P, P, P, P]
         lib.gblu_step_host.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
@@ -147,7 +150,7 @@ def load(build_if_missing: bool = True):
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
-                  "gblu_refactorize_f32", "gblu_solve_refined"):
+                  "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -244,6 +247,13 @@ class Solver:
         rep = ctypes.c_int32(0)
         rc = _check(load().gblu_refactorize(self._h, _dev_ptr(Ax, self.device, self.nnz),
                                             _stream(stream), ctypes.byref(rep)))
+        return rc, bool(rep.value)
+
+    def refactorize_forced(self, Ax, force_col, stream=None):
+        """refactorize with the check of step force_col failing (re-pivoting protocol)."""
+        rep = ctypes.c_int32(0)
+        rc = _check(load().gblu_refactorize_forced(self._h, _dev_ptr(Ax, self.device, self.nnz),
+                                                   _stream(stream), int(force_col), ctypes.byref(rep)))
         return rc, bool(rep.value)
 
     def solve(self, b, x=None, stream=None):
