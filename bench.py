@@ -64,6 +64,10 @@ def make_workload(name, n_steps, seed, mesh=(200, 200, 4)):
     if name == "mesh":
         ckt = inputs.workload_mesh(nx=mesh[0], ny=mesh[1], nz=mesh[2])
         desc = f"rc_mesh_{mesh[0]}x{mesh[1]}x{mesh[2]}"
+    elif name == "mesh_ill":
+        # the same mesh with every conductance log-uniform in [1e-9, 1e4] S
+        ckt = inputs.workload_mesh(nx=mesh[0], ny=mesh[1], nz=mesh[2], g_range=(1e-9, 1e4))
+        desc = f"rc_mesh_ill_{mesh[0]}x{mesh[1]}x{mesh[2]}"
     elif name == "small":
         ckt = inputs.workload_small()
         desc = "mna_grid_40x50_vsrc20"
@@ -80,7 +84,7 @@ def make_workload(name, n_steps, seed, mesh=(200, 200, 4)):
     rng = np.random.default_rng(seed)
     vals, rhs = [], []
     for s in range(n_steps):
-        if name == "mesh":
+        if name in ("mesh", "mesh_ill"):
             ckt = inputs.redraw_transistors(ckt, rng)
             vals.append(ckt.values())
         elif name == "batch":
@@ -304,6 +308,102 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None},
         "single_path": {"value": single, "unit": METRIC,
                         "note": "the same sets one at a time through gblu_refactorize + gblu_solve"},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_uneven(args, rank, world, local_rank):
+    """Uneven-pattern batch: 64 MNA grids with n log-uniform in [1k, 50k];
+    every step re-factorizes all of them with new values in one launch
+    (gblu_refactorize_multi) and solves each."""
+    import torch
+    from paper_2411_14082_gb300 import gblu
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(args.seed + 17 * rank)
+    V = 4   # value sets per pattern, reused cyclically
+    pats = []
+    t0 = time.perf_counter()
+    for i, nt in enumerate(np.exp(rng.uniform(np.log(1000), np.log(50000), args.patterns))):
+        side = max(8, int(round(np.sqrt(nt - 20))))
+        ny = max(8, int(round((nt - 20) / side)))
+        ckt = inputs.mna_grid2d(side, ny, seed=args.seed + 1000 + i)
+        n, Ap, Ai, Ax0 = ckt.csc()
+        Q = inputs.grid_nd_order(ckt)
+        s = gblu.Solver(dev)
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(torch.from_numpy(Ax0).cuda(dev))
+        vals, rhs = [], []
+        for _ in range(V):
+            ckt = inputs.perturb_elements(ckt, rng)
+            vals.append(torch.from_numpy(ckt.values()).cuda(dev))
+            rhs.append(torch.from_numpy(inputs.rhs(n, rng)).cuda(dev))
+        st = s.stats()
+        pats.append(dict(s=s, n=n, vals=vals, rhs=rhs, flops=st["flops"], x=torch.empty(n, dtype=torch.float64,
+                                                                                         device=f"cuda:{dev}")))
+    t_setup = time.perf_counter() - t0
+    solvers = [p["s"] for p in pats]
+    stream = torch.cuda.current_stream(dev)
+    total = args.warmup + args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(total)]
+    reps = 0
+    for i in range(total):
+        if i == args.warmup:
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler()
+            clocks.start()
+        j = i % V
+        ev[i][0].record(stream)
+        reps += sum(gblu.refactorize_multi(solvers, [p["vals"][j] for p in pats]))
+        ev[i][1].record(stream)
+        gblu.solve_multi(solvers, [p["rhs"][j] for p in pats], [p["x"] for p in pats])
+        ev[i][2].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t_rf = [ev[i][0].elapsed_time(ev[i][1]) / 1e3 for i in range(args.warmup, total)]
+    t_sv = [ev[i][1].elapsed_time(ev[i][2]) / 1e3 for i in range(args.warmup, total)]
+    t_all = sum(ev[i][0].elapsed_time(ev[i][2]) / 1e3 for i in range(args.warmup, total))
+    res = torch.zeros(4, dtype=torch.float64, device=f"cuda:{dev}")
+    worst = 0.0
+    j = (total - 1) % V
+    for p in pats:
+        p["s"].residual(p["vals"][j], p["rhs"][j], p["x"], out=res)
+        worst = max(worst, float(res[0].item()))
+    # the same systems one handle at a time, for context (not the metric)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        j = (args.warmup + i) % V
+        for p in pats:
+            p["s"].refactorize(p["vals"][j])
+            p["s"].solve(p["rhs"][j], p["x"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    single = len(pats) * args.steps / (e0.elapsed_time(e1) / 1e3)
+    F = sum(p["flops"] for p in pats)
+    ns = [p["n"] for p in pats]
+    line = {
+        "metric": "refactor+solve/s (systems)", "value": world * len(pats) * args.steps / t_all,
+        "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"uneven_{len(pats)}_mna_grids", "patterns": len(pats),
+                   "n_min": int(min(ns)), "n_max": int(max(ns)), "n_total": int(sum(ns)),
+                   "refactor_gflop_per_step": F / 1e9,
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "max_rel_residual": worst, "residual_ok": bool(worst <= 1e-12), "repivots": int(reps),
+        "phases_ms": {"refactor_multi": 1e3 * float(np.mean(t_rf)), "solves": 1e3 * float(np.mean(t_sv)),
+                      "setup_s": t_setup},
+        "roofline": {"kernel": "refactor_multi (one launch, all patterns)", "bound": "alu",
+                     "achieved": F / float(np.mean(t_rf)) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": F / float(np.mean(t_rf)) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None},
+        "single_path": {"value": single, "unit": "systems/s",
+                        "note": "the same systems one handle at a time (gblu_refactorize + gblu_solve)"},
         "clocks": clk,
     }
     if rank == 0:
@@ -637,7 +737,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mesh", choices=["mesh", "small", "batch", "serve"])
+    ap.add_argument("--workload", default="mesh", choices=["mesh", "mesh_ill", "small", "batch", "serve", "uneven"])
+    ap.add_argument("--patterns", type=int, default=64, help="patterns of the uneven workload")
     ap.add_argument("--serve-budget-gb", type=int, default=64, help="device memory budget of the serve workload")
     ap.add_argument("--serve-max-batch", type=int, default=16)
     ap.add_argument("--repivot-frac", type=float, default=0.0,
@@ -662,6 +763,8 @@ def main():
         return run_batch(args, rank, world, local_rank)
     if args.workload == "serve":
         return run_serve(args, rank, world, local_rank)
+    if args.workload == "uneven":
+        return run_uneven(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

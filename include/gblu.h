@@ -205,6 +205,26 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
                      void *stream);
 
 /*
+ * Batch over handles of DIFFERENT patterns (this library's extension): the
+ * checked re-factorization of Algorithms 3 and 4 for every handle hs[i]
+ * with its own values Ax_dev[i] (device, its analyze slot order), into that
+ * handle's own factors, in one persistent launch.  The handles' tasks share
+ * one ticket queue: each handle's tasks keep their topological order and
+ * the handles are interleaved so that they advance at the same relative
+ * pace.  A handle whose check fails then restarts alone, as in
+ * gblu_refactorize (Section IV-C); repivoted (optional, host int32[nh]) is
+ * 1 for those.  All handles must be factorized, distinct and on one device.
+ * The launch runs on `stream` and the call synchronizes it once (plus once
+ * per restart).  Results equal those of gblu_refactorize on each handle.
+ * gblu_solve_multi: gblu_solve for every handle, b_dev[i] -> x_dev[i],
+ * asynchronous on `stream`.
+ */
+int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_dev, void *stream,
+                           int32_t *repivoted);
+int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, double *const *x_dev,
+                     void *stream);
+
+/*
  * Mixed precision (this library's extension; the paper factors in double).
  *
  * gblu_refactorize_f32: the checked re-factorization of Algorithms 3 and 4

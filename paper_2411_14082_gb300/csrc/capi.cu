@@ -2,6 +2,7 @@
 // checked re-factorization with restart, solve, residual, stats and export.
 // The orchestration runs on the host; every numerical step runs in the
 // kernels of kernels.cu.
+#include <queue>
 #include <chrono>
 #include <cuda_runtime.h>
 
@@ -127,6 +128,12 @@ struct gblu_ctx {
     DBuf<int64_t> cbeg;
     DBuf<int32_t> sflag;
     DBuf<unsigned> sbits;
+    // multi-pattern batches led by this handle: merged ticket order, cached
+    // for the handles (and structure versions) it was built for
+    DBuf<SetTask> morder;
+    std::vector<std::pair<const void *, uint64_t>> morder_key;
+    int64_t morder_n = 0;
+    uint64_t struct_version = 0;
     DBuf<double> sx;
 };
 
@@ -209,6 +216,7 @@ int status_code(gblu_ctx *h)
 int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st)
 {
     h->S = std::move(S);
+    h->struct_version++;
     h->f32_valid = false;
     const int resident_warps = h->ref_blocks_per_sm * h->sm_count * (kRefThreads / 32);
     SolveSplit sp;
@@ -993,6 +1001,104 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, st);
+}
+
+int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_dev, void *stream,
+                           int32_t *repivoted)
+{
+    if (nh < 1 || !hs || !Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "multi: nh >= 1 and non-null arrays");
+    for (int32_t i = 0; i < nh; i++) {
+        CK(check_handle(hs[i]));
+        if (!hs[i]->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "multi: handle %d is not factorized", i);
+        if (!Ax_dev[i]) return fail(GBLU_ERR_INVALID_INPUT, "multi: null values for handle %d", i);
+        if (hs[i]->device != hs[0]->device) return fail(GBLU_ERR_INVALID_INPUT, "multi: handles on different devices");
+        if (repivoted) repivoted[i] = 0;
+    }
+    {
+        std::vector<const void *> u(hs, hs + nh);
+        std::sort(u.begin(), u.end());
+        if (std::adjacent_find(u.begin(), u.end()) != u.end())
+            return fail(GBLU_ERR_INVALID_INPUT, "multi: a handle appears twice");
+    }
+    gblu_ctx *h0 = hs[0];
+    DeviceGuard g(h0->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // one epoch for every set (epochs only grow, so old flags never match)
+    int32_t ep = 0;
+    for (int32_t i = 0; i < nh; i++) ep = std::max(ep, hs[i]->epoch);
+    ep++;
+    // merged ticket order: every set's tasks in its own (topological) order,
+    // interleaved so that all sets advance at the same relative pace
+    std::vector<std::pair<const void *, uint64_t>> key(nh);
+    for (int32_t i = 0; i < nh; i++) key[i] = {hs[i], hs[i]->struct_version};
+    if (key != h0->morder_key || !h0->morder.p) {
+        std::vector<int64_t> T(nh);
+        int64_t total = 0;
+        for (int32_t i = 0; i < nh; i++) total += (T[i] = (int64_t)hs[i]->W.task_ptr.size() - 1);
+        if (total > INT32_MAX) return fail(GBLU_ERR_INVALID_INPUT, "multi: too many tasks");
+        std::vector<SetTask> ord;
+        ord.reserve(total);
+        using Item = std::pair<double, int32_t>;   // (next key, set)
+        std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+        std::vector<int64_t> next(nh, 0);
+        for (int32_t i = 0; i < nh; i++)
+            if (T[i] > 0) pq.push({0.5 / (double)T[i], i});
+        while (!pq.empty()) {
+            const int32_t i = pq.top().second;
+            pq.pop();
+            ord.push_back({i, (int32_t)next[i]});
+            if (++next[i] < T[i]) pq.push({((double)next[i] + 0.5) / (double)T[i], i});
+        }
+        CK(upload(h0, h0->morder, ord, st));
+        h0->morder_key = key;
+        h0->morder_n = total;
+    }
+    CK(ensure(h0, h0->bargs, (size_t)nh));
+    CK(ensure(h0, h0->bticket, 1));
+    h0->bargs_host.resize(nh);
+    for (int32_t i = 0; i < nh; i++) {
+        gblu_ctx *h = hs[i];
+        h->epoch = ep;
+        h->n_refactor++;
+        RefactorArgs a = refactor_args(h, Ax_dev[i]);
+        a.dense_p = INT_MAX;   // the dense tail is not used in batches
+        h0->bargs_host[i] = a;
+    }
+    CU(cudaMemcpyAsync(h0->bargs.p, h0->bargs_host.data(), sizeof(RefactorArgs) * nh, cudaMemcpyHostToDevice, st));
+    {
+        gblu_ctx *h = h0;   // the launch is counted on the leading handle
+        KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, h0->ref_grid,
+                                 ep, h0->bticket.p, st));
+        h->launches++;   // the control-block reset kernel
+    }
+    for (int32_t i = 0; i < nh; i++)
+        CU(cudaMemcpyAsync(hs[i]->hctl, hs[i]->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // sets whose check failed restart alone (Section IV-C)
+    for (int32_t i = 0; i < nh; i++) {
+        gblu_ctx *h = hs[i];
+        if (h->hctl->status != 0) {
+            h->factorized = false;
+            return fail(h->hctl->status, "multi: handle %d: device status %d", i, h->hctl->status);
+        }
+        h->last_first_bad = h->hctl->interrupted ? h->hctl->first_bad : -1;
+        if (!h->hctl->interrupted) continue;
+        h->n_repivot++;
+        const int rc = run_restart(h, Ax_dev[i], st);
+        if (rc != GBLU_OK) {
+            h->factorized = false;
+            return rc;
+        }
+        if (repivoted) repivoted[i] = 1;
+    }
+    return GBLU_OK;
+}
+
+int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, double *const *x_dev, void *stream)
+{
+    if (nh < 1 || !hs || !b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "multi: nh >= 1 and non-null arrays");
+    for (int32_t i = 0; i < nh; i++) CK(gblu_solve(hs[i], b_dev[i], x_dev[i], stream));
+    return GBLU_OK;
 }
 
 int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed)

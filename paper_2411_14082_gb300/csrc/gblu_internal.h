@@ -136,6 +136,11 @@ struct DevCtl {
 
 #define GBLU_INTERNAL_POOL_FULL (-100)
 
+// one ticket of a batch over sets of different patterns: task `task` of set `set`
+struct SetTask {
+    int32_t set, task;
+};
+
 // R: the value type of the factors being computed (double; float for the
 // single-precision factorization of the mixed-precision solve)
 template <typename R>
@@ -223,6 +228,8 @@ int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int 
 int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
                           int grid, int epoch, int32_t *ticket, void *stream);
+int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
+                          int npairs, int grid, int epoch, int32_t *ticket, void *stream);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);

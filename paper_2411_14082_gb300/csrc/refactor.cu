@@ -641,21 +641,24 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
 template <bool kWait>
 __global__ void __launch_bounds__(kThreads, 2)
 refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
-                      int32_t *ticket)
+                      int32_t *ticket, const SetTask *order)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_skip;
     __shared__ GroupShared<double> s_grp[2];
     double *xs = reinterpret_cast<double *>(smem);
     int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)sets[0].cap_long * sizeof(double));
-    const long long total = (long long)ntasks * nsets;
+    // ticket t: task t / nsets of set t % nsets, or, with an order array
+    // (sets of different patterns), the (set, task) pair order[t]
+    const long long total = order ? (long long)ntasks : (long long)ntasks * nsets;
     for (int iter = 0;; ++iter) {
         if (threadIdx.x == 0) {
             const long long t = persistent ? (long long)atomicAdd(ticket, 1) : (iter == 0 ? (long long)blockIdx.x : total);
             s_t = t < total ? (int)t : -1;
             s_skip = 0;
             if (t < total) {
-                const DevCtl *c = sets[(int)(t % nsets)].ctl;
+                const int si = order ? __ldg(&order[t].set) : (int)(t % nsets);
+                const DevCtl *c = sets[si].ctl;
                 s_skip = ld_volatile(&c->interrupted) || ld_volatile(&c->status);
             }
         }
@@ -664,11 +667,28 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
         __syncthreads();
         if (t < 0) break;
         if (skip) continue;
+        const int si = order ? __ldg(&order[t].set) : t % nsets;
+        const int task = order ? __ldg(&order[t].task) : task_begin + t / nsets;
         // a local copy: stores through the work vector cannot alias it, so its
         // fields stay in registers instead of being reloaded from memory
-        const RefactorArgs as = sets[t % nsets];
-        run_task<double, kWait, false>(as, task_begin + t / nsets, xs, rs, epoch, s_grp);
+        const RefactorArgs as = sets[si];
+        run_task<double, kWait, false>(as, task, xs, rs, epoch, s_grp);
     }
+}
+
+// control blocks of sets that each have their own (multi-pattern batches)
+__global__ void begin_multi_kernel(const RefactorArgs *sets, int nsets, int32_t *ticket)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsets; s += gridDim.x * blockDim.x) {
+        DevCtl *c = sets[s].ctl;
+        c->ticket = 0;
+        c->interrupted = 0;
+        c->first_bad = INT_MAX;
+        c->status = 0;
+        c->where = 0;
+        c->where_k = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
 }
 
 __global__ void begin_batch_kernel(DevCtl *ctl, int nsets, int32_t *ticket)
@@ -739,13 +759,25 @@ int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
     cudaStream_t st = (cudaStream_t)stream;
     if (pipeline) {
         refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, a0.task_begin,
-                                                                           a0.ntasks, epoch, 1, ticket);
+                                                                           a0.ntasks, epoch, 1, ticket, nullptr);
     } else {
         const long long blocks = (long long)a0.ntasks * nsets;
         if (blocks > INT_MAX) return (int)cudaErrorInvalidValue;
         refactor_batch_kernel<false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
-            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket);
+            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr);
     }
+    return (int)cudaGetLastError();
+}
+
+int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
+                          int npairs, int grid, int epoch, int32_t *ticket, void *stream)
+{
+    if (npairs <= 0 || nsets <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int g = (nsets + 255) / 256;
+    begin_multi_kernel<<<g, 256, 0, st>>>(sets_dev, nsets, ticket);
+    refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
+                                                                       order_dev);
     return (int)cudaGetLastError();
 }
 

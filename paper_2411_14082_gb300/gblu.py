@@ -39,6 +39,7 @@ EXPORTED = [
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
+    "gblu_refactorize_multi", "gblu_solve_multi",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -116,6 +117,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_factorize.argtypes = [P, P, P]
         lib.gblu_refactorize.argtypes = [P, P, P, ctypes.POINTER(I32)]
         lib.gblu_refactorize_forced.argtypes = [P, P, P, I32, ctypes.POINTER(I32)]
+        lib.gblu_refactorize_multi.argtypes = [I32, P, P, P, P]
+        lib.gblu_solve_multi.argtypes = [I32, P, P, P, P]
         lib.gblu_solve.argtypes = [P, P, P, P]
         lib.gblu_residual.argtypes = [P, P, P, P, P, P]
         lib.gblu_step_host.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
@@ -150,7 +153,8 @@ def load(build_if_missing: bool = True):
         for f in ("gblu_create", "gblu_analyze", "gblu_factorize", "gblu_refactorize", "gblu_step_host",
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
-                  "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced"):
+                  "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
+                  "gblu_refactorize_multi", "gblu_solve_multi"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -417,6 +421,35 @@ def levels(n, Up, Ui):
     _check(int(nl) if nl < 0 else 0)
     return lv, int(nl)
 
+
+
+def refactorize_multi(solvers, Ax_list, stream=None):
+    """One launch re-factorizing several handles of different patterns, each
+    with its own values (gblu_refactorize_multi).  Returns the per-handle
+    repivoted flags."""
+    nh = len(solvers)
+    if nh != len(Ax_list) or nh == 0:
+        raise ValueError("one value array per solver")
+    dev = solvers[0].device
+    hs = (ctypes.c_void_p * nh)(*[s._h for s in solvers])
+    ax = (ctypes.c_void_p * nh)(*[_dev_ptr(a, dev, s.nnz) for s, a in zip(solvers, Ax_list)])
+    rep = (ctypes.c_int32 * nh)()
+    _check(load().gblu_refactorize_multi(nh, hs, ax, _stream(stream), rep))
+    return [bool(v) for v in rep]
+
+
+def solve_multi(solvers, b_list, x_list=None, stream=None):
+    """gblu_solve for every handle; returns the solutions."""
+    import torch
+    nh = len(solvers)
+    if x_list is None:
+        x_list = [torch.empty_like(b) for b in b_list]
+    dev = solvers[0].device
+    hs = (ctypes.c_void_p * nh)(*[s._h for s in solvers])
+    bp = (ctypes.c_void_p * nh)(*[_dev_ptr(b, dev, s.n) for s, b in zip(solvers, b_list)])
+    xp = (ctypes.c_void_p * nh)(*[_dev_ptr(x, dev, s.n) for s, x in zip(solvers, x_list)])
+    _check(load().gblu_solve_multi(nh, hs, bp, xp, _stream(stream)))
+    return x_list
 
 def _check_server(code):
     if code < 0:

@@ -117,3 +117,63 @@ def test_batch_argument_errors():
     assert failed.tolist() == [0]
     with pytest.raises(ValueError):
         s.solve_batch(LUx, dev(np.zeros((2, n))))
+
+
+def multi_cases():
+    out = []
+    for (nx, ny, seed) in ((10, 12, 1), (20, 25, 2), (30, 30, 3), (40, 50, 4), (16, 60, 5)):
+        ckt = inputs.mna_grid2d(nx, ny, seed=seed)
+        n, Ap, Ai, Ax0 = ckt.csc()
+        out.append((ckt, n, Ap, Ai, Ax0, inputs.grid_nd_order(ckt)))
+    ckt = inputs.rc_mesh3d(14, 14, 3, seed=6, n_fet=30)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    out.append((ckt, n, Ap, Ai, Ax0, inputs.grid_nd_order(ckt)))
+    return out
+
+
+def test_multi_pattern_batch_equals_single_handles():
+    cases = multi_cases()
+    rng = np.random.default_rng(21)
+
+    def handles():
+        hs = []
+        for ckt, n, Ap, Ai, Ax0, Q in cases:
+            s = gblu.Solver(DEV)
+            s.analyze(n, Ap, Ai, Q)
+            s.factorize(dev(Ax0))
+            hs.append(s)
+        return hs
+
+    multi, single = handles(), handles()
+    lus = [O.factorize(c[1], c[2], c[3], c[4], c[5], 1e-3) for c in cases]
+    for step in range(3):
+        vals = [inputs.perturb_elements(c[0], rng, frac=0.05, sigma=0.2).values() for c in cases]
+        rhs = [inputs.rhs(c[1], rng) for c in cases]
+        if step == 2:
+            # pattern 3 gets a pivot that fails its check (the others do not)
+            ckt, n, Ap, Ai, Ax0, Q = cases[3]
+            ref = O.refactorize(lus[3], Ap, Ai, vals[3])
+            k = n // 2
+            while True:
+                c = Q[k]
+                rows = Ai[Ap[c]:Ap[c + 1]]
+                hit = np.nonzero(rows == lus[3].piv[k])[0]
+                if len(hit) and ref.Lp[k + 1] > ref.Lp[k]:
+                    break
+                k += 1
+            vals[3] = vals[3].copy()
+            vals[3][Ap[c] + hit[0]] -= ref.Ux[ref.Up[k + 1] - 1] * (1.0 - 1e-9)
+        reps = gblu.refactorize_multi(multi, [dev(v) for v in vals])
+        xm = [x.cpu().numpy() for x in gblu.solve_multi(multi, [dev(b) for b in rhs])]
+        for i, (c, s) in enumerate(zip(cases, single)):
+            _, rep = s.refactorize(dev(vals[i]))
+            assert rep == reps[i]
+            xs = s.solve(dev(rhs[i])).cpu().numpy()
+            assert np.array_equal(xs, xm[i]), f"pattern {i} differs from its single handle"
+            lus[i] = O.refactorize(lus[i], c[2], c[3], vals[i])
+            compare_factors(multi[i].export_factors(), lus[i], 1e-10)
+            assert O.residual(c[1], c[2], c[3], vals[i], xm[i], rhs[i]) <= 1e-12
+        if step == 2:
+            assert reps[3] and sum(reps) == 1 + sum(reps[i] for i in range(len(cases)) if i != 3)
+    with pytest.raises(gblu.GbluError):
+        gblu.refactorize_multi([multi[0], multi[0]], [dev(cases[0][4])] * 2)
