@@ -133,6 +133,12 @@ struct gblu_ctx {
     DBuf<SetTask> morder;
     std::vector<std::pair<const void *, uint64_t>> morder_key;
     int64_t morder_n = 0;
+    DBuf<SetTask> mlorder, muorder;   // merged row tickets of multi-pattern solves
+    std::vector<std::pair<const void *, uint64_t>> msolve_key;
+    int64_t mlorder_n = 0, muorder_n = 0;
+    DBuf<SolveArgs> margs;
+    std::vector<SolveArgs> margs_host;
+    DBuf<int32_t> mticket;
     uint64_t struct_version = 0;
     DBuf<double> sx;
 };
@@ -833,26 +839,15 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
 // both triangular solves of nsets systems on the installed structure: set s
 // with factor values LUx + s*lu_stride, right-hand side b_dev + s*b_stride,
 // solution x_dev + s*x_stride
-static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const double *b_dev, int64_t b_stride,
-                        double *x_dev, int64_t x_stride, int32_t nsets, cudaStream_t st)
+// solve arguments of one system on the handle's structure (the row-block
+// fields are set per triangle by the caller)
+static SolveArgs solve_args(gblu_ctx *h, const double *LUx, const double *b_dev, double *x_dev)
 {
-    const int32_t n = h->S.n;
-    if (nsets > 1) {   // per-set intermediate vectors
-        if ((int64_t)n * nsets > INT_MAX) return fail(GBLU_ERR_INVALID_INPUT, "batch too large");
-        CK(ensure(h, h->y, (size_t)n * nsets));
-        CK(ensure(h, h->z, (size_t)n * nsets));
-        CK(ensure(h, h->ext_l, (size_t)n * nsets));
-        CK(ensure(h, h->ext_u, (size_t)n * nsets));
-    }
-    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n * nsets, st));
     SolveArgs a{};
-    a.n = n;
+    a.n = h->S.n;
     a.LUx = LUx;
-    a.nsets = nsets;
-    a.lu_stride = lu_stride;
-    a.b_stride = b_stride;
-    a.x_stride = x_stride;
-    a.v_stride = n;
+    a.nsets = 1;
+    a.v_stride = h->S.n;
     a.Lrp = h->Lrp.p;
     a.Urp = h->Urp.p;
     a.Lcol = h->Lcol.p;
@@ -868,6 +863,26 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
     a.x = x_dev;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
+    return a;
+}
+
+static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const double *b_dev, int64_t b_stride,
+                        double *x_dev, int64_t x_stride, int32_t nsets, cudaStream_t st)
+{
+    const int32_t n = h->S.n;
+    if (nsets > 1) {   // per-set intermediate vectors
+        if ((int64_t)n * nsets > INT_MAX) return fail(GBLU_ERR_INVALID_INPUT, "batch too large");
+        CK(ensure(h, h->y, (size_t)n * nsets));
+        CK(ensure(h, h->z, (size_t)n * nsets));
+        CK(ensure(h, h->ext_l, (size_t)n * nsets));
+        CK(ensure(h, h->ext_u, (size_t)n * nsets));
+    }
+    KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n * nsets, st));
+    SolveArgs a = solve_args(h, LUx, b_dev, x_dev);
+    a.nsets = nsets;
+    a.lu_stride = lu_stride;
+    a.b_stride = b_stride;
+    a.x_stride = x_stride;
     const Schedule &W = h->W;
     // sparse part (rows [0, lp0) / [0, up0)) in row blocks: block levels
     // before the dividing level one launch each, the rest one sync-free launch
@@ -1097,7 +1112,96 @@ int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_
 int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, double *const *x_dev, void *stream)
 {
     if (nh < 1 || !hs || !b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "multi: nh >= 1 and non-null arrays");
-    for (int32_t i = 0; i < nh; i++) CK(gblu_solve(hs[i], b_dev[i], x_dev[i], stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    // handles whose solve is all sparse row blocks go into one launch per
+    // triangle; the others (trailing dense pieces) are solved one by one
+    std::vector<gblu_ctx *> fused;
+    std::vector<int32_t> fi;
+    for (int32_t i = 0; i < nh; i++) {
+        gblu_ctx *h = hs[i];
+        CK(check_handle(h));
+        if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "multi: handle %d is not factorized", i);
+        if (!b_dev[i] || !x_dev[i]) return fail(GBLU_ERR_INVALID_INPUT, "multi: null vector for handle %d", i);
+        if (h->device != hs[0]->device) return fail(GBLU_ERR_INVALID_INPUT, "multi: handles on different devices");
+        if (h->W.lcut.size() > 1 || h->W.ucut.size() > 1) {
+            CK(gblu_solve(h, b_dev[i], x_dev[i], stream));
+        } else {
+            fused.push_back(h);
+            fi.push_back(i);
+        }
+    }
+    {
+        std::vector<const void *> u(hs, hs + nh);
+        std::sort(u.begin(), u.end());
+        if (std::adjacent_find(u.begin(), u.end()) != u.end())
+            return fail(GBLU_ERR_INVALID_INPUT, "multi: a handle appears twice");
+    }
+    const int32_t nf = (int32_t)fused.size();
+    if (nf == 0) return GBLU_OK;
+    gblu_ctx *h0 = fused[0];
+    DeviceGuard g(h0->device);
+    std::vector<std::pair<const void *, uint64_t>> key(nf);
+    for (int32_t i = 0; i < nf; i++) key[i] = {fused[i], fused[i]->struct_version};
+    if (key != h0->msolve_key || !h0->mlorder.p) {
+        // every set's rows in its own ticket order, interleaved by relative progress
+        auto merge = [&](bool lower, DBuf<SetTask> &out, int64_t &count) -> int {
+            std::vector<int64_t> T(nf);
+            int64_t total = 0;
+            for (int32_t i = 0; i < nf; i++)
+                total += (T[i] = (int64_t)(lower ? fused[i]->W.lsv_tick.size() : fused[i]->W.usv_tick.size()));
+            if (total > INT32_MAX) return fail(GBLU_ERR_INVALID_INPUT, "multi: too many rows");
+            std::vector<SetTask> ord;
+            ord.reserve(total);
+            using Item = std::pair<double, int32_t>;
+            std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+            std::vector<int64_t> next(nf, 0);
+            for (int32_t i = 0; i < nf; i++)
+                if (T[i] > 0) pq.push({0.5 / (double)T[i], i});
+            while (!pq.empty()) {
+                const int32_t i = pq.top().second;
+                pq.pop();
+                ord.push_back({i, (int32_t)next[i]});
+                if (++next[i] < T[i]) pq.push({((double)next[i] + 0.5) / (double)T[i], i});
+            }
+            CK(upload(h0, out, ord, st));
+            count = total;
+            return GBLU_OK;
+        };
+        CK(merge(true, h0->mlorder, h0->mlorder_n));
+        CK(merge(false, h0->muorder, h0->muorder_n));
+        h0->msolve_key = key;
+    }
+    h0->margs_host.resize(2 * (size_t)nf);
+    int32_t max_n = 0;
+    for (int32_t i = 0; i < nf; i++) {
+        gblu_ctx *h = fused[i];
+        SolveArgs a = solve_args(h, h->vals.p, b_dev[fi[i]], x_dev[fi[i]]);
+        SolveArgs lo = a, up = a;
+        lo.bs = h->lbs.p;
+        lo.rb = h->lrb.p;
+        lo.ext = h->ext_l.p;
+        lo.rows = h->lsv_tick.p;
+        lo.nrows = (int32_t)h->W.lsv_tick.size();
+        up.bs = h->ubs.p;
+        up.rb = h->urb.p;
+        up.ext = h->ext_u.p;
+        up.rows = h->usv_tick.p;
+        up.nrows = (int32_t)h->W.usv_tick.size();
+        h0->margs_host[i] = lo;
+        h0->margs_host[nf + i] = up;
+        max_n = std::max(max_n, h->S.n);
+    }
+    CK(ensure(h0, h0->margs, 2 * (size_t)nf));
+    CK(ensure(h0, h0->mticket, 2));
+    CU(cudaMemcpyAsync(h0->margs.p, h0->margs_host.data(), sizeof(SolveArgs) * 2 * nf, cudaMemcpyHostToDevice, st));
+    {
+        gblu_ctx *h = h0;
+        KL(launch_solve_multi(h0->margs.p, h0->margs.p + nf, nf, max_n, h0->mlorder.p, (int)h0->mlorder_n,
+                              h0->muorder.p, (int)h0->muorder_n, h0->solve_grid, h0->mticket.p, st));
+        h->launches += 2;   // three kernels
+    }
+    // the argument block is read by the kernels: keep the host copy unchanged
+    // until they have been issued (the copy above is stream-ordered)
     return GBLU_OK;
 }
 

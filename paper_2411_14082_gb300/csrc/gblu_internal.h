@@ -262,6 +262,9 @@ int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu
 int launch_solve_finish(const SolveArgs &a, bool lower, void *stream);
 int launch_lsolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
 int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream);
+// several handles' sparse solves in one launch per triangle (no dense pieces)
+int launch_solve_multi(const SolveArgs *lo, const SolveArgs *up, int nsets, int max_n, const SetTask *order_l,
+                       int total_l, const SetTask *order_u, int total_u, int grid, int32_t *tickets, void *stream);
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
                     const int32_t *Aslot, const double *Ax, const double *b,
                     const double *x, double *out, double *partial, int nblocks,

@@ -640,6 +640,45 @@ GBLU_SYNCFREE_KERNEL(lsolve_syncfree_kernel, lsolve_sf_row, ticket_l)
 GBLU_SYNCFREE_KERNEL(usolve_syncfree_kernel, usolve_sf_row, ticket_u)
 #undef GBLU_SYNCFREE_KERNEL
 
+// Several handles of different patterns in one launch per triangle: sets[s]
+// is handle s's whole sparse triangle (rows in its ticket order); ticket t
+// is row ticket order[t].task of set order[t].set.  Every set's rows keep
+// their order, so a row only waits on rows with smaller tickets.
+template <bool kLower>
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32)
+solve_multi_kernel(const SolveArgs *sets, const SetTask *order, int total, int32_t *ticket)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= total) break;
+        const SetTask o = order[t];
+        const SolveArgs a = sets[o.set];
+        const bool stop = kLower ? lsolve_sf_row(a, o.task, lane) : usolve_sf_row(a, o.task, lane);
+        if (stop) break;
+    }
+}
+
+// the sentinel fill of begin_solve_kernel for every set (blockIdx.y = set)
+__global__ void begin_multi_solve_kernel(const SolveArgs *lo, const SolveArgs *up, int32_t *tickets)
+{
+    const double sent = __longlong_as_double((long long)kSentinel);
+    const SolveArgs &a = lo[blockIdx.y];
+    double *eu = up[blockIdx.y].ext;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        a.y[i] = sent;
+        a.z[i] = sent;
+        a.ext[i] = sent;
+        eu[i] = sent;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        tickets[0] = 0;
+        tickets[1] = 0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Trailing block of the structure-adaptive solve (Section V-B, Algorithm 6):
 // for every trapezoid slice, the rectangular part (columns outside the
@@ -1033,6 +1072,19 @@ int launch_solve_finish(const SolveArgs &a, bool lower, void *stream)
         if (batch) usolve_finish_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
         else usolve_finish_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a);
     }
+    return (int)cudaGetLastError();
+}
+
+int launch_solve_multi(const SolveArgs *lo, const SolveArgs *up, int nsets, int max_n, const SetTask *order_l,
+                       int total_l, const SetTask *order_u, int total_u, int grid, int32_t *tickets, void *stream)
+{
+    if (nsets <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int gx = (max_n + 255) / 256;
+    gx = gx < 1 ? 1 : (gx > 64 ? 64 : gx);
+    begin_multi_solve_kernel<<<dim3(gx, nsets), 256, 0, st>>>(lo, up, tickets);
+    solve_multi_kernel<true><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(lo, order_l, total_l, tickets);
+    solve_multi_kernel<false><<<grid, kSolveWarpsPerBlock * 32, 0, st>>>(up, order_u, total_u, tickets + 1);
     return (int)cudaGetLastError();
 }
 
