@@ -572,6 +572,14 @@ def run_ours(args, rank, world, local_rank):
             ev_s[i][1].record(stream)
             iters.append(it)
             repiv += int(rep)
+        elif args.graph:
+            # refactor + solve replayed from one CUDA graph, one sync per step
+            ev_r[i][0].record(stream)
+            _, rep = s.step(vals[i], rhs[i], xs[i])
+            ev_r[i][1].record(stream)
+            ev_s[i][0].record(stream)
+            ev_s[i][1].record(stream)
+            repiv += int(rep)
         elif i in forced:
             ev_r[i][0].record(stream)
             _, rep = s.refactorize_forced(vals[i], forced[i])
@@ -707,6 +715,9 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["traffic"] = None
         line["roofline"]["peak_source"] = "FP32 ALU rate: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (nominal)"
         line["e2e"]["note"] = "double-precision host-buffer entry point"
+    if args.graph:
+        line["config"]["graph"] = True
+        line["phases_ms"]["note"] = "refactor = the whole graph-replayed step (refactor + solve)"
     if forced:
         tm = np.array(tail_ms)
         plain = [t for j, t in enumerate(t_ref) if j + args.warmup not in forced]
@@ -741,6 +752,7 @@ def main():
     ap.add_argument("--patterns", type=int, default=64, help="patterns of the uneven workload")
     ap.add_argument("--serve-budget-gb", type=int, default=64, help="device memory budget of the serve workload")
     ap.add_argument("--serve-max-batch", type=int, default=16)
+    ap.add_argument("--graph", action="store_true", help="time gblu_step (CUDA-graph replay) per step")
     ap.add_argument("--repivot-frac", type=float, default=0.0,
                     help="fraction of timed runs that re-pivot at a random step (general-case protocol)")
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],

@@ -162,6 +162,20 @@ int gblu_refactorize_forced(gblu_handle h, const double *Ax_dev, void *stream, i
                             int32_t *repivoted);
 
 /*
+ * One Newton step on device buffers, replayed from a CUDA graph: the
+ * checked re-factorization of Ax_dev (as gblu_refactorize) and the solve of
+ * b_dev into x_dev, with one synchronization at the end instead of one
+ * between the two.  The graph (staging copies of Ax and b, all launches of
+ * the refactorization, the status copy and the solve) is captured on the
+ * first call and again after the structure changes.  The solve runs before
+ * the check status is known; if a check failed, the call restarts with
+ * pivoting and solves again (returns GBLU_REPIVOTED, *repivoted = 1).
+ * Results equal gblu_refactorize + gblu_solve.  x_dev must not alias b_dev.
+ */
+int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, void *stream,
+              int32_t *repivoted);
+
+/*
  * Solve A x = b with the current factors: y = L^-1 P b, z = U^-1 y,
  * x(Q) = z (Algorithm 2 and the parallel solve of Section V).  b_dev and
  * x_dev are device float64[n]; they may alias.  Asynchronous on `stream`.

@@ -139,7 +139,16 @@ struct gblu_ctx {
     DBuf<SolveArgs> margs;
     std::vector<SolveArgs> margs_host;
     DBuf<int32_t> mticket;
+    // captured refactor + solve (gblu_step): replayed while the structure is
+    // the one it was captured on
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    uint64_t gversion = 0;
+    int32_t *epoch_host = nullptr;   // pinned: the epoch the next replay stores
+    long long glaunches = 0;         // kernels per replay
     uint64_t struct_version = 0;
+    uint64_t layout_version = 0;     // bumped by every device (re)allocation
+    uint64_t glayout = 0;
     DBuf<double> sx;
 };
 
@@ -169,6 +178,7 @@ int ensure(gblu_ctx *h, DBuf<T> &b, size_t count)
         b.p = nullptr;
         b.cap = 0;
     }
+    h->layout_version++;   // captured graphs hold the old address
     cudaError_t e = cudaMalloc((void **)&b.p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -186,6 +196,7 @@ void release(gblu_ctx *h, DBuf<T> &b)
     if (b.p) {
         cudaFree(b.p);
         h->device_bytes -= b.cap * sizeof(T);
+        h->layout_version++;
     }
     b.p = nullptr;
     b.cap = 0;
@@ -324,10 +335,11 @@ RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
     return a;
 }
 
-int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+// the launches of one checked re-factorization; ep = the epoch the kernels
+// store in the ready flags, or -1: read it from the control block (graph
+// replay, where the epoch changes between launches of the same graph)
+int issue_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int ep)
 {
-    const int32_t n = h->S.n;
-    h->epoch++;
     KL(launch_begin_refactor(h->ctl, st));
     RefactorArgs a = refactor_args(h, Ax);
     const std::vector<int32_t> &ltp = h->W.level_task_ptr;
@@ -335,13 +347,13 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
     for (int32_t l = 0; l < div; l++) {   // cluster mode: one launch per level
         a.task_begin = ltp[l];
         a.ntasks = ltp[l + 1] - ltp[l];
-        KL(launch_refactor_tasks(a, false, 0, h->epoch, st));
+        KL(launch_refactor_tasks(a, false, 0, ep, st));
     }
     const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
     if (ltp[div] < ntask) {               // pipeline mode: one persistent launch
         a.task_begin = ltp[div];
         a.ntasks = ntask - ltp[div];
-        KL(launch_refactor_tasks(a, true, h->ref_grid, h->epoch, st));
+        KL(launch_refactor_tasks(a, true, h->ref_grid, ep, st));
     }
     if (h->W.dense_m > 0) {   // the dense tail: blocked LU of the block, then scatter
         DenseArgs2 d{};
@@ -355,13 +367,19 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
         d.s0 = h->dense_s0.p;
         d.LUx = h->vals.p;
         d.finish = h->finish.p;
-        d.epoch = h->epoch;
+        d.epoch = ep;
         long long nl = 0;
         const int e = launch_dense_lu(d, st, &nl);
         h->launches += nl;
         if (e != 0) return fail(GBLU_ERR_CUDA, "dense tail launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
-    (void)n;
+    return GBLU_OK;
+}
+
+int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+{
+    h->epoch++;
+    CK(issue_refactor(h, Ax, st, h->epoch));
     CK(read_ctl(h, st));
     CK(status_code(h));
     *interrupted = h->hctl->interrupted;
@@ -693,6 +711,11 @@ void gblu_destroy(gblu_handle h)
         release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
         release(h, h->tpinv); release(h, h->cnu); release(h, h->cnl); release(h, h->smark);
         release(h, h->slist); release(h, h->sclass); release(h, h->cbeg); release(h, h->sx);
+        release(h, h->sflag); release(h, h->sbits); release(h, h->morder); release(h, h->mlorder);
+        release(h, h->muorder); release(h, h->margs); release(h, h->mticket);
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->gstream) cudaStreamDestroy(h->gstream);
+        if (h->epoch_host) cudaFreeHost(h->epoch_host);
         if (h->ctl) cudaFree(h->ctl);
         if (h->hctl) cudaFreeHost(h->hctl);
     }
@@ -1203,6 +1226,88 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
     // the argument block is read by the kernels: keep the host copy unchanged
     // until they have been issued (the copy above is stream-ordered)
     return GBLU_OK;
+}
+
+// capture [epoch -> control block, checked re-factorization, control block
+// -> host, solve] on the handle's staging buffers into one graph
+static int capture_step(gblu_ctx *h)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    if (!h->gstream) CU(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    if (!h->epoch_host) CU(cudaMallocHost((void **)&h->epoch_host, sizeof(int32_t)));
+    cudaStream_t gs = h->gstream;
+    const long long l0 = h->launches;
+    CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int rc = GBLU_OK;
+    if (cudaMemcpyAsync(&h->ctl->epoch, h->epoch_host, sizeof(int32_t), cudaMemcpyHostToDevice, gs) != cudaSuccess)
+        rc = fail(GBLU_ERR_CUDA, "graph capture: epoch copy failed");
+    if (rc == GBLU_OK) rc = issue_refactor(h, h->stage_ax.p, gs, -1);
+    if (rc == GBLU_OK &&
+        cudaMemcpyAsync(h->hctl, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, gs) != cudaSuccess)
+        rc = fail(GBLU_ERR_CUDA, "graph capture: status copy failed");
+    if (rc == GBLU_OK) rc = solve_values(h, h->vals.p, 0, h->stage_b.p, 0, h->stage_x.p, 0, 1, gs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(gs, &graph);
+    h->glaunches = h->launches - l0;
+    h->launches = l0;   // counted per replay instead
+    if (rc != GBLU_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(GBLU_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+        h->gexec = nullptr;
+        return fail(GBLU_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+    }
+    h->gversion = h->struct_version;
+    h->glayout = h->layout_version;
+    return GBLU_OK;
+}
+
+int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, void *stream,
+              int32_t *repivoted)
+{
+    CK(check_handle(h));
+    if (repivoted) *repivoted = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    if (!Ax_dev || !b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = h->S.n;
+    const size_t nnz = h->P.Ai.size();
+    CK(ensure(h, h->stage_ax, nnz));
+    CK(ensure(h, h->stage_b, n));
+    CK(ensure(h, h->stage_x, n));
+    if (!h->gexec || h->gversion != h->struct_version || h->glayout != h->layout_version) CK(capture_step(h));
+    CU(cudaMemcpyAsync(h->stage_ax.p, Ax_dev, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(h->stage_b.p, b_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // the previous call ended with a synchronization, so the pinned epoch
+    // word is free to change
+    h->epoch++;
+    h->n_refactor++;
+    *h->epoch_host = h->epoch;
+    CU(cudaGraphLaunch(h->gexec, st));
+    h->launches += h->glaunches;
+    CU(cudaMemcpyAsync(x_dev, h->stage_x.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    CK(status_code(h));
+    h->last_first_bad = h->hctl->interrupted ? h->hctl->first_bad : -1;
+    if (!h->hctl->interrupted) return GBLU_OK;
+    // the check failed: the solve of the replay is void; restart, solve again
+    h->n_repivot++;
+    int rc = run_restart(h, h->stage_ax.p, st);
+    if (rc != GBLU_OK) {
+        h->factorized = false;
+        return rc;
+    }
+    CK(solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, st));
+    if (repivoted) *repivoted = 1;
+    return GBLU_REPIVOTED;
 }
 
 int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed)

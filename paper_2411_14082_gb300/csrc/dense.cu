@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) dense_scatter_kernel(DenseArgs2 d)
     for (int r = threadIdx.x; r < d.m; r += blockDim.x) d.LUx[base + r] = sc[r];
     // the stores are ordered before the release by the barrier
     __syncthreads();
-    if (threadIdx.x == 0) st_release(d.finish + d.p + c, d.epoch);
+    if (threadIdx.x == 0) st_release(d.finish + d.p + c, d.epoch < 0 ? ld_volatile(&d.ctl->epoch) : d.epoch);
 }
 
 size_t panel_smem(int rows) { return (size_t)rows * kNb * sizeof(double); }

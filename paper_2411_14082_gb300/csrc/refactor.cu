@@ -614,6 +614,8 @@ __device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *x
 template <typename R, bool kWait, bool kDense>
 __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgsT<R> a, int epoch, int persistent)
 {
+    // a replayed graph passes -1: the epoch was written to the control block
+    if (epoch < 0) epoch = ld_volatile(&a.ctl->epoch);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_quit;
     __shared__ GroupShared<R> s_grp[2];

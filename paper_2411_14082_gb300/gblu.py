@@ -39,7 +39,7 @@ EXPORTED = [
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
-    "gblu_refactorize_multi", "gblu_solve_multi",
+    "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
         lib.gblu_refactorize.argtypes = [P, P, P, ctypes.POINTER(I32)]
         lib.gblu_refactorize_forced.argtypes = [P, P, P, I32, ctypes.POINTER(I32)]
         lib.gblu_refactorize_multi.argtypes = [I32, P, P, P, P]
+        lib.gblu_step.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
         lib.gblu_solve_multi.argtypes = [I32, P, P, P, P]
         lib.gblu_solve.argtypes = [P, P, P, P]
         lib.gblu_residual.argtypes = [P, P, P, P, P, P]
@@ -154,7 +155,7 @@ def load(build_if_missing: bool = True):
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
                   "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
-                  "gblu_refactorize_multi", "gblu_solve_multi"):
+                  "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -252,6 +253,17 @@ class Solver:
         rc = _check(load().gblu_refactorize(self._h, _dev_ptr(Ax, self.device, self.nnz),
                                             _stream(stream), ctypes.byref(rep)))
         return rc, bool(rep.value)
+
+    def step(self, Ax, b, x=None, stream=None):
+        """Checked re-factorization and solve replayed from a CUDA graph
+        (gblu_step); returns (x, repivoted)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        rep = ctypes.c_int32(0)
+        _check(load().gblu_step(self._h, _dev_ptr(Ax, self.device, self.nnz), _dev_ptr(b, self.device, self.n),
+                                _dev_ptr(x, self.device, self.n), _stream(stream), ctypes.byref(rep)))
+        return x, bool(rep.value)
 
     def refactorize_forced(self, Ax, force_col, stream=None):
         """refactorize with the check of step force_col failing (re-pivoting protocol)."""

@@ -169,7 +169,10 @@ def test_multi_pattern_batch_equals_single_handles():
             _, rep = s.refactorize(dev(vals[i]))
             assert rep == reps[i]
             xs = s.solve(dev(rhs[i])).cpu().numpy()
-            assert np.array_equal(xs, xm[i]), f"pattern {i} differs from its single handle"
+            if rep:   # the restart set depends on timing: equal within rounding
+                np.testing.assert_allclose(xm[i], xs, rtol=1e-10, atol=1e-12 * np.abs(xs).max())
+            else:
+                assert np.array_equal(xs, xm[i]), f"pattern {i} differs from its single handle"
             lus[i] = O.refactorize(lus[i], c[2], c[3], vals[i])
             compare_factors(multi[i].export_factors(), lus[i], 1e-10)
             assert O.residual(c[1], c[2], c[3], vals[i], xm[i], rhs[i]) <= 1e-12

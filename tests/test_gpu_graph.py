@@ -1,0 +1,64 @@
+"""Graph replay of a Newton step (gblu_step): the same results as
+gblu_refactorize + gblu_solve, bit for bit, and across a step whose check
+fails (restart, new structure, new capture).  On the restarting step itself
+the two runs may differ in the last bits: which columns were finished when
+the check failed depends on timing, and the restart recomputes the others
+in its own order, so that step is compared within rounding."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2411_14082_gb300 import gblu, inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = 0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(f"cuda:{DEV}")
+
+
+@pytest.mark.parametrize("case", ["small_mna", "mesh"])
+def test_step_equals_refactorize_and_solve(case):
+    ckt = inputs.workload_small() if case == "small_mna" else inputs.rc_mesh3d(24, 24, 4, seed=5, n_fet=60)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    g, p = gblu.Solver(DEV), gblu.Solver(DEV)
+    for s in (g, p):
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(dev(Ax0))
+    lu = O.factorize(n, Ap, Ai, Ax0, Q, 1e-3)
+    rng = np.random.default_rng(17)
+    for it in range(6):
+        ckt = inputs.perturb_elements(ckt, rng) if case == "small_mna" else inputs.redraw_transistors(ckt, rng)
+        Ax = ckt.values()
+        if it == 3:
+            # a pivot that fails its check: the replay restarts and solves again
+            ref = O.refactorize(lu, Ap, Ai, Ax)
+            k = n // 2
+            while True:
+                c = Q[k]
+                rows = Ai[Ap[c]:Ap[c + 1]]
+                hit = np.nonzero(rows == lu.piv[k])[0]
+                if len(hit) and ref.Lp[k + 1] > ref.Lp[k]:
+                    break
+                k += 1
+            Ax = Ax.copy()
+            Ax[Ap[c] + hit[0]] -= ref.Ux[ref.Up[k + 1] - 1] * (1.0 - 1e-9)
+        b = inputs.rhs(n, rng)
+        xg, rep_g = g.step(dev(Ax), dev(b))
+        _, rep_p = p.refactorize(dev(Ax))
+        xp = p.solve(dev(b))
+        assert rep_g == rep_p
+        if it == 3:
+            assert rep_g
+        if rep_g:
+            torch.testing.assert_close(xg, xp, rtol=1e-10, atol=1e-12 * xp.abs().max().item())
+        else:
+            assert torch.equal(xg, xp)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        assert O.residual(n, Ap, Ai, Ax, xg.cpu().numpy(), b) <= 1e-12
+    st = g.stats()
+    assert st["n_refactor"] == 6 and st["kernel_launches"] > 0
