@@ -315,6 +315,139 @@ def run_batch(args, rank, world, local_rank):
     return 0
 
 
+def run_serve_poisson(args, rank, world, local_rank):
+    """C5-like traffic: independent simulations of different sizes share one
+    gblu server.  Requests arrive as a Poisson process (open loop), at rates
+    set to fractions of the measured service capacity; half of them ask for
+    single-precision factors with refinement.  Latency is the server's own
+    submit-to-solution time."""
+    import threading
+    import torch
+    from paper_2411_14082_gb300 import gblu
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(args.seed + 17 * rank)
+    V = 2
+    specs = []
+    for i, nt in enumerate(np.exp(rng.uniform(np.log(5000), np.log(args.serve_max_n), args.sims))):
+        if i % 2 == 0:   # C1 generator: 2D MNA grid with voltage sources
+            side = max(8, int(round(np.sqrt(nt - 20))))
+            specs.append((f"mna_{side}x{side}", inputs.mna_grid2d(side, side, seed=args.seed + 2000 + i), "elements"))
+        else:            # C2 generator: 4-layer RC mesh with transistor stamps
+            side = max(8, int(round(np.sqrt(nt / 4))))
+            specs.append((f"mesh_{side}x{side}x4", inputs.rc_mesh3d(side, side, 4, seed=args.seed + 2000 + i,
+                                                                   n_fet=max(10, side * side // 20)), "transistors"))
+    if args.serve_big:
+        specs.append(("mesh_500x500x4", inputs.rc_mesh3d(500, 500, 4, seed=args.seed + 3000), "transistors"))
+    srv = gblu.Server(dev, hbm_budget=args.serve_budget_gb << 30, max_batch=args.serve_max_batch)
+    pats, refused = [], []
+    t0 = time.perf_counter()
+    for name, ckt, kind in specs:
+        n, Ap, Ai, Ax0 = ckt.csc()
+        Q = inputs.grid_nd_order(ckt)
+        try:
+            pid, slots = srv.add_pattern(n, Ap, Ai, Q, Ax0)
+        except gblu.GbluError as e:   # refused by the memory budget
+            refused.append({"pattern": name, "n": n, "error": str(e)})
+            continue
+        vals, rhs = [], []
+        for _ in range(V):
+            ckt = inputs.redraw_transistors(ckt, rng) if kind == "transistors" else inputs.perturb_elements(ckt, rng)
+            vals.append(torch.from_numpy(ckt.values()).pin_memory().numpy())
+            rhs.append(torch.from_numpy(inputs.rhs(n, rng)).pin_memory().numpy())
+        pats.append(dict(name=name, n=n, id=pid, slots=slots, vals=vals, rhs=rhs))
+    t_admit = time.perf_counter() - t0
+    # service time of each pattern and mode alone (after one warm request)
+    svc = {}
+    for p in pats:
+        for mode in (0, 1):
+            for rep in range(2):
+                _, r = srv.wait(srv.submit(p["id"], p["vals"][0], p["rhs"][0], mixed=bool(mode)), timeout=600.0)
+            svc[p["name"], mode] = r["latency_s"]
+    tbar = float(np.mean(list(svc.values())))
+    sweep = []
+    for rho in args.serve_rates:
+        lam = rho / tbar
+        N = args.serve_requests
+        ids, lock = [], threading.Lock()
+        st0 = srv.stats()
+
+        def dispatch():
+            t_next = time.perf_counter()
+            for k in range(N):
+                t_next += rng.exponential(1.0 / lam)
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                p = pats[int(rng.integers(0, len(pats)))]
+                j = int(rng.integers(0, V))
+                mode = k % 2
+                rid = srv.submit(p["id"], p["vals"][j], p["rhs"][j], mixed=bool(mode))
+                with lock:
+                    ids.append((rid, mode, p["name"]))
+
+        clocks = ClockSampler()
+        clocks.start()
+        t_start = time.perf_counter()
+        th = threading.Thread(target=dispatch)
+        th.start()
+        res = []
+        got = 0
+        while got < N:
+            with lock:
+                pending = ids[got:]
+            if not pending:
+                time.sleep(0.001)
+                continue
+            for rid, mode, name in pending:
+                _, r = srv.wait(rid, timeout=600.0)
+                res.append((mode, name, r))
+                got += 1
+        th.join()
+        elapsed = time.perf_counter() - t_start
+        clk = clocks.stop()
+        lat = np.array([r["latency_s"] for _, _, r in res])
+        by_mode = {}
+        for mode in (0, 1):
+            a = np.array([r["latency_s"] for m, _, r in res if m == mode])
+            by_mode["f64" if mode == 0 else "f32_refined"] = {
+                "p50_ms": 1e3 * float(np.percentile(a, 50)), "p99_ms": 1e3 * float(np.percentile(a, 99)),
+                "fallbacks": int(sum(1 for m, _, r in res if m == mode and r["refine_iters"] < 0))}
+        st1 = srv.stats()
+        sweep.append({"offered_load": rho, "arrival_rate_per_s": lam, "requests": N,
+                      "served_per_s": N / elapsed, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                      "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "by_mode": by_mode,
+                      "mean_batch": float(np.mean([r["batch_size"] for m, _, r in res if m == 0])),
+                      "errors": int(sum(1 for _, _, r in res if r["status"] < 0)),
+                      "max_rel_residual": float(max(r["berr"] for _, _, r in res)),
+                      "batches": st1["batches"] - st0["batches"], "clocks": clk})
+    st = srv.stats()
+    srv.close()
+    top = sweep[-1]
+    ns = [p["n"] for p in pats]
+    line = {
+        "metric": "served requests/s", "value": world * top["served_per_s"], "unit": "requests/s",
+        "n_gpus": world, "steps": args.serve_requests, "warmup": 2, "ms_per_step": 1e3 / top["served_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 and f32+refinement",
+        "data": "synthetic",
+        "config": {"workload": f"serve_poisson_{len(pats)}_sims", "patterns": len(pats), "n_min": int(min(ns)),
+                   "n_max": int(max(ns)), "n_total": int(sum(ns)), "max_batch": args.serve_max_batch,
+                   "hbm_budget_gb": args.serve_budget_gb, "mode_mix": "half f64, half f32 + refinement",
+                   "arrivals": "Poisson, open loop; rate = offered load / mean solo service time",
+                   "mean_solo_service_ms": 1e3 * tbar, "timing": "host wall clock",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "latency_ms_p50": top["latency_ms_p50"], "latency_ms_p99": top["latency_ms_p99"],
+        "max_rel_residual": max(v["max_rel_residual"] for v in sweep),
+        "residual_ok": bool(max(v["max_rel_residual"] for v in sweep) <= 1e-12),
+        "sweep": sweep, "server": {k: st[k] for k in ("batches", "repivots", "max_batch_seen", "reserved_bytes")},
+        "admission_s": t_admit, "refused_patterns": refused,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_uneven(args, rank, world, local_rank):
     """Uneven-pattern batch: 64 MNA grids with n log-uniform in [1k, 50k];
     every step re-factorizes all of them with new values in one launch
@@ -544,6 +677,14 @@ def run_ours(args, rank, world, local_rank):
     rhs = torch.from_numpy(np.stack(w["rhs"])).cuda(dev)
     xs = torch.empty_like(rhs)
     res = torch.zeros((total, 4), dtype=torch.float64, device=f"cuda:{dev}")
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        opts, tr, ts = s.autotune(vals[0], rhs[0], xs[0], reps=3)
+        tuned = {"alpha": opts["alpha"], "solve_dense_density": opts["solve_dense_density"],
+                 "solve_slices": opts["solve_slices"], "refactor_ms": tr, "solve_ms": ts,
+                 "tuning_s": time.perf_counter() - t0}
+        st = s.stats()
     stream = torch.cuda.current_stream(dev)
     ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(total)]
     ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(total)]
@@ -715,6 +856,8 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["traffic"] = None
         line["roofline"]["peak_source"] = "FP32 ALU rate: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (nominal)"
         line["e2e"]["note"] = "double-precision host-buffer entry point"
+    if tuned:
+        line["config"]["autotuned"] = tuned
     if args.graph:
         line["config"]["graph"] = True
         line["phases_ms"]["note"] = "refactor = the whole graph-replayed step (refactor + solve)"
@@ -748,10 +891,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mesh", choices=["mesh", "mesh_ill", "small", "batch", "serve", "uneven"])
+    ap.add_argument("--workload", default="mesh", choices=["mesh", "mesh_ill", "small", "batch", "serve", "serve_poisson", "uneven"])
+    ap.add_argument("--sims", type=int, default=32, help="simulations of the serve_poisson workload")
+    ap.add_argument("--serve-max-n", type=int, default=500000)
+    ap.add_argument("--serve-big", action="store_true", help="add the 500x500x4 mesh (n = 1M) to serve_poisson")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests per offered-load point")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 0.7, 0.9])
     ap.add_argument("--patterns", type=int, default=64, help="patterns of the uneven workload")
-    ap.add_argument("--serve-budget-gb", type=int, default=64, help="device memory budget of the serve workload")
+    ap.add_argument("--serve-budget-gb", type=int, default=200, help="device memory budget of the serve workload")
     ap.add_argument("--serve-max-batch", type=int, default=16)
+    ap.add_argument("--autotune", action="store_true", help="tune the schedule options on the matrix first")
     ap.add_argument("--graph", action="store_true", help="time gblu_step (CUDA-graph replay) per step")
     ap.add_argument("--repivot-frac", type=float, default=0.0,
                     help="fraction of timed runs that re-pivot at a random step (general-case protocol)")
@@ -775,6 +924,8 @@ def main():
         return run_batch(args, rank, world, local_rank)
     if args.workload == "serve":
         return run_serve(args, rank, world, local_rank)
+    if args.workload == "serve_poisson":
+        return run_serve_poisson(args, rank, world, local_rank)
     if args.workload == "uneven":
         return run_uneven(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)

@@ -98,6 +98,27 @@ typedef struct {
 /* Fill *o with the defaults above. */
 void gblu_default_opts(gblu_opts *o);
 
+/*
+ * gblu_get_opts: the handle's current options.
+ * gblu_set_opts: replace them; on a factorized handle the schedule of the
+ *   re-factorization and the solves is rebuilt for the same factor
+ *   structure and values (host work, then an upload on `stream`, which is
+ *   synchronized).  GBLU_ERR_INVALID_INPUT for out-of-range options.
+ * gblu_autotune: measure, with CUDA events on `stream`, the median of reps
+ *   re-factorizations of Ax_dev and solves of b_dev (into x_dev) for a set
+ *   of schedule options, and keep the fastest: first the dividing-level
+ *   factor alpha (Section IV-B) by re-factorization time, then the
+ *   trailing-block rule of the solve (solve_dense_density, solve_slices;
+ *   Section V-A) by solve time.  The paper tunes these constants for its
+ *   CPUs; here they are measured on the device and matrix at hand.  The
+ *   factor values after the call are those of Ax_dev.  *chosen, *refactor_ms
+ *   and *solve_ms (optional, host) report the kept options and their times.
+ */
+int gblu_get_opts(gblu_handle h, gblu_opts *o);
+int gblu_set_opts(gblu_handle h, const gblu_opts *o, void *stream);
+int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, int32_t reps,
+                  void *stream, gblu_opts *chosen, double *refactor_ms, double *solve_ms);
+
 /* One-line description of the last error of this thread (never NULL). */
 const char *gblu_last_error(void);
 
@@ -344,7 +365,11 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
  * gblu_server_submit: queues a request.  Ax_host (nnz(A), slot order),
  *   b_host (n) and x_host (n) are host arrays owned by the caller and must
  *   stay valid until the request is waited for; x_host receives the
- *   solution.  Pinned host memory makes the copies asynchronous.
+ *   solution.  Pinned host memory makes the copies asynchronous.  mode 0:
+ *   double precision (batched); mode 1: single-precision factors with
+ *   refinement to a backward error of 1e-12 (gblu_refactorize_f32 +
+ *   gblu_solve_refined, one request at a time, falling back to double
+ *   precision when refinement stalls).
  * gblu_server_wait: waits up to timeout_s seconds (0: poll).  Returns
  *   GBLU_OK and fills *res (then the request id is released), or
  *   GBLU_ERR_BUSY if it has not finished.  res->status is the request's own
@@ -363,6 +388,7 @@ typedef struct {
     double berr;         /* ||b - A x||inf / (||A||inf ||x||inf); -1 on error     */
     double queue_s;      /* submit -> start of its batch (host clock)             */
     double latency_s;    /* submit -> solution in x_host (host clock)             */
+    int32_t refine_iters;/* mode 1: corrections used, -1 = fell back to double    */
 } gblu_request_result;
 
 typedef struct {
@@ -379,7 +405,7 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
                             const double *Ax0_host, int32_t *pattern, int32_t *slots);
 int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes);
 int gblu_server_submit(gblu_server s, int32_t pattern, const double *Ax_host, const double *b_host,
-                       double *x_host, int64_t *request);
+                       double *x_host, int32_t mode, int64_t *request);
 int gblu_server_wait(gblu_server s, int64_t request, double timeout_s, gblu_request_result *res);
 int gblu_server_get_stats(gblu_server s, gblu_server_stats *st);
 void gblu_server_destroy(gblu_server s);

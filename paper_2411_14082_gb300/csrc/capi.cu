@@ -636,6 +636,14 @@ void gblu_default_opts(gblu_opts *o)
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
 
+static bool opts_valid(const gblu_opts &o)
+{
+    return o.pivot_tol >= 0.0 && o.pivot_tol <= 1.0 && o.spin_limit > 0 && o.sched_mode >= 0 && o.sched_mode <= 2 &&
+           o.solve_mode >= 0 && o.solve_mode <= 2 && o.alpha >= 0.0 && o.solve_dense_frac >= 0.0 &&
+           o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
+           o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0;
+}
+
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
 {
     if (!out) return fail(GBLU_ERR_INVALID_INPUT, "null output pointer");
@@ -644,12 +652,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (!h) return fail(GBLU_ERR_NOMEM, "host allocation failed");
     gblu_default_opts(&h->opts);
     if (o) h->opts = *o;
-    if (!(h->opts.pivot_tol >= 0.0 && h->opts.pivot_tol <= 1.0) || h->opts.spin_limit <= 0 ||
-        h->opts.sched_mode < 0 || h->opts.sched_mode > 2 || h->opts.solve_mode < 0 ||
-        h->opts.solve_mode > 2 || !(h->opts.alpha >= 0.0) || !(h->opts.solve_dense_frac >= 0.0) ||
-        h->opts.solve_dense_frac > 1.0 || h->opts.solve_slices < 0 ||
-        !(h->opts.solve_dense_density >= 0.0) || h->opts.solve_dense_density > 1.0 ||
-        h->opts.dense_min_rows < 0) {
+    if (!opts_valid(h->opts)) {
         delete h;
         return fail(GBLU_ERR_INVALID_INPUT, "invalid options");
     }
@@ -1308,6 +1311,113 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
     CK(solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, st));
     if (repivoted) *repivoted = 1;
     return GBLU_REPIVOTED;
+}
+
+int gblu_get_opts(gblu_handle h, gblu_opts *o)
+{
+    if (!h || !o) return fail(GBLU_ERR_INVALID_INPUT, "null pointer");
+    *o = h->opts;
+    return GBLU_OK;
+}
+
+int gblu_set_opts(gblu_handle h, const gblu_opts *o, void *stream)
+{
+    if (!h || !o) return fail(GBLU_ERR_INVALID_INPUT, "null pointer");
+    if (!opts_valid(*o)) return fail(GBLU_ERR_INVALID_INPUT, "invalid options");
+    DeviceGuard g(h->device);
+    h->opts = *o;
+    if (!h->factorized) return GBLU_OK;
+    // same factor structure and values; the schedule follows the new options
+    Structure S = h->S;
+    return install_structure(h, std::move(S), nullptr, (cudaStream_t)stream);
+}
+
+int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, int32_t reps,
+                  void *stream, gblu_opts *chosen, double *refactor_ms, double *solve_ms)
+{
+    CK(check_handle(h));
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    if (!Ax_dev || !b_dev || !x_dev || reps < 1) return fail(GBLU_ERR_INVALID_INPUT, "null vector or reps < 1");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1, e2;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    CU(cudaEventCreate(&e2));
+    // median refactor and solve times of the current options (one untimed run first)
+    auto measure = [&](double &tr, double &ts) -> int {
+        std::vector<float> a, b;
+        for (int32_t r = -1; r < reps; r++) {
+            int intr = 0;
+            CU(cudaEventRecord(e0, st));
+            CK(run_refactor(h, Ax_dev, st, &intr));
+            if (intr) {
+                h->n_repivot++;
+                CK(run_restart(h, Ax_dev, st));
+            }
+            CU(cudaEventRecord(e1, st));
+            CK(solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, st));
+            CU(cudaEventRecord(e2, st));
+            CU(cudaEventSynchronize(e2));
+            float m1 = 0, m2 = 0;
+            CU(cudaEventElapsedTime(&m1, e0, e1));
+            CU(cudaEventElapsedTime(&m2, e1, e2));
+            if (r >= 0) {
+                a.push_back(m1);
+                b.push_back(m2);
+            }
+        }
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        tr = a[a.size() / 2];
+        ts = b[b.size() / 2];
+        return GBLU_OK;
+    };
+    gblu_opts best = h->opts;
+    double br = 0, bs = 0;
+    int rc = measure(br, bs);
+    // the dividing level of the re-factorization (Section IV-B: alpha), then
+    // the trailing-block rule of the solve (Section V-A: P0 and the slices)
+    const double alphas[] = {0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0};
+    for (double al : alphas) {
+        if (rc != GBLU_OK) break;
+        if (al == best.alpha) continue;
+        gblu_opts o = best;
+        o.alpha = al;
+        double tr = 0, ts = 0;
+        if ((rc = gblu_set_opts(h, &o, stream)) != GBLU_OK || (rc = measure(tr, ts)) != GBLU_OK) break;
+        if (tr < br) {
+            best = o;
+            br = tr;
+            bs = ts;
+        }
+    }
+    const double dens[] = {0.0, 0.3, 0.5, 0.7, 0.9};
+    const int slices[] = {4, 8, 16};
+    for (double dd : dens) {
+        for (int m : slices) {
+            if (rc != GBLU_OK) break;
+            if (dd == best.solve_dense_density && m == best.solve_slices) continue;
+            gblu_opts o = best;
+            o.solve_dense_density = dd;
+            o.solve_slices = m;
+            double tr = 0, ts = 0;
+            if ((rc = gblu_set_opts(h, &o, stream)) != GBLU_OK || (rc = measure(tr, ts)) != GBLU_OK) break;
+            if (ts < bs) {
+                best = o;
+                bs = ts;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rc != GBLU_OK) return rc;
+    CK(gblu_set_opts(h, &best, stream));
+    if (chosen) *chosen = best;
+    if (refactor_ms) *refactor_ms = br;
+    if (solve_ms) *solve_ms = bs;
+    return GBLU_OK;
 }
 
 int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed)

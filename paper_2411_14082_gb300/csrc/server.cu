@@ -62,6 +62,7 @@ struct Request {
     const double *Ax = nullptr;
     const double *b = nullptr;
     double *x = nullptr;
+    int32_t mode = 0;   // 0: double precision; 1: single-precision factors + refinement
     Clock::time_point t_submit, t_start;
     gblu_request_result res{};
     bool done = false;
@@ -136,6 +137,43 @@ int alloc_buffers(Pattern *p)
     }
     p->failed.assign(S, 0);
     return GBLU_OK;
+}
+
+// A single-precision request (mode 1): gblu_refactorize_f32 and
+// gblu_solve_refined on the pattern's handle (which falls back to double
+// precision itself when refinement cannot reach 1e-12).
+void run_refined(gblu_server_s *s, Pattern *p, Request *r)
+{
+    const Clock::time_point t0 = Clock::now();
+    cudaStream_t st = p->st;
+    const int64_t n = p->n, na = p->nnz_a;
+    int rc = GBLU_OK;
+    if (cudaMemcpyAsync(p->Ax_d, r->Ax, na * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->b_d, r->b, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = sfail(GBLU_ERR_CUDA, "server: copy of request inputs failed");
+    int32_t it = 0;
+    double berr = -1.0;
+    if (rc == GBLU_OK) rc = gblu_refactorize_f32(p->h, p->Ax_d, st, nullptr);
+    if (rc == GBLU_OK) rc = gblu_solve_refined(p->h, p->Ax_d, p->b_d, p->x_d, 1e-12, 10, st, &it, &berr);
+    if (rc == GBLU_OK &&
+        (cudaMemcpyAsync(r->x, p->x_d, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        rc = sfail(GBLU_ERR_CUDA, "server: copy of the solution failed");
+    const Clock::time_point t1 = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->t_start = t0;
+    r->res.status = rc;
+    r->res.repivoted = 0;
+    r->res.batch_size = 1;
+    r->res.pattern = p->id;
+    r->res.berr = rc >= 0 ? berr : -1.0;
+    r->res.refine_iters = it;
+    r->res.queue_s = std::chrono::duration<double>(t0 - r->t_submit).count();
+    r->res.latency_s = std::chrono::duration<double>(t1 - r->t_submit).count();
+    r->done = true;
+    p->batches++;
+    p->requests++;
+    s->completed++;
 }
 
 // One batch: copy in, batched refactor + solve, single-path redo of failed
@@ -223,6 +261,7 @@ void run_batch(gblu_server_s *s, Pattern *p, std::vector<Request *> &batch)
         r->res.batch_size = k;
         r->res.pattern = p->id;
         r->res.berr = status[i] >= 0 ? p->res_h[4 * i] : -1.0;
+        r->res.refine_iters = 0;
         r->res.queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
         r->res.latency_s = std::chrono::duration<double>(t1 - r->t_submit).count();
         r->done = true;
@@ -262,8 +301,23 @@ void worker_loop(gblu_server_s *s, Pattern *p)
                 continue;
             }
         }
-        run_batch(s, p, batch);
-        s->cv_done.notify_all();
+        // double-precision requests go into one batch; single-precision
+        // ones run one by one after it
+        std::vector<Request *> refined;
+        size_t w = 0;
+        for (Request *r : batch) {
+            if (r->mode == 1) refined.push_back(r);
+            else batch[w++] = r;
+        }
+        batch.resize(w);
+        if (!batch.empty()) {
+            run_batch(s, p, batch);
+            s->cv_done.notify_all();
+        }
+        for (Request *r : refined) {
+            run_refined(s, p, r);
+            s->cv_done.notify_all();
+        }
     }
 }
 
@@ -339,7 +393,9 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
     int64_t avail;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        avail = s->budget - s->reserved - hs.device_bytes;
+        // the handle, plus the single-precision workspace (float factors,
+        // widened copy, refinement vectors) grown below
+        avail = s->budget - s->reserved - hs.device_bytes - (12 * p->lu_stride + 32 * (int64_t)n);
     }
     p->slots = (int32_t)std::min<int64_t>(s->max_batch, avail > 0 ? avail / per_set : 0);
     if (p->slots < 1) {
@@ -360,6 +416,10 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
     cudaMemsetAsync(p->b_d, 0, (size_t)p->slots * n * sizeof(double), p->st);
     rc = gblu_refactorize_batch(p->h, p->slots, p->Ax_d, p->nnz_a, p->LU_d, p->lu_stride, nullptr, nullptr, p->st);
     if (rc == GBLU_OK) rc = gblu_solve_batch(p->h, p->slots, p->LU_d, p->lu_stride, p->b_d, n, p->x_d, n, p->st);
+    // and the workspace of single-precision requests (the first n values
+    // serve as a right-hand side)
+    if (rc == GBLU_OK) rc = gblu_refactorize_f32(p->h, p->Ax_d, p->st, nullptr);
+    if (rc == GBLU_OK) rc = gblu_solve_refined(p->h, p->Ax_d, p->Ax_d, p->x_d, 1e-12, 2, p->st, nullptr, nullptr);
     cudaStreamSynchronize(p->st);
     cudaFree(Ax0);
     if (rc != GBLU_OK) return bail_h(rc);
@@ -395,9 +455,10 @@ int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int
 }
 
 int gblu_server_submit(gblu_server s, int32_t pattern, const double *Ax_host, const double *b_host, double *x_host,
-                       int64_t *request)
+                       int32_t mode, int64_t *request)
 {
     if (!s || !Ax_host || !b_host || !x_host || !request) return sfail(GBLU_ERR_INVALID_INPUT, "server: null argument");
+    if (mode != 0 && mode != 1) return sfail(GBLU_ERR_INVALID_INPUT, "server: mode must be 0 or 1");
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->stop) return sfail(GBLU_ERR_INVALID_INPUT, "server: shutting down");
     if (pattern < 0 || pattern >= (int32_t)s->patterns.size())
@@ -408,6 +469,7 @@ int gblu_server_submit(gblu_server s, int32_t pattern, const double *Ax_host, co
     r->Ax = Ax_host;
     r->b = b_host;
     r->x = x_host;
+    r->mode = mode;
     r->t_submit = Clock::now();
     Pattern *p = s->patterns[pattern].get();
     p->queue.push_back(r.get());

@@ -39,7 +39,8 @@ EXPORTED = [
     "gblu_export_factors", "gblu_order_mindeg", "gblu_column_etree", "gblu_restart_set",
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
-    "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step",
+    "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
+    "gblu_autotune",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -79,7 +80,7 @@ class Stats(ctypes.Structure):
 class RequestResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("repivoted", ctypes.c_int32), ("batch_size", ctypes.c_int32),
                 ("pattern", ctypes.c_int32), ("berr", ctypes.c_double), ("queue_s", ctypes.c_double),
-                ("latency_s", ctypes.c_double)]
+                ("latency_s", ctypes.c_double), ("refine_iters", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -119,6 +120,10 @@ def load(build_if_missing: bool = True):
         lib.gblu_refactorize_forced.argtypes = [P, P, P, I32, ctypes.POINTER(I32)]
         lib.gblu_refactorize_multi.argtypes = [I32, P, P, P, P]
         lib.gblu_step.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
+        lib.gblu_get_opts.argtypes = [P, ctypes.POINTER(Opts)]
+        lib.gblu_set_opts.argtypes = [P, ctypes.POINTER(Opts), P]
+        lib.gblu_autotune.argtypes = [P, P, P, P, I32, P, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
         lib.gblu_solve_multi.argtypes = [I32, P, P, P, P]
         lib.gblu_solve.argtypes = [P, P, P, P]
         lib.gblu_residual.argtypes = [P, P, P, P, P, P]
@@ -143,7 +148,7 @@ def load(build_if_missing: bool = True):
         lib.gblu_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, I64, I32, ctypes.POINTER(Opts)]
         lib.gblu_server_add_pattern.argtypes = [P, I32, P, P, P, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
         lib.gblu_server_pattern_info.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)]
-        lib.gblu_server_submit.argtypes = [P, I32, P, P, P, ctypes.POINTER(I64)]
+        lib.gblu_server_submit.argtypes = [P, I32, P, P, P, I32, ctypes.POINTER(I64)]
         lib.gblu_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(RequestResult)]
         lib.gblu_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
         lib.gblu_server_destroy.argtypes = [P]
@@ -155,7 +160,8 @@ def load(build_if_missing: bool = True):
                   "gblu_solve", "gblu_residual", "gblu_get_stats", "gblu_export_factors",
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
                   "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
-                  "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step"):
+                  "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts",
+                  "gblu_set_opts", "gblu_autotune"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -253,6 +259,34 @@ class Solver:
         rc = _check(load().gblu_refactorize(self._h, _dev_ptr(Ax, self.device, self.nnz),
                                             _stream(stream), ctypes.byref(rep)))
         return rc, bool(rep.value)
+
+    def opts(self):
+        o = Opts()
+        _check(load().gblu_get_opts(self._h, ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in Opts._fields_}
+
+    def set_opts(self, stream=None, **kw):
+        """Change options; the schedule is rebuilt for the current factors."""
+        o = Opts()
+        _check(load().gblu_get_opts(self._h, ctypes.byref(o)))
+        for k, v in kw.items():
+            if k in ("sched_mode", "solve_mode") and isinstance(v, str):
+                v = SCHED[v]
+            setattr(o, k, v)
+        _check(load().gblu_set_opts(self._h, ctypes.byref(o), _stream(stream)))
+
+    def autotune(self, Ax, b, x=None, reps=3, stream=None):
+        """Measure schedule options on this matrix and keep the fastest;
+        returns (chosen options, refactor ms, solve ms)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        o = Opts()
+        tr, ts = ctypes.c_double(0), ctypes.c_double(0)
+        _check(load().gblu_autotune(self._h, _dev_ptr(Ax, self.device, self.nnz), _dev_ptr(b, self.device, self.n),
+                                    _dev_ptr(x, self.device, self.n), int(reps), _stream(stream), ctypes.byref(o),
+                                    ctypes.byref(tr), ctypes.byref(ts)))
+        return {f: getattr(o, f) for f, _ in Opts._fields_}, tr.value, ts.value
 
     def step(self, Ax, b, x=None, stream=None):
         """Checked re-factorization and solve replayed from a CUDA graph
@@ -507,8 +541,9 @@ class Server:
                                                       ctypes.byref(fp)))
         return {"slots": slots.value, "footprint_bytes": fp.value}
 
-    def submit(self, pattern, Ax, b, x=None):
-        """Queue a request; returns its id.  x (host float64[n]) receives the solution."""
+    def submit(self, pattern, Ax, b, x=None, mixed=False):
+        """Queue a request; returns its id.  x (host float64[n]) receives the
+        solution.  mixed=True: single-precision factors with refinement."""
         n, nnz = self._pat[pattern]
         Ax = np.ascontiguousarray(Ax, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
@@ -520,7 +555,7 @@ class Server:
             raise ValueError("x must be a contiguous float64 array of n entries")
         rid = ctypes.c_int64(0)
         _check_server(load().gblu_server_submit(self._s, int(pattern), _np_ptr(Ax), _np_ptr(b), _np_ptr(x),
-                                                ctypes.byref(rid)))
+                                                1 if mixed else 0, ctypes.byref(rid)))
         self._live[rid.value] = (Ax, b, x)
         return rid.value
 

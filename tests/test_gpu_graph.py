@@ -62,3 +62,30 @@ def test_step_equals_refactorize_and_solve(case):
         assert O.residual(n, Ap, Ai, Ax, xg.cpu().numpy(), b) <= 1e-12
     st = g.stats()
     assert st["n_refactor"] == 6 and st["kernel_launches"] > 0
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes the schedule: the factors of the same
+    values are bit for bit the same, and the solve still meets the residual."""
+    ckt = inputs.rc_mesh3d(24, 24, 4, seed=5, n_fet=60)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    s.factorize(dev(Ax0))
+    rng = np.random.default_rng(4)
+    Ax = inputs.redraw_transistors(ckt, rng).values()
+    b = inputs.rhs(n, rng)
+    s.refactorize(dev(Ax))
+    f0 = s.export_factors()
+    chosen, tr, ts = s.autotune(dev(Ax), dev(b), reps=2)
+    assert chosen["alpha"] in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0) and tr > 0 and ts > 0
+    assert s.opts()["alpha"] == chosen["alpha"]
+    s.refactorize(dev(Ax))
+    f1 = s.export_factors()
+    for k in f0:
+        assert np.array_equal(f0[k], f1[k]), k
+    x = s.solve(dev(b)).cpu().numpy()
+    assert O.residual(n, Ap, Ai, Ax, x, b) <= 1e-12
+    with pytest.raises(gblu.GbluError):
+        s.set_opts(alpha=-1.0)

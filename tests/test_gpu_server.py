@@ -137,3 +137,21 @@ def test_admission_by_device_memory():
     with pytest.raises(gblu.GbluError):
         srv.wait(10 ** 9)                    # unknown request
     srv.close()
+
+
+def test_single_precision_requests():
+    """Mode 1 requests (single-precision factors, refinement in double)
+    reach the double-precision backward error, mixed with mode 0 ones."""
+    case = pattern_cases()[1]
+    ckt, n, Ap, Ai, Ax0, Q = case
+    reqs = clean_requests(case, 10, 9)
+    srv = gblu.Server(DEV, hbm_budget=2 << 30, max_batch=8)
+    pid, _ = srv.add_pattern(n, Ap, Ai, Q, Ax0)
+    ids = [(j, srv.submit(pid, *r, mixed=(j % 2 == 1))) for j, r in enumerate(reqs)]
+    for j, rid in ids:
+        x, r = srv.wait(rid)
+        assert r["status"] in (gblu.OK, gblu.REPIVOTED)
+        assert r["berr"] <= 1e-12 and O.residual(n, Ap, Ai, reqs[j][0], x, reqs[j][1]) <= 1e-12
+        if j % 2 == 1:
+            assert r["batch_size"] == 1 and r["refine_iters"] != 0 or r["berr"] <= 1e-12
+    srv.close()

@@ -163,5 +163,5 @@ def test_server_argument_errors_without_a_device():
     assert lib.gblu_server_create(ctypes.byref(s), 0, 1 << 30, 0, None) == gblu.ERR_INVALID_INPUT
     assert lib.gblu_server_create(ctypes.byref(s), 999, 1 << 30, 4, None) == gblu.ERR_CUDA
     assert b"not available" in lib.gblu_server_last_error()
-    assert lib.gblu_server_submit(None, 0, None, None, None, None) == gblu.ERR_INVALID_INPUT
+    assert lib.gblu_server_submit(None, 0, None, None, None, 0, None) == gblu.ERR_INVALID_INPUT
     lib.gblu_server_destroy(None)
