@@ -630,7 +630,7 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_dense_frac = 0.7;
     o->solve_dense_min = 300000;
     o->solve_slices = 8;
-    o->solve_dense_density = 0.5;
+    o->solve_dense_density = 0.9;
     o->dense_min_rows = 0;
 }
 
