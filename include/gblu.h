@@ -412,6 +412,33 @@ int gblu_server_wait(gblu_server s, int64_t request, double timeout_s, gblu_requ
 int gblu_server_get_stats(gblu_server s, gblu_server_stats *st);
 void gblu_server_destroy(gblu_server s);
 
+/*
+ * Static pivoting and scaling (the optional pre-processing of Section
+ * III-A).  Host-only.
+ * gblu_static_pivot: a row permutation maximizing the product of the
+ *   diagonal magnitudes, with scalings that make the matched entries 1 and
+ *   every entry at most 1 in magnitude.  match[j] = the row of A placed on
+ *   the diagonal in column j (so (P A)(j, :) = A(match[j], :));
+ *   row_scale[i], col_scale[j] (optional) = Dr, Dc with
+ *   |Dr[i] a_ij Dc[j]| <= 1 and = 1 where i = match[j].  Entries stored
+ *   with value 0 are not used.  GBLU_ERR_SINGULAR if no perfect matching
+ *   exists on the nonzero entries.
+ * gblu_permute_rows: the CSC pattern of P A: Ai_out[e'] (rows sorted in
+ *   each column) and src_out[e'] = the entry of A that lands in slot e'.
+ * The scaled system Dr P A Dc y = Dr P b gives x = Dc y.  Per value set,
+ * Ax'[e'] = Ax[src[e']] * Dr[Ai[src[e']]] * Dc[j] and b'[j] =
+ * b[match[j]] * Dr[match[j]] are one gblu_gather_scale each, and so is
+ * x = Dc * y (src = NULL).
+ * gblu_gather_scale: out[k] = in[src[k]] * scale[k] for k < m, on the
+ *   device (src NULL: in[k]; scale NULL: 1).  Asynchronous on `stream`.
+ */
+int gblu_static_pivot(int32_t n, const int32_t *Ap, const int32_t *Ai, const double *Ax, int32_t *match,
+                      double *row_scale, double *col_scale);
+int gblu_permute_rows(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *match, int32_t *Ai_out,
+                      int32_t *src_out);
+int gblu_gather_scale(int64_t m, const int32_t *src_dev, const double *scale_dev, const double *in_dev,
+                      double *out_dev, void *stream);
+
 /* Sizes and counters of the current factorization (host struct). */
 typedef struct {
     int32_t n;

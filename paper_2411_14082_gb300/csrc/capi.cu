@@ -1313,6 +1313,16 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
     return GBLU_REPIVOTED;
 }
 
+int gblu_gather_scale(int64_t m, const int32_t *src_dev, const double *scale_dev, const double *in_dev,
+                      double *out_dev, void *stream)
+{
+    if (m < 0 || !in_dev || !out_dev) return fail(GBLU_ERR_INVALID_INPUT, "gather_scale: m >= 0 and non-null vectors");
+    if (in_dev == out_dev && src_dev) return fail(GBLU_ERR_INVALID_INPUT, "gather_scale: a gather cannot be in place");
+    const int e = launch_gather_scale(m, src_dev, scale_dev, in_dev, out_dev, stream);
+    if (e != 0) return fail(GBLU_ERR_CUDA, "gather_scale launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return GBLU_OK;
+}
+
 int gblu_get_opts(gblu_handle h, gblu_opts *o)
 {
     if (!h || !o) return fail(GBLU_ERR_INVALID_INPUT, "null pointer");

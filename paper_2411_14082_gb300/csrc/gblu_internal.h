@@ -256,6 +256,8 @@ constexpr int kDenseNb = 8;         // panel width
 int dense_setup(int max_rows);
 int launch_dense_lu(const DenseArgs2 &d, void *stream, long long *launches);
 
+int launch_gather_scale(int64_t m, const int32_t *src, const double *scale, const double *in, double *out,
+                        void *stream);
 int launch_widen(const float *src, double *dst, int64_t n, void *stream);
 int launch_axpy(double *x, const double *d, int32_t n, void *stream);
 int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream);

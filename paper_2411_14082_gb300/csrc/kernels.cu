@@ -940,6 +940,17 @@ __global__ void residual_final_kernel(const double *partial, int nblocks, double
 
 // mixed precision: single-precision factor values widened for the FP64
 // solves of iterative refinement, and the correction step x += d
+// out[k] = in[src[k]] * scale[k] (src == nullptr: in[k]); the per-step
+// application of a static row permutation and scaling to values and vectors
+__global__ void gather_scale_kernel(int64_t m, const int32_t *src, const double *scale, const double *in,
+                                    double *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = __ldg(in + (src ? __ldg(src + k) : k));
+        out[k] = scale ? v * __ldg(scale + k) : v;
+    }
+}
+
 __global__ void widen_kernel(const float *src, double *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1184,6 +1195,16 @@ int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol, const in
 {
     residual_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(n, Arp, Acol, Aslot, Ax, b, x, partial, rvec);
     residual_final_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nblocks, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_gather_scale(int64_t m, const int32_t *src, const double *scale, const double *in, double *out,
+                        void *stream)
+{
+    if (m <= 0) return 0;
+    int64_t g = (m + 255) / 256;
+    if (g > 8192) g = 8192;
+    gather_scale_kernel<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(m, src, scale, in, out);
     return (int)cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ EXPORTED = [
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
-    "gblu_autotune",
+    "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -121,6 +121,9 @@ def load(build_if_missing: bool = True):
         lib.gblu_refactorize_multi.argtypes = [I32, P, P, P, P]
         lib.gblu_step.argtypes = [P, P, P, P, P, ctypes.POINTER(I32)]
         lib.gblu_get_opts.argtypes = [P, ctypes.POINTER(Opts)]
+        lib.gblu_static_pivot.argtypes = [I32, P, P, P, P, P, P]
+        lib.gblu_permute_rows.argtypes = [I32, P, P, P, P, P]
+        lib.gblu_gather_scale.argtypes = [I64, P, P, P, P, P]
         lib.gblu_set_opts.argtypes = [P, ctypes.POINTER(Opts), P]
         lib.gblu_autotune.argtypes = [P, P, P, P, I32, P, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
@@ -161,7 +164,8 @@ def load(build_if_missing: bool = True):
                   "gblu_order_mindeg", "gblu_column_etree", "gblu_refactorize_batch", "gblu_solve_batch",
                   "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
                   "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts",
-                  "gblu_set_opts", "gblu_autotune"):
+                  "gblu_set_opts", "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows",
+                  "gblu_gather_scale"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -496,6 +500,74 @@ def solve_multi(solvers, b_list, x_list=None, stream=None):
     xp = (ctypes.c_void_p * nh)(*[_dev_ptr(x, dev, s.n) for s, x in zip(solvers, x_list)])
     _check(load().gblu_solve_multi(nh, hs, bp, xp, _stream(stream)))
     return x_list
+
+
+def static_pivot(n, Ap, Ai, Ax):
+    """Maximum-product static pivoting with scaling (gblu_static_pivot, host):
+    returns (match, row_scale, col_scale)."""
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    Ax = np.ascontiguousarray(Ax, dtype=np.float64)
+    match = np.empty(n, np.int32)
+    dr = np.empty(n, np.float64)
+    dc = np.empty(n, np.float64)
+    _check(load().gblu_static_pivot(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Ax), _np_ptr(match), _np_ptr(dr),
+                                    _np_ptr(dc)))
+    return match, dr, dc
+
+
+def permute_rows(n, Ap, Ai, match):
+    """Pattern of P A (gblu_permute_rows): (Ai_out, src)."""
+    Ap, Ai, match = _i32(Ap), _i32(Ai), _i32(match)
+    Ai2 = np.empty_like(Ai)
+    src = np.empty_like(Ai)
+    _check(load().gblu_permute_rows(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(match), _np_ptr(Ai2), _np_ptr(src)))
+    return Ai2, src
+
+
+def gather_scale(inp, out, src=None, scale=None, stream=None):
+    """out[k] = inp[src[k]] * scale[k] on the device (gblu_gather_scale)."""
+    dev = out.device.index
+    m = out.numel()
+    sp = None if src is None else ctypes.c_void_p(src.data_ptr())
+    cp = None if scale is None else _dev_ptr(scale, dev, m)
+    _check(load().gblu_gather_scale(int(m), sp, cp, _dev_ptr(inp, dev), _dev_ptr(out, dev, m), _stream(stream)))
+    return out
+
+
+class StaticScaling:
+    """A pattern with static pivoting and scaling: analyze the returned
+    pattern (Ap, Ai_scaled), then per value set map values and right-hand
+    side to the scaled system on the device and map its solution back."""
+
+    def __init__(self, n, Ap, Ai, Ax, device=0):
+        import torch
+        self.n = int(n)
+        self.match, self.dr, self.dc = static_pivot(n, Ap, Ai, Ax)
+        self.Ai_scaled, src = permute_rows(n, Ap, Ai, self.match)
+        Ap, Ai = _i32(Ap), _i32(Ai)
+        col = np.repeat(np.arange(n, dtype=np.int64), np.diff(Ap))
+        scale = self.dr[Ai[src]] * self.dc[col]
+        d = f"cuda:{device}"
+        self._src = torch.from_numpy(src.astype(np.int32)).to(d)
+        self._scale = torch.from_numpy(scale).to(d)
+        self._bsrc = torch.from_numpy(self.match.astype(np.int32)).to(d)
+        self._bscale = torch.from_numpy(self.dr[self.match]).to(d)
+        self._dc = torch.from_numpy(self.dc).to(d)
+
+    def values(self, Ax, out=None, stream=None):
+        import torch
+        out = torch.empty_like(Ax) if out is None else out
+        return gather_scale(Ax, out, self._src, self._scale, stream)
+
+    def rhs(self, b, out=None, stream=None):
+        import torch
+        out = torch.empty_like(b) if out is None else out
+        return gather_scale(b, out, self._bsrc, self._bscale, stream)
+
+    def solution(self, y, out=None, stream=None):
+        import torch
+        out = torch.empty_like(y) if out is None else out
+        return gather_scale(y, out, None, self._dc, stream)
 
 def _check_server(code):
     if code < 0:

@@ -1,0 +1,59 @@
+"""Static pivoting and scaling on the device path: the scaled system
+Dr P A Dc y = Dr P b is factorized and solved by the library, x = Dc y
+solves the original system to the residual bound, agrees with the oracle's
+solution, and the preferred (diagonal) pivots are kept more often."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+from oracle import oracle as O
+from paper_2411_14082_gb300 import gblu, inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = 0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(f"cuda:{DEV}")
+
+
+def off_diagonal_pivots(s):
+    f = s.export_factors()
+    return int(np.sum(f["piv"] != f["q"]))
+
+
+@pytest.mark.parametrize("case", ["small_mna", "mesh_ill"])
+def test_scaled_system_solves_the_original(case):
+    if case == "small_mna":
+        ckt = inputs.workload_small()
+        step = lambda c, r: inputs.perturb_elements(c, r)
+    else:
+        ckt = inputs.rc_mesh3d(20, 20, 3, seed=9, n_fet=40, g_range=(1e-9, 1e4))
+        step = lambda c, r: inputs.redraw_transistors(c, r)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    ss = gblu.StaticScaling(n, Ap, Ai, Ax0, device=DEV)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, ss.Ai_scaled, Q)
+    s.factorize(ss.values(dev(Ax0)))
+    plain = gblu.Solver(DEV)
+    plain.analyze(n, Ap, Ai, Q)
+    plain.factorize(dev(Ax0))
+    assert off_diagonal_pivots(s) <= off_diagonal_pivots(plain)
+    lu = O.factorize(n, Ap, Ai, Ax0, Q, 1e-3)
+    rng = np.random.default_rng(3)
+    for it in range(3):
+        ckt = step(ckt, rng)
+        Ax = ckt.values()
+        b = inputs.rhs(n, rng)
+        s.refactorize(ss.values(dev(Ax)))
+        x = ss.solution(s.solve(ss.rhs(dev(b)))).cpu().numpy()
+        assert O.residual(n, Ap, Ai, Ax, x, b) <= 1e-12
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        xo = O.solve(lu, b)
+        A = sp.csc_matrix((Ax, Ai, Ap), shape=(n, n))
+        bound = 2.0 * np.abs(np.linalg.inv(A.toarray())).sum(axis=1).max() * (
+            np.abs(b - A @ x).max() + np.abs(b - A @ xo).max())
+        assert np.abs(x - xo).max() <= bound
