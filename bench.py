@@ -38,10 +38,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate of the profiling recipe (non-tensor 
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4": {"refactor_cu_sha256": "e6b9749761d2774e4e59eaaecf484b43d1dbca9969cb0904f1b34d9b6914f93b",
-                          "bytes": 16.366e9 + 444.4e6},
-    "rc_mesh_120x120x4": {"refactor_cu_sha256": "e6b9749761d2774e4e59eaaecf484b43d1dbca9969cb0904f1b34d9b6914f93b",
-                          "bytes": 135.0e6 + 82.4e6},
+    "rc_mesh_200x200x4": {"refactor_cu_sha256": "ec9d1c08d07ee3881fd0d695d186421b7744c7a3ba463b68ddffe3c336db25fb",
+                          "bytes": 16.346e9 + 445.4e6},
+    "rc_mesh_120x120x4": {"refactor_cu_sha256": "ec9d1c08d07ee3881fd0d695d186421b7744c7a3ba463b68ddffe3c336db25fb",
+                          "bytes": 136.0e6 + 82.9e6},
 }
 
 
