@@ -485,6 +485,15 @@ int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx,
 /* Minimum-degree column order of the pattern of A + A^T: perm[k] = column
  * eliminated at step k. */
 int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Nested dissection column order of the pattern of A + A^T, without
+ * coordinates (multilevel: heavy-edge coarsening, greedy growing bisection,
+ * boundary refinement, vertex cover of the cut edges as separator; sets of
+ * at most 256 vertices by minimum degree).  Deterministic.  gblu_analyze
+ * uses it when Q is NULL and n > 20000 (minimum degree below that). */
+int gblu_order_nd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Entries of the strict lower Cholesky factor of (A + A^T)(Q,Q): the fill of
+ * an ordering when every diagonal pivot is kept; negative on invalid input. */
+int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q);
 /* Column elimination tree of A(:,Q) (elimination tree of (A Q)^T (A Q)),
  * parent[k] = parent step of step k or -1 (Section II-B "ETree"). */
 int gblu_column_etree(int32_t n, const int32_t *Ap, const int32_t *Ai,

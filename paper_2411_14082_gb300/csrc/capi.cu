@@ -748,6 +748,8 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
             seen[Q[k]] = 1;
             P.Q[k] = Q[k];
         }
+    } else if (n > 20000) {
+        nd_order(n, Ap, Ai, P.Q.data(), 256);
     } else {
         mindeg_order(n, Ap, Ai, P.Q.data());
     }

@@ -103,6 +103,9 @@ int record_error(int code, const char *msg);
 int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
 void column_etree(const Pattern &P, std::vector<int32_t> &parent);
 void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+// multilevel nested dissection (nd_order.cpp); sets of at most `leaf`
+// vertices are ordered by minimum degree
+void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf);
 // nnz of the Cholesky factor of (A + A^T)(Q,Q) (strict lower part), the
 // size of the LU factors when every diagonal pivot is kept on a structurally
 // symmetric matrix; used to size the first factorization's pool

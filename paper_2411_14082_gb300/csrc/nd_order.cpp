@@ -1,0 +1,414 @@
+// Nested dissection ordering of a general sparse pattern (the fill-reducing
+// ordering family of Section III-A for mesh-like matrices), without
+// coordinates.
+//
+// The graph is that of A + A^T without the diagonal.  A vertex set is split
+// by a vertex separator, the two halves are ordered recursively and the
+// separator is numbered after both; small sets (and sets that do not split
+// well) are ordered by minimum degree.  Each split is multilevel:
+//   coarsen  - heavy-edge matching, repeated until the graph is small;
+//   bisect   - greedy graph growing from a few seeds on the coarsest graph,
+//              keeping the smallest edge cut with balanced vertex weight;
+//   refine   - projected back level by level, each level improved by
+//              Fiduccia-Mattheyses passes (moves of the largest gain, also
+//              negative, under the balance bound; rollback to the best cut);
+//   separate - a vertex cover of the cut edges (greedy, endpoint with more
+//              cut edges first) becomes the separator; separator vertices
+//              with no neighbour on one side then leave it.
+// Random choices use a fixed-seed generator, so the ordering is
+// deterministic.
+#include <algorithm>
+#include <cstdint>
+#include <numeric>
+#include <queue>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "gblu_internal.h"
+
+namespace {
+
+struct Graph {
+    int32_t n = 0;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> adj, ew;   // neighbours and edge weights
+    std::vector<int32_t> vw;        // vertex weights
+    int64_t total_w() const { return std::accumulate(vw.begin(), vw.end(), int64_t(0)); }
+};
+
+// the graph induced by `verts` (global ids) in the global graph g
+Graph induced(const Graph &g, const std::vector<int32_t> &verts, std::vector<int32_t> &local)
+{
+    Graph s;
+    s.n = (int32_t)verts.size();
+    for (int32_t i = 0; i < s.n; i++) local[verts[i]] = i;
+    s.ptr.assign(s.n + 1, 0);
+    for (int32_t i = 0; i < s.n; i++) {
+        const int32_t v = verts[i];
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++)
+            if (local[g.adj[e]] >= 0) {
+                s.adj.push_back(local[g.adj[e]]);
+                s.ew.push_back(1);
+            }
+        s.ptr[i + 1] = (int64_t)s.adj.size();
+    }
+    s.vw.assign(s.n, 1);
+    for (int32_t v : verts) local[v] = -1;
+    return s;
+}
+
+// heavy-edge matching; cmap[v] = coarse vertex of v
+Graph coarsen(const Graph &g, std::vector<int32_t> &cmap, std::mt19937 &rng)
+{
+    std::vector<int32_t> order(g.n), match(g.n, -1);
+    std::iota(order.begin(), order.end(), 0);
+    std::shuffle(order.begin(), order.end(), rng);
+    for (int32_t v : order) {
+        if (match[v] >= 0) continue;
+        int32_t best = -1, bw = -1;
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++) {
+            const int32_t u = g.adj[e];
+            if (u != v && match[u] < 0 && g.ew[e] > bw) {
+                bw = g.ew[e];
+                best = u;
+            }
+        }
+        if (best >= 0) {
+            match[v] = best;
+            match[best] = v;
+        } else {
+            match[v] = v;
+        }
+    }
+    cmap.assign(g.n, -1);
+    int32_t nc = 0;
+    for (int32_t v = 0; v < g.n; v++) {
+        if (cmap[v] >= 0) continue;
+        cmap[v] = nc;
+        cmap[match[v]] = nc;
+        nc++;
+    }
+    Graph c;
+    c.n = nc;
+    c.vw.assign(nc, 0);
+    for (int32_t v = 0; v < g.n; v++) c.vw[cmap[v]] += g.vw[v];
+    std::vector<std::vector<int32_t>> members(nc);
+    for (int32_t v = 0; v < g.n; v++) members[cmap[v]].push_back(v);
+    std::vector<int32_t> slot(nc, -1);
+    c.ptr.assign(nc + 1, 0);
+    for (int32_t cv = 0; cv < nc; cv++) {
+        const int64_t start = (int64_t)c.adj.size();
+        for (int32_t v : members[cv])
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++) {
+                const int32_t cu = cmap[g.adj[e]];
+                if (cu == cv) continue;
+                if (slot[cu] < 0) {
+                    slot[cu] = (int32_t)c.adj.size();
+                    c.adj.push_back(cu);
+                    c.ew.push_back(g.ew[e]);
+                } else {
+                    c.ew[slot[cu]] += g.ew[e];
+                }
+            }
+        for (int64_t e = start; e < (int64_t)c.adj.size(); e++) slot[c.adj[e]] = -1;
+        c.ptr[cv + 1] = (int64_t)c.adj.size();
+    }
+    return c;
+}
+
+int64_t cut_of(const Graph &g, const std::vector<uint8_t> &part)
+{
+    int64_t cut = 0;
+    for (int32_t v = 0; v < g.n; v++)
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++)
+            if (part[v] != part[g.adj[e]]) cut += g.ew[e];
+    return cut / 2;
+}
+
+// greedy graph growing from `seeds` random starts: part 0 grows by BFS
+// until it holds half of the vertex weight
+std::vector<uint8_t> grow_bisect(const Graph &g, std::mt19937 &rng, int seeds)
+{
+    const int64_t W = g.total_w();
+    std::vector<uint8_t> best(g.n, 0);
+    int64_t best_cut = -1;
+    std::vector<uint8_t> part(g.n);
+    std::vector<int32_t> queue;
+    std::uniform_int_distribution<int32_t> pick(0, g.n - 1);
+    for (int s = 0; s < seeds; s++) {
+        std::fill(part.begin(), part.end(), 1);
+        int64_t w0 = 0;
+        queue.clear();
+        std::vector<uint8_t> seen(g.n, 0);
+        int32_t head = 0;
+        int32_t start = pick(rng);
+        queue.push_back(start);
+        seen[start] = 1;
+        while (w0 * 2 < W) {
+            if (head == (int32_t)queue.size()) {   // another component: restart from an unseen vertex
+                int32_t u = -1;
+                for (int32_t t = 0; t < g.n; t++)
+                    if (!seen[t]) {
+                        u = t;
+                        break;
+                    }
+                if (u < 0) break;
+                seen[u] = 1;
+                queue.push_back(u);
+            }
+            const int32_t v = queue[head++];
+            part[v] = 0;
+            w0 += g.vw[v];
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++) {
+                const int32_t u = g.adj[e];
+                if (!seen[u]) {
+                    seen[u] = 1;
+                    queue.push_back(u);
+                }
+            }
+        }
+        const int64_t c = cut_of(g, part);
+        if (best_cut < 0 || c < best_cut) {
+            best_cut = c;
+            best = part;
+        }
+    }
+    return best;
+}
+
+// Fiduccia-Mattheyses passes: repeatedly move the unlocked vertex of
+// largest cut gain (negative gains too) whose move keeps both sides within
+// [lo, hi] of the vertex weight, lock it, and at the end of the pass roll
+// back to the smallest cut seen
+void refine(const Graph &g, std::vector<uint8_t> &part, int passes)
+{
+    const int64_t W = g.total_w();
+    const int64_t lo = (int64_t)(0.40 * (double)W), hi = W - lo;
+    std::vector<int64_t> gain(g.n);
+    std::vector<uint8_t> locked(g.n);
+    using Item = std::pair<int64_t, int32_t>;
+    for (int p = 0; p < passes; p++) {
+        int64_t w0 = 0, cut = 0;
+        for (int32_t v = 0; v < g.n; v++) {
+            if (part[v] == 0) w0 += g.vw[v];
+            int64_t ext = 0, in = 0;
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++)
+                (part[g.adj[e]] != part[v] ? ext : in) += g.ew[e];
+            gain[v] = ext - in;
+            cut += ext;
+        }
+        cut /= 2;
+        std::priority_queue<Item> pq;
+        for (int32_t v = 0; v < g.n; v++) {
+            locked[v] = 0;
+            bool boundary = false;
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1] && !boundary; e++) boundary = part[g.adj[e]] != part[v];
+            if (boundary) pq.push({gain[v], v});
+        }
+        std::vector<int32_t> moves;
+        int64_t best_cut = cut, cur = cut;
+        size_t best_len = 0;
+        const size_t limit = std::max<size_t>(64, (size_t)g.n / 50);
+        while (!pq.empty()) {
+            const Item it = pq.top();
+            pq.pop();
+            const int32_t v = it.second;
+            if (locked[v] || it.first != gain[v]) continue;
+            const int64_t nw0 = part[v] == 0 ? w0 - g.vw[v] : w0 + g.vw[v];
+            if (nw0 < lo || nw0 > hi) continue;
+            locked[v] = 1;
+            part[v] ^= 1;
+            w0 = nw0;
+            cur -= gain[v];
+            moves.push_back(v);
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; e++) {
+                const int32_t u = g.adj[e];
+                if (locked[u]) continue;
+                gain[u] += (part[u] == part[v]) ? -2 * (int64_t)g.ew[e] : 2 * (int64_t)g.ew[e];
+                pq.push({gain[u], u});
+            }
+            if (cur < best_cut) {
+                best_cut = cur;
+                best_len = moves.size();
+            } else if (moves.size() - best_len > limit) {
+                break;
+            }
+        }
+        for (size_t k = moves.size(); k-- > best_len;) part[moves[k]] ^= 1;
+        if (best_len == 0) break;
+    }
+}
+
+// multilevel bisection of g
+std::vector<uint8_t> bisect(const Graph &g, std::mt19937 &rng)
+{
+    std::vector<Graph> levels;
+    std::vector<std::vector<int32_t>> maps;
+    levels.push_back(g);
+    while (levels.back().n > 160 && levels.size() < 40) {
+        std::vector<int32_t> cmap;
+        Graph c = coarsen(levels.back(), cmap, rng);
+        if (c.n > (int32_t)(0.95 * levels.back().n)) break;   // matching stalled
+        maps.push_back(std::move(cmap));
+        levels.push_back(std::move(c));
+    }
+    std::vector<uint8_t> part = grow_bisect(levels.back(), rng, 8);
+    refine(levels.back(), part, 8);
+    for (int l = (int)levels.size() - 2; l >= 0; l--) {
+        std::vector<uint8_t> fine(levels[l].n);
+        for (int32_t v = 0; v < levels[l].n; v++) fine[v] = part[maps[l][v]];
+        part.swap(fine);
+        refine(levels[l], part, 4);
+    }
+    return part;
+}
+
+struct Ordering {
+    const Graph &g;
+    std::vector<int32_t> &out;
+    std::vector<int32_t> local;
+    std::mt19937 rng{20241121u};
+    int32_t leaf;
+
+    void by_mindeg(const std::vector<int32_t> &verts)
+    {
+        if (verts.size() <= 2) {
+            out.insert(out.end(), verts.begin(), verts.end());
+            return;
+        }
+        Graph s = induced(g, verts, local);
+        std::vector<int32_t> Ap(s.ptr.begin(), s.ptr.end()), perm(s.n);
+        gblu::mindeg_order(s.n, Ap.data(), s.adj.data(), perm.data());
+        for (int32_t i = 0; i < s.n; i++) out.push_back(verts[perm[i]]);
+    }
+
+    // vertex separator of a bisection: side[v] = 0 / 1, or 2 for the separator
+    static std::vector<uint8_t> separate(const Graph &s, const std::vector<uint8_t> &part)
+    {
+        // a vertex cover of the cut edges, endpoint with more cut edges first
+        std::vector<int32_t> cdeg(s.n, 0);
+        for (int32_t v = 0; v < s.n; v++)
+            for (int64_t e = s.ptr[v]; e < s.ptr[v + 1]; e++)
+                if (part[v] != part[s.adj[e]]) cdeg[v]++;
+        std::vector<int32_t> byc;
+        for (int32_t v = 0; v < s.n; v++)
+            if (cdeg[v] > 0) byc.push_back(v);
+        std::sort(byc.begin(), byc.end(), [&](int32_t a, int32_t b) { return cdeg[a] != cdeg[b] ? cdeg[a] > cdeg[b] : a < b; });
+        std::vector<uint8_t> side(part.begin(), part.end());
+        for (int32_t v : byc) {
+            bool needed = false;   // an uncovered cut edge left at v
+            for (int64_t e = s.ptr[v]; e < s.ptr[v + 1]; e++) {
+                const int32_t u = s.adj[e];
+                if (side[u] != 2 && side[u] != side[v] && side[v] != 2) {
+                    needed = true;
+                    break;
+                }
+            }
+            if (needed) side[v] = 2;
+        }
+        // refinement: a separator vertex with no neighbour on one side
+        // joins the other side (repeat while that shrinks the separator)
+        for (int pass = 0; pass < 8; pass++) {
+            int moved = 0;
+            int64_t w[2] = {0, 0};
+            for (int32_t v = 0; v < s.n; v++)
+                if (side[v] < 2) w[side[v]] += s.vw[v];
+            for (int32_t v = 0; v < s.n; v++) {
+                if (side[v] != 2) continue;
+                bool has[2] = {false, false};
+                for (int64_t e = s.ptr[v]; e < s.ptr[v + 1]; e++)
+                    if (side[s.adj[e]] < 2) has[side[s.adj[e]]] = true;
+                if (has[0] && has[1]) continue;
+                const int to = !has[0] && !has[1] ? (w[0] <= w[1] ? 0 : 1) : (has[0] ? 0 : 1);
+                side[v] = (uint8_t)to;
+                w[to] += s.vw[v];
+                moved++;
+            }
+            if (!moved) break;
+        }
+        return side;
+    }
+
+    void rec(std::vector<int32_t> verts, int depth)
+    {
+        if ((int32_t)verts.size() <= leaf || depth > 60) {
+            by_mindeg(verts);
+            return;
+        }
+        Graph s = induced(g, verts, local);
+        // a few multilevel trials; keep the smallest separator
+        std::vector<uint8_t> side;
+        int64_t best = -1;
+        for (int t = 0; t < 3; t++) {
+            std::vector<uint8_t> sd = separate(s, bisect(s, rng));
+            int64_t ns = 0, n0 = 0, n1 = 0;
+            for (uint8_t x : sd) (x == 2 ? ns : x == 0 ? n0 : n1)++;
+            if (n0 == 0 || n1 == 0) continue;
+            if (best < 0 || ns < best) {
+                best = ns;
+                side.swap(sd);
+            }
+        }
+        if (best < 0) {
+            by_mindeg(verts);
+            return;
+        }
+        std::vector<int32_t> a, b, sep;
+        for (int32_t v = 0; v < s.n; v++) (side[v] == 2 ? sep : side[v] == 0 ? a : b).push_back(verts[v]);
+        if (a.empty() || b.empty() || sep.size() * 3 > verts.size()) {   // no useful split
+            by_mindeg(verts);
+            return;
+        }
+        rec(std::move(a), depth + 1);
+        rec(std::move(b), depth + 1);
+        out.insert(out.end(), sep.begin(), sep.end());
+    }
+};
+
+}  // namespace
+
+namespace gblu {
+
+void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf)
+{
+    Graph g;
+    g.n = n;
+    std::vector<std::vector<int32_t>> nb(n);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = Ap[c]; p < Ap[c + 1]; p++) {
+            const int32_t r = Ai[p];
+            if (r == c) continue;
+            nb[r].push_back(c);
+            nb[c].push_back(r);
+        }
+    g.ptr.assign(n + 1, 0);
+    for (int32_t v = 0; v < n; v++) {
+        std::sort(nb[v].begin(), nb[v].end());
+        nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+        g.adj.insert(g.adj.end(), nb[v].begin(), nb[v].end());
+        g.ptr[v + 1] = (int64_t)g.adj.size();
+        std::vector<int32_t>().swap(nb[v]);
+    }
+    g.ew.assign(g.adj.size(), 1);
+    g.vw.assign(n, 1);
+    std::vector<int32_t> out;
+    out.reserve(n);
+    Ordering o{g, out, std::vector<int32_t>(n, -1)};
+    o.leaf = leaf;
+    std::vector<int32_t> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    o.rec(std::move(all), 0);
+    std::copy(out.begin(), out.end(), perm);
+}
+
+}  // namespace gblu
+
+extern "C" int gblu_order_nd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    std::string err;
+    if (gblu::validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm)
+        return gblu::record_error(GBLU_ERR_INVALID_INPUT, "order_nd: invalid pattern or null perm");
+    gblu::nd_order(n, Ap, Ai, perm, 256);
+    return GBLU_OK;
+}

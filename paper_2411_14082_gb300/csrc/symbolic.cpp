@@ -539,6 +539,23 @@ extern "C" int32_t gblu_levels(int32_t n, const int64_t *Up, const int32_t *Ui, 
     return nl;
 }
 
+extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !Q) return GBLU_ERR_INVALID_INPUT;
+    Pattern P;
+    P.n = n;
+    P.Ap.assign(Ap, Ap + n + 1);
+    P.Ai.assign(Ai, Ai + Ap[n]);
+    P.Q.assign(Q, Q + n);
+    P.qinv.assign(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        if (Q[k] < 0 || Q[k] >= n || P.qinv[Q[k]] >= 0) return GBLU_ERR_INVALID_INPUT;
+        P.qinv[Q[k]] = k;
+    }
+    return symmetric_fill(P);
+}
+
 extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
 {
     std::string err;

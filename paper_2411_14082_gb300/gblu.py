@@ -40,7 +40,8 @@ EXPORTED = [
     "gblu_levels", "gblu_step_host", "gblu_solve_factors_noalloc", "gblu_refactorize_batch",
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
-    "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale",
+    "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale", "gblu_order_nd",
+    "gblu_symmetric_fill",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -134,6 +135,10 @@ def load(build_if_missing: bool = True):
         lib.gblu_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
         lib.gblu_export_factors.argtypes = [P] * 9
         lib.gblu_order_mindeg.argtypes = [I32, P, P, P]
+        lib.gblu_order_nd.argtypes = [I32, P, P, P]
+        lib.gblu_order_nd.restype = ctypes.c_int
+        lib.gblu_symmetric_fill.argtypes = [I32, P, P, P]
+        lib.gblu_symmetric_fill.restype = I64
         lib.gblu_column_etree.argtypes = [I32, P, P, P, P]
         lib.gblu_restart_set.argtypes = [I32, P, P, P]
         lib.gblu_restart_set.restype = I64
@@ -443,6 +448,23 @@ def order_mindeg(n, Ap, Ai):
     perm = np.empty(n, np.int32)
     _check(load().gblu_order_mindeg(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
     return perm
+
+
+def order_nd(n, Ap, Ai):
+    """Nested dissection order without coordinates (gblu_order_nd, host)."""
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    perm = np.empty(n, np.int32)
+    _check(load().gblu_order_nd(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
+    return perm
+
+
+def symmetric_fill(n, Ap, Ai, Q):
+    """Strict lower Cholesky entries of (A + A^T)(Q,Q) (gblu_symmetric_fill, host)."""
+    Ap, Ai, Q = _i32(Ap), _i32(Ai), _i32(Q)
+    v = load().gblu_symmetric_fill(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q))
+    if v < 0:
+        raise GbluError(int(v), "invalid pattern or order")
+    return int(v)
 
 
 def column_etree(n, Ap, Ai, Q=None):

@@ -165,3 +165,29 @@ def test_server_argument_errors_without_a_device():
     assert b"not available" in lib.gblu_server_last_error()
     assert lib.gblu_server_submit(None, 0, None, None, None, 0, None) == gblu.ERR_INVALID_INPUT
     lib.gblu_server_destroy(None)
+
+
+def test_nested_dissection_order():
+    """gblu_order_nd: a deterministic permutation whose symmetric fill on a
+    mesh is close to the coordinate bisection of the generator and well
+    below minimum degree; on a path graph it is the optimum-fill family
+    (separators last, no fill at all)."""
+    ckt = inputs.rc_mesh3d(40, 40, 4, seed=3, n_fet=80)
+    n, Ap, Ai, _ = ckt.csc()
+    q1 = gblu.order_nd(n, Ap, Ai)
+    q2 = gblu.order_nd(n, Ap, Ai)
+    assert np.array_equal(q1, q2)
+    assert sorted(q1.tolist()) == list(range(n))
+    f_nd = gblu.symmetric_fill(n, Ap, Ai, q1)
+    f_geo = gblu.symmetric_fill(n, Ap, Ai, inputs.grid_nd_order(ckt))
+    f_md = gblu.symmetric_fill(n, Ap, Ai, gblu.order_mindeg(n, Ap, Ai))
+    assert f_nd <= 1.3 * f_geo and f_nd <= 1.2 * f_md
+    # tridiagonal (a path): any order from dissection keeps the fill at n-1
+    m = 3000
+    rows = [np.array([j - 1, j, j + 1]) for j in range(m)]
+    rows = [r[(r >= 0) & (r < m)] for r in rows]
+    Ap2 = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    Ai2 = np.concatenate(rows).astype(np.int32)
+    q = gblu.order_nd(m, Ap2, Ai2)
+    assert sorted(q.tolist()) == list(range(m))
+    assert gblu.symmetric_fill(m, Ap2, Ai2, q) <= 2 * (m - 1)
