@@ -34,6 +34,39 @@ sys.path.insert(0, ROOT)
 from paper_2411_14082_gb300 import inputs  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate of the profiling recipe (non-tensor ALU)
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def unit_bytes(n, nnz_a, nnz_lu):
+    """Algorithmic bytes of one refactor + solve: the refactor's compulsory
+    bytes (A values and slot map, column pointers, factor values written
+    with their row ids) and the solve's (factor values and ids read once,
+    permutation and intermediate vectors)."""
+    b_rf = nnz_a * 12 + 4 * (n + 1) + nnz_lu * 12 + 4 * nnz_a
+    b_sv = 12 * nnz_lu + 16 * (n + 1) + 32 * n
+    return b_rf + b_sv
+
+
+def hbm_roofline(bytes_alg, seconds, traffic=None):
+    """% of the HBM roofline: algorithmic (compulsory) bytes per unit over the
+    unit's time, against the measured copy bandwidth; and the measured DRAM
+    traffic rate when a capture exists."""
+    peak, src = hbm_peak_gbs()
+    gbs = bytes_alg / seconds / 1e9
+    out = {"algorithmic_gbs": gbs, "peak_gbs": peak, "peak_source": src, "frac": gbs / peak,
+           "bytes_per_unit": bytes_alg}
+    if traffic:
+        out["dram_gbs"] = traffic / seconds / 1e9
+        out["dram_frac"] = traffic / seconds / 1e9 / peak
+    return out
 # DRAM bytes (read + write) of one refactorization, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
@@ -308,6 +341,11 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None},
         "single_path": {"value": single, "unit": METRIC,
                         "note": "the same sets one at a time through gblu_refactorize + gblu_solve"},
+        # index bytes once per launch, value bytes once per set
+        "hbm_roofline": hbm_roofline(
+            (4 * nnz + 4 * (n + 1) + 8 * (st["nnz_l"] + st["nnz_u"]))
+            + args.sets * (8 * nnz + 16 * (st["nnz_l"] + st["nnz_u"]) + 16 * (n + 1) + 32 * n),
+            ev_elapsed / args.steps),
         "clocks": clk,
     }
     if rank == 0:
@@ -356,7 +394,8 @@ def run_serve_poisson(args, rank, world, local_rank):
             ckt = inputs.redraw_transistors(ckt, rng) if kind == "transistors" else inputs.perturb_elements(ckt, rng)
             vals.append(torch.from_numpy(ckt.values()).pin_memory().numpy())
             rhs.append(torch.from_numpy(inputs.rhs(n, rng)).pin_memory().numpy())
-        pats.append(dict(name=name, n=n, id=pid, slots=slots, vals=vals, rhs=rhs))
+        pats.append(dict(name=name, n=n, id=pid, slots=slots, vals=vals, rhs=rhs,
+                         ubytes=unit_bytes(n, len(Ai), srv.pattern_info(pid)["nnz_lu"])))
     t_admit = time.perf_counter() - t0
     # service time of each pattern and mode alone (after one warm request)
     svc = {}
@@ -385,7 +424,7 @@ def run_serve_poisson(args, rank, world, local_rank):
                 mode = k % 2
                 rid = srv.submit(p["id"], p["vals"][j], p["rhs"][j], mixed=bool(mode))
                 with lock:
-                    ids.append((rid, mode, p["name"]))
+                    ids.append((rid, mode, p["name"], p["ubytes"]))
 
         clocks = ClockSampler()
         clocks.start()
@@ -393,6 +432,7 @@ def run_serve_poisson(args, rank, world, local_rank):
         th = threading.Thread(target=dispatch)
         th.start()
         res = []
+        moved = [0]
         got = 0
         while got < N:
             with lock:
@@ -400,9 +440,10 @@ def run_serve_poisson(args, rank, world, local_rank):
             if not pending:
                 time.sleep(0.001)
                 continue
-            for rid, mode, name in pending:
+            for rid, mode, name, ub in pending:
                 _, r = srv.wait(rid, timeout=600.0)
                 res.append((mode, name, r))
+                moved[0] += ub
                 got += 1
         th.join()
         elapsed = time.perf_counter() - t_start
@@ -421,7 +462,8 @@ def run_serve_poisson(args, rank, world, local_rank):
                       "mean_batch": float(np.mean([r["batch_size"] for m, _, r in res if m == 0])),
                       "errors": int(sum(1 for _, _, r in res if r["status"] < 0)),
                       "max_rel_residual": float(max(r["berr"] for _, _, r in res)),
-                      "batches": st1["batches"] - st0["batches"], "clocks": clk})
+                      "batches": st1["batches"] - st0["batches"], "clocks": clk,
+                      "hbm_roofline": hbm_roofline(moved[0], elapsed)})
     st = srv.stats()
     srv.close()
     top = sweep[-1]
@@ -438,6 +480,7 @@ def run_serve_poisson(args, rank, world, local_rank):
                    "mean_solo_service_ms": 1e3 * tbar, "timing": "host wall clock",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "latency_ms_p50": top["latency_ms_p50"], "latency_ms_p99": top["latency_ms_p99"],
+        "hbm_roofline": top["hbm_roofline"],
         "max_rel_residual": max(v["max_rel_residual"] for v in sweep),
         "residual_ok": bool(max(v["max_rel_residual"] for v in sweep) <= 1e-12),
         "sweep": sweep, "server": {k: st[k] for k in ("batches", "repivots", "max_batch_seen", "reserved_bytes")},
@@ -476,7 +519,9 @@ def run_uneven(args, rank, world, local_rank):
             vals.append(torch.from_numpy(ckt.values()).cuda(dev))
             rhs.append(torch.from_numpy(inputs.rhs(n, rng)).cuda(dev))
         st = s.stats()
-        pats.append(dict(s=s, n=n, vals=vals, rhs=rhs, flops=st["flops"], x=torch.empty(n, dtype=torch.float64,
+        pats.append(dict(s=s, n=n, vals=vals, rhs=rhs, flops=st["flops"],
+                         ubytes=unit_bytes(n, len(Ai), st["nnz_l"] + st["nnz_u"]),
+                         x=torch.empty(n, dtype=torch.float64,
                                                                                          device=f"cuda:{dev}")))
     t_setup = time.perf_counter() - t0
     solvers = [p["s"] for p in pats]
@@ -537,6 +582,7 @@ def run_uneven(args, rank, world, local_rank):
                      "frac": F / float(np.mean(t_rf)) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None},
         "single_path": {"value": single, "unit": "systems/s",
                         "note": "the same systems one handle at a time (gblu_refactorize + gblu_solve)"},
+        "hbm_roofline": hbm_roofline(sum(p["ubytes"] for p in pats), t_all / args.steps),
         "clocks": clk,
     }
     if rank == 0:
@@ -574,7 +620,9 @@ def run_serve(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for p in pats:
         p["id"], p["slots"] = srv.add_pattern(p["n"], p["Ap"], p["Ai"], p["Q"], p["Ax0"])
-        p["footprint"] = srv.pattern_info(p["id"])["footprint_bytes"]
+        info = srv.pattern_info(p["id"])
+        p["footprint"] = info["footprint_bytes"]
+        p["ubytes"] = unit_bytes(p["n"], len(p["Ai"]), info["nnz_lu"])
     t_admit = time.perf_counter() - t0
     lat = {p["name"]: [] for p in pats}
     bsz = {p["name"]: [] for p in pats}
@@ -638,6 +686,7 @@ def run_serve(args, rank, world, local_rank):
         "latency_ms_p50": 1e3 * float(np.percentile(allv, 50)),
         "latency_ms_p99": 1e3 * float(np.percentile(allv, 99)),
         "per_pattern": per, "max_rel_residual": worst[0], "residual_ok": bool(worst[0] <= 1e-12),
+        "hbm_roofline": hbm_roofline(sum(len(lat[p["name"]]) * p["ubytes"] for p in pats), elapsed),
         "errors": len(bad), "server": {k: st[k] for k in ("batches", "repivots", "max_batch_seen",
                                                            "reserved_bytes")},
         "admission_s": t_admit, "clocks": clk,
@@ -872,6 +921,8 @@ def run_ours(args, rank, world, local_rank):
                                     "(1.19 TFLOP/s measured with independent DFMA chains)",
                      "hbm_view": {"compulsory_gbs": b_rf / t_rf / 1e9,
                                   "streaming_gbs": b_rf_stream / t_rf / 1e9}},
+        "hbm_roofline": hbm_roofline(b_rf + 12 * (st["nnz_l"] + st["nnz_u"]) + 16 * (n + 1) + 32 * n,
+                                     elapsed / args.steps, None),
         "e2e": {"value": world * args.steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": 8 * (nnz + n), "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches),

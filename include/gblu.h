@@ -376,6 +376,8 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
  *   GBLU_OK and fills *res (then the request id is released), or
  *   GBLU_ERR_BUSY if it has not finished.  res->status is the request's own
  *   outcome: GBLU_OK, GBLU_REPIVOTED or an error code.
+ * gblu_server_pattern_info: a pattern's slots, device footprint and factor
+ *   entries (nnz(L) + nnz(U)); each output optional.
  * gblu_server_destroy: finishes every queued request, stops the workers and
  *   frees all device memory of the server.
  * Errors of these calls are described by gblu_server_last_error().
@@ -405,7 +407,8 @@ int gblu_server_create(gblu_server *s, int device, int64_t hbm_budget_bytes, int
                        const gblu_opts *o);
 int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
                             const double *Ax0_host, int32_t *pattern, int32_t *slots);
-int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes);
+int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes,
+                             int64_t *nnz_lu);
 int gblu_server_submit(gblu_server s, int32_t pattern, const double *Ax_host, const double *b_host,
                        double *x_host, int32_t mode, int64_t *request);
 int gblu_server_wait(gblu_server s, int64_t request, double timeout_s, gblu_request_result *res);

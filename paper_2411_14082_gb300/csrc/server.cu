@@ -443,7 +443,8 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
     return GBLU_OK;
 }
 
-int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes)
+int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int64_t *footprint_bytes,
+                             int64_t *nnz_lu)
 {
     if (!s) return sfail(GBLU_ERR_INVALID_INPUT, "server: null server");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -451,6 +452,7 @@ int gblu_server_pattern_info(gblu_server s, int32_t pattern, int32_t *slots, int
         return sfail(GBLU_ERR_INVALID_INPUT, "server: unknown pattern %d", pattern);
     if (slots) *slots = s->patterns[pattern]->slots;
     if (footprint_bytes) *footprint_bytes = s->patterns[pattern]->footprint;
+    if (nnz_lu) *nnz_lu = s->patterns[pattern]->lu_stride;
     return GBLU_OK;
 }
 

@@ -155,7 +155,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_server_last_error.restype = ctypes.c_char_p
         lib.gblu_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, I64, I32, ctypes.POINTER(Opts)]
         lib.gblu_server_add_pattern.argtypes = [P, I32, P, P, P, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
-        lib.gblu_server_pattern_info.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)]
+        lib.gblu_server_pattern_info.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64),
+                                                 ctypes.POINTER(I64)]
         lib.gblu_server_submit.argtypes = [P, I32, P, P, P, I32, ctypes.POINTER(I64)]
         lib.gblu_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(RequestResult)]
         lib.gblu_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
@@ -630,10 +631,10 @@ class Server:
         return pid.value, slots.value
 
     def pattern_info(self, pattern):
-        slots, fp = ctypes.c_int32(0), ctypes.c_int64(0)
+        slots, fp, nlu = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
         _check_server(load().gblu_server_pattern_info(self._s, int(pattern), ctypes.byref(slots),
-                                                      ctypes.byref(fp)))
-        return {"slots": slots.value, "footprint_bytes": fp.value}
+                                                      ctypes.byref(fp), ctypes.byref(nlu)))
+        return {"slots": slots.value, "footprint_bytes": fp.value, "nnz_lu": nlu.value}
 
     def submit(self, pattern, Ax, b, x=None, mixed=False):
         """Queue a request; returns its id.  x (host float64[n]) receives the
