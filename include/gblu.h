@@ -466,6 +466,9 @@ typedef struct {
      * host wall clock: tail kernel, download and repack of the factors,
      * schedule rebuild, upload of the new structure */
     double tail_kernel_ms, tail_repack_ms, tail_schedule_ms, tail_upload_ms;
+    int32_t tail_passes;  /* kernel passes of that run (a restart speculates
+                             that the preferred pivots are kept and repeats
+                             the steps after a step that took another row) */
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

@@ -82,6 +82,7 @@ struct gblu_ctx {
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
     int32_t force_col = -1;                        // forced check failure of the next refactorization
     double t_tail[4] = {0, 0, 0, 0};               // last tail run: kernel, repack, schedule, upload (ms)
+    int32_t tail_passes = 0;                       // kernel passes of the last tail run
     bool analyzed = false, factorized = false;
     Pattern P;
     Structure S;
@@ -438,7 +439,9 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     const size_t words = ((size_t)n + 31) / 32;
     if (!bits_smem) CK(ensure(h, h->sbits, (size_t)slots * words));
     // pool after the canonical columns
-    size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>(2 * restart_len, (int64_t)P.Ai.size())) +
+    // speculative restarts may write a column once per pass
+    size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>((keep_if_same ? 4 : 2) * restart_len,
+                                                                        (int64_t)P.Ai.size())) +
                   (size_t)n;
     using TClock = std::chrono::steady_clock;
     auto ms_since = [](TClock::time_point t) {
@@ -499,13 +502,42 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         t.eps = h->opts.pivot_tol;
         t.spin_limit = h->opts.spin_limit;
         t.ctl = h->ctl;
-        KL(launch_tail(t, slots, h->tail_epoch, st));
-        CK(read_ctl(h, st));
-        if (h->hctl->status == GBLU_INTERNAL_POOL_FULL) {
+        // a restart speculates that the steps keep their preferred pivots;
+        // after a pass in which some step took another row, the steps after
+        // the first such step run again (each pass moves that point forward;
+        // after kMaxSpecPasses the last pass runs without speculation)
+        constexpr int kMaxSpecPasses = 8;
+        std::vector<int32_t> cur = seq;
+        bool pool_full = false;
+        for (int pass = 0;; pass++) {
+            t.speculate = (keep_if_same && pass < kMaxSpecPasses) ? 1 : 0;
+            t.nseq = (int32_t)cur.size();
+            KL(launch_tail(t, slots, h->tail_epoch, st));
+            CK(read_ctl(h, st));
+            h->tail_passes = pass + 1;
+            if (h->hctl->status == GBLU_INTERNAL_POOL_FULL) {
+                pool_full = true;
+                break;
+            }
+            CK(status_code(h));
+            if (!t.speculate || h->hctl->tail_mispredict == INT_MAX) break;
+            const int32_t js = h->hctl->tail_mispredict;
+            std::vector<int32_t> next;
+            for (int32_t k : cur)
+                if (k > js) next.push_back(k);
+            if (next.empty()) break;
+            cur.swap(next);
+            CK(upload(h, h->seq, cur, st));
+            KL(launch_tail_repass(h->ctl, h->seq.p, (int32_t)cur.size(), n, h->tpiv.p, h->tpinv.p, h->done.p, st));
+            CU(cudaMemsetAsync(h->smark.p, 0, (size_t)slots * n * sizeof(int32_t), st));
+            if (!bits_smem) CU(cudaMemsetAsync(h->sbits.p, 0, (size_t)slots * words * sizeof(unsigned), st));
+            t.seq = h->seq.p;
+        }
+        if (pool_full) {
             pool *= 2;
+            CK(upload(h, h->seq, seq, st));
             continue;
         }
-        CK(status_code(h));
         break;
     }
     if (h->hctl->status != 0) return fail(GBLU_ERR_NOMEM, "restart pool could not be sized");
@@ -1592,6 +1624,7 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->tail_repack_ms = h->t_tail[1];
     s->tail_schedule_ms = h->t_tail[2];
     s->tail_upload_ms = h->t_tail[3];
+    s->tail_passes = h->tail_passes;
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

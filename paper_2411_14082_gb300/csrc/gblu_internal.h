@@ -135,6 +135,7 @@ struct DevCtl {
     unsigned long long pool_top;  // next free slot of the tail pool
     int32_t where;        // diagnostic: which wait timed out
     int32_t where_k;
+    int32_t tail_mispredict;  // speculative tail: smallest step whose pivot left its preferred row
 };
 
 #define GBLU_INTERNAL_POOL_FULL (-100)
@@ -194,6 +195,8 @@ struct TailArgs {
     int32_t *smark, *slist, *sclass;
     unsigned *sbits;                // per-CTA step bitmap when it does not fit in shared memory
     int32_t bits_in_smem;           // 1: the bitmap is the kernel's dynamic shared memory
+    int32_t speculate;              // 1: do not wait for an unfinished step whose preferred row is
+                                    //    not in the structure (validated by tail_mispredict)
     double eps;
     long long spin_limit;
     DevCtl *ctl;
@@ -237,6 +240,10 @@ int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);
 int launch_tail(const TailArgs &a, int grid, int epoch, void *stream);
+// another speculative pass over the steps seq[0..nseq): their pivots, row
+// map entries and done flags are cleared; the pool and the other steps stay
+int launch_tail_repass(DevCtl *ctl, const int32_t *seq, int32_t nseq, int32_t n, int32_t *piv, int32_t *pinv,
+                       int32_t *done, void *stream);
 int tail_setup();
 constexpr int32_t kTailSmemBits = 1 << 19;   // steps whose bitmap fits in shared memory
 int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, const int32_t *cnu,

@@ -154,8 +154,13 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
                 const int jj = base + lane;
                 bool notready = false, dep = false;
                 if (jj < k) {
-                    if (ld_acquire(a.done + jj) != epoch) notready = true;
-                    else dep = mark[__ldcg(a.piv + jj)] == stamp;
+                    if (ld_acquire(a.done + jj) != epoch)
+                        // speculative: an unfinished step matters only if its
+                        // preferred row is already in the structure (a step
+                        // that takes another row is caught by tail_mispredict)
+                        notready = !a.speculate || mark[__ldg(a.prefer + jj)] == stamp;
+                    else
+                        dep = mark[__ldcg(a.piv + jj)] == stamp;
                 }
                 const unsigned nr = __ballot_sync(kFull, notready);
                 const unsigned dp = __ballot_sync(kFull, dep);
@@ -209,10 +214,18 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
     int bq = INT_MAX, br = -1, nu = 0, nc = 0, pc = 0, badrow = 0;
     for (int i = tid; i < cnt; i += kTailThreads) {
         const int r = list[i];
-        const int pj = __ldcg(a.pinv + r);
+        int pj = __ldcg(a.pinv + r);
+        if (pj >= k) {
+            // pivotal at a later step, which can only finish first when it
+            // skipped this one speculatively: at step k the row is still a
+            // candidate.  Without speculation it breaks the elimination-tree
+            // bound.
+            if (a.speculate) pj = -1;
+            else badrow = 1;
+        }
         cls[i] = pj;
         if (pj >= 0) {
-            if (pj < lo_k || pj >= k) badrow = 1;
+            if (pj < lo_k) badrow = 1;
             nu++;
             continue;
         }
@@ -253,7 +266,14 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
             if (xp != 0.0 && fabs(xp) >= a.eps * m) piv = pref;
         }
         if (piv < 0) piv = br;
+        if (a.speculate && piv >= 0 && piv != pref) atomicMin(&a.ctl->tail_mispredict, k);
         s_stop = 0;
+        if (badrow && a.speculate) {
+            // only a wrong speculation upstream can give this structure:
+            // the pass is repeated from this step on
+            atomicMin(&a.ctl->tail_mispredict, k - 1);
+            badrow = 0;
+        }
         if (badrow) {
             set_status(a.ctl, GBLU_ERR_INTERNAL);
             a.ctl->where_k = k;
@@ -318,6 +338,7 @@ __global__ void begin_tail_kernel(DevCtl *ctl, unsigned long long pool_base)
 {
     ctl->tail_ticket = 0;
     ctl->tail_frontier = 0;
+    ctl->tail_mispredict = INT_MAX;
     ctl->abort_tail = 0;
     ctl->status = 0;
     ctl->pool_top = pool_base;
@@ -1019,6 +1040,47 @@ int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, c
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream)
 {
     begin_tail_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, pool_base);
+    return (int)cudaGetLastError();
+}
+
+// steps seq[0..nseq) start again; the row -> step map is cleared here and
+// rebuilt from the kept steps by tail_pinv_kernel
+__global__ void tail_repass_kernel(DevCtl *ctl, const int32_t *seq, int32_t nseq, int32_t n, int32_t *piv,
+                                   int32_t *pinv, int32_t *done)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nseq; t += gridDim.x * blockDim.x) {
+        const int k = seq[t];
+        piv[k] = -1;
+        done[k] = 0;
+    }
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) pinv[r] = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->tail_ticket = 0;
+        ctl->tail_frontier = 0;
+        ctl->tail_mispredict = INT_MAX;
+        ctl->abort_tail = 0;
+        ctl->status = 0;
+        ctl->where = 0;
+        ctl->where_k = -1;
+    }
+}
+
+__global__ void tail_pinv_kernel(int32_t n, const int32_t *piv, int32_t *pinv)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int r = piv[k];
+        if (r >= 0) pinv[r] = k;
+    }
+}
+
+int launch_tail_repass(DevCtl *ctl, const int32_t *seq, int32_t nseq, int32_t n, int32_t *piv, int32_t *pinv,
+                       int32_t *done, void *stream)
+{
+    const int m = nseq > n ? nseq : n;
+    int g = (m + 255) / 256;
+    g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
+    tail_repass_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(ctl, seq, nseq, n, piv, pinv, done);
+    tail_pinv_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(n, piv, pinv);
     return (int)cudaGetLastError();
 }
 

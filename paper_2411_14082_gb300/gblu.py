@@ -75,7 +75,8 @@ class Stats(ctypes.Structure):
                 ("last_first_bad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32),
                 ("tail_kernel_ms", ctypes.c_double), ("tail_repack_ms", ctypes.c_double),
-                ("tail_schedule_ms", ctypes.c_double), ("tail_upload_ms", ctypes.c_double)]
+                ("tail_schedule_ms", ctypes.c_double), ("tail_upload_ms", ctypes.c_double),
+                ("tail_passes", ctypes.c_int32)]
 
 
 class RequestResult(ctypes.Structure):
