@@ -1,0 +1,88 @@
+"""Parity at the full size of the 200x200x4 RC mesh (n = 160,000), in the
+launch configuration bench.py times (default options): the first
+factorization, then the checked re-factorization of new transistor values
+and a solve.
+
+* Sampled steps (leaves, middle and the top separator): the factor columns
+  equal the oracle's (its factorization of the same values preferring the
+  GPU's pivot sequence, which is what the re-factorization must compute),
+  entry by entry, within 1e-10 of the componentwise magnitude |L||U|.
+* The same sampled columns satisfy the definition P A Q(:,k) = L U(:,k)
+  within 1e-11 of |L||U|.
+* Every column respects the threshold rule: max |L(:,k)| <= 1/eps.
+* The solve meets the residual bound ||b - A x|| <= 1e-12 ||A|| ||x||.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2411_14082_gb300 import gblu, inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = 0
+EPS = 1e-3
+
+
+def column(p, i, x, k):
+    a, b = int(p[k]), int(p[k + 1])
+    return i[a:b], x[a:b]
+
+
+def lu_times_u(n, Lp, Li, Lx, Up, Ui, Ux, k, absval=False):
+    """L U(:,k) (unit diagonal of L implied) as a dense step-indexed vector."""
+    f = np.abs if absval else (lambda v: v)
+    rows, vals = column(Up, Ui, Ux, k)
+    parts_r, parts_v = [rows.astype(np.int64)], [f(vals)]
+    for i, u in zip(rows.tolist(), f(vals).tolist()):
+        li, lx = column(Lp, Li, Lx, i)
+        parts_r.append(li.astype(np.int64))
+        parts_v.append(f(lx) * u)
+    return np.bincount(np.concatenate(parts_r), weights=np.concatenate(parts_v), minlength=n)
+
+
+def test_full_size_mesh_refactorization():
+    ckt = inputs.workload_mesh()
+    n, Ap, Ai, Ax0 = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    s.factorize(torch.from_numpy(Ax0).cuda(DEV))
+    piv0 = s.export_factors()["piv"].copy()
+    rng = np.random.default_rng(77)
+    Ax = inputs.redraw_transistors(ckt, rng).values()
+    b = inputs.rhs(n, rng)
+    _, rep = s.refactorize(torch.from_numpy(Ax).cuda(DEV))
+    x = s.solve(torch.from_numpy(b).cuda(DEV)).cpu().numpy()
+    assert O.residual(n, Ap, Ai, Ax, x, b) <= 1e-12
+    f = s.export_factors()
+    assert np.array_equal(f["q"], Q)
+    # threshold rule on every column
+    assert np.abs(f["Lx"]).max() <= 1.0 / EPS * (1 + 1e-12)
+    # the oracle's factorization of the same values with the same preference
+    lu = O.factorize(n, Ap, Ai, Ax, Q, EPS, prefer=piv0)
+    assert lu.status == 0
+    assert np.array_equal(f["piv"], lu.piv)
+    # sampled steps: a spread of leaves and the last steps (top separator)
+    ks = sorted(set(np.linspace(0, n - 1, 16).astype(int).tolist() + list(range(n - 8, n))))
+    pinv = np.empty(n, np.int64)
+    pinv[f["piv"]] = np.arange(n)
+    for k in ks:
+        M = lu_times_u(n, lu.Lp, lu.Li, lu.Lx, lu.Up, lu.Ui, lu.Ux, k, absval=True)
+        ou_r, ou_v = column(lu.Up, lu.Ui, lu.Ux, k)
+        gu_r, gu_v = column(f["Up"], f["Ui"], f["Ux"], k)
+        ol_r, ol_v = column(lu.Lp, lu.Li, lu.Lx, k)
+        gl_r, gl_v = column(f["Lp"], f["Li"], f["Lx"], k)
+        assert np.array_equal(gu_r, ou_r) and np.array_equal(gl_r, ol_r), f"pattern of step {k}"
+        d = abs(ou_v[-1])
+        xk = max(np.abs(ou_v).max(), d * (np.abs(ol_v).max() if len(ol_v) else 0.0))
+        assert np.all(np.abs(gu_v - ou_v) <= 1e-10 * np.maximum(M[ou_r], xk)), f"U(:,{k})"
+        if len(ol_r):
+            assert np.all(np.abs(gl_v - ol_v) <= 1e-10 * np.maximum(M[ol_r], xk) / d), f"L(:,{k})"
+        # the definition: (P A Q)(:,k) == L U(:,k) for the GPU factors
+        LU = lu_times_u(n, f["Lp"], f["Li"], f["Lx"], f["Up"], f["Ui"], f["Ux"], k)
+        c = Q[k]
+        a = np.zeros(n)
+        a[pinv[Ai[Ap[c]:Ap[c + 1]]]] = Ax[Ap[c]:Ap[c + 1]]
+        assert np.all(np.abs(LU - a) <= 1e-11 * np.maximum(M, xk)), f"(P A Q)(:,{k})"
