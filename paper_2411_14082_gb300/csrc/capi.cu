@@ -482,6 +482,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         t.seq = h->seq.p;
         t.nseq = (int32_t)nR;
         t.prefer = h->piv.p;
+        t.prefer_inv = h->pinv.p;
         t.clo = h->clo.p;
         t.pinv = h->tpinv.p;
         t.piv = h->tpiv.p;
@@ -521,7 +522,21 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
             }
             CK(status_code(h));
             if (!t.speculate || h->hctl->tail_mispredict == INT_MAX) break;
-            const int32_t js = h->hctl->tail_mispredict;
+            int32_t js = h->hctl->tail_mispredict;
+            // a pass stopped early (a column found its speculation broken)
+            // may leave steps before js unfinished; a finished step is only
+            // known right if every step before it finished, so the next pass
+            // starts at the first unfinished step at the latest
+            if (h->hctl->abort_tail) {
+                std::vector<int32_t> dn(n);
+                CU(cudaMemcpyAsync(dn.data(), h->done.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+                CU(cudaStreamSynchronize(st));
+                for (int32_t k : cur)
+                    if (dn[k] != h->tail_epoch) {
+                        js = std::min(js, k - 1);
+                        break;   // cur is ascending
+                    }
+            }
             std::vector<int32_t> next;
             for (int32_t k : cur)
                 if (k > js) next.push_back(k);

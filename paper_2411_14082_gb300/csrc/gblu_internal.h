@@ -179,6 +179,7 @@ struct TailArgs {
     const int32_t *seq;             // restart steps, ascending
     int32_t nseq;
     const int32_t *prefer;          // preferred original row per step
+    const int32_t *prefer_inv;      // inverse of prefer (row -> step that preferred it)
     const int32_t *clo;             // cetree subtree lower bound per step
     int32_t *pinv;                  // original row -> step (-1 = not pivotal)
     int32_t *piv;                   // step -> original row

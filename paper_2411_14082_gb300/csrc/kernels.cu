@@ -78,17 +78,81 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
                 mark[r] = stamp;
                 x[r] = 0.0;
                 list[atomicAdd(&s_cnt, 1)] = r;
-                const int sr = __ldcg(a.pinv + r);
+                int sr = __ldcg(a.pinv + r);
+                if (sr < 0 && a.speculate) sr = __ldg(a.prefer_inv + r);
                 if (sr > jd && sr < fk) atomicOr(bm + (sr >> 5), 1u << (sr & 31));
             }
             x[r] = fma(-xj, v, x[r]);
         }
     };
     int j = __ldg(a.clo + k);
+    if (a.speculate) {
+        // every dependency is the step of a row in the structure: the row's
+        // pivot step once that step is final, else the step that pivoted it
+        // before (the speculation).  One ascending walk over a step bitmap;
+        // a predicted dependency that is not final yet is waited for.
+        for (int i = tid; i < s_cnt; i += kTailThreads) {
+            const int r = list[i];
+            int sr = __ldcg(a.pinv + r);
+            if (sr < 0) sr = __ldg(a.prefer_inv + r);
+            if (sr >= j && sr < k) atomicOr(bm + (sr >> 5), 1u << (sr & 31));
+        }
+        __syncthreads();
+        int cur = j;
+        for (;;) {
+            if (warp == 0) {
+                int found = k;
+                for (int wb = cur >> 5; wb * 32 < k; wb += 32) {
+                    const int w = wb + lane;
+                    unsigned v = w * 32 < k ? *(const volatile unsigned *)(bm + w) : 0u;
+                    if (w == (cur >> 5)) v &= ~0u << (cur & 31);
+                    const unsigned nz = __ballot_sync(kFull, v != 0u);
+                    if (nz) {
+                        const int l = __ffs(nz) - 1;
+                        const unsigned vv = __shfl_sync(kFull, v, l);
+                        found = min((wb + l) * 32 + __ffs(vv) - 1, k);
+                        break;
+                    }
+                }
+                if (lane == 0) {
+                    s_found = found;
+                    if (found < k) atomicAnd(bm + (found >> 5), ~(1u << (found & 31)));
+                }
+            }
+            __syncthreads();
+            const int jd = s_found;
+            if (jd >= k) break;
+            if (tid == 0) {
+                long long it = 0;
+                while (ld_acquire(a.done + jd) != epoch) {
+                    if (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status)) { s_stop = 1; break; }
+                    if (++it > a.spin_limit) {
+                        set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                        a.ctl->where = 3;
+                        a.ctl->where_k = k;
+                        atomicExch(&a.ctl->abort_tail, 1);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __syncthreads();
+            if (s_stop) {
+                // leave the bitmap clean for the CTA's next column
+                for (int w = (jd >> 5) + tid; w * 32 < k; w += kTailThreads) bm[w] = 0u;
+                return true;
+            }
+            if (mark[__ldcg(a.piv + jd)] == stamp) apply_dep(jd, k);
+            __syncthreads();
+            cur = jd + 1;
+        }
+        j = k;
+    }
     // ---- steps below the done frontier: every such step is final, so the
     // dependencies among them are the steps of the rows in the structure
     // (row -> step map), taken in ascending order from a bitmap
-    if (warp == 0) {
+    if (warp == 0 && !a.speculate) {
         int f = ld_acquire(&a.ctl->tail_frontier);
         for (long long it = 0; f < k && it < a.n; it++) {
             const int jj = f + lane;
@@ -109,7 +173,7 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
     }
     __syncthreads();
     const int fk = min(s_found, k);
-    if (fk > j) {
+    if (fk > j && !a.speculate) {
         for (int i = tid; i < s_cnt; i += kTailThreads) {
             const int sr = __ldcg(a.pinv + list[i]);
             if (sr >= j && sr < fk) atomicOr(bm + (sr >> 5), 1u << (sr & 31));
@@ -268,13 +332,14 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         if (piv < 0) piv = br;
         if (a.speculate && piv >= 0 && piv != pref) atomicMin(&a.ctl->tail_mispredict, k);
         s_stop = 0;
-        if (badrow && a.speculate) {
-            // only a wrong speculation upstream can give this structure:
-            // the pass is repeated from this step on
+        if (a.speculate && (badrow || piv < 0)) {
+            // in a speculative pass only a wrong speculation upstream gives a
+            // structure outside the elimination-tree bound or no nonzero
+            // candidate: stop the pass; it is repeated from this step on
             atomicMin(&a.ctl->tail_mispredict, k - 1);
-            badrow = 0;
-        }
-        if (badrow) {
+            atomicExch(&a.ctl->abort_tail, 1);
+            s_stop = 1;
+        } else if (badrow) {
             set_status(a.ctl, GBLU_ERR_INTERNAL);
             a.ctl->where_k = k;
             atomicExch(&a.ctl->abort_tail, 1);
