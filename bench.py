@@ -259,6 +259,13 @@ def run_reference(args, rank, world):
 def run_batch(args, rank, world, local_rank):
     """Batch workload: every step refactorizes and solves `sets` value sets of
     one pattern through gblu_refactorize_batch / gblu_solve_batch."""
+    # CPU throughput baseline: one single-threaded oracle process per host
+    # core, each on its own value sets of the same pattern (started before
+    # the first CUDA call)
+    procs, t_cpu0, units = [], None, 3
+    if rank == 0 and not args.no_cpu_baseline:
+        t_cpu0 = time.perf_counter()
+        procs = [start_oracle("batch", units, args.seed + 5000 + p) for p in range(os.cpu_count() or 1)]
     import torch
     import torch.distributed as dist
     from paper_2411_14082_gb300 import gblu
@@ -341,6 +348,7 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None},
         "single_path": {"value": single, "unit": METRIC,
                         "note": "the same sets one at a time through gblu_refactorize + gblu_solve"},
+        "cpu_baseline": None,
         # index bytes once per launch, value bytes once per set
         "hbm_roofline": hbm_roofline(
             (4 * nnz + 4 * (n + 1) + 8 * (st["nnz_l"] + st["nnz_u"]))
@@ -348,6 +356,18 @@ def run_batch(args, rank, world, local_rank):
             ev_elapsed / args.steps),
         "clocks": clk,
     }
+    if procs:
+        res = [collect_oracle(p) for p in procs]
+        wall = time.perf_counter() - t_cpu0
+        ok = [r for r in res if r]
+        if ok:
+            done = sum(len(r) for r in ok)
+            line["cpu_baseline"] = {
+                "value": done / max(max(sum(u["seconds"] for u in r) for r in ok), 1e-9), "unit": METRIC,
+                "cores": len(procs), "kind": "oracle",
+                "sample": f"{len(procs)} single-threaded oracle processes, {units} sets each of the same pattern; "
+                          "value = sets / the longest process's oracle time",
+                "wall_s": wall, "max_rel_residual": max(u["residual"] for r in ok for u in r)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
