@@ -36,6 +36,19 @@ from paper_2411_14082_gb300 import inputs  # noqa: E402
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate of the profiling recipe (non-tensor ALU)
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over all ranks (the slowest rank's time); value
+    itself on one rank.  device: where the process group's tensors live
+    ("cuda:i" under NCCL, "cpu" under gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def hbm_peak_gbs():
     """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
     try:
@@ -311,9 +324,7 @@ def run_batch(args, rank, world, local_rank):
     t_sv = [ev[i][1].elapsed_time(ev[i][2]) / 1e3 for i in range(args.warmup, total)]
     ev_elapsed = sum(ev[i][0].elapsed_time(ev[i][2]) / 1e3 for i in range(args.warmup, total))
     if world > 1:
-        tt = torch.tensor([ev_elapsed], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ev_elapsed = float(tt.item())
+        ev_elapsed = max_over_ranks(ev_elapsed, world, f"cuda:{dev}")
     res = torch.zeros(4, dtype=torch.float64, device=f"cuda:{dev}")
     worst = 0.0
     for k in range(args.sets):
@@ -867,9 +878,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     if world > 1:
-        tt = torch.tensor([elapsed], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+        elapsed = max_over_ranks(elapsed, world, f"cuda:{dev}")
     t_ref = [ev_r[i][0].elapsed_time(ev_r[i][1]) / 1e3 for i in range(args.warmup, total)]
     t_sol = [ev_s[i][0].elapsed_time(ev_s[i][1]) / 1e3 for i in range(args.warmup, total)]
     resid = res[args.warmup:, 0].max().item()
@@ -905,9 +914,7 @@ def run_ours(args, rank, world, local_rank):
         eh.step_host(hv[i], hb[i], hx)
     e2e_t = time.perf_counter() - t0
     if world > 1:
-        tt = torch.tensor([e2e_t], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+        e2e_t = max_over_ranks(e2e_t, world, f"cuda:{dev}")
 
     if rank != 0:
         return 0
