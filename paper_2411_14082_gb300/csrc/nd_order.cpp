@@ -394,8 +394,7 @@ void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, in
     g.vw.assign(n, 1);
     std::vector<int32_t> out;
     out.reserve(n);
-    Ordering o{g, out, std::vector<int32_t>(n, -1)};
-    o.leaf = leaf;
+    Ordering o{g, out, std::vector<int32_t>(n, -1), std::mt19937{20241121u}, leaf};
     std::vector<int32_t> all(n);
     std::iota(all.begin(), all.end(), 0);
     o.rec(std::move(all), 0);
