@@ -3,6 +3,8 @@
 // The orchestration runs on the host; every numerical step runs in the
 // kernels of kernels.cu.
 #include <queue>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cuda_runtime.h>
 
@@ -612,27 +614,49 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     if (S2.LUp[n] > INT32_MAX) return fail(GBLU_ERR_NOMEM, "factor too large (> 2^31 entries)");
     S2.LUi.assign(S2.LUp[n], 0);
     std::vector<double> V2(S2.LUp[n]);
-    std::vector<std::pair<int32_t, double>> tmp;
-    for (int32_t k = 0; k < n; k++) {
-        const int64_t b = cbeg[k];
-        int64_t o = S2.LUp[k];
-        // U part: step ids, unchanged numbering for kept columns
-        tmp.clear();
-        for (int64_t e = b; e < b + cnu[k]; e++)
-            tmp.push_back({rmask[k] ? rows[e] : S.LUi[e], vals[e]});
-        std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
-        for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
-        // L part: original rows (pool) or old step ids (kept) -> new step ids
-        tmp.clear();
-        for (int64_t e = b + cnu[k]; e < b + cnu[k] + cnl[k]; e++) {
-            const int32_t orig = rmask[k] ? rows[e] : S.piv[S.LUi[e]];
-            tmp.push_back({pinv_new[orig], vals[e]});
+    // columns are independent: repack them on several host threads, in
+    // ranges of about equal entry counts
+    std::atomic<int32_t> misplaced{-1};
+    auto repack = [&](int32_t k0, int32_t k1) {
+        std::vector<std::pair<int32_t, double>> tmp;
+        for (int32_t k = k0; k < k1; k++) {
+            const int64_t b = cbeg[k];
+            int64_t o = S2.LUp[k];
+            // U part: step ids, unchanged numbering for kept columns
+            tmp.clear();
+            for (int64_t e = b; e < b + cnu[k]; e++)
+                tmp.push_back({rmask[k] ? rows[e] : S.LUi[e], vals[e]});
+            std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
+            for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
+            // L part: original rows (pool) or old step ids (kept) -> new step ids
+            tmp.clear();
+            for (int64_t e = b + cnu[k]; e < b + cnu[k] + cnl[k]; e++) {
+                const int32_t orig = rmask[k] ? rows[e] : S.piv[S.LUi[e]];
+                tmp.push_back({pinv_new[orig], vals[e]});
+            }
+            std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
+            for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
+            if (S2.LUi[S2.LUp[k] + S2.nU[k] - 1] != k) misplaced.store(k);
         }
-        std::sort(tmp.begin(), tmp.end(), [](auto &x, auto &y) { return x.first < y.first; });
-        for (auto &pr : tmp) { S2.LUi[o] = pr.first; V2[o] = pr.second; o++; }
-        if (S2.LUi[S2.LUp[k] + S2.nU[k] - 1] != k)
-            return fail(GBLU_ERR_INTERNAL, "restart: diagonal misplaced in column %d", k);
+    };
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (nt == 1 || n < 4096) {
+        repack(0, n);
+    } else {
+        std::vector<std::thread> pool_threads;
+        int32_t k0 = 0;
+        for (int t = 1; t <= nt; t++) {
+            const int64_t target = S2.LUp[n] * t / nt;
+            int32_t k1 = t == nt ? n
+                                 : (int32_t)(std::lower_bound(S2.LUp.begin(), S2.LUp.end(), target) - S2.LUp.begin());
+            k1 = std::min(std::max(k1, k0), n);
+            if (k1 > k0) pool_threads.emplace_back(repack, k0, k1);
+            k0 = k1;
+        }
+        for (auto &th : pool_threads) th.join();
     }
+    if (misplaced.load() >= 0)
+        return fail(GBLU_ERR_INTERNAL, "restart: diagonal misplaced in column %d", misplaced.load());
     h->n_restart_cols = nR;
     h->t_tail[1] = ms_since(t_r);
     CK(install_structure(h, std::move(S2), &V2, st));
