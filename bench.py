@@ -770,7 +770,8 @@ def run_ours(args, rank, world, local_rank):
     if args.autotune:
         t0 = time.perf_counter()
         opts, tr, ts = s.autotune(vals[0], rhs[0], xs[0], reps=3)
-        tuned = {"alpha": opts["alpha"], "solve_dense_density": opts["solve_dense_density"],
+        tuned = {"alpha": opts["alpha"], "warp_column_max": opts["warp_column_max"],
+                 "solve_dense_density": opts["solve_dense_density"],
                  "solve_slices": opts["solve_slices"], "refactor_ms": tr, "solve_ms": ts,
                  "tuning_s": time.perf_counter() - t0}
         st = s.stats()

@@ -92,6 +92,12 @@ typedef struct {
        the 200x200x4 mesh its one-SM panels cost more than the column
        kernels do on the same block).                                        */
     int dense_min_rows;
+    /* warp assignment of the re-factorization (Section IV-B's task
+       granularity, retuned for warps): columns of at most warp_column_max
+       entries are computed by one warp (eight per CTA), longer ones by half
+       a CTA (up to 4096 entries) or a whole CTA.  32..1024, default 1024;
+       gblu_autotune measures it. */
+    int warp_column_max;
 } gblu_opts;
 
 /* largest dense tail block of the re-factorization (shared-memory panel) */
@@ -109,8 +115,9 @@ void gblu_default_opts(gblu_opts *o);
  * gblu_autotune: measure, with CUDA events on `stream`, the median of reps
  *   re-factorizations of Ax_dev and solves of b_dev (into x_dev) for a set
  *   of schedule options, and keep the fastest: first the dividing-level
- *   factor alpha (Section IV-B) by re-factorization time, then the
- *   trailing-block rule of the solve (solve_dense_density, solve_slices;
+ *   factor alpha (Section IV-B) and the warp assignment (warp_column_max)
+ *   by re-factorization time, then the trailing-block rule of the solve
+ *   (solve_dense_density, solve_slices;
  *   Section V-A) by solve time.  The paper tunes these constants for its
  *   CPUs; here they are measured on the device and matrix at hand.  The
  *   factor values after the call are those of Ax_dev.  *chosen, *refactor_ms

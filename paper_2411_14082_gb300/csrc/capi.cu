@@ -246,7 +246,7 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     sp.slices = h->opts.solve_slices;
     sp.max_piece = kMaxPieceRows;
     const auto t_s = std::chrono::steady_clock::now();
-    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, kRefCapShort, sp,
+    build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, h->opts.warp_column_max, sp,
                    h->opts.dense_min_rows, h->W);
     const auto t_u = std::chrono::steady_clock::now();
     h->t_tail[2] = std::chrono::duration<double, std::milli>(t_u - t_s).count();
@@ -329,7 +329,7 @@ RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
     a.finish = h->finish.p;
     a.task_ptr = h->task_ptr.p;
     a.task_cols = h->task_cols.p;
-    a.cap_short = kRefCapShort;
+    a.cap_short = h->opts.warp_column_max;
     a.cap_long = kRefCapLong;
     a.eps = h->opts.pivot_tol;
     a.force_col = h->force_col;
@@ -703,6 +703,7 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_slices = 8;
     o->solve_dense_density = 0.9;
     o->dense_min_rows = 0;
+    o->warp_column_max = kRefCapShort;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -712,7 +713,8 @@ static bool opts_valid(const gblu_opts &o)
     return o.pivot_tol >= 0.0 && o.pivot_tol <= 1.0 && o.spin_limit > 0 && o.sched_mode >= 0 && o.sched_mode <= 2 &&
            o.solve_mode >= 0 && o.solve_mode <= 2 && o.alpha >= 0.0 && o.solve_dense_frac >= 0.0 &&
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
-           o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0;
+           o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
+           o.warp_column_max <= kRefCapShort;
 }
 
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
@@ -1467,6 +1469,22 @@ int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, doub
         if (al == best.alpha) continue;
         gblu_opts o = best;
         o.alpha = al;
+        double tr = 0, ts = 0;
+        if ((rc = gblu_set_opts(h, &o, stream)) != GBLU_OK || (rc = measure(tr, ts)) != GBLU_OK) break;
+        if (tr < br) {
+            best = o;
+            br = tr;
+            bs = ts;
+        }
+    }
+    // the warp assignment: the longest column one warp computes (Section
+    // IV-B's task granularity), by re-factorization time
+    const int wcols[] = {256, 512, 1024};
+    for (int wc : wcols) {
+        if (rc != GBLU_OK) break;
+        if (wc == best.warp_column_max) continue;
+        gblu_opts o = best;
+        o.warp_column_max = wc;
         double tr = 0, ts = 0;
         if ((rc = gblu_set_opts(h, &o, stream)) != GBLU_OK || (rc = measure(tr, ts)) != GBLU_OK) break;
         if (tr < br) {
