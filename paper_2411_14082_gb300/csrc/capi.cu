@@ -5,6 +5,7 @@
 #include <queue>
 #include <atomic>
 #include <thread>
+#include <nvtx3/nvToolsExt.h>
 #include <chrono>
 #include <cuda_runtime.h>
 
@@ -168,6 +169,14 @@ struct DeviceGuard {
     {
         if (prev >= 0) cudaSetDevice(prev);
     }
+};
+
+// an NVTX range over one library call, for profilers (no cost without one)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 template <class T>
@@ -668,6 +677,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
 // recomputed with pivoting.
 int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
 {
+    NvtxRange nvtx_range("restart");
     const int32_t n = h->P.n;
     std::vector<int32_t> fin(n);
     CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
@@ -873,6 +883,7 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
 
 int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
 {
+    NvtxRange nvtx_range("gblu_factorize");
     CK(check_handle(h));
     if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
     DeviceGuard g(h->device);
@@ -913,6 +924,7 @@ int gblu_refactorize_forced(gblu_handle h, const double *Ax_dev, void *stream, i
 
 int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t *repivoted)
 {
+    NvtxRange nvtx_range("gblu_refactorize");
     CK(check_handle(h));
     if (repivoted) *repivoted = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
@@ -1035,6 +1047,7 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
 
 int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
 {
+    NvtxRange nvtx_range("gblu_solve");
     CK(check_handle(h));
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
     if (!b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
@@ -1046,6 +1059,7 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
                            double *LUx_dev, int64_t lu_stride, int32_t *failed, int32_t *n_failed,
                            void *stream)
 {
+    NvtxRange nvtx_range("gblu_refactorize_batch");
     CK(check_handle(h));
     if (n_failed) *n_failed = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
@@ -1109,6 +1123,7 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
 int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_t lu_stride,
                      const double *b_dev, int64_t b_stride, double *x_dev, int64_t x_stride, void *stream)
 {
+    NvtxRange nvtx_range("gblu_solve_batch");
     CK(check_handle(h));
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "no valid factorization");
     const int32_t n = h->S.n;
@@ -1122,6 +1137,7 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
 int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_dev, void *stream,
                            int32_t *repivoted)
 {
+    NvtxRange nvtx_range("gblu_refactorize_multi");
     if (nh < 1 || !hs || !Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "multi: nh >= 1 and non-null arrays");
     for (int32_t i = 0; i < nh; i++) {
         CK(check_handle(hs[i]));
@@ -1212,6 +1228,7 @@ int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_
 
 int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, double *const *x_dev, void *stream)
 {
+    NvtxRange nvtx_range("gblu_solve_multi");
     if (nh < 1 || !hs || !b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "multi: nh >= 1 and non-null arrays");
     cudaStream_t st = (cudaStream_t)stream;
     // handles whose solve is all sparse row blocks go into one launch per
@@ -1350,6 +1367,7 @@ static int capture_step(gblu_ctx *h)
 int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, void *stream,
               int32_t *repivoted)
 {
+    NvtxRange nvtx_range("gblu_step");
     CK(check_handle(h));
     if (repivoted) *repivoted = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
@@ -1523,6 +1541,7 @@ int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, doub
 
 int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int32_t *check_failed)
 {
+    NvtxRange nvtx_range("gblu_refactorize_f32");
     CK(check_handle(h));
     if (check_failed) *check_failed = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
@@ -1565,6 +1584,7 @@ int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int3
 int gblu_solve_refined(gblu_handle h, const double *Ax_dev, const double *b_dev, double *x_dev, double tol,
                        int32_t max_iter, void *stream, int32_t *iters, double *berr)
 {
+    NvtxRange nvtx_range("gblu_solve_refined");
     CK(check_handle(h));
     if (iters) *iters = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
