@@ -202,9 +202,10 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import oracle as O
 from bench import make_workload
-w = make_workload({name!r}, {steps}, {seed}, {mesh!r})
+first = {first}
+w = make_workload({name!r}, first + {steps}, {seed}, {mesh!r})
 out = []
-for s in range({steps}):
+for s in range(first, first + {steps}):
     Ax, b = w["vals"][s], w["rhs"][s]
     t0 = time.perf_counter()
     lu = O.factorize(w["n"], w["Ap"], w["Ai"], Ax, w["Q"], 1e-3)
@@ -212,12 +213,18 @@ for s in range({steps}):
     t1 = time.perf_counter()
     res = O.residual(w["n"], w["Ap"], w["Ai"], Ax, x, b)
     out.append(dict(seconds=t1 - t0, residual=res, status=lu.status, rejected=lu.n_rejected))
+    if {xfile!r}:
+        np.save({xfile!r}, x)
 print("ORACLE_JSON " + json.dumps(out), flush=True)
 """
 
 
-def start_oracle(name, steps, seed, mesh=(200, 200, 4)):
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, steps=steps, seed=seed, mesh=tuple(mesh))
+def start_oracle(name, steps, seed, mesh=(200, 200, 4), first=0, xfile=""):
+    """The oracle on value sets first .. first+steps-1 of the workload with
+    this seed, in its own process; with xfile, the last solution is saved
+    there (numpy .npy)."""
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, steps=steps, seed=seed, mesh=tuple(mesh), first=first,
+                                 xfile=xfile)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
                             stderr=subprocess.STDOUT, env=env, text=True)
@@ -731,7 +738,12 @@ def run_ours(args, rank, world, local_rank):
     oracle_proc = None
     if rank == 0 and not args.no_cpu_baseline:
         # started before the first CUDA call, in a separate process
-        oracle_proc = start_oracle(args.workload, 1, args.seed + 1000, args.mesh)
+        # the oracle solves the first timed step of this run (same seed and
+        # value set), which checks that step against it and times it
+        import tempfile
+        oracle_x = os.path.join(tempfile.gettempdir(), f"gblu_oracle_x_{os.getpid()}.npy")
+        oracle_proc = start_oracle(args.workload, 1, args.seed + 17 * rank, args.mesh, first=args.warmup,
+                                   xfile=oracle_x)
     import torch
     import torch.distributed as dist
     from paper_2411_14082_gb300 import gblu
@@ -920,6 +932,17 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
     cpu = collect_oracle(oracle_proc) if oracle_proc else None
+    oracle_check = None
+    if cpu and os.path.exists(oracle_x):
+        xo = np.load(oracle_x)
+        os.remove(oracle_x)
+        xg = raw_x[args.warmup] if ss else xs[args.warmup]
+        xg = xg.cpu().numpy()
+        oracle_check = {"step": args.warmup,
+                        "max_rel_diff_x": float(np.abs(xg - xo).max() / np.abs(xo).max()),
+                        "gpu_residual": float(res[args.warmup, 0].item()),
+                        "oracle_residual": cpu[0]["residual"],
+                        "note": "the oracle factorizes the same values with fresh pivoting"}
     F = st["flops"]
     t_rf = float(np.mean(t_ref))
     nnz_lu = st["nnz_l"] + st["nnz_u"]
@@ -992,11 +1015,12 @@ def run_ours(args, rank, world, local_rank):
                                             "schedule": float(tm[:, 2].mean()), "upload": float(tm[:, 3].mean())},
                            "restart_cols_mean": float(tm[:, 4].mean()),
                            "forced_steps": [int(v) for v in tm[:, 5]]}
+    line["oracle_check"] = oracle_check
     if cpu:
         secs = [c["seconds"] for c in cpu]
         line["cpu_baseline"] = {"value": len(secs) / sum(secs), "unit": METRIC, "cores": 1,
                                 "kind": "oracle",
-                                "sample": "1 full refactor+solve unit of the same workload "
+                                "sample": "1 full refactor+solve unit: the first timed step of this run "
                                           "(single-threaded C oracle, separate process)",
                                 "max_rel_residual": max(c["residual"] for c in cpu)}
     else:
