@@ -142,7 +142,9 @@ void gblu_destroy(gblu_handle h);
  * Pre-processing for one sparsity pattern (Section III-A): validates the CSC
  * pattern, takes the column order Q (Q[k] = original column eliminated at
  * step k; rows use the same symmetric order as the preferred pivots), or
- * computes a minimum-degree order on A+A^T when Q is NULL, and builds the
+ * when Q is NULL computes its own fill-reducing order on A+A^T (nested
+ * dissection, gblu_order_nd, for n > 20000; minimum degree below), and
+ * builds the
  * column elimination tree of A(:,Q) (the dependency upper bound of
  * Section II-B used to choose restart columns).  Host-only work.  Ap, Ai,
  * Q are host arrays and are copied.  Any previous factorization of the
