@@ -147,6 +147,7 @@ struct gblu_ctx {
     // the one it was captured on
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
+    cudaStream_t aux = nullptr;      // this handle's solves forked off a multi-pattern call
     uint64_t gversion = 0;
     int32_t *epoch_host = nullptr;   // pinned: the epoch the next replay stores
     long long glaunches = 0;         // kernels per replay
@@ -801,6 +802,7 @@ void gblu_destroy(gblu_handle h)
         release(h, h->muorder); release(h, h->margs); release(h, h->mticket);
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
         if (h->gstream) cudaStreamDestroy(h->gstream);
+        if (h->aux) cudaStreamDestroy(h->aux);
         if (h->epoch_host) cudaFreeHost(h->epoch_host);
         if (h->ctl) cudaFree(h->ctl);
         if (h->hctl) cudaFreeHost(h->hctl);
@@ -1234,7 +1236,7 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
     // handles whose solve is all sparse row blocks go into one launch per
     // triangle; the others (trailing dense pieces) are solved one by one
     std::vector<gblu_ctx *> fused;
-    std::vector<int32_t> fi;
+    std::vector<int32_t> fi, alone;
     for (int32_t i = 0; i < nh; i++) {
         gblu_ctx *h = hs[i];
         CK(check_handle(h));
@@ -1242,7 +1244,7 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
         if (!b_dev[i] || !x_dev[i]) return fail(GBLU_ERR_INVALID_INPUT, "multi: null vector for handle %d", i);
         if (h->device != hs[0]->device) return fail(GBLU_ERR_INVALID_INPUT, "multi: handles on different devices");
         if (h->W.lcut.size() > 1 || h->W.ucut.size() > 1) {
-            CK(gblu_solve(h, b_dev[i], x_dev[i], stream));
+            alone.push_back(i);
         } else {
             fused.push_back(h);
             fi.push_back(i);
@@ -1254,10 +1256,38 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
         if (std::adjacent_find(u.begin(), u.end()) != u.end())
             return fail(GBLU_ERR_INVALID_INPUT, "multi: a handle appears twice");
     }
+    DeviceGuard g(hs[0]->device);
+    // handles with trailing dense pieces solve on their own streams, forked
+    // from `stream` and joined back, overlapping the fused launch (each
+    // solve is latency-bound and uses a fraction of the device)
+    std::vector<cudaEvent_t> joins;
+    if (!alone.empty()) {
+        cudaEvent_t fork;
+        CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        CU(cudaEventRecord(fork, st));
+        for (int32_t i : alone) {
+            gblu_ctx *h = hs[i];
+            if (!h->aux) CU(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+            CU(cudaStreamWaitEvent(h->aux, fork, 0));
+            CK(gblu_solve(h, b_dev[i], x_dev[i], h->aux));
+            cudaEvent_t j;
+            CU(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+            CU(cudaEventRecord(j, h->aux));
+            joins.push_back(j);
+        }
+        cudaEventDestroy(fork);
+    }
+    auto join = [&]() -> int {
+        for (cudaEvent_t j : joins) {
+            CU(cudaStreamWaitEvent(st, j, 0));
+            cudaEventDestroy(j);
+        }
+        joins.clear();
+        return GBLU_OK;
+    };
     const int32_t nf = (int32_t)fused.size();
-    if (nf == 0) return GBLU_OK;
+    if (nf == 0) return join();
     gblu_ctx *h0 = fused[0];
-    DeviceGuard g(h0->device);
     std::vector<std::pair<const void *, uint64_t>> key(nf);
     for (int32_t i = 0; i < nf; i++) key[i] = {fused[i], fused[i]->struct_version};
     if (key != h0->msolve_key || !h0->mlorder.p) {
@@ -1320,7 +1350,7 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
     }
     // the argument block is read by the kernels: keep the host copy unchanged
     // until they have been issued (the copy above is stream-ordered)
-    return GBLU_OK;
+    return join();
 }
 
 // capture [epoch -> control block, checked re-factorization, control block
