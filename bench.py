@@ -774,6 +774,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     t_fac = time.perf_counter() - t0
     st = s.stats()
+    fac_passes = st["tail_passes"]
     vals = torch.from_numpy(np.stack(w["vals"])).cuda(dev)
     rhs = torch.from_numpy(np.stack(w["rhs"])).cuda(dev)
     xs = torch.empty_like(rhs)
@@ -963,7 +964,8 @@ def run_ours(args, rank, world, local_rank):
         "phases_ms": {"refactor": 1e3 * t_rf, "solve": 1e3 * float(np.mean(t_sol)),
                       "refactor_p50": 1e3 * float(np.median(t_ref)),
                       "refactor_p99": 1e3 * float(np.percentile(t_ref, 99)),
-                      "analyze_host": 1e3 * t_an, "first_factorize": 1e3 * t_fac},
+                      "analyze_host": 1e3 * t_an, "first_factorize": 1e3 * t_fac,
+                      "first_factorize_passes": fac_passes},
         "roofline": {"kernel": "refactor (checked re-factorization, all launches)",
                      "bound": "alu", "achieved": F / t_rf / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": F / t_rf / 1e12 / FP64_PEAK_TFLOPS,

@@ -98,6 +98,16 @@ typedef struct {
        a CTA (up to 4096 entries) or a whole CTA.  32..1024, default 1024;
        gblu_autotune measures it. */
     int warp_column_max;
+    /* first factorization (gblu_factorize, Algorithm 1 with the threshold
+       rule): 1 = its passes speculate that each step pivots on its diagonal
+       row A(Q[k],Q[k]) and wait only on the steps that prediction names as
+       dependencies; steps after the first one that took another row run
+       again, and the run falls back to waiting on every earlier unfinished
+       step of the column's elimination subtree once more than four finished
+       steps of a pass have left the diagonal, a pass finishes no step for
+       good, or eight passes have run.  0 = every step waits in that order from the
+       start.  Both give the same factors.  Default 1. */
+    int speculate_first;
 } gblu_opts;
 
 /* largest dense tail block of the re-factorization (shared-memory panel) */

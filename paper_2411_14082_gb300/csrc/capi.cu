@@ -403,8 +403,10 @@ int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupte
 // Factorization with threshold pivoting of the steps in rmask (Algorithm 5;
 // Algorithm 1 when rmask holds every step); the other steps keep their
 // current columns.  Rebuilds the structure and the schedule afterwards.
+// speculate: passes predict that every step takes its preferred row;
+// keep_if_same: a restart, whose structure stays when every pivot is kept.
 int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<uint8_t> &rmask,
-             size_t pool_hint, bool keep_if_same = false)
+             size_t pool_hint, bool keep_if_same, bool speculate)
 {
     const Pattern &P = h->P;
     const int32_t n = P.n;
@@ -452,7 +454,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     if (!bits_smem) CK(ensure(h, h->sbits, (size_t)slots * words));
     // pool after the canonical columns
     // speculative restarts may write a column once per pass
-    size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>((keep_if_same ? 4 : 2) * restart_len,
+    size_t pool = std::max<size_t>(pool_hint, (size_t)std::max<int64_t>((speculate ? 4 : 2) * restart_len,
                                                                         (int64_t)P.Ai.size())) +
                   (size_t)n;
     using TClock = std::chrono::steady_clock;
@@ -515,15 +517,20 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         t.eps = h->opts.pivot_tol;
         t.spin_limit = h->opts.spin_limit;
         t.ctl = h->ctl;
-        // a restart speculates that the steps keep their preferred pivots;
-        // after a pass in which some step took another row, the steps after
-        // the first such step run again (each pass moves that point forward;
-        // after kMaxSpecPasses the last pass runs without speculation)
-        constexpr int kMaxSpecPasses = 8;
+        // a speculative pass predicts that the steps take their preferred
+        // pivots; after a pass in which some step took another row, the
+        // steps after the first such step run again.  The last pass runs
+        // without speculation: after kMaxSpecPasses, after a pass that
+        // finished no step for good, and, in a first factorization (whose
+        // prediction, the diagonal, has no pivot history behind it), after
+        // a pass in which more than kMaxMoved finished steps left their
+        // preferred rows (each wrong prediction costs a pass; a pivot that
+        // moves takes another step's row, so one miss moves two steps)
+        constexpr int kMaxSpecPasses = 8, kMaxMoved = 4;
         std::vector<int32_t> cur = seq;
-        bool pool_full = false;
+        bool pool_full = false, spec = speculate;
         for (int pass = 0;; pass++) {
-            t.speculate = (keep_if_same && pass < kMaxSpecPasses) ? 1 : 0;
+            t.speculate = (spec && pass < kMaxSpecPasses) ? 1 : 0;
             t.nseq = (int32_t)cur.size();
             KL(launch_tail(t, slots, h->tail_epoch, st));
             CK(read_ctl(h, st));
@@ -539,20 +546,32 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
             // may leave steps before js unfinished; a finished step is only
             // known right if every step before it finished, so the next pass
             // starts at the first unfinished step at the latest
-            if (h->hctl->abort_tail) {
-                std::vector<int32_t> dn(n);
+            const bool count_moved = !keep_if_same;
+            if (h->hctl->abort_tail || count_moved) {
+                std::vector<int32_t> dn(n), tp;
                 CU(cudaMemcpyAsync(dn.data(), h->done.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+                if (count_moved) {
+                    tp.resize(n);
+                    CU(cudaMemcpyAsync(tp.data(), h->tpiv.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+                }
                 CU(cudaStreamSynchronize(st));
-                for (int32_t k : cur)
-                    if (dn[k] != h->tail_epoch) {
-                        js = std::min(js, k - 1);
-                        break;   // cur is ascending
-                    }
+                if (h->hctl->abort_tail)
+                    for (int32_t k : cur)
+                        if (dn[k] != h->tail_epoch) {
+                            js = std::min(js, k - 1);
+                            break;   // cur is ascending
+                        }
+                if (count_moved) {
+                    int64_t moved = 0;
+                    for (int32_t k : cur) moved += dn[k] == h->tail_epoch && tp[k] != S.piv[k];
+                    if (moved > kMaxMoved) spec = false;
+                }
             }
             std::vector<int32_t> next;
             for (int32_t k : cur)
                 if (k > js) next.push_back(k);
             if (next.empty()) break;
+            if (next.size() == cur.size()) spec = false;
             cur.swap(next);
             CK(upload(h, h->seq, cur, st));
             KL(launch_tail_repass(h->ctl, h->seq.p, (int32_t)cur.size(), n, h->tpiv.p, h->tpinv.p, h->done.p, st));
@@ -686,7 +705,7 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
     std::vector<uint8_t> finished(n), rmask(n);
     for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
     gblu_restart_set(n, h->P.cetree.data(), finished.data(), rmask.data());
-    return run_tail(h, Ax, st, rmask, 0, true);
+    return run_tail(h, Ax, st, rmask, 0, true, true);
 }
 
 int check_handle(gblu_ctx *h)
@@ -715,6 +734,7 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_dense_density = 0.9;
     o->dense_min_rows = 0;
     o->warp_column_max = kRefCapShort;
+    o->speculate_first = 1;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -725,7 +745,7 @@ static bool opts_valid(const gblu_opts &o)
            o.solve_mode >= 0 && o.solve_mode <= 2 && o.alpha >= 0.0 && o.solve_dense_frac >= 0.0 &&
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
            o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
-           o.warp_column_max <= kRefCapShort;
+           o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1);
 }
 
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
@@ -892,7 +912,8 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     h->factorized = false;
     // no kept columns: an empty structure whose preferred pivots are the
-    // diagonal rows Q[k]; every step is computed with pivoting
+    // diagonal rows Q[k]; every step is computed with pivoting, in passes
+    // that speculate that each step takes its diagonal row
     const int32_t n = h->P.n;
     Structure S;
     S.n = n;
@@ -903,10 +924,11 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     S.pinv = h->P.qinv;
     h->S = std::move(S);
     CK(upload(h, h->piv, h->S.piv, st));
+    CK(upload(h, h->pinv, h->S.pinv, st));
     CU(cudaStreamSynchronize(st));
     const size_t hint = (size_t)(1.25 * (double)(2 * symmetric_fill(h->P) + n));
     std::vector<uint8_t> all(n, 1);
-    CK(run_tail(h, Ax_dev, st, all, hint));
+    CK(run_tail(h, Ax_dev, st, all, hint, false, h->opts.speculate_first != 0));
     h->factorized = true;
     return GBLU_OK;
 }

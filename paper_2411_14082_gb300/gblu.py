@@ -61,7 +61,7 @@ class Opts(ctypes.Structure):
                 ("spin_limit", ctypes.c_longlong), ("solve_dense_frac", ctypes.c_double),
                 ("solve_dense_min", ctypes.c_longlong), ("solve_slices", ctypes.c_int),
                 ("solve_dense_density", ctypes.c_double), ("dense_min_rows", ctypes.c_int),
-                ("warp_column_max", ctypes.c_int)]
+                ("warp_column_max", ctypes.c_int), ("speculate_first", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -218,7 +218,8 @@ class Solver:
 
     def __init__(self, device=0, pivot_tol=1e-3, sched_mode="auto", solve_mode="auto",
                  alpha=2.0, spin_limit=1 << 24, solve_dense_frac=None, solve_dense_min=None,
-                 solve_slices=None, solve_dense_density=None, dense_min_rows=None, warp_column_max=None):
+                 solve_slices=None, solve_dense_density=None, dense_min_rows=None, warp_column_max=None,
+                 speculate_first=None):
         lib = load()
         o = Opts()
         lib.gblu_default_opts(ctypes.byref(o))
@@ -239,6 +240,8 @@ class Solver:
             o.dense_min_rows = dense_min_rows
         if warp_column_max is not None:
             o.warp_column_max = warp_column_max
+        if speculate_first is not None:
+            o.speculate_first = int(bool(speculate_first))
         h = ctypes.c_void_p()
         _check(lib.gblu_create(ctypes.byref(h), int(device), ctypes.byref(o)))
         self._h = h

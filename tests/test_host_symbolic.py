@@ -191,3 +191,19 @@ def test_nested_dissection_order():
     q = gblu.order_nd(m, Ap2, Ai2)
     assert sorted(q.tolist()) == list(range(m))
     assert gblu.symmetric_fill(m, Ap2, Ai2, q) <= 2 * (m - 1)
+
+
+def test_default_options_match_the_header():
+    """gblu_default_opts fills the structure the binding declares: the last
+    fields land where the library writes them."""
+    import ctypes
+    lib = gblu.load()
+    o = gblu.Opts()
+    lib.gblu_default_opts(ctypes.byref(o))
+    assert o.pivot_tol == 1e-3 and o.alpha == 2.0 and o.spin_limit == 1 << 24
+    assert o.solve_dense_density == 0.9 and o.solve_slices == 8
+    assert o.warp_column_max == 1024 and o.speculate_first == 1
+    # an out-of-range switch is rejected before any device work
+    o.speculate_first = 2
+    h = ctypes.c_void_p()
+    assert lib.gblu_create(ctypes.byref(h), 0, ctypes.byref(o)) == gblu.ERR_INVALID_INPUT
