@@ -180,6 +180,28 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// events of one call, destroyed on every way out of it (an event whose
+// work is still pending is released once that work completes)
+struct EventList {
+    std::vector<cudaEvent_t> ev;
+    EventList() = default;
+    EventList(const EventList &) = delete;
+    EventList &operator=(const EventList &) = delete;
+    ~EventList()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    int record(cudaStream_t s, cudaEvent_t *out)
+    {
+        cudaEvent_t e;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ev.push_back(e);
+        CU(cudaEventRecord(e, s));
+        *out = e;
+        return GBLU_OK;
+    }
+};
+
 template <class T>
 int ensure(gblu_ctx *h, DBuf<T> &b, size_t count)
 {
@@ -1282,29 +1304,25 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
     // handles with trailing dense pieces solve on their own streams, forked
     // from `stream` and joined back, overlapping the fused launch (each
     // solve is latency-bound and uses a fraction of the device)
+    EventList events;
     std::vector<cudaEvent_t> joins;
     if (!alone.empty()) {
         cudaEvent_t fork;
-        CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        CU(cudaEventRecord(fork, st));
+        CK(events.record(st, &fork));
         for (int32_t i : alone) {
             gblu_ctx *h = hs[i];
             if (!h->aux) CU(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
             CU(cudaStreamWaitEvent(h->aux, fork, 0));
             CK(gblu_solve(h, b_dev[i], x_dev[i], h->aux));
             cudaEvent_t j;
-            CU(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
-            CU(cudaEventRecord(j, h->aux));
+            CK(events.record(h->aux, &j));
             joins.push_back(j);
         }
-        cudaEventDestroy(fork);
     }
+    // `stream` waits for the forked solves (an error before this leaves
+    // them unjoined; the call then reports it)
     auto join = [&]() -> int {
-        for (cudaEvent_t j : joins) {
-            CU(cudaStreamWaitEvent(st, j, 0));
-            cudaEventDestroy(j);
-        }
-        joins.clear();
+        for (cudaEvent_t j : joins) CU(cudaStreamWaitEvent(st, j, 0));
         return GBLU_OK;
     };
     const int32_t nf = (int32_t)fused.size();
