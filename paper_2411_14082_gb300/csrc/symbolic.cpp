@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "gblu_internal.h"
 
@@ -135,6 +136,35 @@ int64_t symmetric_fill(const Pattern &P)
 // kept if it holds min_entries entries.  The rows [P0, n) are cut into
 // `slices` pieces of equal entry counts (at most max_piece rows each).
 // Returns n when no block qualifies.
+// fn(k0, k1, t) on up to kHostThreads host threads t over index ranges
+// [k0, k1) of about equal weight (ptr: n+1 ascending offsets, the weight of
+// index k is ptr[k+1] - ptr[k]); small inputs run on the calling thread
+constexpr int kHostThreads = 16;
+
+template <class T, class F>
+static void parallel_ranges(int32_t n, const T *ptr, F &&fn)
+{
+    const int nt = (int)std::max(1u, std::min((unsigned)kHostThreads, std::thread::hardware_concurrency()));
+    const int64_t total = n > 0 ? (int64_t)ptr[n] - (int64_t)ptr[0] : 0;
+    if (nt == 1 || total < (1 << 20)) {
+        fn(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    int32_t k0 = 0;
+    for (int t = 1; t <= nt; t++) {
+        int32_t k1 = n;
+        if (t < nt) {
+            const T target = (T)((int64_t)ptr[0] + total * t / nt);
+            k1 = (int32_t)(std::lower_bound(ptr, ptr + n + 1, target) - ptr);
+        }
+        k1 = std::min(std::max(k1, k0), n);
+        if (k1 > k0) th.emplace_back(fn, k0, k1, t - 1);
+        k0 = k1;
+    }
+    for (std::thread &x : th) x.join();
+}
+
 static int32_t dense_split(int32_t n, const std::vector<int64_t> &count_from, const std::vector<int64_t> &rowlen,
                            const SolveSplit &sp, std::vector<int32_t> &cut)
 {
@@ -215,99 +245,113 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             }
         }
     }
-    // ---- EGraph levels and the dividing level (Section IV-B); columns of
-    // the dense tail wait only for their dependencies before it ----
-    std::vector<int32_t> level;
-    W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
-    W.level_ptr.assign(W.n_levels + 1, 0);
-    for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
-    for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
-    W.level_cols.assign(n, 0);
-    {
-        std::vector<int32_t> pos(W.level_ptr.begin(), W.level_ptr.end() - 1);
-        for (int32_t k = 0; k < n; k++) W.level_cols[pos[level[k]]++] = k;
-    }
     const double thr = alpha * (double)resident_warps;
-    W.div_level = W.n_levels;
-    for (int32_t l = 0; l < W.n_levels; l++)
-        if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
-    if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
-    if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
-    // ---- tasks, in level order: long columns alone, medium columns in pairs,
-    // short ones in groups of up to 8.  A pending item is only merged with
-    // the column that immediately follows it, so a task never comes before
-    // a task holding one of its dependencies.  Groups stay inside a level
-    // before the dividing level.
-    W.task_ptr.assign(1, 0);
-    W.task_cols.clear();
-    W.task_cols.reserve(n);
-    W.level_task_ptr.assign(1, 0);
-    {
-        const int64_t half = kRefCapLong / 2;   // medium: up to half the CTA's entries
-        int32_t group = 0;      // short columns pending
-        bool pend_med = false;  // one medium column pending
-        auto close = [&]() {
-            if (group || pend_med) W.task_ptr.push_back((int32_t)W.task_cols.size());
-            group = 0;
-            pend_med = false;
-        };
-        for (int32_t l = 0; l < W.n_levels; l++) {
-            for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
-                const int32_t k = W.level_cols[p];
-                const int64_t len = S.LUp[k + 1] - S.LUp[k];
-                if (len > half) {
-                    close();
-                    W.task_cols.push_back(k);
-                    W.task_ptr.push_back((int32_t)W.task_cols.size());
-                } else if (len > cap_short) {
-                    if (pend_med) {
-                        W.task_cols.push_back(k);
-                        W.task_ptr.push_back((int32_t)W.task_cols.size());
-                        pend_med = false;
-                    } else {
+    // ---- EGraph levels, the dividing level (Section IV-B) and the tasks:
+    // on a thread of their own, beside the slot maps and row-wise copies
+    // below (they write disjoint members of W) ----
+    std::thread level_thread([&]() {
+        // columns of the dense tail wait only for their dependencies before it
+        std::vector<int32_t> level;
+        W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
+        W.level_ptr.assign(W.n_levels + 1, 0);
+        for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
+        for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
+        W.level_cols.assign(n, 0);
+        {
+            std::vector<int32_t> pos(W.level_ptr.begin(), W.level_ptr.end() - 1);
+            for (int32_t k = 0; k < n; k++) W.level_cols[pos[level[k]]++] = k;
+        }
+        W.div_level = W.n_levels;
+        for (int32_t l = 0; l < W.n_levels; l++)
+            if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
+        if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
+        if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
+        // ---- tasks, in level order: long columns alone, medium columns in pairs,
+        // short ones in groups of up to 8.  A pending item is only merged with
+        // the column that immediately follows it, so a task never comes before
+        // a task holding one of its dependencies.  Groups stay inside a level
+        // before the dividing level.
+        W.task_ptr.assign(1, 0);
+        W.task_cols.clear();
+        W.task_cols.reserve(n);
+        W.level_task_ptr.assign(1, 0);
+        {
+            const int64_t half = kRefCapLong / 2;   // medium: up to half the CTA's entries
+            int32_t group = 0;      // short columns pending
+            bool pend_med = false;  // one medium column pending
+            auto close = [&]() {
+                if (group || pend_med) W.task_ptr.push_back((int32_t)W.task_cols.size());
+                group = 0;
+                pend_med = false;
+            };
+            for (int32_t l = 0; l < W.n_levels; l++) {
+                for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
+                    const int32_t k = W.level_cols[p];
+                    const int64_t len = S.LUp[k + 1] - S.LUp[k];
+                    if (len > half) {
                         close();
                         W.task_cols.push_back(k);
-                        pend_med = true;
+                        W.task_ptr.push_back((int32_t)W.task_cols.size());
+                    } else if (len > cap_short) {
+                        if (pend_med) {
+                            W.task_cols.push_back(k);
+                            W.task_ptr.push_back((int32_t)W.task_cols.size());
+                            pend_med = false;
+                        } else {
+                            close();
+                            W.task_cols.push_back(k);
+                            pend_med = true;
+                        }
+                    } else {
+                        if (pend_med) close();
+                        W.task_cols.push_back(k);
+                        if (++group == 8) close();
                     }
-                } else {
-                    if (pend_med) close();
-                    W.task_cols.push_back(k);
-                    if (++group == 8) close();
+                }
+                if (l < W.div_level) {
+                    close();
+                    W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
                 }
             }
-            if (l < W.div_level) {
-                close();
-                W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
+            close();
+        }
+    });
+    // ---- flops of one refactorization (partial sums of integers, exact in
+    // any order below 2^53) ----
+    double part[kHostThreads] = {};
+    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int t) {
+        double fl = 0;
+        for (int32_t k = k0; k < k1; k++)
+            for (int64_t e = S.LUp[k]; e < S.LUp[k] + S.nU[k] - 1; e++) {
+                const int32_t j = S.LUi[e];
+                fl += 2.0 * (double)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
             }
-        }
-        close();
-    }
-    // ---- flops of one refactorization ----
-    double fl = 0;
-    for (int32_t k = 0; k < n; k++)
-        for (int64_t e = S.LUp[k]; e < S.LUp[k] + S.nU[k] - 1; e++) {
-            const int32_t j = S.LUi[e];
-            fl += 2.0 * (double)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
-        }
-    W.flops = fl;
+        part[t] = fl;
+    });
+    W.flops = 0;
+    for (double v : part) W.flops += v;
     // ---- A slot -> position in its column (columns are sorted) ----
     const int64_t nnzA = (int64_t)P.Ai.size();
     W.amap.assign(nnzA, -1);
-    for (int32_t c = 0; c < n; c++) {
-        const int32_t k = P.qinv[c];
-        const int32_t *col = S.LUi.data() + S.LUp[k];
-        const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
-        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-            const int32_t s = S.pinv[P.Ai[p]];
-            const int32_t *it = std::lower_bound(col, col + len, s);
-            W.amap[p] = (it != col + len && *it == s) ? (int32_t)(it - col) : -1;
+    parallel_ranges(n, P.Ap.data(), [&](int32_t c0, int32_t c1, int) {
+        for (int32_t c = c0; c < c1; c++) {
+            const int32_t k = P.qinv[c];
+            const int32_t *col = S.LUi.data() + S.LUp[k];
+            const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
+            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+                const int32_t s = S.pinv[P.Ai[p]];
+                const int32_t *it = std::lower_bound(col, col + len, s);
+                W.amap[p] = (it != col + len && *it == s) ? (int32_t)(it - col) : -1;
+            }
         }
-    }
+    });
     // ---- original row ids of L entries (used by the restart kernel) ----
     W.LUi_orig.assign(S.LUi.size(), 0);
-    for (int32_t k = 0; k < n; k++)
-        for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
-            W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
+    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
+        for (int32_t k = k0; k < k1; k++)
+            for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
+                W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
+    });
     // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
     W.chain.assign(n, 0);
     for (int32_t j = 0; j + 1 < n; j++) {
@@ -316,15 +360,34 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
         W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
     }
-    // ---- row-wise copies for the solves ----
+    // ---- row-wise copies for the solves: entry counts per row from
+    // per-thread histograms over column ranges; then each thread fills the
+    // rows of its own row range, taking the columns in ascending order (so
+    // every row lists its entries by ascending column, as a serial pass
+    // would) and finding its rows in each sorted column by binary search ----
     W.Lrp.assign(n + 1, 0);
     W.Urp.assign(n + 1, 0);
     W.Udiag.assign(n, 0);
-    for (int32_t k = 0; k < n; k++) {
-        const int64_t d = S.LUp[k] + S.nU[k] - 1;
-        W.Udiag[k] = (int32_t)d;
-        for (int64_t e = S.LUp[k]; e < d; e++) W.Urp[S.LUi[e] + 1]++;
-        for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) W.Lrp[S.LUi[e] + 1]++;
+    {
+        std::vector<std::vector<int64_t>> hl(kHostThreads), hu(kHostThreads);
+        parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int t) {
+            std::vector<int64_t> &cl = hl[t], &cu = hu[t];
+            cl.assign(n, 0);
+            cu.assign(n, 0);
+            for (int32_t k = k0; k < k1; k++) {
+                const int64_t d = S.LUp[k] + S.nU[k] - 1;
+                W.Udiag[k] = (int32_t)d;
+                for (int64_t e = S.LUp[k]; e < d; e++) cu[S.LUi[e]]++;
+                for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) cl[S.LUi[e]]++;
+            }
+        });
+        for (int t = 0; t < kHostThreads; t++) {
+            if (hl[t].empty()) continue;
+            for (int32_t i = 0; i < n; i++) {
+                W.Lrp[i + 1] += hl[t][i];
+                W.Urp[i + 1] += hu[t][i];
+            }
+        }
     }
     for (int32_t i = 0; i < n; i++) { W.Lrp[i + 1] += W.Lrp[i]; W.Urp[i + 1] += W.Urp[i]; }
     W.Lcol.assign(W.Lrp[n], 0);
@@ -332,20 +395,32 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     W.Urow_col.assign(W.Urp[n], 0);
     W.Uslot.assign(W.Urp[n], 0);
     {
+        std::vector<int64_t> both(n + 1);
+        for (int32_t i = 0; i <= n; i++) both[i] = W.Lrp[i] + W.Urp[i];
         std::vector<int64_t> lp(W.Lrp.begin(), W.Lrp.end() - 1), up(W.Urp.begin(), W.Urp.end() - 1);
-        for (int32_t k = 0; k < n; k++) {
-            const int64_t d = S.LUp[k] + S.nU[k] - 1;
-            for (int64_t e = S.LUp[k]; e < d; e++) {
-                const int32_t i = S.LUi[e];
-                W.Urow_col[up[i]] = k;
-                W.Uslot[up[i]++] = (int32_t)e;
+        parallel_ranges(n, both.data(), [&](int32_t r0, int32_t r1, int) {
+            for (int32_t k = 0; k < n; k++) {
+                const int32_t *c = S.LUi.data();
+                const int64_t b = S.LUp[k], d = b + S.nU[k] - 1, e1 = S.LUp[k + 1];
+                // U rows of column k are below k; L rows above it
+                if (k > r0) {
+                    int64_t e = std::lower_bound(c + b, c + d, r0) - c;
+                    for (; e < d && c[e] < r1; e++) {
+                        const int32_t i = c[e];
+                        W.Urow_col[up[i]] = k;
+                        W.Uslot[up[i]++] = (int32_t)e;
+                    }
+                }
+                if (k + 1 < r1) {
+                    int64_t e = std::lower_bound(c + d + 1, c + e1, r0) - c;
+                    for (; e < e1 && c[e] < r1; e++) {
+                        const int32_t i = c[e];
+                        W.Lcol[lp[i]] = k;
+                        W.Lslot[lp[i]++] = (int32_t)e;
+                    }
+                }
             }
-            for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) {
-                const int32_t i = S.LUi[e];
-                W.Lcol[lp[i]] = k;
-                W.Lslot[lp[i]++] = (int32_t)e;
-            }
-        }
+        });
     }
     // ---- structure-adaptive split of both triangular factors (Section V) ----
     {
@@ -480,8 +555,13 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         for (int32_t l = 0; l < nlev; l++)
             if ((double)(tptr[l + 1] - tptr[l]) < thr) { div = l; break; }
     };
+    // the two triangles' levels are independent
+    std::thread upper([&]() {
+        levelize(false, W.ubs, W.usv_ptr, W.usv_rows, W.usv_tptr, W.usv_tick, W.urb, W.usv_levels, W.usv_div);
+    });
     levelize(true, W.lbs, W.lsv_ptr, W.lsv_rows, W.lsv_tptr, W.lsv_tick, W.lrb, W.lsv_levels, W.lsv_div);
-    levelize(false, W.ubs, W.usv_ptr, W.usv_rows, W.usv_tptr, W.usv_tick, W.urb, W.usv_levels, W.usv_div);
+    upper.join();
+    level_thread.join();
 }
 
 }  // namespace gblu
