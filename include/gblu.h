@@ -105,8 +105,10 @@ typedef struct {
        again, and the run falls back to waiting on every earlier unfinished
        step of the column's elimination subtree once more than four finished
        steps of a pass have left the diagonal, a pass finishes no step for
-       good, or eight passes have run.  0 = every step waits in that order from the
-       start.  Both give the same factors.  Default 1. */
+       good, or eight passes have run.  It does not speculate at all when
+       more than four columns of A have an absent or zero diagonal entry.
+       0 = every step waits in that order from the start.  Both give the
+       same factors.  Default 1. */
     int speculate_first;
 } gblu_opts;
 

@@ -159,6 +159,11 @@ struct gblu_ctx {
 
 namespace {
 
+// a first factorization (whose pivot prediction, the diagonal, has no
+// history behind it) speculates while at most this many steps of a pass
+// leave their diagonal rows
+constexpr int kSpecMaxMoved = 4;
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = false;
@@ -545,10 +550,10 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         // without speculation: after kMaxSpecPasses, after a pass that
         // finished no step for good, and, in a first factorization (whose
         // prediction, the diagonal, has no pivot history behind it), after
-        // a pass in which more than kMaxMoved finished steps left their
+        // a pass in which more than kSpecMaxMoved finished steps left their
         // preferred rows (each wrong prediction costs a pass; a pivot that
         // moves takes another step's row, so one miss moves two steps)
-        constexpr int kMaxSpecPasses = 8, kMaxMoved = 4;
+        constexpr int kMaxSpecPasses = 8;
         std::vector<int32_t> cur = seq;
         bool pool_full = false, spec = speculate;
         for (int pass = 0;; pass++) {
@@ -586,7 +591,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
                 if (count_moved) {
                     int64_t moved = 0;
                     for (int32_t k : cur) moved += dn[k] == h->tail_epoch && tp[k] != S.piv[k];
-                    if (moved > kMaxMoved) spec = false;
+                    if (moved > kSpecMaxMoved) spec = false;
                 }
             }
             std::vector<int32_t> next;
@@ -947,10 +952,30 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     h->S = std::move(S);
     CK(upload(h, h->piv, h->S.piv, st));
     CK(upload(h, h->pinv, h->S.pinv, st));
+    bool spec = h->opts.speculate_first != 0;
+    if (spec && n > 0) {
+        // the prediction fails where A's diagonal entry is absent or zero
+        // (the branch rows of MNA voltage sources) unless fill makes it
+        // nonzero: with more such steps than a pass tolerates, every step
+        // waits in order from the start
+        const std::vector<int32_t> &Ap = h->P.Ap, &Ai = h->P.Ai;
+        std::vector<double> ax(Ai.size());
+        if (!ax.empty())
+            CU(cudaMemcpyAsync(ax.data(), Ax_dev, sizeof(double) * ax.size(), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        int64_t zero_diag = 0;
+        for (int32_t k = 0; k < n && zero_diag <= kSpecMaxMoved; k++) {
+            const int32_t c = h->P.Q[k];
+            bool nz = false;
+            for (int32_t p = Ap[c]; p < Ap[c + 1] && !nz; p++) nz = Ai[p] == c && ax[p] != 0.0;
+            zero_diag += !nz;
+        }
+        spec = zero_diag <= kSpecMaxMoved;
+    }
     CU(cudaStreamSynchronize(st));
     const size_t hint = (size_t)(1.25 * (double)(2 * symmetric_fill(h->P) + n));
     std::vector<uint8_t> all(n, 1);
-    CK(run_tail(h, Ax_dev, st, all, hint, false, h->opts.speculate_first != 0));
+    CK(run_tail(h, Ax_dev, st, all, hint, false, spec));
     h->factorized = true;
     return GBLU_OK;
 }
