@@ -154,10 +154,8 @@ void gblu_destroy(gblu_handle h);
  * Pre-processing for one sparsity pattern (Section III-A): validates the CSC
  * pattern, takes the column order Q (Q[k] = original column eliminated at
  * step k; rows use the same symmetric order as the preferred pivots), or
- * when Q is NULL computes its own fill-reducing order on A+A^T (nested
- * dissection, gblu_order_nd, for n > 20000; minimum degree below), and
- * builds the
- * column elimination tree of A(:,Q) (the dependency upper bound of
+ * when Q is NULL computes its own fill-reducing order on A+A^T
+ * (gblu_order_auto), and builds the column elimination tree of A(:,Q) (the dependency upper bound of
  * Section II-B used to choose restart columns).  Host-only work.  Ap, Ai,
  * Q are host arrays and are copied.  Any previous factorization of the
  * handle is discarded.
@@ -512,15 +510,44 @@ int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx,
 /* Minimum-degree column order of the pattern of A + A^T: perm[k] = column
  * eliminated at step k. */
 int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Constrained minimum degree (the ordering Section III-A applies after an
+ * incomplete nested dissection): group[i] >= 0 for every vertex; the
+ * vertices are eliminated group by group in increasing group number, and
+ * within a group by least approximate degree in the whole graph (ties to
+ * the lower index).  With one group it equals gblu_order_mindeg. */
+int gblu_order_cmd(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *group, int32_t *perm);
 /* Nested dissection column order of the pattern of A + A^T, without
  * coordinates (multilevel: heavy-edge coarsening, greedy growing bisection,
  * boundary refinement, vertex cover of the cut edges as separator; sets of
- * at most 256 vertices by minimum degree).  Deterministic.  gblu_analyze
- * uses it when Q is NULL and n > 20000 (minimum degree below that). */
+ * at most 256 vertices by minimum degree).  Deterministic. */
 int gblu_order_nd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Incomplete nested dissection followed by constrained minimum degree
+ * (Section III-A): the dissection of gblu_order_nd only assigns groups (each
+ * set of at most 256 vertices, then each separator after its two halves),
+ * and one minimum-degree pass orders the whole graph, taking the groups in
+ * that order, so leaf orders see their boundaries and separators are
+ * ordered as well.  Deterministic. */
+int gblu_order_cnd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* methods of gblu_order_auto */
+#define GBLU_ORDER_MINDEG 0   /* gblu_order_mindeg */
+#define GBLU_ORDER_ND 1       /* gblu_order_nd     */
+#define GBLU_ORDER_CND 2      /* gblu_order_cnd    */
+/* Section III-A's selection: several orders are computed on host threads
+ * (minimum degree up to n = 50000, nested dissection, and nested dissection
+ * with constrained minimum degree), and the one whose factorization costs
+ * the fewest flops when every diagonal pivot is kept (gblu_symmetric_cost)
+ * is written to perm; ties go to that list's order.  *method (optional)
+ * receives its GBLU_ORDER_* code.  gblu_analyze uses it when Q is NULL. */
+int gblu_order_auto(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t *method);
 /* Entries of the strict lower Cholesky factor of (A + A^T)(Q,Q): the fill of
  * an ordering when every diagonal pivot is kept; negative on invalid input. */
 int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q);
+/* The same fill (*fill, optional) and the factorization's flops when every
+ * diagonal pivot is kept on that symmetric pattern, F = sum_j 2 c_j^2 with
+ * c_j the entries of column j (*flops, optional).  GBLU_ERR_INVALID_INPUT
+ * for an invalid pattern or a Q that is not a permutation. */
+int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q, int64_t *fill,
+                        double *flops);
 /* Column elimination tree of A(:,Q) (elimination tree of (A Q)^T (A Q)),
  * parent[k] = parent step of step k or -1 (Section II-B "ETree"). */
 int gblu_column_etree(int32_t n, const int32_t *Ap, const int32_t *Ai,

@@ -880,10 +880,8 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
             seen[Q[k]] = 1;
             P.Q[k] = Q[k];
         }
-    } else if (n > 20000) {
-        nd_order(n, Ap, Ai, P.Q.data(), 256);
     } else {
-        mindeg_order(n, Ap, Ai, P.Q.data());
+        auto_order(n, Ap, Ai, P.Q.data());
     }
     P.qinv.assign(n, 0);
     for (int32_t k = 0; k < n; k++) P.qinv[P.Q[k]] = k;

@@ -102,14 +102,24 @@ int record_error(int code, const char *msg);
 
 int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
 void column_etree(const Pattern &P, std::vector<int32_t> &parent);
-void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+// minimum degree on A + A^T; with `group`, constrained: groups are
+// eliminated in increasing order
+void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm,
+                  const int32_t *group = nullptr);
 // multilevel nested dissection (nd_order.cpp); sets of at most `leaf`
-// vertices are ordered by minimum degree
-void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf);
+// vertices are ordered by minimum degree, each on its own, and separators
+// keep their vertex order.  constrained: the dissection only assigns groups
+// (each leaf set, then each separator after its two halves) and constrained
+// minimum degree orders the whole graph
+void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf,
+              bool constrained = false);
+// the order of fewest factorization flops among the candidate methods
+// (computed on host threads); returns the GBLU_ORDER_* method chosen
+int auto_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
 // nnz of the Cholesky factor of (A + A^T)(Q,Q) (strict lower part), the
 // size of the LU factors when every diagonal pivot is kept on a structurally
 // symmetric matrix; used to size the first factorization's pool
-int64_t symmetric_fill(const Pattern &P);
+int64_t symmetric_fill(const Pattern &P, double *flops = nullptr);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
                     int dense_min_rows, Schedule &W);

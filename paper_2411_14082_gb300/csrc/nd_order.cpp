@@ -17,12 +17,20 @@
 //              with no neighbour on one side then leave it.
 // Random choices use a fixed-seed generator, so the ordering is
 // deterministic.
+//
+// Constrained form (Section III-A's incomplete nested dissection followed by
+// constrained minimum degree): the same dissection only numbers groups, each
+// leaf set and then each separator after its two halves, and one
+// constrained minimum-degree pass orders the whole graph group by group, so
+// the leaves' orders see their boundaries and the separators are ordered
+// too.
 #include <algorithm>
 #include <cstdint>
 #include <numeric>
 #include <queue>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gblu_internal.h"
@@ -270,9 +278,16 @@ struct Ordering {
     std::vector<int32_t> local;
     std::mt19937 rng{20241121u};
     int32_t leaf;
+    std::vector<int32_t> *group = nullptr;   // constrained form: group of each vertex
+    int32_t next_group = 0;
 
     void by_mindeg(const std::vector<int32_t> &verts)
     {
+        if (group) {
+            for (int32_t v : verts) (*group)[v] = next_group;
+            next_group++;
+            return;
+        }
         if (verts.size() <= 2) {
             out.insert(out.end(), verts.begin(), verts.end());
             return;
@@ -362,7 +377,12 @@ struct Ordering {
         }
         rec(std::move(a), depth + 1);
         rec(std::move(b), depth + 1);
-        out.insert(out.end(), sep.begin(), sep.end());
+        if (group) {
+            for (int32_t v : sep) (*group)[v] = next_group;
+            next_group++;
+        } else {
+            out.insert(out.end(), sep.begin(), sep.end());
+        }
     }
 };
 
@@ -370,7 +390,7 @@ struct Ordering {
 
 namespace gblu {
 
-void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf)
+void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t leaf, bool constrained)
 {
     Graph g;
     g.n = n;
@@ -395,13 +415,75 @@ void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, in
     std::vector<int32_t> out;
     out.reserve(n);
     Ordering o{g, out, std::vector<int32_t>(n, -1), std::mt19937{20241121u}, leaf};
+    std::vector<int32_t> grp;
+    if (constrained) {
+        grp.assign(n, 0);
+        o.group = &grp;
+    }
     std::vector<int32_t> all(n);
     std::iota(all.begin(), all.end(), 0);
     o.rec(std::move(all), 0);
+    if (constrained) {
+        mindeg_order(n, Ap, Ai, perm, grp.data());
+        return;
+    }
     std::copy(out.begin(), out.end(), perm);
 }
 
+// Section III-A runs several orderings and keeps the best.  Candidates here:
+// minimum degree (up to kAutoMindegMax unknowns; beyond that it is slow and,
+// on meshes, poor), nested dissection, and incomplete nested dissection with
+// constrained minimum degree, each on a host thread of its own.  The one
+// whose factorization costs the fewest flops when every diagonal pivot is
+// kept (F = sum_j 2 c_j^2 of the symmetric pattern, the re-factorization's
+// work) wins; ties go to the earlier candidate.
+int auto_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    constexpr int32_t kAutoMindegMax = 50000;
+    struct Candidate {
+        int method;
+        std::vector<int32_t> perm;
+        double flops = 0.0;
+    };
+    std::vector<Candidate> cand;
+    if (n <= kAutoMindegMax) cand.push_back({GBLU_ORDER_MINDEG, {}, 0.0});
+    cand.push_back({GBLU_ORDER_ND, {}, 0.0});
+    cand.push_back({GBLU_ORDER_CND, {}, 0.0});
+    auto run = [n, Ap, Ai](Candidate *c) {
+        c->perm.resize(n);
+        if (c->method == GBLU_ORDER_MINDEG) mindeg_order(n, Ap, Ai, c->perm.data());
+        else nd_order(n, Ap, Ai, c->perm.data(), 256, c->method == GBLU_ORDER_CND);
+        Pattern P;
+        P.n = n;
+        P.Ap.assign(Ap, Ap + n + 1);
+        P.Ai.assign(Ai, Ai + Ap[n]);
+        P.Q = c->perm;
+        P.qinv.assign(n, 0);
+        for (int32_t k = 0; k < n; k++) P.qinv[c->perm[k]] = k;
+        symmetric_fill(P, &c->flops);
+    };
+    std::vector<std::thread> th;
+    for (size_t i = 1; i < cand.size(); i++) th.emplace_back(run, &cand[i]);
+    run(&cand[0]);
+    for (std::thread &t : th) t.join();
+    size_t best = 0;
+    for (size_t i = 1; i < cand.size(); i++)
+        if (cand[i].flops < cand[best].flops) best = i;
+    std::copy(cand[best].perm.begin(), cand[best].perm.end(), perm);
+    return cand[best].method;
+}
+
 }  // namespace gblu
+
+extern "C" int gblu_order_auto(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, int32_t *method)
+{
+    std::string err;
+    if (gblu::validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm)
+        return gblu::record_error(GBLU_ERR_INVALID_INPUT, "order_auto: invalid pattern or null perm");
+    const int m = gblu::auto_order(n, Ap, Ai, perm);
+    if (method) *method = m;
+    return GBLU_OK;
+}
 
 extern "C" int gblu_order_nd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
 {
@@ -409,5 +491,14 @@ extern "C" int gblu_order_nd(int32_t n, const int32_t *Ap, const int32_t *Ai, in
     if (gblu::validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm)
         return gblu::record_error(GBLU_ERR_INVALID_INPUT, "order_nd: invalid pattern or null perm");
     gblu::nd_order(n, Ap, Ai, perm, 256);
+    return GBLU_OK;
+}
+
+extern "C" int gblu_order_cnd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    std::string err;
+    if (gblu::validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm)
+        return gblu::record_error(GBLU_ERR_INVALID_INPUT, "order_cnd: invalid pattern or null perm");
+    gblu::nd_order(n, Ap, Ai, perm, 256, true);
     return GBLU_OK;
 }

@@ -9,6 +9,12 @@
 // the approximate external degree of Amestoy, Davis and Duff (1996).
 // Elements contained in Lp are absorbed as well.  Ties go to the lower
 // index, so the order is deterministic.
+//
+// Constrained form (the constrained minimum degree that Section III-A
+// applies after an incomplete nested dissection): every variable carries a
+// group number and the pivot is the variable of least degree among those of
+// the lowest group still present, so groups are eliminated in order while
+// the degrees still see the whole graph.
 #include <algorithm>
 #include <set>
 #include <vector>
@@ -17,7 +23,7 @@
 
 namespace gblu {
 
-void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, const int32_t *group)
 {
     std::vector<std::vector<int32_t>> A(n), E(n), Lel(n);
     for (int32_t c = 0; c < n; c++)
@@ -34,10 +40,12 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
     std::vector<char> elim(n, 0), alive(n, 0);
     std::vector<int32_t> deg(n), mark(n, -1), wmark(n, -1);
     std::vector<int64_t> w(n, 0);
-    std::set<std::pair<int32_t, int32_t>> pq;
+    // key: group (high word), then degree; ties by index
+    auto key = [&](int32_t i) { return ((int64_t)(group ? group[i] : 0) << 32) | (int64_t)deg[i]; };
+    std::set<std::pair<int64_t, int32_t>> pq;
     for (int32_t i = 0; i < n; i++) {
         deg[i] = (int32_t)A[i].size();
-        pq.insert({deg[i], i});
+        pq.insert({key(i), i});
     }
     std::vector<int32_t> Lp;
     for (int32_t k = 0; k < n; k++) {
@@ -94,9 +102,9 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
             int64_t d = (int64_t)Ai_.size() + (int64_t)Lp.size() - 1 + ext;
             if (d > remaining - 1) d = remaining - 1;
             if (d < 0) d = 0;
-            pq.erase({deg[i], i});
+            pq.erase({key(i), i});
             deg[i] = (int32_t)d;
-            pq.insert({deg[i], i});
+            pq.insert({key(i), i});
         }
     }
 }

@@ -81,8 +81,10 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
 // visited for row k ("row subtree").  When every diagonal pivot is kept on a
 // structurally symmetric matrix, L and U^T both have this pattern; it sizes
 // the pool of the first factorization (pivoting can change it, and the pool
-// then grows).
-int64_t symmetric_fill(const Pattern &P)
+// then grows).  With c_j the entries of column j, the factorization then
+// costs F = sum_j 2 c_j^2 flops (every U(j,k) != 0 uses the c_j entries of
+// L(:,j), and U(j,:) has c_j entries above the diagonal): *flops.
+int64_t symmetric_fill(const Pattern &P, double *flops)
 {
     const int32_t n = P.n;
     std::vector<int64_t> cnt(n + 1, 0);
@@ -114,13 +116,19 @@ int64_t symmetric_fill(const Pattern &P)
         }
     }
     int64_t total = 0;
+    std::vector<int64_t> colcount(flops ? n : 0, 0);
     for (int32_t k = 0; k < n; k++) {
         mark[k] = k;
         for (int64_t e = cnt[k]; e < cnt[k + 1]; e++)
             for (int32_t j = lowadj[e]; j != -1 && mark[j] != k; j = parent[j]) {
                 mark[j] = k;
                 total++;
+                if (flops) colcount[j]++;
             }
+    }
+    if (flops) {
+        *flops = 0.0;
+        for (int64_t c : colcount) *flops += 2.0 * (double)c * (double)c;
     }
     return total;
 }
@@ -619,10 +627,12 @@ extern "C" int32_t gblu_levels(int32_t n, const int64_t *Up, const int32_t *Ui, 
     return nl;
 }
 
-extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)
+extern "C" int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                                   int64_t *fill, double *flops)
 {
     std::string err;
-    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !Q) return GBLU_ERR_INVALID_INPUT;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !Q)
+        return record_error(GBLU_ERR_INVALID_INPUT, "symmetric cost: invalid pattern or null Q");
     Pattern P;
     P.n = n;
     P.Ap.assign(Ap, Ap + n + 1);
@@ -630,10 +640,20 @@ extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32
     P.Q.assign(Q, Q + n);
     P.qinv.assign(n, -1);
     for (int32_t k = 0; k < n; k++) {
-        if (Q[k] < 0 || Q[k] >= n || P.qinv[Q[k]] >= 0) return GBLU_ERR_INVALID_INPUT;
+        if (Q[k] < 0 || Q[k] >= n || P.qinv[Q[k]] >= 0)
+            return record_error(GBLU_ERR_INVALID_INPUT, "symmetric cost: Q is not a permutation");
         P.qinv[Q[k]] = k;
     }
-    return symmetric_fill(P);
+    const int64_t f = symmetric_fill(P, flops);
+    if (fill) *fill = f;
+    return GBLU_OK;
+}
+
+extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)
+{
+    int64_t fill = 0;
+    const int rc = gblu_symmetric_cost(n, Ap, Ai, Q, &fill, nullptr);
+    return rc != GBLU_OK ? rc : fill;
 }
 
 extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
@@ -641,5 +661,16 @@ extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai
     std::string err;
     if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm) return GBLU_ERR_INVALID_INPUT;
     mindeg_order(n, Ap, Ai, perm);
+    return GBLU_OK;
+}
+
+extern "C" int gblu_order_cmd(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *group, int32_t *perm)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm || !group)
+        return record_error(GBLU_ERR_INVALID_INPUT, "order_cmd: invalid pattern or null array");
+    for (int32_t i = 0; i < n; i++)
+        if (group[i] < 0) return record_error(GBLU_ERR_INVALID_INPUT, "order_cmd: negative group");
+    mindeg_order(n, Ap, Ai, perm, group);
     return GBLU_OK;
 }

@@ -41,7 +41,7 @@ EXPORTED = [
     "gblu_solve_batch", "gblu_refactorize_f32", "gblu_solve_refined", "gblu_refactorize_forced",
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
     "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale", "gblu_order_nd",
-    "gblu_symmetric_fill",
+    "gblu_symmetric_fill", "gblu_order_cnd", "gblu_symmetric_cost", "gblu_order_cmd", "gblu_order_auto",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -141,6 +141,14 @@ def load(build_if_missing: bool = True):
         lib.gblu_order_nd.restype = ctypes.c_int
         lib.gblu_symmetric_fill.argtypes = [I32, P, P, P]
         lib.gblu_symmetric_fill.restype = I64
+        lib.gblu_order_cnd.argtypes = [I32, P, P, P]
+        lib.gblu_order_cnd.restype = ctypes.c_int
+        lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
+        lib.gblu_symmetric_cost.restype = ctypes.c_int
+        lib.gblu_order_cmd.argtypes = [I32, P, P, P, P]
+        lib.gblu_order_cmd.restype = ctypes.c_int
+        lib.gblu_order_auto.argtypes = [I32, P, P, P, P]
+        lib.gblu_order_auto.restype = ctypes.c_int
         lib.gblu_column_etree.argtypes = [I32, P, P, P, P]
         lib.gblu_restart_set.argtypes = [I32, P, P, P]
         lib.gblu_restart_set.restype = I64
@@ -464,6 +472,44 @@ def order_nd(n, Ap, Ai):
     perm = np.empty(n, np.int32)
     _check(load().gblu_order_nd(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
     return perm
+
+
+def order_cnd(n, Ap, Ai):
+    """Incomplete nested dissection + constrained minimum degree (gblu_order_cnd, host)."""
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    perm = np.empty(n, np.int32)
+    _check(load().gblu_order_cnd(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
+    return perm
+
+
+def order_cmd(n, Ap, Ai, group):
+    """Constrained minimum degree: groups eliminated in increasing order (gblu_order_cmd, host)."""
+    Ap, Ai, group = _i32(Ap), _i32(Ai), _i32(group)
+    perm = np.empty(n, np.int32)
+    _check(load().gblu_order_cmd(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(group), _np_ptr(perm)))
+    return perm
+
+
+ORDER_METHODS = {0: "mindeg", 1: "nd", 2: "cnd"}
+
+
+def order_auto(n, Ap, Ai):
+    """The candidate order of fewest flops (gblu_order_auto, host): (perm, method name)."""
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    perm = np.empty(n, np.int32)
+    m = ctypes.c_int32()
+    _check(load().gblu_order_auto(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm), ctypes.byref(m)))
+    return perm, ORDER_METHODS[m.value]
+
+
+def symmetric_cost(n, Ap, Ai, Q):
+    """(fill, flops) of an order when every diagonal pivot is kept (gblu_symmetric_cost, host)."""
+    Ap, Ai, Q = _i32(Ap), _i32(Ai), _i32(Q)
+    fill = ctypes.c_int64()
+    flops = ctypes.c_double()
+    _check(load().gblu_symmetric_cost(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), ctypes.byref(fill),
+                                      ctypes.byref(flops)))
+    return int(fill.value), float(flops.value)
 
 
 def symmetric_fill(n, Ap, Ai, Q):

@@ -410,7 +410,8 @@ def test_library_ordering_when_no_q_given():
     Axd = dev(Ax)
     s.factorize(Axd)
     f = s.export_factors()
-    lu = O.factorize(n, Ap, Ai, Ax, gblu.order_mindeg(n, Ap, Ai), 1e-3)
+    assert np.array_equal(f["q"], gblu.order_auto(n, Ap, Ai)[0])
+    lu = O.factorize(n, Ap, Ai, Ax, f["q"], 1e-3)
     compare_factors(f, lu, RTOL)
     solve_and_check(s, n, Ap, Ai, Ax, Axd, np.random.default_rng(0))
 
