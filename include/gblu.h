@@ -510,6 +510,12 @@ int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx,
 /* Minimum-degree column order of the pattern of A + A^T: perm[k] = column
  * eliminated at step k. */
 int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
+/* Approximate minimum deficiency on the pattern of A + A^T (the minimum
+ * degree variant Section III-A also runs): each step eliminates the vertex
+ * whose elimination is estimated to add the fewest entries,
+ * d(d-1)/2 - c(c-1)/2 with d its approximate degree and c+1 the size of the
+ * largest clique (element) it belongs to; ties to the lower index. */
+int gblu_order_amf(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
 /* Constrained minimum degree (the ordering Section III-A applies after an
  * incomplete nested dissection): group[i] >= 0 for every vertex; the
  * vertices are eliminated group by group in increasing group number, and
@@ -532,9 +538,11 @@ int gblu_order_cnd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *per
 #define GBLU_ORDER_MINDEG 0   /* gblu_order_mindeg */
 #define GBLU_ORDER_ND 1       /* gblu_order_nd     */
 #define GBLU_ORDER_CND 2      /* gblu_order_cnd    */
+#define GBLU_ORDER_AMF 3      /* gblu_order_amf    */
 /* Section III-A's selection: several orders are computed on host threads
- * (minimum degree up to n = 50000, nested dissection, and nested dissection
- * with constrained minimum degree), and the one whose factorization costs
+ * (minimum degree and approximate minimum deficiency up to n = 50000,
+ * nested dissection, and nested dissection with constrained minimum
+ * degree), and the one whose factorization costs
  * the fewest flops when every diagonal pivot is kept (gblu_symmetric_cost)
  * is written to perm; ties go to that list's order.  *method (optional)
  * receives its GBLU_ORDER_* code.  gblu_analyze uses it when Q is NULL. */

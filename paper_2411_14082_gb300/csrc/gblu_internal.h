@@ -103,9 +103,10 @@ int record_error(int code, const char *msg);
 int validate_pattern(int32_t n, const int32_t *Ap, const int32_t *Ai, std::string &err);
 void column_etree(const Pattern &P, std::vector<int32_t> &parent);
 // minimum degree on A + A^T; with `group`, constrained: groups are
-// eliminated in increasing order
+// eliminated in increasing order; deficiency: least estimated fill instead
+// of least degree
 void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm,
-                  const int32_t *group = nullptr);
+                  const int32_t *group = nullptr, bool deficiency = false);
 // multilevel nested dissection (nd_order.cpp); sets of at most `leaf`
 // vertices are ordered by minimum degree, each on its own, and separators
 // keep their vertex order.  constrained: the dissection only assigns groups

@@ -431,9 +431,10 @@ void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, in
 }
 
 // Section III-A runs several orderings and keeps the best.  Candidates here:
-// minimum degree (up to kAutoMindegMax unknowns; beyond that it is slow and,
-// on meshes, poor), nested dissection, and incomplete nested dissection with
-// constrained minimum degree, each on a host thread of its own.  The one
+// minimum degree and approximate minimum deficiency (up to kAutoMindegMax
+// unknowns; beyond that they are slow and, on meshes, poor), nested
+// dissection, and incomplete nested dissection with constrained minimum
+// degree, each on a host thread of its own.  The one
 // whose factorization costs the fewest flops when every diagonal pivot is
 // kept (F = sum_j 2 c_j^2 of the symmetric pattern, the re-factorization's
 // work) wins; ties go to the earlier candidate.
@@ -446,13 +447,18 @@ int auto_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
         double flops = 0.0;
     };
     std::vector<Candidate> cand;
-    if (n <= kAutoMindegMax) cand.push_back({GBLU_ORDER_MINDEG, {}, 0.0});
+    if (n <= kAutoMindegMax) {
+        cand.push_back({GBLU_ORDER_MINDEG, {}, 0.0});
+        cand.push_back({GBLU_ORDER_AMF, {}, 0.0});
+    }
     cand.push_back({GBLU_ORDER_ND, {}, 0.0});
     cand.push_back({GBLU_ORDER_CND, {}, 0.0});
     auto run = [n, Ap, Ai](Candidate *c) {
         c->perm.resize(n);
-        if (c->method == GBLU_ORDER_MINDEG) mindeg_order(n, Ap, Ai, c->perm.data());
-        else nd_order(n, Ap, Ai, c->perm.data(), 256, c->method == GBLU_ORDER_CND);
+        if (c->method == GBLU_ORDER_MINDEG || c->method == GBLU_ORDER_AMF)
+            mindeg_order(n, Ap, Ai, c->perm.data(), nullptr, c->method == GBLU_ORDER_AMF);
+        else
+            nd_order(n, Ap, Ai, c->perm.data(), 256, c->method == GBLU_ORDER_CND);
         Pattern P;
         P.n = n;
         P.Ap.assign(Ap, Ap + n + 1);

@@ -15,6 +15,13 @@
 // group number and the pivot is the variable of least degree among those of
 // the lowest group still present, so groups are eliminated in order while
 // the degrees still see the whole graph.
+//
+// Deficiency form (the approximate minimum deficiency variant Section III-A
+// also runs): the pivot is the variable whose elimination is estimated to
+// create the fewest new entries, d(d-1)/2 - c(c-1)/2, where d is its
+// approximate degree and c+1 the size of the largest element it belongs to
+// (the pairs of that clique exist already); the approximate mean local fill
+// score of Rothberg and Eisenstat.
 #include <algorithm>
 #include <set>
 #include <vector>
@@ -23,7 +30,8 @@
 
 namespace gblu {
 
-void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, const int32_t *group)
+void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, const int32_t *group,
+                  bool deficiency)
 {
     std::vector<std::vector<int32_t>> A(n), E(n), Lel(n);
     for (int32_t c = 0; c < n; c++)
@@ -38,13 +46,20 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
         A[i].erase(std::unique(A[i].begin(), A[i].end()), A[i].end());
     }
     std::vector<char> elim(n, 0), alive(n, 0);
-    std::vector<int32_t> deg(n), mark(n, -1), wmark(n, -1);
-    std::vector<int64_t> w(n, 0);
-    // key: group (high word), then degree; ties by index
-    auto key = [&](int32_t i) { return ((int64_t)(group ? group[i] : 0) << 32) | (int64_t)deg[i]; };
+    std::vector<int32_t> mark(n, -1), wmark(n, -1);
+    std::vector<int64_t> w(n, 0), score(n);
+    // key: group (bits 40 and up), then the score (degree, or estimated
+    // fill); ties by index
+    constexpr int64_t kScoreMax = (int64_t(1) << 40) - 1;
+    auto key = [&](int32_t i) { return ((int64_t)(group ? group[i] : 0) << 40) | score[i]; };
+    auto score_of = [&](int64_t d, int64_t c) -> int64_t {
+        if (!deficiency) return d;
+        c = std::min(c, d);
+        return std::min(kScoreMax, (d * (d - 1) - c * (c - 1)) / 2);
+    };
     std::set<std::pair<int64_t, int32_t>> pq;
     for (int32_t i = 0; i < n; i++) {
-        deg[i] = (int32_t)A[i].size();
+        score[i] = score_of((int64_t)A[i].size(), 0);
         pq.insert({key(i), i});
     }
     std::vector<int32_t> Lp;
@@ -81,7 +96,7 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
         for (int32_t i : Lp) {
             std::vector<int32_t> &Ei = E[i];
             size_t o = 0;
-            int64_t ext = 0;
+            int64_t ext = 0, clique = (int64_t)Lp.size() - 1;
             for (int32_t e : Ei) {
                 if (!alive[e] || e == p) continue;
                 if (wmark[e] == k && w[e] <= 0) {  // e inside Lp: absorb
@@ -91,6 +106,7 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
                 }
                 Ei[o++] = e;
                 ext += (wmark[e] == k) ? w[e] : (int64_t)Lel[e].size();
+                clique = std::max(clique, (int64_t)Lel[e].size() - 1);
             }
             Ei.resize(o);
             Ei.push_back(p);
@@ -103,7 +119,7 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
             if (d > remaining - 1) d = remaining - 1;
             if (d < 0) d = 0;
             pq.erase({key(i), i});
-            deg[i] = (int32_t)d;
+            score[i] = score_of(d, clique);
             pq.insert({key(i), i});
         }
     }

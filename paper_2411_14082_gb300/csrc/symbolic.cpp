@@ -664,6 +664,15 @@ extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai
     return GBLU_OK;
 }
 
+extern "C" int gblu_order_amf(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !perm)
+        return record_error(GBLU_ERR_INVALID_INPUT, "order_amf: invalid pattern or null perm");
+    mindeg_order(n, Ap, Ai, perm, nullptr, true);
+    return GBLU_OK;
+}
+
 extern "C" int gblu_order_cmd(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *group, int32_t *perm)
 {
     std::string err;

@@ -42,6 +42,7 @@ EXPORTED = [
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
     "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale", "gblu_order_nd",
     "gblu_symmetric_fill", "gblu_order_cnd", "gblu_symmetric_cost", "gblu_order_cmd", "gblu_order_auto",
+    "gblu_order_amf",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -145,6 +146,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_order_cnd.restype = ctypes.c_int
         lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
         lib.gblu_symmetric_cost.restype = ctypes.c_int
+        lib.gblu_order_amf.argtypes = [I32, P, P, P]
+        lib.gblu_order_amf.restype = ctypes.c_int
         lib.gblu_order_cmd.argtypes = [I32, P, P, P, P]
         lib.gblu_order_cmd.restype = ctypes.c_int
         lib.gblu_order_auto.argtypes = [I32, P, P, P, P]
@@ -482,6 +485,14 @@ def order_cnd(n, Ap, Ai):
     return perm
 
 
+def order_amf(n, Ap, Ai):
+    """Approximate minimum deficiency order (gblu_order_amf, host)."""
+    Ap, Ai = _i32(Ap), _i32(Ai)
+    perm = np.empty(n, np.int32)
+    _check(load().gblu_order_amf(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
+    return perm
+
+
 def order_cmd(n, Ap, Ai, group):
     """Constrained minimum degree: groups eliminated in increasing order (gblu_order_cmd, host)."""
     Ap, Ai, group = _i32(Ap), _i32(Ai), _i32(group)
@@ -490,7 +501,7 @@ def order_cmd(n, Ap, Ai, group):
     return perm
 
 
-ORDER_METHODS = {0: "mindeg", 1: "nd", 2: "cnd"}
+ORDER_METHODS = {0: "mindeg", 1: "nd", 2: "cnd", 3: "amf"}
 
 
 def order_auto(n, Ap, Ai):

@@ -280,16 +280,36 @@ def test_constrained_nested_dissection_and_automatic_choice():
     assert sorted(q_cnd.tolist()) == list(range(n))
     assert np.array_equal(q_cnd, gblu.order_cnd(n, Ap, Ai))
     costs = {"mindeg": gblu.symmetric_cost(n, Ap, Ai, gblu.order_mindeg(n, Ap, Ai))[1],
+             "amf": gblu.symmetric_cost(n, Ap, Ai, gblu.order_amf(n, Ap, Ai))[1],
              "nd": gblu.symmetric_cost(n, Ap, Ai, q_nd)[1],
              "cnd": gblu.symmetric_cost(n, Ap, Ai, q_cnd)[1]}
     assert costs["cnd"] <= costs["nd"]
     q, method = gblu.order_auto(n, Ap, Ai)
     assert costs[method] == min(costs.values())
     assert gblu.symmetric_cost(n, Ap, Ai, q)[1] == costs[method]
-    # small circuit: minimum degree is a candidate too
+    # small circuit: the minimum-degree family is a candidate too
     ckt = inputs.workload_small()
     n, Ap, Ai, _ = ckt.csc()
     q, method = gblu.order_auto(n, Ap, Ai)
     best = min(gblu.symmetric_cost(n, Ap, Ai, f(n, Ap, Ai))[1]
-               for f in (gblu.order_mindeg, gblu.order_nd, gblu.order_cnd))
+               for f in (gblu.order_mindeg, gblu.order_amf, gblu.order_nd, gblu.order_cnd))
     assert gblu.symmetric_cost(n, Ap, Ai, q)[1] == best
+
+
+def test_minimum_deficiency_order():
+    """gblu_order_amf: a deterministic permutation that, on the C1 grid and
+    on the bordered grid, costs fewer flops than minimum degree (measured:
+    2.4 against 2.8 and 205 against 236 MFLOP), and on a path adds no fill."""
+    for ckt in (inputs.workload_small(), inputs.bordered_grid()):
+        n, Ap, Ai, _ = ckt.csc()
+        q = gblu.order_amf(n, Ap, Ai)
+        assert sorted(q.tolist()) == list(range(n))
+        assert np.array_equal(q, gblu.order_amf(n, Ap, Ai))
+        assert gblu.symmetric_cost(n, Ap, Ai, q)[1] < gblu.symmetric_cost(n, Ap, Ai, gblu.order_mindeg(n, Ap, Ai))[1]
+    m = 500
+    rows = [np.array([j - 1, j, j + 1]) for j in range(m)]
+    rows = [r[(r >= 0) & (r < m)] for r in rows]
+    Ap2 = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    Ai2 = np.concatenate(rows).astype(np.int32)
+    q = gblu.order_amf(m, Ap2, Ai2)
+    assert gblu.symmetric_fill(m, Ap2, Ai2, q) == m - 1
