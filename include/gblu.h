@@ -542,7 +542,7 @@ int gblu_order_cnd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *per
 /* Section III-A's selection: several orders are computed on host threads
  * (minimum degree and approximate minimum deficiency up to n = 50000,
  * nested dissection, and nested dissection with constrained minimum
- * degree), and the one whose factorization costs
+ * degree up to n = 200000), and the one whose factorization costs
  * the fewest flops when every diagonal pivot is kept (gblu_symmetric_cost)
  * is written to perm; ties go to that list's order.  *method (optional)
  * receives its GBLU_ORDER_* code.  gblu_analyze uses it when Q is NULL. */
