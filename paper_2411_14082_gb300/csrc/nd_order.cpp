@@ -15,8 +15,11 @@
 //   separate - a vertex cover of the cut edges (greedy, endpoint with more
 //              cut edges first) becomes the separator; separator vertices
 //              with no neighbour on one side then leave it.
-// Random choices use a fixed-seed generator, so the ordering is
-// deterministic.
+// Each split keeps the smallest of three trials (twelve at the two top
+// levels, whose separators become the largest dense blocks).  Every node of
+// the dissection tree draws from its own generator, seeded from its
+// parent's, and the subtrees of the top four levels run on threads of their
+// own: the ordering is deterministic and independent of thread timing.
 //
 // Constrained form (Section III-A's incomplete nested dissection followed by
 // constrained minimum degree): the same dissection only numbers groups, each
@@ -272,30 +275,45 @@ std::vector<uint8_t> bisect(const Graph &g, std::mt19937 &rng)
     return part;
 }
 
+// one block of the result, in elimination order: a leaf set (ordered by
+// minimum degree in the plain form) or a separator (vertex order)
+struct Block {
+    std::vector<int32_t> verts;
+};
+
+// seed of a child of the dissection-tree node with seed `s` (splitmix64
+// finalizer), so that every node draws from its own generator and the
+// result does not depend on which thread runs which subtree
+uint64_t child_seed(uint64_t s, uint64_t child)
+{
+    uint64_t z = s + 0x9E3779B97F4A7C15ULL * (child + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// bisection trials at the dissection tree's top levels
+constexpr int kTopDepth = 2, kTopTrials = 12;
+
 struct Ordering {
     const Graph &g;
-    std::vector<int32_t> &out;
-    std::vector<int32_t> local;
-    std::mt19937 rng{20241121u};
     int32_t leaf;
-    std::vector<int32_t> *group = nullptr;   // constrained form: group of each vertex
-    int32_t next_group = 0;
+    bool constrained;    // leaves keep their vertex order (groups only)
+    int par_depth;       // subtrees above this depth run on threads of their own
 
-    void by_mindeg(const std::vector<int32_t> &verts)
+    void leaf_block(std::vector<int32_t> &&verts, std::vector<int32_t> &local, std::vector<Block> &out) const
     {
-        if (group) {
-            for (int32_t v : verts) (*group)[v] = next_group;
-            next_group++;
-            return;
+        Block blk;
+        if (constrained || verts.size() <= 2) {
+            blk.verts = std::move(verts);
+        } else {
+            Graph s = induced(g, verts, local);
+            std::vector<int32_t> Ap(s.ptr.begin(), s.ptr.end()), perm(s.n);
+            gblu::mindeg_order(s.n, Ap.data(), s.adj.data(), perm.data());
+            blk.verts.resize(s.n);
+            for (int32_t i = 0; i < s.n; i++) blk.verts[i] = verts[perm[i]];
         }
-        if (verts.size() <= 2) {
-            out.insert(out.end(), verts.begin(), verts.end());
-            return;
-        }
-        Graph s = induced(g, verts, local);
-        std::vector<int32_t> Ap(s.ptr.begin(), s.ptr.end()), perm(s.n);
-        gblu::mindeg_order(s.n, Ap.data(), s.adj.data(), perm.data());
-        for (int32_t i = 0; i < s.n; i++) out.push_back(verts[perm[i]]);
+        out.push_back(std::move(blk));
     }
 
     // vertex separator of a bisection: side[v] = 0 / 1, or 2 for the separator
@@ -345,17 +363,24 @@ struct Ordering {
         return side;
     }
 
-    void rec(std::vector<int32_t> verts, int depth)
+    // blocks of `verts` in elimination order: the two halves' blocks, then
+    // the separator.  local: scratch of n entries, all -1, owned by the
+    // calling thread.
+    void rec(std::vector<int32_t> verts, int depth, uint64_t seed, std::vector<int32_t> &local,
+             std::vector<Block> &out) const
     {
         if ((int32_t)verts.size() <= leaf || depth > 60) {
-            by_mindeg(verts);
+            leaf_block(std::move(verts), local, out);
             return;
         }
         Graph s = induced(g, verts, local);
-        // a few multilevel trials; keep the smallest separator
+        std::mt19937 rng{(uint32_t)(seed ^ (seed >> 32))};
+        // a few multilevel trials (more near the root, whose separators
+        // become the largest dense blocks); keep the smallest separator
         std::vector<uint8_t> side;
         int64_t best = -1;
-        for (int t = 0; t < 3; t++) {
+        const int trials = depth < kTopDepth ? kTopTrials : 3;
+        for (int t = 0; t < trials; t++) {
             std::vector<uint8_t> sd = separate(s, bisect(s, rng));
             int64_t ns = 0, n0 = 0, n1 = 0;
             for (uint8_t x : sd) (x == 2 ? ns : x == 0 ? n0 : n1)++;
@@ -366,23 +391,33 @@ struct Ordering {
             }
         }
         if (best < 0) {
-            by_mindeg(verts);
+            leaf_block(std::move(verts), local, out);
             return;
         }
         std::vector<int32_t> a, b, sep;
         for (int32_t v = 0; v < s.n; v++) (side[v] == 2 ? sep : side[v] == 0 ? a : b).push_back(verts[v]);
         if (a.empty() || b.empty() || sep.size() * 3 > verts.size()) {   // no useful split
-            by_mindeg(verts);
+            leaf_block(std::move(verts), local, out);
             return;
         }
-        rec(std::move(a), depth + 1);
-        rec(std::move(b), depth + 1);
-        if (group) {
-            for (int32_t v : sep) (*group)[v] = next_group;
-            next_group++;
+        std::vector<int32_t>().swap(verts);
+        if (depth < par_depth) {
+            // the first half on a thread of its own, with its own scratch
+            std::vector<Block> out_a;
+            std::thread ta([&]() {
+                std::vector<int32_t> local_a(g.n, -1);
+                rec(std::move(a), depth + 1, child_seed(seed, 0), local_a, out_a);
+            });
+            std::vector<Block> out_b;
+            rec(std::move(b), depth + 1, child_seed(seed, 1), local, out_b);
+            ta.join();
+            for (Block &x : out_a) out.push_back(std::move(x));
+            for (Block &x : out_b) out.push_back(std::move(x));
         } else {
-            out.insert(out.end(), sep.begin(), sep.end());
+            rec(std::move(a), depth + 1, child_seed(seed, 0), local, out);
+            rec(std::move(b), depth + 1, child_seed(seed, 1), local, out);
         }
+        out.push_back(Block{std::move(sep)});
     }
 };
 
@@ -412,22 +447,25 @@ void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, in
     }
     g.ew.assign(g.adj.size(), 1);
     g.vw.assign(n, 1);
-    std::vector<int32_t> out;
-    out.reserve(n);
-    Ordering o{g, out, std::vector<int32_t>(n, -1), std::mt19937{20241121u}, leaf};
-    std::vector<int32_t> grp;
-    if (constrained) {
-        grp.assign(n, 0);
-        o.group = &grp;
-    }
-    std::vector<int32_t> all(n);
+    // up to 2^kParDepth subtrees on threads of their own
+    constexpr int kParDepth = 4;
+    const Ordering o{g, leaf, constrained, kParDepth};
+    std::vector<int32_t> all(n), local(n, -1);
     std::iota(all.begin(), all.end(), 0);
-    o.rec(std::move(all), 0);
+    std::vector<Block> blocks;
+    o.rec(std::move(all), 0, 20241121u, local, blocks);
     if (constrained) {
+        // groups in block order: each leaf set, then each separator after
+        // its two halves
+        std::vector<int32_t> grp(n, 0);
+        for (size_t b = 0; b < blocks.size(); b++)
+            for (int32_t v : blocks[b].verts) grp[v] = (int32_t)b;
         mindeg_order(n, Ap, Ai, perm, grp.data());
         return;
     }
-    std::copy(out.begin(), out.end(), perm);
+    int32_t k = 0;
+    for (const Block &b : blocks)
+        for (int32_t v : b.verts) perm[k++] = v;
 }
 
 // Section III-A runs several orderings and keeps the best.  Candidates here:

@@ -271,7 +271,7 @@ def test_constrained_minimum_degree():
 def test_constrained_nested_dissection_and_automatic_choice():
     """gblu_order_cnd orders a mesh with no more flops than plain nested
     dissection on it (the measured gain of Section III-A's constrained pass:
-    0.56 against 0.58 GFLOP on this 60x60x4 mesh); gblu_order_auto returns
+    0.550 against 0.565 GFLOP on this 60x60x4 mesh); gblu_order_auto returns
     the candidate of fewest flops and says which."""
     ckt = inputs.workload_mesh(nx=60, ny=60)
     n, Ap, Ai, _ = ckt.csc()
