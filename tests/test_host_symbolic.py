@@ -313,3 +313,22 @@ def test_minimum_deficiency_order():
     Ai2 = np.concatenate(rows).astype(np.int32)
     q = gblu.order_amf(m, Ap2, Ai2)
     assert gblu.symmetric_fill(m, Ap2, Ai2, q) == m - 1
+
+
+def test_every_order_is_a_permutation_on_random_patterns():
+    """All ordering entry points on random patterns from 1 to 400 unknowns,
+    unsymmetric, with empty rows and columns off the diagonal: each returns a
+    permutation, and the automatic choice is the cheapest candidate."""
+    rng = np.random.default_rng(31)
+    fns = {"mindeg": gblu.order_mindeg, "amf": gblu.order_amf, "nd": gblu.order_nd, "cnd": gblu.order_cnd}
+    for trial in range(40):
+        n = int(rng.integers(1, 400))
+        _, Ap, Ai, _ = inputs.random_sparse(n, rng.uniform(0.0, 0.05), rng)
+        costs = {}
+        for name, fn in fns.items():
+            q = fn(n, Ap, Ai)
+            assert sorted(q.tolist()) == list(range(n)), name
+            costs[name] = gblu.symmetric_cost(n, Ap, Ai, q)[1]
+        q, method = gblu.order_auto(n, Ap, Ai)
+        assert sorted(q.tolist()) == list(range(n))
+        assert costs[method] == min(costs.values())
