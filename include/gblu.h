@@ -225,6 +225,17 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
 int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream);
 
 /*
+ * Status of the handle's last device work, after synchronizing `stream`
+ * (the device status word of Section IV's pivot check and waits, latched
+ * in the handle's control block until the next call resets it): the error
+ * the device recorded (GBLU_ERR_DEVICE_TIMEOUT, GBLU_ERR_SINGULAR, ...), or
+ * else GBLU_REPIVOTED when the last gblu_refactorize / gblu_step restarted
+ * with pivoting, else GBLU_OK.  The numeric calls already return these
+ * codes; this reads them again without new work.
+ */
+int gblu_last_status(gblu_handle h, void *stream);
+
+/*
  * Batch of value sets on the installed structure (many same-pattern systems,
  * e.g. the Newton iterations of independent simulations of one circuit): the
  * checked re-factorization of Algorithms 3 and 4 for every set, in one

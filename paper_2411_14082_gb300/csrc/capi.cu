@@ -86,6 +86,7 @@ struct gblu_ctx {
     int32_t force_col = -1;                        // forced check failure of the next refactorization
     double t_tail[4] = {0, 0, 0, 0};               // last tail run: kernel, repack, schedule, upload (ms)
     int32_t tail_passes = 0;                       // kernel passes of the last tail run
+    bool last_repivot = false;                     // the last refactorization restarted
     bool analyzed = false, factorized = false;
     Pattern P;
     Structure S;
@@ -932,6 +933,7 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
 {
     NvtxRange nvtx_range("gblu_factorize");
     CK(check_handle(h));
+    h->last_repivot = false;
     if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -978,6 +980,15 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     return GBLU_OK;
 }
 
+int gblu_last_status(gblu_handle h, void *stream)
+{
+    CK(check_handle(h));
+    DeviceGuard g(h->device);
+    CK(read_ctl(h, (cudaStream_t)stream));
+    if (h->hctl->status != 0) return status_code(h);
+    return h->last_repivot ? GBLU_REPIVOTED : GBLU_OK;
+}
+
 int gblu_refactorize_forced(gblu_handle h, const double *Ax_dev, void *stream, int32_t force_col,
                             int32_t *repivoted)
 {
@@ -995,6 +1006,7 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
 {
     NvtxRange nvtx_range("gblu_refactorize");
     CK(check_handle(h));
+    h->last_repivot = false;
     if (repivoted) *repivoted = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
     if (!Ax_dev) return fail(GBLU_ERR_INVALID_INPUT, "null Ax_dev");
@@ -1015,6 +1027,7 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
         return rc;
     }
     if (repivoted) *repivoted = 1;
+    h->last_repivot = true;
     return GBLU_REPIVOTED;
 }
 
@@ -1462,6 +1475,7 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
 {
     NvtxRange nvtx_range("gblu_step");
     CK(check_handle(h));
+    h->last_repivot = false;
     if (repivoted) *repivoted = 0;
     if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
     if (!Ax_dev || !b_dev || !x_dev) return fail(GBLU_ERR_INVALID_INPUT, "null vector");
@@ -1496,6 +1510,7 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
     }
     CK(solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, st));
     if (repivoted) *repivoted = 1;
+    h->last_repivot = true;
     return GBLU_REPIVOTED;
 }
 

@@ -42,7 +42,7 @@ EXPORTED = [
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
     "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale", "gblu_order_nd",
     "gblu_symmetric_fill", "gblu_order_cnd", "gblu_symmetric_cost", "gblu_order_cmd", "gblu_order_auto",
-    "gblu_order_amf",
+    "gblu_order_amf", "gblu_last_status",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -146,6 +146,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_order_cnd.restype = ctypes.c_int
         lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
         lib.gblu_symmetric_cost.restype = ctypes.c_int
+        lib.gblu_last_status.argtypes = [P, P]
+        lib.gblu_last_status.restype = ctypes.c_int
         lib.gblu_order_amf.argtypes = [I32, P, P, P]
         lib.gblu_order_amf.restype = ctypes.c_int
         lib.gblu_order_cmd.argtypes = [I32, P, P, P, P]
@@ -424,6 +426,11 @@ class Solver:
                                     _dev_ptr(x, self.device, self.n),
                                     _dev_ptr(out, self.device, 4), _stream(stream)))
         return out
+
+    def last_status(self, stream=None) -> int:
+        """gblu_last_status: the code of the handle's last device work (OK,
+        REPIVOTED or a negative device error), returned, not raised."""
+        return int(load().gblu_last_status(self._h, _stream(stream)))
 
     def stats(self) -> dict:
         s = Stats()

@@ -35,6 +35,7 @@ def test_forced_repivot_matches_oracle(case):
         lu = O.refactorize(lu, Ap, Ai, Ax)
         rc, rep = s.refactorize_forced(dev(Ax), force)
         assert rep and rc == gblu.REPIVOTED
+        assert s.last_status() == gblu.REPIVOTED
         st = s.stats()
         assert st["n_restart_cols"] >= 1 and st["tail_kernel_ms"] > 0
         compare_factors(s.export_factors(), lu, 1e-10)
@@ -44,5 +45,6 @@ def test_forced_repivot_matches_oracle(case):
     # no forcing: an ordinary checked refactorization again
     rc, rep = s.refactorize_forced(dev(Ax), -1)
     assert not rep and rc == gblu.OK
+    assert s.last_status() == gblu.OK
     with pytest.raises(gblu.GbluError):
         s.refactorize_forced(dev(Ax), n)
