@@ -472,9 +472,9 @@ void nd_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm, in
 // minimum degree and approximate minimum deficiency (up to kAutoMindegMax
 // unknowns; beyond that they are slow and, on meshes, poor), nested
 // dissection, and incomplete nested dissection with constrained minimum
-// degree (up to kAutoCndMax unknowns: its minimum-degree pass over the large
-// separators costs about 4.5x the dissection at 360,000 unknowns for a
-// 0.3% gain), each on a host thread of its own.  The one
+// degree (up to kAutoCndMax unknowns: its minimum-degree pass over the
+// whole graph costs about 2.2x the dissection at 360,000 unknowns for a
+// 0.25% gain), each on a host thread of its own.  The one
 // whose factorization costs the fewest flops when every diagonal pivot is
 // kept (F = sum_j 2 c_j^2 of the symmetric pattern, the re-factorization's
 // work) wins; ties go to the earlier candidate.

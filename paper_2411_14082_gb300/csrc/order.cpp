@@ -23,7 +23,8 @@
 // (the pairs of that clique exist already); the approximate mean local fill
 // score of Rothberg and Eisenstat.
 #include <algorithm>
-#include <set>
+#include <functional>
+#include <queue>
 #include <vector>
 
 #include "gblu_internal.h"
@@ -57,15 +58,21 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
         c = std::min(c, d);
         return std::min(kScoreMax, (d * (d - 1) - c * (c - 1)) / 2);
     };
-    std::set<std::pair<int64_t, int32_t>> pq;
+    // min-heap of (key, variable) with lazy deletion: an update pushes a new
+    // entry, and a popped entry counts only if it still holds the variable's
+    // key; the first valid entry is the least (key, index) pair, as in an
+    // ordered set.  Rebuilt from the live variables when stale entries pile up.
+    using Entry = std::pair<int64_t, int32_t>;
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
     for (int32_t i = 0; i < n; i++) {
         score[i] = score_of((int64_t)A[i].size(), 0);
-        pq.insert({key(i), i});
+        pq.push({key(i), i});
     }
     std::vector<int32_t> Lp;
     for (int32_t k = 0; k < n; k++) {
-        const int32_t p = pq.begin()->second;
-        pq.erase(pq.begin());
+        while (elim[pq.top().second] || pq.top().first != key(pq.top().second)) pq.pop();
+        const int32_t p = pq.top().second;
+        pq.pop();
         perm[k] = p;
         elim[p] = 1;
         // ---- element p: Lp = variables adjacent to p directly or via elements
@@ -118,9 +125,19 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
             int64_t d = (int64_t)Ai_.size() + (int64_t)Lp.size() - 1 + ext;
             if (d > remaining - 1) d = remaining - 1;
             if (d < 0) d = 0;
-            pq.erase({key(i), i});
-            score[i] = score_of(d, clique);
-            pq.insert({key(i), i});
+            const int64_t s = score_of(d, clique);
+            if (s != score[i]) {
+                score[i] = s;
+                pq.push({key(i), i});
+            }
+        }
+        if (pq.size() > (size_t)4 * (size_t)(n - k) + 1024) {
+            std::vector<Entry> live;
+            live.reserve(n - k);
+            for (int32_t v = 0; v < n; v++)
+                if (!elim[v]) live.push_back({key(v), v});
+            pq = std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>>(std::greater<Entry>(),
+                                                                                     std::move(live));
         }
     }
 }
