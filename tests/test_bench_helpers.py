@@ -33,9 +33,14 @@ def test_traffic_matches_the_committed_refactor_kernel(bench):
 
 
 def test_hbm_roofline_uses_the_measured_peak(bench):
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    """The measured copy bandwidth when the peaks file is there, else the
+    stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, src = bench.hbm_peak_gbs()
-    assert src == "measured" and peak == peaks["hbm_gbs"]
+    if os.path.exists(path):
+        assert src == "measured" and peak == json.load(open(path))["hbm_gbs"]
+    else:
+        assert src == "fallback" and peak == 6800.0
     r = bench.hbm_roofline(2.0e9, 0.5, traffic=4.0e9)
     assert r["algorithmic_gbs"] == pytest.approx(4.0)
     assert r["frac"] == pytest.approx(4.0 / peak)
