@@ -332,3 +332,23 @@ def test_every_order_is_a_permutation_on_random_patterns():
         q, method = gblu.order_auto(n, Ap, Ai)
         assert sorted(q.tolist()) == list(range(n))
         assert costs[method] == min(costs.values())
+
+
+def test_orders_of_degenerate_patterns():
+    """One unknown, a diagonal matrix, a matrix with an empty column and a
+    dense block: every order is a permutation and the estimate is exact."""
+    cases = [(1, np.array([0, 1]), np.array([0])),
+             (5, np.arange(6), np.arange(5)),
+             (4, np.array([0, 2, 2, 4, 5]), np.array([0, 3, 1, 2, 3]))]
+    m = 12
+    _, Ap, Ai, _ = inputs.dense_to_csc(np.ones((m, m)))
+    cases.append((m, Ap, Ai))
+    for n, Ap, Ai in cases:
+        for fn in (gblu.order_mindeg, gblu.order_amf, gblu.order_nd, gblu.order_cnd,
+                   lambda n, Ap, Ai: gblu.order_auto(n, Ap, Ai)[0]):
+            q = fn(n, np.asarray(Ap), np.asarray(Ai))
+            assert sorted(q.tolist()) == list(range(n))
+            assert gblu.symmetric_cost(n, Ap, Ai, q) == brute_cost(n, np.asarray(Ap), np.asarray(Ai), q)
+    # a dense block fills completely whatever the order
+    fill, flops = gblu.symmetric_cost(m, Ap, Ai, np.arange(m))
+    assert fill == m * (m - 1) // 2 and flops == sum(2 * c * c for c in range(m))
