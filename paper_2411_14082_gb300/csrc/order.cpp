@@ -49,10 +49,10 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
     std::vector<char> elim(n, 0), alive(n, 0);
     std::vector<int32_t> mark(n, -1), wmark(n, -1);
     std::vector<int64_t> w(n, 0), score(n);
-    // key: group (bits 40 and up), then the score (degree, or estimated
-    // fill); ties by index
-    constexpr int64_t kScoreMax = (int64_t(1) << 40) - 1;
-    auto key = [&](int32_t i) { return ((int64_t)(group ? group[i] : 0) << 40) | score[i]; };
+    // key: group, then the score (degree, or estimated fill); ties by index
+    constexpr int64_t kScoreMax = INT64_MAX / 4;
+    using Key = std::pair<int32_t, int64_t>;
+    auto key = [&](int32_t i) { return Key{group ? group[i] : 0, score[i]}; };
     auto score_of = [&](int64_t d, int64_t c) -> int64_t {
         if (!deficiency) return d;
         c = std::min(c, d);
@@ -62,7 +62,7 @@ void mindeg_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm
     // entry, and a popped entry counts only if it still holds the variable's
     // key; the first valid entry is the least (key, index) pair, as in an
     // ordered set.  Rebuilt from the live variables when stale entries pile up.
-    using Entry = std::pair<int64_t, int32_t>;
+    using Entry = std::pair<Key, int32_t>;
     std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
     for (int32_t i = 0; i < n; i++) {
         score[i] = score_of((int64_t)A[i].size(), 0);
