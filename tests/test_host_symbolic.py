@@ -352,3 +352,30 @@ def test_orders_of_degenerate_patterns():
     # a dense block fills completely whatever the order
     fill, flops = gblu.symmetric_cost(m, Ap, Ai, np.arange(m))
     assert fill == m * (m - 1) // 2 and flops == sum(2 * c * c for c in range(m))
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/gblu.h is a C ABI: a C99 program that includes it compiles
+    without warnings, links against the library and calls a host entry
+    point."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = gblu.load()
+    libdir = os.path.dirname(lib._name)
+    src = tmp_path / "use_gblu.c"
+    src.write_text('#include "gblu.h"\n'
+                   "int main(void) {\n"
+                   "    gblu_opts o;\n"
+                   "    int32_t Ap[3] = {0, 2, 3}, Ai[3] = {0, 1, 1}, perm[2];\n"
+                   "    gblu_default_opts(&o);\n"
+                   "    if (o.pivot_tol != 1e-3) return 1;\n"
+                   "    return gblu_order_mindeg(2, Ap, Ai, perm) == GBLU_OK ? 0 : 2;\n"
+                   "}\n")
+    exe = tmp_path / "use_gblu"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lgblu",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    assert subprocess.run([str(exe)]).returncode == 0
