@@ -379,3 +379,11 @@ def test_header_is_plain_c_and_links(tmp_path):
                     "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lgblu",
                     f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built library the binding raises."""
+    monkeypatch.setattr(gblu, "_lib", None)
+    monkeypatch.setattr(gblu._build, "LIB", os.path.join(ROOT, "no_such_dir", "libgblu.so"))
+    with pytest.raises(OSError):
+        gblu.load(build_if_missing=False)
