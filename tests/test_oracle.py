@@ -182,7 +182,7 @@ def test_tiny_structure_matches_dense_fill():
 @pytest.mark.parametrize("eps", [1e-3, 0.5])
 def test_reconstruction_and_threshold_rule(eps):
     rng = np.random.default_rng(3)
-    for trial in range(400):
+    for trial in range(10000):
         n = int(rng.integers(1, 9))
         _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.2, 0.9), rng, zero_diag_frac=0.25)
         Q = rng.permutation(n).astype(np.int32)
