@@ -287,3 +287,29 @@ def test_small_mna_workload_residual_and_refactor_sequence():
         b = inputs.rhs(n, rng)
         assert O.residual(n, Ap, Ai, Ax, O.solve(lu2, b), b) <= 1e-12
         lu = lu2
+
+
+def test_solution_matches_superlu_within_the_conditioning_bound():
+    """The oracle's solution of the C1 grid and of a small RC mesh against
+    SuperLU's (scipy.sparse.linalg.splu: its own ordering and pivoting, so
+    only x is compared).  Two solutions with residuals r1, r2 differ by at
+    most ||A^-1||_inf (||r1||_inf + ||r2||_inf); the bound uses a dense
+    inverse of A, and each computed residual is widened by the rounding of
+    its own evaluation (row length times unit roundoff times |A||x|)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    for ckt in (inputs.workload_small(), inputs.rc_mesh3d(12, 12, 4, seed=5, n_fet=30)):
+        n, Ap, Ai, Ax = ckt.csc()
+        A = sp.csc_matrix((Ax, Ai, Ap), shape=(n, n))
+        lu = O.factorize(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt), 1e-3)
+        assert lu.status == O.OK
+        b = inputs.rhs(n, np.random.default_rng(2))
+        x_o = O.solve(lu, b)
+        x_s = spla.splu(A).solve(b)
+        absA = abs(A)
+        row_len = np.diff(A.tocsr().indptr).max() + 1
+        r_o = np.abs(b - A @ x_o).max() + row_len * U_ROUND * (absA @ np.abs(x_o) + np.abs(b)).max()
+        r_s = np.abs(b - A @ x_s).max() + row_len * U_ROUND * (absA @ np.abs(x_s) + np.abs(b)).max()
+        inv_norm = np.abs(np.linalg.inv(A.toarray())).sum(axis=1).max()
+        assert np.abs(x_o - x_s).max() <= inv_norm * (r_o + r_s) * (1 + 1e-6)
+        assert O.residual(n, Ap, Ai, Ax, x_o, b) <= 1e-12
