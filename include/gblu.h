@@ -516,7 +516,12 @@ int gblu_export_factors(gblu_handle h, int64_t *Lp, int32_t *Li, double *Lx,
 
 /*
  * Host-only helpers (no device work), exposed so that the symbolic layer can
- * be checked on machines without a GPU.
+ * be checked on machines without a GPU.  Common to all of them: Ap, Ai (a
+ * CSC pattern, columns in any row order) and every other argument are host
+ * arrays owned by the caller, read or written only during the call; perm
+ * and other outputs have n entries.  An invalid pattern (n < 1, Ap[0] != 0,
+ * Ap decreasing, a row index outside [0, n), a duplicate entry in a column)
+ * or a null output gives GBLU_ERR_INVALID_INPUT and writes nothing.
  */
 /* Minimum-degree column order of the pattern of A + A^T: perm[k] = column
  * eliminated at step k. */
