@@ -473,3 +473,27 @@ def test_structure_adaptive_solve(slices):
     assert s.stats()["solve_p0_l"] == (p0 if p0 < n and suffix[p0] >= 100 else n)
     x = s.solve(dev(b)).cpu().numpy()
     np.testing.assert_allclose(x, x_ref, rtol=1e-9, atol=1e-12 * np.abs(x_ref).max())
+
+
+def test_library_ordering_on_meshes():
+    """gblu_analyze without Q on meshes (its automatic choice among minimum
+    degree, minimum deficiency and the two dissections): the factors of the
+    first factorization and of a re-factorization equal the oracle's on the
+    order the library chose."""
+    for ckt in (inputs.rc_mesh3d(16, 16, 4, seed=9, n_fet=40), inputs.rc_mesh3d(30, 30, 4, seed=10, n_fet=60)):
+        n, Ap, Ai, Ax = ckt.csc()
+        s = gblu.Solver(DEV)
+        s.analyze(n, Ap, Ai, None)
+        Axd = dev(Ax)
+        s.factorize(Axd)
+        f = s.export_factors()
+        assert np.array_equal(f["q"], gblu.order_auto(n, Ap, Ai)[0])
+        lu = O.factorize(n, Ap, Ai, Ax, f["q"], 1e-3)
+        compare_factors(f, lu, RTOL)
+        Ax2 = inputs.redraw_transistors(ckt, np.random.default_rng(4)).values()
+        lu2 = O.refactorize(lu, Ap, Ai, Ax2)
+        Axd2 = dev(Ax2)
+        rc, rep = s.refactorize(Axd2)
+        assert rep == (lu2.n_rejected > 0)
+        compare_factors(s.export_factors(), lu2, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax2, Axd2, np.random.default_rng(0))
