@@ -556,9 +556,9 @@ int gblu_order_cnd(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *per
 #define GBLU_ORDER_CND 2      /* gblu_order_cnd    */
 #define GBLU_ORDER_AMF 3      /* gblu_order_amf    */
 /* Section III-A's selection: several orders are computed on host threads
- * (minimum degree and approximate minimum deficiency up to n = 50000,
- * nested dissection, and nested dissection with constrained minimum
- * degree up to n = 200000), and the one whose factorization costs
+ * (minimum degree, approximate minimum deficiency and nested dissection
+ * with constrained minimum degree up to n = 200000, nested dissection at
+ * every size), and the one whose factorization costs
  * the fewest flops when every diagonal pivot is kept (gblu_symmetric_cost)
  * is written to perm; ties go to that list's order.  *method (optional)
  * receives its GBLU_ORDER_* code.  gblu_analyze uses it when Q is NULL. */
