@@ -572,6 +572,21 @@ int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, con
  * for an invalid pattern or a Q that is not a permutation. */
 int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q, int64_t *fill,
                         double *flops);
+/* The structure-adaptive split of one triangular factor (Section V-A), as
+ * the solve setup computes it.  count_from[p] (n+1 entries, count_from[n]
+ * = 0): strict entries of the trailing block [p, n); rowlen[i] (n): all
+ * entries of row i.  density == 0 is the paper's rule: P0 = the largest p
+ * whose trailing block holds at least frac of all entries and at least
+ * min_entries.  density > 0: P0 = the start of the longest trailing block
+ * whose entry density count_from[p] / ((n-p)(n-p-1)/2) stays at least
+ * density, kept if it holds min_entries entries.  Rows [P0, n) are cut
+ * into `slices` pieces of about equal entry counts, each at most max_piece
+ * rows: cut receives P0, the inner cut rows and n (*ncut entries; room for
+ * n+1 is enough).  Returns P0, n when no block qualifies (then *ncut = 0),
+ * or GBLU_ERR_INVALID_INPUT. */
+int32_t gblu_solve_partition(int32_t n, const int64_t *count_from, const int64_t *rowlen, double density,
+                             double frac, long long min_entries, int slices, int max_piece, int32_t *cut,
+                             int32_t *ncut);
 /* Column elimination tree of A(:,Q) (elimination tree of (A Q)^T (A Q)),
  * parent[k] = parent step of step k or -1 (Section II-B "ETree"). */
 int gblu_column_etree(int32_t n, const int32_t *Ap, const int32_t *Ai,

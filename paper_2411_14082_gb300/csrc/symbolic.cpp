@@ -664,6 +664,27 @@ extern "C" int gblu_order_mindeg(int32_t n, const int32_t *Ap, const int32_t *Ai
     return GBLU_OK;
 }
 
+extern "C" int32_t gblu_solve_partition(int32_t n, const int64_t *count_from, const int64_t *rowlen,
+                                        double density, double frac, long long min_entries, int slices,
+                                        int max_piece, int32_t *cut, int32_t *ncut)
+{
+    if (n < 1 || !count_from || !rowlen || !cut || !ncut || slices < 0 || max_piece < 1 || frac < 0.0 ||
+        density < 0.0)
+        return record_error(GBLU_ERR_INVALID_INPUT, "solve partition: invalid arguments");
+    SolveSplit sp;
+    sp.density = density;
+    sp.frac = frac;
+    sp.min_entries = min_entries;
+    sp.slices = slices;
+    sp.max_piece = max_piece;
+    std::vector<int64_t> cf(count_from, count_from + n + 1), rl(rowlen, rowlen + n);
+    std::vector<int32_t> c;
+    const int32_t p0 = dense_split(n, cf, rl, sp, c);
+    std::copy(c.begin(), c.end(), cut);
+    *ncut = (int32_t)c.size();
+    return p0;
+}
+
 extern "C" int gblu_order_amf(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm)
 {
     std::string err;

@@ -42,7 +42,7 @@ EXPORTED = [
     "gblu_refactorize_multi", "gblu_solve_multi", "gblu_step", "gblu_get_opts", "gblu_set_opts",
     "gblu_autotune", "gblu_static_pivot", "gblu_permute_rows", "gblu_gather_scale", "gblu_order_nd",
     "gblu_symmetric_fill", "gblu_order_cnd", "gblu_symmetric_cost", "gblu_order_cmd", "gblu_order_auto",
-    "gblu_order_amf", "gblu_last_status",
+    "gblu_order_amf", "gblu_last_status", "gblu_solve_partition",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
 ]
@@ -146,6 +146,9 @@ def load(build_if_missing: bool = True):
         lib.gblu_order_cnd.restype = ctypes.c_int
         lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
         lib.gblu_symmetric_cost.restype = ctypes.c_int
+        lib.gblu_solve_partition.argtypes = [I32, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+                                             ctypes.c_int, ctypes.c_int, P, P]
+        lib.gblu_solve_partition.restype = I32
         lib.gblu_last_status.argtypes = [P, P]
         lib.gblu_last_status.restype = ctypes.c_int
         lib.gblu_order_amf.argtypes = [I32, P, P, P]
@@ -490,6 +493,20 @@ def order_cnd(n, Ap, Ai):
     perm = np.empty(n, np.int32)
     _check(load().gblu_order_cnd(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(perm)))
     return perm
+
+
+def solve_partition(count_from, rowlen, density=0.0, frac=0.7, min_entries=300000, slices=8, max_piece=4096):
+    """Section V-A's split of one triangle (gblu_solve_partition, host): (P0, cut rows)."""
+    count_from = np.ascontiguousarray(count_from, dtype=np.int64)
+    rowlen = np.ascontiguousarray(rowlen, dtype=np.int64)
+    n = len(rowlen)
+    cut = np.empty(n + 1, np.int32)
+    ncut = ctypes.c_int32()
+    p0 = load().gblu_solve_partition(int(n), _np_ptr(count_from), _np_ptr(rowlen), float(density), float(frac),
+                                     int(min_entries), int(slices), int(max_piece), _np_ptr(cut),
+                                     ctypes.byref(ncut))
+    _check(min(p0, 0))
+    return int(p0), cut[:ncut.value].copy()
 
 
 def order_amf(n, Ap, Ai):

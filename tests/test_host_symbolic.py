@@ -387,3 +387,58 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(gblu._build, "LIB", os.path.join(ROOT, "no_such_dir", "libgblu.so"))
     with pytest.raises(OSError):
         gblu.load(build_if_missing=False)
+
+
+def test_solve_partition_rule():
+    """Section V-A's split of a triangle, on synthetic count profiles.
+
+    Paper rule: P0 is the largest p whose trailing block [p, n) holds at
+    least 70% of the entries and at least min_entries; density rule: the
+    longest trailing block whose density stays at least the threshold.
+    Slices: P0 and n included, consecutive, at most max_piece rows, each
+    (but the last) closed at the first row where its entries reach an equal
+    share of the block's."""
+    rng = np.random.default_rng(12)
+    for trial in range(200):
+        n = int(rng.integers(2, 400))
+        # per-column strict counts growing toward the end (a dense-ish tail)
+        strict = np.minimum(np.arange(n)[::-1], rng.integers(0, 4, n) + (np.arange(n) > n * rng.uniform(0.3, 0.9)) * n)
+        strict = np.minimum(strict, n - 1 - np.arange(n))
+        count_from = np.concatenate([np.cumsum(strict[::-1])[::-1], [0]]).astype(np.int64)
+        rowlen = (rng.integers(0, 5, n) + strict).astype(np.int64)
+        total = count_from[0]
+        min_entries = int(rng.integers(0, max(1, total)))
+        slices = int(rng.integers(1, 9))
+        max_piece = int(rng.integers(1, 60))
+        # paper's rule
+        p0, cut = gblu.solve_partition(count_from, rowlen, 0.0, 0.7, min_entries, slices, max_piece)
+        want = n
+        if total > 0:
+            for p in range(n - 1, -1, -1):
+                if count_from[p] >= 0.7 * total and count_from[p] >= min_entries:
+                    want = p
+                    break
+        assert p0 == want
+        if p0 < n:
+            assert cut[0] == p0 and cut[-1] == n and np.all(np.diff(cut) > 0)
+            assert np.all(np.diff(cut) <= max_piece)
+            per = rowlen[p0:].sum() / slices
+            for a, b in zip(cut[:-2], cut[1:-1]):
+                acc = np.cumsum(rowlen[a:b])
+                # closed at the first row reaching the share, or at max_piece rows
+                assert acc[-1] >= per or b - a == max_piece
+                assert len(acc) == 1 or acc[-2] < per
+        else:
+            assert len(cut) == 0
+        # density rule
+        d = float(rng.uniform(0.3, 1.0))
+        p0, _ = gblu.solve_partition(count_from, rowlen, d, 0.7, min_entries, slices, max_piece)
+        want = n
+        for p in range(n - 2, -1, -1):
+            m = n - p
+            if count_from[p] < d * m * (m - 1) / 2:
+                break
+            want = p
+        if want < n and count_from[want] < min_entries:
+            want = n
+        assert p0 == want
