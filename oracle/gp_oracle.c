@@ -376,10 +376,19 @@ int orc_solve(const orc_lu *lu, const double *b, double *x)
     return ORC_OK;
 }
 
+/* the IEEE maximum: NaN if either argument is NaN */
+static double max_nan(double m, double v)
+{
+    if (isnan(m) || isnan(v)) return NAN;
+    return v > m ? v : m;
+}
+
 /*
  * Relative residual ||b - A x||_inf / (||A||_inf * ||x||_inf) of a CSC
  * matrix; out[0] = the ratio, out[1] = ||b - A x||_inf, out[2] = ||A||_inf,
- * out[3] = ||x||_inf.
+ * out[3] = ||x||_inf.  A NaN in r, in a row sum of |A| or in x makes that
+ * norm, and the ratio, NaN (the maximum of a set holding a NaN is NaN), so a
+ * solution with a NaN entry never passes a residual bound.
  */
 int orc_residual(int n, const int *Ap, const int *Ai, const double *Ax,
                  const double *x, const double *b, double *out)
@@ -396,9 +405,9 @@ int orc_residual(int n, const int *Ap, const int *Ai, const double *Ax,
     }
     double rn = 0, an = 0, xn = 0;
     for (int i = 0; i < n; i++) {
-        if (fabs(r[i]) > rn) rn = fabs(r[i]);
-        if (rs[i] > an) an = rs[i];
-        if (fabs(x[i]) > xn) xn = fabs(x[i]);
+        rn = max_nan(rn, fabs(r[i]));
+        an = max_nan(an, rs[i]);
+        xn = max_nan(xn, fabs(x[i]));
     }
     out[0] = (an > 0 && xn > 0) ? rn / (an * xn) : rn;
     out[1] = rn;

@@ -12,7 +12,8 @@ Functions (all arrays numpy, CSC int32 / float64):
   sequence preferred (the result that re-factorization with pivot check and
   restart, Section IV, must produce).
 * ``solve(lu, b)`` -- forward and back substitution (Algorithm 2).
-* ``residual(n, Ap, Ai, Ax, x, b)`` -- ||b-Ax||_inf / (||A||_inf ||x||_inf).
+* ``residual(n, Ap, Ai, Ax, x, b)`` -- ||b-Ax||_inf / (||A||_inf ||x||_inf);
+  ``residual_parts`` gives the ratio and its three norms.
 """
 from __future__ import annotations
 
@@ -178,6 +179,12 @@ def solve(lu: OracleLU, b) -> np.ndarray:
 
 def residual(n, Ap, Ai, Ax, x, b, lib=None) -> float:
     """||b - A x||_inf / (||A||_inf ||x||_inf)."""
+    return float(residual_parts(n, Ap, Ai, Ax, x, b, lib)[0])
+
+
+def residual_parts(n, Ap, Ai, Ax, x, b, lib=None) -> np.ndarray:
+    """[ratio, ||b - A x||_inf, ||A||_inf, ||x||_inf] (ratio = ||r|| when
+    ||A|| or ||x|| is 0; every norm is NaN if an entry it takes is NaN)."""
     lib = lib or _load()
     out = np.zeros(4)
     Ap = np.ascontiguousarray(Ap, dtype=np.int32)
@@ -188,4 +195,4 @@ def residual(n, Ap, Ai, Ax, x, b, lib=None) -> float:
     rc = lib.orc_residual(int(n), _ptr(Ap), _ptr(Ai), _ptr(Ax), _ptr(x), _ptr(b), _ptr(out))
     if rc != OK:
         raise RuntimeError(f"oracle residual failed: {rc}")
-    return float(out[0])
+    return out

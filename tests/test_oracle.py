@@ -313,3 +313,57 @@ def test_solution_matches_superlu_within_the_conditioning_bound():
         inv_norm = np.abs(np.linalg.inv(A.toarray())).sum(axis=1).max()
         assert np.abs(x_o - x_s).max() <= inv_norm * (r_o + r_s) * (1 + 1e-6)
         assert O.residual(n, Ap, Ai, Ax, x_o, b) <= 1e-12
+
+
+# ---------------------------------------------------------------- residual
+def test_residual_parts_exact_on_small_integer_systems():
+    """||b - A x||_inf, ||A||_inf (largest row sum of |A|) and ||x||_inf of
+    small integer systems, computed exactly with rationals: every partial
+    sum is an integer below 2^53, so the oracle's float64 values must be
+    exact, and the ratio must be their correctly rounded quotient."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    for trial in range(200):
+        n = int(rng.integers(1, 12))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, 0.4, rng, zero_diag_frac=0.3, dominance=0.5)
+        Ax = rng.integers(-50, 51, len(Ax)).astype(np.float64)
+        x = rng.integers(-30, 31, n).astype(np.float64)
+        b = rng.integers(-99, 100, n).astype(np.float64)
+        r = [Fraction(int(v)) for v in b]
+        rs = [Fraction(0)] * n
+        for c in range(n):
+            for p in range(Ap[c], Ap[c + 1]):
+                r[Ai[p]] -= Fraction(int(Ax[p])) * int(x[c])
+                rs[Ai[p]] += abs(Fraction(int(Ax[p])))
+        rn = max(abs(v) for v in r)
+        an = max(rs)
+        xn = max(abs(int(v)) for v in x)
+        out = O.residual_parts(n, Ap, Ai, Ax, x, b)
+        assert out[1] == float(rn) and out[2] == float(an) and out[3] == float(xn)
+        want = float(rn / (an * xn)) if an > 0 and xn > 0 else float(rn)
+        assert out[0] == want
+
+
+def test_residual_special_cases():
+    """x = 0 gives ratio ||b||; A = 0 gives ratio ||b - 0||; the identity
+    with x = b gives 0; a NaN anywhere in x or A makes the ratio NaN (the
+    maximum of a set that holds a NaN is NaN), so it fails every bound."""
+    n = 5
+    Ap = np.arange(n + 1, dtype=np.int32)
+    Ai = np.arange(n, dtype=np.int32)
+    I = np.ones(n)
+    b = np.array([1.0, -3.0, 2.0, 0.5, -0.25])
+    out = O.residual_parts(n, Ap, Ai, I, np.zeros(n), b)
+    assert out[0] == 3.0 and out[1] == 3.0 and out[2] == 1.0 and out[3] == 0.0
+    out = O.residual_parts(n, Ap, Ai, np.zeros(n), b, b)
+    assert out[0] == 3.0 and out[2] == 0.0
+    assert O.residual_parts(n, Ap, Ai, I, b, b)[0] == 0.0
+    for pos in range(n):
+        x = b.copy()
+        x[pos] = np.nan
+        out = O.residual_parts(n, Ap, Ai, I, x, b)
+        assert np.isnan(out[0]) and np.isnan(out[1]) and np.isnan(out[3])
+        A = I.copy()
+        A[pos] = np.nan
+        out = O.residual_parts(n, Ap, Ai, A, b, b)
+        assert np.isnan(out[0]) and np.isnan(out[2])

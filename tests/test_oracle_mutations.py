@@ -3,7 +3,7 @@
 Each case plants one mistake in a copy of the oracle source (on the CPU,
 in a temporary directory), builds it, and requires that at least one pin
 (golden examples, brute-force dense elimination, LAPACK at eps = 1, solve
-against numpy) rejects the planted build.
+against numpy, exact residuals of integer systems) rejects the planted build.
 """
 import os
 import subprocess
@@ -30,6 +30,10 @@ MUTATIONS = {
     "solve_no_divide": ("double zk = y[k] / lu->Ux[dpos];", "double zk = y[k];"),
     "solve_no_perm_b": ("y[k] = b[lu->piv[k]];", "y[k] = b[k];"),
     "keep_zero_pivot": ("pref_cand && x[pref] != 0.0 && fabs", "pref_cand && fabs"),
+    "residual_sign": ("r[Ai[p]] -= Ax[p] * x[c];", "r[Ai[p]] += Ax[p] * x[c];"),
+    "residual_row_sum_no_abs": ("rs[Ai[p]] += fabs(Ax[p]);", "rs[Ai[p]] += Ax[p];"),
+    "residual_col_sum": ("rs[Ai[p]] += fabs(Ax[p]);", "rs[c] += fabs(Ax[p]);"),
+    "residual_nan_skipped": ("if (isnan(m) || isnan(v)) return NAN;", ""),
 }
 
 
@@ -68,6 +72,27 @@ def _pins_pass(lib):
         b = rng.uniform(-1, 1, n)
         if not np.allclose(O.solve(lu, b), np.linalg.solve(A, b), rtol=1e-8, atol=1e-10):
             return False
+    # residual: exact on small integer systems, NaN propagates
+    from fractions import Fraction
+    for trial in range(40):
+        n = int(rng.integers(1, 9))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, 0.5, rng, zero_diag_frac=0.3, dominance=0.5)
+        Ax = rng.integers(-9, 10, len(Ax)).astype(np.float64)
+        x = rng.integers(-9, 10, n).astype(np.float64)
+        b = rng.integers(-9, 10, n).astype(np.float64)
+        r = [Fraction(int(v)) for v in b]
+        rs = [Fraction(0)] * n
+        for c in range(n):
+            for p in range(Ap[c], Ap[c + 1]):
+                r[Ai[p]] -= int(Ax[p]) * int(x[c])
+                rs[Ai[p]] += abs(int(Ax[p]))
+        out = O.residual_parts(n, Ap, Ai, Ax, x, b, lib=lib)
+        if (out[1], out[2], out[3]) != (float(max(abs(v) for v in r)), float(max(rs)),
+                                        float(np.abs(x).max())):
+            return False
+    xn = np.array([1.0, np.nan, 2.0])
+    if not np.isnan(O.residual_parts(3, np.arange(4), np.arange(3), np.ones(3), xn, np.ones(3), lib=lib)[0]):
+        return False
     # brute force on tiny matrices, real and small-integer values (ties)
     for trial in range(300):
         n = int(rng.integers(1, 8))
