@@ -50,6 +50,7 @@ extern "C" {
 #define GBLU_ERR_NOT_FACTORIZED (-7) /* refactorize/solve before a factorization    */
 #define GBLU_ERR_INTERNAL (-8)       /* a structural invariant check failed         */
 #define GBLU_ERR_BUSY (-9)           /* a server request has not finished yet       */
+#define GBLU_ERR_NONFINITE (-10)     /* a NaN or infinite value reached a pivot column */
 
 /* Scheduling of the re-factorization (Section IV-B: cluster and pipeline modes). */
 #define GBLU_SCHED_AUTO 0     /* level-synchronous front, sync-free tail      */
@@ -173,7 +174,8 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
  * Ax_dev: device float64[nnz] in the slot order of the analyze call's Ai.
  * Builds the factors and, on the host, the fixed-pattern schedule for
  * refactorize and solve.  Synchronizes `stream`.
- * Returns GBLU_OK or GBLU_ERR_SINGULAR (factors then invalid).
+ * Returns GBLU_OK, GBLU_ERR_SINGULAR or GBLU_ERR_NONFINITE (a NaN or
+ * infinite value in a column; factors then invalid).
  */
 int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
 
@@ -186,7 +188,9 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
  * GBLU_REPIVOTED.  The result equals a factorization with pivoting that
  * prefers the previous pivot sequence.  Synchronizes `stream` once (to read
  * the 4-byte check status).  *repivoted (optional, host) is set to 1 if a
- * restart happened, else 0.
+ * restart happened, else 0.  A NaN or infinite value anywhere in a column
+ * fails its check; the restart then returns GBLU_ERR_NONFINITE instead of
+ * storing it in the factors.
  */
 int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream,
                      int32_t *repivoted);
@@ -348,8 +352,8 @@ int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host,
  * convenience.  It solves A x = b from factors the caller keeps in its own
  * device buffers, with sync-free row solves like gblu_solve's, and
  * allocates nothing: its scratch (intermediate vector, ready flags,
- * tickets) is one file-scope device array of 8 MB that every GPU loading
- * the library holds until the process exits.
+ * tickets) is one file-scope device array of 8 MB, held on a device from
+ * the time the library's module is loaded there until the process exits.
  *   Factors, row-wise (CSR) in step numbering, all device arrays:
  *   Lrp[n+1]/Lcol/Lval = strict lower part of L (unit diagonal implied),
  *   Urp[n+1]/Ucol/Uval = strict upper part of U, Udiag[n] = U(k,k),
@@ -357,19 +361,25 @@ int gblu_step_host(gblu_handle h, const double *Ax_host, const double *b_host,
  *   (gblu_export_factors gives the same factors column-wise).
  *   b_dev[n] -> x_dev[n] (must not alias); status_dev (optional device
  *   int32) receives 0 or GBLU_ERR_DEVICE_TIMEOUT when the solve finishes.
+ *   The return code only covers the launches: without status_dev a wait
+ *   that ran out (x_dev then partly written) cannot be seen.
+ *   spin_limit: polls of one ready flag before the wait gives up (<= 0:
+ *   2^24).
  * n must be <= GBLU_NOALLOC_MAX_N; larger n returns GBLU_ERR_INVALID_INPUT
- * with a message.  Asynchronous on `stream`.  Every call shares the scratch
- * array (it keeps the last call's contents; each call clears its flags
- * first): calls that overlap on the GPU race, so serialize them.  The first
- * call on a device looks up the array's device address with that device
- * current; make it before any stream capture.
+ * with a message.  Asynchronous on `stream`.  Within one process every call
+ * on a device shares the scratch array (it keeps the last call's contents;
+ * each call clears its flags first): calls that overlap on the GPU
+ * (different streams or host threads) race, so serialize them.  Each call
+ * looks up the array's device address with the current device; the first
+ * call on a device also queries the occupancy, so make it before any stream
+ * capture.
  */
 #define GBLU_NOALLOC_MAX_N 524288
 int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lcol,
                                const double *Lval, const int64_t *Urp, const int32_t *Ucol,
                                const double *Uval, const double *Udiag, const int32_t *piv,
                                const int32_t *q, const double *b_dev, double *x_dev,
-                               int32_t *status_dev, void *stream);
+                               int32_t *status_dev, long long spin_limit, void *stream);
 
 /*
  * Solve server (this library's extension; the paper solves one matrix at a
@@ -502,6 +512,17 @@ typedef struct {
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);
+
+/*
+ * Measurement aid (not part of the paper's method): the FP64 fused
+ * multiply-add rate of `device`, the roof of the re-factorization, which
+ * runs on the non-tensor FP64 pipe.  Times a kernel of eight independent
+ * multiply-add chains per thread on every SM (best of three after a warm-up
+ * run) and writes TFLOP/s (2 flops per multiply-add) to *tflops (host).
+ * Allocates and frees a small device buffer; synchronizes the device.
+ * Returns GBLU_OK, GBLU_ERR_INVALID_INPUT (tflops NULL) or GBLU_ERR_CUDA.
+ */
+int gblu_fp64_fma_rate(int device, double *tflops);
 
 /*
  * Copy the current factors to host arrays (for verification): column k of

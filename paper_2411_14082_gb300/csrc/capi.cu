@@ -266,6 +266,8 @@ int status_code(gblu_ctx *h)
         return fail(s, "device wait timed out (site %d, column %d)", h->hctl->where, h->hctl->where_k);
     if (s == GBLU_ERR_SINGULAR) return fail(s, "singular: no nonzero pivot candidate at step %d", h->hctl->where_k);
     if (s == GBLU_ERR_INTERNAL) return fail(s, "internal structure check failed on the device");
+    if (s == GBLU_ERR_NONFINITE)
+        return fail(s, "a NaN or infinite value in the column of step %d (check the values of A)", h->hctl->where_k);
     return fail(s, "device status %d", s);
 }
 

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kPanelThreads) dense_panel_kernel(DenseArgs2 d
     for (int c = 0; c < w; c++) {
         double *col = P + (size_t)c * R;
         double mx = 0.0;
-        for (int r = c + 1 + tid; r < R; r += kPanelThreads) mx = fmax(mx, fabs(col[r]));
+        for (int r = c + 1 + tid; r < R; r += kPanelThreads) mx = max_nan(mx, fabs(col[r]));
         mx = warp_max(mx);
         if (lane == 0) s_red[wid] = mx;
         __syncthreads();
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kPanelThreads) dense_panel_kernel(DenseArgs2 d
             v = warp_max(v);
             if (lane == 0) {
                 const double piv = col[c];
-                if (!((piv != 0.0) && (fabs(piv) >= d.eps * v))) {
+                if (!((piv != 0.0) && isfinite(piv) && (fabs(piv) >= d.eps * v))) {
                     s_fail = 1;
                     atomicExch(&d.ctl->interrupted, 1);
                     atomicMin(&d.ctl->first_bad, d.p + c0 + c);

@@ -47,15 +47,19 @@ __device__ __forceinline__ void set_status(DevCtl *ctl, int code)
     atomicCAS(&ctl->status, 0, code);
 }
 
+// the IEEE maximum: NaN if either argument is NaN (fmax would drop it)
+__device__ __forceinline__ double max_nan(double m, double v) { return (v > m || v != v) ? v : m; }
+__device__ __forceinline__ float max_nan(float m, float v) { return (v > m || v != v) ? v : m; }
+
 __device__ __forceinline__ double warp_max(double v)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_nan(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
 
 __device__ __forceinline__ float warp_max(float v)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_nan(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
 

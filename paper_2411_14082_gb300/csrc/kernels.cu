@@ -278,6 +278,7 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
     int bq = INT_MAX, br = -1, nu = 0, nc = 0, pc = 0, badrow = 0;
     for (int i = tid; i < cnt; i += kTailThreads) {
         const int r = list[i];
+        if (!isfinite(x[r])) badrow |= 4;   // a NaN or infinite value in the column
         int pj = __ldcg(a.pinv + r);
         if (pj >= k) {
             // pivotal at a later step, which can only finish first when it
@@ -324,6 +325,8 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         }
         badrow = (pc >> 1) | badrow;
         pc &= 1;
+        const bool nonfinite = (badrow & 4) != 0;
+        badrow &= 3;
         int piv = -1;
         if (pc) {
             const double xp = x[pref];
@@ -332,11 +335,16 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
         if (piv < 0) piv = br;
         if (a.speculate && piv >= 0 && piv != pref) atomicMin(&a.ctl->tail_mispredict, k);
         s_stop = 0;
-        if (a.speculate && (badrow || piv < 0)) {
+        if (a.speculate && (badrow || piv < 0 || nonfinite)) {
             // in a speculative pass only a wrong speculation upstream gives a
             // structure outside the elimination-tree bound or no nonzero
             // candidate: stop the pass; it is repeated from this step on
             atomicMin(&a.ctl->tail_mispredict, k - 1);
+            atomicExch(&a.ctl->abort_tail, 1);
+            s_stop = 1;
+        } else if (nonfinite) {
+            set_status(a.ctl, GBLU_ERR_NONFINITE);
+            a.ctl->where_k = k;
             atomicExch(&a.ctl->abort_tail, 1);
             s_stop = 1;
         } else if (badrow) {
@@ -991,14 +999,14 @@ __global__ void residual_kernel(int32_t n, const int64_t *Arp, const int32_t *Ac
         s = warp_sum(s);
         as = warp_sum(as);
         if (rvec && lane == 0) rvec[i] = b[i] - s;
-        rmax = fmax(rmax, fabs(b[i] - s));
-        amax = fmax(amax, as);
-        xmax = fmax(xmax, fabs(x[i]));
+        rmax = max_nan(rmax, fabs(b[i] - s));
+        amax = max_nan(amax, as);
+        xmax = max_nan(xmax, fabs(x[i]));
     }
     if (lane == 0) { sr[warp] = rmax; sa[warp] = amax; sx[warp] = xmax; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; w++) { rmax = fmax(rmax, sr[w]); amax = fmax(amax, sa[w]); xmax = fmax(xmax, sx[w]); }
+        for (int w = 1; w < 8; w++) { rmax = max_nan(rmax, sr[w]); amax = max_nan(amax, sa[w]); xmax = max_nan(xmax, sx[w]); }
         partial[3 * blockIdx.x + 0] = rmax;
         partial[3 * blockIdx.x + 1] = amax;
         partial[3 * blockIdx.x + 2] = xmax;
@@ -1009,9 +1017,9 @@ __global__ void residual_final_kernel(const double *partial, int nblocks, double
 {
     double r = 0.0, a = 0.0, x = 0.0;
     for (int i = threadIdx.x; i < nblocks; i += 32) {
-        r = fmax(r, partial[3 * i]);
-        a = fmax(a, partial[3 * i + 1]);
-        x = fmax(x, partial[3 * i + 2]);
+        r = max_nan(r, partial[3 * i]);
+        a = max_nan(a, partial[3 * i + 1]);
+        x = max_nan(x, partial[3 * i + 2]);
     }
     r = warp_max(r);
     a = warp_max(a);

@@ -27,6 +27,7 @@ ERR_CUDA = -6
 ERR_NOT_FACTORIZED = -7
 ERR_INTERNAL = -8
 ERR_BUSY = -9
+ERR_NONFINITE = -10
 
 SCHED = {"auto": 0, "level": 1, "syncfree": 2}
 
@@ -45,6 +46,7 @@ EXPORTED = [
     "gblu_order_amf", "gblu_last_status", "gblu_solve_partition",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
+    "gblu_fp64_fma_rate",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -160,8 +162,10 @@ def load(build_if_missing: bool = True):
         lib.gblu_column_etree.argtypes = [I32, P, P, P, P]
         lib.gblu_restart_set.argtypes = [I32, P, P, P]
         lib.gblu_restart_set.restype = I64
-        lib.gblu_solve_factors_noalloc.argtypes = [I32] + [P] * 13
+        lib.gblu_solve_factors_noalloc.argtypes = [I32] + [P] * 12 + [ctypes.c_longlong, P]
         lib.gblu_solve_factors_noalloc.restype = ctypes.c_int
+        lib.gblu_fp64_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.gblu_fp64_fma_rate.restype = ctypes.c_int
         lib.gblu_levels.argtypes = [I32, P, P, P]
         lib.gblu_levels.restype = I32
         lib.gblu_refactorize_batch.argtypes = [P, I32, P, I64, P, I64, P, ctypes.POINTER(I32), P]
@@ -454,10 +458,18 @@ class Solver:
         return out
 
 
+def fp64_fma_rate(device=0) -> float:
+    """gblu_fp64_fma_rate: the device's measured FP64 multiply-add rate, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load().gblu_fp64_fma_rate(int(device), ctypes.byref(v)))
+    return float(v.value)
+
+
 def solve_factors_noalloc(n, Lrp, Lcol, Lval, Urp, Ucol, Uval, Udiag, piv, q, b, x,
-                          status=None, stream=None):
+                          status=None, stream=None, spin_limit=0):
     """Allocation-free solve from caller-held row-wise factors (all CUDA tensors:
-    Lrp/Urp int64, Lcol/Ucol/piv/q int32, values float64)."""
+    Lrp/Urp int64, Lcol/Ucol/piv/q int32, values float64); spin_limit <= 0:
+    the library's default wait limit."""
     import torch
     ptrs = []
     for t, dt in ((Lrp, torch.int64), (Lcol, torch.int32), (Lval, torch.float64),
@@ -468,7 +480,7 @@ def solve_factors_noalloc(n, Lrp, Lcol, Lval, Urp, Ucol, Uval, Udiag, piv, q, b,
             raise TypeError(f"expected a contiguous CUDA {dt} tensor")
         ptrs.append(ctypes.c_void_p(t.data_ptr()))
     st = None if status is None else ctypes.c_void_p(status.data_ptr())
-    return _check(load().gblu_solve_factors_noalloc(int(n), *ptrs, st, _stream(stream)))
+    return _check(load().gblu_solve_factors_noalloc(int(n), *ptrs, st, int(spin_limit), _stream(stream)))
 
 
 # ---------------------------------------------------------------- host-only helpers
