@@ -12,6 +12,13 @@ of its componentwise magnitude and the largest entry of its column.  Entries
 that are rounding noise around an exact zero (cancellation) differ between
 two valid summation orders by far more than their own size; the column
 scale keeps them comparable.
+
+The strict per-column metric is reported beside it:
+    ||L_g(:,k) - L_o(:,k)||_inf / ||L_o(:,k)||_inf   (the same for U)
+and asserted (<= rtol) on every column above the cancellation noise floor,
+i.e. whose inf-norm (for L, times |U(k,k)|) is at least 1e-3 of the largest
+|L||U| magnitude summed into it: such a column lost at most three digits to
+cancellation, so rounding differences cannot reach rtol in it.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -36,9 +43,15 @@ def abs_product(lu):
     return k, M.data
 
 
-def compare_part(n, gp, gi, gx, op, oi, ox, scale_of):
+NOISE_FLOOR = 1e-3
+LOG = []   # one dict per compare_factors call (printed by tests run with -s)
+
+
+def compare_part(n, gp, gi, gx, op, oi, ox, scale_of, mag_of=None, colmul=None):
     """Oracle entries must all be in the GPU pattern; GPU-only entries must be
-    exact zeros.  Returns max |diff| / scale over the oracle entries."""
+    exact zeros.  Returns (max |diff| / scale over the oracle entries,
+    per-column max |diff|, per-column max |oracle entry|, per-column max
+    magnitude from mag_of)."""
     gk, _ = _keys(gp, gi, n)
     ok, ocols = _keys(op, oi, n)
     pos = np.searchsorted(gk, ok)
@@ -48,8 +61,26 @@ def compare_part(n, gp, gi, gx, op, oi, ox, scale_of):
     extra[pos] = False
     assert np.all(gx[extra] == 0.0), "GPU-only pattern entries must be exact zeros"
     scale = scale_of(ok, ocols)
-    err = np.abs(gx[pos] - ox) / np.where(scale > 0, scale, 1.0)
-    return float(err.max()) if len(err) else 0.0
+    diff = np.abs(gx[pos] - ox)
+    err = diff / np.where(scale > 0, scale, 1.0)
+    cdiff, cnorm, cmag = np.zeros(n), np.zeros(n), np.zeros(n)
+    if len(ok):
+        np.maximum.at(cdiff, ocols, diff)
+        np.maximum.at(cnorm, ocols, np.abs(ox))
+        if mag_of is not None:
+            np.maximum.at(cmag, ocols, mag_of(ok))
+    return (float(err.max()) if len(err) else 0.0), cdiff, cnorm, cmag
+
+
+def strict_columns(cdiff, cnorm, cmag, colmul, rtol):
+    """Strict per-column errors; columns above the noise floor are asserted."""
+    has = cnorm > 0
+    rel = np.where(has, cdiff / np.where(has, cnorm, 1.0), 0.0)
+    above = has & (cnorm * colmul >= NOISE_FLOOR * cmag)
+    worst = float(rel[above].max()) if above.any() else 0.0
+    bad = np.nonzero(above & (rel > rtol))[0]
+    assert len(bad) == 0, f"strict per-column error {rel[bad].max():.3e} > {rtol} at columns {bad[:10]}"
+    return worst, int(above.sum()), int(has.sum()), float(rel.max()) if has.any() else 0.0
 
 
 def compare_factors(f, lu, rtol=1e-10):
@@ -72,9 +103,16 @@ def compare_factors(f, lu, rtol=1e-10):
         p = np.minimum(np.searchsorted(mk, keys), len(mk) - 1)
         return np.where(mk[p] == keys, mv[p], 0.0) if len(mk) else np.zeros(len(keys))
 
-    el = compare_part(n, f["Lp"], f["Li"], f["Lx"], lu.Lp, lu.Li, lu.Lx,
-                      lambda keys, cols: np.maximum(m_at(keys), xcol[cols]) / udiag[cols])
-    eu = compare_part(n, f["Up"], f["Ui"], f["Ux"], lu.Up, lu.Ui, lu.Ux,
-                      lambda keys, cols: np.maximum(m_at(keys), xcol[cols]))
+    el, ldiff, lnorm, lmag = compare_part(n, f["Lp"], f["Li"], f["Lx"], lu.Lp, lu.Li, lu.Lx,
+                                          lambda keys, cols: np.maximum(m_at(keys), xcol[cols]) / udiag[cols],
+                                          m_at)
+    eu, udiff, unorm, umag = compare_part(n, f["Up"], f["Ui"], f["Ux"], lu.Up, lu.Ui, lu.Ux,
+                                          lambda keys, cols: np.maximum(m_at(keys), xcol[cols]), m_at)
     assert el <= rtol and eu <= rtol, f"factor mismatch: L {el:.3e}, U {eu:.3e} (tol {rtol})"
-    return max(el, eu)
+    sl = strict_columns(ldiff, lnorm, lmag, udiag, rtol)
+    su = strict_columns(udiff, unorm, umag, np.ones(n), rtol)
+    rec = dict(n=n, componentwise=max(el, eu), strict_above_floor=max(sl[0], su[0]),
+               strict_all=max(sl[3], su[3]), l_cols_checked=sl[1], l_cols=sl[2],
+               u_cols_checked=su[1], u_cols=su[2])
+    LOG.append(rec)
+    return rec

@@ -3,14 +3,19 @@ launch configuration bench.py times (default options): the first
 factorization, then the checked re-factorization of new transistor values
 and a solve.
 
-* Sampled steps (leaves, middle and the top separator): the factor columns
-  equal the oracle's (its factorization of the same values preferring the
-  GPU's pivot sequence, which is what the re-factorization must compute),
-  entry by entry, within 1e-10 of the componentwise magnitude |L||U|.
-* The same sampled columns satisfy the definition P A Q(:,k) = L U(:,k)
-  within 1e-11 of |L||U|.
+* Every column: the factor entries equal the oracle's (its factorization of
+  the same values preferring the GPU's pivot sequence, which is what the
+  re-factorization must compute) within 1e-10 of the column's work-vector
+  scale X_k = max(max|U(:,k)|, |U(k,k)| max|L(:,k)|), and the strict
+  per-column metric ||F_g(:,k) - F_o(:,k)||_inf / ||F_o(:,k)||_inf (F = L,
+  U) is within 1e-10 on every column whose norm (for L, times |U(k,k)|) is
+  at least 1e-6 of X_k; both are printed.
+* Sampled steps (leaves, middle and the top separator): within 1e-10 of the
+  componentwise magnitude |L||U|, and P A Q(:,k) = L U(:,k) within 1e-11 of
+  it.
 * Every column respects the threshold rule: max |L(:,k)| <= 1/eps.
-* The solve meets the residual bound ||b - A x|| <= 1e-12 ||A|| ||x||.
+* x equals the oracle's solution of the same b within 1e-10 (norm-wise
+  relative), and both meet ||b - A x|| <= 1e-12 ||A|| ||x||.
 """
 import numpy as np
 import pytest
@@ -42,6 +47,42 @@ def lu_times_u(n, Lp, Li, Lx, Up, Ui, Ux, k, absval=False):
     return np.bincount(np.concatenate(parts_r), weights=np.concatenate(parts_v), minlength=n)
 
 
+def col_of(p):
+    p = np.asarray(p, dtype=np.int64)
+    return np.repeat(np.arange(len(p) - 1), np.diff(p))
+
+
+def every_column(n, f, lu, rtol=1e-10, floor=1e-6):
+    for part in ("L", "U"):
+        gp, gx = f[part + "p"], f[part + "x"]
+        op, oi, ox = getattr(lu, part + "p"), getattr(lu, part + "i"), getattr(lu, part + "x")
+        assert np.array_equal(np.asarray(gp, np.int64), np.asarray(op, np.int64)), f"{part} column counts"
+        assert np.array_equal(f[part + "i"], oi), f"{part} row indices"
+    udiag = np.abs(lu.Ux[np.asarray(lu.Up[1:], np.int64) - 1])
+    cu, cl = col_of(lu.Up), col_of(lu.Lp)
+    unorm, lnorm = np.zeros(n), np.zeros(n)
+    np.maximum.at(unorm, cu, np.abs(lu.Ux))
+    np.maximum.at(lnorm, cl, np.abs(lu.Lx))
+    X = np.maximum(unorm, udiag * lnorm)
+    du, dl = np.abs(f["Ux"] - lu.Ux), np.abs(f["Lx"] - lu.Lx)
+    wu = float((du / X[cu]).max())
+    wl = float((dl * udiag[cl] / X[cl]).max()) if len(dl) else 0.0
+    udiff, ldiff = np.zeros(n), np.zeros(n)
+    np.maximum.at(udiff, cu, du)
+    np.maximum.at(ldiff, cl, dl)
+    su = udiff / np.where(unorm > 0, unorm, 1.0)
+    sl = ldiff / np.where(lnorm > 0, lnorm, 1.0)
+    au = unorm >= floor * X
+    al = (lnorm > 0) & (udiag * lnorm >= floor * X)
+    print(f"\nC2 full size, every column: work-vector-scaled error {max(wu, wl):.3e}; "
+          f"strict per-column error {max(su[au].max(), sl[al].max() if al.any() else 0):.3e} "
+          f"on {au.sum()} U and {al.sum()} L columns above the floor "
+          f"(of {n} and {(lnorm > 0).sum()}); worst over all columns {max(su.max(), sl.max()):.3e}")
+    assert wu <= rtol and wl <= rtol
+    assert su[au].max() <= rtol
+    assert not al.any() or sl[al].max() <= rtol
+
+
 def test_full_size_mesh_refactorization():
     ckt = inputs.workload_mesh()
     n, Ap, Ai, Ax0 = ckt.csc()
@@ -64,6 +105,14 @@ def test_full_size_mesh_refactorization():
     lu = O.factorize(n, Ap, Ai, Ax, Q, EPS, prefer=piv0)
     assert lu.status == 0
     assert np.array_equal(f["piv"], lu.piv)
+    # every column, against the work-vector scale, and the strict metric
+    every_column(n, f, lu)
+    # the solution against the oracle's
+    xo = O.solve(lu, b)
+    dx = np.abs(x - xo).max() / np.abs(xo).max()
+    print(f"\nC2 full size: max|x_gpu - x_oracle| / max|x_oracle| = {dx:.3e}")
+    assert dx <= 1e-10
+    assert O.residual(n, Ap, Ai, Ax, xo, b) <= 1e-12
     # sampled steps: a spread of leaves and the last steps (top separator)
     ks = sorted(set(np.linspace(0, n - 1, 16).astype(int).tolist() + list(range(n - 8, n))))
     pinv = np.empty(n, np.int64)

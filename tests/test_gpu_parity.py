@@ -114,6 +114,36 @@ def test_random_small_matrices_factorize_and_refactorize(sched):
             lu = lu2
 
 
+def test_column_scaled_ill_conditioned_matrices():
+    """Random matrices with their columns scaled by 10^U(-13, 0): condition
+    numbers far above the 1e12 the random tests above keep, yet the pivot
+    sequence is that of the unscaled matrix (the threshold test compares
+    entries of one column, and the factors of A D are L and U D), so the
+    factors must still equal the oracle's."""
+    rng = np.random.default_rng(43)
+    seen = 0
+    for trial in range(60):
+        n = int(rng.integers(2, 60))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.05, 0.3), rng,
+                                             zero_diag_frac=rng.uniform(0, 0.3), dominance=1.0)
+        if not well_conditioned(n, Ap, Ai, Ax):
+            continue
+        scale = 10.0 ** rng.uniform(-13, 0, n)
+        Ax = Ax * np.repeat(scale, np.diff(Ap))
+        seen += not well_conditioned(n, Ap, Ai, Ax, limit=1e12)
+        Q = rng.permutation(n).astype(np.int32)
+        lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+        if lu.status != O.OK:
+            continue
+        s = gblu.Solver(DEV)
+        s.analyze(n, Ap, Ai, Q)
+        Axd = dev(Ax)
+        s.factorize(Axd)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    assert seen >= 20
+
+
 def test_small_mna_workload_sequence():
     """n = 2,020 MNA grid with voltage sources: 1 factorize, then 10
     refactorizations with 5% of the element conductances perturbed
@@ -127,16 +157,27 @@ def test_small_mna_workload_sequence():
     lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
     Axd = dev(Ax)
     s.factorize(Axd)
-    compare_factors(s.export_factors(), lu, RTOL)
+    recs = [compare_factors(s.export_factors(), lu, RTOL)]
     solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    dx = []
     for it in range(10):
         ckt = inputs.perturb_elements(ckt, rng)
         Ax = ckt.values()
         Axd = dev(Ax)
         lu = O.refactorize(lu, Ap, Ai, Ax)
         s.refactorize(Axd)
-        compare_factors(s.export_factors(), lu, RTOL)
-        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+        recs.append(compare_factors(s.export_factors(), lu, RTOL))
+        xg, b = solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+        xo = O.solve(lu, b)
+        dx.append(np.abs(xg - xo).max() / np.abs(xo).max())
+        assert dx[-1] <= 1e-10
+    print(f"\nC1 sequence (11 factorizations): componentwise error "
+          f"{max(r['componentwise'] for r in recs):.3e}, strict per-column error "
+          f"{max(r['strict_above_floor'] for r in recs):.3e} above the floor "
+          f"({min(r['l_cols_checked'] for r in recs)}/{recs[0]['l_cols']} L and "
+          f"{min(r['u_cols_checked'] for r in recs)}/{recs[0]['u_cols']} U columns), "
+          f"{max(r['strict_all'] for r in recs):.3e} over all columns; "
+          f"x vs oracle {max(dx):.3e}")
     # the raw-entry perturbation fires the pivot check more often
     for it in range(5):
         Ax = inputs.perturb_entries(ckt.values(), rng, frac=0.05, sigma=0.3)
@@ -149,6 +190,37 @@ def test_small_mna_workload_sequence():
 
 def mesh_small(seed=7):
     return inputs.rc_mesh3d(40, 40, 4, seed=seed, n_fet=100)
+
+
+def test_ill_conditioned_mesh_factors_match_oracle():
+    """The ill-conditioned mesh variant (every conductance log-uniform in
+    [1e-9, 1e4]; 1-norm condition number about 2e11 at 40x40x4), with no
+    condition-number filter: the first
+    factorization and three re-factorizations with redrawn transistor values
+    equal the oracle's factors within the tolerance, and every solve meets
+    the residual bound (a backward error, so conditioning does not enter)."""
+    ckt = inputs.rc_mesh3d(40, 40, 4, seed=11, n_fet=100, g_range=(1e-9, 1e4))
+    n, Ap, Ai, Ax = ckt.csc()
+    A = np.zeros((n, n))
+    for c in range(n):
+        A[Ai[Ap[c]:Ap[c + 1]], c] = Ax[Ap[c]:Ap[c + 1]]
+    assert np.linalg.cond(A, 1) > 1e11
+    Q = inputs.grid_nd_order(ckt)
+    rng = np.random.default_rng(12)
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, Q)
+    lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+    Axd = dev(Ax)
+    s.factorize(Axd)
+    compare_factors(s.export_factors(), lu, RTOL)
+    solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
+    for it in range(3):
+        Ax = inputs.redraw_transistors(ckt, rng).values()
+        Axd = dev(Ax)
+        lu = O.refactorize(lu, Ap, Ai, Ax)
+        s.refactorize(Axd)
+        compare_factors(s.export_factors(), lu, RTOL)
+        solve_and_check(s, n, Ap, Ai, Ax, Axd, rng)
 
 
 def test_schedules_give_bitwise_identical_results():
