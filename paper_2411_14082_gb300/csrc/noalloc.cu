@@ -12,12 +12,15 @@
 // an interface convenience.
 //
 // Limits and sharing: n <= GBLU_NOALLOC_MAX_N; the array (8 MB + 256 B) is
-// held by every GPU that loads the library until the process exits.  All
-// calls share it, so calls that overlap on the GPU (different streams,
-// threads or processes sharing a context) race and must be serialized by the
-// caller.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current; make that first call
-// before any stream capture.
+// held on a device from the time this module is loaded there until the
+// process exits.  Within one process all calls on a device share it, so
+// calls that overlap on the GPU (different streams or host threads on the
+// same device) race and must be serialized by the caller; another process
+// loads its own copy of the module and so has its own array.  Every call
+// looks up the array's device address (cudaGetSymbolAddress, which
+// allocates nothing) with the current device, so the address stays right
+// after a device reset; the first call on a device also queries occupancy,
+// so make it before any stream capture.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,7 +33,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr int kWarps = 8;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr long long kSpinLimit = 1LL << 24;
+constexpr long long kDefaultSpinLimit = 1LL << 24;
 
 // layout: y double[MAX_N] | lflag int32[MAX_N] | uflag int32[MAX_N] | ctl int32[64]
 constexpr size_t kYBytes = (size_t)GBLU_NOALLOC_MAX_N * sizeof(double);
@@ -44,6 +47,7 @@ struct Scratch {
     double *y;
     int32_t *lflag, *uflag;
     int32_t *ctl;  // [0] ticket L, [1] ticket U, [2] status
+    long long spin_limit;
 };
 
 __device__ __forceinline__ int ld_acquire(const int32_t *p)
@@ -79,7 +83,7 @@ __device__ bool wait_flag(const int32_t *flag, Scratch s)
 {
     long long it = 0;
     while (ld_acquire(flag) != 1) {
-        if (++it > kSpinLimit || *(volatile int32_t *)(s.ctl + 2) != 0) {
+        if (++it > s.spin_limit || *(volatile int32_t *)(s.ctl + 2) != 0) {
             atomicCAS(s.ctl + 2, 0, GBLU_ERR_DEVICE_TIMEOUT);
             return false;
         }
@@ -154,7 +158,6 @@ __global__ void noalloc_status_kernel(Scratch s, int32_t *status_dev)
 
 struct DeviceSetup {
     bool ready = false;
-    unsigned char *base = nullptr;
     int grid = 0;
 };
 
@@ -168,7 +171,7 @@ extern "C" int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const i
                                           const int32_t *Ucol, const double *Uval,
                                           const double *Udiag, const int32_t *piv,
                                           const int32_t *q, const double *b_dev, double *x_dev,
-                                          int32_t *status_dev, void *stream)
+                                          int32_t *status_dev, long long spin_limit, void *stream)
 {
     using gblu::record_error;
     if (n < 1 || n > GBLU_NOALLOC_MAX_N)
@@ -181,17 +184,20 @@ extern "C" int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return record_error(GBLU_ERR_CUDA, "gblu_solve_factors_noalloc: no usable current device");
+    // every call, with the device current: the host-side name of the array
+    // is not a device address, and the address can change when the module
+    // is loaded again after a device reset
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return record_error(GBLU_ERR_CUDA, "gblu_solve_factors_noalloc: cudaGetSymbolAddress failed");
+    }
+    unsigned char *base = static_cast<unsigned char *>(ptr);
     DeviceSetup *ds = &g_setup[dev];
     {
-        // once per device, with that device current: the host-side name of
-        // the array is not a device address
+        // the grid size, once per device
         std::lock_guard<std::mutex> lock(g_setup_mutex);
         if (!ds->ready) {
-            void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return record_error(GBLU_ERR_CUDA, "gblu_solve_factors_noalloc: cudaGetSymbolAddress failed");
-            }
             int sms = 0, per_l = 0, per_u = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, noalloc_lsolve_kernel,
@@ -201,17 +207,17 @@ extern "C" int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const i
                 cudaGetLastError();
                 return record_error(GBLU_ERR_CUDA, "gblu_solve_factors_noalloc: device query failed");
             }
-            ds->base = static_cast<unsigned char *>(ptr);
             ds->grid = sms * (per_l < per_u ? per_l : per_u);
             if (ds->grid < 1) ds->grid = 1;
             ds->ready = true;
         }
     }
     Scratch s;
-    s.y = reinterpret_cast<double *>(ds->base);
-    s.lflag = reinterpret_cast<int32_t *>(ds->base + kYBytes);
-    s.uflag = reinterpret_cast<int32_t *>(ds->base + kYBytes + kFlagBytes);
-    s.ctl = reinterpret_cast<int32_t *>(ds->base + kYBytes + 2 * kFlagBytes);
+    s.y = reinterpret_cast<double *>(base);
+    s.lflag = reinterpret_cast<int32_t *>(base + kYBytes);
+    s.uflag = reinterpret_cast<int32_t *>(base + kYBytes + kFlagBytes);
+    s.ctl = reinterpret_cast<int32_t *>(base + kYBytes + 2 * kFlagBytes);
+    s.spin_limit = spin_limit > 0 ? spin_limit : kDefaultSpinLimit;
     cudaStream_t st = (cudaStream_t)stream;
     const int cgrid = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
     noalloc_clear_kernel<<<cgrid, 256, 0, st>>>(s, n);

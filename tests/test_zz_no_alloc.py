@@ -72,3 +72,35 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
                                    z32, z32, zd, zd2)
     assert ei.value.code == gblu.ERR_INVALID_INPUT
     assert "GBLU_NOALLOC_MAX_N" in str(ei.value)
+
+
+def test_noalloc_wait_limit_reports_timeout_and_context_survives():
+    """With a wait limit of one poll, a row that needs a value not yet
+    published gives up at once: status_dev receives GBLU_ERR_DEVICE_TIMEOUT
+    (the only place a caller can see it; the call itself returned when the
+    kernels were queued).  A later call with the default limit on the same
+    device solves correctly, so the context is intact."""
+    ckt = inputs.rc_mesh3d(40, 40, 4, seed=7, n_fet=100)
+    n, Ap, Ai, Ax = ckt.csc()
+    s = gblu.Solver(DEV)
+    s.analyze(n, Ap, Ai, inputs.grid_nd_order(ckt))
+    s.factorize(torch.from_numpy(Ax).cuda(DEV))
+    R = row_wise(s.export_factors(), n)
+    b = torch.from_numpy(inputs.rhs(n, np.random.default_rng(4))).cuda(DEV)
+    status = torch.full((1,), -77, dtype=torch.int32, device=f"cuda:{DEV}")
+    seen = []
+    for call in range(3):
+        x = torch.zeros_like(b)
+        gblu.solve_factors_noalloc(n, R["Lrp"], R["Lcol"], R["Lval"], R["Urp"], R["Ucol"],
+                                   R["Uval"], R["Udiag"], R["piv"], R["q"], b, x, status,
+                                   spin_limit=1)
+        torch.cuda.synchronize()
+        seen.append(status.item())
+    assert gblu.ERR_DEVICE_TIMEOUT in seen and set(seen) <= {0, gblu.ERR_DEVICE_TIMEOUT}
+    x = torch.full_like(b, float("nan"))
+    gblu.solve_factors_noalloc(n, R["Lrp"], R["Lcol"], R["Lval"], R["Urp"], R["Ucol"],
+                               R["Uval"], R["Udiag"], R["piv"], R["q"], b, x, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    xr = s.solve(b).cpu().numpy()
+    np.testing.assert_allclose(x.cpu().numpy(), xr, rtol=RTOL, atol=RTOL * np.abs(xr).max())
