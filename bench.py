@@ -268,7 +268,7 @@ def run_reference(args, rank, world):
         "max_rel_residual": max(r["residual"] for r in res),
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": f"{steps} full refactor+solve unit(s) of the workload, "
-                                   "single-threaded C oracle"},
+                                   "single-threaded C oracle", "host": host_info()},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -385,7 +385,8 @@ def run_batch(args, rank, world, local_rank):
                 "cores": len(procs), "kind": "oracle",
                 "sample": f"{len(procs)} single-threaded oracle processes, {units} sets each of the same pattern; "
                           "value = sets / the longest process's oracle time",
-                "wall_s": wall, "max_rel_residual": max(u["residual"] for r in ok for u in r)}
+                "wall_s": wall, "max_rel_residual": max(u["residual"] for r in ok for u in r),
+                "host": host_info()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -734,16 +735,72 @@ def run_serve(args, rank, world, local_rank):
     return 0
 
 
+def host_info():
+    """Host cores and CPU model of the machine the oracle ran on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def auto_order_variant(args, w, dev, vals, rhs, stream):
+    """The headline step on a handle analyzed without Q, i.e. with the
+    library's own ordering (gblu_order_auto's choice), timed with events over
+    args.auto_order_steps steps after two warm-up steps."""
+    import torch
+    from paper_2411_14082_gb300 import gblu
+    n = w["n"]
+    a = gblu.Solver(dev)
+    t0 = time.perf_counter()
+    a.analyze(n, w["Ap"], w["Ai"], None)
+    t_an = time.perf_counter() - t0
+    a.factorize(torch.from_numpy(w["Ax0"]).cuda(dev))
+    st = a.stats()
+    x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
+    res = torch.zeros(4, dtype=torch.float64, device=f"cuda:{dev}")
+    k = min(args.auto_order_steps, len(w["vals"]) - 2)
+    for i in range(2):
+        a.refactorize(vals[i])
+        a.solve(rhs[i], x)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    worst = 0.0
+    e0.record(stream)
+    for i in range(2, 2 + k):
+        a.refactorize(vals[i])
+        a.solve(rhs[i], x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    secs = e0.elapsed_time(e1) / 1e3
+    a.residual(vals[1 + k], rhs[1 + k], x, out=res)
+    worst = float(res[0].item())
+    out = {"value": k / secs, "unit": METRIC, "steps": k, "ms_per_step": 1e3 * secs / k,
+           "ordering": "library (gblu_analyze with Q = NULL)", "analyze_host_s": t_an,
+           "refactor_gflop": st["flops"] / 1e9, "nnz_lu": int(st["nnz_l"] + st["nnz_u"]),
+           "last_rel_residual": worst}
+    del a
+    torch.cuda.synchronize(dev)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     oracle_proc = None
-    if rank == 0 and not args.no_cpu_baseline:
-        # started before the first CUDA call, in a separate process
-        # the oracle solves the first timed step of this run (same seed and
-        # value set), which checks that step against it and times it
-        import tempfile
-        oracle_x = os.path.join(tempfile.gettempdir(), f"gblu_oracle_x_{os.getpid()}.npy")
-        oracle_proc = start_oracle(args.workload, 1, args.seed + 17 * rank, args.mesh, first=args.warmup,
-                                   xfile=oracle_x)
     import torch
     import torch.distributed as dist
     from paper_2411_14082_gb300 import gblu
@@ -875,6 +932,13 @@ def run_ours(args, rank, world, local_rank):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
+    # the FP64 pipe's measured rate, beside the nominal peak (before the
+    # timed region, never during it)
+    try:
+        fp64_probe = gblu.fp64_fma_rate(dev)
+    except gblu.GbluError:
+        fp64_probe = None
+    torch.cuda.synchronize(dev)
     clocks = ClockSampler(uuid)
     clocks.start()
     launches0 = s.stats()["kernel_launches"]
@@ -895,6 +959,8 @@ def run_ours(args, rank, world, local_rank):
         elapsed = max_over_ranks(elapsed, world, f"cuda:{dev}")
     t_ref = [ev_r[i][0].elapsed_time(ev_r[i][1]) / 1e3 for i in range(args.warmup, total)]
     t_sol = [ev_s[i][0].elapsed_time(ev_s[i][1]) / 1e3 for i in range(args.warmup, total)]
+    # one unit = refactor + solve of one step, from its first to its last event
+    t_unit = [ev_r[i][0].elapsed_time(ev_s[i][1]) / 1e3 for i in range(args.warmup, total)]
     resid = res[args.warmup:, 0].max().item()
     fwd = None
     if mixed:
@@ -930,8 +996,21 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         e2e_t = max_over_ranks(e2e_t, world, f"cuda:{dev}")
 
+    # ---- the same refactor + solve with the library's own ordering
+    # (gblu_analyze without Q), timed alone after the headline region
+    auto = None
+    if args.auto_order_steps > 0 and not (mixed or ss or args.graph or forced):
+        auto = auto_order_variant(args, w, dev, vals, rhs, stream)
+
     if rank != 0:
         return 0
+    if not args.no_cpu_baseline:
+        # after every GPU measurement, in a separate process: the oracle
+        # solves the first timed step of this run (same seed and value set),
+        # which checks that step against it and times it
+        oracle_x = os.path.join(tempfile.gettempdir(), f"gblu_oracle_x_{os.getpid()}.npy")
+        oracle_proc = start_oracle(args.workload, 1, args.seed + 17 * rank, args.mesh, first=args.warmup,
+                                   xfile=oracle_x)
     cpu = collect_oracle(oracle_proc) if oracle_proc else None
     oracle_check = None
     if cpu and os.path.exists(oracle_x):
@@ -964,14 +1043,18 @@ def run_ours(args, rank, world, local_rank):
         "phases_ms": {"refactor": 1e3 * t_rf, "solve": 1e3 * float(np.mean(t_sol)),
                       "refactor_p50": 1e3 * float(np.median(t_ref)),
                       "refactor_p99": 1e3 * float(np.percentile(t_ref, 99)),
+                      "solve_p50": 1e3 * float(np.median(t_sol)),
+                      "solve_p99": 1e3 * float(np.percentile(t_sol, 99)),
+                      "unit_p50": 1e3 * float(np.median(t_unit)),
+                      "unit_p99": 1e3 * float(np.percentile(t_unit, 99)),
                       "analyze_host": 1e3 * t_an, "first_factorize": 1e3 * t_fac,
                       "first_factorize_passes": fac_passes},
         "roofline": {"kernel": "refactor (checked re-factorization, all launches)",
                      "bound": "alu", "achieved": F / t_rf / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": F / t_rf / 1e12 / FP64_PEAK_TFLOPS,
                      "traffic": refactor_traffic(w["name"]),
-                     "peak_source": "FP64 ALU rate: 152 SMs x 2.07 GHz x 4 FLOP/clock "
-                                    "(1.19 TFLOP/s measured with independent DFMA chains)",
+                     "peak_source": "FP64 ALU rate: 152 SMs x 2.07 GHz x 4 FLOP/clock",
+                     "peak_probe_tflops": fp64_probe,
                      "hbm_view": {"compulsory_gbs": b_rf / t_rf / 1e9,
                                   "streaming_gbs": b_rf_stream / t_rf / 1e9}},
         "hbm_roofline": hbm_roofline(b_rf + 12 * (st["nnz_l"] + st["nnz_u"]) + 16 * (n + 1) + 32 * n,
@@ -1018,13 +1101,17 @@ def run_ours(args, rank, world, local_rank):
                            "restart_cols_mean": float(tm[:, 4].mean()),
                            "forced_steps": [int(v) for v in tm[:, 5]]}
     line["oracle_check"] = oracle_check
+    if auto:
+        line["auto_order"] = auto
     if cpu:
         secs = [c["seconds"] for c in cpu]
         line["cpu_baseline"] = {"value": len(secs) / sum(secs), "unit": METRIC, "cores": 1,
                                 "kind": "oracle",
                                 "sample": "1 full refactor+solve unit: the first timed step of this run "
-                                          "(single-threaded C oracle, separate process)",
-                                "max_rel_residual": max(c["residual"] for c in cpu)}
+                                          "(single-threaded C oracle, separate process, run after the "
+                                          "GPU measurements)",
+                                "max_rel_residual": max(c["residual"] for c in cpu),
+                                "host": host_info()}
     else:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
@@ -1057,6 +1144,8 @@ def main():
     ap.add_argument("--sets", type=int, default=256, help="value sets per step of the batch workload")
     ap.add_argument("--seed", type=int, default=inputs.BASE_SEED + 1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--auto-order-steps", type=int, default=5,
+                    help="steps of the variant with the library's own ordering (0: skip)")
     ap.add_argument("--mesh", default="200x200x4",
                     help="grid of the mesh workload (smaller grids for profiling runs)")
     args = ap.parse_args()
