@@ -188,9 +188,9 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
  * GBLU_REPIVOTED.  The result equals a factorization with pivoting that
  * prefers the previous pivot sequence.  Synchronizes `stream` once (to read
  * the 4-byte check status).  *repivoted (optional, host) is set to 1 if a
- * restart happened, else 0.  A NaN or infinite value anywhere in a column
- * fails its check; the restart then returns GBLU_ERR_NONFINITE instead of
- * storing it in the factors.
+ * restart happened, else 0.  A NaN or infinite pivot or entry of L fails
+ * the check; the restart then returns GBLU_ERR_NONFINITE instead of storing
+ * it in the factors (a NaN that stays in U shows in gblu_residual).
  */
 int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream,
                      int32_t *repivoted);

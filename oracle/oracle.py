@@ -102,6 +102,7 @@ class OracleLU:
     Ui: np.ndarray | None = None
     Ux: np.ndarray | None = None
     eps: float = 1e-3
+    inputs: tuple | None = None   # (Ap, Ai, Ax) it was computed from
     _h: object = None
     _lib: object = None
 
@@ -143,7 +144,8 @@ def factorize(n, Ap, Ai, Ax, Q, eps=1e-3, prefer=None, lib=None) -> OracleLU:
     if not h:
         raise MemoryError("oracle factorization ran out of memory")
     lu = OracleLU(n=int(n), status=lib.orc_status(h), bad_step=lib.orc_bad_step(h),
-                  n_rejected=lib.orc_rejected(h), Q=Q.copy(), eps=eps, _h=h, _lib=lib)
+                  n_rejected=lib.orc_rejected(h), Q=Q.copy(), eps=eps, inputs=(Ap, Ai, Ax),
+                  _h=h, _lib=lib)
     if lu.status == OK:
         nl, nu = lib.orc_nnz_l(h), lib.orc_nnz_u(h)
         lu.Lp = np.empty(n + 1, np.int32)

@@ -1682,6 +1682,11 @@ int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int3
         a.ntasks = ntask - ltp[div];
         KL(launch_refactor_tasks_f32(a, true, h->ref32_grid, h->epoch, st));
     }
+    // the pivots in double: a pivot that single precision cannot place
+    // clearly on the passing side of the threshold fails here, and the
+    // double-precision re-factorization then decides
+    KL(launch_f32_verify(h->S.n, h->LUp.p, h->LUi.p, h->nU.p, h->vals32.p, h->Lrp.p, h->Lcol.p, h->Lslot.p,
+                         h->opts.pivot_tol, h->ctl, h->sm_count * 8, st));
     CK(read_ctl(h, st));
     CK(status_code(h));
     h->f32_valid = !h->hctl->interrupted;

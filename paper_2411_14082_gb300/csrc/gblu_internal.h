@@ -281,6 +281,12 @@ int launch_dense_lu(const DenseArgs2 &d, void *stream, long long *launches);
 int launch_gather_scale(int64_t m, const int32_t *src, const double *scale, const double *in, double *out,
                         void *stream);
 int launch_widen(const float *src, double *dst, int64_t n, void *stream);
+// double-precision verification of single-precision pivots: a column whose
+// pivot does not clear the threshold by the single-precision error estimate
+// sets interrupted / first_bad
+int launch_f32_verify(int32_t n, const int64_t *LUp, const int32_t *LUi, const int32_t *nU, const float *LUx,
+                      const int64_t *Lrp, const int32_t *Lcol, const int32_t *Lslot, double eps, DevCtl *ctl,
+                      int grid, void *stream);
 int launch_axpy(double *x, const double *d, int32_t n, void *stream);
 int launch_begin_solve(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n, void *stream);
 int launch_solve_finish(const SolveArgs &a, bool lower, void *stream);

@@ -1045,6 +1045,57 @@ __global__ void gather_scale_kernel(int64_t m, const int32_t *src, const double 
     }
 }
 
+// Pivot verification of a single-precision re-factorization, in double.
+// Column k's single-precision pivot d carries a rounding error of the order
+// of u32 * S_k, where S_k = |d| + sum_j |L(k,j)| |U(j,k)| is the magnitude
+// summed into it (u32 = 2^-24); the max m = |d| max|L(:,k)| is close to its
+// double value.  The column passes only if the threshold test still holds
+// with d moved towards zero by kF32Margin * S_k and m enlarged by the same
+// relative amount: then the double-precision check of the same step passes
+// too, up to that estimate.  Any other column counts as failed, so that the
+// double-precision re-factorization (its check, and its restart) decides.
+// One warp per column; row k of L comes from the row-wise copy, U(j,k) from
+// a bisection in the column's sorted U rows.
+constexpr double kF32Margin = 1.0 / 4096.0;
+
+__global__ void f32_verify_kernel(int32_t n, const int64_t *LUp, const int32_t *LUi, const int32_t *nU,
+                                  const float *LUx, const int64_t *Lrp, const int32_t *Lcol,
+                                  const int32_t *Lslot, double eps, DevCtl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps) {
+        const int64_t beg = __ldg(LUp + k), end = __ldg(LUp + k + 1);
+        const int nu = __ldg(nU + k);
+        const double d = (double)__ldg(LUx + beg + nu - 1);
+        double lmax = 0.0, sum = 0.0;
+        for (int64_t e = beg + nu + lane; e < end; e += 32) lmax = max_nan(lmax, fabs((double)__ldg(LUx + e)));
+        for (int64_t e = __ldg(Lrp + k) + lane; e < __ldg(Lrp + k + 1); e += 32) {
+            const int j = __ldg(Lcol + e);
+            int lo = 0, hi = nu - 2;   // the U rows above the diagonal, ascending
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(LUi + beg + mid) < j) lo = mid + 1;
+                else hi = mid;
+            }
+            if (hi >= 0 && lo == hi && __ldg(LUi + beg + lo) == j)
+                sum += fabs((double)__ldg(LUx + __ldg(Lslot + e))) * fabs((double)__ldg(LUx + beg + lo));
+        }
+        lmax = warp_max(lmax);
+        sum = warp_sum(sum);
+        if (lane == 0) {
+            const double S = fabs(d) + sum;
+            const double m = fabs(d) * lmax;
+            const bool ok = d != 0.0 && isfinite(d) && isfinite(S) && !(m != m) &&
+                            fabs(d) - kF32Margin * S >= eps * m * (1.0 + kF32Margin);
+            if (!ok) {
+                atomicExch(&ctl->interrupted, 1);
+                atomicMin(&ctl->first_bad, k);
+            }
+        }
+    }
+}
+
 __global__ void widen_kernel(const float *src, double *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1322,6 +1373,14 @@ int solve_syncfree_grid(int *grid)
     for (int i = 1; i < 4; i++) per = p[i] < per ? p[i] : per;
     *grid = sms * per;
     return 0;
+}
+
+int launch_f32_verify(int32_t n, const int64_t *LUp, const int32_t *LUi, const int32_t *nU, const float *LUx,
+                      const int64_t *Lrp, const int32_t *Lcol, const int32_t *Lslot, double eps, DevCtl *ctl,
+                      int grid, void *stream)
+{
+    f32_verify_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, LUp, LUi, nU, LUx, Lrp, Lcol, Lslot, eps, ctl);
+    return (int)cudaGetLastError();
 }
 
 int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol, const int32_t *Aslot,

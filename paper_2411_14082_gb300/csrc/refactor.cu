@@ -243,19 +243,13 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
         for (int i = nD + lane; i < len; i += 32) Sc[i - nD] = x[i];
         return false;
     }
-    // m = max |x(L rows)|, or NaN when any entry of the column is NaN or
-    // infinite: the check below then fails and the restart reports it
+    // m = max |x(L rows)|, NaN if one of them is NaN; with an infinite m or
+    // pivot the check fails too, and the restart reports the value
     const R d = x[nU - 1];
     R m = R(0);
-    bool fin = true;
-    for (int i = lane; i < len; i += 32) {
-        const R v = x[i];
-        fin = fin && isfinite(v);
-        if (i >= nU) m = fmax(m, fabs(v));
-    }
-    if (!fin) m = R(NAN);
+    for (int i = nU + lane; i < len; i += 32) m = max_nan(m, fabs(x[i]));
     m = warp_max(m);
-    if (!((d != R(0)) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
+    if (!((d != R(0)) && isfinite(d) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
         if (lane == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
@@ -554,23 +548,17 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
         for (int i = nD + tid; i < len; i += kT) Sc[i - nD] = x[i];
         return false;
     }
-    // m = max |x(L rows)|, or NaN when any entry of the column is NaN or
-    // infinite: the check below then fails and the restart reports it
+    // m = max |x(L rows)|, NaN if one of them is NaN; with an infinite m or
+    // pivot the check fails too, and the restart reports the value
     const R d = x[nU - 1];
     R m = R(0);
-    bool fin = true;
-    for (int i = tid; i < len; i += kT) {
-        const R v = x[i];
-        fin = fin && isfinite(v);
-        if (i >= nU) m = fmax(m, fabs(v));
-    }
-    if (!fin) m = R(NAN);
+    for (int i = nU + tid; i < len; i += kT) m = max_nan(m, fabs(x[i]));
     m = warp_max(m);
     if (lane == 0) sh.red[warp] = m;
     group_sync<NW>(g);
     m = sh.red[0];
     for (int w = 1; w < NW; w++) m = max_nan(m, sh.red[w]);
-    if (!((d != R(0)) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
+    if (!((d != R(0)) && isfinite(d) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
         if (tid == 0) {
             atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
