@@ -317,9 +317,14 @@ def run_batch(args, rank, world, local_rank):
             clocks.start()
             t0 = time.perf_counter()
         ev[i][0].record(stream)
-        _, failed = s.refactorize_batch(vals, LUx)
-        ev[i][1].record(stream)
-        s.solve_batch(LUx, rhs, xs)
+        if args.graph:
+            # refactor + solve of the batch replayed from one CUDA graph
+            failed = s.step_batch(vals, LUx, rhs, xs)
+            ev[i][1].record(stream)
+        else:
+            _, failed = s.refactorize_batch(vals, LUx)
+            ev[i][1].record(stream)
+            s.solve_batch(LUx, rhs, xs)
         ev[i][2].record(stream)
         nfail += int(failed.sum())
     torch.cuda.synchronize(dev)
@@ -337,6 +342,24 @@ def run_batch(args, rank, world, local_rank):
     for k in range(args.sets):
         s.residual(vals[k], rhs[k], xs[k], out=res)
         worst = max(worst, float(res[0].item()))
+    # the other form (graph replay or eager launches) on the same sets, for context
+    other = "eager" if args.graph else "graph_replay"
+    alt_steps = min(5, args.steps)
+    for i in range(alt_steps + 1):   # the first graph call captures
+        if i == 1:
+            torch.cuda.synchronize(dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+        if args.graph:
+            s.refactorize_batch(vals, LUx)
+            s.solve_batch(LUx, rhs, xs)
+        else:
+            s.step_batch(vals, LUx, rhs, xs)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    alt = {"form": other, "value": args.sets * alt_steps / (a0.elapsed_time(a1) / 1e3), "unit": METRIC,
+           "ms_per_step": a0.elapsed_time(a1) / alt_steps}
     # the one-matrix path on the same sets, for context (not the metric)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -356,9 +379,12 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": w["name"] + f"_x{args.sets}", "n": n, "nnz_a": nnz,
                    "nnz_lu": int(st["nnz_l"] + st["nnz_u"]), "sets_per_step": args.sets,
                    "refactor_gflop_per_set": F / 1e9, "ordering": "geometric nested dissection",
+                   "form": "graph replay (gblu_step_batch)" if args.graph else
+                           "eager launches (gblu_refactorize_batch + gblu_solve_batch)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "max_rel_residual": worst, "residual_ok": bool(worst <= 1e-12), "failed_sets": nfail,
         "phases_ms": {"refactor_batch": 1e3 * float(np.mean(t_rf)), "solve_batch": 1e3 * float(np.mean(t_sv)),
+                      "note": "graph replay: refactor_batch = the whole replayed step" if args.graph else None,
                       "wall_per_step": 1e3 * elapsed / args.steps},
         "roofline": {"kernel": "refactor batch (all launches)", "bound": "alu",
                      "achieved": args.sets * F / float(np.mean(t_rf)) / 1e12, "peak": FP64_PEAK_TFLOPS,
@@ -366,6 +392,7 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None},
         "single_path": {"value": single, "unit": METRIC,
                         "note": "the same sets one at a time through gblu_refactorize + gblu_solve"},
+        other: alt,
         "cpu_baseline": None,
         # index bytes once per launch, value bytes once per set
         "hbm_roofline": hbm_roofline(

@@ -276,6 +276,27 @@ int gblu_solve_batch(gblu_handle h, int32_t nsets, const double *LUx_dev, int64_
                      void *stream);
 
 /*
+ * gblu_refactorize_batch followed by gblu_solve_batch, replayed from one
+ * CUDA graph (this library's extension of the batched form; the paper runs
+ * one matrix at a time).  Arguments and results as in those two calls: the
+ * sets' values at Ax_dev + s*ax_stride, factor values written at LUx_dev +
+ * s*lu_stride, right-hand sides at b_dev + s*b_stride, solutions at x_dev +
+ * s*x_stride; failed[s] / *n_failed (optional host) as in
+ * gblu_refactorize_batch, and the x of a failed set is not valid.
+ * The first call with a given set count, buffer addresses and strides (or
+ * after the structure or the handle's device buffers changed) runs the two
+ * calls eagerly and captures them; later calls with the same arguments
+ * replay the graph: one launch of every kernel, one synchronization of
+ * `stream`, and a read of the sets' control blocks.  The buffers' contents
+ * may change between calls; their addresses must not.  Errors as in
+ * gblu_refactorize_batch, plus GBLU_ERR_CUDA if the capture fails.
+ */
+int gblu_step_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
+                    double *LUx_dev, int64_t lu_stride, const double *b_dev, int64_t b_stride,
+                    double *x_dev, int64_t x_stride, int32_t *failed, int32_t *n_failed,
+                    void *stream);
+
+/*
  * Batch over handles of DIFFERENT patterns (this library's extension): the
  * checked re-factorization of Algorithms 3 and 4 for every handle hs[i]
  * with its own values Ax_dev[i] (device, its analyze slot order), into that

@@ -155,6 +155,16 @@ struct gblu_ctx {
     uint64_t struct_version = 0;
     uint64_t layout_version = 0;     // bumped by every device (re)allocation
     uint64_t glayout = 0;
+    // captured batch refactor + batch solve (gblu_step_batch): replayed while
+    // the structure, the device layout and the caller's buffers are the ones
+    // it was captured with
+    cudaGraphExec_t bgexec = nullptr;
+    std::vector<int64_t> bgkey;      // nsets, buffer addresses and strides
+    uint64_t bgversion = 0, bglayout = 0;
+    long long bglaunches = 0;
+    DBuf<RefactorArgs> bgargs;       // argument blocks the graph reads
+    DevCtl *bgctl_host = nullptr;    // pinned: per-set control blocks after a replay
+    int32_t bgctl_cap = 0;
     DBuf<double> sx;
 };
 
@@ -851,6 +861,9 @@ void gblu_destroy(gblu_handle h)
         release(h, h->sflag); release(h, h->sbits); release(h, h->morder); release(h, h->mlorder);
         release(h, h->muorder); release(h, h->margs); release(h, h->mticket);
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->bgexec) cudaGraphExecDestroy(h->bgexec);
+        if (h->bgctl_host) cudaFreeHost(h->bgctl_host);
+        release(h, h->bgargs);
         if (h->gstream) cudaStreamDestroy(h->gstream);
         if (h->aux) cudaStreamDestroy(h->aux);
         if (h->epoch_host) cudaFreeHost(h->epoch_host);
@@ -1514,6 +1527,126 @@ int gblu_step(gblu_handle h, const double *Ax_dev, const double *b_dev, double *
     if (repivoted) *repivoted = 1;
     h->last_repivot = true;
     return GBLU_REPIVOTED;
+}
+
+// capture [flag reset, batch refactor (cluster levels, pipeline), control
+// blocks -> pinned host, batch solve] for the given buffers into one graph.
+// The flags are cleared inside the graph, so every replay uses epoch 1.
+static int capture_step_batch(gblu_ctx *h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
+                              double *LUx_dev, int64_t lu_stride, const double *b_dev, int64_t b_stride,
+                              double *x_dev, int64_t x_stride)
+{
+    if (h->bgexec) {
+        cudaGraphExecDestroy(h->bgexec);
+        h->bgexec = nullptr;
+    }
+    const int32_t n = h->S.n;
+    CK(ensure(h, h->bgargs, (size_t)nsets));
+    if (h->bgctl_cap < nsets) {
+        if (h->bgctl_host) cudaFreeHost(h->bgctl_host);
+        h->bgctl_host = nullptr;
+        h->bgctl_cap = 0;
+        CU(cudaMallocHost((void **)&h->bgctl_host, sizeof(DevCtl) * (size_t)nsets));
+        h->bgctl_cap = nsets;
+    }
+    if (!h->gstream) CU(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    const RefactorArgs base = refactor_args(h, nullptr);
+    std::vector<RefactorArgs> args(nsets, base);
+    for (int32_t s = 0; s < nsets; s++) {
+        args[s].Ax = Ax_dev + s * ax_stride;
+        args[s].LUx = LUx_dev + s * lu_stride;
+        args[s].finish = h->bfinish.p + (size_t)s * n;
+        args[s].ctl = h->bctl.p + s;
+        args[s].dense_p = INT_MAX;   // the dense tail is not used in batches
+    }
+    cudaStream_t gs = h->gstream;
+    CU(cudaMemcpyAsync(h->bgargs.p, args.data(), sizeof(RefactorArgs) * nsets, cudaMemcpyHostToDevice, gs));
+    CU(cudaStreamSynchronize(gs));
+    const long long l0 = h->launches;
+    CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int rc = GBLU_OK;
+    auto step = [&]() -> int {
+        CU(cudaMemsetAsync(h->bfinish.p, 0, sizeof(int32_t) * (size_t)nsets * n, gs));
+        KL(launch_begin_batch(h->bctl.p, nsets, h->bticket.p, gs));
+        RefactorArgs a0 = base;
+        const std::vector<int32_t> &ltp = h->W.level_task_ptr;
+        const int32_t div = h->W.div_level;
+        for (int32_t l = 0; l < div; l++) {
+            a0.task_begin = ltp[l];
+            a0.ntasks = ltp[l + 1] - ltp[l];
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, false, 0, 1, h->bticket.p, gs));
+        }
+        const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
+        if (ltp[div] < ntask) {
+            a0.task_begin = ltp[div];
+            a0.ntasks = ntask - ltp[div];
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->ref_grid, 1, h->bticket.p, gs));
+        }
+        CU(cudaMemcpyAsync(h->bgctl_host, h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, gs));
+        return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, gs);
+    };
+    rc = step();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(gs, &graph);
+    h->bglaunches = h->launches - l0;
+    h->launches = l0;   // counted per replay instead
+    if (rc != GBLU_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(GBLU_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&h->bgexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+        h->bgexec = nullptr;
+        return fail(GBLU_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e2));
+    }
+    h->bgversion = h->struct_version;
+    h->bglayout = h->layout_version;
+    return GBLU_OK;
+}
+
+int gblu_step_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride, double *LUx_dev,
+                    int64_t lu_stride, const double *b_dev, int64_t b_stride, double *x_dev, int64_t x_stride,
+                    int32_t *failed, int32_t *n_failed, void *stream)
+{
+    NvtxRange nvtx_range("gblu_step_batch");
+    CK(check_handle(h));
+    if (n_failed) *n_failed = 0;
+    if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "gblu_factorize has not succeeded");
+    const int32_t n = h->S.n;
+    if (nsets < 1 || !b_dev || !x_dev || b_stride < n || x_stride < n)
+        return fail(GBLU_ERR_INVALID_INPUT, "step batch: nsets >= 1, non-null vectors, strides >= n");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::vector<int64_t> key = {nsets, (int64_t)(uintptr_t)Ax_dev, ax_stride, (int64_t)(uintptr_t)LUx_dev,
+                                      lu_stride, (int64_t)(uintptr_t)b_dev, b_stride, (int64_t)(uintptr_t)x_dev,
+                                      x_stride};
+    if (!h->bgexec || key != h->bgkey || h->bgversion != h->struct_version || h->bglayout != h->layout_version) {
+        // first call with these buffers: run eagerly (this sizes every
+        // buffer the graph uses), then capture for the next calls
+        CK(gblu_refactorize_batch(h, nsets, Ax_dev, ax_stride, LUx_dev, lu_stride, failed, n_failed, stream));
+        CK(gblu_solve_batch(h, nsets, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, stream));
+        CU(cudaStreamSynchronize(st));
+        h->bgkey.clear();
+        CK(capture_step_batch(h, nsets, Ax_dev, ax_stride, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride));
+        h->bgkey = key;
+        return GBLU_OK;
+    }
+    h->n_refactor += nsets;
+    CU(cudaGraphLaunch(h->bgexec, st));
+    h->launches += h->bglaunches;
+    CU(cudaStreamSynchronize(st));
+    int32_t nf = 0;
+    for (int32_t s = 0; s < nsets; s++) {
+        const DevCtl &c = h->bgctl_host[s];
+        if (c.status != 0) return fail(c.status, "batch set %d: device status %d (wait %d at column %d)", s,
+                                       c.status, c.where, c.where_k);
+        if (failed) failed[s] = c.interrupted ? 1 : 0;
+        nf += c.interrupted ? 1 : 0;
+    }
+    if (n_failed) *n_failed = nf;
+    return GBLU_OK;
 }
 
 int gblu_gather_scale(int64_t m, const int32_t *src_dev, const double *scale_dev, const double *in_dev,

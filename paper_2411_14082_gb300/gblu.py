@@ -46,7 +46,7 @@ EXPORTED = [
     "gblu_order_amf", "gblu_last_status", "gblu_solve_partition",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
-    "gblu_fp64_fma_rate",
+    "gblu_fp64_fma_rate", "gblu_step_batch",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -164,6 +164,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_restart_set.restype = I64
         lib.gblu_solve_factors_noalloc.argtypes = [I32] + [P] * 12 + [ctypes.c_longlong, P]
         lib.gblu_solve_factors_noalloc.restype = ctypes.c_int
+        lib.gblu_step_batch.argtypes = [P, I32, P, I64, P, I64, P, I64, P, I64, P, ctypes.POINTER(I32), P]
+        lib.gblu_step_batch.restype = ctypes.c_int
         lib.gblu_fp64_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.gblu_fp64_fma_rate.restype = ctypes.c_int
         lib.gblu_levels.argtypes = [I32, P, P, P]
@@ -390,6 +392,24 @@ class Solver:
                                        ctypes.c_void_p(b.data_ptr()), self.n, ctypes.c_void_p(x.data_ptr()),
                                        self.n, _stream(stream)))
         return x
+
+    def step_batch(self, Ax, LUx, b, x, stream=None):
+        """refactorize_batch + solve_batch replayed from a CUDA graph
+        (gblu_step_batch); Ax [nsets, nnz(A)], LUx [nsets, nnz(L+U)], b and x
+        [nsets, n].  Returns failed (numpy int32 [nsets])."""
+        nsets = Ax.shape[0]
+        for t in (Ax, LUx, b, x):
+            _dev_ptr(t, self.device)
+        if (Ax.dim() != 2 or Ax.shape[1] != self.nnz or LUx.dim() != 2 or LUx.shape[0] != nsets
+                or b.shape != x.shape or b.dim() != 2 or b.shape[0] != nsets or b.shape[1] != self.n):
+            raise ValueError("Ax [nsets, nnz(A)], LUx [nsets, nnz(L+U)], b and x [nsets, n]")
+        failed = np.zeros(nsets, np.int32)
+        nf = ctypes.c_int32(0)
+        _check(load().gblu_step_batch(self._h, nsets, ctypes.c_void_p(Ax.data_ptr()), self.nnz,
+                                      ctypes.c_void_p(LUx.data_ptr()), LUx.shape[1],
+                                      ctypes.c_void_p(b.data_ptr()), self.n, ctypes.c_void_p(x.data_ptr()),
+                                      self.n, _np_ptr(failed), ctypes.byref(nf), _stream(stream)))
+        return failed
 
     def refactorize_f32(self, Ax, stream=None):
         """Single-precision checked re-factorization; returns True if a pivot failed."""

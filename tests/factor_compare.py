@@ -15,13 +15,17 @@ scale keeps them comparable.
 
 The strict per-column metric is reported beside it:
     ||L_g(:,k) - L_o(:,k)||_inf / ||L_o(:,k)||_inf   (the same for U)
-and asserted (<= rtol) on every column above the rounding noise floor.  The
-floor is measured, not guessed: the oracle factorizes A again with every
-value moved by a few units in the last place (same pivot sequence), and a
-column whose own oracle result then moves by more than rtol / 100 (relative
-to its norm) is sensitive at the rounding level, so two valid summation
-orders can differ there by more than rtol; the strict metric is asserted on
-all other columns.
+and asserted (<= rtol) on every column above the rounding noise floor.  A
+column is at the floor, where two valid summation orders can differ by more
+than rtol, when one of its dependencies is at the floor (it inherits that
+rounding-level error through L(:,j) U(j,k)) or when
+  * cancellation took more than three digits from it: the largest |L||U|
+    magnitude summed into one of its entries exceeds 1e3 times the column's
+    norm (for L: its norm times |U(k,k)|, and the pivot's own ratio
+    (|L||U|)(k,k) / |U(k,k)|, since L(:,k) is divided by the pivot), or
+  * it is sensitive to rounding-level changes of A: the oracle factorizes A
+    again with every value moved by up to two units in the last place (same
+    pivot sequence), and the column moves by more than rtol / 100.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -47,6 +51,7 @@ def abs_product(lu):
 
 
 SENSITIVE = 1e-2   # a column is at the noise floor when the oracle moves by rtol * SENSITIVE
+CANCEL = 1e3       # ... or when cancellation took more than three digits from it
 LOG = []   # one dict per compare_factors call (printed by tests run with -s)
 
 
@@ -103,11 +108,28 @@ def column_sensitivity(lu, seed=0):
     return sl, su
 
 
-def strict_columns(cdiff, cnorm, sens, rtol):
+def at_floor(lu, l_ratio, u_ratio, sens, rtol):
+    """Columns at the noise floor: cancellation or rounding sensitivity of
+    their own, or a dependency (a U row j of column k) at the floor, whose
+    rounding-level error the column inherits through L(:,j) U(j,k)."""
+    n = lu.n
+    own = (l_ratio > CANCEL) | (u_ratio > CANCEL)
+    if sens is not None:
+        own |= (sens[0] > SENSITIVE * rtol) | (sens[1] > SENSITIVE * rtol)
+    bad = own.copy()
+    Up = np.asarray(lu.Up, np.int64)
+    for k in range(n):
+        if not bad[k]:
+            deps = lu.Ui[Up[k]:Up[k + 1] - 1]
+            bad[k] = bool(bad[deps].any()) if len(deps) else False
+    return bad
+
+
+def strict_columns(cdiff, cnorm, floor, rtol):
     """Strict per-column errors; columns above the noise floor are asserted."""
     has = cnorm > 0
     rel = np.where(has, cdiff / np.where(has, cnorm, 1.0), 0.0)
-    above = has if sens is None else has & (sens <= SENSITIVE * rtol)
+    above = has & ~floor
     worst = float(rel[above].max()) if above.any() else 0.0
     bad = np.nonzero(above & (rel > rtol))[0]
     assert len(bad) == 0, f"strict per-column error {rel[bad].max():.3e} > {rtol} at columns {bad[:10]}"
@@ -138,10 +160,25 @@ def compare_factors(f, lu, rtol=1e-10):
                                     lambda keys, cols: np.maximum(m_at(keys), xcol[cols]) / udiag[cols])
     eu, udiff, unorm = compare_part(n, f["Up"], f["Ui"], f["Ux"], lu.Up, lu.Ui, lu.Ux,
                                     lambda keys, cols: np.maximum(m_at(keys), xcol[cols]))
+    # cancellation ratio of each column: the largest |L||U| magnitude summed
+    # into an entry over the column's norm (for L also the pivot's own ratio,
+    # since L(:,k) is divided by it)
+    lk, lcols = _keys(lu.Lp, lu.Li, n)
+    uk, ucols = _keys(lu.Up, lu.Ui, n)
+    lmag, umag = np.zeros(n), np.zeros(n)
+    if len(lk):
+        np.maximum.at(lmag, lcols, m_at(lk))
+    if len(uk):
+        np.maximum.at(umag, ucols, m_at(uk))
+    diag = np.arange(n, dtype=np.int64)
+    piv_ratio = m_at(diag * n + diag) / np.where(udiag > 0, udiag, 1.0)
+    l_ratio = np.maximum(piv_ratio, lmag / np.where(lnorm > 0, udiag * lnorm, 1.0))
+    u_ratio = umag / np.where(unorm > 0, unorm, 1.0)
     assert el <= rtol and eu <= rtol, f"factor mismatch: L {el:.3e}, U {eu:.3e} (tol {rtol})"
     sens = column_sensitivity(lu)
-    sl = strict_columns(ldiff, lnorm, None if sens is None else sens[0], rtol)
-    su = strict_columns(udiff, unorm, None if sens is None else sens[1], rtol)
+    floor = at_floor(lu, l_ratio, u_ratio, sens, rtol)
+    sl = strict_columns(ldiff, lnorm, floor, rtol)
+    su = strict_columns(udiff, unorm, floor, rtol)
     rec = dict(n=n, componentwise=max(el, eu), strict_above_floor=max(sl[0], su[0]),
                strict_all=max(sl[3], su[3]), l_cols_checked=sl[1], l_cols=sl[2],
                u_cols_checked=su[1], u_cols=su[2])

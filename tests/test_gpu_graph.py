@@ -89,3 +89,50 @@ def test_autotune_keeps_results():
     assert O.residual(n, Ap, Ai, Ax, x, b) <= 1e-12
     with pytest.raises(gblu.GbluError):
         s.set_opts(alpha=-1.0)
+
+
+def test_step_batch_replay_equals_eager_batch():
+    """gblu_step_batch (graph replay after the first call) gives the factor
+    values, solutions and failed flags of gblu_refactorize_batch followed
+    by gblu_solve_batch, bit for bit, over several calls whose values change
+    in the same buffers; one call has a set whose check fails."""
+    ckt = inputs.rc_mesh3d(24, 24, 4, seed=5, n_fet=60)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    Q = inputs.grid_nd_order(ckt)
+    g, p = gblu.Solver(DEV), gblu.Solver(DEV)
+    for s in (g, p):
+        s.analyze(n, Ap, Ai, Q)
+        s.factorize(dev(Ax0))
+    lu = O.factorize(n, Ap, Ai, Ax0, Q, 1e-3)
+    nsets = 12
+    rng = np.random.default_rng(23)
+    st = g.stats()
+    nlu = st["nnz_l"] + st["nnz_u"]
+    Ax = torch.empty((nsets, len(Ai)), dtype=torch.float64, device=f"cuda:{DEV}")
+    b = torch.empty((nsets, n), dtype=torch.float64, device=f"cuda:{DEV}")
+    LUg = torch.empty((nsets, nlu), dtype=torch.float64, device=f"cuda:{DEV}")
+    xg = torch.empty_like(b)
+    launches = []
+    for call in range(4):
+        vals = np.stack([inputs.scale_values(Ax0, rng, 0.2) for _ in range(nsets)])
+        if call == 2:
+            # set 5: the pivot of one step is made to fail its check
+            ref = O.refactorize(lu, Ap, Ai, vals[5])
+            k = (2 * n) // 3
+            c = Q[k]
+            hit = np.nonzero(Ai[Ap[c]:Ap[c + 1]] == lu.piv[k])[0][0]
+            vals[5, Ap[c] + hit] -= ref.Ux[ref.Up[k + 1] - 1] * (1.0 - 1e-9)
+        Ax.copy_(torch.from_numpy(vals))
+        b.copy_(torch.from_numpy(np.stack([inputs.rhs(n, rng) for _ in range(nsets)])))
+        l0 = g.stats()["kernel_launches"]
+        fg = g.step_batch(Ax, LUg, b, xg)
+        launches.append(g.stats()["kernel_launches"] - l0)
+        LUp, fp = p.refactorize_batch(Ax)
+        xp = p.solve_batch(LUp, b)
+        assert np.array_equal(fg, fp)
+        assert bool(fg[5]) == (call == 2) and fg.sum() == (call == 2)
+        ok = fg == 0
+        assert torch.equal(LUg[torch.from_numpy(ok).to(LUg.device)], LUp[torch.from_numpy(ok).to(LUg.device)])
+        assert torch.equal(xg[torch.from_numpy(ok).to(xg.device)], xp[torch.from_numpy(ok).to(xg.device)])
+    # replays launch the same kernels as the eager first call
+    assert launches[1] == launches[2] == launches[3] > 0
