@@ -71,14 +71,14 @@ typedef struct {
                             with GBLU_ERR_DEVICE_TIMEOUT, default 1<<24           */
     /* structure-adaptive solve (Section V-A): the trailing block L(P0:n,P0:n)
        (and U likewise) is split off when it holds at least solve_dense_frac
-       of the factor's entries and at least solve_dense_min entries; it is cut
-       into solve_slices trapezoid slices of equal entry counts (the paper's
-       rule: 0.7, 300000, 8).  solve_dense_density > 0 retunes the rule for
-       the GPU: P0 is then the start of the longest trailing block whose
+       of the factor's entries and at least solve_dense_min entries (the
+       paper's rule: 0.7, 300000).  solve_dense_density > 0 retunes the rule
+       for the GPU: P0 is then the start of the longest trailing block whose
        entry density stays at least that value (solve_dense_frac ignored);
-       default 0.9 (gblu_autotune's choice on the 200x200x4 mesh: solve
-       9.3 ms against 11.0 ms at 0.5).  solve_slices = 0 disables the
-       split.                                                                */
+       default 0.9.  The block is solved in trapezoid slices of 32 rows, one
+       warp each, sync-free (Section V-B); solve_slices is the number of
+       slices of equal entry counts reported by gblu_get_stats for the
+       paper's own cut, and solve_slices = 0 disables the split.           */
     double solve_dense_frac;
     long long solve_dense_min;
     int solve_slices;
@@ -130,8 +130,8 @@ void gblu_default_opts(gblu_opts *o);
  *   of schedule options, and keep the fastest: first the dividing-level
  *   factor alpha (Section IV-B) and the warp assignment (warp_column_max)
  *   by re-factorization time, then the trailing-block rule of the solve
- *   (solve_dense_density, solve_slices;
- *   Section V-A) by solve time.  The paper tunes these constants for its
+ *   (solve_dense_density, and solve_slices = 0 to disable it; Section
+ *   V-A) by solve time.  The paper tunes these constants for its
  *   CPUs; here they are measured on the device and matrix at hand.  The
  *   factor values after the call are those of Ax_dev.  *chosen, *refactor_ms
  *   and *solve_ms (optional, host) report the kept options and their times.
@@ -514,7 +514,7 @@ typedef struct {
     int32_t div_level;    /* first level scheduled sync-free                 */
     int32_t n_solve_levels_l, n_solve_levels_u;  /* levels of the sparse blocks     */
     int32_t solve_p0_l, solve_p0_u;  /* first row of the trailing dense block (n: none) */
-    int32_t solve_slices_l, solve_slices_u;
+    int32_t solve_slices_l, solve_slices_u;  /* the paper's slices of the trailing block */
     int32_t etree_height;
     int64_t n_refactor;   /* refactorize calls                               */
     int64_t n_repivot;    /* refactorize calls that restarted with pivoting  */

@@ -80,7 +80,7 @@ struct gblu_ctx {
     int device = 0;
     gblu_opts opts{};
     int sm_count = 0;
-    int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0;
+    int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_grid = 0;
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
     int32_t force_col = -1;                        // forced check failure of the next refactorization
@@ -110,9 +110,9 @@ struct gblu_ctx {
     // solves
     DBuf<int64_t> Lrp, Urp;
     DBuf<int32_t> Lcol, Lslot, Ucol, Uslot, Udiag, lsv_rows, usv_rows, lbs, ubs, lrb, urb, lsv_tick, usv_tick,
-        ltcnt, utstart;
-    DBuf<int64_t> lsplit, usplit;
-    DBuf<double> y, z, ext_l, ext_u, partial, stage_ax, stage_b, stage_x;
+        lseg, useg;
+    DBuf<int64_t> ltri0, ufar;
+    DBuf<double> y, z, ext_l, ext_u, far, partial, stage_ax, stage_b, stage_x;
     // dense tail of the re-factorization: the block and its column offsets
     DBuf<double> dense;
     DBuf<int32_t> dense_s0;
@@ -347,10 +347,11 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->urb, h->W.urb, st));
     CK(upload(h, h->lsv_tick, h->W.lsv_tick, st));
     CK(upload(h, h->usv_tick, h->W.usv_tick, st));
-    CK(upload(h, h->lsplit, h->W.lsplit, st));
-    CK(upload(h, h->ltcnt, h->W.ltcnt, st));
-    CK(upload(h, h->usplit, h->W.usplit, st));
-    CK(upload(h, h->utstart, h->W.utstart, st));
+    CK(upload(h, h->ltri0, h->W.ltri0, st));
+    CK(upload(h, h->lseg, h->W.lseg, st));
+    CK(upload(h, h->ufar, h->W.ufar, st));
+    CK(upload(h, h->useg, h->W.useg, st));
+    if (h->W.up0 < n) CK(ensure(h, h->far, (size_t)n));
     // host vectors are uploaded asynchronously: keep them alive until done
     CU(cudaStreamSynchronize(st));
     h->t_tail[3] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_u).count();
@@ -814,7 +815,8 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = refactor_setup_f32(kRefCapLong, &h->ref32_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
-    if (e == cudaSuccess && r == 0) r = dense_piece_setup(kMaxPieceRows);
+    int trail_per_sm = 0;
+    if (e == cudaSuccess && r == 0) r = trail_setup(&trail_per_sm);
     if (e == cudaSuccess && r == 0) r = dense_setup(GBLU_DENSE_MAX_ROWS);
     if (e == cudaSuccess && r == 0) r = tail_setup();
     if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
@@ -828,6 +830,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     h->ref_grid = h->ref_blocks_per_sm * h->sm_count;
     h->ref32_grid = h->ref32_blocks_per_sm * h->sm_count;
     h->res_blocks = h->sm_count * 4;
+    h->trail_grid = std::max(1, trail_per_sm) * h->sm_count;
     *out = h;
     return GBLU_OK;
 }
@@ -851,8 +854,8 @@ void gblu_destroy(gblu_handle h)
         release(h, h->bfinish); release(h, h->bticket); release(h, h->bctl); release(h, h->bargs);
         release(h, h->vals32); release(h, h->vals_w); release(h, h->ir_r); release(h, h->ir_d); release(h, h->ir_out);
         if (h->ir_host) cudaFreeHost(h->ir_host);
-        release(h, h->ltcnt);
-        release(h, h->utstart); release(h, h->lsplit); release(h, h->usplit);
+        release(h, h->lseg);
+        release(h, h->useg); release(h, h->ltri0); release(h, h->ufar); release(h, h->far);
         release(h, h->y); release(h, h->z); release(h, h->partial);
         release(h, h->stage_ax); release(h, h->stage_b); release(h, h->stage_x);
         release(h, h->seq); release(h, h->restart); release(h, h->done); release(h, h->tpiv);
@@ -1086,6 +1089,7 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
         CK(ensure(h, h->z, (size_t)n * nsets));
         CK(ensure(h, h->ext_l, (size_t)n * nsets));
         CK(ensure(h, h->ext_u, (size_t)n * nsets));
+        if (h->W.up0 < n) CK(ensure(h, h->far, (size_t)n * nsets));
     }
     KL(launch_begin_solve(h->ctl, h->y.p, h->z.p, h->ext_l.p, h->ext_u.p, n * nsets, st));
     SolveArgs a = solve_args(h, LUx, b_dev, x_dev);
@@ -1125,18 +1129,23 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
         }
         return GBLU_OK;
     };
-    // forward: sparse block, then the trapezoid slices in order
+    // forward: sparse row blocks, then the trailing block (its rows' sums
+    // over earlier columns, then its 32-row slices sync-free)
     CK(sparse(true));
-    for (size_t q = 0; q + 1 < W.lcut.size(); q++) {
-        KL(launch_dense_piece(a, true, W.lp0, W.lcut[q], W.lcut[q + 1], h->lsplit.p, h->ltcnt.p,
-                              h->LUp.p, h->LUi.p, h->nU.p, st));
-        h->launches++;  // rectangular part + triangular piece
+    if (W.lp0 < n) {
+        const TrailArgs t{W.lp0, n, W.lnb, h->lseg.p, h->LUp.p, h->LUi.p, h->nU.p, h->ltri0.p};
+        a.ext = h->ext_l.p;
+        KL(launch_trail(a, t, true, h->trail_grid, st));
+        h->launches++;   // two kernels
     }
-    // backward: the slices from the last one, then the sparse block
-    for (size_t q = W.ucut.size(); q-- > 1;) {
-        KL(launch_dense_piece(a, false, W.up0, W.ucut[q - 1], W.ucut[q], h->usplit.p, h->utstart.p,
-                              h->LUp.p, h->LUi.p, h->nU.p, st));
-        h->launches++;
+    // backward: the trailing block's slices, then the sums of the rows above
+    // it over its columns, then the sparse row blocks
+    if (W.up0 < n) {
+        const TrailArgs t{W.up0, n, W.unb, h->useg.p, h->LUp.p, h->LUi.p, h->nU.p, h->ufar.p};
+        a.far = h->far.p;
+        KL(launch_trail(a, t, false, h->trail_grid, st));
+        if (W.up0 > 0) h->launches++;
+        a.ufar = h->ufar.p;
     }
     CK(sparse(false));
     return GBLU_OK;
@@ -1338,7 +1347,7 @@ int gblu_solve_multi(int32_t nh, gblu_handle *hs, const double *const *b_dev, do
         if (!h->factorized) return fail(GBLU_ERR_NOT_FACTORIZED, "multi: handle %d is not factorized", i);
         if (!b_dev[i] || !x_dev[i]) return fail(GBLU_ERR_INVALID_INPUT, "multi: null vector for handle %d", i);
         if (h->device != hs[0]->device) return fail(GBLU_ERR_INVALID_INPUT, "multi: handles on different devices");
-        if (h->W.lcut.size() > 1 || h->W.ucut.size() > 1) {
+        if (h->W.lp0 < h->S.n || h->W.up0 < h->S.n) {
             alone.push_back(i);
         } else {
             fused.push_back(h);
@@ -1755,7 +1764,9 @@ int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, doub
         }
     }
     const double dens[] = {0.0, 0.3, 0.5, 0.7, 0.9};
-    const int slices[] = {4, 8, 16};
+    // slices only switch the trailing block on (> 0) or off (0): the
+    // kernels cut it into 32-row slices whatever the count
+    const int slices[] = {0, 8};
     for (double dd : dens) {
         for (int m : slices) {
             if (rc != GBLU_OK) break;

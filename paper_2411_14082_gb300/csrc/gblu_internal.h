@@ -71,22 +71,26 @@ struct Schedule {
     std::vector<int32_t> lsv_ptr, lsv_rows, lsv_tptr, lsv_tick; int32_t lsv_levels = 0, lsv_div = 0;
     std::vector<int32_t> usv_ptr, usv_rows, usv_tptr, usv_tick; int32_t usv_levels = 0, usv_div = 0;
     // structure-adaptive solve (Section V): rows [p0, n) form the trailing
-    // block, cut at slice boundaries cut[0] = p0 < ... < cut[m] = n.
-    // Forward: the rectangular part of row i (p0 <= i) is its CSR entries
-    // [Lrp[i], lsplit[i - p0]) (columns before the row's slice), the
-    // triangular piece of column j is its first ltcnt[j - p0] L entries.
-    // Backward: the rectangular part of row i is [usplit[i - p0], Urp[i+1])
-    // (columns after the row's slice), the triangular piece of column j is
-    // its U entries from utstart[j - p0] to the diagonal.
+    // block; cut[0] = p0 < ... < cut[m] = n are the paper's slices of equal
+    // entry counts (reported; the kernels use 32-row slices).  The block is
+    // solved in slices of kTrailRows rows (block I = rows p0 + 32 I ...):
+    // forward: row i >= lp0 has its entries before the block in CSR
+    // [Lrp[i], ltri0[i - lp0]); lseg[(j - lp0) * (lnb + 1) + I] = number of
+    // L entries of column j >= lp0 with row < lp0 + 32 I.
+    // backward: useg[(j - up0) * (unb + 1) + I] = position (from LUp[j]) of
+    // the first U entry of column j >= up0 with row >= up0 + 32 I (I = unb:
+    // past the diagonal); row i < up0 has its entries in the block's
+    // columns in CSR [ufar[i], Urp[i+1]).
     int32_t lp0 = 0, up0 = 0;
+    int32_t lnb = 0, unb = 0;
+    std::vector<int64_t> ltri0, ufar;
+    std::vector<int32_t> lseg, useg;
     // dense tail of the re-factorization: columns [dense_p, n) form a
     // structurally dense block of dense_m = n - dense_p rows (0: none);
     // dense_s0[c] = slot of row dense_p inside column dense_p + c
     int32_t dense_p = 0, dense_m = 0;
     std::vector<int32_t> dense_s0;
     std::vector<int32_t> lcut, ucut;
-    std::vector<int64_t> lsplit, usplit;
-    std::vector<int32_t> ltcnt, utstart;
 };
 
 struct SolveSplit {
@@ -147,6 +151,7 @@ struct DevCtl {
     int32_t where;        // diagnostic: which wait timed out
     int32_t where_k;
     int32_t tail_mispredict;  // speculative tail: smallest step whose pivot left its preferred row
+    int32_t ticket_tl, ticket_tu;  // tickets of the trailing-block solve kernels
 };
 
 #define GBLU_INTERNAL_POOL_FULL (-100)
@@ -225,6 +230,8 @@ struct SolveArgs {
     const int32_t *bs;              // row blocks: block b is rows [bs[b], bs[b+1])
     const int32_t *rb;              // block of each row
     double *ext;                    // per row: its sum over entries outside its block
+    double *far;                    // backward, rows < up0: their sum over the trailing block's columns
+    const int64_t *ufar;            // backward, rows < up0: first CSR entry in those columns (null: none)
     const int32_t *rows;            // rows in ticket order, or block ids (level finish)
     int32_t nrows;                  // number of entries of rows
     // batches (nsets > 1): set s reads LUx + s*lu_stride, b + s*b_stride and
@@ -301,10 +308,19 @@ int launch_residual(int32_t n, const int64_t *Arp, const int32_t *Acol,
                     void *stream, double *rvec = nullptr);
 int solve_syncfree_grid(int *grid);
 // one trapezoid slice of the trailing block: rectangular part, then triangular piece
-int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,
-                       const int64_t *split, const int32_t *tri, const int64_t *LUp,
-                       const int32_t *LUi, const int32_t *nU, void *stream);
-int dense_piece_setup(int max_rows);
+// trailing block of the structure-adaptive solve, rows [p0, n) in slices of
+// kTrailRows rows.  Forward: the rows' sums over the columns before p0
+// (into ext), then the slices, sync-free; backward: the slices, then the
+// sums of rows < p0 over the block's columns (into far)
+struct TrailArgs {
+    int32_t p0, n, nb;
+    const int32_t *seg;             // lseg / useg of the Schedule
+    const int64_t *LUp;
+    const int32_t *LUi, *nU;
+    const int64_t *rows;            // forward: ltri0; backward: ufar
+};
+int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, void *stream);
+int trail_setup(int *blocks_per_sm);
 
 constexpr int kRefThreads = 256;       // 8 warps per refactor CTA
 constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short columns)
@@ -313,6 +329,7 @@ constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
 constexpr int kSolveBlockRows = 32;   // rows of one block of the sparse solves
 constexpr int kSolveBlockThreads = 256;
-constexpr int kMaxPieceRows = 4096;    // rows of one triangular piece (216 KB shared memory)
+constexpr int kMaxPieceRows = 4096;    // rows of one paper slice (reported partition)
+constexpr int kTrailRows = 32;         // rows of one slice of the trailing-block kernels
 
 }  // namespace gblu

@@ -493,6 +493,8 @@ __global__ void begin_solve_kernel(DevCtl *ctl, double *y, double *z, double *el
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->ticket_l = 0;
         ctl->ticket_u = 0;
+        ctl->ticket_tl = 0;
+        ctl->ticket_tu = 0;
     }
 }
 
@@ -573,7 +575,8 @@ __device__ __forceinline__ void lblock_finish(const SolveArgs &a, int f, int w, 
 __device__ __forceinline__ bool urow_ext(const SolveArgs &a, int i, int q, int w, int lane, bool wait,
                                          double &s)
 {
-    const int64_t rb = __ldg(a.Urp + i) + (w - 1 - q), re = __ldg(a.Urp + i + 1);
+    // entries in the trailing block's columns were summed into far[i] already
+    const int64_t rb = __ldg(a.Urp + i) + (w - 1 - q), re = a.ufar ? __ldg(a.ufar + i) : __ldg(a.Urp + i + 1);
     double acc = 0.0;
     bool ok = true;
     for (int64_t e = re - 1 - lane; e >= rb; e -= 32) {
@@ -584,6 +587,7 @@ __device__ __forceinline__ bool urow_ext(const SolveArgs &a, int i, int q, int w
         acc = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), zj, acc);
     }
     s = warp_sum(acc);
+    if (a.ufar) s += __ldcg(a.far + i);
     return __all_sync(kFull, ok);
 }
 
@@ -624,6 +628,7 @@ __device__ __forceinline__ SolveArgs set_view(const SolveArgs &a, int s)
     v.y = a.y + (int64_t)s * a.v_stride;
     v.z = a.z + (int64_t)s * a.v_stride;
     v.ext = a.ext + (int64_t)s * a.v_stride;
+    if (a.far) v.far = a.far + (int64_t)s * a.v_stride;
     return v;
 }
 
@@ -774,210 +779,190 @@ __global__ void begin_multi_solve_kernel(const SolveArgs *lo, const SolveArgs *u
 }
 
 // ---------------------------------------------------------------------------
-// Trailing block of the structure-adaptive solve (Section V-B, Algorithm 6):
-// for every trapezoid slice, the rectangular part (columns outside the
-// slice, already final) is a parallel sparse matrix-vector product, then the
-// triangular piece is solved by one CTA, column by column, with the piece's
-// part of the vector in shared memory.
-struct DenseArgs {
-    int32_t p0, r0, r1;                 // trailing block start, piece rows [r0, r1)
-    const int64_t *split;               // per row of the block (see Schedule)
-    const int32_t *tri;                 // per column: ltcnt (forward) / utstart (backward)
-    const int64_t *LUp;
-    const int32_t *LUi, *nU;
-};
+// Trailing block of the structure-adaptive solve (Section V-B, Algorithm 6).
+// The paper cuts the trailing rows [p0, n) into trapezoid slices, each a
+// rectangular product with the final part of the vector followed by a small
+// triangle.  Here a slice is kTrailRows = 32 rows, one warp (lane q holds
+// row p0 + 32 I + q of slice I), and the slices run sync-free: slice I takes
+// the 32-column blocks J of its rectangle as their values are published,
+// one 32 x 32 tile at a time (staged in shared memory from the factor's
+// column storage before the wait, then 32 multiply-adds per lane into four
+// accumulators), and finishes with its diagonal triangle by shuffles.  The
+// chain of dependent steps is the chain of slices, not of rows.  Values are
+// published by overwriting the solve's NaN sentinel, as in the row blocks.
+// Forward, the rows' entries before p0 (final before the block starts) are
+// summed first by a fully parallel launch; backward, the block comes first
+// and the sums of rows < p0 over its columns follow in a parallel launch.
+constexpr int kTB = kTrailRows;
+constexpr int kTileLd = kTB + 1;      // padded leading dimension of a tile
+constexpr int kTrailWarps = 4;        // slices (warps) per CTA
 
-// forward rectangular part: y[i] = b[piv[i]] - L(i, columns before the slice) y
-__device__ __forceinline__ void lsolve_rect(const SolveArgs &a, const DenseArgs &d, int i, int lane)
+// out = sum over CSR entries [e0, e1) of LUx[slot[e]] * v[col[e]], one warp,
+// four entries per lane in flight
+__device__ __forceinline__ double row_dot(const double *LUx, const int32_t *col, const int32_t *slot,
+                                          const double *v, int64_t e0, int64_t e1, int lane)
 {
-    const int64_t rb = __ldg(a.Lrp + i), re = __ldg(d.split + (i - d.p0));
-    double s = 0.0;
-    for (int64_t e = rb + lane; e < re; e += 32)
-        s = fma(__ldg(a.LUx + __ldg(a.Lslot + e)), __ldcg(a.y + __ldg(a.Lcol + e)), s);
-    s = warp_sum(s);
-    if (lane == 0) a.y[i] = __ldg(a.b + __ldg(a.piv + i)) - s;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t e = e0 + lane;
+    for (; e + 96 < e1; e += 128) {
+        const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64), c3 = __ldg(col + e + 96);
+        const int q0 = __ldg(slot + e), q1 = __ldg(slot + e + 32), q2 = __ldg(slot + e + 64), q3 = __ldg(slot + e + 96);
+        const double v0 = __ldcg(v + c0), v1 = __ldcg(v + c1), v2 = __ldcg(v + c2), v3 = __ldcg(v + c3);
+        s0 = fma(__ldg(LUx + q0), v0, s0);
+        s1 = fma(__ldg(LUx + q1), v1, s1);
+        s0 = fma(__ldg(LUx + q2), v2, s0);
+        s1 = fma(__ldg(LUx + q3), v3, s1);
+    }
+    for (; e < e1; e += 32) s0 = fma(__ldg(LUx + __ldg(slot + e)), __ldcg(v + __ldg(col + e)), s0);
+    return warp_sum(s0 + s1);
 }
 
+// forward, rows i >= p0: ext[i] = L(i, columns < p0) y
 template <bool kBatch>
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) lsolve_rect_kernel(SolveArgs a, DenseArgs d)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) ltrail_rect_kernel(SolveArgs a0, TrailArgs t)
 {
-    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
-    if (i >= d.r1) return;
-    if (kBatch) lsolve_rect(set_view(a, blockIdx.y), d, i, threadIdx.x & 31);
-    else lsolve_rect(a, d, i, threadIdx.x & 31);
+    const int i = t.p0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= t.n) return;
+    const SolveArgs a = kBatch ? set_view(a0, blockIdx.y) : a0;
+    const double s = row_dot(a.LUx, a.Lcol, a.Lslot, a.y, __ldg(a.Lrp + i), __ldg(t.rows + (i - t.p0)), lane);
+    if (lane == 0) a.ext[i] = s;
 }
 
-// backward rectangular part: z[i] = y[i] - U(i, columns after the slice) z
-__device__ __forceinline__ void usolve_rect(const SolveArgs &a, const DenseArgs &d, int i, int lane)
-{
-    const int64_t rb = __ldg(d.split + (i - d.p0)), re = __ldg(a.Urp + i + 1);
-    double s = 0.0;
-    for (int64_t e = re - 1 - lane; e >= rb; e -= 32)
-        s = fma(__ldg(a.LUx + __ldg(a.Uslot + e)), __ldcg(a.z + __ldg(a.Ucol + e)), s);
-    s = warp_sum(s);
-    if (lane == 0) a.z[i] = __ldcg(a.y + i) - s;
-}
-
+// backward, rows i < p0: far[i] = U(i, columns >= p0) z
 template <bool kBatch>
-__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) usolve_rect_kernel(SolveArgs a, DenseArgs d)
+__global__ void __launch_bounds__(kSolveWarpsPerBlock * 32) utrail_far_kernel(SolveArgs a0, TrailArgs t)
 {
-    const int i = d.r0 + blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5);
-    if (i >= d.r1) return;
-    if (kBatch) usolve_rect(set_view(a, blockIdx.y), d, i, threadIdx.x & 31);
-    else usolve_rect(a, d, i, threadIdx.x & 31);
+    const int i = blockIdx.x * kSolveWarpsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= t.p0) return;
+    const SolveArgs a = kBatch ? set_view(a0, blockIdx.y) : a0;
+    const double s = row_dot(a.LUx, a.Ucol, a.Uslot, a.z, __ldg(t.rows + i), __ldg(a.Urp + i + 1), lane);
+    if (lane == 0) a.far[i] = s;
 }
 
-constexpr int kTriThreads = 256;
-constexpr int kTriStages = 6;      // columns in flight: the current one and 5 ahead
-constexpr int kTriRing = 1024;     // entries of one column staged per stage (4 per thread)
-
-// asynchronous global -> shared copies (cp.async); each thread later reads
-// only the slots it copied itself, so its own wait_group is enough
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+// Stage the tile of slice I (rows i0 = p0 + 32 I ...) and column block J:
+// tile[c * kTileLd + r] = F(i0 + r, j0 + c), zero where the factor has no
+// entry.  Column j's entries with rows in slice I are [seg[j][I],
+// seg[j][I+1]) from base(j); lane c first reads column j0 + c's bounds.
+// false (tile untouched): the slice's rows have no entry in these columns.
+__device__ __forceinline__ bool trail_stage(double *tile, const double *LUx, const TrailArgs &t, bool lower,
+                                            int I, int J, int lane)
 {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all_but_newest() { asm volatile("cp.async.wait_group %0;" ::"n"(kTriStages - 1) : "memory"); }
-
-// shared memory of a triangular piece of m rows: a ring of kTriStages
-// staged columns (values, rows), then per row: the vector, the start and
-// count of its column's piece entries, its diagonal and its result
-struct TriSmem {
-    double *rv, *vec, *diag, *out;
-    long long *sb;
-    int32_t *ri, *sc;
-};
-__device__ __forceinline__ TriSmem tri_layout(unsigned char *smem, int m)
-{
-    TriSmem t;
-    t.rv = reinterpret_cast<double *>(smem);
-    t.vec = t.rv + kTriStages * kTriRing;
-    t.diag = t.vec + m;
-    t.out = t.diag + m;
-    t.sb = reinterpret_cast<long long *>(t.out + m);
-    t.ri = reinterpret_cast<int32_t *>(t.sb + m);
-    t.sc = t.ri + kTriStages * kTriRing;
-    return t;
-}
-
-// stage column q's first min(count, kTriRing) piece entries into ring slot
-// `stage` (thread tid copies entries tid, tid + kTriThreads, ...); always
-// commits one group so that group counting stays uniform
-__device__ __forceinline__ void tri_issue(const TriSmem &t, const SolveArgs &a, const DenseArgs &d,
-                                          int q, int stage, bool valid, int tid)
-{
-    if (valid) {
-        const long long b = t.sb[q];
-        const int c = min(t.sc[q], kTriRing);
-        for (int p = tid; p < c; p += kTriThreads) {
-            cp_async8(t.rv + stage * kTriRing + p, a.LUx + b + p);
-            cp_async4(t.ri + stage * kTriRing + p, d.LUi + b + p);
+    const int i0 = t.p0 + kTB * I, j0 = t.p0 + kTB * J;
+    const int wj = min(kTB, t.n - j0);
+    int s = 0, e = 0;
+    int64_t base = 0;
+    if (lane < wj) {
+        const int j = j0 + lane;
+        const int32_t *sg = t.seg + (int64_t)(j - t.p0) * (t.nb + 1);
+        s = __ldg(sg + I);
+        e = __ldg(sg + I + 1);
+        base = __ldg(t.LUp + j) + (lower ? __ldg(t.nU + j) : 0);
+    }
+    if (!__any_sync(kFull, e > s)) return false;
+    for (int idx = lane; idx < kTB * kTileLd; idx += 32) tile[idx] = 0.0;
+    __syncwarp();
+#pragma unroll 4
+    for (int c = 0; c < wj; c++) {
+        const int sc = __shfl_sync(kFull, s, c), ec = __shfl_sync(kFull, e, c);
+        const int64_t bc = __shfl_sync(kFull, base, c);
+        if (sc + lane < ec) {
+            const int64_t p = bc + sc + lane;
+            tile[c * kTileLd + (__ldg(t.LUi + p) - i0)] = __ldg(LUx + p);
         }
     }
-    cp_commit();
+    __syncwarp();
+    return true;
 }
 
-// forward triangular piece [r0, r1): columns in increasing order; the first
-// tri[j] L entries of column j are its rows inside the piece
-__device__ __forceinline__ void lsolve_tri(const SolveArgs &a, const DenseArgs &d)
+// forward slice I; true = a wait gave up
+__device__ bool ltrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int m = d.r1 - d.r0, tid = threadIdx.x;
-    const TriSmem t = tri_layout(smem, m);
-    for (int q = tid; q < m; q += kTriThreads) {
-        const int j = d.r0 + q;
-        t.vec[q] = __ldcg(a.y + j);
-        t.sb[q] = __ldg(d.LUp + j) + __ldg(d.nU + j);
-        t.sc[q] = __ldg(d.tri + (j - d.p0));
-    }
-    __syncthreads();
-    for (int q = 0; q < kTriStages - 1; q++) tri_issue(t, a, d, q, q % kTriStages, q < m, tid);
-    for (int q = 0; q < m; q++) {
-        const int qa = q + kTriStages - 1;
-        tri_issue(t, a, d, qa, qa % kTriStages, qa < m, tid);
-        cp_wait_all_but_newest();
-        const int s = q % kTriStages;
-        const double yj = t.vec[q];
-        const int c = t.sc[q];
-        for (int p = tid; p < min(c, kTriRing); p += kTriThreads) {
-            const int r = t.ri[s * kTriRing + p] - d.r0;
-            t.vec[r] = fma(-t.rv[s * kTriRing + p], yj, t.vec[r]);
+    const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    for (int J = 0; J < I; J++) {   // full column blocks before the slice
+        if (!trail_stage(tile, a.LUx, t, true, I, J, lane)) continue;   // nothing to wait for
+        double yq;
+        const bool ok = await_value(a.y, t.p0 + kTB * J + lane, a, 7, i0, yq);
+        if (!__all_sync(kFull, ok)) return true;
+#pragma unroll
+        for (int c = 0; c < kTB; c += 4) {
+            acc0 = fma(tile[(c + 0) * kTileLd + lane], __shfl_sync(kFull, yq, c + 0), acc0);
+            acc1 = fma(tile[(c + 1) * kTileLd + lane], __shfl_sync(kFull, yq, c + 1), acc1);
+            acc2 = fma(tile[(c + 2) * kTileLd + lane], __shfl_sync(kFull, yq, c + 2), acc2);
+            acc3 = fma(tile[(c + 3) * kTileLd + lane], __shfl_sync(kFull, yq, c + 3), acc3);
         }
-        for (int p = kTriRing + tid; p < c; p += kTriThreads) {   // longer columns
-            const int r = __ldg(d.LUi + t.sb[q] + p) - d.r0;
-            t.vec[r] = fma(-__ldg(a.LUx + t.sb[q] + p), yj, t.vec[r]);
-        }
-        __syncthreads();
+        __syncwarp();
     }
-    for (int q = tid; q < m; q += kTriThreads) a.y[d.r0 + q] = t.vec[q];
+    if (!trail_stage(tile, a.LUx, t, true, I, I, lane))   // the slice's own unit lower triangle
+        for (int idx = lane; idx < kTB * kTileLd; idx += 32) tile[idx] = 0.0;
+    __syncwarp();
+    double v = 0.0;
+    if (lane < w) v = __ldg(a.b + __ldg(a.piv + i)) - __ldcg(a.ext + i) - ((acc0 + acc1) + (acc2 + acc3));
+    for (int c = 0; c < w - 1; c++) {
+        const double yc = __shfl_sync(kFull, v, c);
+        if (lane > c && lane < w) v = fma(-tile[c * kTileLd + lane], yc, v);
+    }
+    if (lane < w) st_relaxed_f64(a.y + i, v);
+    return false;
 }
 
-// backward triangular piece [r0, r1): columns in decreasing order; the U
-// entries of column j from position tri[j] to the diagonal are its rows
-// inside the piece
-__device__ __forceinline__ void usolve_tri(const SolveArgs &a, const DenseArgs &d)
+// backward slice I; true = a wait gave up
+__device__ bool utrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int m = d.r1 - d.r0, tid = threadIdx.x;
-    const TriSmem t = tri_layout(smem, m);
-    for (int q = tid; q < m; q += kTriThreads) {
-        const int j = d.r0 + q;
-        t.vec[q] = __ldcg(a.z + j);
-        const long long b = __ldg(d.LUp + j) + __ldg(d.tri + (j - d.p0));
-        t.sb[q] = b;
-        t.sc[q] = (int)(__ldg(d.LUp + j) + __ldg(d.nU + j) - 1 - b);
-        t.diag[q] = __ldg(a.LUx + __ldg(a.Udiag + j));
-    }
-    __syncthreads();
-    // step i handles column q = m - 1 - i
-    for (int i = 0; i < kTriStages - 1; i++) tri_issue(t, a, d, m - 1 - i, i % kTriStages, i < m, tid);
-    for (int i = 0; i < m; i++) {
-        const int ia = i + kTriStages - 1;
-        tri_issue(t, a, d, m - 1 - ia, ia % kTriStages, ia < m, tid);
-        cp_wait_all_but_newest();
-        const int q = m - 1 - i, s = i % kTriStages;
-        // every thread divides; the piece entries of column q are rows above
-        // q, so nobody writes vec[q] in this step
-        const double zj = t.vec[q] / t.diag[q];
-        if (tid == 0) t.out[q] = zj;
-        const int c = t.sc[q];
-        for (int p = tid; p < min(c, kTriRing); p += kTriThreads) {
-            const int r = t.ri[s * kTriRing + p] - d.r0;
-            t.vec[r] = fma(-t.rv[s * kTriRing + p], zj, t.vec[r]);
+    const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    for (int J = t.nb - 1; J > I; J--) {   // column blocks after the slice, last first
+        const int j0 = t.p0 + kTB * J, wj = min(kTB, t.n - j0);
+        if (!trail_stage(tile, a.LUx, t, false, I, J, lane)) continue;   // nothing to wait for
+        double zq = 0.0;
+        bool ok = true;
+        if (lane < wj) ok = await_value(a.z, j0 + lane, a, 8, i0, zq);
+        if (!__all_sync(kFull, ok)) return true;
+#pragma unroll
+        for (int c = 0; c < kTB; c += 4) {   // columns past wj hold zero tiles and zq = 0
+            acc0 = fma(tile[(c + 0) * kTileLd + lane], __shfl_sync(kFull, zq, c + 0), acc0);
+            acc1 = fma(tile[(c + 1) * kTileLd + lane], __shfl_sync(kFull, zq, c + 1), acc1);
+            acc2 = fma(tile[(c + 2) * kTileLd + lane], __shfl_sync(kFull, zq, c + 2), acc2);
+            acc3 = fma(tile[(c + 3) * kTileLd + lane], __shfl_sync(kFull, zq, c + 3), acc3);
         }
-        for (int p = kTriRing + tid; p < c; p += kTriThreads) {   // longer columns
-            const int r = __ldg(d.LUi + t.sb[q] + p) - d.r0;
-            t.vec[r] = fma(-__ldg(a.LUx + t.sb[q] + p), zj, t.vec[r]);
-        }
-        __syncthreads();
+        __syncwarp();
     }
-    for (int q = tid; q < m; q += kTriThreads) {
-        const int j = d.r0 + q;
-        a.z[j] = t.out[q];
-        a.x[__ldg(a.Q + j)] = t.out[q];
+    trail_stage(tile, a.LUx, t, false, I, I, lane);   // the slice's upper triangle, diagonal included
+    double v = 0.0, zl = 0.0;
+    if (lane < w) v = __ldcg(a.y + i) - ((acc0 + acc1) + (acc2 + acc3));
+    for (int c = w - 1; c >= 0; c--) {
+        const double zc = __shfl_sync(kFull, v, c) / tile[c * kTileLd + c];
+        if (lane == c) zl = zc;
+        if (lane < c) v = fma(-tile[c * kTileLd + lane], zc, v);
     }
+    if (lane < w) {
+        st_relaxed_f64(a.z + i, zl);
+        a.x[__ldg(a.Q + i)] = zl;
+    }
+    return false;
 }
 
-// one CTA per piece; a batch runs one CTA per set (blockIdx.x)
-template <bool kBatch>
-__global__ void __launch_bounds__(kTriThreads) lsolve_tri_kernel(SolveArgs a, DenseArgs d)
+// slices handed out by ticket in their dependency order (forward ascending,
+// backward descending); in a batch ticket t is slice t / nsets of set
+// t % nsets, so a warp only waits on smaller tickets
+template <bool kLower, bool kBatch>
+__global__ void __launch_bounds__(kTrailWarps * 32) trail_slice_kernel(SolveArgs a0, TrailArgs t)
 {
-    if (kBatch) lsolve_tri(set_view(a, blockIdx.x), d);
-    else lsolve_tri(a, d);
-}
-
-template <bool kBatch>
-__global__ void __launch_bounds__(kTriThreads) usolve_tri_kernel(SolveArgs a, DenseArgs d)
-{
-    if (kBatch) usolve_tri(set_view(a, blockIdx.x), d);
-    else usolve_tri(a, d);
+    extern __shared__ __align__(16) double tsmem[];
+    const int lane = threadIdx.x & 31;
+    double *tile = tsmem + (threadIdx.x >> 5) * (kTB * kTileLd);
+    const int nsets = kBatch ? a0.nsets : 1;
+    const int total = t.nb * nsets;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(kLower ? &a0.ctl->ticket_tl : &a0.ctl->ticket_tu, 1);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= total) break;
+        const int s = k % nsets, q = k / nsets;
+        const SolveArgs a = kBatch ? set_view(a0, s) : a0;
+        const bool stop = kLower ? ltrail_slice(a, t, q, tile, lane) : utrail_slice(a, t, t.nb - 1 - q, tile, lane);
+        if (stop) break;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1301,53 +1286,48 @@ int launch_usolve(const SolveArgs &a, bool level_mode, int grid, void *stream)
     return (int)cudaGetLastError();
 }
 
-size_t tri_smem(int rows)
+int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, void *stream)
 {
-    return (size_t)kTriStages * kTriRing * (sizeof(double) + sizeof(int32_t)) +
-           (size_t)rows * (3 * sizeof(double) + sizeof(long long) + sizeof(int32_t));
-}
-
-int launch_dense_piece(const SolveArgs &a, bool lower, int32_t p0, int32_t r0, int32_t r1,
-                       const int64_t *split, const int32_t *tri, const int64_t *LUp,
-                       const int32_t *LUi, const int32_t *nU, void *stream)
-{
-    if (r1 <= r0) return 0;
-    DenseArgs d{p0, r0, r1, split, tri, LUp, LUi, nU};
-    const bool batch = a.nsets > 1;
-    const dim3 g((r1 - r0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, batch ? a.nsets : 1);
-    const int gt = batch ? a.nsets : 1;
-    const size_t sm = tri_smem(r1 - r0);
+    if (t.nb <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
+    const bool batch = a.nsets > 1;
+    const int sets = batch ? a.nsets : 1;
+    const size_t sm = (size_t)kTrailWarps * kTB * kTileLd * sizeof(double);
+    const long long total = (long long)t.nb * sets;
+    long long g = (total + kTrailWarps - 1) / kTrailWarps;
+    if (g > grid) g = grid;
+    if (g < 1) g = 1;
     if (lower) {
+        const dim3 gr((t.n - t.p0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, sets);
         if (batch) {
-            lsolve_rect_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-            lsolve_tri_kernel<true><<<gt, kTriThreads, sm, st>>>(a, d);
+            ltrail_rect_kernel<true><<<gr, kSolveWarpsPerBlock * 32, 0, st>>>(a, t);
+            trail_slice_kernel<true, true><<<(unsigned)g, kTrailWarps * 32, sm, st>>>(a, t);
         } else {
-            lsolve_rect_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-            lsolve_tri_kernel<false><<<gt, kTriThreads, sm, st>>>(a, d);
+            ltrail_rect_kernel<false><<<gr, kSolveWarpsPerBlock * 32, 0, st>>>(a, t);
+            trail_slice_kernel<true, false><<<(unsigned)g, kTrailWarps * 32, sm, st>>>(a, t);
         }
     } else {
+        const dim3 gr((t.p0 + kSolveWarpsPerBlock - 1) / kSolveWarpsPerBlock, sets);
         if (batch) {
-            usolve_rect_kernel<true><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-            usolve_tri_kernel<true><<<gt, kTriThreads, sm, st>>>(a, d);
+            trail_slice_kernel<false, true><<<(unsigned)g, kTrailWarps * 32, sm, st>>>(a, t);
+            if (t.p0 > 0) utrail_far_kernel<true><<<gr, kSolveWarpsPerBlock * 32, 0, st>>>(a, t);
         } else {
-            usolve_rect_kernel<false><<<g, kSolveWarpsPerBlock * 32, 0, st>>>(a, d);
-            usolve_tri_kernel<false><<<gt, kTriThreads, sm, st>>>(a, d);
+            trail_slice_kernel<false, false><<<(unsigned)g, kTrailWarps * 32, sm, st>>>(a, t);
+            if (t.p0 > 0) utrail_far_kernel<false><<<gr, kSolveWarpsPerBlock * 32, 0, st>>>(a, t);
         }
     }
     return (int)cudaGetLastError();
 }
 
-int dense_piece_setup(int max_rows)
+int trail_setup(int *blocks_per_sm)
 {
-    const int sm = (int)tri_smem(max_rows);
-    cudaError_t e = cudaFuncSetAttribute(lsolve_tri_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const size_t sm = (size_t)kTrailWarps * kTB * kTileLd * sizeof(double);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, trail_slice_kernel<true, false>,
+                                                                  kTrailWarps * 32, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(usolve_tri_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(lsolve_tri_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(usolve_tri_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trail_slice_kernel<false, false>, kTrailWarps * 32, sm);
+    *blocks_per_sm = a < b ? a : b;
     return (int)e;
 }
 

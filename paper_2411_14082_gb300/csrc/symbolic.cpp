@@ -442,48 +442,51 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         for (int32_t i = 0; i < n; i++) ru[i] = W.Urp[i + 1] - W.Urp[i];
         W.up0 = dense_split(n, cu, ru, split, W.ucut);
     }
-    W.lsplit.clear();
-    W.ltcnt.clear();
+    // ---- trailing block in 32-row slices (forward L, backward U) ----
+    W.ltri0.clear();
+    W.lseg.clear();
+    W.lnb = 0;
     if (W.lp0 < n) {
-        W.lsplit.resize(n - W.lp0);
-        W.ltcnt.resize(n - W.lp0);
-        size_t piece = 0;
+        const int32_t m = n - W.lp0, nb = (m + kTrailRows - 1) / kTrailRows;
+        W.lnb = nb;
+        W.ltri0.resize(m);
         for (int32_t i = W.lp0; i < n; i++) {
-            while (i >= W.lcut[piece + 1]) piece++;
-            const int32_t lo = W.lcut[piece];
             const int32_t *c = W.Lcol.data() + W.Lrp[i];
             const int32_t len = (int32_t)(W.Lrp[i + 1] - W.Lrp[i]);
-            W.lsplit[i - W.lp0] = W.Lrp[i] + (std::lower_bound(c, c + len, lo) - c);
+            W.ltri0[i - W.lp0] = W.Lrp[i] + (std::lower_bound(c, c + len, W.lp0) - c);
         }
-        piece = 0;
+        W.lseg.assign((size_t)m * (nb + 1), 0);
         for (int32_t j = W.lp0; j < n; j++) {
-            while (j >= W.lcut[piece + 1]) piece++;
-            const int32_t hi = W.lcut[piece + 1];
             const int32_t *r = S.LUi.data() + S.LUp[j] + S.nU[j];
             const int32_t len = (int32_t)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
-            W.ltcnt[j - W.lp0] = (int32_t)(std::lower_bound(r, r + len, hi) - r);
+            int32_t *sg = W.lseg.data() + (size_t)(j - W.lp0) * (nb + 1);
+            for (int32_t I = 0; I <= nb; I++) {
+                const int64_t lo = (int64_t)W.lp0 + (int64_t)kTrailRows * I;
+                sg[I] = lo >= n ? len : (int32_t)(std::lower_bound(r, r + len, (int32_t)lo) - r);
+            }
         }
     }
-    W.usplit.clear();
-    W.utstart.clear();
+    W.ufar.clear();
+    W.useg.clear();
+    W.unb = 0;
     if (W.up0 < n) {
-        W.usplit.resize(n - W.up0);
-        W.utstart.resize(n - W.up0);
-        size_t piece = 0;
-        for (int32_t i = W.up0; i < n; i++) {
-            while (i >= W.ucut[piece + 1]) piece++;
-            const int32_t hi = W.ucut[piece + 1];
+        const int32_t m = n - W.up0, nb = (m + kTrailRows - 1) / kTrailRows;
+        W.unb = nb;
+        W.ufar.resize(W.up0);
+        for (int32_t i = 0; i < W.up0; i++) {
             const int32_t *c = W.Urow_col.data() + W.Urp[i];
             const int32_t len = (int32_t)(W.Urp[i + 1] - W.Urp[i]);
-            W.usplit[i - W.up0] = W.Urp[i] + (std::lower_bound(c, c + len, hi) - c);
+            W.ufar[i] = W.Urp[i] + (std::lower_bound(c, c + len, W.up0) - c);
         }
-        piece = 0;
+        W.useg.assign((size_t)m * (nb + 1), 0);
         for (int32_t j = W.up0; j < n; j++) {
-            while (j >= W.ucut[piece + 1]) piece++;
-            const int32_t lo = W.ucut[piece];
             const int32_t *r = S.LUi.data() + S.LUp[j];
-            const int32_t len = S.nU[j] - 1;
-            W.utstart[j - W.up0] = (int32_t)(std::lower_bound(r, r + len, lo) - r);
+            const int32_t len = S.nU[j];   // U rows ascending, the diagonal (row j) last
+            int32_t *sg = W.useg.data() + (size_t)(j - W.up0) * (nb + 1);
+            for (int32_t I = 0; I <= nb; I++) {
+                const int64_t lo = (int64_t)W.up0 + (int64_t)kTrailRows * I;
+                sg[I] = lo >= n ? len : (int32_t)(std::lower_bound(r, r + len, (int32_t)lo) - r);
+            }
         }
     }
     // ---- row blocks of the sparse solves and their levels ----
