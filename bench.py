@@ -299,6 +299,8 @@ def run_batch(args, rank, world, local_rank):
     s = gblu.Solver(dev)
     s.analyze(n, w["Ap"], w["Ai"], w["Q"])
     s.factorize(torch.from_numpy(w["Ax0"]).cuda(dev))
+    if args.batch_group >= 0:
+        s.set_opts(batch_group=args.batch_group)
     st = s.stats()
     vals = torch.from_numpy(np.stack(w["vals"])).cuda(dev)
     rhs = torch.from_numpy(np.stack(w["rhs"])).cuda(dev)
@@ -379,6 +381,7 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": w["name"] + f"_x{args.sets}", "n": n, "nnz_a": nnz,
                    "nnz_lu": int(st["nnz_l"] + st["nnz_u"]), "sets_per_step": args.sets,
                    "refactor_gflop_per_set": F / 1e9, "ordering": "geometric nested dissection",
+                   "batch_group": s.opts()["batch_group"],
                    "form": "graph replay (gblu_step_batch)" if args.graph else
                            "eager launches (gblu_refactorize_batch + gblu_solve_batch)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
@@ -1196,6 +1199,8 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
                     help="mixed: single-precision refactor + refinement in double")
     ap.add_argument("--sets", type=int, default=256, help="value sets per step of the batch workload")
+    ap.add_argument("--batch-group", type=int, default=-1,
+                    help="sets per group of the batch launch (0: from the L2 size; default: the library's)")
     ap.add_argument("--seed", type=int, default=inputs.BASE_SEED + 1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--auto-order-steps", type=int, default=5,

@@ -111,6 +111,12 @@ typedef struct {
        0 = every step waits in that order from the start.  Both give the
        same factors.  Default 1. */
     int speculate_first;
+    /* batches of value sets (gblu_refactorize_batch): the persistent launch
+       takes the sets in groups of batch_group, all tasks of one group before
+       the next group's, so that the factors being read stay in L2 (0 = as
+       many sets as fit in half of L2; >= nsets: every set at once).
+       Default 0. */
+    int batch_group;
 } gblu_opts;
 
 /* largest dense tail block of the re-factorization (shared-memory panel) */

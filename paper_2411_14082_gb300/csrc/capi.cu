@@ -80,6 +80,7 @@ struct gblu_ctx {
     int device = 0;
     gblu_opts opts{};
     int sm_count = 0;
+    int l2_bytes = 0;
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_grid = 0;
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
@@ -776,6 +777,7 @@ void gblu_default_opts(gblu_opts *o)
     o->dense_min_rows = 0;
     o->warp_column_max = kRefCapShort;
     o->speculate_first = 1;
+    o->batch_group = 0;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -786,7 +788,8 @@ static bool opts_valid(const gblu_opts &o)
            o.solve_mode >= 0 && o.solve_mode <= 2 && o.alpha >= 0.0 && o.solve_dense_frac >= 0.0 &&
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
            o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
-           o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1);
+           o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1) &&
+           o.batch_group >= 0;
 }
 
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
@@ -808,6 +811,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
         return fail(GBLU_ERR_CUDA, "cannot use CUDA device %d", device);
     }
     cudaError_t e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hctl, sizeof(DevCtl));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->ctl, sizeof(DevCtl));
     if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(DevCtl));
@@ -1161,6 +1165,18 @@ int gblu_solve(gblu_handle h, const double *b_dev, double *x_dev, void *stream)
     return solve_values(h, h->vals.p, 0, b_dev, 0, x_dev, 0, 1, (cudaStream_t)stream);
 }
 
+// sets per group of a batch's persistent launch: the option, else as many
+// sets as fit in half of L2 (their factor and A values)
+static int batch_group(gblu_ctx *h, int32_t nsets)
+{
+    int g = h->opts.batch_group;
+    if (g <= 0) {
+        const double per = 8.0 * ((double)h->S.nnz() + (double)h->P.Ai.size());
+        g = (int)std::max(1.0, 0.5 * (double)h->l2_bytes / std::max(per, 1.0));
+    }
+    return std::min(g, (int)nsets);
+}
+
 int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, int64_t ax_stride,
                            double *LUx_dev, int64_t lu_stride, int32_t *failed, int32_t *n_failed,
                            void *stream)
@@ -1203,13 +1219,14 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
     for (int32_t l = 0; l < div; l++) {   // cluster mode
         a0.task_begin = ltp[l];
         a0.ntasks = ltp[l + 1] - ltp[l];
-        KL(launch_refactor_batch(h->bargs.p, a0, nsets, false, 0, h->epoch, h->bticket.p, st));
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, false, 0, h->epoch, h->bticket.p, st, nsets));
     }
     const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
     if (ltp[div] < ntask) {               // pipeline mode
         a0.task_begin = ltp[div];
         a0.ntasks = ntask - ltp[div];
-        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->ref_grid, h->epoch, h->bticket.p, st));
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->ref_grid, h->epoch, h->bticket.p, st,
+                                 batch_group(h, nsets)));
     }
     h->bctl_host.resize(nsets);
     CU(cudaMemcpyAsync(h->bctl_host.data(), h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, st));
@@ -1583,13 +1600,14 @@ static int capture_step_batch(gblu_ctx *h, int32_t nsets, const double *Ax_dev, 
         for (int32_t l = 0; l < div; l++) {
             a0.task_begin = ltp[l];
             a0.ntasks = ltp[l + 1] - ltp[l];
-            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, false, 0, 1, h->bticket.p, gs));
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, false, 0, 1, h->bticket.p, gs, nsets));
         }
         const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
         if (ltp[div] < ntask) {
             a0.task_begin = ltp[div];
             a0.ntasks = ntask - ltp[div];
-            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->ref_grid, 1, h->bticket.p, gs));
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->ref_grid, 1, h->bticket.p, gs,
+                                     batch_group(h, nsets)));
         }
         CU(cudaMemcpyAsync(h->bgctl_host, h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, gs));
         return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, gs);

@@ -252,7 +252,7 @@ int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int 
 // batch of value sets on one structure (sets_dev: one argument block per set)
 int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
-                          int grid, int epoch, int32_t *ticket, void *stream);
+                          int grid, int epoch, int32_t *ticket, void *stream, int group);
 int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
                           int npairs, int grid, int epoch, int32_t *ticket, void *stream);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);

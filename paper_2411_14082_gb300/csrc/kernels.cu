@@ -534,12 +534,47 @@ __device__ __forceinline__ bool await_value(const double *v, int j, const SolveA
 constexpr int kBR = kSolveBlockRows;
 
 // forward: sum over the entries of row i outside its block (all but its last q)
+// v[j] for four columns at once: one relaxed load each in flight, then a
+// bounded wait on those still holding the sentinel
+__device__ __forceinline__ bool fetch4(const double *v, const int (&j)[4], bool wait, const SolveArgs &a, int site,
+                                       int row, double (&out)[4])
+{
+    if (!wait) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) out[u] = __ldcg(v + j[u]);
+        return true;
+    }
+    unsigned long long b[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) b[u] = ld_relaxed_u64(v + j[u]);
+    bool ok = true;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        if (b[u] != kSentinel) out[u] = __longlong_as_double((long long)b[u]);
+        else if (ok) ok = await_value(v, j[u], a, site, row, out[u]);
+    }
+    return ok;
+}
+
 __device__ __forceinline__ bool lrow_ext(const SolveArgs &a, int i, int q, int lane, bool wait, double &s)
 {
     const int64_t rb = __ldg(a.Lrp + i), re = __ldg(a.Lrp + i + 1) - q;
     double acc = 0.0;
     bool ok = true;
-    for (int64_t e = rb + lane; e < re; e += 32) {
+    int64_t e = rb + lane;
+    // four entries per lane in flight, applied in the same order as one by one
+    for (; e + 96 < re && ok; e += 128) {
+        int j[4];
+        double lv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) j[u] = __ldg(a.Lcol + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) lv[u] = __ldg(a.LUx + __ldg(a.Lslot + e + 32 * u));
+        ok = fetch4(a.y, j, wait, a, 3, i, yv);
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc = fma(lv[u], yv[u], acc);
+    }
+    for (; e < re; e += 32) {
         const int j = __ldg(a.Lcol + e);
         double yj = 0.0;
         if (!wait) yj = __ldcg(a.y + j);
@@ -579,7 +614,20 @@ __device__ __forceinline__ bool urow_ext(const SolveArgs &a, int i, int q, int w
     const int64_t rb = __ldg(a.Urp + i) + (w - 1 - q), re = a.ufar ? __ldg(a.ufar + i) : __ldg(a.Urp + i + 1);
     double acc = 0.0;
     bool ok = true;
-    for (int64_t e = re - 1 - lane; e >= rb; e -= 32) {
+    int64_t e = re - 1 - lane;
+    // four entries per lane in flight, applied in the same order as one by one
+    for (; e - 96 >= rb && ok; e -= 128) {
+        int j[4];
+        double uv[4], zv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) j[u] = __ldg(a.Ucol + e - 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) uv[u] = __ldg(a.LUx + __ldg(a.Uslot + e - 32 * u));
+        ok = fetch4(a.z, j, wait, a, 4, i, zv);
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc = fma(uv[u], zv[u], acc);
+    }
+    for (; e >= rb; e -= 32) {
         const int j = __ldg(a.Ucol + e);
         double zj = 0.0;
         if (!wait) zj = __ldcg(a.z + j);

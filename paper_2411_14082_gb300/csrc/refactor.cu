@@ -640,14 +640,45 @@ __global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgs
 
 // Batch of value sets on one structure: sets[s] is the argument block of
 // set s (its A values, factor values, ready flags and control block; the
-// structure fields are shared).  Ticket t is task task_begin + t / nsets of
-// set t % nsets, so every set meets its tasks in a topological order.  A set
-// whose check failed (or whose wait gave up) is skipped from then on; the
-// other sets go on.
+// structure fields are shared).  The sets go in groups of `group`: the
+// tickets of a group are its tasks in order, each for all the group's sets
+// (task-major inside the group), and the next group follows; so every set
+// meets its tasks in a topological order, and only a group's factors are
+// being read at a time.  A set whose check failed (or whose wait gave up)
+// is skipped from then on; the other sets go on.
+// ticket t of a batch in groups of g sets (the last group may be smaller):
+// the group's tickets are task-major, set-minor
+__device__ __forceinline__ void group_split(long long t, int ntasks, int nsets, int g, int &task, int &set)
+{
+    const long long full = (long long)(nsets / g) * g;   // sets in full groups
+    const long long tf = (long long)ntasks * full;
+    if (t < tf) {
+        const long long gi = t / ((long long)ntasks * g), r = t % ((long long)ntasks * g);
+        task = (int)(r / g);
+        set = (int)(gi * g + r % g);
+    } else {
+        const long long r = t - tf, gl = nsets - full;
+        task = (int)(r / gl);
+        set = (int)(full + r % gl);
+    }
+}
+__device__ __forceinline__ int group_set(long long t, int ntasks, int nsets, int g)
+{
+    int task, set;
+    group_split(t, ntasks, nsets, g, task, set);
+    return set;
+}
+__device__ __forceinline__ int group_task(long long t, int ntasks, int nsets, int g)
+{
+    int task, set;
+    group_split(t, ntasks, nsets, g, task, set);
+    return task;
+}
+
 template <bool kWait>
 __global__ void __launch_bounds__(kThreads, 2)
 refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
-                      int32_t *ticket, const SetTask *order)
+                      int32_t *ticket, const SetTask *order, int group)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_skip;
@@ -663,7 +694,7 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
             s_t = t < total ? (int)t : -1;
             s_skip = 0;
             if (t < total) {
-                const int si = order ? __ldg(&order[t].set) : (int)(t % nsets);
+                const int si = order ? __ldg(&order[t].set) : group_set(t, ntasks, nsets, group);
                 const DevCtl *c = sets[si].ctl;
                 s_skip = ld_volatile(&c->interrupted) || ld_volatile(&c->status);
             }
@@ -673,8 +704,8 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
         __syncthreads();
         if (t < 0) break;
         if (skip) continue;
-        const int si = order ? __ldg(&order[t].set) : t % nsets;
-        const int task = order ? __ldg(&order[t].task) : task_begin + t / nsets;
+        const int si = order ? __ldg(&order[t].set) : group_set(t, ntasks, nsets, group);
+        const int task = order ? __ldg(&order[t].task) : task_begin + group_task(t, ntasks, nsets, group);
         // a local copy: stores through the work vector cannot alias it, so its
         // fields stay in registers instead of being reloaded from memory
         const RefactorArgs as = sets[si];
@@ -759,18 +790,21 @@ int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream)
 }
 
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
-                          int grid, int epoch, int32_t *ticket, void *stream)
+                          int grid, int epoch, int32_t *ticket, void *stream, int group)
 {
     if (a0.ntasks <= 0 || nsets <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
+    if (group < 1 || group > nsets) group = nsets;
     if (pipeline) {
         refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, a0.task_begin,
-                                                                           a0.ntasks, epoch, 1, ticket, nullptr);
+                                                                           a0.ntasks, epoch, 1, ticket, nullptr,
+                                                                           group);
     } else {
+        // a level launch has no waits: one group holding every set
         const long long blocks = (long long)a0.ntasks * nsets;
         if (blocks > INT_MAX) return (int)cudaErrorInvalidValue;
         refactor_batch_kernel<false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
-            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr);
+            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets);
     }
     return (int)cudaGetLastError();
 }
@@ -783,7 +817,7 @@ int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
     int g = (nsets + 255) / 256;
     begin_multi_kernel<<<g, 256, 0, st>>>(sets_dev, nsets, ticket);
     refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
-                                                                       order_dev);
+                                                                       order_dev, 1);
     return (int)cudaGetLastError();
 }
 
