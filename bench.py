@@ -855,6 +855,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         s.analyze(n, w["Ap"], w["Ai"], w["Q"])
     t_an = time.perf_counter() - t0
+    if args.solve_ctas >= 0:
+        s.set_opts(solve_ctas_per_sm=args.solve_ctas)
     Ax0 = torch.from_numpy(w["Ax0"]).cuda(dev)
     t0 = time.perf_counter()
     s.factorize(ss.values(Ax0) if ss else Ax0)
@@ -904,6 +906,22 @@ def run_ours(args, rank, world, local_rank):
     nforce = int(round(args.repivot_frac * args.steps))
     forced = {int(i) + args.warmup: int(frng.integers(0, n))
               for i in frng.choice(args.steps, size=nforce, replace=False)} if nforce else {}
+    genuine = {}
+    if forced and args.repivot_mode == "genuine":
+        # a real pivot failure instead of a forced one: at a random step with
+        # no dependency (its pivot is A's entry itself) and other candidates,
+        # the pivot entry of A is scaled by 1e-9, so the check fails and the
+        # pivot moves; the values are prepared before the timed region
+        f0 = s.export_factors()
+        leaves = np.nonzero((np.diff(f0["Up"]) == 1) & (np.diff(f0["Lp"]) > 0))[0]
+        for i in forced:
+            k = int(leaves[frng.integers(0, len(leaves))])
+            c, pr = int(f0["q"][k]), int(f0["piv"][k])
+            slot = int(w["Ap"][c]) + int(np.nonzero(w["Ai"][w["Ap"][c]:w["Ap"][c + 1]] == pr)[0][0])
+            v = vals[i].clone()
+            v[slot] *= 1e-9
+            genuine[i] = v
+            forced[i] = k
     tail_ms = []
 
     def step(i):
@@ -929,12 +947,15 @@ def run_ours(args, rank, world, local_rank):
             repiv += int(rep)
         elif i in forced:
             ev_r[i][0].record(stream)
-            _, rep = s.refactorize_forced(vals[i], forced[i])
+            if i in genuine:
+                _, rep = s.refactorize(genuine[i])
+            else:
+                _, rep = s.refactorize_forced(vals[i], forced[i])
             ev_r[i][1].record(stream)
             repiv += int(rep)
             ts = s.stats()
             tail_ms.append([ts["tail_kernel_ms"], ts["tail_repack_ms"], ts["tail_schedule_ms"],
-                            ts["tail_upload_ms"], ts["n_restart_cols"], forced[i]])
+                            ts["tail_upload_ms"], ts["n_restart_cols"], forced[i], ts["tail_passes"], int(rep)])
             ev_s[i][0].record(stream)
             s.solve(rhs[i], xs[i])
             ev_s[i][1].record(stream)
@@ -950,7 +971,7 @@ def run_ours(args, rank, world, local_rank):
             ss.solution(sy, out=raw_x[i])
             rs.residual(raw_vals[i], raw_rhs[i], raw_x[i], out=res[i])
         else:
-            s.residual(vals[i], rhs[i], xs[i], out=res[i])
+            s.residual(genuine[i] if i in genuine else vals[i], rhs[i], xs[i], out=res[i])
 
     for i in range(args.warmup):
         step(i)
@@ -1150,7 +1171,11 @@ def run_ours(args, rank, world, local_rank):
         tm = np.array(tail_ms)
         plain = [t for j, t in enumerate(t_ref) if j + args.warmup not in forced]
         line["config"]["repivot_frac"] = args.repivot_frac
+        line["config"]["repivot_mode"] = args.repivot_mode
         line["repivot"] = {"runs": len(forced), "mean_refactor_ms_all": 1e3 * float(np.mean(t_ref)),
+                           "restarts": int(tm[:, 7].sum()),
+                           "restarts_kept_every_pivot": int(((tm[:, 6] == 0) & (tm[:, 7] == 1)).sum()),
+                           "restart_refactor_ms": [1e3 * t for j, t in enumerate(t_ref) if j + args.warmup in forced],
                            "mean_refactor_ms_plain": 1e3 * float(np.mean(plain)) if plain else None,
                            "slowdown": float(np.mean(t_ref) / np.mean(plain)) if plain else None,
                            "tail_ms_mean": {"kernel": float(tm[:, 0].mean()), "repack": float(tm[:, 1].mean()),
@@ -1196,9 +1221,14 @@ def main():
     ap.add_argument("--graph", action="store_true", help="time gblu_step (CUDA-graph replay) per step")
     ap.add_argument("--repivot-frac", type=float, default=0.0,
                     help="fraction of timed runs that re-pivot at a random step (general-case protocol)")
+    ap.add_argument("--repivot-mode", default="forced", choices=["forced", "genuine"],
+                    help="forced: the check of a random step is treated as failed (the paper's protocol); "
+                         "genuine: a random step's pivot entry is made tiny so that its pivot really moves")
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
                     help="mixed: single-precision refactor + refinement in double")
     ap.add_argument("--sets", type=int, default=256, help="value sets per step of the batch workload")
+    ap.add_argument("--solve-ctas", type=int, default=-1,
+                    help="CTAs per SM of the sync-free solves (0: as many as fit; default: the library's)")
     ap.add_argument("--batch-group", type=int, default=-1,
                     help="sets per group of the batch launch (0: from the L2 size; default: the library's)")
     ap.add_argument("--seed", type=int, default=inputs.BASE_SEED + 1)

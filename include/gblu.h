@@ -117,6 +117,10 @@ typedef struct {
        many sets as fit in half of L2; >= nsets: every set at once).
        Default 0. */
     int batch_group;
+    /* CTAs (8 warps each) per SM of the sync-free solve launches; 0 = as
+       many as fit.  Fewer resident warps poll fewer unpublished values at a
+       time.  gblu_autotune measures it. */
+    int solve_ctas_per_sm;
 } gblu_opts;
 
 /* largest dense tail block of the re-factorization (shared-memory panel) */
@@ -137,7 +141,8 @@ void gblu_default_opts(gblu_opts *o);
  *   factor alpha (Section IV-B) and the warp assignment (warp_column_max)
  *   by re-factorization time, then the trailing-block rule of the solve
  *   (solve_dense_density, and solve_slices = 0 to disable it; Section
- *   V-A) by solve time.  The paper tunes these constants for its
+ *   V-A) and the resident CTAs of the sync-free solves
+ *   (solve_ctas_per_sm) by solve time.  The paper tunes these constants for its
  *   CPUs; here they are measured on the device and matrix at hand.  The
  *   factor values after the call are those of Ax_dev.  *chosen, *refactor_ms
  *   and *solve_ms (optional, host) report the kept options and their times.
@@ -188,10 +193,14 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
 /*
  * Fast re-factorization with pivot check (Section IV, Algorithms 3-5):
  * recomputes the factors of new values on the previous pattern and pivot
- * order, checking every pivot.  If a pivot fails, the unfinished columns and
- * their elimination-tree ancestors are recomputed with pivoting (preferring
- * the previous pivots) and the schedule is rebuilt; the call then returns
- * GBLU_REPIVOTED.  The result equals a factorization with pivoting that
+ * order, checking every pivot.  If a pivot fails, the restart recomputes
+ * with pivoting, preferring the previous pivots, in two stages: first the
+ * unfinished columns on the installed structure, speculating that every
+ * step keeps its preferred row, with the same check confirming each (exact
+ * when all pass: the structure is then the old one); if a check fails
+ * again, the unfinished columns and their elimination-tree ancestors go
+ * through the pivoting kernel and the schedule is rebuilt.  The call then
+ * returns GBLU_REPIVOTED.  The result equals a factorization with pivoting that
  * prefers the previous pivot sequence.  Synchronizes `stream` once (to read
  * the 4-byte check status).  *repivoted (optional, host) is set to 1 if a
  * restart happened, else 0.  A NaN or infinite pivot or entry of L fails
@@ -535,7 +544,11 @@ typedef struct {
     double tail_kernel_ms, tail_repack_ms, tail_schedule_ms, tail_upload_ms;
     int32_t tail_passes;  /* kernel passes of that run (a restart speculates
                              that the preferred pivots are kept and repeats
-                             the steps after a step that took another row) */
+                             the steps after a step that took another row);
+                             0: the restart's first stage, the unfinished
+                             columns re-factorized on the installed
+                             structure with the check, kept every pivot
+                             (tail_kernel_ms is then that stage's time) */
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

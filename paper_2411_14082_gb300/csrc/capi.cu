@@ -737,10 +737,51 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
 // Restart (Section IV-C): every column that did not finish in this
 // re-factorization, and all of its column-elimination-tree ancestors, is
 // recomputed with pivoting.
+// First stage of a restart: the unfinished columns on the installed
+// structure, speculating that every step keeps its preferred pivot (the
+// previous one), which the threshold check then confirms column by column.
+// With every check passing, the structure is the old one (it follows from
+// the pattern of A and the pivot order) and the result is exactly the
+// factorization with pivoting that prefers the previous pivots; the
+// finished columns of the failed pass keep their values.  A column whose
+// check fails again needs another pivot: *interrupted = 1, and the columns
+// finished by now stay final for the pivoting stage.
+int restart_on_structure(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+{
+    KL(launch_begin_refactor(h->ctl, st));
+    RefactorArgs a = refactor_args(h, Ax);
+    a.force_col = -1;
+    a.skip_done = 1;
+    a.task_begin = 0;
+    a.ntasks = (int32_t)h->W.task_ptr.size() - 1;
+    KL(launch_refactor_tasks(a, true, h->ref_grid, h->epoch, st));
+    CK(read_ctl(h, st));
+    CK(status_code(h));
+    *interrupted = h->hctl->interrupted;
+    return GBLU_OK;
+}
+
 int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
 {
     NvtxRange nvtx_range("restart");
     const int32_t n = h->P.n;
+    if (h->W.dense_m == 0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        std::vector<int32_t> fin0(n);
+        CU(cudaMemcpyAsync(fin0.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        int interrupted = 0;
+        CK(restart_on_structure(h, Ax, st, &interrupted));
+        if (!interrupted) {
+            int64_t redone = 0;
+            for (int32_t k = 0; k < n; k++) redone += fin0[k] != h->epoch;
+            h->n_restart_cols = redone;
+            h->tail_passes = 0;
+            h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            h->t_tail[1] = h->t_tail[2] = h->t_tail[3] = 0.0;
+            return GBLU_OK;
+        }
+    }
     std::vector<int32_t> fin(n);
     CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -778,6 +819,7 @@ void gblu_default_opts(gblu_opts *o)
     o->warp_column_max = kRefCapShort;
     o->speculate_first = 1;
     o->batch_group = 0;
+    o->solve_ctas_per_sm = 0;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -789,7 +831,7 @@ static bool opts_valid(const gblu_opts &o)
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
            o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
            o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1) &&
-           o.batch_group >= 0;
+           o.batch_group >= 0 && o.solve_ctas_per_sm >= 0;
 }
 
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
@@ -1083,6 +1125,15 @@ static SolveArgs solve_args(gblu_ctx *h, const double *LUx, const double *b_dev,
     return a;
 }
 
+// grid of the sync-free solve launches: the option's CTAs per SM, at most
+// as many as fit
+static int solve_grid(gblu_ctx *h)
+{
+    const int per = h->opts.solve_ctas_per_sm;
+    if (per <= 0 || per * h->sm_count >= h->solve_grid) return h->solve_grid;
+    return per * h->sm_count;
+}
+
 static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const double *b_dev, int64_t b_stride,
                         double *x_dev, int64_t x_stride, int32_t nsets, cudaStream_t st)
 {
@@ -1128,8 +1179,8 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
         if (div < nlev) {
             a.rows = tick + tptr[div];
             a.nrows = nrows - tptr[div];
-            KL(lower ? launch_lsolve(a, false, h->solve_grid, st)
-                     : launch_usolve(a, false, h->solve_grid, st));
+            KL(lower ? launch_lsolve(a, false, solve_grid(h), st)
+                     : launch_usolve(a, false, solve_grid(h), st));
         }
         return GBLU_OK;
     };
@@ -1798,6 +1849,17 @@ int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, doub
                 best = o;
                 bs = ts;
             }
+        }
+    }
+    for (int per : {0, 1, 2, 4}) {   // resident warps of the sync-free solves
+        if (rc != GBLU_OK || per == best.solve_ctas_per_sm) continue;
+        gblu_opts o = best;
+        o.solve_ctas_per_sm = per;
+        double tr = 0, ts = 0;
+        if ((rc = gblu_set_opts(h, &o, stream)) != GBLU_OK || (rc = measure(tr, ts)) != GBLU_OK) break;
+        if (ts < bs) {
+            best = o;
+            bs = ts;
         }
     }
     cudaEventDestroy(e0);

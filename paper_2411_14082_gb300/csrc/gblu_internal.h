@@ -183,6 +183,7 @@ struct RefactorArgsT {
     int32_t cap_short, cap_long;    // shared-memory work vector entries (warp / CTA)
     double eps;
     int32_t force_col = -1;         // evaluation aid: this column's check fails
+    int32_t skip_done = 0;          // 1: a column whose ready flag holds the epoch is final; skip it
     long long spin_limit;
     DevCtl *ctl;
 };

@@ -909,23 +909,36 @@ __device__ __forceinline__ bool trail_stage(double *tile, const double *LUx, con
     if (!__any_sync(kFull, e > s)) return false;
     for (int idx = lane; idx < kTB * kTileLd; idx += 32) tile[idx] = 0.0;
     __syncwarp();
-#pragma unroll 4
-    for (int c = 0; c < wj; c++) {
-        const int sc = __shfl_sync(kFull, s, c), ec = __shfl_sync(kFull, e, c);
-        const int64_t bc = __shfl_sync(kFull, base, c);
-        if (sc + lane < ec) {
-            const int64_t p = bc + sc + lane;
-            tile[c * kTileLd + (__ldg(t.LUi + p) - i0)] = __ldg(LUx + p);
+    // sixteen columns' loads in flight at a time (lane q: entry q of each
+    // column's segment), then their scatter into the tile
+#pragma unroll
+    for (int h = 0; h < kTB; h += 16) {
+        double v[16];
+        int r[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            const int c = h + u;
+            const int sc = __shfl_sync(kFull, s, c), ec = __shfl_sync(kFull, e, c);
+            const int64_t bc = __shfl_sync(kFull, base, c);
+            const bool has = c < wj && sc + lane < ec;
+            r[u] = has ? __ldg(t.LUi + bc + sc + lane) - i0 : -1;
+            v[u] = has ? __ldg(LUx + bc + sc + lane) : 0.0;
         }
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+            if (r[u] >= 0) tile[(h + u) * kTileLd + r[u]] = v[u];
     }
     __syncwarp();
     return true;
 }
 
 // forward slice I; true = a wait gave up
-__device__ bool ltrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, int lane)
+__device__ bool ltrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, double *dtile, int lane)
 {
     const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
+    // the slice's own unit lower triangle first: off the critical path
+    if (!trail_stage(dtile, a.LUx, t, true, I, I, lane))
+        for (int idx = lane; idx < kTB * kTileLd; idx += 32) dtile[idx] = 0.0;
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
     for (int J = 0; J < I; J++) {   // full column blocks before the slice
         if (!trail_stage(tile, a.LUx, t, true, I, J, lane)) continue;   // nothing to wait for
@@ -941,23 +954,23 @@ __device__ bool ltrail_slice(const SolveArgs &a, const TrailArgs &t, int I, doub
         }
         __syncwarp();
     }
-    if (!trail_stage(tile, a.LUx, t, true, I, I, lane))   // the slice's own unit lower triangle
-        for (int idx = lane; idx < kTB * kTileLd; idx += 32) tile[idx] = 0.0;
     __syncwarp();
     double v = 0.0;
     if (lane < w) v = __ldg(a.b + __ldg(a.piv + i)) - __ldcg(a.ext + i) - ((acc0 + acc1) + (acc2 + acc3));
     for (int c = 0; c < w - 1; c++) {
         const double yc = __shfl_sync(kFull, v, c);
-        if (lane > c && lane < w) v = fma(-tile[c * kTileLd + lane], yc, v);
+        if (lane > c && lane < w) v = fma(-dtile[c * kTileLd + lane], yc, v);
     }
     if (lane < w) st_relaxed_f64(a.y + i, v);
     return false;
 }
 
 // backward slice I; true = a wait gave up
-__device__ bool utrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, int lane)
+__device__ bool utrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, double *dtile, int lane)
 {
     const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
+    // the slice's upper triangle, diagonal included, first: off the critical path
+    trail_stage(dtile, a.LUx, t, false, I, I, lane);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
     for (int J = t.nb - 1; J > I; J--) {   // column blocks after the slice, last first
         const int j0 = t.p0 + kTB * J, wj = min(kTB, t.n - j0);
@@ -975,13 +988,12 @@ __device__ bool utrail_slice(const SolveArgs &a, const TrailArgs &t, int I, doub
         }
         __syncwarp();
     }
-    trail_stage(tile, a.LUx, t, false, I, I, lane);   // the slice's upper triangle, diagonal included
     double v = 0.0, zl = 0.0;
     if (lane < w) v = __ldcg(a.y + i) - ((acc0 + acc1) + (acc2 + acc3));
     for (int c = w - 1; c >= 0; c--) {
-        const double zc = __shfl_sync(kFull, v, c) / tile[c * kTileLd + c];
+        const double zc = __shfl_sync(kFull, v, c) / dtile[c * kTileLd + c];
         if (lane == c) zl = zc;
-        if (lane < c) v = fma(-tile[c * kTileLd + lane], zc, v);
+        if (lane < c) v = fma(-dtile[c * kTileLd + lane], zc, v);
     }
     if (lane < w) {
         st_relaxed_f64(a.z + i, zl);
@@ -998,7 +1010,7 @@ __global__ void __launch_bounds__(kTrailWarps * 32) trail_slice_kernel(SolveArgs
 {
     extern __shared__ __align__(16) double tsmem[];
     const int lane = threadIdx.x & 31;
-    double *tile = tsmem + (threadIdx.x >> 5) * (kTB * kTileLd);
+    double *tile = tsmem + (threadIdx.x >> 5) * (2 * kTB * kTileLd), *dtile = tile + kTB * kTileLd;
     const int nsets = kBatch ? a0.nsets : 1;
     const int total = t.nb * nsets;
     for (;;) {
@@ -1008,7 +1020,8 @@ __global__ void __launch_bounds__(kTrailWarps * 32) trail_slice_kernel(SolveArgs
         if (k >= total) break;
         const int s = k % nsets, q = k / nsets;
         const SolveArgs a = kBatch ? set_view(a0, s) : a0;
-        const bool stop = kLower ? ltrail_slice(a, t, q, tile, lane) : utrail_slice(a, t, t.nb - 1 - q, tile, lane);
+        const bool stop = kLower ? ltrail_slice(a, t, q, tile, dtile, lane)
+                                 : utrail_slice(a, t, t.nb - 1 - q, tile, dtile, lane);
         if (stop) break;
     }
 }
@@ -1340,7 +1353,7 @@ int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, v
     cudaStream_t st = (cudaStream_t)stream;
     const bool batch = a.nsets > 1;
     const int sets = batch ? a.nsets : 1;
-    const size_t sm = (size_t)kTrailWarps * kTB * kTileLd * sizeof(double);
+    const size_t sm = (size_t)kTrailWarps * 2 * kTB * kTileLd * sizeof(double);
     const long long total = (long long)t.nb * sets;
     long long g = (total + kTrailWarps - 1) / kTrailWarps;
     if (g > grid) g = grid;
@@ -1369,10 +1382,14 @@ int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, v
 
 int trail_setup(int *blocks_per_sm)
 {
-    const size_t sm = (size_t)kTrailWarps * kTB * kTileLd * sizeof(double);
+    const size_t sm = (size_t)kTrailWarps * 2 * kTB * kTileLd * sizeof(double);
     int a = 0, b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, trail_slice_kernel<true, false>,
-                                                                  kTrailWarps * 32, sm);
+    cudaError_t e = cudaSuccess;
+    for (auto f : {trail_slice_kernel<true, false>, trail_slice_kernel<false, false>, trail_slice_kernel<true, true>,
+                   trail_slice_kernel<false, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, trail_slice_kernel<true, false>, kTrailWarps * 32, sm);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trail_slice_kernel<false, false>, kTrailWarps * 32, sm);
     *blocks_per_sm = a < b ? a : b;

@@ -104,6 +104,7 @@ template <typename R, bool kWait, bool kDense>
 __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, int lane,
                          int epoch)
 {
+    if (a.skip_done && ld_acquire(a.finish + k) == epoch) return false;   // final already
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
     const int nU = __ldg(a.nU + k);
@@ -328,6 +329,7 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
 {
     static_assert(NW >= 2, "a group needs a leader and workers");
     constexpr int kT = NW * 32, kTw = (NW - 1) * 32;
+    if (a.skip_done && ld_acquire(a.finish + k) == epoch) return false;   // final already (uniform in the group)
     const int tid = threadIdx.x - g * kT, lane = tid & 31, warp = tid >> 5;
     const int64_t beg = __ldg(a.LUp + k);
     const int len = (int)(__ldg(a.LUp + k + 1) - beg);
