@@ -81,10 +81,6 @@ struct gblu_ctx {
     gblu_opts opts{};
     int sm_count = 0;
     int l2_bytes = 0;
-    // first task of the pipeline part from which every task is one column
-    // longer than kRefCapLong: those run in a launch of their own with the
-    // larger work vector (ntasks: none)
-    int32_t long_begin = 0;
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_grid = 0;
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
@@ -307,18 +303,6 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     h->t_tail[2] = std::chrono::duration<double, std::milli>(t_u - t_s).count();
     for (int32_t v : h->W.amap)
         if (v < 0) return fail(GBLU_ERR_INTERNAL, "an entry of A is outside the factor pattern");
-    {
-        const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
-        int32_t lb = ntask;
-        while (lb > h->W.level_task_ptr[h->W.div_level]) {
-            const int32_t t = lb - 1, c0 = h->W.task_ptr[t];
-            if (h->W.task_ptr[t + 1] - c0 != 1) break;
-            const int32_t k = h->W.task_cols[c0];
-            if (h->S.LUp[k + 1] - h->S.LUp[k] <= kRefCapLong) break;
-            lb = t;
-        }
-        h->long_begin = lb;
-    }
     const int32_t n = h->S.n;
     const size_t nnz = (size_t)h->S.nnz();
     CK(upload(h, h->LUp, h->S.LUp, st));
@@ -421,19 +405,10 @@ int issue_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int ep)
         KL(launch_refactor_tasks(a, false, 0, ep, st));
     }
     const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
-    const int32_t lb = h->W.dense_m > 0 ? ntask : h->long_begin;
-    if (ltp[div] < lb) {                  // pipeline mode: one persistent launch
+    if (ltp[div] < ntask) {               // pipeline mode: one persistent launch
         a.task_begin = ltp[div];
-        a.ntasks = lb - ltp[div];
+        a.ntasks = ntask - ltp[div];
         KL(launch_refactor_tasks(a, true, h->ref_grid, ep, st));
-    }
-    if (lb < ntask) {                     // the long columns at the end, work vectors in shared memory
-        a.task_begin = lb;
-        a.ntasks = ntask - lb;
-        a.cap_long = kRefCapLongMax;
-        KL(launch_zero_ticket(&h->ctl->ticket, st));
-        KL(launch_refactor_tasks(a, true, h->sm_count, ep, st));
-        a.cap_long = kRefCapLong;
     }
     if (h->W.dense_m > 0) {   // the dense tail: blocked LU of the block, then scatter
         DenseArgs2 d{};
@@ -1298,19 +1273,11 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
         KL(launch_refactor_batch(h->bargs.p, a0, nsets, false, 0, h->epoch, h->bticket.p, st, nsets));
     }
     const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
-    const int32_t lb = h->long_begin;
-    if (ltp[div] < lb) {                  // pipeline mode
+    if (ltp[div] < ntask) {               // pipeline mode
         a0.task_begin = ltp[div];
-        a0.ntasks = lb - ltp[div];
+        a0.ntasks = ntask - ltp[div];
         KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->ref_grid, h->epoch, h->bticket.p, st,
                                  batch_group(h, nsets)));
-    }
-    if (lb < ntask) {                     // the long columns: every set at once, larger work vectors
-        a0.task_begin = lb;
-        a0.ntasks = ntask - lb;
-        KL(launch_zero_ticket(h->bticket.p, st));
-        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->sm_count, h->epoch, h->bticket.p, st, nsets,
-                                 kRefCapLongMax));
     }
     h->bctl_host.resize(nsets);
     CU(cudaMemcpyAsync(h->bctl_host.data(), h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, st));
@@ -1687,19 +1654,11 @@ static int capture_step_batch(gblu_ctx *h, int32_t nsets, const double *Ax_dev, 
             KL(launch_refactor_batch(h->bgargs.p, a0, nsets, false, 0, 1, h->bticket.p, gs, nsets));
         }
         const int32_t ntask = (int32_t)h->W.task_ptr.size() - 1;
-        const int32_t lb = h->long_begin;
-        if (ltp[div] < lb) {
+        if (ltp[div] < ntask) {
             a0.task_begin = ltp[div];
-            a0.ntasks = lb - ltp[div];
+            a0.ntasks = ntask - ltp[div];
             KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->ref_grid, 1, h->bticket.p, gs,
                                      batch_group(h, nsets)));
-        }
-        if (lb < ntask) {
-            a0.task_begin = lb;
-            a0.ntasks = ntask - lb;
-            KL(launch_zero_ticket(h->bticket.p, gs));
-            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->sm_count, 1, h->bticket.p, gs, nsets,
-                                     kRefCapLongMax));
         }
         CU(cudaMemcpyAsync(h->bgctl_host, h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, gs));
         return solve_values(h, LUx_dev, lu_stride, b_dev, b_stride, x_dev, x_stride, nsets, gs);

@@ -245,8 +245,6 @@ struct SolveArgs {
 
 // kernel launchers (kernels.cu); each returns a cudaError_t as int
 int launch_begin_refactor(DevCtl *ctl, void *stream);
-// a ticket counter back to 0 (before a second persistent launch)
-int launch_zero_ticket(int32_t *ticket, void *stream);
 int refactor_setup(int cap_long, int *blocks_per_sm);
 int refactor_setup_f32(int cap_long, int *blocks_per_sm);
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream);
@@ -254,10 +252,8 @@ int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int ep
 int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int grid, int epoch, void *stream);
 // batch of value sets on one structure (sets_dev: one argument block per set)
 int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
-// cap > 0: a launch of long columns only, with that work-vector capacity
-// (up to kRefCapLongMax; one CTA per SM)
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
-                          int grid, int epoch, int32_t *ticket, void *stream, int group, int cap = 0);
+                          int grid, int epoch, int32_t *ticket, void *stream, int group);
 int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
                           int npairs, int grid, int epoch, int32_t *ticket, void *stream);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
@@ -330,7 +326,6 @@ int trail_setup(int *blocks_per_sm);
 constexpr int kRefThreads = 256;       // 8 warps per refactor CTA
 constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short columns)
 constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
-constexpr int kRefCapLongMax = 16384;          // launches of long columns only, 192 KB
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
 constexpr int kSolveBlockRows = 32;   // rows of one block of the sparse solves

@@ -680,15 +680,13 @@ __device__ __forceinline__ int group_task(long long t, int ntasks, int nsets, in
 template <bool kWait>
 __global__ void __launch_bounds__(kThreads, 2)
 refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
-                      int32_t *ticket, const SetTask *order, int group, int cap_override)
+                      int32_t *ticket, const SetTask *order, int group)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_skip;
     __shared__ GroupShared<double> s_grp[2];
-    // cap_override > 0: the launch's work-vector capacity (long columns)
-    const int cap = cap_override > 0 ? cap_override : sets[0].cap_long;
     double *xs = reinterpret_cast<double *>(smem);
-    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)cap * sizeof(double));
+    int32_t *rs = reinterpret_cast<int32_t *>(smem + (size_t)sets[0].cap_long * sizeof(double));
     // ticket t: task t / nsets of set t % nsets, or, with an order array
     // (sets of different patterns), the (set, task) pair order[t]
     const long long total = order ? (long long)ntasks : (long long)ntasks * nsets;
@@ -712,8 +710,7 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
         const int task = order ? __ldg(&order[t].task) : task_begin + group_task(t, ntasks, nsets, group);
         // a local copy: stores through the work vector cannot alias it, so its
         // fields stay in registers instead of being reloaded from memory
-        RefactorArgs as = sets[si];
-        as.cap_long = cap;
+        const RefactorArgs as = sets[si];
         run_task<double, kWait, false>(as, task, xs, rs, epoch, s_grp);
     }
 }
@@ -778,13 +775,6 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
         e = cudaFuncSetAttribute(refactor_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(refactor_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    // launches of long columns only may use a larger work vector
-    const size_t big = (size_t)kRefCapLongMax * (sizeof(double) + sizeof(int32_t));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
     if (e != cudaSuccess) return (int)e;
     int b1 = 0, b2 = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<double, true, false>, kThreads, sm);
@@ -792,14 +782,6 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<double, true, true>, kThreads, sm);
     *blocks_per_sm = b1 < b2 ? b1 : b2;
     return (int)e;
-}
-
-__global__ void zero_ticket_kernel(int32_t *ticket) { *ticket = 0; }
-
-int launch_zero_ticket(int32_t *ticket, void *stream)
-{
-    zero_ticket_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ticket);
-    return (int)cudaGetLastError();
 }
 
 int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream)
@@ -810,23 +792,21 @@ int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream)
 }
 
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
-                          int grid, int epoch, int32_t *ticket, void *stream, int group, int cap)
+                          int grid, int epoch, int32_t *ticket, void *stream, int group)
 {
     if (a0.ntasks <= 0 || nsets <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
     if (group < 1 || group > nsets) group = nsets;
     if (pipeline) {
-        RefactorArgs ac = a0;
-        if (cap > 0) ac.cap_long = cap;
-        refactor_batch_kernel<true><<<grid, kThreads, task_smem(ac), st>>>(sets_dev, nsets, a0.task_begin,
+        refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, a0.task_begin,
                                                                            a0.ntasks, epoch, 1, ticket, nullptr,
-                                                                           group, cap);
+                                                                           group);
     } else {
         // a level launch has no waits: one group holding every set
         const long long blocks = (long long)a0.ntasks * nsets;
         if (blocks > INT_MAX) return (int)cudaErrorInvalidValue;
         refactor_batch_kernel<false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
-            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets, 0);
+            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets);
     }
     return (int)cudaGetLastError();
 }
@@ -839,7 +819,7 @@ int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
     int g = (nsets + 255) / 256;
     begin_multi_kernel<<<g, 256, 0, st>>>(sets_dev, nsets, ticket);
     refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
-                                                                       order_dev, 1, 0);
+                                                                       order_dev, 1);
     return (int)cudaGetLastError();
 }
 
