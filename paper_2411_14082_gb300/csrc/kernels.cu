@@ -125,8 +125,12 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
             if (tid == 0) {
                 long long it = 0;
                 while (ld_acquire(a.done + jd) != epoch) {
-                    if (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status)) { s_stop = 1; break; }
-                    if (++it > a.spin_limit) {
+                    ++it;
+                    if ((it & 63) == 0 && (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status))) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if (it > a.spin_limit) {
                         set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
                         a.ctl->where = 3;
                         a.ctl->where_k = k;
@@ -245,8 +249,12 @@ __device__ bool tail_column(const TailArgs &a, int k, double *x, int32_t *mark,
             if (tid == 0) {
                 long long it = 0;
                 while (ld_acquire(a.done + found) != epoch) {
-                    if (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status)) { s_stop = 1; break; }
-                    if (++it > a.spin_limit) {
+                    ++it;
+                    if ((it & 63) == 0 && (ld_volatile(&a.ctl->abort_tail) || ld_volatile(&a.ctl->status))) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if (it > a.spin_limit) {
                         set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
                         a.ctl->where = 2;
                         a.ctl->where_k = k;
@@ -505,7 +513,9 @@ __device__ __forceinline__ bool await_value(const double *v, int j, const SolveA
     unsigned long long b = ld_relaxed_u64(v + j);
     long long it = 0;
     while (b == kSentinel) {
-        if (++it > a.spin_limit || ld_volatile(&a.ctl->status)) {
+        // the shared status word is read only every 64 polls: thousands of
+        // waiting lanes polling one address would queue on its L2 slice
+        if (++it > a.spin_limit || ((it & 63) == 0 && ld_volatile(&a.ctl->status))) {
             set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
             a.ctl->where = site;
             a.ctl->where_k = row;
@@ -843,7 +853,7 @@ __global__ void begin_multi_solve_kernel(const SolveArgs *lo, const SolveArgs *u
 // and the sums of rows < p0 over its columns follow in a parallel launch.
 constexpr int kTB = kTrailRows;
 constexpr int kTileLd = kTB + 1;      // padded leading dimension of a tile
-constexpr int kTrailWarps = 4;        // slices (warps) per CTA
+constexpr int kTrailWarps = 4;        // warps per slice (one CTA)
 
 // out = sum over CSR entries [e0, e1) of LUx[slot[e]] * v[col[e]], one warp,
 // four entries per lane in flight
@@ -932,97 +942,108 @@ __device__ __forceinline__ bool trail_stage(double *tile, const double *LUx, con
     return true;
 }
 
-// forward slice I; true = a wait gave up
-__device__ bool ltrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, double *dtile, int lane)
+// One slice per CTA of kTrailWarps warps: warp w takes the column blocks
+// J = w, w + 4, ... of the slice's rectangle (forward: J < I ascending;
+// backward: J > I descending), staging the next block's tile before it
+// waits for the current one's values; its four partial sums per row go to
+// shared memory, and warp 0 adds them in a fixed order (so the result does
+// not depend on timing) and finishes the slice's triangle.  true = a wait
+// gave up.
+template <bool kLower>
+__device__ bool trail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *wt, double *dtile, double *part,
+                            int *s_bad, int warp, int lane)
 {
     const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
-    // the slice's own unit lower triangle first: off the critical path
-    if (!trail_stage(dtile, a.LUx, t, true, I, I, lane))
+    if (warp == 0 && !trail_stage(dtile, a.LUx, t, kLower, I, I, lane))   // off the critical path
         for (int idx = lane; idx < kTB * kTileLd; idx += 32) dtile[idx] = 0.0;
+    // this warp's blocks: J(m) = first + step * m while in range
+    const int first = kLower ? warp : t.nb - 1 - warp, step = kLower ? kTrailWarps : -kTrailWarps;
+    auto in_range = [&](int J) { return kLower ? J < I : J > I; };
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    for (int J = 0; J < I; J++) {   // full column blocks before the slice
-        if (!trail_stage(tile, a.LUx, t, true, I, J, lane)) continue;   // nothing to wait for
-        double yq;
-        const bool ok = await_value(a.y, t.p0 + kTB * J + lane, a, 7, i0, yq);
-        if (!__all_sync(kFull, ok)) return true;
+    bool ok = true;
+    int J = first;
+    bool have = in_range(J) && trail_stage(wt, a.LUx, t, kLower, I, J, lane);
+    for (int m = 0; in_range(J) && ok; m++) {
+        const int Jn = J + step;
+        double *cur = wt + (m & 1) * (kTB * kTileLd), *nxt = wt + ((m + 1) & 1) * (kTB * kTileLd);
+        const bool have_n = in_range(Jn) && trail_stage(nxt, a.LUx, t, kLower, I, Jn, lane);
+        if (have) {
+            const int j0 = t.p0 + kTB * J, wj = min(kTB, t.n - j0);
+            double vq = 0.0;
+            bool got = true;
+            if (lane < wj) got = await_value(kLower ? a.y : a.z, j0 + lane, a, kLower ? 7 : 8, i0, vq);
+            ok = __all_sync(kFull, got);
+            if (ok) {
 #pragma unroll
-        for (int c = 0; c < kTB; c += 4) {
-            acc0 = fma(tile[(c + 0) * kTileLd + lane], __shfl_sync(kFull, yq, c + 0), acc0);
-            acc1 = fma(tile[(c + 1) * kTileLd + lane], __shfl_sync(kFull, yq, c + 1), acc1);
-            acc2 = fma(tile[(c + 2) * kTileLd + lane], __shfl_sync(kFull, yq, c + 2), acc2);
-            acc3 = fma(tile[(c + 3) * kTileLd + lane], __shfl_sync(kFull, yq, c + 3), acc3);
+                for (int c = 0; c < kTB; c += 4) {   // columns past wj hold zero tiles and vq = 0
+                    acc0 = fma(cur[(c + 0) * kTileLd + lane], __shfl_sync(kFull, vq, c + 0), acc0);
+                    acc1 = fma(cur[(c + 1) * kTileLd + lane], __shfl_sync(kFull, vq, c + 1), acc1);
+                    acc2 = fma(cur[(c + 2) * kTileLd + lane], __shfl_sync(kFull, vq, c + 2), acc2);
+                    acc3 = fma(cur[(c + 3) * kTileLd + lane], __shfl_sync(kFull, vq, c + 3), acc3);
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        have = have_n;
+        J = Jn;
     }
-    __syncwarp();
-    double v = 0.0;
-    if (lane < w) v = __ldg(a.b + __ldg(a.piv + i)) - __ldcg(a.ext + i) - ((acc0 + acc1) + (acc2 + acc3));
-    for (int c = 0; c < w - 1; c++) {
-        const double yc = __shfl_sync(kFull, v, c);
-        if (lane > c && lane < w) v = fma(-dtile[c * kTileLd + lane], yc, v);
+    part[warp * 32 + lane] = (acc0 + acc1) + (acc2 + acc3);
+    if (!ok && lane == 0) *s_bad = 1;
+    __syncthreads();
+    if (*s_bad) return true;
+    if (warp == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < kTrailWarps; q++) sum += part[q * 32 + lane];
+        if (kLower) {
+            double v = 0.0;
+            if (lane < w) v = __ldg(a.b + __ldg(a.piv + i)) - __ldcg(a.ext + i) - sum;
+            for (int c = 0; c < w - 1; c++) {
+                const double yc = __shfl_sync(kFull, v, c);
+                if (lane > c && lane < w) v = fma(-dtile[c * kTileLd + lane], yc, v);
+            }
+            if (lane < w) st_relaxed_f64(a.y + i, v);
+        } else {
+            double v = 0.0, zl = 0.0;
+            if (lane < w) v = __ldcg(a.y + i) - sum;
+            for (int c = w - 1; c >= 0; c--) {
+                const double zc = __shfl_sync(kFull, v, c) / dtile[c * kTileLd + c];
+                if (lane == c) zl = zc;
+                if (lane < c) v = fma(-dtile[c * kTileLd + lane], zc, v);
+            }
+            if (lane < w) {
+                st_relaxed_f64(a.z + i, zl);
+                a.x[__ldg(a.Q + i)] = zl;
+            }
+        }
     }
-    if (lane < w) st_relaxed_f64(a.y + i, v);
+    __syncthreads();   // tiles and partial sums are reused by the next slice
     return false;
 }
 
-// backward slice I; true = a wait gave up
-__device__ bool utrail_slice(const SolveArgs &a, const TrailArgs &t, int I, double *tile, double *dtile, int lane)
-{
-    const int i0 = t.p0 + kTB * I, w = min(kTB, t.n - i0), i = i0 + lane;
-    // the slice's upper triangle, diagonal included, first: off the critical path
-    trail_stage(dtile, a.LUx, t, false, I, I, lane);
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    for (int J = t.nb - 1; J > I; J--) {   // column blocks after the slice, last first
-        const int j0 = t.p0 + kTB * J, wj = min(kTB, t.n - j0);
-        if (!trail_stage(tile, a.LUx, t, false, I, J, lane)) continue;   // nothing to wait for
-        double zq = 0.0;
-        bool ok = true;
-        if (lane < wj) ok = await_value(a.z, j0 + lane, a, 8, i0, zq);
-        if (!__all_sync(kFull, ok)) return true;
-#pragma unroll
-        for (int c = 0; c < kTB; c += 4) {   // columns past wj hold zero tiles and zq = 0
-            acc0 = fma(tile[(c + 0) * kTileLd + lane], __shfl_sync(kFull, zq, c + 0), acc0);
-            acc1 = fma(tile[(c + 1) * kTileLd + lane], __shfl_sync(kFull, zq, c + 1), acc1);
-            acc2 = fma(tile[(c + 2) * kTileLd + lane], __shfl_sync(kFull, zq, c + 2), acc2);
-            acc3 = fma(tile[(c + 3) * kTileLd + lane], __shfl_sync(kFull, zq, c + 3), acc3);
-        }
-        __syncwarp();
-    }
-    double v = 0.0, zl = 0.0;
-    if (lane < w) v = __ldcg(a.y + i) - ((acc0 + acc1) + (acc2 + acc3));
-    for (int c = w - 1; c >= 0; c--) {
-        const double zc = __shfl_sync(kFull, v, c) / dtile[c * kTileLd + c];
-        if (lane == c) zl = zc;
-        if (lane < c) v = fma(-dtile[c * kTileLd + lane], zc, v);
-    }
-    if (lane < w) {
-        st_relaxed_f64(a.z + i, zl);
-        a.x[__ldg(a.Q + i)] = zl;
-    }
-    return false;
-}
-
-// slices handed out by ticket in their dependency order (forward ascending,
-// backward descending); in a batch ticket t is slice t / nsets of set
-// t % nsets, so a warp only waits on smaller tickets
+// slices handed out by ticket (one per CTA) in their dependency order
+// (forward ascending, backward descending); in a batch ticket t is slice
+// t / nsets of set t % nsets, so a CTA only waits on smaller tickets
 template <bool kLower, bool kBatch>
 __global__ void __launch_bounds__(kTrailWarps * 32) trail_slice_kernel(SolveArgs a0, TrailArgs t)
 {
     extern __shared__ __align__(16) double tsmem[];
-    const int lane = threadIdx.x & 31;
-    double *tile = tsmem + (threadIdx.x >> 5) * (2 * kTB * kTileLd), *dtile = tile + kTB * kTileLd;
+    __shared__ double part[kTrailWarps * 32];
+    __shared__ int s_k, s_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *dtile = tsmem, *wt = tsmem + kTB * kTileLd + warp * (2 * kTB * kTileLd);
     const int nsets = kBatch ? a0.nsets : 1;
     const int total = t.nb * nsets;
+    if (threadIdx.x == 0) s_bad = 0;
     for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(kLower ? &a0.ctl->ticket_tl : &a0.ctl->ticket_tu, 1);
-        k = __shfl_sync(kFull, k, 0);
+        if (threadIdx.x == 0) s_k = atomicAdd(kLower ? &a0.ctl->ticket_tl : &a0.ctl->ticket_tu, 1);
+        __syncthreads();
+        const int k = s_k;
+        __syncthreads();
         if (k >= total) break;
         const int s = k % nsets, q = k / nsets;
         const SolveArgs a = kBatch ? set_view(a0, s) : a0;
-        const bool stop = kLower ? ltrail_slice(a, t, q, tile, dtile, lane)
-                                 : utrail_slice(a, t, t.nb - 1 - q, tile, dtile, lane);
-        if (stop) break;
+        if (trail_slice<kLower>(a, t, kLower ? q : t.nb - 1 - q, wt, dtile, part, &s_bad, warp, lane)) break;
     }
 }
 
@@ -1353,9 +1374,9 @@ int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, v
     cudaStream_t st = (cudaStream_t)stream;
     const bool batch = a.nsets > 1;
     const int sets = batch ? a.nsets : 1;
-    const size_t sm = (size_t)kTrailWarps * 2 * kTB * kTileLd * sizeof(double);
+    const size_t sm = (size_t)(2 * kTrailWarps + 1) * kTB * kTileLd * sizeof(double);
     const long long total = (long long)t.nb * sets;
-    long long g = (total + kTrailWarps - 1) / kTrailWarps;
+    long long g = total;   // one slice per CTA
     if (g > grid) g = grid;
     if (g < 1) g = 1;
     if (lower) {
@@ -1382,7 +1403,7 @@ int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, v
 
 int trail_setup(int *blocks_per_sm)
 {
-    const size_t sm = (size_t)kTrailWarps * 2 * kTB * kTileLd * sizeof(double);
+    const size_t sm = (size_t)(2 * kTrailWarps + 1) * kTB * kTileLd * sizeof(double);
     int a = 0, b = 0;
     cudaError_t e = cudaSuccess;
     for (auto f : {trail_slice_kernel<true, false>, trail_slice_kernel<false, false>, trail_slice_kernel<true, true>,

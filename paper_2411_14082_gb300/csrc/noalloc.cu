@@ -83,7 +83,8 @@ __device__ bool wait_flag(const int32_t *flag, Scratch s)
 {
     long long it = 0;
     while (ld_acquire(flag) != 1) {
-        if (++it > s.spin_limit || *(volatile int32_t *)(s.ctl + 2) != 0) {
+        // the shared status word is read only every 64 polls
+        if (++it > s.spin_limit || ((it & 63) == 0 && *(volatile int32_t *)(s.ctl + 2) != 0)) {
             atomicCAS(s.ctl + 2, 0, GBLU_ERR_DEVICE_TIMEOUT);
             return false;
         }

@@ -152,8 +152,11 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
             if (run == 0) {
                 long long it = 0;
                 while (ld_acquire(a.finish + rows[t]) != epoch) {
-                    if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return true;
-                    if (++it > a.spin_limit) {
+                    // the shared control words are read only every 32 polls
+                    ++it;
+                    if ((it & 31) == 0 && (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)))
+                        return true;
+                    if (it > a.spin_limit) {
                         if (lane == 0) {
                             set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
                             a.ctl->where = 1;
@@ -397,8 +400,11 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
                 if (kWait && run == 0) {
                     long long it = 0;
                     while (ld_acquire(a.finish + rows[t]) != epoch) {
-                        if (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)) return false;
-                        if (++it > a.spin_limit) {
+                        // the shared control words are read only every 32 polls
+                        ++it;
+                        if ((it & 31) == 0 && (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status)))
+                            return false;
+                        if (it > a.spin_limit) {
                             if (lane == 0) {
                                 set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
                                 a.ctl->where = 1;
