@@ -301,6 +301,11 @@ def run_batch(args, rank, world, local_rank):
     s.factorize(torch.from_numpy(w["Ax0"]).cuda(dev))
     if args.batch_group >= 0:
         s.set_opts(batch_group=args.batch_group)
+    # a set whose check fails in the batch is solved again on a handle of its
+    # own (restart with pivoting), inside the step, as the batch API asks
+    redo = gblu.Solver(dev)
+    redo.analyze(n, w["Ap"], w["Ai"], w["Q"])
+    redo.factorize(torch.from_numpy(w["Ax0"]).cuda(dev))
     st = s.stats()
     vals = torch.from_numpy(np.stack(w["vals"])).cuda(dev)
     rhs = torch.from_numpy(np.stack(w["rhs"])).cuda(dev)
@@ -327,6 +332,9 @@ def run_batch(args, rank, world, local_rank):
             _, failed = s.refactorize_batch(vals, LUx)
             ev[i][1].record(stream)
             s.solve_batch(LUx, rhs, xs)
+        for k in np.nonzero(failed)[0]:
+            redo.refactorize(vals[int(k)])
+            redo.solve(rhs[int(k)], xs[int(k)])
         ev[i][2].record(stream)
         nfail += int(failed.sum())
     torch.cuda.synchronize(dev)
@@ -354,10 +362,13 @@ def run_batch(args, rank, world, local_rank):
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
         if args.graph:
-            s.refactorize_batch(vals, LUx)
+            _, failed = s.refactorize_batch(vals, LUx)
             s.solve_batch(LUx, rhs, xs)
         else:
-            s.step_batch(vals, LUx, rhs, xs)
+            failed = s.step_batch(vals, LUx, rhs, xs)
+        for k in np.nonzero(failed)[0]:
+            redo.refactorize(vals[int(k)])
+            redo.solve(rhs[int(k)], xs[int(k)])
     a1.record(stream)
     torch.cuda.synchronize(dev)
     alt = {"form": other, "value": args.sets * alt_steps / (a0.elapsed_time(a1) / 1e3), "unit": METRIC,
@@ -386,6 +397,8 @@ def run_batch(args, rank, world, local_rank):
                            "eager launches (gblu_refactorize_batch + gblu_solve_batch)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "max_rel_residual": worst, "residual_ok": bool(worst <= 1e-12), "failed_sets": nfail,
+        "failed_sets_note": "sets whose check failed were re-factorized with pivoting on a second handle "
+                            "inside the step (their time is in solve_batch)",
         "phases_ms": {"refactor_batch": 1e3 * float(np.mean(t_rf)), "solve_batch": 1e3 * float(np.mean(t_sv)),
                       "note": "graph replay: refactor_batch = the whole replayed step" if args.graph else None,
                       "wall_per_step": 1e3 * elapsed / args.steps},

@@ -596,14 +596,21 @@ __device__ __forceinline__ bool lrow_ext(const SolveArgs &a, int i, int q, int l
 }
 
 // forward block finish: lane p < w holds e = the outside sum of row f+p
-__device__ __forceinline__ void lblock_finish(const SolveArgs &a, int f, int w, int lane, double e)
+// the block's unit lower triangle: lane p < w holds row f+p's entries
+// L(f+p, f .. f+p-1), its last p entries (loaded before the block's values
+// are awaited, off the dependency chain)
+__device__ __forceinline__ void lblock_load(const SolveArgs &a, int f, int w, int lane, double (&tv)[kBR - 1])
 {
-    // row f+p's last p entries are L(f+p, f .. f+p-1)
     const int64_t rend = lane < w ? __ldg(a.Lrp + f + lane + 1) - lane : 0;
-    double tv[kBR - 1];
 #pragma unroll
     for (int d = 0; d < kBR - 1; d++)
         tv[d] = (d < lane && lane < w) ? __ldg(a.LUx + __ldg(a.Lslot + rend + d)) : 0.0;
+}
+
+// forward block finish: lane p < w holds e = the outside sum of row f+p
+__device__ __forceinline__ void lblock_solve(const SolveArgs &a, int f, int w, int lane, double e,
+                                             const double (&tv)[kBR - 1])
+{
     double v = lane < w ? __ldg(a.b + __ldg(a.piv + f + lane)) - e : 0.0;
 #pragma unroll
     for (int d = 0; d < kBR - 1; d++) {
@@ -613,6 +620,13 @@ __device__ __forceinline__ void lblock_finish(const SolveArgs &a, int f, int w, 
         }
     }
     if (lane < w) st_relaxed_f64(a.y + f + lane, v);
+}
+
+__device__ __forceinline__ void lblock_finish(const SolveArgs &a, int f, int w, int lane, double e)
+{
+    double tv[kBR - 1];
+    lblock_load(a, f, w, lane, tv);
+    lblock_solve(a, f, w, lane, e, tv);
 }
 
 // backward: sum over the entries of row i outside its block (all but its
@@ -649,21 +663,28 @@ __device__ __forceinline__ bool urow_ext(const SolveArgs &a, int i, int q, int w
     return __all_sync(kFull, ok);
 }
 
-// backward block finish: lane p < w holds e = the outside sum of row f+p
-__device__ __forceinline__ void ublock_finish(const SolveArgs &a, int f, int w, int lane, double e)
+// the block's upper triangle: lane p < w holds row f+p's entries
+// U(f+p, f+p+1 .. f+w-1) (its first w-1-p entries) and the reciprocal of
+// its diagonal, computed by every lane at once (a division per step of the
+// substitution would sit on the dependency chain)
+__device__ __forceinline__ void ublock_load(const SolveArgs &a, int f, int w, int lane, double (&tu)[kBR], double &rd)
 {
-    // row f+p's first w-1-p entries are U(f+p, f+p+1 .. f+w-1)
     const int64_t rbeg = lane < w ? __ldg(a.Urp + f + lane) - lane - 1 : 0;
-    double tu[kBR];
 #pragma unroll
     for (int d = 0; d < kBR; d++)
         tu[d] = (lane < d && d < w) ? __ldg(a.LUx + __ldg(a.Uslot + rbeg + d)) : 0.0;
-    const double dg = lane < w ? __ldg(a.LUx + __ldg(a.Udiag + f + lane)) : 1.0;
+    rd = lane < w ? 1.0 / __ldg(a.LUx + __ldg(a.Udiag + f + lane)) : 1.0;
+}
+
+// backward block finish: lane p < w holds e = the outside sum of row f+p
+__device__ __forceinline__ void ublock_solve(const SolveArgs &a, int f, int w, int lane, double e,
+                                             const double (&tu)[kBR], double rd)
+{
     double v = lane < w ? __ldcg(a.y + f + lane) - e : 0.0, zl = 0.0;
 #pragma unroll
     for (int d = kBR - 1; d >= 0; d--) {
         if (d < w) {
-            const double zd = __shfl_sync(kFull, v, d) / __shfl_sync(kFull, dg, d);
+            const double zd = __shfl_sync(kFull, v, d) * __shfl_sync(kFull, rd, d);
             if (lane == d) zl = zd;
             if (lane < d) v = fma(-tu[d], zd, v);
         }
@@ -672,6 +693,13 @@ __device__ __forceinline__ void ublock_finish(const SolveArgs &a, int f, int w, 
         st_relaxed_f64(a.z + f + lane, zl);
         a.x[__ldg(a.Q + f + lane)] = zl;
     }
+}
+
+__device__ __forceinline__ void ublock_finish(const SolveArgs &a, int f, int w, int lane, double e)
+{
+    double tu[kBR], rd;
+    ublock_load(a, f, w, lane, tu, rd);
+    ublock_solve(a, f, w, lane, e, tu, rd);
 }
 
 // Batches (gblu_solve_batch): the same kernels over nsets right-hand sides
@@ -746,16 +774,20 @@ __device__ __forceinline__ bool lsolve_sf_row(const SolveArgs &a, int t, int lan
     const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
     const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
     double s;
-    if (!lrow_ext(a, i, q, lane, true, s)) return true;
     if (q < w - 1) {
+        if (!lrow_ext(a, i, q, lane, true, s)) return true;
         if (lane == 0) st_relaxed_f64(a.ext + i, s);
         return false;
     }
-    double e = s;   // the last row finishes the block
+    // the last row finishes the block; its triangle is loaded first
+    double tv[kBR - 1];
+    lblock_load(a, f, w, lane, tv);
+    if (!lrow_ext(a, i, q, lane, true, s)) return true;
+    double e = s;
     bool ok = true;
     if (lane < w - 1) ok = await_value(a.ext, f + lane, a, 5, f + lane, e);
     if (!__all_sync(kFull, ok)) return true;
-    lblock_finish(a, f, w, lane, e);
+    lblock_solve(a, f, w, lane, e, tv);
     return false;
 }
 
@@ -764,16 +796,20 @@ __device__ __forceinline__ bool usolve_sf_row(const SolveArgs &a, int t, int lan
     const int i = __ldg(a.rows + t), b = __ldg(a.rb + i);
     const int f = __ldg(a.bs + b), w = __ldg(a.bs + b + 1) - f, q = i - f;
     double s;
-    if (!urow_ext(a, i, q, w, lane, true, s)) return true;
     if (q > 0) {
+        if (!urow_ext(a, i, q, w, lane, true, s)) return true;
         if (lane == 0) st_relaxed_f64(a.ext + i, s);
         return false;
     }
-    double e = s;   // the first row finishes the block
+    // the first row finishes the block; its triangle is loaded first
+    double tu[kBR], rd;
+    ublock_load(a, f, w, lane, tu, rd);
+    if (!urow_ext(a, i, q, w, lane, true, s)) return true;
+    double e = s;
     bool ok = true;
     if (lane >= 1 && lane < w) ok = await_value(a.ext, f + lane, a, 6, f + lane, e);
     if (!__all_sync(kFull, ok)) return true;
-    ublock_finish(a, f, w, lane, e);
+    ublock_solve(a, f, w, lane, e, tu, rd);
     return false;
 }
 
@@ -1006,8 +1042,10 @@ __device__ bool trail_slice(const SolveArgs &a, const TrailArgs &t, int I, doubl
         } else {
             double v = 0.0, zl = 0.0;
             if (lane < w) v = __ldcg(a.y + i) - sum;
+            // reciprocals of the diagonal by every lane at once, off the chain
+            const double rd = lane < w ? 1.0 / dtile[lane * kTileLd + lane] : 1.0;
             for (int c = w - 1; c >= 0; c--) {
-                const double zc = __shfl_sync(kFull, v, c) / dtile[c * kTileLd + c];
+                const double zc = __shfl_sync(kFull, v, c) * __shfl_sync(kFull, rd, c);
                 if (lane == c) zl = zc;
                 if (lane < c) v = fma(-dtile[c * kTileLd + lane], zc, v);
             }
