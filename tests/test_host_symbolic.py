@@ -442,3 +442,38 @@ def test_solve_partition_rule():
         if want < n and count_from[want] < min_entries:
             want = n
         assert p0 == want
+
+
+def test_solve_partition_hand_worked_profiles():
+    """Section V-A's rule on profiles worked out by hand (not by a copy of
+    the loops): P0, then the slice cuts, including the edge cases P0 = n-2,
+    an empty triangle and a minimum count above the total.
+
+    Profile: strict per-column counts [0, 1, 1, 2, 1, 0] give
+    count_from = [5, 5, 4, 3, 1, 0, 0]; 70% of 5 is 3.5, so scanning p from
+    n-1 down, p = 2 (4 entries) is the first position that holds enough.
+    With min_entries 5 it is p = 1; with min_entries 6 no block qualifies."""
+    cf = np.array([5, 5, 4, 3, 1, 0, 0], np.int64)
+    rowlen = np.array([1, 2, 3, 1, 2, 1], np.int64)
+    # rows 2..5 hold 3 + 1 + 2 + 1 = 7 entries; two slices of 3.5: the first
+    # closes at row 3 (3, then 4 >= 3.5), the last runs to the end
+    assert_p0_cut(cf, rowlen, 0.0, 4, 2, 10, 2, [2, 4, 6])
+    # at most one row per slice
+    assert_p0_cut(cf, rowlen, 0.0, 4, 2, 1, 2, [2, 3, 4, 5, 6])
+    assert_p0_cut(cf, rowlen, 0.0, 5, 1, 10, 1, [1, 6])
+    assert_p0_cut(cf, rowlen, 0.0, 6, 2, 10, 6, [])
+    # an empty triangle has no trailing block
+    assert_p0_cut(np.zeros(7, np.int64), rowlen, 0.0, 0, 2, 10, 6, [])
+    # density rule, P0 = n - 2: strict counts [0, 0, 0, 1, 0] give
+    # count_from = [1, 1, 1, 1, 0, 0]; the 2-row block [3, 5) has its one
+    # entry (density 1), the 3-row block [2, 5) would need 3
+    cf2 = np.array([1, 1, 1, 1, 0, 0], np.int64)
+    rl2 = np.array([0, 0, 1, 1, 1], np.int64)
+    assert_p0_cut(cf2, rl2, 1.0, 1, 8, 10, 3, [3, 4, 5])
+    assert_p0_cut(cf2, rl2, 1.0, 2, 8, 10, 5, [])   # below the minimum count
+
+
+def assert_p0_cut(count_from, rowlen, density, min_entries, slices, max_piece, p0_want, cut_want):
+    p0, cut = gblu.solve_partition(count_from, rowlen, density, 0.7, min_entries, slices, max_piece)
+    assert p0 == p0_want
+    assert list(cut) == cut_want
