@@ -802,6 +802,129 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
+def forms_section(args, s, w, dev, vals, rhs, stream):
+    """The other forms of the method, each timed briefly after the headline
+    region with CUDA events (context beside the headline, not the metric):
+    the mixed-precision step on the same matrix (single-precision factors
+    with refinement in double, C4), a 256-set batch of the bordered grid in
+    one persistent launch (C3), and the 2,020-unknown MNA grid one step at a
+    time (C1).  Each gives its rate, the refactorization's ALU roofline and
+    the unit's share of the HBM roofline, and its largest relative residual."""
+    import torch
+    from paper_2411_14082_gb300 import gblu
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def roof(F, t, peak):
+        return {"achieved_tflops": F / t / 1e12, "peak_tflops": peak, "frac": F / t / 1e12 / peak}
+
+    # mixed precision on the same handle and values (C4)
+    st = s.stats()
+    n, nnz, nlu = w["n"], int(w["Ap"][-1]), st["nnz_l"] + st["nnz_u"]
+    x = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
+    k = min(5, len(w["vals"]) - 1)
+    for i in range(2):
+        s.refactorize_f32(vals[i])
+        s.solve_refined(vals[i], rhs[i], x, tol=1e-12)
+    torch.cuda.synchronize(dev)
+    t_rf, t_all, its, berr = [], 0.0, [], 0.0
+    for i in range(k):
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        s.refactorize_f32(vals[i])
+        e1.record(stream)
+        _, it, be = s.solve_refined(vals[i], rhs[i], x, tol=1e-12)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        its.append(it)
+        berr = max(berr, be)
+        if it >= 0:
+            t_rf.append(e0.elapsed_time(e1) / 1e3)
+        t_all += e0.elapsed_time(e2) / 1e3
+    F = st["flops"]
+    out["mixed_precision"] = {
+        "workload": w["name"], "value": k / t_all, "unit": METRIC, "steps": k, "ms_per_step": 1e3 * t_all / k,
+        "refine_iters": its, "fallbacks": sum(1 for v in its if v < 0), "max_backward_error": berr,
+        "roofline_fp32": roof(F, float(np.mean(t_rf)), 152 * 128 * 2 * 2.07e9 / 1e12) if t_rf else None,
+        "hbm_roofline": hbm_roofline(unit_bytes(n, nnz, nlu), t_all / k)}
+    # batch of value sets (C3)
+    wb = make_workload("batch", args.forms_sets, args.seed + 5)
+    nb_, nnzb = wb["n"], int(wb["Ap"][-1])
+    hb = gblu.Solver(dev)
+    hb.analyze(nb_, wb["Ap"], wb["Ai"], wb["Q"])
+    hb.factorize(torch.from_numpy(wb["Ax0"]).cuda(dev))
+    redo = gblu.Solver(dev)
+    redo.analyze(nb_, wb["Ap"], wb["Ai"], wb["Q"])
+    redo.factorize(torch.from_numpy(wb["Ax0"]).cuda(dev))
+    stb = hb.stats()
+    bv = torch.from_numpy(np.stack(wb["vals"])).cuda(dev)
+    bb = torch.from_numpy(np.stack(wb["rhs"])).cuda(dev)
+    bx = torch.empty_like(bb)
+    LUx = torch.empty((args.forms_sets, stb["nnz_l"] + stb["nnz_u"]), dtype=torch.float64, device=f"cuda:{dev}")
+    t_b, t_rfb, nfail = 0.0, [], 0
+    for i in range(3):   # the first call warms up
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        _, failed = hb.refactorize_batch(bv, LUx)
+        e1.record(stream)
+        hb.solve_batch(LUx, bb, bx)
+        for j in np.nonzero(failed)[0]:
+            redo.refactorize(bv[int(j)])
+            redo.solve(bb[int(j)], bx[int(j)])
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            t_b += e0.elapsed_time(e2) / 1e3
+            t_rfb.append(e0.elapsed_time(e1) / 1e3)
+            nfail += int(failed.sum())
+    res = torch.zeros(4, dtype=torch.float64, device=f"cuda:{dev}")
+    worst = 0.0
+    for j in range(args.forms_sets):
+        hb.residual(bv[j], bb[j], bx[j], out=res)
+        worst = max(worst, float(res[0].item()))
+    Fb = stb["flops"] * args.forms_sets
+    out["batch"] = {
+        "workload": wb["name"] + f"_x{args.forms_sets}", "value": 2 * args.forms_sets / t_b, "unit": METRIC,
+        "steps": 2, "ms_per_step": 1e3 * t_b / 2, "failed_sets_redone": nfail,
+        "roofline_fp64": roof(Fb, float(np.mean(t_rfb)), FP64_PEAK_TFLOPS),
+        "hbm_roofline": hbm_roofline((4 * nnzb + 4 * (nb_ + 1) + 8 * (stb["nnz_l"] + stb["nnz_u"]))
+                                     + args.forms_sets * (8 * nnzb + 16 * (stb["nnz_l"] + stb["nnz_u"])
+                                                          + 16 * (nb_ + 1) + 32 * nb_), t_b / 2),
+        "max_rel_residual": worst}
+    del hb, redo, bv, bb, bx, LUx
+    # the small MNA grid (C1), one refactor + solve at a time
+    ws = make_workload("small", 25, args.seed + 7)
+    ns, nnzs = ws["n"], int(ws["Ap"][-1])
+    hs = gblu.Solver(dev)
+    hs.analyze(ns, ws["Ap"], ws["Ai"], ws["Q"])
+    hs.factorize(torch.from_numpy(ws["Ax0"]).cuda(dev))
+    sv = torch.from_numpy(np.stack(ws["vals"])).cuda(dev)
+    sb = torch.from_numpy(np.stack(ws["rhs"])).cuda(dev)
+    sx = torch.empty_like(sb)
+    for i in range(5):
+        hs.refactorize(sv[i])
+        hs.solve(sb[i], sx[i])
+    torch.cuda.synchronize(dev)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for i in range(5, 25):
+        hs.refactorize(sv[i])
+        hs.solve(sb[i], sx[i])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_s = e0.elapsed_time(e1) / 1e3
+    worst = 0.0
+    for i in range(5, 25):
+        hs.residual(sv[i], sb[i], sx[i], out=res)
+        worst = max(worst, float(res[0].item()))
+    sts = hs.stats()
+    out["small_mna"] = {
+        "workload": ws["name"], "value": 20 / t_s, "unit": METRIC, "steps": 20, "ms_per_step": 1e3 * t_s / 20,
+        "hbm_roofline": hbm_roofline(unit_bytes(ns, nnzs, sts["nnz_l"] + sts["nnz_u"]), t_s / 20),
+        "max_rel_residual": worst, "repivots": sts["n_repivot"]}
+    return out
+
+
 def auto_order_variant(args, w, dev, vals, rhs, stream):
     """The headline step on a handle analyzed without Q, i.e. with the
     library's own ordering (gblu_order_auto's choice), timed with events over
@@ -1076,6 +1199,9 @@ def run_ours(args, rank, world, local_rank):
     auto = None
     if args.auto_order_steps > 0 and not (mixed or ss or args.graph or forced):
         auto = auto_order_variant(args, w, dev, vals, rhs, stream)
+    forms = None
+    if args.forms and not (mixed or ss or args.graph or forced) and args.workload == "mesh":
+        forms = forms_section(args, s, w, dev, vals, rhs, stream)
 
     if rank != 0:
         return 0
@@ -1198,6 +1324,8 @@ def run_ours(args, rank, world, local_rank):
     line["oracle_check"] = oracle_check
     if auto:
         line["auto_order"] = auto
+    if forms:
+        line["forms"] = forms
     if cpu:
         secs = [c["seconds"] for c in cpu]
         line["cpu_baseline"] = {"value": len(secs) / sum(secs), "unit": METRIC, "cores": 1,
@@ -1246,6 +1374,9 @@ def main():
                     help="sets per group of the batch launch (0: from the L2 size; default: the library's)")
     ap.add_argument("--seed", type=int, default=inputs.BASE_SEED + 1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", type=int, default=1,
+                    help="1: also time the mixed-precision, batched and small forms briefly (context keys)")
+    ap.add_argument("--forms-sets", type=int, default=256, help="value sets of the batched form")
     ap.add_argument("--auto-order-steps", type=int, default=5,
                     help="steps of the variant with the library's own ordering (0: skip)")
     ap.add_argument("--mesh", default="200x200x4",
