@@ -84,10 +84,10 @@ def hbm_roofline(bytes_alg, seconds, traffic=None):
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4": {"refactor_cu_sha256": "ec9d1c08d07ee3881fd0d695d186421b7744c7a3ba463b68ddffe3c336db25fb",
-                          "bytes": 16.346e9 + 445.4e6},
-    "rc_mesh_120x120x4": {"refactor_cu_sha256": "ec9d1c08d07ee3881fd0d695d186421b7744c7a3ba463b68ddffe3c336db25fb",
-                          "bytes": 136.0e6 + 82.9e6},
+    "rc_mesh_200x200x4": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
+                          "bytes": 16.34e9 + 36.2e6 + 442.6e6},
+    "rc_mesh_120x120x4": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
+                          "bytes": 135.8e6 + 83.6e6},
 }
 
 
