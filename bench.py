@@ -506,7 +506,7 @@ def run_serve_poisson(args, rank, world, local_rank):
                 mode = k % 2
                 rid = srv.submit(p["id"], p["vals"][j], p["rhs"][j], mixed=bool(mode))
                 with lock:
-                    ids.append((rid, mode, p["name"], p["ubytes"]))
+                    ids.append((rid, mode, p["name"], p["ubytes"], p["n"]))
 
         clocks = ClockSampler()
         clocks.start()
@@ -514,6 +514,7 @@ def run_serve_poisson(args, rank, world, local_rank):
         th = threading.Thread(target=dispatch)
         th.start()
         res = []
+        sizes = []
         moved = [0]
         got = 0
         while got < N:
@@ -522,9 +523,10 @@ def run_serve_poisson(args, rank, world, local_rank):
             if not pending:
                 time.sleep(0.001)
                 continue
-            for rid, mode, name, ub in pending:
+            for rid, mode, name, ub, nn in pending:
                 _, r = srv.wait(rid, timeout=600.0)
                 res.append((mode, name, r))
+                sizes.append(nn)
                 moved[0] += ub
                 got += 1
         th.join()
@@ -538,7 +540,13 @@ def run_serve_poisson(args, rank, world, local_rank):
                 "p50_ms": 1e3 * float(np.percentile(a, 50)), "p99_ms": 1e3 * float(np.percentile(a, 99)),
                 "fallbacks": int(sum(1 for m, _, r in res if m == mode and r["refine_iters"] < 0))}
         st1 = srv.stats()
-        sweep.append({"offered_load": rho, "arrival_rate_per_s": lam, "requests": N,
+        by_size = {}
+        for cls, sel in (("n<=100k", [z <= 100000 for z in sizes]), ("n>100k", [z > 100000 for z in sizes])):
+            a = np.array([r["latency_s"] for (m_, nm_, r), keep in zip(res, sel) if keep])
+            if len(a):
+                by_size[cls] = {"requests": int(len(a)), "p50_ms": 1e3 * float(np.percentile(a, 50)),
+                                "p99_ms": 1e3 * float(np.percentile(a, 99))}
+        sweep.append({"offered_load": rho, "by_size": by_size, "arrival_rate_per_s": lam, "requests": N,
                       "served_per_s": N / elapsed, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                       "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "by_mode": by_mode,
                       "mean_batch": float(np.mean([r["batch_size"] for m, _, r in res if m == 0])),

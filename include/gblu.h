@@ -121,6 +121,10 @@ typedef struct {
        many as fit.  Fewer resident warps poll fewer unpublished values at a
        time.  gblu_autotune measures it. */
     int solve_ctas_per_sm;
+    /* SMs the handle's persistent launches (re-factorization, pivoting,
+       sync-free solves) may use; 0 = all.  A server gives its large patterns
+       part of the device so that small requests run beside them. */
+    int max_sms;
 } gblu_opts;
 
 /* largest dense tail block of the re-factorization (shared-memory panel) */
@@ -428,7 +432,10 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
  * request whose pivot check fails is redone with gblu_refactorize (restart
  * with pivoting, Section IV-C), and the pattern keeps the new pivot
  * sequence.  Each result is bit-for-bit the result of the same request run
- * alone on a handle in the same pivot state.
+ * alone on a handle in the same pivot state.  A pattern of 250,000 unknowns
+ * or more gets max_sms = 3/4 of the SMs and a low-priority stream; the
+ * others get high-priority streams, so that small requests start beside a
+ * large one's persistent launches.
  *
  * gblu_server_create: budget = device bytes the server may hold in total;
  *   max_batch = most requests per batch; o = options of the handles (NULL:

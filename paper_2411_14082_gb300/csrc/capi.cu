@@ -81,7 +81,7 @@ struct gblu_ctx {
     gblu_opts opts{};
     int sm_count = 0;
     int l2_bytes = 0;
-    int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_grid = 0;
+    int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_per_sm = 0;
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
     int32_t force_col = -1;                        // forced check failure of the next refactorization
@@ -218,6 +218,14 @@ struct EventList {
         return GBLU_OK;
     }
 };
+
+// SMs the handle's persistent launches may use (the max_sms option), and a
+// persistent grid of per_sm CTAs on each of them
+int sms_used(const gblu_ctx *h)
+{
+    return (h->opts.max_sms > 0 && h->opts.max_sms < h->sm_count) ? h->opts.max_sms : h->sm_count;
+}
+int pgrid(const gblu_ctx *h, int per_sm) { return std::max(1, per_sm) * sms_used(h); }
 
 template <class T>
 int ensure(gblu_ctx *h, DBuf<T> &b, size_t count)
@@ -408,7 +416,7 @@ int issue_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int ep)
     if (ltp[div] < ntask) {               // pipeline mode: one persistent launch
         a.task_begin = ltp[div];
         a.ntasks = ntask - ltp[div];
-        KL(launch_refactor_tasks(a, true, h->ref_grid, ep, st));
+        KL(launch_refactor_tasks(a, true, pgrid(h, h->ref_blocks_per_sm), ep, st));
     }
     if (h->W.dense_m > 0) {   // the dense tail: blocked LU of the block, then scatter
         DenseArgs2 d{};
@@ -483,7 +491,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     CK(ensure(h, h->tpiv, n));
     CK(ensure(h, h->tpinv, n));
     // scratch: one dense work vector per CTA
-    int slots = std::min<int64_t>((int64_t)nR, (int64_t)h->sm_count * 2);
+    int slots = std::min<int64_t>((int64_t)nR, (int64_t)sms_used(h) * 2);
     const size_t per_slot = (size_t)n * (sizeof(double) + 2 * sizeof(int32_t));
     const size_t budget = (size_t)4 << 30;
     slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)slots, budget / per_slot));
@@ -754,7 +762,7 @@ int restart_on_structure(gblu_ctx *h, const double *Ax, cudaStream_t st, int *in
     a.skip_done = 1;
     a.task_begin = 0;
     a.ntasks = (int32_t)h->W.task_ptr.size() - 1;
-    KL(launch_refactor_tasks(a, true, h->ref_grid, h->epoch, st));
+    KL(launch_refactor_tasks(a, true, pgrid(h, h->ref_blocks_per_sm), h->epoch, st));
     CK(read_ctl(h, st));
     CK(status_code(h));
     *interrupted = h->hctl->interrupted;
@@ -820,6 +828,7 @@ void gblu_default_opts(gblu_opts *o)
     o->speculate_first = 1;
     o->batch_group = 0;
     o->solve_ctas_per_sm = 0;
+    o->max_sms = 0;
 }
 
 const char *gblu_last_error(void) { return g_err.c_str(); }
@@ -831,7 +840,7 @@ static bool opts_valid(const gblu_opts &o)
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
            o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
            o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1) &&
-           o.batch_group >= 0 && o.solve_ctas_per_sm >= 0;
+           o.batch_group >= 0 && o.solve_ctas_per_sm >= 0 && o.max_sms >= 0;
 }
 
 int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
@@ -876,7 +885,7 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     h->ref_grid = h->ref_blocks_per_sm * h->sm_count;
     h->ref32_grid = h->ref32_blocks_per_sm * h->sm_count;
     h->res_blocks = h->sm_count * 4;
-    h->trail_grid = std::max(1, trail_per_sm) * h->sm_count;
+    h->trail_per_sm = std::max(1, trail_per_sm);
     *out = h;
     return GBLU_OK;
 }
@@ -1129,9 +1138,9 @@ static SolveArgs solve_args(gblu_ctx *h, const double *LUx, const double *b_dev,
 // as many as fit
 static int solve_grid(gblu_ctx *h)
 {
+    const int fit = h->solve_grid / std::max(1, h->sm_count);   // CTAs per SM that fit
     const int per = h->opts.solve_ctas_per_sm;
-    if (per <= 0 || per * h->sm_count >= h->solve_grid) return h->solve_grid;
-    return per * h->sm_count;
+    return pgrid(h, (per <= 0 || per >= fit) ? fit : per);
 }
 
 static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const double *b_dev, int64_t b_stride,
@@ -1190,7 +1199,7 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
     if (W.lp0 < n) {
         const TrailArgs t{W.lp0, n, W.lnb, h->lseg.p, h->LUp.p, h->LUi.p, h->nU.p, h->ltri0.p};
         a.ext = h->ext_l.p;
-        KL(launch_trail(a, t, true, h->trail_grid, st));
+        KL(launch_trail(a, t, true, pgrid(h, h->trail_per_sm), st));
         h->launches++;   // two kernels
     }
     // backward: the trailing block's slices, then the sums of the rows above
@@ -1198,7 +1207,7 @@ static int solve_values(gblu_ctx *h, const double *LUx, int64_t lu_stride, const
     if (W.up0 < n) {
         const TrailArgs t{W.up0, n, W.unb, h->useg.p, h->LUp.p, h->LUi.p, h->nU.p, h->ufar.p};
         a.far = h->far.p;
-        KL(launch_trail(a, t, false, h->trail_grid, st));
+        KL(launch_trail(a, t, false, pgrid(h, h->trail_per_sm), st));
         if (W.up0 > 0) h->launches++;
         a.ufar = h->ufar.p;
     }
@@ -1276,7 +1285,7 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
     if (ltp[div] < ntask) {               // pipeline mode
         a0.task_begin = ltp[div];
         a0.ntasks = ntask - ltp[div];
-        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, h->ref_grid, h->epoch, h->bticket.p, st,
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, pgrid(h, h->ref_blocks_per_sm), h->epoch, h->bticket.p, st,
                                  batch_group(h, nsets)));
     }
     h->bctl_host.resize(nsets);
@@ -1373,7 +1382,7 @@ int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_
     CU(cudaMemcpyAsync(h0->bargs.p, h0->bargs_host.data(), sizeof(RefactorArgs) * nh, cudaMemcpyHostToDevice, st));
     {
         gblu_ctx *h = h0;   // the launch is counted on the leading handle
-        KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, h0->ref_grid,
+        KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, pgrid(h0, h0->ref_blocks_per_sm),
                                  ep, h0->bticket.p, st));
         h->launches++;   // the control-block reset kernel
     }
@@ -1657,7 +1666,7 @@ static int capture_step_batch(gblu_ctx *h, int32_t nsets, const double *Ax_dev, 
         if (ltp[div] < ntask) {
             a0.task_begin = ltp[div];
             a0.ntasks = ntask - ltp[div];
-            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, h->ref_grid, 1, h->bticket.p, gs,
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, pgrid(h, h->ref_blocks_per_sm), 1, h->bticket.p, gs,
                                      batch_group(h, nsets)));
         }
         CU(cudaMemcpyAsync(h->bgctl_host, h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, gs));
@@ -1904,7 +1913,7 @@ int gblu_refactorize_f32(gblu_handle h, const double *Ax_dev, void *stream, int3
     if (ltp[div] < ntask) {
         a.task_begin = ltp[div];
         a.ntasks = ntask - ltp[div];
-        KL(launch_refactor_tasks_f32(a, true, h->ref32_grid, h->epoch, st));
+        KL(launch_refactor_tasks_f32(a, true, pgrid(h, h->ref32_blocks_per_sm), h->epoch, st));
     }
     // the pivots in double: a pivot that single precision cannot place
     // clearly on the passing side of the threshold fails here, and the

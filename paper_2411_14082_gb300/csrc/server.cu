@@ -43,6 +43,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// patterns of at least this many unknowns share the device with small ones
+// (max_sms = 3/4 of the SMs, low stream priority)
+constexpr int32_t kBigPattern = 250000;
+
 thread_local std::string s_err = "no error";
 
 int sfail(int code, const char *fmt, ...)
@@ -369,7 +373,25 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
     };
     rc = gblu_analyze(p->h, n, Ap, Ai, Q);
     if (rc != GBLU_OK) return bail_h(rc);
-    if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess)
+    // a large pattern's persistent launches hold a quarter of the SMs back
+    // and run on a low-priority stream, so that the CTAs of small requests
+    // queued meanwhile start on free SMs instead of waiting for its launch
+    // to end (kernels are not preempted)
+    const bool big = n >= kBigPattern;
+    if (big) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        gblu_opts ho{};
+        gblu_get_opts(p->h, &ho);
+        if (ho.max_sms == 0 || ho.max_sms > sms * 3 / 4) {
+            ho.max_sms = std::max(1, sms * 3 / 4);
+            rc = gblu_set_opts(p->h, &ho, nullptr);
+            if (rc != GBLU_OK) return bail_h(rc);
+        }
+    }
+    int pr_least = 0, pr_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&pr_least, &pr_greatest);
+    if (cudaStreamCreateWithPriority(&p->st, cudaStreamNonBlocking, big ? pr_least : pr_greatest) != cudaSuccess)
         return bail(sfail(GBLU_ERR_CUDA, "server: stream creation failed"));
     p->n = n;
     p->nnz_a = Ap[n];

@@ -65,7 +65,7 @@ class Opts(ctypes.Structure):
                 ("solve_dense_min", ctypes.c_longlong), ("solve_slices", ctypes.c_int),
                 ("solve_dense_density", ctypes.c_double), ("dense_min_rows", ctypes.c_int),
                 ("warp_column_max", ctypes.c_int), ("speculate_first", ctypes.c_int),
-                ("batch_group", ctypes.c_int), ("solve_ctas_per_sm", ctypes.c_int)]
+                ("batch_group", ctypes.c_int), ("solve_ctas_per_sm", ctypes.c_int), ("max_sms", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
