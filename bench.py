@@ -84,9 +84,9 @@ def hbm_roofline(bytes_alg, seconds, traffic=None):
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
+    "rc_mesh_200x200x4/geometric": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
                           "bytes": 16.34e9 + 36.2e6 + 442.6e6},
-    "rc_mesh_120x120x4": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
+    "rc_mesh_120x120x4/geometric": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
                           "bytes": 135.8e6 + 83.6e6},
 }
 
@@ -933,16 +933,18 @@ def forms_section(args, s, w, dev, vals, rhs, stream):
     return out
 
 
-def auto_order_variant(args, w, dev, vals, rhs, stream):
-    """The headline step on a handle analyzed without Q, i.e. with the
-    library's own ordering (gblu_order_auto's choice), timed with events over
-    args.auto_order_steps steps after two warm-up steps."""
+def ordering_variant(args, w, dev, vals, rhs, stream):
+    """The headline step with the other ordering (the generator's geometric
+    nested dissection when the headline uses the library's, and the reverse),
+    timed with events over args.auto_order_steps steps after two warm-up
+    steps."""
     import torch
     from paper_2411_14082_gb300 import gblu
     n = w["n"]
     a = gblu.Solver(dev)
+    geometric = args.ordering == "library"
     t0 = time.perf_counter()
-    a.analyze(n, w["Ap"], w["Ai"], None)
+    a.analyze(n, w["Ap"], w["Ai"], w["Q"] if geometric else None)
     t_an = time.perf_counter() - t0
     a.factorize(torch.from_numpy(w["Ax0"]).cuda(dev))
     st = a.stats()
@@ -965,7 +967,8 @@ def auto_order_variant(args, w, dev, vals, rhs, stream):
     a.residual(vals[1 + k], rhs[1 + k], x, out=res)
     worst = float(res[0].item())
     out = {"value": k / secs, "unit": METRIC, "steps": k, "ms_per_step": 1e3 * secs / k,
-           "ordering": "library (gblu_analyze with Q = NULL)", "analyze_host_s": t_an,
+           "ordering": ("geometric nested dissection from the generator's coordinates" if geometric
+                        else "library (gblu_analyze with Q = NULL)"), "analyze_host_s": t_an,
            "refactor_gflop": st["flops"] / 1e9, "nnz_lu": int(st["nnz_l"] + st["nnz_u"]),
            "last_rel_residual": worst}
     del a
@@ -988,16 +991,19 @@ def run_ours(args, rank, world, local_rank):
     n, nnz = w["n"], int(w["Ap"][-1])
     s = gblu.Solver(dev)
     ss = rs = None
+    # the library's own ordering (gblu_analyze without Q), or the generator's
+    # geometric nested dissection
+    qarg = None if args.ordering == "library" else w["Q"]
     t0 = time.perf_counter()
     if args.static_scaling:
         # static pivoting and scaling: the handle factors Dr P A Dc; a second
         # handle on the original pattern only computes residuals
         ss = gblu.StaticScaling(n, w["Ap"], w["Ai"], w["Ax0"], device=dev)
-        s.analyze(n, w["Ap"], ss.Ai_scaled, w["Q"])
+        s.analyze(n, w["Ap"], ss.Ai_scaled, qarg)
         rs = gblu.Solver(dev)
-        rs.analyze(n, w["Ap"], w["Ai"], w["Q"])
+        rs.analyze(n, w["Ap"], w["Ai"], qarg)
     else:
-        s.analyze(n, w["Ap"], w["Ai"], w["Q"])
+        s.analyze(n, w["Ap"], w["Ai"], qarg)
     t_an = time.perf_counter() - t0
     if args.solve_ctas >= 0:
         s.set_opts(solve_ctas_per_sm=args.solve_ctas)
@@ -1187,7 +1193,7 @@ def run_ours(args, rank, world, local_rank):
     eh = s
     if ss:
         eh = gblu.Solver(dev)
-        eh.analyze(n, w["Ap"], w["Ai"], w["Q"])
+        eh.analyze(n, w["Ap"], w["Ai"], qarg)
         eh.factorize(Ax0)
     hv = [torch.from_numpy(v).pin_memory().numpy() for v in w["vals"][args.warmup:]]
     hb = [torch.from_numpy(b).pin_memory().numpy() for b in w["rhs"][args.warmup:]]
@@ -1206,7 +1212,7 @@ def run_ours(args, rank, world, local_rank):
     # (gblu_analyze without Q), timed alone after the headline region
     auto = None
     if args.auto_order_steps > 0 and not (mixed or ss or args.graph or forced):
-        auto = auto_order_variant(args, w, dev, vals, rhs, stream)
+        auto = ordering_variant(args, w, dev, vals, rhs, stream)
     forms = None
     if args.forms and not (mixed or ss or args.graph or forced) and args.workload == "mesh":
         forms = forms_section(args, s, w, dev, vals, rhs, stream)
@@ -1245,7 +1251,9 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "nnz_a": nnz, "nnz_lu": int(nnz_lu),
-                   "refactor_gflop": F / 1e9, "ordering": "geometric nested dissection",
+                   "refactor_gflop": F / 1e9,
+                   "ordering": ("library (gblu_analyze with Q = NULL)" if args.ordering == "library"
+                                else "geometric nested dissection from the generator's coordinates"),
                    "l2": "inputs and factors larger than L2 (no flush)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "max_rel_residual": resid, "residual_ok": bool(resid <= 1e-12),
@@ -1262,7 +1270,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": "refactor (checked re-factorization, all launches)",
                      "bound": "alu", "achieved": F / t_rf / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": F / t_rf / 1e12 / FP64_PEAK_TFLOPS,
-                     "traffic": refactor_traffic(w["name"]),
+                     "traffic": refactor_traffic(w["name"] + "/" + args.ordering),
                      "peak_source": "FP64 ALU rate: 152 SMs x 2.07 GHz x 4 FLOP/clock",
                      "peak_probe_tflops": fp64_probe,
                      "hbm_view": {"compulsory_gbs": b_rf / t_rf / 1e9,
@@ -1331,7 +1339,7 @@ def run_ours(args, rank, world, local_rank):
                            "forced_steps": [int(v) for v in tm[:, 5]]}
     line["oracle_check"] = oracle_check
     if auto:
-        line["auto_order"] = auto
+        line["other_ordering"] = auto
     if forms:
         line["forms"] = forms
     if cpu:
@@ -1340,7 +1348,9 @@ def run_ours(args, rank, world, local_rank):
                                 "kind": "oracle",
                                 "sample": "1 full refactor+solve unit: the first timed step of this run "
                                           "(single-threaded C oracle, separate process, run after the "
-                                          "GPU measurements)",
+                                          "GPU measurements; the oracle orders by the generator's "
+                                          "geometric nested dissection, an input independent of the "
+                                          "library)",
                                 "max_rel_residual": max(c["residual"] for c in cpu),
                                 "host": host_info()}
     else:
@@ -1385,8 +1395,11 @@ def main():
     ap.add_argument("--forms", type=int, default=1,
                     help="1: also time the mixed-precision, batched and small forms briefly (context keys)")
     ap.add_argument("--forms-sets", type=int, default=256, help="value sets of the batched form")
+    ap.add_argument("--ordering", default="library", choices=["library", "geometric"],
+                    help="library: gblu_analyze without Q (the library's choice); geometric: the "
+                         "generator's nested dissection")
     ap.add_argument("--auto-order-steps", type=int, default=5,
-                    help="steps of the variant with the library's own ordering (0: skip)")
+                    help="steps of the variant with the other ordering (0: skip)")
     ap.add_argument("--mesh", default="200x200x4",
                     help="grid of the mesh workload (smaller grids for profiling runs)")
     args = ap.parse_args()
