@@ -498,10 +498,6 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
         if (warp == 0) {
             if (lane < nR) {   // only the first 32 entries of R can fall in the leader's slots
                 const int row = __ldg(a.LUi + lbl + lane);
-                // the first eight dependencies' values, loaded before the slot search
-                R p0[8];
-#pragma unroll
-                for (int u = 0; u < 8; u++) p0[u] = u < w ? __ldcg(a.LUx + r.base[u] + lane) : R(0);
                 const int sl = find_slot(rows, tl + 1 + lane, tl + (row - jl), len, row);
                 if (sl < 0) {
                     bad = true;
@@ -511,7 +507,7 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
                         R lv[8];
 #pragma unroll
                         for (int u = 0; u < 8; u++)
-                            lv[u] = d0 == 0 ? p0[u] : (d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : R(0));
+                            lv[u] = d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : R(0);
 #pragma unroll
                         for (int u = 0; u < 8; u++)
                             if (d0 + u < w) v = fma(-x[t + d0 + u], lv[u], v);
