@@ -203,16 +203,13 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
             const long long lbl = __shfl_sync(kFull, m_lb, q0 + w - 1);
             const int nR = __shfl_sync(kFull, m_nl, q0 + w - 1);
             bool bad = false;
-            const long long lb0 = __shfl_sync(kFull, m_lb, q0) + (w - 1);   // the first dependency's R values
             for (int r0 = 0; r0 < nR; r0 += 32 * kBatch) {
                 int sl[kBatch], key[kBatch], lo[kBatch], hi[kBatch];
-                R v[kBatch], l0[kBatch];
+                R v[kBatch];
 #pragma unroll
                 for (int u = 0; u < kBatch; u++) {
                     const int r = r0 + u * 32 + lane;
                     key[u] = r < nR ? __ldg(a.LUi + lbl + r) : -1;
-                    // loaded before the slot search instead of after it
-                    l0[u] = r < nR ? __ldcg(a.LUx + lb0 + r) : R(0);
                     lo[u] = tl + 1 + r;
                     hi[u] = tl + (key[u] - jl);
                 }
@@ -222,13 +219,7 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
                     if (key[u] >= 0 && sl[u] < 0) bad = true;
                     v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
-                {
-                    const R mv = x[t];
-#pragma unroll
-                    for (int u = 0; u < kBatch; u++)
-                        if (sl[u] >= 0) v[u] = fma(-mv, l0[u], v[u]);
-                }
-                for (int d = 1; d < w; d++) {
+                for (int d = 0; d < w; d++) {
                     const R mv = x[t + d];
                     const long long lbd = __shfl_sync(kFull, m_lb, q0 + d);
                     const R *lv = a.LUx + lbd + (w - 1 - d) + r0 + lane;
@@ -526,14 +517,11 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
             const int wt = tid - 32;
             for (int r0 = 0; r0 < nR; r0 += kRows * kTw) {
                 int sl[kRows], key[kRows], lo[kRows], hi[kRows];
-                R v[kRows], l0[kRows];
+                R v[kRows];
 #pragma unroll
                 for (int u = 0; u < kRows; u++) {
                     const int rr = r0 + u * kTw + wt;
                     key[u] = rr < nR ? __ldg(a.LUi + lbl + rr) : -1;
-                    // the first dependency's values, loaded before the slot
-                    // search instead of after it
-                    l0[u] = rr < nR ? __ldcg(a.LUx + r.base[0] + rr) : R(0);
                     lo[u] = tl + 1 + rr;
                     hi[u] = tl + (key[u] - jl);
                 }
@@ -544,14 +532,8 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
                     if (sl[u] >= 0 && sl[u] < hend) sl[u] = -1;   // the leader's
                     v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
-                {
-                    const R m = x[t];
-#pragma unroll
-                    for (int u = 0; u < kRows; u++)
-                        if (sl[u] >= 0) v[u] = fma(-m, l0[u], v[u]);
-                }
 #pragma unroll 4
-                for (int d = 1; d < w; d++) {
+                for (int d = 0; d < w; d++) {
                     const R m = x[t + d];
                     const R *lv = a.LUx + r.base[d] + r0 + wt;
 #pragma unroll
