@@ -1016,6 +1016,10 @@ def run_ours(args, rank, world, local_rank):
     t_fac = time.perf_counter() - t0
     st = s.stats()
     fac_passes = st["tail_passes"]
+    first_how = {0: "pivoting kernel", 1: "predicted structure", 2: "predicted structure, then pivoting kernel"}
+    first_detail = {"how": first_how.get(st["first_mode"], "?"), "structure_host": st["first_symbolic_ms"],
+                    "kernels": st["tail_kernel_ms"], "schedule_host": st["tail_schedule_ms"],
+                    "upload": st["tail_upload_ms"]}
     vals = torch.from_numpy(np.stack(w["vals"])).cuda(dev)
     rhs = torch.from_numpy(np.stack(w["rhs"])).cuda(dev)
     xs = torch.empty_like(rhs)
@@ -1268,7 +1272,7 @@ def run_ours(args, rank, world, local_rank):
                       "unit_p50": 1e3 * float(np.median(t_unit)),
                       "unit_p99": 1e3 * float(np.percentile(t_unit, 99)),
                       "analyze_host": 1e3 * t_an, "first_factorize": 1e3 * t_fac,
-                      "first_factorize_passes": fac_passes},
+                      "first_factorize_passes": fac_passes, "first_factorize_parts": first_detail},
         "roofline": {"kernel": "refactor (checked re-factorization, all launches)",
                      "bound": "alu", "achieved": F / t_rf / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": F / t_rf / 1e12 / FP64_PEAK_TFLOPS,

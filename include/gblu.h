@@ -100,16 +100,25 @@ typedef struct {
        gblu_autotune measures it. */
     int warp_column_max;
     /* first factorization (gblu_factorize, Algorithm 1 with the threshold
-       rule): 1 = its passes speculate that each step pivots on its diagonal
-       row A(Q[k],Q[k]) and wait only on the steps that prediction names as
+       rule and the diagonal row A(Q[k],Q[k]) preferred):
+       2 = the prediction that every step keeps its diagonal row becomes a
+       structure (gblu_symmetric_structure) that is installed, and the
+       checked re-factorization kernel computes every column on it; when a
+       check fails, the unfinished steps and their column-elimination-tree
+       ancestors continue as in 1.  Taken when every column of A has a
+       nonzero diagonal entry and at most 2% of the off-diagonal entries of
+       A lack their transposed entry; otherwise as 1.
+       1 = the pivoting kernel's passes speculate that each step pivots on
+       its diagonal row and wait only on the steps that prediction names as
        dependencies; steps after the first one that took another row run
        again, and the run falls back to waiting on every earlier unfinished
        step of the column's elimination subtree once more than four finished
        steps of a pass have left the diagonal, a pass finishes no step for
        good, or eight passes have run.  It does not speculate at all when
        more than four columns of A have an absent or zero diagonal entry.
-       0 = every step waits in that order from the start.  Both give the
-       same factors.  Default 1. */
+       0 = every step waits in that order from the start.  All three give
+       the same pivots and factor values (2 may store exact zeros at the
+       extra positions of its structure).  Default 2. */
     int speculate_first;
     /* batches of value sets (gblu_refactorize_batch): the persistent launch
        takes the sets in groups of batch_group, all tasks of one group before
@@ -186,6 +195,11 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
  * column-elimination subtree).  Every step prefers its diagonal row Q[k] and
  * keeps it unless |x(Q[k])| < pivot_tol * max|other candidates| or
  * x(Q[k]) == 0, else takes the largest candidate (ties: the row first in Q).
+ * By default (speculate_first = 2) the prediction that every step keeps its
+ * diagonal row is first installed as a structure and the checked
+ * re-factorization kernel computes the columns on it; where a check fails,
+ * the pivoting kernel recomputes the unfinished columns and their
+ * column-elimination-tree ancestors (the restart of Section IV-C).
  * Ax_dev: device float64[nnz] in the slot order of the analyze call's Ai.
  * Builds the factors and, on the host, the fixed-pattern schedule for
  * refactorize and solve.  Synchronizes `stream`.
@@ -556,6 +570,13 @@ typedef struct {
                              columns re-factorized on the installed
                              structure with the check, kept every pivot
                              (tail_kernel_ms is then that stage's time) */
+    /* last gblu_factorize: 0 = the pivoting kernel computed every step;
+       1 = the checked re-factorization on the predicted structure passed
+       every check (tail_kernel_ms is its time, first_symbolic_ms the
+       structure's on the host); 2 = a check failed there and the pivoting
+       kernel finished the restart set (the tail_* fields describe it) */
+    int32_t first_mode;
+    double first_symbolic_ms;
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);
@@ -640,6 +661,19 @@ int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, con
  * for an invalid pattern or a Q that is not a permutation. */
 int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q, int64_t *fill,
                         double *flops);
+/* The factor structure that gblu_factorize predicts before its first
+ * factorization (Algorithm 1 with every step keeping its diagonal row, so
+ * that the checked re-factorization kernel can compute it): in step
+ * numbering, column k holds its U rows ascending, then k, then its L rows
+ * ascending, L and U^T taking the pattern of the Cholesky factor of
+ * (A + A^T)(Q,Q).  That pattern contains the pattern of the LU factors of
+ * A(Q,Q) without row exchanges and equals it when A is structurally
+ * symmetric; the extra entries compute to exact zeros.  With LUp (n+1),
+ * LUi (nnz entries) and nU (n, U entries of each column with the diagonal)
+ * all non-NULL they are filled; returns nnz, or GBLU_ERR_INVALID_INPUT for
+ * an invalid pattern or a Q that is not a permutation. */
+int64_t gblu_symmetric_structure(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                                 int64_t *LUp, int32_t *LUi, int32_t *nU);
 /* The structure-adaptive split of one triangular factor (Section V-A), as
  * the solve setup computes it.  count_from[p] (n+1 entries, count_from[n]
  * = 0): strict entries of the trailing block [p, n); rowlen[i] (n): all

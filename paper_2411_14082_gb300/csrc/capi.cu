@@ -87,6 +87,9 @@ struct gblu_ctx {
     int32_t force_col = -1;                        // forced check failure of the next refactorization
     double t_tail[4] = {0, 0, 0, 0};               // last tail run: kernel, repack, schedule, upload (ms)
     int32_t tail_passes = 0;                       // kernel passes of the last tail run
+    int32_t first_mode = 0;                        // last gblu_factorize: 0 pivoting kernel only,
+                                                   // 1 predicted structure, 2 and then the pivoting kernel
+    double t_first_symbolic = 0.0;                 // its structure prediction (host ms)
     bool last_repivot = false;                     // the last refactorization restarted
     bool analyzed = false, factorized = false;
     Pattern P;
@@ -825,7 +828,7 @@ void gblu_default_opts(gblu_opts *o)
     o->solve_dense_density = 0.9;
     o->dense_min_rows = 0;
     o->warp_column_max = kRefCapShort;
-    o->speculate_first = 1;
+    o->speculate_first = 2;
     o->batch_group = 0;
     o->solve_ctas_per_sm = 0;
     o->max_sms = 0;
@@ -839,7 +842,7 @@ static bool opts_valid(const gblu_opts &o)
            o.solve_mode >= 0 && o.solve_mode <= 2 && o.alpha >= 0.0 && o.solve_dense_frac >= 0.0 &&
            o.solve_dense_frac <= 1.0 && o.solve_slices >= 0 && o.solve_dense_density >= 0.0 &&
            o.solve_dense_density <= 1.0 && o.dense_min_rows >= 0 && o.warp_column_max >= 32 &&
-           o.warp_column_max <= kRefCapShort && (o.speculate_first == 0 || o.speculate_first == 1) &&
+           o.warp_column_max <= kRefCapShort && (o.speculate_first >= 0 && o.speculate_first <= 2) &&
            o.batch_group >= 0 && o.solve_ctas_per_sm >= 0 && o.max_sms >= 0;
 }
 
@@ -1002,6 +1005,16 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
     return GBLU_OK;
 }
 
+// The predicted structure is a superset of the exact one by the fill that
+// the unsymmetric entries of A add; with at most 2% of the off-diagonal
+// entries unsymmetric it stays close (0.1% more entries on the RC meshes
+// with transistors, whose transconductance entries are the unsymmetric ones)
+static bool nearly_symmetric(const Pattern &P)
+{
+    const int64_t offdiag = (int64_t)P.Ai.size() - P.n;
+    return offdiag <= 0 || unsymmetric_entries(P) * 50 <= offdiag;
+}
+
 int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
 {
     NvtxRange nvtx_range("gblu_factorize");
@@ -1026,6 +1039,7 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     CK(upload(h, h->piv, h->S.piv, st));
     CK(upload(h, h->pinv, h->S.pinv, st));
     bool spec = h->opts.speculate_first != 0;
+    int64_t zero_diag = 0;
     if (spec && n > 0) {
         // the prediction fails where A's diagonal entry is absent or zero
         // (the branch rows of MNA voltage sources) unless fill makes it
@@ -1036,7 +1050,6 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
         if (!ax.empty())
             CU(cudaMemcpyAsync(ax.data(), Ax_dev, sizeof(double) * ax.size(), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        int64_t zero_diag = 0;
         for (int32_t k = 0; k < n && zero_diag <= kSpecMaxMoved; k++) {
             const int32_t c = h->P.Q[k];
             bool nz = false;
@@ -1046,6 +1059,45 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
         spec = zero_diag <= kSpecMaxMoved;
     }
     CU(cudaStreamSynchronize(st));
+    h->first_mode = 0;
+    h->t_first_symbolic = 0.0;
+    if (spec && h->opts.speculate_first == 2 && zero_diag == 0 && nearly_symmetric(h->P)) {
+        // the prediction as a structure: L and U^T with the pattern of the
+        // Cholesky factor of (A + A^T)(Q,Q), which holds the pattern of the
+        // factors when every step keeps its diagonal row; the checked
+        // re-factorization kernel then computes every column, and the check
+        // is the threshold rule with the diagonal preferred (Algorithm 1)
+        const auto t0 = std::chrono::steady_clock::now();
+        Structure S2;
+        symmetric_structure(h->P, S2);
+        h->t_first_symbolic = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        CK(install_structure(h, std::move(S2), nullptr, st));
+        const auto t1 = std::chrono::steady_clock::now();
+        int interrupted = 0;
+        h->force_col = -1;
+        CK(run_refactor(h, Ax_dev, st, &interrupted));
+        h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+        h->t_tail[1] = 0.0;
+        h->tail_passes = 0;
+        h->n_restart_cols = 0;
+        h->first_mode = 1;
+        if (interrupted) {
+            // a step needs another row: its unfinished steps and their
+            // column-elimination-tree ancestors go through the pivoting
+            // kernel, as in the second stage of a restart (Section IV-C);
+            // the finished steps kept their diagonal rows
+            std::vector<int32_t> fin(n);
+            CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            std::vector<uint8_t> finished(n), rmask(n);
+            for (int32_t k = 0; k < n; k++) finished[k] = fin[k] == h->epoch;
+            gblu_restart_set(n, h->P.cetree.data(), finished.data(), rmask.data());
+            CK(run_tail(h, Ax_dev, st, rmask, 0, true, true));
+            h->first_mode = 2;
+        }
+        h->factorized = true;
+        return GBLU_OK;
+    }
     const size_t hint = (size_t)(1.25 * (double)(2 * symmetric_fill(h->P) + n));
     std::vector<uint8_t> all(n, 1);
     CK(run_tail(h, Ax_dev, st, all, hint, false, spec));
@@ -2050,6 +2102,8 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->tail_schedule_ms = h->t_tail[2];
     s->tail_upload_ms = h->t_tail[3];
     s->tail_passes = h->tail_passes;
+    s->first_mode = h->first_mode;
+    s->first_symbolic_ms = h->t_first_symbolic;
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

@@ -125,6 +125,12 @@ int auto_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
 // size of the LU factors when every diagonal pivot is kept on a structurally
 // symmetric matrix; used to size the first factorization's pool
 int64_t symmetric_fill(const Pattern &P, double *flops = nullptr);
+// factor structure when every step keeps its diagonal row: L and U^T with
+// the pattern of that Cholesky factor (a superset of the exact LU pattern,
+// equal on structurally symmetric matrices); piv = Q
+void symmetric_structure(const Pattern &P, Structure &S);
+// off-diagonal entries of A whose transposed position is not an entry of A
+int64_t unsymmetric_entries(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
                     int dense_min_rows, Schedule &W);

@@ -75,6 +75,44 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
     return nl;
 }
 
+// Lower adjacency of S = (A + A^T)(Q,Q) by row (cnt[n+1] offsets; the steps j < i
+// adjacent to step i) and the elimination tree of S (Liu's algorithm with
+// path compression).
+static void symmetric_graph(const Pattern &P, std::vector<int64_t> &cnt, std::vector<int32_t> &lowadj,
+                            std::vector<int32_t> &parent)
+{
+    const int32_t n = P.n;
+    cnt.assign(n + 1, 0);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+            const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+            if (i != j) cnt[std::max(i, j) + 1]++;
+        }
+    for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    lowadj.assign(cnt[n], 0);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int32_t c = 0; c < n; c++)
+            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+                const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+                if (i != j) lowadj[pos[std::max(i, j)]++] = std::min(i, j);
+            }
+    }
+    std::vector<int32_t> anc(n, -1);
+    parent.assign(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
+            int32_t i = lowadj[e];
+            while (i != -1 && i < k) {
+                const int32_t next = anc[i];
+                anc[i] = k;
+                if (next == -1) parent[i] = k;
+                i = next;
+            }
+        }
+    }
+}
+
 // Number of entries of the strict lower Cholesky factor of
 // S = (A + A^T)(Q,Q): row structures come from the elimination tree of S by
 // walking up from every off-diagonal entry of row k until a node already
@@ -87,34 +125,9 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
 int64_t symmetric_fill(const Pattern &P, double *flops)
 {
     const int32_t n = P.n;
-    std::vector<int64_t> cnt(n + 1, 0);
-    for (int32_t c = 0; c < n; c++)
-        for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-            const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
-            if (i != j) cnt[std::max(i, j) + 1]++;
-        }
-    for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
-    std::vector<int32_t> lowadj(cnt[n]);
-    {
-        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-        for (int32_t c = 0; c < n; c++)
-            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-                const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
-                if (i != j) lowadj[pos[std::max(i, j)]++] = std::min(i, j);
-            }
-    }
-    std::vector<int32_t> parent(n, -1), anc(n, -1), mark(n, -1);
-    for (int32_t k = 0; k < n; k++) {
-        for (int64_t e = cnt[k]; e < cnt[k + 1]; e++) {
-            int32_t i = lowadj[e];
-            while (i != -1 && i < k) {
-                const int32_t next = anc[i];
-                anc[i] = k;
-                if (next == -1) parent[i] = k;
-                i = next;
-            }
-        }
-    }
+    std::vector<int64_t> cnt;
+    std::vector<int32_t> lowadj, parent, mark(n, -1);
+    symmetric_graph(P, cnt, lowadj, parent);
     int64_t total = 0;
     std::vector<int64_t> colcount(flops ? n : 0, 0);
     for (int32_t k = 0; k < n; k++) {
@@ -575,6 +588,118 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     level_thread.join();
 }
 
+// Off-diagonal entries of A whose transposed position is not an entry of A
+// (duplicates counted once per entry); A is structurally symmetric at 0.
+int64_t unsymmetric_entries(const Pattern &P)
+{
+    const int32_t n = P.n;
+    std::vector<int32_t> rp(n + 1, 0);
+    for (int32_t p = 0; p < P.Ap[n]; p++) rp[P.Ai[p] + 1]++;
+    for (int32_t i = 0; i < n; i++) rp[i + 1] += rp[i];
+    std::vector<int32_t> cols(P.Ap[n]);
+    {
+        std::vector<int32_t> pos(rp.begin(), rp.end() - 1);
+        for (int32_t c = 0; c < n; c++)
+            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) cols[pos[P.Ai[p]]++] = c;
+    }
+    // column j's rows marked; row j's columns c must each be marked (A(c, j))
+    std::vector<int32_t> mark(n, -1);
+    int64_t miss = 0;
+    for (int32_t j = 0; j < n; j++) {
+        for (int32_t p = P.Ap[j]; p < P.Ap[j + 1]; p++) mark[P.Ai[p]] = j;
+        for (int32_t e = rp[j]; e < rp[j + 1]; e++) miss += cols[e] != j && mark[cols[e]] != j;
+    }
+    return miss;
+}
+
+// Factor structure of a first factorization that predicts every step to
+// keep its diagonal row (piv = Q).  L and U^T take the pattern of the
+// Cholesky factor of S = (A + A^T)(Q,Q): column k holds the row subtree of k
+// in the elimination tree of S (its U rows, ascending), k itself, then the
+// rows i > k whose row subtree contains k.  This pattern contains the
+// pattern of the LU factors of A(Q,Q) without row exchanges, and equals it
+// when A is structurally symmetric (George and Ng); an entry outside the
+// exact pattern only sums products with a structural zero, so it computes to
+// an exact zero for finite values.  Three passes over the row subtrees: their
+// sizes, then on host threads over fixed row ranges the L entries each range
+// gives every column, then the entries themselves, each range writing its
+// own part of every L column so that the rows stay ascending.
+void symmetric_structure(const Pattern &P, Structure &S)
+{
+    const int32_t n = P.n;
+    std::vector<int64_t> adjp;
+    std::vector<int32_t> adj, parent;
+    symmetric_graph(P, adjp, adj, parent);
+    std::vector<int64_t> rowp(n + 1, 0);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int32_t k = 0; k < n; k++) {
+            mark[k] = k;
+            int64_t c = 0;
+            for (int64_t e = adjp[k]; e < adjp[k + 1]; e++)
+                for (int32_t j = adj[e]; mark[j] != k; j = parent[j]) {
+                    mark[j] = k;
+                    c++;
+                }
+            rowp[k + 1] = rowp[k] + c;
+        }
+    }
+    // walk(k, fn): fn(j) for every j of the row subtree of k
+    auto walk = [&](int32_t k, std::vector<int32_t> &mark, auto &&fn) {
+        mark[k] = k;
+        for (int64_t e = adjp[k]; e < adjp[k + 1]; e++)
+            for (int32_t j = adj[e]; mark[j] != k; j = parent[j]) {
+                mark[j] = k;
+                fn(j);
+            }
+    };
+    std::vector<std::vector<int32_t>> part(kHostThreads);
+    parallel_ranges(n, rowp.data(), [&](int32_t k0, int32_t k1, int t) {
+        std::vector<int32_t> mark(n, -1);
+        std::vector<int32_t> &c = part[t];
+        c.assign(n, 0);
+        for (int32_t k = k0; k < k1; k++) walk(k, mark, [&](int32_t j) { c[j]++; });
+    });
+    S.n = n;
+    S.LUp.assign(n + 1, 0);
+    S.nU.assign(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        int64_t nl = 0;
+        for (const std::vector<int32_t> &c : part)
+            if (!c.empty()) nl += c[k];
+        S.nU[k] = (int32_t)(rowp[k + 1] - rowp[k]) + 1;
+        S.LUp[k + 1] = S.LUp[k] + S.nU[k] + nl;
+    }
+    // each range's first slot in every L column, ranges in ascending order
+    for (int32_t k = 0; k < n; k++) {
+        int64_t o = S.LUp[k] + S.nU[k];
+        for (std::vector<int32_t> &c : part)
+            if (!c.empty()) {
+                const int32_t m = c[k];
+                c[k] = (int32_t)(o - S.LUp[k]);
+                o += m;
+            }
+    }
+    S.LUi.assign(S.LUp[n], 0);
+    int32_t *LUi = S.LUi.data();
+    parallel_ranges(n, rowp.data(), [&](int32_t k0, int32_t k1, int t) {
+        std::vector<int32_t> mark(n, -1);
+        std::vector<int32_t> &off = part[t];
+        for (int32_t k = k0; k < k1; k++) {
+            int32_t *u = LUi + S.LUp[k];
+            int32_t m = 0;
+            walk(k, mark, [&](int32_t j) {
+                u[m++] = j;
+                LUi[S.LUp[j] + off[j]++] = k;
+            });
+            std::sort(u, u + m);
+            u[m] = k;
+        }
+    });
+    S.piv = P.Q;
+    S.pinv = P.qinv;
+}
+
 }  // namespace gblu
 
 
@@ -650,6 +775,33 @@ extern "C" int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *
     const int64_t f = symmetric_fill(P, flops);
     if (fill) *fill = f;
     return GBLU_OK;
+}
+
+extern "C" int64_t gblu_symmetric_structure(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                                            int64_t *LUp, int32_t *LUi, int32_t *nU)
+{
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !Q)
+        return record_error(GBLU_ERR_INVALID_INPUT, "symmetric structure: invalid pattern or null Q");
+    Pattern P;
+    P.n = n;
+    P.Ap.assign(Ap, Ap + n + 1);
+    P.Ai.assign(Ai, Ai + Ap[n]);
+    P.Q.assign(Q, Q + n);
+    P.qinv.assign(n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        if (Q[k] < 0 || Q[k] >= n || P.qinv[Q[k]] >= 0)
+            return record_error(GBLU_ERR_INVALID_INPUT, "symmetric structure: Q is not a permutation");
+        P.qinv[Q[k]] = k;
+    }
+    Structure S;
+    symmetric_structure(P, S);
+    if (LUp && LUi && nU) {
+        std::memcpy(LUp, S.LUp.data(), sizeof(int64_t) * (n + 1));
+        std::memcpy(nU, S.nU.data(), sizeof(int32_t) * n);
+        std::memcpy(LUi, S.LUi.data(), sizeof(int32_t) * S.LUi.size());
+    }
+    return S.nnz();
 }
 
 extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)

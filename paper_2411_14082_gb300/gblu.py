@@ -46,7 +46,7 @@ EXPORTED = [
     "gblu_order_amf", "gblu_last_status", "gblu_solve_partition",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
-    "gblu_fp64_fma_rate", "gblu_step_batch",
+    "gblu_fp64_fma_rate", "gblu_step_batch", "gblu_symmetric_structure",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -81,7 +81,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("dense_rows", ctypes.c_int32),
                 ("tail_kernel_ms", ctypes.c_double), ("tail_repack_ms", ctypes.c_double),
                 ("tail_schedule_ms", ctypes.c_double), ("tail_upload_ms", ctypes.c_double),
-                ("tail_passes", ctypes.c_int32)]
+                ("tail_passes", ctypes.c_int32), ("first_mode", ctypes.c_int32),
+                ("first_symbolic_ms", ctypes.c_double)]
 
 
 class RequestResult(ctypes.Structure):
@@ -145,6 +146,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_order_nd.restype = ctypes.c_int
         lib.gblu_symmetric_fill.argtypes = [I32, P, P, P]
         lib.gblu_symmetric_fill.restype = I64
+        lib.gblu_symmetric_structure.argtypes = [I32, P, P, P, P, P, P]
+        lib.gblu_symmetric_structure.restype = I64
         lib.gblu_order_cnd.argtypes = [I32, P, P, P]
         lib.gblu_order_cnd.restype = ctypes.c_int
         lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
@@ -264,7 +267,7 @@ class Solver:
         if warp_column_max is not None:
             o.warp_column_max = warp_column_max
         if speculate_first is not None:
-            o.speculate_first = int(bool(speculate_first))
+            o.speculate_first = int(speculate_first)
         h = ctypes.c_void_p()
         _check(lib.gblu_create(ctypes.byref(h), int(device), ctypes.byref(o)))
         self._h = h
@@ -587,6 +590,22 @@ def symmetric_fill(n, Ap, Ai, Q):
     if v < 0:
         raise GbluError(int(v), "invalid pattern or order")
     return int(v)
+
+
+def symmetric_structure(n, Ap, Ai, Q):
+    """The structure gblu_factorize predicts for its first factorization
+    (gblu_symmetric_structure, host): (LUp, LUi, nU) in step numbering."""
+    Ap, Ai, Q = _i32(Ap), _i32(Ai), _i32(Q)
+    lib = load()
+    nnz = lib.gblu_symmetric_structure(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), None, None, None)
+    if nnz < 0:
+        raise GbluError(int(nnz), "invalid pattern or order")
+    LUp = np.empty(n + 1, np.int64)
+    LUi = np.empty(max(nnz, 1), np.int32)
+    nU = np.empty(n, np.int32)
+    lib.gblu_symmetric_structure(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), _np_ptr(LUp), _np_ptr(LUi),
+                                 _np_ptr(nU))
+    return LUp, LUi[:nnz], nU
 
 
 def column_etree(n, Ap, Ai, Q=None):

@@ -1,6 +1,9 @@
 """First factorization (Algorithm 1 with the threshold rule and the diagonal
 as the preferred row) in speculative passes against the same factorization
-that waits on every earlier unfinished step in order.
+that waits on every earlier unfinished step in order, and (the default) on
+the predicted structure: the checked re-factorization kernel computes every
+column there, and a failing check sends the unfinished steps and their
+column-elimination-tree ancestors to the pivoting kernel.
 
 The two give the same dependencies in the same ascending order, so their
 factors are bit-for-bit equal; both equal the oracle within the parity
@@ -50,14 +53,36 @@ def same_factors(f, g):
         assert np.array_equal(f[key], g[key]), key
 
 
+def structure_path_taken(n, Ap, Ai, Ax, Q):
+    """The library's rule for the predicted structure: every diagonal entry
+    present and nonzero, at most 2% of the off-diagonal entries without
+    their transposed entry."""
+    if zero_diagonals(n, Ap, Ai, Ax, Q):
+        return False
+    cols = np.repeat(np.arange(n), np.diff(np.asarray(Ap, np.int64)))
+    off = [(int(r), int(c)) for r, c in zip(Ai, cols) if r != c]
+    keys = set(off)
+    miss = sum((c, r) not in keys for r, c in off)
+    return miss * 50 <= len(off)
+
+
 def check(n, Ap, Ai, Ax, Q, rtol=1e-10):
     lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
     assert lu.status == O.OK
     moved = int(np.count_nonzero(lu.piv != Q))
-    fs, ss = factor(n, Ap, Ai, Ax, Q, True)
-    fw, sw = factor(n, Ap, Ai, Ax, Q, False)
+    fs, ss = factor(n, Ap, Ai, Ax, Q, 1)
+    fw, sw = factor(n, Ap, Ai, Ax, Q, 0)
     same_factors(fs, fw)
     compare_factors(fs, lu, rtol)
+    fp, sp_ = factor(n, Ap, Ai, Ax, Q, 2)
+    compare_factors(fp, lu, rtol)
+    if structure_path_taken(n, Ap, Ai, Ax, Q):
+        assert sp_["first_mode"] == (1 if moved == 0 else 2)
+        if moved == 0:
+            assert sp_["tail_passes"] == 0
+    else:
+        assert sp_["first_mode"] == 0
+        same_factors(fp, fs)
     assert sw["tail_passes"] == 1
     if moved == 0 or zero_diagonals(n, Ap, Ai, Ax, Q) > 4:
         assert ss["tail_passes"] == 1
@@ -69,6 +94,7 @@ def check(n, Ap, Ai, Ax, Q, rtol=1e-10):
 def test_mesh_every_step_keeps_its_diagonal():
     ckt = inputs.rc_mesh3d(40, 40, 4, seed=7, n_fet=100)
     n, Ap, Ai, Ax = ckt.csc()
+    assert structure_path_taken(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt))
     moved, passes = check(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt))
     assert moved == 0 and passes == 1
 
@@ -114,6 +140,7 @@ def test_one_step_leaves_its_diagonal():
         if lu.status != O.OK or np.count_nonzero(lu.piv != Q) != 2:
             assert tried < 20
             continue
+        assert structure_path_taken(n, Ap, Ai, Ax2, Q)
         moved, passes = check(n, Ap, Ai, Ax2, Q)
         assert moved == 2 and passes in (2, 3)
         return
@@ -153,7 +180,7 @@ def test_singular_matrix_is_reported_after_speculation():
     Ap = np.array([0, 3, 6, 9])
     Ai = np.array([0, 1, 2, 0, 1, 2, 0, 1, 2])
     Ax = np.array([1.0, 2.0, 3.0, 2.0, 4.0, 6.0, 1.0, 0.0, 1.0])
-    for speculate in (True, False):
+    for speculate in (2, 1, 0):
         s = gblu.Solver(DEV, speculate_first=speculate)
         s.analyze(3, Ap, Ai, np.arange(3))
         with pytest.raises(gblu.GbluError) as ei:

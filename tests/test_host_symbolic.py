@@ -202,9 +202,9 @@ def test_default_options_match_the_header():
     lib.gblu_default_opts(ctypes.byref(o))
     assert o.pivot_tol == 1e-3 and o.alpha == 2.0 and o.spin_limit == 1 << 24
     assert o.solve_dense_density == 0.9 and o.solve_slices == 8
-    assert o.warp_column_max == 1024 and o.speculate_first == 1
+    assert o.warp_column_max == 1024 and o.speculate_first == 2
     # an out-of-range switch is rejected before any device work
-    o.speculate_first = 2
+    o.speculate_first = 3
     h = ctypes.c_void_p()
     assert lib.gblu_create(ctypes.byref(h), 0, ctypes.byref(o)) == gblu.ERR_INVALID_INPUT
 
@@ -236,6 +236,78 @@ def test_symmetric_cost_against_brute_force():
         assert gblu.symmetric_fill(n, Ap, Ai, Q) == bf
     with pytest.raises(gblu.GbluError):
         gblu.symmetric_cost(3, np.array([0, 1, 2, 3]), np.array([0, 1, 2]), np.array([0, 0, 1]))
+
+
+def boolean_lu(B):
+    """Pattern of the LU factors of the square boolean matrix B (diagonal
+    set) without row exchanges: dense boolean right-looking elimination."""
+    B = B.copy()
+    np.fill_diagonal(B, True)
+    n = len(B)
+    for k in range(n):
+        rows = np.nonzero(B[k + 1:, k])[0] + k + 1
+        cols = np.nonzero(B[k, k + 1:])[0] + k + 1
+        B[np.ix_(rows, cols)] = True
+    return B
+
+
+def structure_pattern(n, LUp, LUi, nU):
+    """Dense boolean L + U of a structure in step numbering; also checks the
+    column layout: U rows ascending, the diagonal last, L rows ascending."""
+    M = np.zeros((n, n), dtype=bool)
+    for k in range(n):
+        col = LUi[LUp[k]:LUp[k + 1]]
+        u, low = col[:nU[k]], col[nU[k]:]
+        assert u[-1] == k and np.all(np.diff(u) > 0) and np.all(u < k + 1)
+        assert np.all(np.diff(low) > 0) and np.all(low > k)
+        M[col, k] = True
+    return M
+
+
+def test_predicted_first_structure():
+    """gblu_symmetric_structure (the structure the first factorization
+    predicts) is the Cholesky pattern of (A + A^T)(Q,Q) for L and U^T,
+    found here by dense boolean elimination; it contains the pattern of the
+    LU factors of A(Q,Q) without row exchanges and equals it when A is
+    structurally symmetric."""
+    rng = np.random.default_rng(29)
+    for trial in range(40):
+        n = int(rng.integers(1, 60))
+        _, Ap, Ai, _ = inputs.random_sparse(n, rng.uniform(0.02, 0.2), rng)
+        if trial % 2:   # structurally symmetric
+            _, Ap, Ai, _ = inputs.dense_to_csc(np.ones((n, n)), (lambda m: m | m.T)(dense_pattern(n, Ap, Ai)))
+        Q = rng.permutation(n).astype(np.int32)
+        LUp, LUi, nU = gblu.symmetric_structure(n, Ap, Ai, Q)
+        M = structure_pattern(n, LUp, LUi, nU)
+        A = dense_pattern(n, Ap, Ai)
+        chol = boolean_lu((A | A.T)[np.ix_(Q, Q)])
+        assert np.array_equal(M, chol)
+        assert np.array_equal(M, M.T)
+        exact = boolean_lu(A[np.ix_(Q, Q)])
+        assert not np.any(exact & ~M)
+        if trial % 2:
+            assert np.array_equal(M, exact)
+    with pytest.raises(gblu.GbluError):
+        gblu.symmetric_structure(3, np.array([0, 1, 2, 3]), np.array([0, 1, 2]), np.array([0, 0, 1]))
+
+
+def test_predicted_structure_holds_the_oracle_factors():
+    """On diagonally dominant values the oracle keeps every diagonal row
+    (Algorithm 1 with the threshold rule), and its L and U lie inside the
+    predicted structure."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(31)
+    for trial in range(10):
+        n = int(rng.integers(5, 80))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.03, 0.15), rng, dominance=4.0 * n)
+        Q = rng.permutation(n).astype(np.int32)
+        lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
+        assert lu.status == O.OK and np.array_equal(lu.piv, Q)
+        M = structure_pattern(n, *gblu.symmetric_structure(n, Ap, Ai, Q))
+        for part in ("L", "U"):
+            p, i = np.asarray(getattr(lu, part + "p"), np.int64), getattr(lu, part + "i")
+            cols = np.repeat(np.arange(n), np.diff(p))
+            assert np.all(M[i, cols]), part
 
 
 def test_constrained_minimum_degree():
