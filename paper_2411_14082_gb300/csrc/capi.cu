@@ -265,8 +265,8 @@ void release(gblu_ctx *h, DBuf<T> &b)
     b.cap = 0;
 }
 
-template <class T>
-int upload(gblu_ctx *h, DBuf<T> &b, const std::vector<T> &v, cudaStream_t st)
+template <class T, class A>
+int upload(gblu_ctx *h, DBuf<T> &b, const std::vector<T, A> &v, cudaStream_t st)
 {
     CK(ensure(h, b, v.size()));
     if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
@@ -694,7 +694,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
         S2.LUp[k + 1] = S2.LUp[k] + cnu[k] + cnl[k];
     }
     if (S2.LUp[n] > INT32_MAX) return fail(GBLU_ERR_NOMEM, "factor too large (> 2^31 entries)");
-    S2.LUi.assign(S2.LUp[n], 0);
+    S2.LUi.resize(S2.LUp[n]);
     std::vector<double> V2(S2.LUp[n]);
     // columns are independent: repack them on several host threads, in
     // ranges of about equal entry counts

@@ -3,7 +3,9 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gblu.h"
@@ -24,12 +26,39 @@ struct Pattern {
     std::vector<int32_t> Acol, Aslot;
 };
 
+// Host vector whose resize leaves new elements of trivial types
+// uninitialized: the factor-sized index arrays are written in full by host
+// threads right after they are sized, so that their pages are first touched
+// in parallel rather than zeroed on one thread.
+template <class T>
+struct NoInitAllocator : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAllocator<U>;
+    };
+    NoInitAllocator() = default;
+    template <class U>
+    NoInitAllocator(const NoInitAllocator<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept
+    {
+        ::new ((void *)p) U;
+    }
+    template <class U, class... Args>
+    void construct(U *p, Args &&...args)
+    {
+        ::new ((void *)p) U(std::forward<Args>(args)...);
+    }
+};
+template <class T>
+using BigVec = std::vector<T, NoInitAllocator<T>>;
+
 // Fixed-pattern factor structure in step numbering (CSC, per column: the U
 // rows ascending with the diagonal last, then the L rows ascending).
 struct Structure {
     int32_t n = 0;
     std::vector<int64_t> LUp;  // n+1
-    std::vector<int32_t> LUi;  // step numbers
+    BigVec<int32_t> LUi;       // step numbers
     std::vector<int32_t> nU;   // U entries of each column incl. the diagonal
     std::vector<int32_t> piv;  // original row pivotal at each step
     std::vector<int32_t> pinv;
@@ -49,15 +78,15 @@ struct Schedule {
     // the sync-free tasks start at level_task_ptr[div_level]
     std::vector<int32_t> task_ptr, task_cols, level_task_ptr;
     std::vector<int32_t> amap;        // A slot -> position inside its column
-    std::vector<int32_t> LUi_orig;    // L entries: original row ids (U: step ids)
+    BigVec<int32_t> LUi_orig;         // L entries: original row ids (U: step ids)
     // chain[j] = 1 iff L(:,j) = {j+1} followed by the rows of L(:,j+1), i.e.
     // j and j+1 are consecutive columns of one supernode of L
     std::vector<uint8_t> chain;
     double flops = 0;
     // solves: row-wise (CSR) copies, slots into the factor value array
     std::vector<int64_t> Lrp, Urp;        // n+1
-    std::vector<int32_t> Lcol, Urow_col;  // column (step) of each entry
-    std::vector<int32_t> Lslot, Uslot;    // slot in LUx
+    BigVec<int32_t> Lcol, Urow_col;       // column (step) of each entry
+    BigVec<int32_t> Lslot, Uslot;         // slot in LUx
     std::vector<int32_t> Udiag;           // slot of U(i,i)
     // sparse part of each solve (rows [0, lp0) forward, [0, up0) backward),
     // solved in row blocks: block b is rows [lbs[b], lbs[b+1]), at most

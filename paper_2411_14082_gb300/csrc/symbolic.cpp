@@ -2,6 +2,7 @@
 // estimate of a first factorization and the fixed-pattern schedules.  No
 // device code and no CUDA calls in this file.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -186,6 +187,31 @@ static void parallel_ranges(int32_t n, const T *ptr, F &&fn)
     for (std::thread &x : th) x.join();
 }
 
+// fn(k0, k1, t) over chunks [k0, k1) of `chunk` indices, taken in turn by
+// up to kHostThreads host threads t as each finishes its previous chunk (for
+// work whose cost per index is not known in advance)
+template <class F>
+static void parallel_chunks(int32_t n, int32_t chunk, F &&fn)
+{
+    const int nt = (int)std::max(1u, std::min((unsigned)kHostThreads, std::thread::hardware_concurrency()));
+    if (nt == 1 || n <= chunk) {
+        if (n > 0) fn(0, n, 0);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    auto run = [&](int t) {
+        for (;;) {
+            const int64_t k0 = next.fetch_add(chunk);
+            if (k0 >= n) break;
+            fn((int32_t)k0, (int32_t)std::min<int64_t>(n, k0 + chunk), t);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(run, t);
+    run(0);
+    for (std::thread &x : th) x.join();
+}
+
 static int32_t dense_split(int32_t n, const std::vector<int64_t> &count_from, const std::vector<int64_t> &rowlen,
                            const SolveSplit &sp, std::vector<int32_t> &cut)
 {
@@ -354,7 +380,7 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     // ---- A slot -> position in its column (columns are sorted) ----
     const int64_t nnzA = (int64_t)P.Ai.size();
     W.amap.assign(nnzA, -1);
-    parallel_ranges(n, P.Ap.data(), [&](int32_t c0, int32_t c1, int) {
+    parallel_chunks(n, 2048, [&](int32_t c0, int32_t c1, int) {
         for (int32_t c = c0; c < c1; c++) {
             const int32_t k = P.qinv[c];
             const int32_t *col = S.LUi.data() + S.LUp[k];
@@ -367,7 +393,7 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         }
     });
     // ---- original row ids of L entries (used by the restart kernel) ----
-    W.LUi_orig.assign(S.LUi.size(), 0);
+    W.LUi_orig.resize(S.LUi.size());
     parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
         for (int32_t k = k0; k < k1; k++)
             for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
@@ -381,11 +407,11 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
         W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
     }
-    // ---- row-wise copies for the solves: entry counts per row from
-    // per-thread histograms over column ranges; then each thread fills the
-    // rows of its own row range, taking the columns in ascending order (so
+    // ---- row-wise copies for the solves: per-thread histograms of the row
+    // entries over column ranges give each range its first position in
+    // every row; each thread then copies its columns in ascending order, so
     // every row lists its entries by ascending column, as a serial pass
-    // would) and finding its rows in each sorted column by binary search ----
+    // would ----
     W.Lrp.assign(n + 1, 0);
     W.Urp.assign(n + 1, 0);
     W.Udiag.assign(n, 0);
@@ -409,36 +435,38 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
                 W.Urp[i + 1] += hu[t][i];
             }
         }
-    }
-    for (int32_t i = 0; i < n; i++) { W.Lrp[i + 1] += W.Lrp[i]; W.Urp[i + 1] += W.Urp[i]; }
-    W.Lcol.assign(W.Lrp[n], 0);
-    W.Lslot.assign(W.Lrp[n], 0);
-    W.Urow_col.assign(W.Urp[n], 0);
-    W.Uslot.assign(W.Urp[n], 0);
-    {
-        std::vector<int64_t> both(n + 1);
-        for (int32_t i = 0; i <= n; i++) both[i] = W.Lrp[i] + W.Urp[i];
+        for (int32_t i = 0; i < n; i++) {
+            W.Lrp[i + 1] += W.Lrp[i];
+            W.Urp[i + 1] += W.Urp[i];
+        }
         std::vector<int64_t> lp(W.Lrp.begin(), W.Lrp.end() - 1), up(W.Urp.begin(), W.Urp.end() - 1);
-        parallel_ranges(n, both.data(), [&](int32_t r0, int32_t r1, int) {
-            for (int32_t k = 0; k < n; k++) {
-                const int32_t *c = S.LUi.data();
-                const int64_t b = S.LUp[k], d = b + S.nU[k] - 1, e1 = S.LUp[k + 1];
-                // U rows of column k are below k; L rows above it
-                if (k > r0) {
-                    int64_t e = std::lower_bound(c + b, c + d, r0) - c;
-                    for (; e < d && c[e] < r1; e++) {
-                        const int32_t i = c[e];
-                        W.Urow_col[up[i]] = k;
-                        W.Uslot[up[i]++] = (int32_t)e;
-                    }
+        for (int t = 0; t < kHostThreads; t++) {
+            if (hl[t].empty()) continue;
+            for (int32_t i = 0; i < n; i++) {
+                const int64_t a = hl[t][i], b = hu[t][i];
+                hl[t][i] = lp[i];
+                hu[t][i] = up[i];
+                lp[i] += a;
+                up[i] += b;
+            }
+        }
+        W.Lcol.resize(W.Lrp[n]);
+        W.Lslot.resize(W.Lrp[n]);
+        W.Urow_col.resize(W.Urp[n]);
+        W.Uslot.resize(W.Urp[n]);
+        parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int t) {
+            std::vector<int64_t> &ol = hl[t], &ou = hu[t];
+            for (int32_t k = k0; k < k1; k++) {
+                const int64_t d = S.LUp[k] + S.nU[k] - 1;
+                for (int64_t e = S.LUp[k]; e < d; e++) {
+                    const int64_t q = ou[S.LUi[e]]++;
+                    W.Urow_col[q] = k;
+                    W.Uslot[q] = (int32_t)e;
                 }
-                if (k + 1 < r1) {
-                    int64_t e = std::lower_bound(c + d + 1, c + e1, r0) - c;
-                    for (; e < e1 && c[e] < r1; e++) {
-                        const int32_t i = c[e];
-                        W.Lcol[lp[i]] = k;
-                        W.Lslot[lp[i]++] = (int32_t)e;
-                    }
+                for (int64_t e = d + 1; e < S.LUp[k + 1]; e++) {
+                    const int64_t q = ol[S.LUi[e]]++;
+                    W.Lcol[q] = k;
+                    W.Lslot[q] = (int32_t)e;
                 }
             }
         });
@@ -541,7 +569,7 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             int32_t v = 0;
             for (int32_t i = bs[b]; i < bs[b + 1]; i++) {
                 const std::vector<int64_t> &rp = lower ? W.Lrp : W.Urp;
-                const std::vector<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
+                const BigVec<int32_t> &cc = lower ? W.Lcol : W.Urow_col;
                 for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
                     const int32_t j = cc[e];
                     if (j < nrows && blk[j] != b) v = std::max(v, lv[blk[j]] + 1);
@@ -620,30 +648,16 @@ int64_t unsymmetric_entries(const Pattern &P)
 // pattern of the LU factors of A(Q,Q) without row exchanges, and equals it
 // when A is structurally symmetric (George and Ng); an entry outside the
 // exact pattern only sums products with a structural zero, so it computes to
-// an exact zero for finite values.  Three passes over the row subtrees: their
-// sizes, then on host threads over fixed row ranges the L entries each range
-// gives every column, then the entries themselves, each range writing its
-// own part of every L column so that the rows stay ascending.
+// an exact zero for finite values.  Three passes over the row subtrees on
+// host threads: their sizes, then over fixed row ranges the L entries each
+// range gives every column, then the entries themselves, each range writing
+// its own part of every L column so that the rows stay ascending.
 void symmetric_structure(const Pattern &P, Structure &S)
 {
     const int32_t n = P.n;
     std::vector<int64_t> adjp;
     std::vector<int32_t> adj, parent;
     symmetric_graph(P, adjp, adj, parent);
-    std::vector<int64_t> rowp(n + 1, 0);
-    {
-        std::vector<int32_t> mark(n, -1);
-        for (int32_t k = 0; k < n; k++) {
-            mark[k] = k;
-            int64_t c = 0;
-            for (int64_t e = adjp[k]; e < adjp[k + 1]; e++)
-                for (int32_t j = adj[e]; mark[j] != k; j = parent[j]) {
-                    mark[j] = k;
-                    c++;
-                }
-            rowp[k + 1] = rowp[k] + c;
-        }
-    }
     // walk(k, fn): fn(j) for every j of the row subtree of k
     auto walk = [&](int32_t k, std::vector<int32_t> &mark, auto &&fn) {
         mark[k] = k;
@@ -653,6 +667,20 @@ void symmetric_structure(const Pattern &P, Structure &S)
                 fn(j);
             }
     };
+    std::vector<int64_t> rowp(n + 1, 0);
+    {
+        std::vector<std::vector<int32_t>> marks(kHostThreads);
+        parallel_chunks(n, 1024, [&](int32_t k0, int32_t k1, int t) {
+            std::vector<int32_t> &mark = marks[t];
+            if (mark.empty()) mark.assign(n, -1);
+            for (int32_t k = k0; k < k1; k++) {
+                int64_t c = 0;
+                walk(k, mark, [&](int32_t) { c++; });
+                rowp[k + 1] = c;
+            }
+        });
+    }
+    for (int32_t k = 0; k < n; k++) rowp[k + 1] += rowp[k];
     std::vector<std::vector<int32_t>> part(kHostThreads);
     parallel_ranges(n, rowp.data(), [&](int32_t k0, int32_t k1, int t) {
         std::vector<int32_t> mark(n, -1);
@@ -680,19 +708,46 @@ void symmetric_structure(const Pattern &P, Structure &S)
                 o += m;
             }
     }
-    S.LUi.assign(S.LUp[n], 0);
+    S.LUi.resize(S.LUp[n]);
     int32_t *LUi = S.LUi.data();
+    // the walk from one entry of row k climbs the tree to ascending steps, so
+    // the U rows of column k come as ascending runs, merged pairwise
     parallel_ranges(n, rowp.data(), [&](int32_t k0, int32_t k1, int t) {
-        std::vector<int32_t> mark(n, -1);
+        std::vector<int32_t> mark(n, -1), bnd, tmp;
         std::vector<int32_t> &off = part[t];
         for (int32_t k = k0; k < k1; k++) {
             int32_t *u = LUi + S.LUp[k];
             int32_t m = 0;
-            walk(k, mark, [&](int32_t j) {
-                u[m++] = j;
-                LUi[S.LUp[j] + off[j]++] = k;
-            });
-            std::sort(u, u + m);
+            bnd.clear();
+            mark[k] = k;
+            for (int64_t e = adjp[k]; e < adjp[k + 1]; e++) {
+                int32_t j = adj[e];
+                if (mark[j] == k) continue;
+                bnd.push_back(m);
+                for (; mark[j] != k; j = parent[j]) {
+                    mark[j] = k;
+                    u[m++] = j;
+                    LUi[S.LUp[j] + off[j]++] = k;
+                }
+            }
+            size_t nr = bnd.size();
+            bnd.push_back(m);
+            if (nr > 1) {
+                tmp.resize(m);
+                int32_t *src = u, *dst = tmp.data();
+                while (nr > 1) {
+                    size_t w = 0;
+                    for (size_t r = 0; r < nr; r += 2) {
+                        const int32_t a = bnd[r], mid = bnd[std::min(r + 1, nr)], b = bnd[std::min(r + 2, nr)];
+                        std::merge(src + a, src + mid, src + mid, src + b, dst + a);
+                        bnd[w++] = a;
+                    }
+                    bnd[w] = m;
+                    nr = w;
+                    std::swap(src, dst);
+                }
+                if (src != u) std::copy(src, src + m, u);
+            }
             u[m] = k;
         }
     });
