@@ -297,7 +297,7 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
 // i+1 and publishes its descriptor; one barrier per run.
 constexpr int kMaxRun = 32;
 constexpr int kTri = kMaxRun * (kMaxRun - 1) / 2;   // strictly lower triangle
-constexpr int kRows = 4;                            // rows of R per thread per pass
+constexpr int kRows = 2;                            // rows of R per thread per pass
 
 // offset of column d of the staged triangle (column d holds kMaxRun-1-d rows)
 __device__ __forceinline__ int tri_off(int d) { return d * (kMaxRun - 1) - d * (d - 1) / 2; }
@@ -532,7 +532,7 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
                     if (sl[u] >= 0 && sl[u] < hend) sl[u] = -1;   // the leader's
                     v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
-#pragma unroll 4
+#pragma unroll 8
                 for (int d = 0; d < w; d++) {
                     const R m = x[t + d];
                     const R *lv = a.LUx + r.base[d] + r0 + wt;
