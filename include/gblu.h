@@ -96,7 +96,7 @@ typedef struct {
     /* warp assignment of the re-factorization (Section IV-B's task
        granularity, retuned for warps): columns of at most warp_column_max
        entries are computed by one warp (eight per CTA), longer ones by half
-       a CTA (up to 4096 entries) or a whole CTA.  32..1024, default 1024;
+       a CTA (up to 2560 entries) or a whole CTA.  32..640, default 640;
        gblu_autotune measures it. */
     int warp_column_max;
     /* first factorization (gblu_factorize, Algorithm 1 with the threshold

@@ -82,6 +82,7 @@ struct gblu_ctx {
     int sm_count = 0;
     int l2_bytes = 0;
     int ref_blocks_per_sm = 0, ref_grid = 0, solve_grid = 0, res_blocks = 0, trail_per_sm = 0;
+    int batch_blocks_per_sm = 0;   // refactor_batch_kernel CTAs that fit on an SM
     int ref32_blocks_per_sm = 0, ref32_grid = 0;
     bool f32_valid = false, f32_widened = false;   // single-precision factors of the last call
     int32_t force_col = -1;                        // forced check failure of the next refactorization
@@ -870,14 +871,14 @@ int gblu_create(gblu_handle *out, int device, const gblu_opts *o)
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->ctl, sizeof(DevCtl));
     if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(DevCtl));
     int r = 0;
-    if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm);
+    if (e == cudaSuccess) r = refactor_setup(kRefCapLong, &h->ref_blocks_per_sm, &h->batch_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = refactor_setup_f32(kRefCapLong, &h->ref32_blocks_per_sm);
     if (e == cudaSuccess && r == 0) r = solve_syncfree_grid(&h->solve_grid);
     int trail_per_sm = 0;
     if (e == cudaSuccess && r == 0) r = trail_setup(&trail_per_sm);
     if (e == cudaSuccess && r == 0) r = dense_setup(GBLU_DENSE_MAX_ROWS);
     if (e == cudaSuccess && r == 0) r = tail_setup();
-    if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1) {
+    if (e != cudaSuccess || r != 0 || h->ref_blocks_per_sm < 1 || h->batch_blocks_per_sm < 1) {
         const char *msg = cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)r);
         if (h->hctl) cudaFreeHost(h->hctl);
         if (h->ctl) cudaFree(h->ctl);
@@ -1337,7 +1338,7 @@ int gblu_refactorize_batch(gblu_handle h, int32_t nsets, const double *Ax_dev, i
     if (ltp[div] < ntask) {               // pipeline mode
         a0.task_begin = ltp[div];
         a0.ntasks = ntask - ltp[div];
-        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, pgrid(h, h->ref_blocks_per_sm), h->epoch, h->bticket.p, st,
+        KL(launch_refactor_batch(h->bargs.p, a0, nsets, true, pgrid(h, h->batch_blocks_per_sm), h->epoch, h->bticket.p, st,
                                  batch_group(h, nsets)));
     }
     h->bctl_host.resize(nsets);
@@ -1434,7 +1435,7 @@ int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_
     CU(cudaMemcpyAsync(h0->bargs.p, h0->bargs_host.data(), sizeof(RefactorArgs) * nh, cudaMemcpyHostToDevice, st));
     {
         gblu_ctx *h = h0;   // the launch is counted on the leading handle
-        KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, pgrid(h0, h0->ref_blocks_per_sm),
+        KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, pgrid(h0, h0->batch_blocks_per_sm),
                                  ep, h0->bticket.p, st));
         h->launches++;   // the control-block reset kernel
     }
@@ -1718,7 +1719,7 @@ static int capture_step_batch(gblu_ctx *h, int32_t nsets, const double *Ax_dev, 
         if (ltp[div] < ntask) {
             a0.task_begin = ltp[div];
             a0.ntasks = ntask - ltp[div];
-            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, pgrid(h, h->ref_blocks_per_sm), 1, h->bticket.p, gs,
+            KL(launch_refactor_batch(h->bgargs.p, a0, nsets, true, pgrid(h, h->batch_blocks_per_sm), 1, h->bticket.p, gs,
                                      batch_group(h, nsets)));
         }
         CU(cudaMemcpyAsync(h->bgctl_host, h->bctl.p, sizeof(DevCtl) * nsets, cudaMemcpyDeviceToHost, gs));
@@ -1879,7 +1880,7 @@ int gblu_autotune(gblu_handle h, const double *Ax_dev, const double *b_dev, doub
     }
     // the warp assignment: the longest column one warp computes (Section
     // IV-B's task granularity), by re-factorization time
-    const int wcols[] = {256, 512, 1024};
+    const int wcols[] = {256, 512, kRefCapShort};
     for (int wc : wcols) {
         if (rc != GBLU_OK) break;
         if (wc == best.warp_column_max) continue;

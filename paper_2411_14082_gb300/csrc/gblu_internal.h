@@ -280,7 +280,7 @@ struct SolveArgs {
 
 // kernel launchers (kernels.cu); each returns a cudaError_t as int
 int launch_begin_refactor(DevCtl *ctl, void *stream);
-int refactor_setup(int cap_long, int *blocks_per_sm);
+int refactor_setup(int cap_long, int *blocks_per_sm, int *batch_blocks_per_sm);
 int refactor_setup_f32(int cap_long, int *blocks_per_sm);
 int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int epoch, void *stream);
 // the same tasks with single-precision factor values (no dense tail)
@@ -359,8 +359,8 @@ int launch_trail(const SolveArgs &a, const TrailArgs &t, bool lower, int grid, v
 int trail_setup(int *blocks_per_sm);
 
 constexpr int kRefThreads = 256;       // 8 warps per refactor CTA
-constexpr int kRefCapShort = 1024;     // work-vector entries per warp (short columns)
-constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 96 KB
+constexpr int kRefCapShort = 640;      // work-vector entries per warp (short columns)
+constexpr int kRefCapLong = 8 * kRefCapShort;  // per CTA (long columns), 60 KB: 3 CTAs per SM
 constexpr int kTailThreads = 256;
 constexpr int kSolveWarpsPerBlock = 8;
 constexpr int kSolveBlockRows = 32;   // rows of one block of the sparse solves

@@ -10,8 +10,8 @@
 // the stores U(:,k) = x(U rows), L(:,k) = x(L rows) / x(k).
 //
 // Work is handed out as tasks (built on the host in level order): a task is
-// one long column (all 8 warps of a CTA, work vector of up to 8,192 entries
-// in shared memory), two medium columns (4 warps and up to 4,096 entries
+// one long column (all 8 warps of a CTA, work vector of up to 5,120 entries
+// in shared memory), two medium columns (4 warps and up to 2,560 entries
 // each, synchronized by named barriers), or up to 8 short columns (one per
 // warp).  The
 // slot of an L(:,j) row inside column k comes from a binary search in the
@@ -219,6 +219,7 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
                     if (key[u] >= 0 && sl[u] < 0) bad = true;
                     v[u] = sl[u] >= 0 ? x[sl[u]] : R(0);
                 }
+#pragma unroll 8
                 for (int d = 0; d < w; d++) {
                     const R mv = x[t + d];
                     const long long lbd = __shfl_sync(kFull, m_lb, q0 + d);
@@ -624,7 +625,7 @@ __device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *x
 // Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
 // (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
 template <typename R, bool kWait, bool kDense>
-__global__ void __launch_bounds__(kThreads, 2) refactor_task_kernel(RefactorArgsT<R> a, int epoch, int persistent)
+__global__ void __launch_bounds__(kThreads, 3) refactor_task_kernel(RefactorArgsT<R> a, int epoch, int persistent)
 {
     // a replayed graph passes -1: the epoch was written to the control block
     if (epoch < 0) epoch = ld_volatile(&a.ctl->epoch);
@@ -684,7 +685,7 @@ __device__ __forceinline__ int group_task(long long t, int ntasks, int nsets, in
 }
 
 template <bool kWait>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
                       int32_t *ticket, const SetTask *order, int group)
 {
@@ -763,7 +764,7 @@ int launch_begin_refactor(DevCtl *ctl, void *stream)
     return (int)cudaGetLastError();
 }
 
-int refactor_setup(int cap_long, int *blocks_per_sm)
+int refactor_setup(int cap_long, int *blocks_per_sm, int *batch_blocks_per_sm)
 {
     const size_t sm = (size_t)cap_long * (sizeof(double) + sizeof(int32_t));
     cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<double, true, false>,
@@ -787,6 +788,10 @@ int refactor_setup(int cap_long, int *blocks_per_sm)
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<double, true, true>, kThreads, sm);
     *blocks_per_sm = b1 < b2 ? b1 : b2;
+    // the batch kernel keeps a copy of its set's argument block (it spills a
+    // few registers at three CTAs per SM, which measured faster than two)
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch_blocks_per_sm, refactor_batch_kernel<true>, kThreads, sm);
     return (int)e;
 }
 

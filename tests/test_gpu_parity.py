@@ -332,9 +332,12 @@ def test_every_column_task_kind(sched):
     rng = np.random.default_rng(17)
     lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-3)
     ln = np.diff(lu.Lp) + np.diff(lu.Up)
-    kinds = [(ln <= 1024).sum(), ((ln > 1024) & (ln <= 4096)).sum(),
-             ((ln > 4096) & (ln <= 8192)).sum(), ((ln > 8192) & (ln <= 16384)).sum(),
-             (ln > 16384).sum()]
+    # one warp up to 640 entries; half a CTA up to 2,560; a whole CTA with
+    # its work vector in shared memory up to 5,120, its rows alone there up
+    # to 10,240, and beyond that in global memory
+    kinds = [(ln <= 640).sum(), ((ln > 640) & (ln <= 2560)).sum(),
+             ((ln > 2560) & (ln <= 5120)).sum(), ((ln > 5120) & (ln <= 10240)).sum(),
+             (ln > 10240).sum()]
     assert min(kinds) >= 1 and kinds[3] >= 2, kinds
     s = gblu.Solver(DEV, sched_mode=sched, solve_mode=sched)
     s.analyze(n, Ap, Ai, Q)

@@ -202,7 +202,7 @@ def test_default_options_match_the_header():
     lib.gblu_default_opts(ctypes.byref(o))
     assert o.pivot_tol == 1e-3 and o.alpha == 2.0 and o.spin_limit == 1 << 24
     assert o.solve_dense_density == 0.9 and o.solve_slices == 8
-    assert o.warp_column_max == 1024 and o.speculate_first == 2
+    assert o.warp_column_max == 640 and o.speculate_first == 2
     # an out-of-range switch is rejected before any device work
     o.speculate_first = 3
     h = ctypes.c_void_p()
