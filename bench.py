@@ -84,12 +84,10 @@ def hbm_roofline(bytes_alg, seconds, traffic=None):
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4/library": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
-                                  "bytes": 18.126e9 + 400.8e6},
-    "rc_mesh_200x200x4/geometric": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
-                          "bytes": 16.34e9 + 36.2e6 + 442.6e6},
-    "rc_mesh_120x120x4/geometric": {"refactor_cu_sha256": "8490c075cf94c9024618f1b274fbf6f58ae265dc3566a02f273d1ac730fcd426",
-                          "bytes": 135.8e6 + 83.6e6},
+    "rc_mesh_200x200x4/library": {"refactor_cu_sha256": "653344a75926a1654876d75cfd42a67982710dbe225ee03a70e68fecc00e6df1",
+                                  "bytes": 17.954e9 + 811.2e6},
+    "rc_mesh_120x120x4/library": {"refactor_cu_sha256": "653344a75926a1654876d75cfd42a67982710dbe225ee03a70e68fecc00e6df1",
+                                  "bytes": 4.98e6 + 86.82e6 + 57.50e6},
 }
 
 
