@@ -577,6 +577,11 @@ typedef struct {
        kernel finished the restart set (the tail_* fields describe it) */
     int32_t first_mode;
     double first_symbolic_ms;
+    /* wide columns of the installed structure (at most 64 L entries, at
+       least 256 supernode runs among the dependencies): the re-factorization
+       applies all but their last run of dependencies row by row through the
+       rows of L (0 when the per-CTA scratch would exceed 1 GiB) */
+    int64_t wide_cols;
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

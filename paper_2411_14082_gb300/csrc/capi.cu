@@ -111,6 +111,13 @@ struct gblu_ctx {
     DBuf<int64_t> LUp;
     DBuf<int32_t> LUi, nU, rows, finish, task_ptr, task_cols, amap, piv, pinv;
     DBuf<uint8_t> chain;
+    // wide columns taken row by row: their pull starts and the per-CTA dense
+    // scratch (pull_slots CTAs x n values and n tags, one counter each)
+    DBuf<int32_t> pull_start;
+    DBuf<double> pull_x;
+    DBuf<unsigned long long> pull_tag, pull_ctr;
+    DBuf<int32_t> pull_lock;
+    int32_t pull_slots = 0;
     DBuf<double> vals;
     // solves
     DBuf<int64_t> Lrp, Urp;
@@ -321,6 +328,25 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
     CK(upload(h, h->LUi, h->S.LUi, st));
     CK(upload(h, h->nU, h->S.nU, st));
     CK(upload(h, h->chain, h->W.chain, st));
+    h->pull_slots = 0;
+    if (h->W.pull_cols > 0) {
+        // one scratch per CTA that a persistent launch can hold; only while it
+        // stays within kPullScratchBytes (the columns are pushed otherwise)
+        const int slots = std::max(h->ref_blocks_per_sm, h->batch_blocks_per_sm) * h->sm_count;
+        const size_t bytes = (size_t)slots * (size_t)n * (sizeof(double) + sizeof(unsigned long long));
+        if (bytes <= kPullScratchBytes) {
+            CK(upload(h, h->pull_start, h->W.pull_start, st));
+            CK(ensure(h, h->pull_x, (size_t)slots * n));
+            CK(ensure(h, h->pull_tag, (size_t)slots * n));
+            CK(ensure(h, h->pull_ctr, (size_t)slots));
+            CK(ensure(h, h->pull_lock, (size_t)slots));
+            // tags start below every counter value; every scratch free
+            CU(cudaMemsetAsync(h->pull_tag.p, 0, sizeof(unsigned long long) * (size_t)slots * n, st));
+            CU(cudaMemsetAsync(h->pull_ctr.p, 0, sizeof(unsigned long long) * (size_t)slots, st));
+            CU(cudaMemsetAsync(h->pull_lock.p, 0, sizeof(int32_t) * (size_t)slots, st));
+            h->pull_slots = slots;
+        }
+    }
     CK(upload(h, h->dense_s0, h->W.dense_s0, st));
     if (h->W.dense_m > 0) CK(ensure(h, h->dense, (size_t)h->W.dense_m * h->W.dense_m));
     CK(upload(h, h->piv, h->S.piv, st));
@@ -399,6 +425,18 @@ RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
     a.force_col = h->force_col;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
+    if (h->pull_slots > 0) {
+        a.pull_start = h->pull_start.p;
+        a.Lrp = h->Lrp.p;
+        a.Lcol = h->Lcol.p;
+        a.Lslot = h->Lslot.p;
+        a.pull_x = h->pull_x.p;
+        a.pull_tag = h->pull_tag.p;
+        a.pull_ctr = h->pull_ctr.p;
+        a.pull_lock = h->pull_lock.p;
+        a.pull_slots = h->pull_slots;
+    }
+    a.n = h->S.n;
     return a;
 }
 
@@ -1435,8 +1473,10 @@ int gblu_refactorize_multi(int32_t nh, gblu_handle *hs, const double *const *Ax_
     CU(cudaMemcpyAsync(h0->bargs.p, h0->bargs_host.data(), sizeof(RefactorArgs) * nh, cudaMemcpyHostToDevice, st));
     {
         gblu_ctx *h = h0;   // the launch is counted on the leading handle
+        bool pull = false;
+        for (int32_t i = 0; i < nh; i++) pull = pull || hs[i]->pull_slots > 0;
         KL(launch_refactor_multi(h0->bargs.p, h0->bargs_host[0], nh, h0->morder.p, (int)h0->morder_n, pgrid(h0, h0->batch_blocks_per_sm),
-                                 ep, h0->bticket.p, st));
+                                 ep, h0->bticket.p, st, pull));
         h->launches++;   // the control-block reset kernel
     }
     for (int32_t i = 0; i < nh; i++)
@@ -2105,6 +2145,7 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->tail_passes = h->tail_passes;
     s->first_mode = h->first_mode;
     s->first_symbolic_ms = h->t_first_symbolic;
+    s->wide_cols = h->pull_slots > 0 ? h->W.pull_cols : 0;
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

@@ -120,7 +120,18 @@ struct Schedule {
     int32_t dense_p = 0, dense_m = 0;
     std::vector<int32_t> dense_s0;
     std::vector<int32_t> lcut, ucut;
+    // columns computed row by row over their first dependencies (wide
+    // columns: many dependencies in short supernode runs and a short L
+    // part): pull_start[k] = how many of column k's U entries above the
+    // diagonal are taken that way (0: none); pull_cols = columns with > 0
+    std::vector<int32_t> pull_start;
+    int64_t pull_cols = 0;
 };
+// wide columns: at most kPullMaxL entries in L and at least kPullMinRuns
+// supernode runs among the dependencies
+constexpr int kPullMaxL = 64;
+constexpr int kPullMinRuns = 256;
+constexpr size_t kPullScratchBytes = (size_t)1 << 30;
 
 struct SolveSplit {
     double density = 0.0;   // > 0: longest trailing block at least this dense
@@ -221,6 +232,18 @@ struct RefactorArgsT {
     int32_t skip_done = 0;          // 1: a column whose ready flag holds the epoch is final; skip it
     long long spin_limit;
     DevCtl *ctl;
+    // wide columns (Schedule::pull_start): their first pull_start[k]
+    // dependencies are applied row by row, through rows of L (CSR Lrp,
+    // Lcol, Lslot) and one of pull_slots dense scratches of n values and n
+    // tags (pull_lock[s] = 1 while a CTA holds scratch s); none when
+    // pull_start is null
+    const int32_t *pull_start = nullptr;
+    const int64_t *Lrp = nullptr;
+    const int32_t *Lcol = nullptr, *Lslot = nullptr;
+    double *pull_x = nullptr;
+    unsigned long long *pull_tag = nullptr, *pull_ctr = nullptr;
+    int32_t *pull_lock = nullptr;
+    int32_t pull_slots = 0, n = 0;
 };
 using RefactorArgs = RefactorArgsT<double>;
 
@@ -290,7 +313,7 @@ int launch_begin_batch(DevCtl *ctl, int nsets, int32_t *ticket, void *stream);
 int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, bool pipeline,
                           int grid, int epoch, int32_t *ticket, void *stream, int group);
 int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
-                          int npairs, int grid, int epoch, int32_t *ticket, void *stream);
+                          int npairs, int grid, int epoch, int32_t *ticket, void *stream, bool pull);
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream);
 int launch_tail_init(int32_t n, const int32_t *restart_mask, const int32_t *piv_old,
                      int32_t *pinv, int32_t *piv, int32_t *done, int epoch, void *stream);

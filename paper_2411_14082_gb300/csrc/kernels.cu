@@ -475,19 +475,6 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(TailArgs a, int epoc
 // and no fence per dependency; a lane consumes each dependency as soon as it
 // lands.  Backward rows walk their entries from the highest column down,
 // the order in which those values are produced.
-constexpr unsigned long long kSentinel = 0xFFF4B1A5C0DEF00DULL;
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed_f64(double *p, double v)
-{
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
-}
 
 __global__ void begin_solve_kernel(DevCtl *ctl, double *y, double *z, double *el, double *eu, int n)
 {

@@ -27,8 +27,10 @@
 // bounded by spin_limit iterations.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "gblu_internal.h"
@@ -316,7 +318,13 @@ struct RunDesc {
     long long base[kMaxRun];   // value of R entry r for dependency d: LUx[base[d] + r]
     long long lbl;             // start of R's rows in LUi
     int t, w, jl, nR, done;
+    int small;                 // nR <= kSmallRun: the leader alone applies every row
 };
+
+// a run whose rectangle has at most this many rows is applied by the leader
+// warp alone (a row per lane), without waking the workers: a chain of such
+// runs then costs one group barrier instead of one per run
+constexpr int kSmallRun = 32;
 
 // shared state of one group (declared once per CTA, for up to two groups)
 template <typename R>
@@ -325,9 +333,175 @@ struct GroupShared {
     R red[kWarps];
     R tri[kTri];               // the leader's staged triangle, column d at tri_off(d)
     int stop;
+    int pull_slot;                 // the scratch of the wide column in progress
+    unsigned long long pull_tag;   // and its tag there
 };
 
-template <typename R, bool kWait, bool kDense, int NW>
+// Wide columns (Schedule::pull_start): many dependencies in short supernode
+// runs and a short L part, like the rails of a bordered matrix, on which
+// every grid column depends.  The dependency loop would apply thousands of
+// runs of a few columns one after another, each costing a barrier and a
+// round trip through L2.  Instead the first p0 dependencies, j = rows[0..p0),
+// are applied row by row through the rows of L (CSR Lrp, Lcol, Lslot), by
+// the whole CTA:
+//   - the prefix rows r (U entries above rows[p0]) form a sparse unit lower
+//     triangular system: x(r) = A(r,k) - sum L(r,j) x(j) over row r of L in
+//     ascending j, taking only j of the prefix.  One thread per row, each
+//     thread's rows in ascending order, each term waiting for x(j) to be
+//     published in a dense per-CTA scratch (a sentinel until then; a per-CTA
+//     tag marks the prefix's entries).  The fused multiply-adds come in the
+//     order of the dependency loop, so these entries are the same bits.
+//   - every later row (the other U rows, the diagonal, the L rows) subtracts
+//     the sum over the prefix of its row of L: one warp per row, lanes over
+//     the entries, then a tree (these additions come in another order).
+// The dependency loop then goes on from dependency p0.  The scratch is one of
+// pull_slots, held while the prefix is computed (a CTA takes a free one;
+// there are as many as CTAs fit on the device).  Returns false if a wait
+// gave up (the column stops).
+// the fields pull_rows reads (the instantiations without wide columns do
+// not compile it in)
+struct PullArgs {
+    const int64_t *Lrp;
+    const int32_t *Lcol, *Lslot;
+    const double *LUx;
+    const int32_t *finish;
+    double *pull_x;
+    unsigned long long *pull_tag, *pull_ctr;
+    int32_t *pull_lock;
+    DevCtl *ctl;
+    long long spin_limit;
+    int32_t pull_slots, n;
+};
+
+__device__ __forceinline__ PullArgs pull_args(const RefactorArgsT<double> &a)
+{
+    return PullArgs{a.Lrp,    a.Lcol,     a.Lslot,    a.LUx, a.finish,     a.pull_x,     a.pull_tag,
+                    a.pull_ctr, a.pull_lock, a.ctl, a.spin_limit, a.pull_slots, a.n};
+}
+
+template <bool kWait>
+__device__ __forceinline__ bool pull_rows(const PullArgs a, int k, double *x, const int32_t *rows, int len, int p0,
+                                       int epoch, int tid, GroupShared<double> &sh)
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    bool fail = false;
+    if (tid == 0) {
+        int slot = -1;
+        for (long long it = 0; slot < 0; ++it) {
+            const int c = (int)((blockIdx.x + it) % a.pull_slots);
+            if (atomicCAS(a.pull_lock + c, 0, 1) == 0) {
+                slot = c;
+            } else if (it > a.spin_limit) {
+                set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+                a.ctl->where = 11;
+                a.ctl->where_k = k;
+                break;
+            }
+        }
+        sh.pull_slot = slot;
+        if (slot >= 0) sh.pull_tag = ++a.pull_ctr[slot];
+    }
+    __syncthreads();
+    const int slot = sh.pull_slot;
+    if (slot < 0) return false;
+    double *xd = a.pull_x + (size_t)slot * a.n;
+    unsigned long long *xt = a.pull_tag + (size_t)slot * a.n;
+    const unsigned long long tag = sh.pull_tag;
+    auto release = [&]() {
+        __syncthreads();
+        if (tid == 0) atomicExch(a.pull_lock + slot, 0);
+    };
+    auto give_up = [&](long long it, int site) -> bool {
+        if ((it & 31) == 0 && (ld_volatile(&a.ctl->interrupted) || ld_volatile(&a.ctl->status))) return true;
+        if (it > a.spin_limit) {
+            set_status(a.ctl, GBLU_ERR_DEVICE_TIMEOUT);
+            a.ctl->where = site;
+            a.ctl->where_k = k;
+            return true;
+        }
+        if (it > 64) __nanosleep(64);
+        return false;
+    };
+    // the prefix's dependencies are final
+    if (kWait)
+        for (int s = tid; s < p0 && !fail; s += kThreads) {
+            const int j = rows[s];
+            for (long long it = 1; ld_acquire(a.finish + j) != epoch; ++it)
+                if (give_up(it, 9)) {
+                    fail = true;
+                    break;
+                }
+        }
+    if (__syncthreads_or(fail)) {
+        release();
+        return false;
+    }
+    const double sent = __longlong_as_double((long long)kSentinel);
+    for (int s = tid; s < p0; s += kThreads) {
+        st_relaxed_f64(xd + rows[s], sent);
+        st_relaxed_u64(xt + rows[s], tag);
+    }
+    __syncthreads();
+    for (int s = tid; s < p0 && !fail; s += kThreads) {
+        const int r = rows[s];
+        double acc = x[s];
+        const int64_t e1 = __ldg(a.Lrp + r + 1);
+        for (int64_t e = __ldg(a.Lrp + r); e < e1; e++) {
+            const int j = __ldg(a.Lcol + e);
+            if (ld_relaxed_u64(xt + j) != tag) continue;
+            const double l = __ldcg(a.LUx + __ldg(a.Lslot + e));
+            unsigned long long b = ld_relaxed_u64(xd + j);
+            for (long long it = 1; b == kSentinel; ++it) {
+                if (give_up(it, 10)) {
+                    fail = true;
+                    break;
+                }
+                b = ld_relaxed_u64(xd + j);
+            }
+            if (fail) break;
+            acc = fma(-__longlong_as_double((long long)b), l, acc);
+        }
+        x[s] = acc;
+        st_relaxed_f64(xd + r, acc);
+    }
+    if (__syncthreads_or(fail)) {
+        release();
+        return false;
+    }
+    const int jlim = rows[p0 - 1];   // the last dependency of the prefix
+    for (int s = p0 + warp; s < len; s += kWarps) {
+        const int r = rows[s];
+        const int64_t e1 = __ldg(a.Lrp + r + 1);
+        double part = 0.0;
+        for (int64_t e0 = __ldg(a.Lrp + r) + lane; e0 < e1; e0 += 32 * 4) {
+            int j[4];
+            double l[4], v[4];
+            unsigned long long tg[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t e = e0 + 32 * u;
+                j[u] = e < e1 ? __ldg(a.Lcol + e) : INT_MAX;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const bool in = j[u] <= jlim;   // ascending: the rest is past the prefix
+                tg[u] = in ? ld_relaxed_u64(xt + j[u]) : 0ull;
+                l[u] = in ? __ldcg(a.LUx + __ldg(a.Lslot + e0 + 32 * u)) : 0.0;
+                v[u] = in ? __longlong_as_double((long long)ld_relaxed_u64(xd + j[u])) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (j[u] <= jlim && tg[u] == tag) part = fma(v[u], l[u], part);
+            if (j[3] > jlim) break;
+        }
+        part = warp_sum(part);
+        if (lane == 0) x[s] -= part;
+    }
+    release();
+    return true;
+}
+
+template <typename R, bool kWait, bool kDense, int NW, bool kPull>
 __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, int epoch, int g, int cap,
                         GroupShared<R> &sh)
 {
@@ -343,11 +517,15 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
     const bool dcol = kDense && k >= a.dense_p;
     const int nD = dcol ? __ldg(a.dense_s0 + (k - a.dense_p)) : nU - 1;
     // up to cap entries: work vector and rows in shared memory; up to as many
-    // rows as the work-vector area holds (2*cap in double precision): the
-    // rows alone (slot searches stay in shared memory), the work vector in
-    // place in global memory; longer: both in global memory
+    // rows as the shared area holds (in double precision 3*cap for a whole
+    // CTA, whose row area follows its work-vector area, and 2*cap for half a
+    // CTA): the rows alone (slot searches stay in shared memory), the work
+    // vector in place in global memory; longer: both in global memory
     const bool in_smem = len <= cap;
-    const bool rows_smem = !in_smem && len <= cap * (int)(sizeof(R) / sizeof(int32_t));
+    const bool joined = reinterpret_cast<const unsigned char *>(rs) == reinterpret_cast<const unsigned char *>(xs + cap);
+    const int row_cap = joined ? cap * (int)((sizeof(R) + sizeof(int32_t)) / sizeof(int32_t))
+                               : cap * (int)(sizeof(R) / sizeof(int32_t));
+    const bool rows_smem = !in_smem && len <= row_cap;
     int32_t *rsw = reinterpret_cast<int32_t *>(xs);   // rows over the work-vector area
     R *x = in_smem ? xs : a.LUx + beg;
     const int32_t *rows = in_smem ? rs : (rows_smem ? rsw : a.LUi + beg);
@@ -368,6 +546,12 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
         for (int e = ab + tid; e < ae; e += kT) x[__ldg(a.amap + e)] = (R)__ldg(a.Ax + e);
     }
     group_sync<NW>(g);
+    // a wide column: its first p0 dependencies row by row (pull_rows)
+    int p0 = 0;
+    if constexpr (kPull && NW == kWarps && std::is_same<R, double>::value) {
+        if (a.pull_start && !dcol) p0 = min(__ldg(a.pull_start + k), nD);
+        if (p0 > 0 && !pull_rows<kWait>(pull_args(a), k, x, rows, len, p0, epoch, tid, sh)) return true;
+    }
 
     // ---- leader state: the staged window of dependencies [mbase, mbase+32),
     // lane q holding dependency mbase+q; [mbase, ready) are ready
@@ -461,15 +645,16 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
             r.jl = rows[t + w - 1];
             r.lbl = lbl;
             r.nR = nRl;
+            r.small = nRl <= kSmallRun;
             r.done = 0;
         }
         return true;
     };
 
     if (warp == 0) {
-        if (nD == 0) {
+        if (p0 >= nD) {
             if (lane == 0) sh.run[0].done = 1;
-        } else if (!lead_next(0, 0) && lane == 0) {
+        } else if (!lead_next(p0, 0) && lane == 0) {
             sh.stop = 1;
         }
     }
@@ -483,38 +668,61 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
         if (sh.stop) return true;
         const RunDesc &r = sh.run[i & 1];
         if (r.done) break;
-        const int t = r.t, w = r.w, nR = r.nR, jl = r.jl;
+        const int t = r.t, w = r.w, nR = r.nR, jl = r.jl, small = r.small;
         const long long lbl = r.lbl;
         const int tl = t + w - 1, hend = t + w + kMaxRun;   // the leader's slots: [t+w, hend)
         bool bad = false;
         if (warp == 0) {
-            if (lane < nR) {   // only the first 32 entries of R can fall in the leader's slots
-                const int row = __ldg(a.LUi + lbl + lane);
-                const int sl = find_slot(rows, tl + 1 + lane, tl + (row - jl), len, row);
-                if (sl < 0) {
-                    bad = true;
-                } else if (sl < hend) {
-                    R v = x[sl];
-                    for (int d0 = 0; d0 < w; d0 += 8) {   // eight loads in flight
-                        R lv[8];
+            // a large run: the rows of R in the leader's slots (only the first
+            // 32 entries of R can fall there); a small run: every row of R, and
+            // so on through the small runs that follow, while the workers wait
+            // at the barrier; the run that ends the chain (or the first run
+            // after a large one) is published
+            const RunDesc *cur = &r;
+            const bool all = small != 0;
+            const int p = (i + 1) & 1;
+            for (;;) {
+                const int ct = cur->t, cw = cur->w, cnR = cur->nR, cjl = cur->jl;
+                const long long clbl = cur->lbl;
+                const int ctl = ct + cw - 1, chend = all ? INT_MAX : ct + cw + kMaxRun;
+                const int nrow = all ? cnR : min(cnR, 32);
+                for (int rr = lane; rr < nrow; rr += 32) {
+                    const int row = __ldg(a.LUi + clbl + rr);
+                    const int sl = find_slot(rows, ctl + 1 + rr, ctl + (row - cjl), len, row);
+                    if (sl < 0) {
+                        bad = true;
+                    } else if (sl < chend) {
+                        R v = x[sl];
+                        for (int d0 = 0; d0 < cw; d0 += 8) {   // eight loads in flight
+                            R lv[8];
 #pragma unroll
-                        for (int u = 0; u < 8; u++)
-                            lv[u] = d0 + u < w ? __ldcg(a.LUx + r.base[d0 + u] + lane) : R(0);
+                            for (int u = 0; u < 8; u++)
+                                lv[u] = d0 + u < cw ? __ldcg(a.LUx + cur->base[d0 + u] + rr) : R(0);
 #pragma unroll
-                        for (int u = 0; u < 8; u++)
-                            if (d0 + u < w) v = fma(-x[t + d0 + u], lv[u], v);
+                            for (int u = 0; u < 8; u++)
+                                if (d0 + u < cw) v = fma(-x[ct + d0 + u], lv[u], v);
+                        }
+                        x[sl] = v;
                     }
-                    x[sl] = v;
                 }
+                __syncwarp();
+                const int tn = ct + cw;
+                if (__any_sync(kFull, bad)) break;
+                if (tn >= nD) {
+                    if (lane == 0) sh.run[p].done = 1;
+                    break;
+                }
+                if (!lead_next(tn, p)) {
+                    if (lane == 0) sh.stop = 1;
+                    break;
+                }
+                __syncwarp();
+                // after a large run the workers may still be updating rows of
+                // the next one: a small run that follows waits for the barrier
+                if (!all || !sh.run[p].small) break;
+                cur = &sh.run[p];   // only the leader reads this buffer before the barrier
             }
-            __syncwarp();
-            const int tn = t + w;
-            if (tn >= nD) {
-                if (lane == 0) sh.run[(i + 1) & 1].done = 1;
-            } else if (!lead_next(tn, (i + 1) & 1) && lane == 0) {
-                sh.stop = 1;
-            }
-        } else {
+        } else if (!small) {
             const int wt = tid - 32;
             for (int r0 = 0; r0 < nR; r0 += kRows * kTw) {
                 int sl[kRows], key[kRows], lo[kRows], hi[kRows];
@@ -598,7 +806,7 @@ __global__ void begin_refactor_kernel(DevCtl *ctl)
 
 // One task of the schedule: one long column (whole CTA), two medium
 // columns (a half each) or up to 8 short ones (a warp each); true = stop.
-template <typename R, bool kWait, bool kDense>
+template <typename R, bool kWait, bool kDense, bool kPull>
 __device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *xs, int32_t *rs, int epoch,
                                          GroupShared<R> *s_grp)
 {
@@ -607,11 +815,11 @@ __device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *x
     const int k0 = __ldg(a.task_cols + c0);
     const int64_t len0 = __ldg(a.LUp + k0 + 1) - __ldg(a.LUp + k0);
     if (c1 - c0 == 1 && len0 > a.cap_short)            // one long column: whole CTA
-        return col_grp<R, kWait, kDense, kWarps>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
+        return col_grp<R, kWait, kDense, kWarps, kPull>(a, k0, xs, rs, epoch, 0, a.cap_long, s_grp[0]);
     if (c1 - c0 == 2 && len0 > a.cap_short) {          // two medium columns: a half each
         const int g = warp / (kWarps / 2);
         const int half = a.cap_long / 2;
-        const bool hs = col_grp<R, kWait, kDense, kWarps / 2>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
+        const bool hs = col_grp<R, kWait, kDense, kWarps / 2, false>(a, __ldg(a.task_cols + c0 + g), xs + (size_t)g * half,
                                                           rs + (size_t)g * half, epoch, g, half, s_grp[g]);
         return __syncthreads_or(hs);
     }
@@ -624,7 +832,7 @@ __device__ __forceinline__ bool run_task(const RefactorArgsT<R> &a, int tt, R *x
 
 // Tasks [task_begin, task_begin + ntasks): one per CTA in cluster mode
 // (persistent == 0), taken by ticket in pipeline mode (persistent == 1).
-template <typename R, bool kWait, bool kDense>
+template <typename R, bool kWait, bool kDense, bool kPull>
 __global__ void __launch_bounds__(kThreads, 3) refactor_task_kernel(RefactorArgsT<R> a, int epoch, int persistent)
 {
     // a replayed graph passes -1: the epoch was written to the control block
@@ -643,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 3) refactor_task_kernel(RefactorArgs
         const int t = s_t, quit = s_quit;
         __syncthreads();
         if (t >= a.ntasks || quit) break;
-        if (run_task<R, kWait, kDense>(a, a.task_begin + t, xs, rs, epoch, s_grp)) break;
+        if (run_task<R, kWait, kDense, kPull>(a, a.task_begin + t, xs, rs, epoch, s_grp)) break;
     }
 }
 
@@ -684,7 +892,7 @@ __device__ __forceinline__ int group_task(long long t, int ntasks, int nsets, in
     return task;
 }
 
-template <bool kWait>
+template <bool kWait, bool kPull>
 __global__ void __launch_bounds__(kThreads, 3)
 refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int ntasks, int epoch, int persistent,
                       int32_t *ticket, const SetTask *order, int group)
@@ -718,7 +926,7 @@ refactor_batch_kernel(const RefactorArgs *sets, int nsets, int task_begin, int n
         // a local copy: stores through the work vector cannot alias it, so its
         // fields stay in registers instead of being reloaded from memory
         const RefactorArgs as = sets[si];
-        run_task<double, kWait, false>(as, task, xs, rs, epoch, s_grp);
+        run_task<double, kWait, false, kPull>(as, task, xs, rs, epoch, s_grp);
     }
 }
 
@@ -764,34 +972,44 @@ int launch_begin_refactor(DevCtl *ctl, void *stream)
     return (int)cudaGetLastError();
 }
 
+// the shared-memory allowance of every instantiation of a kernel template
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t sm, cudaError_t e)
+{
+    return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) : e;
+}
+
 int refactor_setup(int cap_long, int *blocks_per_sm, int *batch_blocks_per_sm)
 {
     const size_t sm = (size_t)cap_long * (sizeof(double) + sizeof(int32_t));
-    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<double, true, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<double, false, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<double, true, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<double, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaSuccess;
+    e = allow_smem(refactor_task_kernel<double, true, false, false>, sm, e);
+    e = allow_smem(refactor_task_kernel<double, false, false, false>, sm, e);
+    e = allow_smem(refactor_task_kernel<double, true, true, false>, sm, e);
+    e = allow_smem(refactor_task_kernel<double, false, true, false>, sm, e);
+    e = allow_smem(refactor_task_kernel<double, true, false, true>, sm, e);
+    e = allow_smem(refactor_task_kernel<double, false, false, true>, sm, e);
+    e = allow_smem(refactor_batch_kernel<true, false>, sm, e);
+    e = allow_smem(refactor_batch_kernel<false, false>, sm, e);
+    e = allow_smem(refactor_batch_kernel<true, true>, sm, e);
+    e = allow_smem(refactor_batch_kernel<false, true>, sm, e);
     if (e != cudaSuccess) return (int)e;
-    int b1 = 0, b2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, refactor_task_kernel<double, true, false>, kThreads, sm);
+    // persistent grids are sized for the instantiation that fits fewest
+    int b[3] = {0, 0, 0};
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], refactor_task_kernel<double, true, false, false>, kThreads, sm);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, refactor_task_kernel<double, true, true>, kThreads, sm);
-    *blocks_per_sm = b1 < b2 ? b1 : b2;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], refactor_task_kernel<double, true, true, false>, kThreads, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], refactor_task_kernel<double, true, false, true>, kThreads, sm);
+    *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
     // the batch kernel keeps a copy of its set's argument block (it spills a
     // few registers at three CTAs per SM, which measured faster than two)
+    int c[2] = {0, 0};
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch_blocks_per_sm, refactor_batch_kernel<true>, kThreads, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c[0], refactor_batch_kernel<true, false>, kThreads, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c[1], refactor_batch_kernel<true, true>, kThreads, sm);
+    *batch_blocks_per_sm = std::min(c[0], c[1]);
     return (int)e;
 }
 
@@ -809,27 +1027,39 @@ int launch_refactor_batch(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
     cudaStream_t st = (cudaStream_t)stream;
     if (group < 1 || group > nsets) group = nsets;
     if (pipeline) {
-        refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, a0.task_begin,
-                                                                           a0.ntasks, epoch, 1, ticket, nullptr,
-                                                                           group);
+        if (a0.pull_start)
+            refactor_batch_kernel<true, true><<<grid, kThreads, task_smem(a0), st>>>(
+                sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 1, ticket, nullptr, group);
+        else
+            refactor_batch_kernel<true, false><<<grid, kThreads, task_smem(a0), st>>>(
+                sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 1, ticket, nullptr, group);
     } else {
         // a level launch has no waits: one group holding every set
         const long long blocks = (long long)a0.ntasks * nsets;
         if (blocks > INT_MAX) return (int)cudaErrorInvalidValue;
-        refactor_batch_kernel<false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
-            sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets);
+        if (a0.pull_start)
+            refactor_batch_kernel<false, true><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
+                sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets);
+        else
+            refactor_batch_kernel<false, false><<<(unsigned)blocks, kThreads, task_smem(a0), st>>>(
+                sets_dev, nsets, a0.task_begin, a0.ntasks, epoch, 0, ticket, nullptr, nsets);
     }
     return (int)cudaGetLastError();
 }
 
 int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, int nsets, const SetTask *order_dev,
-                          int npairs, int grid, int epoch, int32_t *ticket, void *stream)
+                          int npairs, int grid, int epoch, int32_t *ticket, void *stream, bool pull)
 {
     if (npairs <= 0 || nsets <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
     int g = (nsets + 255) / 256;
     begin_multi_kernel<<<g, 256, 0, st>>>(sets_dev, nsets, ticket);
-    refactor_batch_kernel<true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
+    // pull: some set has wide columns (each set's argument block says which)
+    if (pull)
+        refactor_batch_kernel<true, true><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
+                                                                       order_dev, 1);
+    else
+        refactor_batch_kernel<true, false><<<grid, kThreads, task_smem(a0), st>>>(sets_dev, nsets, 0, npairs, epoch, 1, ticket,
                                                                        order_dev, 1);
     return (int)cudaGetLastError();
 }
@@ -837,13 +1067,13 @@ int launch_refactor_multi(const RefactorArgs *sets_dev, const RefactorArgs &a0, 
 int refactor_setup_f32(int cap_long, int *blocks_per_sm)
 {
     const size_t sm = (size_t)cap_long * (sizeof(float) + sizeof(int32_t));
-    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<float, true, false>,
+    cudaError_t e = cudaFuncSetAttribute(refactor_task_kernel<float, true, false, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(refactor_task_kernel<float, false, false>,
+        e = cudaFuncSetAttribute(refactor_task_kernel<float, false, false, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, refactor_task_kernel<float, true, false>,
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, refactor_task_kernel<float, true, false, false>,
                                                               kThreads, sm);
 }
 
@@ -851,8 +1081,8 @@ int launch_refactor_tasks_f32(const RefactorArgsT<float> &a, bool pipeline, int 
 {
     if (a.ntasks <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    if (pipeline) refactor_task_kernel<float, true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
-    else refactor_task_kernel<float, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+    if (pipeline) refactor_task_kernel<float, true, false, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+    else refactor_task_kernel<float, false, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
     return (int)cudaGetLastError();
 }
 
@@ -862,11 +1092,14 @@ int launch_refactor_tasks(const RefactorArgs &a, bool pipeline, int grid, int ep
     cudaStream_t st = (cudaStream_t)stream;
     const bool dense = a.dense_p < INT_MAX;   // a dense tail is in use
     if (pipeline) {
-        if (dense) refactor_task_kernel<double, true, true><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
-        else refactor_task_kernel<double, true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        if (dense) refactor_task_kernel<double, true, true, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        else if (a.pull_start) refactor_task_kernel<double, true, false, true><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
+        else refactor_task_kernel<double, true, false, false><<<grid, kThreads, task_smem(a), st>>>(a, epoch, 1);
     } else {
-        if (dense) refactor_task_kernel<double, false, true><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
-        else refactor_task_kernel<double, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        if (dense) refactor_task_kernel<double, false, true, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        else if (a.pull_start)
+            refactor_task_kernel<double, false, false, true><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
+        else refactor_task_kernel<double, false, false, false><<<a.ntasks, kThreads, task_smem(a), st>>>(a, epoch, 0);
     }
     return (int)cudaGetLastError();
 }

@@ -292,6 +292,43 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             }
         }
     }
+    // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
+    W.chain.assign(n, 0);
+    parallel_ranges(n, S.LUp.data(), [&](int32_t j0, int32_t j1, int) {
+        for (int32_t j = j0; j < j1 && j + 1 < n; j++) {
+            const int64_t a = S.LUp[j] + S.nU[j], ae = S.LUp[j + 1];
+            const int64_t b = S.LUp[j + 1] + S.nU[j + 1], be = S.LUp[j + 2];
+            if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
+            W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
+        }
+    });
+    // ---- wide columns: at most kPullMaxL L entries and at least kPullMinRuns
+    // supernode runs among the dependencies.  All but the last chain of linked
+    // dependencies are taken row by row (pull_start = where that chain
+    // starts); none in the dense tail ----
+    W.pull_start.assign(n, 0);
+    {
+        std::atomic<int64_t> cnt{0};
+        parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
+            int64_t c = 0;
+            for (int32_t k = k0; k < k1 && k < W.dense_p; k++) {
+                const int64_t b = S.LUp[k];
+                const int32_t nd = S.nU[k] - 1, nl = (int32_t)(S.LUp[k + 1] - b) - S.nU[k];
+                if (nl > kPullMaxL || nd < kPullMinRuns) continue;
+                const int32_t *u = S.LUi.data() + b;
+                auto linked = [&](int32_t i) { return u[i] == u[i - 1] + 1 && W.chain[u[i - 1]] != 0; };
+                int32_t runs = 1;
+                for (int32_t i = 1; i < nd; i++) runs += !linked(i);
+                if (runs < kPullMinRuns) continue;
+                int32_t p = nd - 1;
+                while (p > 0 && linked(p)) p--;
+                W.pull_start[k] = p;
+                c += p > 0;
+            }
+            cnt += c;
+        });
+        W.pull_cols = cnt.load();
+    }
     const double thr = alpha * (double)resident_warps;
     // ---- EGraph levels, the dividing level (Section IV-B) and the tasks:
     // on a thread of their own, beside the slot maps and row-wise copies
@@ -335,7 +372,7 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
                 for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
                     const int32_t k = W.level_cols[p];
                     const int64_t len = S.LUp[k + 1] - S.LUp[k];
-                    if (len > half) {
+                    if (len > half || W.pull_start[k] > 0) {   // a whole CTA
                         close();
                         W.task_cols.push_back(k);
                         W.task_ptr.push_back((int32_t)W.task_cols.size());
@@ -399,14 +436,6 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
                 W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
     });
-    // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
-    W.chain.assign(n, 0);
-    for (int32_t j = 0; j + 1 < n; j++) {
-        const int64_t a = S.LUp[j] + S.nU[j], ae = S.LUp[j + 1];
-        const int64_t b = S.LUp[j + 1] + S.nU[j + 1], be = S.LUp[j + 2];
-        if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
-        W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
-    }
     // ---- row-wise copies for the solves: per-thread histograms of the row
     // entries over column ranges give each range its first position in
     // every row; each thread then copies its columns in ascending order, so

@@ -334,14 +334,16 @@ def test_every_column_task_kind(sched):
     ln = np.diff(lu.Lp) + np.diff(lu.Up)
     # one warp up to 640 entries; half a CTA up to 2,560; a whole CTA with
     # its work vector in shared memory up to 5,120, its rows alone there up
-    # to 10,240, and beyond that in global memory
+    # to 15,360, and beyond that in global memory
     kinds = [(ln <= 640).sum(), ((ln > 640) & (ln <= 2560)).sum(),
-             ((ln > 2560) & (ln <= 5120)).sum(), ((ln > 5120) & (ln <= 10240)).sum(),
-             (ln > 10240).sum()]
+             ((ln > 2560) & (ln <= 5120)).sum(), ((ln > 5120) & (ln <= 15360)).sum(),
+             (ln > 15360).sum()]
     assert min(kinds) >= 1 and kinds[3] >= 2, kinds
     s = gblu.Solver(DEV, sched_mode=sched, solve_mode=sched)
     s.analyze(n, Ap, Ai, Q)
     s.factorize(dev(Ax))
+    # the rails are wide columns: most of their dependencies go row by row
+    assert s.stats()["wide_cols"] >= 4
     compare_factors(s.export_factors(), lu, RTOL)
     for it in range(3):
         ckt = inputs.perturb_elements(ckt, rng, frac=0.2)
