@@ -30,6 +30,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving workloads run one stream per pattern: give the device as many
+# hardware work queues as it has (set before any CUDA context exists), so
+# that a short launch is not queued behind a long one of another stream
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_2411_14082_gb300 import inputs  # noqa: E402
 
@@ -546,7 +550,11 @@ def run_serve_poisson(args, rank, world, local_rank):
             if len(a):
                 by_size[cls] = {"requests": int(len(a)), "p50_ms": 1e3 * float(np.percentile(a, 50)),
                                 "p99_ms": 1e3 * float(np.percentile(a, 99))}
-        sweep.append({"offered_load": rho, "by_size": by_size, "arrival_rate_per_s": lam, "requests": N,
+        slowest = sorted(res, key=lambda t: -t[2]["latency_s"])[:5]
+        slow = [{"pattern": nm, "mode": "f64" if m == 0 else "f32_refined", "latency_ms": 1e3 * r["latency_s"],
+                 "queue_ms": 1e3 * r["queue_s"], "refine_iters": r["refine_iters"], "repivoted": r["repivoted"]}
+                for m, nm, r in slowest]
+        sweep.append({"offered_load": rho, "by_size": by_size, "slowest": slow, "arrival_rate_per_s": lam, "requests": N,
                       "served_per_s": N / elapsed, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                       "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "by_mode": by_mode,
                       "mean_batch": float(np.mean([r["batch_size"] for m, _, r in res if m == 0])),

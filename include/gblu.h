@@ -446,10 +446,13 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
  * request whose pivot check fails is redone with gblu_refactorize (restart
  * with pivoting, Section IV-C), and the pattern keeps the new pivot
  * sequence.  Each result is bit-for-bit the result of the same request run
- * alone on a handle in the same pivot state.  A pattern of 250,000 unknowns
- * or more gets max_sms = 3/4 of the SMs and a low-priority stream; the
- * others get high-priority streams, so that small requests start beside a
- * large one's persistent launches.
+ * alone on a handle in the same pivot state.  A pattern of more than
+ * 100,000 unknowns gets max_sms = 3/4 of the SMs and a low-priority stream;
+ * the others get high-priority streams, so that small requests start beside
+ * a large one's persistent launches.  Streams share the device's hardware
+ * work queues (8 by default): a process serving many patterns should set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 before it creates its CUDA context, or a
+ * short launch can wait in a queue behind a long one of another pattern.
  *
  * gblu_server_create: budget = device bytes the server may hold in total;
  *   max_batch = most requests per batch; o = options of the handles (NULL:

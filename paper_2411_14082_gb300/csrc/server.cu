@@ -43,9 +43,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// patterns of at least this many unknowns share the device with small ones
+// patterns of more than this many unknowns share the device with small ones
 // (max_sms = 3/4 of the SMs, low stream priority)
-constexpr int32_t kBigPattern = 250000;
+constexpr int32_t kSmallPatternMax = 100000;
 
 thread_local std::string s_err = "no error";
 
@@ -377,7 +377,7 @@ int gblu_server_add_pattern(gblu_server s, int32_t n, const int32_t *Ap, const i
     // and run on a low-priority stream, so that the CTAs of small requests
     // queued meanwhile start on free SMs instead of waiting for its launch
     // to end (kernels are not preempted)
-    const bool big = n >= kBigPattern;
+    const bool big = n > kSmallPatternMax;
     if (big) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
