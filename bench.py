@@ -88,10 +88,8 @@ def hbm_roofline(bytes_alg, seconds, traffic=None):
 # (dram__bytes_read.sum + dram__bytes_write.sum over its launches); valid only
 # for the kernel source it was taken on
 REFACTOR_TRAFFIC = {
-    "rc_mesh_200x200x4/library": {"refactor_cu_sha256": "653344a75926a1654876d75cfd42a67982710dbe225ee03a70e68fecc00e6df1",
-                                  "bytes": 17.954e9 + 811.2e6},
-    "rc_mesh_120x120x4/library": {"refactor_cu_sha256": "653344a75926a1654876d75cfd42a67982710dbe225ee03a70e68fecc00e6df1",
-                                  "bytes": 4.98e6 + 86.82e6 + 57.50e6},
+    "rc_mesh_200x200x4/library": {"refactor_cu_sha256": "b1d7df7c211691040ccf7bec8733c132b7df22f76fec3cbd2181a7ab0a602e56",
+                                  "bytes": 19.269e9 + 988.6e6},
 }
 
 
