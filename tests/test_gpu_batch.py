@@ -38,9 +38,17 @@ def singles(n, Ap, Ai, Q, Ax0, sets, rhs):
     return xs, reps
 
 
-@pytest.mark.parametrize("case", ["small_mna", "mesh"])
+def batch_case(case):
+    if case == "small_mna":
+        return inputs.workload_small()
+    if case == "rails":   # six rails, each a wide column (its dependencies applied row by row)
+        return inputs.bordered_grid(60, 60, n_rails=6, density=0.2)
+    return inputs.rc_mesh3d(40, 40, 4, seed=5, n_fet=100)
+
+
+@pytest.mark.parametrize("case", ["small_mna", "mesh", "rails"])
 def test_batch_equals_single_path_bitwise(case):
-    ckt = inputs.workload_small() if case == "small_mna" else inputs.rc_mesh3d(40, 40, 4, seed=5, n_fet=100)
+    ckt = batch_case(case)
     n, Ap, Ai, Ax0 = ckt.csc()
     Q = inputs.grid_nd_order(ckt)
     nsets = 6
@@ -51,6 +59,8 @@ def test_batch_equals_single_path_bitwise(case):
     sb = gblu.Solver(DEV)
     sb.analyze(n, Ap, Ai, Q)
     sb.factorize(dev(Ax0))
+    if case == "rails":
+        assert sb.stats()["wide_cols"] == 6
     LUx, failed = sb.refactorize_batch(dev(np.stack(sets)))
     assert np.array_equal(failed.astype(bool), np.array(reps))
     x = sb.solve_batch(LUx, dev(np.stack(rhs))).cpu().numpy()
@@ -92,6 +102,8 @@ def test_batch_reports_the_failing_set_alone():
     sb = gblu.Solver(DEV)
     sb.analyze(n, Ap, Ai, Q)
     sb.factorize(dev(Ax0))
+    if case == "rails":
+        assert sb.stats()["wide_cols"] == 6
     LUx, failed = sb.refactorize_batch(dev(np.stack(sets)))
     assert failed[bad] == 1 and failed.sum() == 1 + sum(reps[i] for i in range(nsets) if i != bad)
     x = sb.solve_batch(LUx, dev(np.stack(rhs))).cpu().numpy()
@@ -126,6 +138,10 @@ def multi_cases():
         n, Ap, Ai, Ax0 = ckt.csc()
         out.append((ckt, n, Ap, Ai, Ax0, inputs.grid_nd_order(ckt)))
     ckt = inputs.rc_mesh3d(14, 14, 3, seed=6, n_fet=30)
+    n, Ap, Ai, Ax0 = ckt.csc()
+    out.append((ckt, n, Ap, Ai, Ax0, inputs.grid_nd_order(ckt)))
+    # and one with wide columns (four rails), beside patterns without any
+    ckt = inputs.bordered_grid(50, 50, n_rails=4, density=0.3)
     n, Ap, Ai, Ax0 = ckt.csc()
     out.append((ckt, n, Ap, Ai, Ax0, inputs.grid_nd_order(ckt)))
     return out
