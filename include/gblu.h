@@ -449,7 +449,10 @@ int gblu_solve_factors_noalloc(int32_t n, const int64_t *Lrp, const int32_t *Lco
  * alone on a handle in the same pivot state.  A pattern of more than
  * 100,000 unknowns gets max_sms = 3/4 of the SMs and a low-priority stream;
  * the others get high-priority streams, so that small requests start beside
- * a large one's persistent launches.  Streams share the device's hardware
+ * a large one's persistent launches.  Request values, right-hand sides and
+ * solutions pass through pinned host buffers of the server (a copy to or
+ * from pageable memory would queue behind other streams' copies in the
+ * driver's shared staging).  Streams share the device's hardware
  * work queues (8 by default): a process serving many patterns should set
  * CUDA_DEVICE_MAX_CONNECTIONS=32 before it creates its CUDA context, or a
  * short launch can wait in a queue behind a long one of another pattern.

@@ -29,6 +29,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -82,6 +83,12 @@ struct Pattern {
     cudaStream_t st = nullptr;
     double *Ax_d = nullptr, *LU_d = nullptr, *b_d = nullptr, *x_d = nullptr, *res_d = nullptr;
     double *res_h = nullptr;   // pinned, 4 per slot
+    // pinned staging of every slot's values, right-hand side and solution:
+    // a copy between the device and pageable host memory goes through the
+    // driver's own staging, shared by every stream, and waits behind the
+    // copies of other streams (one of them behind a pattern's seconds-long
+    // launches); requests are copied into and out of these on the host
+    double *in_h = nullptr, *out_h = nullptr;
     std::vector<int32_t> failed;
     std::deque<Request *> queue;
     std::condition_variable cv;
@@ -117,6 +124,8 @@ void free_pattern(Pattern *p)
     cudaFree(p->x_d);
     cudaFree(p->res_d);
     if (p->res_h) cudaFreeHost(p->res_h);
+    if (p->in_h) cudaFreeHost(p->in_h);
+    if (p->out_h) cudaFreeHost(p->out_h);
     if (p->st) cudaStreamDestroy(p->st);
     p->Ax_d = p->LU_d = p->b_d = p->x_d = p->res_d = p->res_h = nullptr;
     p->st = nullptr;
@@ -135,11 +144,38 @@ int alloc_buffers(Pattern *p)
         cudaMalloc(&p->b_d, S * p->n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->x_d, S * p->n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->res_d, S * 4 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&p->res_h, S * 4 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&p->res_h, S * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&p->in_h, S * (p->nnz_a + p->n) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&p->out_h, S * p->n * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return sfail(GBLU_ERR_NOMEM, "server: batch buffers for %d sets do not fit on the device", p->slots);
     }
     p->failed.assign(S, 0);
+    return GBLU_OK;
+}
+
+// slot i's inputs through the pinned staging (host copies, then one
+// asynchronous copy each) and its solution back the same way
+int stage_in(Pattern *p, const Request *r, int i, cudaStream_t st)
+{
+    const int64_t n = p->n, na = p->nnz_a;
+    double *hx = p->in_h + (size_t)i * (na + n);
+    std::memcpy(hx, r->Ax, na * sizeof(double));
+    std::memcpy(hx + na, r->b, n * sizeof(double));
+    if (cudaMemcpyAsync(p->Ax_d + (size_t)i * na, hx, na * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(p->b_d + (size_t)i * n, hx + na, n * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return sfail(GBLU_ERR_CUDA, "server: copy of request inputs failed");
+    return GBLU_OK;
+}
+
+int stage_out(Pattern *p, int i, cudaStream_t st)
+{
+    const int64_t n = p->n;
+    if (cudaMemcpyAsync(p->out_h + (size_t)i * n, p->x_d + (size_t)i * n, n * sizeof(double),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return sfail(GBLU_ERR_CUDA, "server: copy of the solution failed");
     return GBLU_OK;
 }
 
@@ -151,18 +187,15 @@ void run_refined(gblu_server_s *s, Pattern *p, Request *r)
     const Clock::time_point t0 = Clock::now();
     cudaStream_t st = p->st;
     const int64_t n = p->n, na = p->nnz_a;
-    int rc = GBLU_OK;
-    if (cudaMemcpyAsync(p->Ax_d, r->Ax, na * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(p->b_d, r->b, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        rc = sfail(GBLU_ERR_CUDA, "server: copy of request inputs failed");
+    int rc = stage_in(p, r, 0, st);
     int32_t it = 0;
     double berr = -1.0;
     if (rc == GBLU_OK) rc = gblu_refactorize_f32(p->h, p->Ax_d, st, nullptr);
     if (rc == GBLU_OK) rc = gblu_solve_refined(p->h, p->Ax_d, p->b_d, p->x_d, 1e-12, 10, st, &it, &berr);
-    if (rc == GBLU_OK &&
-        (cudaMemcpyAsync(r->x, p->x_d, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-         cudaStreamSynchronize(st) != cudaSuccess))
+    if (rc == GBLU_OK) rc = stage_out(p, 0, st);
+    if (rc == GBLU_OK && cudaStreamSynchronize(st) != cudaSuccess)
         rc = sfail(GBLU_ERR_CUDA, "server: copy of the solution failed");
+    if (rc == GBLU_OK) std::memcpy(r->x, p->out_h, n * sizeof(double));
     const Clock::time_point t1 = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     r->t_start = t0;
@@ -191,11 +224,7 @@ void run_batch(gblu_server_s *s, Pattern *p, std::vector<Request *> &batch)
     int rc = GBLU_OK;
     for (int i = 0; i < k && rc == GBLU_OK; i++) {
         batch[i]->t_start = t0;
-        if (cudaMemcpyAsync(p->Ax_d + i * na, batch[i]->Ax, na * sizeof(double), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(p->b_d + i * n, batch[i]->b, n * sizeof(double), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess)
-            rc = sfail(GBLU_ERR_CUDA, "server: copy of request inputs failed");
+        rc = stage_in(p, batch[i], i, st);
     }
     int32_t nf = 0;
     if (rc == GBLU_OK)
@@ -222,16 +251,16 @@ void run_batch(gblu_server_s *s, Pattern *p, std::vector<Request *> &batch)
         for (int i = 0; i < k; i++) {
             if (status[i] < 0) continue;
             const int r = gblu_residual(p->h, p->Ax_d + i * na, p->b_d + i * n, p->x_d + i * n, p->res_d + 4 * i, st);
-            if (r != GBLU_OK) status[i] = r;
-            else if (cudaMemcpyAsync(batch[i]->x, p->x_d + i * n, n * sizeof(double), cudaMemcpyDeviceToHost, st) !=
-                     cudaSuccess)
-                status[i] = sfail(GBLU_ERR_CUDA, "server: copy of the solution failed");
+            const int c = r != GBLU_OK ? r : stage_out(p, i, st);
+            if (c != GBLU_OK) status[i] = c;   // keep GBLU_REPIVOTED
         }
         if (cudaMemcpyAsync(p->res_h, p->res_d, 4 * k * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             const int e = sfail(GBLU_ERR_CUDA, "server: stream failed");
             for (int i = 0; i < k; i++) status[i] = e;
         }
+        for (int i = 0; i < k; i++)
+            if (status[i] >= 0) std::memcpy(batch[i]->x, p->out_h + (size_t)i * n, n * sizeof(double));
     } else {
         cudaStreamSynchronize(st);
     }
