@@ -1115,7 +1115,8 @@ def run_ours(args, rank, world, local_rank):
             repiv += int(rep)
             ts = s.stats()
             tail_ms.append([ts["tail_kernel_ms"], ts["tail_repack_ms"], ts["tail_schedule_ms"],
-                            ts["tail_upload_ms"], ts["n_restart_cols"], forced[i], ts["tail_passes"], int(rep)])
+                            ts["tail_upload_ms"], ts["n_restart_cols"], forced[i], ts["tail_passes"], int(rep),
+                            ts["repredictions"]])
             ev_s[i][0].record(stream)
             s.solve(rhs[i], xs[i])
             ev_s[i][1].record(stream)
@@ -1339,7 +1340,8 @@ def run_ours(args, rank, world, local_rank):
         line["config"]["repivot_mode"] = args.repivot_mode
         line["repivot"] = {"runs": len(forced), "mean_refactor_ms_all": 1e3 * float(np.mean(t_ref)),
                            "restarts": int(tm[:, 7].sum()),
-                           "restarts_kept_every_pivot": int(((tm[:, 6] == 0) & (tm[:, 7] == 1)).sum()),
+                           "restarts_kept_every_pivot": int(((tm[:, 6] == 0) & (tm[:, 8] == 0) & (tm[:, 7] == 1)).sum()),
+                           "repredictions": [int(v) for v in tm[:, 8]],
                            "restart_refactor_ms": [1e3 * t for j, t in enumerate(t_ref) if j + args.warmup in forced],
                            "mean_refactor_ms_plain": 1e3 * float(np.mean(plain)) if plain else None,
                            "slowdown": float(np.mean(t_ref) / np.mean(plain)) if plain else None,

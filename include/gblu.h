@@ -104,8 +104,12 @@ typedef struct {
        2 = the prediction that every step keeps its diagonal row becomes a
        structure (gblu_symmetric_structure) that is installed, and the
        checked re-factorization kernel computes every column on it; when a
-       check fails, the unfinished steps and their column-elimination-tree
-       ancestors continue as in 1.  Taken when every column of A has a
+       check fails, the threshold rule's row at the first failing step is
+       exchanged with the row of the step that held it and the structure is
+       predicted again (as a restart on a predicted structure does, see
+       gblu_refactorize); after six such rounds, a round without progress or
+       a non-finite candidate, every step goes through the pivoting kernel
+       as in 1.  Taken when every column of A has a
        nonzero diagonal entry and at most 2% of the off-diagonal entries of
        A lack their transposed entry; otherwise as 1.
        1 = the pivoting kernel's passes speculate that each step pivots on
@@ -198,8 +202,8 @@ int gblu_analyze(gblu_handle h, int32_t n, const int32_t *Ap, const int32_t *Ai,
  * By default (speculate_first = 2) the prediction that every step keeps its
  * diagonal row is first installed as a structure and the checked
  * re-factorization kernel computes the columns on it; where a check fails,
- * the pivoting kernel recomputes the unfinished columns and their
- * column-elimination-tree ancestors (the restart of Section IV-C).
+ * the pivot moves by re-prediction (see gblu_refactorize), or, when that
+ * gives up, the pivoting kernel computes every step.
  * Ax_dev: device float64[nnz] in the slot order of the analyze call's Ai.
  * Builds the factors and, on the host, the fixed-pattern schedule for
  * refactorize and solve.  Synchronizes `stream`.
@@ -216,8 +220,18 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
  * unfinished columns on the installed structure, speculating that every
  * step keeps its preferred row, with the same check confirming each (exact
  * when all pass: the structure is then the old one); if a check fails
- * again, the unfinished columns and their elimination-tree ancestors go
- * through the pivoting kernel and the schedule is rebuilt.  The call then
+ * again, a pivot must move.  On a structure that was predicted (the first
+ * factorization's, or a re-prediction's), the first failing step takes the
+ * threshold rule's row, the step that held that row takes the failing
+ * step's row, the structure is predicted again for these pivot rows (the
+ * Cholesky pattern of B + B^T with B = A(piv, Q), which holds the factors
+ * of B without exchanges) and every column is re-factorized on it with the
+ * check; a step whose preferred row went elsewhere must then pivot on its
+ * largest candidate.  Up to six rounds, each moving the first failure
+ * forward; if they do not finish, every step goes through the pivoting
+ * kernel.  On another structure, the unfinished columns and their
+ * elimination-tree ancestors go through the pivoting kernel.  Either way
+ * the schedule is rebuilt.  The call then
  * returns GBLU_REPIVOTED.  The result equals a factorization with pivoting that
  * prefers the previous pivot sequence.  Synchronizes `stream` once (to read
  * the 4-byte check status).  *repivoted (optional, host) is set to 1 if a
@@ -579,8 +593,10 @@ typedef struct {
     /* last gblu_factorize: 0 = the pivoting kernel computed every step;
        1 = the checked re-factorization on the predicted structure passed
        every check (tail_kernel_ms is its time, first_symbolic_ms the
-       structure's on the host); 2 = a check failed there and the pivoting
-       kernel finished the restart set (the tail_* fields describe it) */
+       structure's on the host); 3 = a check failed there and re-predicted
+       structures (repredictions of them) completed the factorization;
+       2 = the re-prediction gave up and the pivoting kernel computed every
+       step (the tail_* fields describe it) */
     int32_t first_mode;
     double first_symbolic_ms;
     /* wide columns of the installed structure (at most 64 L entries, at
@@ -588,6 +604,12 @@ typedef struct {
        applies all but their last run of dependencies row by row through the
        rows of L (0 when the per-CTA scratch would exceed 1 GiB) */
     int64_t wide_cols;
+    /* structure re-predictions of the last restart or first factorization
+       on a predicted structure: each is one pivot exchange found by the
+       threshold rule at the first failing step, a new predicted structure
+       (the Cholesky pattern of B + B^T for B = A with the new pivot rows)
+       and one checked re-factorization of every column (0: none needed) */
+    int32_t repredictions;
 } gblu_stats;
 
 int gblu_get_stats(gblu_handle h, gblu_stats *s);

@@ -91,6 +91,10 @@ struct gblu_ctx {
     int32_t first_mode = 0;                        // last gblu_factorize: 0 pivoting kernel only,
                                                    // 1 predicted structure, 2 and then the pivoting kernel
     double t_first_symbolic = 0.0;                 // its structure prediction (host ms)
+    bool predicted = false;                        // the installed structure is a symmetric prediction
+    int32_t repredictions = 0;                     // structure re-predictions of the last restart or
+                                                   // first factorization
+    bool strict_on = false, no_stop = false;       // re-factorization check modes of a re-prediction
     bool last_repivot = false;                     // the last refactorization restarted
     bool analyzed = false, factorized = false;
     Pattern P;
@@ -111,6 +115,10 @@ struct gblu_ctx {
     DBuf<int64_t> LUp;
     DBuf<int32_t> LUi, nU, rows, finish, task_ptr, task_cols, amap, piv, pinv;
     DBuf<uint8_t> chain;
+    // re-prediction: steps whose predicted row is not the preferred one, and
+    // the pivot choice read back (step, non-finite flag)
+    DBuf<uint8_t> strict;
+    DBuf<int32_t> pchoice;
     // wide columns taken row by row: their pull starts and the per-CTA dense
     // scratch (pull_slots CTAs x n values and n tags, one counter each)
     DBuf<int32_t> pull_start;
@@ -425,6 +433,8 @@ RefactorArgs refactor_args(gblu_ctx *h, const double *Ax)
     a.force_col = h->force_col;
     a.spin_limit = h->opts.spin_limit;
     a.ctl = h->ctl;
+    a.strict_col = h->strict_on ? h->strict.p : nullptr;
+    a.no_stop = h->no_stop ? 1 : 0;
     if (h->pull_slots > 0) {
         a.pull_start = h->pull_start.p;
         a.Lrp = h->Lrp.p;
@@ -781,6 +791,7 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
     h->n_restart_cols = nR;
     h->t_tail[1] = ms_since(t_r);
     CK(install_structure(h, std::move(S2), &V2, st));
+    h->predicted = false;
     return GBLU_OK;
 }
 
@@ -796,32 +807,139 @@ int run_tail(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<u
 // finished columns of the failed pass keep their values.  A column whose
 // check fails again needs another pivot: *interrupted = 1, and the columns
 // finished by now stay final for the pivoting stage.
-int restart_on_structure(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
+// With no_stop, a failing column does not end the launch: every column is
+// computed, so first_bad is the first step whose check fails (every column
+// before it passed), and that column holds its unnormalized values for the
+// pivot choice of a re-prediction.
+int restart_on_structure(gblu_ctx *h, const double *Ax, cudaStream_t st, bool no_stop, int *interrupted)
 {
     KL(launch_begin_refactor(h->ctl, st));
     RefactorArgs a = refactor_args(h, Ax);
     a.force_col = -1;
     a.skip_done = 1;
+    a.no_stop = no_stop ? 1 : 0;
     a.task_begin = 0;
     a.ntasks = (int32_t)h->W.task_ptr.size() - 1;
     KL(launch_refactor_tasks(a, true, pgrid(h, h->ref_blocks_per_sm), h->epoch, st));
     CK(read_ctl(h, st));
     CK(status_code(h));
-    *interrupted = h->hctl->interrupted;
+    *interrupted = h->hctl->interrupted || h->hctl->first_bad != INT_MAX;
     return GBLU_OK;
+}
+
+// Restart by re-prediction (Section IV-C/D, with the threshold rule of
+// Section II-A).  On entry the installed structure is a symmetric prediction
+// for the pivot rows it holds (pred), every step before k passed its check,
+// and column k, whose check failed, holds its unnormalized values.  The
+// threshold rule then takes at step k the candidate of largest magnitude,
+// the row of some later step s; s is predicted to take k's row in exchange
+// (the row that a kept step s would otherwise lose is k's), the structure is
+// predicted again for the new rows (the Cholesky pattern of B + B^T, B =
+// A(pred, Q)), and the checked re-factorization computes every column in
+// no-stop mode.  Where a step's predicted row is not its preferred one
+// (prefer), the rule takes the largest candidate, so its check asks for a
+// strict maximum (strict_col).  Steps before the first failure keep their
+// rows and values, so every round moves the first failure forward.  *solved
+// = false after kMaxRepredict rounds, a non-finite or all-zero candidate
+// set, a round without progress or a structure that grows past a quarter of
+// the preferred one: the caller then runs the pivoting kernel.
+constexpr int kMaxRepredict = 6;
+
+int repredict(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<int32_t> &prefer, int32_t k,
+              bool *solved)
+{
+    *solved = false;
+    h->repredictions = 0;
+    const int32_t n = h->P.n;
+    const int64_t nnz_limit = h->S.nnz() + h->S.nnz() / 4 + n;
+    std::vector<int32_t> pred = h->S.piv;
+    std::vector<uint8_t> strict(n, 0);
+    for (int32_t j = 0; j < n; j++) strict[j] = pred[j] != prefer[j];
+    CK(ensure(h, h->pchoice, 2));
+    for (int round = 0; round < kMaxRepredict; round++) {
+        if (k < 0 || k >= n) return GBLU_OK;
+        KL(launch_pivot_choice(h->LUp.p, h->LUi.p, h->vals.p, h->nU.p, h->piv.p, h->qinv.p, k, h->pchoice.p, st));
+        int32_t ch[2] = {-1, 0};
+        CU(cudaMemcpyAsync(ch, h->pchoice.p, sizeof ch, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        const int32_t s = ch[0];
+        if (ch[1] || s <= k || s >= n) return GBLU_OK;
+        std::swap(pred[k], pred[s]);
+        strict[k] = pred[k] != prefer[k];
+        strict[s] = pred[s] != prefer[s];
+        Structure S2;
+        symmetric_structure(h->P, S2, &pred);
+        if (S2.nnz() > nnz_limit) return GBLU_OK;
+        CK(install_structure(h, std::move(S2), nullptr, st));
+        h->predicted = true;
+        CK(upload(h, h->strict, strict, st));
+        h->strict_on = true;
+        h->no_stop = true;
+        int interrupted = 0;
+        const int rc = run_refactor(h, Ax, st, &interrupted);
+        h->strict_on = false;
+        h->no_stop = false;
+        CK(rc);
+        h->repredictions = round + 1;
+        const int32_t kn = h->hctl->first_bad;
+        if (kn == INT_MAX) {
+            *solved = true;
+            return GBLU_OK;
+        }
+        if (kn <= k) return GBLU_OK;
+        k = kn;
+    }
+    return GBLU_OK;
+}
+
+// Every step recomputed by the pivoting kernel, preferring the rows
+// prefer[k] (the definition of a factorization with preferred pivots, used
+// when a re-prediction gives up)
+int pivot_every_step(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<int32_t> &prefer)
+{
+    const int32_t n = h->P.n;
+    Structure E;
+    E.n = n;
+    E.LUp.assign(n + 1, 0);
+    E.nU.assign(n, 0);
+    E.piv = prefer;
+    E.pinv.assign(n, -1);
+    for (int32_t k = 0; k < n; k++) E.pinv[prefer[k]] = k;
+    h->S = std::move(E);
+    CK(upload(h, h->piv, h->S.piv, st));
+    CK(upload(h, h->pinv, h->S.pinv, st));
+    const size_t hint = (size_t)(1.25 * (double)(2 * symmetric_fill(h->P) + n));
+    std::vector<uint8_t> all(n, 1);
+    return run_tail(h, Ax, st, all, hint, false, true);
 }
 
 int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
 {
     NvtxRange nvtx_range("restart");
     const int32_t n = h->P.n;
+    h->repredictions = 0;
     if (h->W.dense_m == 0) {
         const auto t0 = std::chrono::steady_clock::now();
         std::vector<int32_t> fin0(n);
         CU(cudaMemcpyAsync(fin0.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         int interrupted = 0;
-        CK(restart_on_structure(h, Ax, st, &interrupted));
+        // on a predicted structure a pivot that must move is found exactly
+        // (no-stop) and re-predicted; on another structure the restart set
+        // goes to the pivoting kernel
+        const bool repred = h->predicted;
+        CK(restart_on_structure(h, Ax, st, repred, &interrupted));
+        if (interrupted && repred) {
+            const std::vector<int32_t> prefer = h->S.piv;
+            bool solved = false;
+            CK(repredict(h, Ax, st, prefer, h->hctl->first_bad, &solved));
+            if (!solved) CK(pivot_every_step(h, Ax, st, prefer));
+            h->n_restart_cols = n;
+            h->tail_passes = solved ? 0 : h->tail_passes;
+            h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (solved) h->t_tail[1] = h->t_tail[3] = 0.0;
+            return GBLU_OK;
+        }
         if (!interrupted) {
             int64_t redone = 0;
             for (int32_t k = 0; k < n; k++) redone += fin0[k] != h->epoch;
@@ -1100,6 +1218,8 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
     CU(cudaStreamSynchronize(st));
     h->first_mode = 0;
     h->t_first_symbolic = 0.0;
+    h->predicted = false;
+    h->repredictions = 0;
     if (spec && h->opts.speculate_first == 2 && zero_diag == 0 && nearly_symmetric(h->P)) {
         // the prediction as a structure: L and U^T with the pattern of the
         // Cholesky factor of (A + A^T)(Q,Q), which holds the pattern of the
@@ -1111,20 +1231,29 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
         symmetric_structure(h->P, S2);
         h->t_first_symbolic = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         CK(install_structure(h, std::move(S2), nullptr, st));
+        h->predicted = true;
         const auto t1 = std::chrono::steady_clock::now();
         int interrupted = 0;
         h->force_col = -1;
-        CK(run_refactor(h, Ax_dev, st, &interrupted));
+        // no-stop: a failing step does not end the launch, so the first one
+        // is known exactly and its column keeps its values for the pivot
+        // choice (the dense tail's block checks its columns itself, so with
+        // a dense tail a failure stops the launch as in a re-factorization)
+        const bool repred = h->W.dense_m == 0;
+        h->no_stop = repred;
+        const int rc = run_refactor(h, Ax_dev, st, &interrupted);
+        h->no_stop = false;
+        CK(rc);
         h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
         h->t_tail[1] = 0.0;
         h->tail_passes = 0;
         h->n_restart_cols = 0;
         h->first_mode = 1;
-        if (interrupted) {
-            // a step needs another row: its unfinished steps and their
-            // column-elimination-tree ancestors go through the pivoting
-            // kernel, as in the second stage of a restart (Section IV-C);
-            // the finished steps kept their diagonal rows
+        if (!repred && interrupted) {
+            // the unfinished steps and their column-elimination-tree
+            // ancestors go through the pivoting kernel, as in the second
+            // stage of a restart (Section IV-C); the finished steps kept
+            // their diagonal rows
             std::vector<int32_t> fin(n);
             CU(cudaMemcpyAsync(fin.data(), h->finish.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
             CU(cudaStreamSynchronize(st));
@@ -1133,6 +1262,19 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
             gblu_restart_set(n, h->P.cetree.data(), finished.data(), rmask.data());
             CK(run_tail(h, Ax_dev, st, rmask, 0, true, true));
             h->first_mode = 2;
+        } else if (repred && h->hctl->first_bad != INT_MAX) {
+            // a step needs another row: the structure is predicted again for
+            // the rows the threshold rule takes (the restart's re-prediction,
+            // with the diagonal rows preferred); if that gives up, the
+            // pivoting kernel computes every step
+            bool solved = false;
+            CK(repredict(h, Ax_dev, st, h->P.Q, h->hctl->first_bad, &solved));
+            if (solved) {
+                h->first_mode = 3;
+            } else {
+                CK(pivot_every_step(h, Ax_dev, st, h->P.Q));
+                h->first_mode = 2;
+            }
         }
         h->factorized = true;
         return GBLU_OK;
@@ -2146,6 +2288,7 @@ int gblu_get_stats(gblu_handle h, gblu_stats *s)
     s->first_mode = h->first_mode;
     s->first_symbolic_ms = h->t_first_symbolic;
     s->wide_cols = h->pull_slots > 0 ? h->W.pull_cols : 0;
+    s->repredictions = h->repredictions;
     if (h->factorized) {
         int64_t nu = 0;
         for (int32_t v : h->S.nU) nu += v;

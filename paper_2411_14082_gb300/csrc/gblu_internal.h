@@ -167,8 +167,11 @@ int auto_order(int32_t n, const int32_t *Ap, const int32_t *Ai, int32_t *perm);
 int64_t symmetric_fill(const Pattern &P, double *flops = nullptr);
 // factor structure when every step keeps its diagonal row: L and U^T with
 // the pattern of that Cholesky factor (a superset of the exact LU pattern,
-// equal on structurally symmetric matrices); piv = Q
-void symmetric_structure(const Pattern &P, Structure &S);
+// equal on structurally symmetric matrices); piv = Q.  With piv given, the
+// same for the steps taking the rows piv[k]: the pattern of the Cholesky
+// factor of B + B^T, B = A(piv, Q), which holds the factors of B without
+// row exchanges
+void symmetric_structure(const Pattern &P, Structure &S, const std::vector<int32_t> *piv = nullptr);
 // off-diagonal entries of A whose transposed position is not an entry of A
 int64_t unsymmetric_entries(const Pattern &P);
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
@@ -230,6 +233,14 @@ struct RefactorArgsT {
     double eps;
     int32_t force_col = -1;         // evaluation aid: this column's check fails
     int32_t skip_done = 0;          // 1: a column whose ready flag holds the epoch is final; skip it
+    // restart by re-prediction: strict_col[k] = 1 where step k's predicted
+    // row is not its preferred one, so that the threshold rule takes the
+    // candidate of largest magnitude there and the check asks the predicted
+    // row's |x| to exceed every other candidate's; no_stop = 1: a failed
+    // check records first_bad, stores the column unnormalized and publishes
+    // it, and the launch runs on (later columns are then meaningless)
+    const uint8_t *strict_col = nullptr;
+    int32_t no_stop = 0;
     long long spin_limit;
     DevCtl *ctl;
     // wide columns (Schedule::pull_start): their first pull_start[k]
@@ -327,6 +338,10 @@ constexpr int32_t kTailSmemBits = 1 << 19;   // steps whose bitmap fits in share
 int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, const int32_t *cnu,
                         const int32_t *cnl, const int32_t *prow, const int64_t *LUp, const int32_t *LUi,
                         const int32_t *pinv, int32_t n, double *vals, int32_t *bad, void *stream);
+// the pivot of step k after its check failed: the candidate of largest |x|
+// in column k (values unnormalized), out[0] its step, out[1] a non-finite flag
+int launch_pivot_choice(const int64_t *LUp, const int32_t *LUi, const double *LUx, const int32_t *nU,
+                        const int32_t *piv, const int32_t *qinv, int32_t k, int32_t *out, void *stream);
 // dense tail of the re-factorization (dense.cu)
 struct DenseArgs2 {
     double *S;                      // m x m, column-major, leading dimension ld

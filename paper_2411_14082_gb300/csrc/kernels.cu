@@ -1253,6 +1253,83 @@ int launch_pool_scatter(const int32_t *seq, int32_t nseq, const int64_t *cbeg, c
     return (int)cudaGetLastError();
 }
 
+// Threshold pivoting at the first step whose check failed (Section II-A,
+// the pivot choice of Algorithm 1).  The candidates of column k are its
+// predicted pivot slot (step k) and its L rows (steps s > k), slot s standing
+// for the row piv[s]; the column holds its values unnormalized (a failed
+// check in no-stop mode).  The choice is the candidate of largest |x|, ties
+// going to the row that comes first in the column order Q (smallest
+// qinv[row]); a zero candidate is never chosen.  out[0] = the chosen slot's
+// step (-1 when every candidate is zero), out[1] = 1 when a candidate is
+// infinite or NaN.  One block.
+__global__ void pivot_choice_kernel(const int64_t *LUp, const int32_t *LUi, const double *LUx, const int32_t *nU,
+                                    const int32_t *piv, const int32_t *qinv, int32_t k, int32_t *out)
+{
+    __shared__ double s_a[32];
+    __shared__ int s_q[32], s_s[32], s_bad[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t beg = LUp[k];
+    const int len = (int)(LUp[k + 1] - beg);
+    const int u = nU[k];
+    double ba = 0.0;
+    int bq = INT_MAX, bs = -1;
+    bool bad = false;
+    for (int i = u - 1 + (int)threadIdx.x; i < len; i += blockDim.x) {
+        const double v = LUx[beg + i];
+        if (!isfinite(v)) {
+            bad = true;
+            continue;
+        }
+        const double av = fabs(v);
+        if (av == 0.0) continue;
+        const int s = LUi[beg + i];
+        const int q = qinv[piv[s]];
+        if (av > ba || (av == ba && q < bq)) {
+            ba = av;
+            bq = q;
+            bs = s;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oa = __shfl_down_sync(0xffffffffu, ba, o);
+        const int oq = __shfl_down_sync(0xffffffffu, bq, o);
+        const int os = __shfl_down_sync(0xffffffffu, bs, o);
+        if (oa > ba || (oa == ba && oq < bq)) {
+            ba = oa;
+            bq = oq;
+            bs = os;
+        }
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        s_a[warp] = ba;
+        s_q[warp] = bq;
+        s_s[warp] = bs;
+        s_bad[warp] = any_bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int flag = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            flag |= s_bad[w];
+            if (s_a[w] > ba || (s_a[w] == ba && s_q[w] < bq)) {
+                ba = s_a[w];
+                bq = s_q[w];
+                bs = s_s[w];
+            }
+        }
+        out[0] = bs;
+        out[1] = flag;
+    }
+}
+
+int launch_pivot_choice(const int64_t *LUp, const int32_t *LUi, const double *LUx, const int32_t *nU,
+                        const int32_t *piv, const int32_t *qinv, int32_t k, int32_t *out, void *stream)
+{
+    pivot_choice_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(LUp, LUi, LUx, nU, piv, qinv, k, out);
+    return (int)cudaGetLastError();
+}
+
 int launch_begin_tail(DevCtl *ctl, unsigned long long pool_base, void *stream)
 {
     begin_tail_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, pool_base);

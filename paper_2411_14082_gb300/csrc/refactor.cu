@@ -93,6 +93,20 @@ __device__ __forceinline__ void find_slots(const int32_t *rows, const int (&lo0)
     for (int u = 0; u < K; u++) slot[u] = (lo[u] == hi[u] && rows[lo[u]] == key[u]) ? lo[u] : -1;
 }
 
+// The pivot check of step k (Algorithms 3 and 4): d = x(k), the predicted
+// pivot, m = max |x| over the column's L rows (NaN if one of them is NaN).
+// The threshold rule keeps the preferred row when d != 0 and |d| >= eps*m;
+// a step whose preferred row went to an earlier step (strict_col) takes the
+// candidate of largest magnitude, so there |d| > m.  An infinite or NaN d or
+// m fails either way, and the restart reports the value.
+template <typename R>
+__device__ __forceinline__ bool check_pivot(const RefactorArgsT<R> &a, int k, R d, R m)
+{
+    if (k == a.force_col || !(d != R(0)) || !isfinite(d)) return false;
+    if (a.strict_col && a.strict_col[k]) return fabs(d) > m;
+    return fabs(d) >= a.eps * m;
+}
+
 // one column, one warp.  Dependencies are applied in runs of consecutive
 // columns of one supernode of L, as in the group kernel below (there with
 // the full description), here with runs of at most kWarpRun columns and the
@@ -256,14 +270,15 @@ __device__ bool col_warp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, i
     R m = R(0);
     for (int i = nU + lane; i < len; i += 32) m = max_nan(m, fabs(x[i]));
     m = warp_max(m);
-    if (!((d != R(0)) && isfinite(d) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
+    const bool pass = check_pivot(a, k, d, m);
+    if (!pass) {
         if (lane == 0) {
-            atomicExch(&a.ctl->interrupted, 1);
+            if (!a.no_stop) atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
         }
-        return false;
+        if (!a.no_stop) return false;
     }
-    const R inv = R(1) / d;
+    const R inv = pass ? R(1) / d : R(1);   // a failed column stays unnormalized
     if (in_smem) {
         for (int i = lane; i < len; i += 32) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
     } else {
@@ -775,14 +790,15 @@ __device__ bool col_grp(const RefactorArgsT<R> &a, int k, R *xs, int32_t *rs, in
     group_sync<NW>(g);
     m = sh.red[0];
     for (int w = 1; w < NW; w++) m = max_nan(m, sh.red[w]);
-    if (!((d != R(0)) && isfinite(d) && (fabs(d) >= a.eps * m)) || k == a.force_col) {
+    const bool pass = check_pivot(a, k, d, m);
+    if (!pass) {
         if (tid == 0) {
-            atomicExch(&a.ctl->interrupted, 1);
+            if (!a.no_stop) atomicExch(&a.ctl->interrupted, 1);
             atomicMin(&a.ctl->first_bad, k);
         }
-        return false;
+        if (!a.no_stop) return false;
     }
-    const R inv = R(1) / d;
+    const R inv = pass ? R(1) / d : R(1);   // a failed column stays unnormalized
     if (in_smem) {
         for (int i = tid; i < len; i += kT) a.LUx[beg + i] = (i < nU) ? xs[i] : xs[i] * inv;
     } else {

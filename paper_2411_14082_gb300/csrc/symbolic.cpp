@@ -80,13 +80,15 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
 // adjacent to step i) and the elimination tree of S (Liu's algorithm with
 // path compression).
 static void symmetric_graph(const Pattern &P, std::vector<int64_t> &cnt, std::vector<int32_t> &lowadj,
-                            std::vector<int32_t> &parent)
+                            std::vector<int32_t> &parent, const int32_t *rowstep = nullptr)
 {
     const int32_t n = P.n;
+    // entry A(r, c) joins the steps rowstep[r] (qinv[r] by default) and qinv[c]
+    const int32_t *rs = rowstep ? rowstep : P.qinv.data();
     cnt.assign(n + 1, 0);
     for (int32_t c = 0; c < n; c++)
         for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-            const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+            const int32_t i = rs[P.Ai[p]], j = P.qinv[c];
             if (i != j) cnt[std::max(i, j) + 1]++;
         }
     for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
@@ -95,7 +97,7 @@ static void symmetric_graph(const Pattern &P, std::vector<int64_t> &cnt, std::ve
         std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
         for (int32_t c = 0; c < n; c++)
             for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-                const int32_t i = P.qinv[P.Ai[p]], j = P.qinv[c];
+                const int32_t i = rs[P.Ai[p]], j = P.qinv[c];
                 if (i != j) lowadj[pos[std::max(i, j)]++] = std::min(i, j);
             }
     }
@@ -670,7 +672,8 @@ int64_t unsymmetric_entries(const Pattern &P)
 }
 
 // Factor structure of a first factorization that predicts every step to
-// keep its diagonal row (piv = Q).  L and U^T take the pattern of the
+// keep its diagonal row (piv = Q; or the rows piv[k] when given, with A
+// read as B = A(piv, Q) below).  L and U^T take the pattern of the
 // Cholesky factor of S = (A + A^T)(Q,Q): column k holds the row subtree of k
 // in the elimination tree of S (its U rows, ascending), k itself, then the
 // rows i > k whose row subtree contains k.  This pattern contains the
@@ -681,12 +684,17 @@ int64_t unsymmetric_entries(const Pattern &P)
 // host threads: their sizes, then over fixed row ranges the L entries each
 // range gives every column, then the entries themselves, each range writing
 // its own part of every L column so that the rows stay ascending.
-void symmetric_structure(const Pattern &P, Structure &S)
+void symmetric_structure(const Pattern &P, Structure &S, const std::vector<int32_t> *piv)
 {
     const int32_t n = P.n;
+    std::vector<int32_t> pinv;
+    if (piv) {
+        pinv.assign(n, -1);
+        for (int32_t k = 0; k < n; k++) pinv[(*piv)[k]] = k;
+    }
     std::vector<int64_t> adjp;
     std::vector<int32_t> adj, parent;
-    symmetric_graph(P, adjp, adj, parent);
+    symmetric_graph(P, adjp, adj, parent, piv ? pinv.data() : nullptr);
     // walk(k, fn): fn(j) for every j of the row subtree of k
     auto walk = [&](int32_t k, std::vector<int32_t> &mark, auto &&fn) {
         mark[k] = k;
@@ -780,8 +788,13 @@ void symmetric_structure(const Pattern &P, Structure &S)
             u[m] = k;
         }
     });
-    S.piv = P.Q;
-    S.pinv = P.qinv;
+    if (piv) {
+        S.piv = *piv;
+        S.pinv = std::move(pinv);
+    } else {
+        S.piv = P.Q;
+        S.pinv = P.qinv;
+    }
 }
 
 }  // namespace gblu

@@ -82,7 +82,8 @@ class Stats(ctypes.Structure):
                 ("tail_kernel_ms", ctypes.c_double), ("tail_repack_ms", ctypes.c_double),
                 ("tail_schedule_ms", ctypes.c_double), ("tail_upload_ms", ctypes.c_double),
                 ("tail_passes", ctypes.c_int32), ("first_mode", ctypes.c_int32),
-                ("first_symbolic_ms", ctypes.c_double), ("wide_cols", ctypes.c_int64)]
+                ("first_symbolic_ms", ctypes.c_double), ("wide_cols", ctypes.c_int64),
+                ("repredictions", ctypes.c_int32)]
 
 
 class RequestResult(ctypes.Structure):

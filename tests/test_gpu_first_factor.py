@@ -2,8 +2,10 @@
 as the preferred row) in speculative passes against the same factorization
 that waits on every earlier unfinished step in order, and (the default) on
 the predicted structure: the checked re-factorization kernel computes every
-column there, and a failing check sends the unfinished steps and their
-column-elimination-tree ancestors to the pivoting kernel.
+column there; at the first failing check the threshold rule's row is
+exchanged with the row of the step that held it and the structure is
+predicted again (first_mode 3), and when that gives up the pivoting kernel
+computes every step (first_mode 2).
 
 The two give the same dependencies in the same ascending order, so their
 factors are bit-for-bit equal; both equal the oracle within the parity
@@ -77,9 +79,14 @@ def check(n, Ap, Ai, Ax, Q, rtol=1e-10):
     fp, sp_ = factor(n, Ap, Ai, Ax, Q, 2)
     compare_factors(fp, lu, rtol)
     if structure_path_taken(n, Ap, Ai, Ax, Q):
-        assert sp_["first_mode"] == (1 if moved == 0 else 2)
         if moved == 0:
+            assert sp_["first_mode"] == 1 and sp_["repredictions"] == 0
             assert sp_["tail_passes"] == 0
+        else:
+            assert sp_["first_mode"] in (2, 3)
+            if sp_["first_mode"] == 3:
+                # every round fixes at least one moved step's row
+                assert 1 <= sp_["repredictions"] <= moved
     else:
         assert sp_["first_mode"] == 0
         same_factors(fp, fs)
@@ -88,14 +95,14 @@ def check(n, Ap, Ai, Ax, Q, rtol=1e-10):
         assert ss["tail_passes"] == 1
     else:
         assert ss["tail_passes"] >= 2
-    return moved, ss["tail_passes"]
+    return moved, ss["tail_passes"], sp_
 
 
 def test_mesh_every_step_keeps_its_diagonal():
     ckt = inputs.rc_mesh3d(40, 40, 4, seed=7, n_fet=100)
     n, Ap, Ai, Ax = ckt.csc()
     assert structure_path_taken(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt))
-    moved, passes = check(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt))
+    moved, passes, _ = check(n, Ap, Ai, Ax, inputs.grid_nd_order(ckt))
     assert moved == 0 and passes == 1
 
 
@@ -107,7 +114,7 @@ def test_mna_grid_with_voltage_sources():
     n, Ap, Ai, Ax = ckt.csc()
     Q = inputs.grid_nd_order(ckt)
     assert zero_diagonals(n, Ap, Ai, Ax, Q) > 4
-    moved, passes = check(n, Ap, Ai, Ax, Q)
+    moved, passes, _ = check(n, Ap, Ai, Ax, Q)
     assert moved > 4 and passes == 1
 
 
@@ -116,7 +123,9 @@ def test_one_step_leaves_its_diagonal():
     becomes 1e-9 of the unshifted one, below the threshold: that step takes
     another step's row, and that step (two moved pivots in all) takes another
     row in turn.  The steps after each of the two run again, in speculative
-    passes."""
+    passes.  On the predicted structure the two steps exchange their rows:
+    one re-prediction (the failing step takes the row of the step that held
+    it, which takes the failing step's row) is exactly right."""
     ckt = inputs.rc_mesh3d(40, 40, 4, seed=13, n_fet=100)
     n, Ap, Ai, Ax = ckt.csc()
     Q = inputs.grid_nd_order(ckt)
@@ -141,8 +150,9 @@ def test_one_step_leaves_its_diagonal():
             assert tried < 20
             continue
         assert structure_path_taken(n, Ap, Ai, Ax2, Q)
-        moved, passes = check(n, Ap, Ai, Ax2, Q)
+        moved, passes, sp_ = check(n, Ap, Ai, Ax2, Q)
         assert moved == 2 and passes in (2, 3)
+        assert sp_["first_mode"] == 3 and sp_["repredictions"] == 1
         return
     pytest.fail("no step found whose shifted diagonal swaps two pivots")
 
