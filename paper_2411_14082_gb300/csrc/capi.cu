@@ -852,6 +852,8 @@ int repredict(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<
     h->repredictions = 0;
     const int32_t n = h->P.n;
     const int64_t nnz_limit = h->S.nnz() + h->S.nnz() / 4 + n;
+    // the failing step reported for the call is the first check's
+    const int32_t first_bad = h->last_first_bad;
     std::vector<int32_t> pred = h->S.piv;
     std::vector<uint8_t> strict(n, 0);
     for (int32_t j = 0; j < n; j++) strict[j] = pred[j] != prefer[j];
@@ -879,6 +881,7 @@ int repredict(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<
         const int rc = run_refactor(h, Ax, st, &interrupted);
         h->strict_on = false;
         h->no_stop = false;
+        h->last_first_bad = first_bad;
         CK(rc);
         h->repredictions = round + 1;
         const int32_t kn = h->hctl->first_bad;
@@ -1263,6 +1266,7 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
             CK(run_tail(h, Ax_dev, st, rmask, 0, true, true));
             h->first_mode = 2;
         } else if (repred && h->hctl->first_bad != INT_MAX) {
+            h->last_first_bad = h->hctl->first_bad;
             // a step needs another row: the structure is predicted again for
             // the rows the threshold rule takes (the restart's re-prediction,
             // with the diagonal rows preferred); if that gives up, the
