@@ -113,7 +113,7 @@ struct Schedule {
     int32_t lp0 = 0, up0 = 0;
     int32_t lnb = 0, unb = 0;
     std::vector<int64_t> ltri0, ufar;
-    std::vector<int32_t> lseg, useg;
+    BigVec<int32_t> lseg, useg;
     // dense tail of the re-factorization: columns [dense_p, n) form a
     // structurally dense block of dense_m = n - dense_p rows (0: none);
     // dense_s0[c] = slot of row dense_p inside column dense_p + c

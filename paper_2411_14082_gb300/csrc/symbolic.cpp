@@ -514,53 +514,6 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         for (int32_t i = 0; i < n; i++) ru[i] = W.Urp[i + 1] - W.Urp[i];
         W.up0 = dense_split(n, cu, ru, split, W.ucut);
     }
-    // ---- trailing block in 32-row slices (forward L, backward U) ----
-    W.ltri0.clear();
-    W.lseg.clear();
-    W.lnb = 0;
-    if (W.lp0 < n) {
-        const int32_t m = n - W.lp0, nb = (m + kTrailRows - 1) / kTrailRows;
-        W.lnb = nb;
-        W.ltri0.resize(m);
-        for (int32_t i = W.lp0; i < n; i++) {
-            const int32_t *c = W.Lcol.data() + W.Lrp[i];
-            const int32_t len = (int32_t)(W.Lrp[i + 1] - W.Lrp[i]);
-            W.ltri0[i - W.lp0] = W.Lrp[i] + (std::lower_bound(c, c + len, W.lp0) - c);
-        }
-        W.lseg.assign((size_t)m * (nb + 1), 0);
-        for (int32_t j = W.lp0; j < n; j++) {
-            const int32_t *r = S.LUi.data() + S.LUp[j] + S.nU[j];
-            const int32_t len = (int32_t)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
-            int32_t *sg = W.lseg.data() + (size_t)(j - W.lp0) * (nb + 1);
-            for (int32_t I = 0; I <= nb; I++) {
-                const int64_t lo = (int64_t)W.lp0 + (int64_t)kTrailRows * I;
-                sg[I] = lo >= n ? len : (int32_t)(std::lower_bound(r, r + len, (int32_t)lo) - r);
-            }
-        }
-    }
-    W.ufar.clear();
-    W.useg.clear();
-    W.unb = 0;
-    if (W.up0 < n) {
-        const int32_t m = n - W.up0, nb = (m + kTrailRows - 1) / kTrailRows;
-        W.unb = nb;
-        W.ufar.resize(W.up0);
-        for (int32_t i = 0; i < W.up0; i++) {
-            const int32_t *c = W.Urow_col.data() + W.Urp[i];
-            const int32_t len = (int32_t)(W.Urp[i + 1] - W.Urp[i]);
-            W.ufar[i] = W.Urp[i] + (std::lower_bound(c, c + len, W.up0) - c);
-        }
-        W.useg.assign((size_t)m * (nb + 1), 0);
-        for (int32_t j = W.up0; j < n; j++) {
-            const int32_t *r = S.LUi.data() + S.LUp[j];
-            const int32_t len = S.nU[j];   // U rows ascending, the diagonal (row j) last
-            int32_t *sg = W.useg.data() + (size_t)(j - W.up0) * (nb + 1);
-            for (int32_t I = 0; I <= nb; I++) {
-                const int64_t lo = (int64_t)W.up0 + (int64_t)kTrailRows * I;
-                sg[I] = lo >= n ? len : (int32_t)(std::lower_bound(r, r + len, (int32_t)lo) - r);
-            }
-        }
-    }
     // ---- row blocks of the sparse solves and their levels ----
     // forward: rows i-1 and i share a block when L(:,i-1) = {i} + L(:,i)
     // (then row f+q holds L(f+q, f..f+q-1) as its last q entries);
@@ -638,11 +591,82 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
         for (int32_t l = 0; l < nlev; l++)
             if ((double)(tptr[l + 1] - tptr[l]) < thr) { div = l; break; }
     };
-    // the two triangles' levels are independent
+    // the two triangles' levels are independent, and independent of the
+    // trailing block's slices below
     std::thread upper([&]() {
         levelize(false, W.ubs, W.usv_ptr, W.usv_rows, W.usv_tptr, W.usv_tick, W.urb, W.usv_levels, W.usv_div);
     });
-    levelize(true, W.lbs, W.lsv_ptr, W.lsv_rows, W.lsv_tptr, W.lsv_tick, W.lrb, W.lsv_levels, W.lsv_div);
+    std::thread lower([&]() {
+        levelize(true, W.lbs, W.lsv_ptr, W.lsv_rows, W.lsv_tptr, W.lsv_tick, W.lrb, W.lsv_levels, W.lsv_div);
+    });
+    // ---- trailing block in 32-row slices (forward L, backward U), over
+    // column chunks on the host threads; a column's rows ascend, so the
+    // slice boundaries are found in one walk down them ----
+    W.ltri0.clear();
+    W.lseg.clear();
+    W.lnb = 0;
+    if (W.lp0 < n) {
+        const int32_t m = n - W.lp0, nb = (m + kTrailRows - 1) / kTrailRows;
+        W.lnb = nb;
+        W.ltri0.resize(m);
+        W.lseg.resize((size_t)m * (nb + 1));
+        parallel_chunks(m, 256, [&](int32_t a, int32_t b, int) {
+            for (int32_t i = W.lp0 + a; i < W.lp0 + b; i++) {
+                const int32_t *c = W.Lcol.data() + W.Lrp[i];
+                const int32_t len = (int32_t)(W.Lrp[i + 1] - W.Lrp[i]);
+                W.ltri0[i - W.lp0] = W.Lrp[i] + (std::lower_bound(c, c + len, W.lp0) - c);
+            }
+            for (int32_t j = W.lp0 + a; j < W.lp0 + b; j++) {
+                const int32_t *r = S.LUi.data() + S.LUp[j] + S.nU[j];
+                const int32_t len = (int32_t)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
+                int32_t *sg = W.lseg.data() + (size_t)(j - W.lp0) * (nb + 1);
+                int32_t pos = 0;
+                for (int32_t I = 0; I <= nb; I++) {
+                    const int64_t lo = (int64_t)W.lp0 + (int64_t)kTrailRows * I;
+                    if (lo >= n) {
+                        sg[I] = len;
+                        continue;
+                    }
+                    while (pos < len && r[pos] < lo) pos++;
+                    sg[I] = pos;
+                }
+            }
+        });
+    }
+    W.ufar.clear();
+    W.useg.clear();
+    W.unb = 0;
+    if (W.up0 < n) {
+        const int32_t m = n - W.up0, nb = (m + kTrailRows - 1) / kTrailRows;
+        W.unb = nb;
+        W.ufar.resize(W.up0);
+        parallel_chunks(W.up0, 2048, [&](int32_t a, int32_t b, int) {
+            for (int32_t i = a; i < b; i++) {
+                const int32_t *c = W.Urow_col.data() + W.Urp[i];
+                const int32_t len = (int32_t)(W.Urp[i + 1] - W.Urp[i]);
+                W.ufar[i] = W.Urp[i] + (std::lower_bound(c, c + len, W.up0) - c);
+            }
+        });
+        W.useg.resize((size_t)m * (nb + 1));
+        parallel_chunks(m, 256, [&](int32_t a, int32_t b, int) {
+            for (int32_t j = W.up0 + a; j < W.up0 + b; j++) {
+                const int32_t *r = S.LUi.data() + S.LUp[j];
+                const int32_t len = S.nU[j];   // U rows ascending, the diagonal (row j) last
+                int32_t *sg = W.useg.data() + (size_t)(j - W.up0) * (nb + 1);
+                int32_t pos = 0;
+                for (int32_t I = 0; I <= nb; I++) {
+                    const int64_t lo = (int64_t)W.up0 + (int64_t)kTrailRows * I;
+                    if (lo >= n) {
+                        sg[I] = len;
+                        continue;
+                    }
+                    while (pos < len && r[pos] < lo) pos++;
+                    sg[I] = pos;
+                }
+            }
+        });
+    }
+    lower.join();
     upper.join();
     level_thread.join();
 }
