@@ -707,6 +707,17 @@ int gblu_symmetric_cost(int32_t n, const int32_t *Ap, const int32_t *Ai, const i
  * an invalid pattern or a Q that is not a permutation. */
 int64_t gblu_symmetric_structure(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
                                  int64_t *LUp, int32_t *LUi, int32_t *nU);
+/* The same for given pivot rows: the structure that a restart or a first
+ * factorization predicts after pivot exchanges (gblu_refactorize), for the
+ * steps taking the original rows piv[k] (a permutation; NULL = Q, which is
+ * gblu_symmetric_structure).  With B = A(piv, Q), L and U^T take the
+ * pattern of the Cholesky factor of B + B^T, which contains the pattern of
+ * the LU factors of B without row exchanges (a structurally zero diagonal
+ * entry of B does not matter: fill follows paths through lower steps).
+ * Arguments, results and errors as gblu_symmetric_structure; piv is a host
+ * array. */
+int64_t gblu_predicted_structure(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                                 const int32_t *piv, int64_t *LUp, int32_t *LUi, int32_t *nU);
 /* The structure-adaptive split of one triangular factor (Section V-A), as
  * the solve setup computes it.  count_from[p] (n+1 entries, count_from[n]
  * = 0): strict entries of the trailing block [p, n); rowlen[i] (n): all

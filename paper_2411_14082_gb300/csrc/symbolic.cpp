@@ -925,6 +925,36 @@ extern "C" int64_t gblu_symmetric_structure(int32_t n, const int32_t *Ap, const 
     return S.nnz();
 }
 
+extern "C" int64_t gblu_predicted_structure(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q,
+                                            const int32_t *piv, int64_t *LUp, int32_t *LUi, int32_t *nU)
+{
+    if (!piv) return gblu_symmetric_structure(n, Ap, Ai, Q, LUp, LUi, nU);
+    std::string err;
+    if (validate_pattern(n, Ap, Ai, err) != GBLU_OK || !Q)
+        return record_error(GBLU_ERR_INVALID_INPUT, "predicted structure: invalid pattern or null Q");
+    Pattern P;
+    P.n = n;
+    P.Ap.assign(Ap, Ap + n + 1);
+    P.Ai.assign(Ai, Ai + Ap[n]);
+    P.Q.assign(Q, Q + n);
+    P.qinv.assign(n, -1);
+    std::vector<int32_t> pv(piv, piv + n), seen(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        if (Q[k] < 0 || Q[k] >= n || P.qinv[Q[k]] >= 0 || pv[k] < 0 || pv[k] >= n || seen[pv[k]])
+            return record_error(GBLU_ERR_INVALID_INPUT, "predicted structure: Q or piv is not a permutation");
+        P.qinv[Q[k]] = k;
+        seen[pv[k]] = 1;
+    }
+    Structure S;
+    symmetric_structure(P, S, &pv);
+    if (LUp && LUi && nU) {
+        std::memcpy(LUp, S.LUp.data(), sizeof(int64_t) * (n + 1));
+        std::memcpy(nU, S.nU.data(), sizeof(int32_t) * n);
+        std::memcpy(LUi, S.LUi.data(), sizeof(int32_t) * S.LUi.size());
+    }
+    return S.nnz();
+}
+
 extern "C" int64_t gblu_symmetric_fill(int32_t n, const int32_t *Ap, const int32_t *Ai, const int32_t *Q)
 {
     int64_t fill = 0;

@@ -46,7 +46,7 @@ EXPORTED = [
     "gblu_order_amf", "gblu_last_status", "gblu_solve_partition",
     "gblu_server_last_error", "gblu_server_create", "gblu_server_add_pattern", "gblu_server_pattern_info",
     "gblu_server_submit", "gblu_server_wait", "gblu_server_get_stats", "gblu_server_destroy",
-    "gblu_fp64_fma_rate", "gblu_step_batch", "gblu_symmetric_structure",
+    "gblu_fp64_fma_rate", "gblu_step_batch", "gblu_symmetric_structure", "gblu_predicted_structure",
 ]
 
 NOALLOC_MAX_N = 524288
@@ -149,6 +149,8 @@ def load(build_if_missing: bool = True):
         lib.gblu_symmetric_fill.restype = I64
         lib.gblu_symmetric_structure.argtypes = [I32, P, P, P, P, P, P]
         lib.gblu_symmetric_structure.restype = I64
+        lib.gblu_predicted_structure.argtypes = [I32, P, P, P, P, P, P, P]
+        lib.gblu_predicted_structure.restype = I64
         lib.gblu_order_cnd.argtypes = [I32, P, P, P]
         lib.gblu_order_cnd.restype = ctypes.c_int
         lib.gblu_symmetric_cost.argtypes = [I32, P, P, P, P, P]
@@ -605,6 +607,24 @@ def symmetric_structure(n, Ap, Ai, Q):
     LUi = np.empty(max(nnz, 1), np.int32)
     nU = np.empty(n, np.int32)
     lib.gblu_symmetric_structure(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), _np_ptr(LUp), _np_ptr(LUi),
+                                 _np_ptr(nU))
+    return LUp, LUi[:nnz], nU
+
+
+def predicted_structure(n, Ap, Ai, Q, piv=None):
+    """The structure predicted for the steps taking the original rows piv
+    (gblu_predicted_structure, host; piv None = Q): (LUp, LUi, nU)."""
+    Ap, Ai, Q = _i32(Ap), _i32(Ai), _i32(Q)
+    pv = None if piv is None else _i32(piv)
+    pp = None if pv is None else _np_ptr(pv)
+    lib = load()
+    nnz = lib.gblu_predicted_structure(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), pp, None, None, None)
+    if nnz < 0:
+        raise GbluError(int(nnz), "invalid pattern, order or rows")
+    LUp = np.empty(n + 1, np.int64)
+    LUi = np.empty(max(nnz, 1), np.int32)
+    nU = np.empty(n, np.int32)
+    lib.gblu_predicted_structure(int(n), _np_ptr(Ap), _np_ptr(Ai), _np_ptr(Q), pp, _np_ptr(LUp), _np_ptr(LUi),
                                  _np_ptr(nU))
     return LUp, LUi[:nnz], nU
 

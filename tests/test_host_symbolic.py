@@ -310,6 +310,50 @@ def test_predicted_structure_holds_the_oracle_factors():
             assert np.all(M[i, cols]), part
 
 
+def test_predicted_structure_for_given_rows():
+    """gblu_predicted_structure with pivot rows piv (the structure a restart
+    predicts after pivot exchanges) is the Cholesky pattern of B + B^T for
+    B = A(piv, Q), found by dense boolean elimination; it contains the
+    pattern of B's LU factors without row exchanges, also where B has
+    structurally zero diagonal entries (fill makes them nonzero), and the
+    oracle's factors whenever the oracle keeps the rows piv (Algorithm 1
+    with those rows preferred and a tiny threshold).  piv = Q is
+    gblu_symmetric_structure."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(37)
+    kept = kept_zero = zero_diag = 0
+    for trial in range(120):
+        n = int(rng.integers(2, 50))
+        _, Ap, Ai, Ax = inputs.random_sparse(n, rng.uniform(0.05, 0.3), rng, dominance=2.0)
+        Q = rng.permutation(n).astype(np.int32)
+        piv = Q.copy()
+        for _ in range(int(rng.integers(1, 4))):   # a few exchanges of two steps' rows
+            a, b = rng.choice(n, 2, replace=False)
+            piv[a], piv[b] = piv[b], piv[a]
+        M = structure_pattern(n, *gblu.predicted_structure(n, Ap, Ai, Q, piv))
+        A = dense_pattern(n, Ap, Ai)
+        B = A[np.ix_(piv, Q)]
+        zd = bool(np.any(~np.diag(B)))
+        zero_diag += zd
+        assert np.array_equal(M, boolean_lu(B | B.T))
+        assert not np.any(boolean_lu(B) & ~M)
+        lu = O.factorize(n, Ap, Ai, Ax, Q, 1e-12, prefer=piv)
+        if lu.status == O.OK and np.array_equal(lu.piv, piv):
+            kept += 1
+            kept_zero += zd
+            for part in ("L", "U"):
+                p, i = np.asarray(getattr(lu, part + "p"), np.int64), getattr(lu, part + "i")
+                cols = np.repeat(np.arange(n), np.diff(p))
+                assert np.all(M[i, cols]), part
+    assert kept >= 25 and kept_zero >= 15 and zero_diag >= 80
+    _, Ap, Ai, _ = inputs.random_sparse(30, 0.1, rng)
+    Q = rng.permutation(30).astype(np.int32)
+    for got, want in zip(gblu.predicted_structure(30, Ap, Ai, Q, None), gblu.symmetric_structure(30, Ap, Ai, Q)):
+        assert np.array_equal(got, want)
+    with pytest.raises(gblu.GbluError):
+        gblu.predicted_structure(3, np.array([0, 1, 2, 3]), np.array([0, 1, 2]), np.arange(3), np.array([0, 0, 1]))
+
+
 def test_constrained_minimum_degree():
     """gblu_order_cmd: one group gives plain minimum degree; with groups the
     elimination order never goes back to a lower group, and a group
