@@ -581,7 +581,11 @@ typedef struct {
     int32_t dense_rows;   /* rows of the dense tail block (0: none)          */
     /* last factorization with pivoting (first factorization or restart),
      * host wall clock: tail kernel, download and repack of the factors,
-     * schedule rebuild, upload of the new structure */
+     * schedule rebuild, upload of the new structure.  On a predicted
+     * structure the solve part of the schedule is built on the host while
+     * the re-factorization runs; it counts in tail_schedule_ms and in
+     * tail_kernel_ms (the re-factorization's wall clock), and its upload
+     * in tail_kernel_ms only. */
     double tail_kernel_ms, tail_repack_ms, tail_schedule_ms, tail_upload_ms;
     int32_t tail_passes;  /* kernel passes of that run (a restart speculates
                              that the preferred pivots are kept and repeats

@@ -95,6 +95,7 @@ struct gblu_ctx {
     int32_t repredictions = 0;                     // structure re-predictions of the last restart or
                                                    // first factorization
     bool strict_on = false, no_stop = false;       // re-factorization check modes of a re-prediction
+    bool solve_pending = false;                    // an install's solve part is still to be built
     bool last_repivot = false;                     // the last refactorization restarted
     bool analyzed = false, factorized = false;
     Pattern P;
@@ -309,23 +310,70 @@ int status_code(gblu_ctx *h)
     return fail(s, "device status %d", s);
 }
 
+static SolveSplit solve_split(const gblu_opts &o)
+{
+    SolveSplit sp;
+    sp.density = o.solve_dense_density;
+    sp.frac = o.solve_dense_frac;
+    sp.min_entries = o.solve_dense_min;
+    sp.slices = o.solve_slices;
+    sp.max_piece = kMaxPieceRows;
+    return sp;
+}
+
+// The solve part of the schedule on the device (and the original row ids of
+// the restart kernel); l_rows_done: the row-wise copy of L went up with the
+// re-factorization part (the wide columns read it).  Synchronizes `st`:
+// the host vectors are uploaded asynchronously.
+static int upload_solve(gblu_ctx *h, cudaStream_t st, bool l_rows_done)
+{
+    const int32_t n = h->S.n;
+    const size_t nnz = (size_t)h->S.nnz();
+    if (nnz > 0)
+        CU(cudaMemcpyAsync(h->rows.p, h->W.LUi_orig.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (!l_rows_done) {
+        CK(upload(h, h->Lrp, h->W.Lrp, st));
+        CK(upload(h, h->Lcol, h->W.Lcol, st));
+        CK(upload(h, h->Lslot, h->W.Lslot, st));
+    }
+    CK(upload(h, h->Urp, h->W.Urp, st));
+    CK(upload(h, h->Ucol, h->W.Urow_col, st));
+    CK(upload(h, h->Uslot, h->W.Uslot, st));
+    CK(upload(h, h->Udiag, h->W.Udiag, st));
+    CK(upload(h, h->lsv_rows, h->W.lsv_rows, st));
+    CK(upload(h, h->usv_rows, h->W.usv_rows, st));
+    CK(upload(h, h->lbs, h->W.lbs, st));
+    CK(upload(h, h->ubs, h->W.ubs, st));
+    CK(upload(h, h->lrb, h->W.lrb, st));
+    CK(upload(h, h->urb, h->W.urb, st));
+    CK(upload(h, h->lsv_tick, h->W.lsv_tick, st));
+    CK(upload(h, h->usv_tick, h->W.usv_tick, st));
+    CK(upload(h, h->ltri0, h->W.ltri0, st));
+    CK(upload(h, h->lseg, h->W.lseg, st));
+    CK(upload(h, h->ufar, h->W.ufar, st));
+    CK(upload(h, h->useg, h->W.useg, st));
+    if (h->W.up0 < n) CK(ensure(h, h->far, (size_t)n));
+    CU(cudaStreamSynchronize(st));
+    return GBLU_OK;
+}
+
 // Install a factor structure: schedule on the host, arrays on the device.
-// values (optional) are the factor values in canonical order.
-int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st)
+// values (optional) are the factor values in canonical order.  With
+// defer_solve only what the re-factorization reads is built and uploaded
+// (nothing synchronizes); finish_install adds the rest, on the host while
+// the stream runs the re-factorization.
+int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *values, cudaStream_t st,
+                      bool defer_solve = false)
 {
     h->S = std::move(S);
     h->struct_version++;
     h->f32_valid = false;
     const int resident_warps = h->ref_blocks_per_sm * h->sm_count * (kRefThreads / 32);
-    SolveSplit sp;
-    sp.density = h->opts.solve_dense_density;
-    sp.frac = h->opts.solve_dense_frac;
-    sp.min_entries = h->opts.solve_dense_min;
-    sp.slices = h->opts.solve_slices;
-    sp.max_piece = kMaxPieceRows;
+    const SolveSplit sp = solve_split(h->opts);
     const auto t_s = std::chrono::steady_clock::now();
     build_schedule(h->P, h->S, h->opts.alpha, resident_warps, h->opts.sched_mode, h->opts.warp_column_max, sp,
-                   h->opts.dense_min_rows, h->W);
+                   h->opts.dense_min_rows, h->W, defer_solve);
+    h->solve_pending = defer_solve;
     const auto t_u = std::chrono::steady_clock::now();
     h->t_tail[2] = std::chrono::duration<double, std::milli>(t_u - t_s).count();
     for (int32_t v : h->W.amap)
@@ -375,33 +423,38 @@ int install_structure(gblu_ctx *h, Structure &&S, const std::vector<double> *val
         CK(ensure(h, h->rows, nnz));
         CK(ensure(h, h->vals, nnz));
     }
-    if (nnz > 0)
-        CU(cudaMemcpyAsync(h->rows.p, h->W.LUi_orig.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     if (values && nnz > 0)
         CU(cudaMemcpyAsync(h->vals.p, values->data(), nnz * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(upload(h, h->Lrp, h->W.Lrp, st));
-    CK(upload(h, h->Urp, h->W.Urp, st));
-    CK(upload(h, h->Lcol, h->W.Lcol, st));
-    CK(upload(h, h->Lslot, h->W.Lslot, st));
-    CK(upload(h, h->Ucol, h->W.Urow_col, st));
-    CK(upload(h, h->Uslot, h->W.Uslot, st));
-    CK(upload(h, h->Udiag, h->W.Udiag, st));
-    CK(upload(h, h->lsv_rows, h->W.lsv_rows, st));
-    CK(upload(h, h->usv_rows, h->W.usv_rows, st));
-    CK(upload(h, h->lbs, h->W.lbs, st));
-    CK(upload(h, h->ubs, h->W.ubs, st));
-    CK(upload(h, h->lrb, h->W.lrb, st));
-    CK(upload(h, h->urb, h->W.urb, st));
-    CK(upload(h, h->lsv_tick, h->W.lsv_tick, st));
-    CK(upload(h, h->usv_tick, h->W.usv_tick, st));
-    CK(upload(h, h->ltri0, h->W.ltri0, st));
-    CK(upload(h, h->lseg, h->W.lseg, st));
-    CK(upload(h, h->ufar, h->W.ufar, st));
-    CK(upload(h, h->useg, h->W.useg, st));
-    if (h->W.up0 < n) CK(ensure(h, h->far, (size_t)n));
-    // host vectors are uploaded asynchronously: keep them alive until done
-    CU(cudaStreamSynchronize(st));
+    if (defer_solve) {
+        // the wide columns read the rows of L; the host vectors stay alive
+        // in the handle until finish_install synchronizes
+        if (h->W.rowwise_ready) {
+            CK(upload(h, h->Lrp, h->W.Lrp, st));
+            CK(upload(h, h->Lcol, h->W.Lcol, st));
+            CK(upload(h, h->Lslot, h->W.Lslot, st));
+        }
+        h->t_tail[3] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_u).count();
+        return GBLU_OK;
+    }
+    CK(upload_solve(h, st, false));
     h->t_tail[3] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_u).count();
+    return GBLU_OK;
+}
+
+// The solve part of a deferred install_structure: built on the host (while
+// the stream may still run a re-factorization, which does not read it),
+// then uploaded behind the work on the stream.
+int finish_install(gblu_ctx *h, cudaStream_t st)
+{
+    if (!h->solve_pending) return GBLU_OK;
+    const bool l_rows_done = h->W.rowwise_ready;
+    const auto t_s = std::chrono::steady_clock::now();
+    build_solve_schedule(h->S, solve_split(h->opts), h->W);
+    h->t_tail[2] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_s).count();
+    // its uploads wait behind the stream's work, so their time is the
+    // caller's (the re-factorization's), not tail_upload_ms
+    CK(upload_solve(h, st, l_rows_done));
+    h->solve_pending = false;
     return GBLU_OK;
 }
 
@@ -491,10 +544,13 @@ int issue_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int ep)
     return GBLU_OK;
 }
 
+// A deferred install's solve part is finished on the host while the
+// re-factorization runs.
 int run_refactor(gblu_ctx *h, const double *Ax, cudaStream_t st, int *interrupted)
 {
     h->epoch++;
     CK(issue_refactor(h, Ax, st, h->epoch));
+    CK(finish_install(h, st));
     CK(read_ctl(h, st));
     CK(status_code(h));
     *interrupted = h->hctl->interrupted;
@@ -872,7 +928,7 @@ int repredict(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<
         Structure S2;
         symmetric_structure(h->P, S2, &pred);
         if (S2.nnz() > nnz_limit) return GBLU_OK;
-        CK(install_structure(h, std::move(S2), nullptr, st));
+        CK(install_structure(h, std::move(S2), nullptr, st, true));
         h->predicted = true;
         CK(upload(h, h->strict, strict, st));
         h->strict_on = true;
@@ -1233,7 +1289,7 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream)
         Structure S2;
         symmetric_structure(h->P, S2);
         h->t_first_symbolic = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        CK(install_structure(h, std::move(S2), nullptr, st));
+        CK(install_structure(h, std::move(S2), nullptr, st, true));
         h->predicted = true;
         const auto t1 = std::chrono::steady_clock::now();
         int interrupted = 0;

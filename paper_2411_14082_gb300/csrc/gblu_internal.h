@@ -126,6 +126,10 @@ struct Schedule {
     // diagonal are taken that way (0: none); pull_cols = columns with > 0
     std::vector<int32_t> pull_start;
     int64_t pull_cols = 0;
+    // dividing threshold of the levels (alpha x resident warps); which parts
+    // are built: the row-wise copies, and the whole solve part
+    double thr = 0.0;
+    bool rowwise_ready = false, solve_ready = false;
 };
 // wide columns: at most kPullMaxL entries in L and at least kPullMinRuns
 // supernode runs among the dependencies
@@ -174,9 +178,12 @@ int64_t symmetric_fill(const Pattern &P, double *flops = nullptr);
 void symmetric_structure(const Pattern &P, Structure &S, const std::vector<int32_t> *piv = nullptr);
 // off-diagonal entries of A whose transposed position is not an entry of A
 int64_t unsymmetric_entries(const Pattern &P);
+// The schedule of a structure; with defer_solve, only what the
+// re-factorization reads (the solve part follows by build_solve_schedule)
 void build_schedule(const Pattern &P, const Structure &S, double alpha,
                     int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
-                    int dense_min_rows, Schedule &W);
+                    int dense_min_rows, Schedule &W, bool defer_solve = false);
+void build_solve_schedule(const Structure &S, const SolveSplit &split, Schedule &W);
 // levels of the column dependency graph; with cut < n, the dependencies of
 // columns k >= cut on columns >= cut are left out
 int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,

@@ -255,194 +255,14 @@ static int32_t dense_split(int32_t n, const std::vector<int64_t> &count_from, co
     return p0;
 }
 
-void build_schedule(const Pattern &P, const Structure &S, double alpha,
-                    int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
-                    int dense_min_rows, Schedule &W)
+// Row-wise (CSR) copies of L and U for the solves and the wide columns:
+// per-thread histograms of the row entries over column ranges give each
+// range its first position in every row; each thread then copies its
+// columns in ascending order, so every row lists its entries by ascending
+// column, as a serial pass would.
+static void rowwise_copies(const Structure &S, Schedule &W)
 {
     const int32_t n = S.n;
-    // ---- dense tail: the longest trailing block [p, n) in which every
-    // column holds every row >= p (low[k] = first row of the unbroken run of
-    // rows that ends at n-1 in column k) ----
-    W.dense_p = n;
-    W.dense_m = 0;
-    W.dense_s0.clear();
-    if (dense_min_rows > 0 && n > 0) {
-        int32_t pd = n, mx = 0;
-        for (int32_t p = n - 1; p >= 0; p--) {
-            const int64_t b = S.LUp[p], e = S.LUp[p + 1];
-            int32_t low = n;
-            if (e > b && S.LUi[e - 1] == n - 1) {
-                int64_t q = e - 1;
-                while (q > b && S.LUi[q - 1] == S.LUi[q] - 1) q--;
-                low = S.LUi[q];
-            }
-            mx = std::max(mx, low);
-            if (mx > p) break;
-            pd = p;
-        }
-        int32_t m = n - pd;
-        if (m > GBLU_DENSE_MAX_ROWS) { m = GBLU_DENSE_MAX_ROWS; pd = n - m; }
-        if (m >= dense_min_rows) {
-            W.dense_p = pd;
-            W.dense_m = m;
-            W.dense_s0.resize(m);
-            for (int32_t c = 0; c < m; c++) {
-                const int32_t k = pd + c;
-                const int32_t *r = S.LUi.data() + S.LUp[k];
-                const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
-                W.dense_s0[c] = (int32_t)(std::lower_bound(r, r + len, pd) - r);
-            }
-        }
-    }
-    // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
-    W.chain.assign(n, 0);
-    parallel_ranges(n, S.LUp.data(), [&](int32_t j0, int32_t j1, int) {
-        for (int32_t j = j0; j < j1 && j + 1 < n; j++) {
-            const int64_t a = S.LUp[j] + S.nU[j], ae = S.LUp[j + 1];
-            const int64_t b = S.LUp[j + 1] + S.nU[j + 1], be = S.LUp[j + 2];
-            if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
-            W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
-        }
-    });
-    // ---- wide columns: at most kPullMaxL L entries and at least kPullMinRuns
-    // supernode runs among the dependencies.  All but the last chain of linked
-    // dependencies are taken row by row (pull_start = where that chain
-    // starts); none in the dense tail ----
-    W.pull_start.assign(n, 0);
-    {
-        std::atomic<int64_t> cnt{0};
-        parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
-            int64_t c = 0;
-            for (int32_t k = k0; k < k1 && k < W.dense_p; k++) {
-                const int64_t b = S.LUp[k];
-                const int32_t nd = S.nU[k] - 1, nl = (int32_t)(S.LUp[k + 1] - b) - S.nU[k];
-                if (nl > kPullMaxL || nd < kPullMinRuns) continue;
-                const int32_t *u = S.LUi.data() + b;
-                auto linked = [&](int32_t i) { return u[i] == u[i - 1] + 1 && W.chain[u[i - 1]] != 0; };
-                int32_t runs = 1;
-                for (int32_t i = 1; i < nd; i++) runs += !linked(i);
-                if (runs < kPullMinRuns) continue;
-                int32_t p = nd - 1;
-                while (p > 0 && linked(p)) p--;
-                W.pull_start[k] = p;
-                c += p > 0;
-            }
-            cnt += c;
-        });
-        W.pull_cols = cnt.load();
-    }
-    const double thr = alpha * (double)resident_warps;
-    // ---- EGraph levels, the dividing level (Section IV-B) and the tasks:
-    // on a thread of their own, beside the slot maps and row-wise copies
-    // below (they write disjoint members of W) ----
-    std::thread level_thread([&]() {
-        // columns of the dense tail wait only for their dependencies before it
-        std::vector<int32_t> level;
-        W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
-        W.level_ptr.assign(W.n_levels + 1, 0);
-        for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
-        for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
-        W.level_cols.assign(n, 0);
-        {
-            std::vector<int32_t> pos(W.level_ptr.begin(), W.level_ptr.end() - 1);
-            for (int32_t k = 0; k < n; k++) W.level_cols[pos[level[k]]++] = k;
-        }
-        W.div_level = W.n_levels;
-        for (int32_t l = 0; l < W.n_levels; l++)
-            if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
-        if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
-        if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
-        // ---- tasks, in level order: long columns alone, medium columns in pairs,
-        // short ones in groups of up to 8.  A pending item is only merged with
-        // the column that immediately follows it, so a task never comes before
-        // a task holding one of its dependencies.  Groups stay inside a level
-        // before the dividing level.
-        W.task_ptr.assign(1, 0);
-        W.task_cols.clear();
-        W.task_cols.reserve(n);
-        W.level_task_ptr.assign(1, 0);
-        {
-            const int64_t half = kRefCapLong / 2;   // medium: up to half the CTA's entries
-            int32_t group = 0;      // short columns pending
-            bool pend_med = false;  // one medium column pending
-            auto close = [&]() {
-                if (group || pend_med) W.task_ptr.push_back((int32_t)W.task_cols.size());
-                group = 0;
-                pend_med = false;
-            };
-            for (int32_t l = 0; l < W.n_levels; l++) {
-                for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
-                    const int32_t k = W.level_cols[p];
-                    const int64_t len = S.LUp[k + 1] - S.LUp[k];
-                    if (len > half || W.pull_start[k] > 0) {   // a whole CTA
-                        close();
-                        W.task_cols.push_back(k);
-                        W.task_ptr.push_back((int32_t)W.task_cols.size());
-                    } else if (len > cap_short) {
-                        if (pend_med) {
-                            W.task_cols.push_back(k);
-                            W.task_ptr.push_back((int32_t)W.task_cols.size());
-                            pend_med = false;
-                        } else {
-                            close();
-                            W.task_cols.push_back(k);
-                            pend_med = true;
-                        }
-                    } else {
-                        if (pend_med) close();
-                        W.task_cols.push_back(k);
-                        if (++group == 8) close();
-                    }
-                }
-                if (l < W.div_level) {
-                    close();
-                    W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
-                }
-            }
-            close();
-        }
-    });
-    // ---- flops of one refactorization (partial sums of integers, exact in
-    // any order below 2^53) ----
-    double part[kHostThreads] = {};
-    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int t) {
-        double fl = 0;
-        for (int32_t k = k0; k < k1; k++)
-            for (int64_t e = S.LUp[k]; e < S.LUp[k] + S.nU[k] - 1; e++) {
-                const int32_t j = S.LUi[e];
-                fl += 2.0 * (double)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
-            }
-        part[t] = fl;
-    });
-    W.flops = 0;
-    for (double v : part) W.flops += v;
-    // ---- A slot -> position in its column (columns are sorted) ----
-    const int64_t nnzA = (int64_t)P.Ai.size();
-    W.amap.assign(nnzA, -1);
-    parallel_chunks(n, 2048, [&](int32_t c0, int32_t c1, int) {
-        for (int32_t c = c0; c < c1; c++) {
-            const int32_t k = P.qinv[c];
-            const int32_t *col = S.LUi.data() + S.LUp[k];
-            const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
-            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
-                const int32_t s = S.pinv[P.Ai[p]];
-                const int32_t *it = std::lower_bound(col, col + len, s);
-                W.amap[p] = (it != col + len && *it == s) ? (int32_t)(it - col) : -1;
-            }
-        }
-    });
-    // ---- original row ids of L entries (used by the restart kernel) ----
-    W.LUi_orig.resize(S.LUi.size());
-    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
-        for (int32_t k = k0; k < k1; k++)
-            for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
-                W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
-    });
-    // ---- row-wise copies for the solves: per-thread histograms of the row
-    // entries over column ranges give each range its first position in
-    // every row; each thread then copies its columns in ascending order, so
-    // every row lists its entries by ascending column, as a serial pass
-    // would ----
     W.Lrp.assign(n + 1, 0);
     W.Urp.assign(n + 1, 0);
     W.Udiag.assign(n, 0);
@@ -502,6 +322,26 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
             }
         });
     }
+    W.rowwise_ready = true;
+}
+
+// The solve part of the schedule (Section V and the row blocks of the
+// sparse solves), which the re-factorization does not read: the original
+// row ids of the restart kernel, the row-wise copies (unless the wide
+// columns needed them already), the structure-adaptive split, the
+// trailing block's slices and the row blocks with their levels.
+void build_solve_schedule(const Structure &S, const SolveSplit &split, Schedule &W)
+{
+    const int32_t n = S.n;
+    const double thr = W.thr;
+    // ---- original row ids of L entries (used by the restart kernel) ----
+    W.LUi_orig.resize(S.LUi.size());
+    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
+        for (int32_t k = k0; k < k1; k++)
+            for (int64_t e = S.LUp[k]; e < S.LUp[k + 1]; e++)
+                W.LUi_orig[e] = (e - S.LUp[k] >= S.nU[k]) ? S.piv[S.LUi[e]] : S.LUi[e];
+    });
+    if (!W.rowwise_ready) rowwise_copies(S, W);
     // ---- structure-adaptive split of both triangular factors (Section V) ----
     {
         std::vector<int64_t> cf(n + 1, 0), rl(n, 0);
@@ -668,6 +508,195 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     }
     lower.join();
     upper.join();
+    W.solve_ready = true;
+}
+
+void build_schedule(const Pattern &P, const Structure &S, double alpha,
+                    int resident_warps, int sched_mode, int cap_short, const SolveSplit &split,
+                    int dense_min_rows, Schedule &W, bool defer_solve)
+{
+    const int32_t n = S.n;
+    W.rowwise_ready = false;
+    W.solve_ready = false;
+    // ---- dense tail: the longest trailing block [p, n) in which every
+    // column holds every row >= p (low[k] = first row of the unbroken run of
+    // rows that ends at n-1 in column k) ----
+    W.dense_p = n;
+    W.dense_m = 0;
+    W.dense_s0.clear();
+    if (dense_min_rows > 0 && n > 0) {
+        int32_t pd = n, mx = 0;
+        for (int32_t p = n - 1; p >= 0; p--) {
+            const int64_t b = S.LUp[p], e = S.LUp[p + 1];
+            int32_t low = n;
+            if (e > b && S.LUi[e - 1] == n - 1) {
+                int64_t q = e - 1;
+                while (q > b && S.LUi[q - 1] == S.LUi[q] - 1) q--;
+                low = S.LUi[q];
+            }
+            mx = std::max(mx, low);
+            if (mx > p) break;
+            pd = p;
+        }
+        int32_t m = n - pd;
+        if (m > GBLU_DENSE_MAX_ROWS) { m = GBLU_DENSE_MAX_ROWS; pd = n - m; }
+        if (m >= dense_min_rows) {
+            W.dense_p = pd;
+            W.dense_m = m;
+            W.dense_s0.resize(m);
+            for (int32_t c = 0; c < m; c++) {
+                const int32_t k = pd + c;
+                const int32_t *r = S.LUi.data() + S.LUp[k];
+                const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
+                W.dense_s0[c] = (int32_t)(std::lower_bound(r, r + len, pd) - r);
+            }
+        }
+    }
+    // ---- supernode links of L: L(:,j) = {j+1} + L(:,j+1) ----
+    W.chain.assign(n, 0);
+    parallel_ranges(n, S.LUp.data(), [&](int32_t j0, int32_t j1, int) {
+        for (int32_t j = j0; j < j1 && j + 1 < n; j++) {
+            const int64_t a = S.LUp[j] + S.nU[j], ae = S.LUp[j + 1];
+            const int64_t b = S.LUp[j + 1] + S.nU[j + 1], be = S.LUp[j + 2];
+            if (ae - a != be - b + 1 || S.LUi[a] != j + 1) continue;
+            W.chain[j] = std::equal(S.LUi.begin() + a + 1, S.LUi.begin() + ae, S.LUi.begin() + b) ? 1 : 0;
+        }
+    });
+    // ---- wide columns: at most kPullMaxL L entries and at least kPullMinRuns
+    // supernode runs among the dependencies.  All but the last chain of linked
+    // dependencies are taken row by row (pull_start = where that chain
+    // starts); none in the dense tail ----
+    W.pull_start.assign(n, 0);
+    {
+        std::atomic<int64_t> cnt{0};
+        parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int) {
+            int64_t c = 0;
+            for (int32_t k = k0; k < k1 && k < W.dense_p; k++) {
+                const int64_t b = S.LUp[k];
+                const int32_t nd = S.nU[k] - 1, nl = (int32_t)(S.LUp[k + 1] - b) - S.nU[k];
+                if (nl > kPullMaxL || nd < kPullMinRuns) continue;
+                const int32_t *u = S.LUi.data() + b;
+                auto linked = [&](int32_t i) { return u[i] == u[i - 1] + 1 && W.chain[u[i - 1]] != 0; };
+                int32_t runs = 1;
+                for (int32_t i = 1; i < nd; i++) runs += !linked(i);
+                if (runs < kPullMinRuns) continue;
+                int32_t p = nd - 1;
+                while (p > 0 && linked(p)) p--;
+                W.pull_start[k] = p;
+                c += p > 0;
+            }
+            cnt += c;
+        });
+        W.pull_cols = cnt.load();
+    }
+    const double thr = alpha * (double)resident_warps;
+    W.thr = thr;
+    // ---- EGraph levels, the dividing level (Section IV-B) and the tasks:
+    // on a thread of their own, beside the slot maps and row-wise copies
+    // below (they write disjoint members of W) ----
+    std::thread level_thread([&]() {
+        // columns of the dense tail wait only for their dependencies before it
+        std::vector<int32_t> level;
+        W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
+        W.level_ptr.assign(W.n_levels + 1, 0);
+        for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
+        for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
+        W.level_cols.assign(n, 0);
+        {
+            std::vector<int32_t> pos(W.level_ptr.begin(), W.level_ptr.end() - 1);
+            for (int32_t k = 0; k < n; k++) W.level_cols[pos[level[k]]++] = k;
+        }
+        W.div_level = W.n_levels;
+        for (int32_t l = 0; l < W.n_levels; l++)
+            if ((double)(W.level_ptr[l + 1] - W.level_ptr[l]) < thr) { W.div_level = l; break; }
+        if (sched_mode == GBLU_SCHED_LEVEL) W.div_level = W.n_levels;
+        if (sched_mode == GBLU_SCHED_SYNCFREE) W.div_level = 0;
+        // ---- tasks, in level order: long columns alone, medium columns in pairs,
+        // short ones in groups of up to 8.  A pending item is only merged with
+        // the column that immediately follows it, so a task never comes before
+        // a task holding one of its dependencies.  Groups stay inside a level
+        // before the dividing level.
+        W.task_ptr.assign(1, 0);
+        W.task_cols.clear();
+        W.task_cols.reserve(n);
+        W.level_task_ptr.assign(1, 0);
+        {
+            const int64_t half = kRefCapLong / 2;   // medium: up to half the CTA's entries
+            int32_t group = 0;      // short columns pending
+            bool pend_med = false;  // one medium column pending
+            auto close = [&]() {
+                if (group || pend_med) W.task_ptr.push_back((int32_t)W.task_cols.size());
+                group = 0;
+                pend_med = false;
+            };
+            for (int32_t l = 0; l < W.n_levels; l++) {
+                for (int32_t p = W.level_ptr[l]; p < W.level_ptr[l + 1]; p++) {
+                    const int32_t k = W.level_cols[p];
+                    const int64_t len = S.LUp[k + 1] - S.LUp[k];
+                    if (len > half || W.pull_start[k] > 0) {   // a whole CTA
+                        close();
+                        W.task_cols.push_back(k);
+                        W.task_ptr.push_back((int32_t)W.task_cols.size());
+                    } else if (len > cap_short) {
+                        if (pend_med) {
+                            W.task_cols.push_back(k);
+                            W.task_ptr.push_back((int32_t)W.task_cols.size());
+                            pend_med = false;
+                        } else {
+                            close();
+                            W.task_cols.push_back(k);
+                            pend_med = true;
+                        }
+                    } else {
+                        if (pend_med) close();
+                        W.task_cols.push_back(k);
+                        if (++group == 8) close();
+                    }
+                }
+                if (l < W.div_level) {
+                    close();
+                    W.level_task_ptr.push_back((int32_t)W.task_ptr.size() - 1);
+                }
+            }
+            close();
+        }
+    });
+    // ---- flops of one refactorization (partial sums of integers, exact in
+    // any order below 2^53) ----
+    double part[kHostThreads] = {};
+    parallel_ranges(n, S.LUp.data(), [&](int32_t k0, int32_t k1, int t) {
+        double fl = 0;
+        for (int32_t k = k0; k < k1; k++)
+            for (int64_t e = S.LUp[k]; e < S.LUp[k] + S.nU[k] - 1; e++) {
+                const int32_t j = S.LUi[e];
+                fl += 2.0 * (double)(S.LUp[j + 1] - S.LUp[j] - S.nU[j]);
+            }
+        part[t] = fl;
+    });
+    W.flops = 0;
+    for (double v : part) W.flops += v;
+    // ---- A slot -> position in its column (columns are sorted) ----
+    const int64_t nnzA = (int64_t)P.Ai.size();
+    W.amap.assign(nnzA, -1);
+    parallel_chunks(n, 2048, [&](int32_t c0, int32_t c1, int) {
+        for (int32_t c = c0; c < c1; c++) {
+            const int32_t k = P.qinv[c];
+            const int32_t *col = S.LUi.data() + S.LUp[k];
+            const int32_t len = (int32_t)(S.LUp[k + 1] - S.LUp[k]);
+            for (int32_t p = P.Ap[c]; p < P.Ap[c + 1]; p++) {
+                const int32_t s = S.pinv[P.Ai[p]];
+                const int32_t *it = std::lower_bound(col, col + len, s);
+                W.amap[p] = (it != col + len && *it == s) ? (int32_t)(it - col) : -1;
+            }
+        }
+    });
+    if (defer_solve) {
+        // the wide columns read rows of L during the re-factorization
+        if (W.pull_cols > 0) rowwise_copies(S, W);
+        level_thread.join();
+        return;
+    }
+    build_solve_schedule(S, split, W);
     level_thread.join();
 }
 
