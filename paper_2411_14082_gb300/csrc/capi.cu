@@ -972,6 +972,23 @@ int pivot_every_step(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::
     return run_tail(h, Ax, st, all, hint, false, true);
 }
 
+// The pivot moves of a restart on a predicted structure, from the first
+// failing step k of a no-stop pass (Section IV-C/D): re-prediction, else
+// the pivoting kernel over every step, with the installed pivots preferred.
+int restart_repredicted(gblu_ctx *h, const double *Ax, cudaStream_t st, int32_t k,
+                        std::chrono::steady_clock::time_point t0)
+{
+    const std::vector<int32_t> prefer = h->S.piv;
+    bool solved = false;
+    CK(repredict(h, Ax, st, prefer, k, &solved));
+    if (!solved) CK(pivot_every_step(h, Ax, st, prefer));
+    h->n_restart_cols = h->P.n;
+    if (solved) h->tail_passes = 0;
+    h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (solved) h->t_tail[1] = h->t_tail[3] = 0.0;
+    return GBLU_OK;
+}
+
 int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
 {
     NvtxRange nvtx_range("restart");
@@ -988,17 +1005,7 @@ int run_restart(gblu_ctx *h, const double *Ax, cudaStream_t st)
         // goes to the pivoting kernel
         const bool repred = h->predicted;
         CK(restart_on_structure(h, Ax, st, repred, &interrupted));
-        if (interrupted && repred) {
-            const std::vector<int32_t> prefer = h->S.piv;
-            bool solved = false;
-            CK(repredict(h, Ax, st, prefer, h->hctl->first_bad, &solved));
-            if (!solved) CK(pivot_every_step(h, Ax, st, prefer));
-            h->n_restart_cols = n;
-            h->tail_passes = solved ? 0 : h->tail_passes;
-            h->t_tail[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            if (solved) h->t_tail[1] = h->t_tail[3] = 0.0;
-            return GBLU_OK;
-        }
+        if (interrupted && repred) return restart_repredicted(h, Ax, st, h->hctl->first_bad, t0);
         if (!interrupted) {
             int64_t redone = 0;
             for (int32_t k = 0; k < n; k++) redone += fin0[k] != h->epoch;
@@ -1380,10 +1387,34 @@ int gblu_refactorize(gblu_handle h, const double *Ax_dev, void *stream, int32_t 
     cudaStream_t st = (cudaStream_t)stream;
     int interrupted = 0;
     h->n_refactor++;
+    // On a predicted structure a failed check needs a pivot to move: the
+    // restart's first stage would meet the same failure (the same values,
+    // dependencies and order), unless the failure was forced.  The pass
+    // then runs in no-stop mode, so the first failing step is exact and its
+    // column holds the values for the pivot choice, and the restart goes
+    // straight to re-prediction.
+    const bool direct = h->predicted && h->force_col < 0 && h->W.dense_m == 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    h->no_stop = direct;
     int rc = run_refactor(h, Ax_dev, st, &interrupted);
+    h->no_stop = false;
     if (rc != GBLU_OK) {
         h->factorized = false;
         return rc;
+    }
+    if (direct && h->hctl->first_bad != INT_MAX) {
+        NvtxRange nvtx_range("restart");
+        h->n_repivot++;
+        h->repredictions = 0;
+        h->last_first_bad = h->hctl->first_bad;
+        rc = restart_repredicted(h, Ax_dev, st, h->hctl->first_bad, t0);
+        if (rc != GBLU_OK) {
+            h->factorized = false;
+            return rc;
+        }
+        if (repivoted) *repivoted = 1;
+        h->last_repivot = true;
+        return GBLU_REPIVOTED;
     }
     if (!interrupted) return GBLU_OK;
     h->n_repivot++;
