@@ -62,6 +62,9 @@ struct Structure {
     std::vector<int32_t> nU;   // U entries of each column incl. the diagonal
     std::vector<int32_t> piv;  // original row pivotal at each step
     std::vector<int32_t> pinv;
+    // a predicted structure (symmetric_structure): L and U^T have the
+    // pattern of one Cholesky factor
+    bool symmetric = false;
     int64_t nnz() const { return LUp.empty() ? 0 : LUp.back(); }
 };
 

@@ -76,6 +76,27 @@ int32_t levels_of(int32_t n, const int64_t *Up, const int32_t *Ui,
     return nl;
 }
 
+// EGraph levels of a Cholesky-pattern structure (symmetric_structure).
+// Column k depends on the steps of its row subtree, which holds every child
+// of k in the elimination tree (the parent of j is the first L row of
+// column j), and each step depends on its own children, so levels grow up
+// every tree path and the level of k is its height: one more than its
+// highest child, 0 for a leaf.  Equals levels_of on such a structure.
+static int32_t tree_levels(const Structure &S, std::vector<int32_t> &level)
+{
+    const int32_t n = S.n;
+    level.assign(n, 0);
+    int32_t nl = n > 0 ? 1 : 0;
+    for (int32_t j = 0; j < n; j++) {
+        const int64_t l0 = S.LUp[j] + S.nU[j];
+        if (l0 >= S.LUp[j + 1]) continue;
+        const int32_t p = S.LUi[l0];
+        if (level[j] + 1 > level[p]) level[p] = level[j] + 1;
+        if (level[p] + 1 > nl) nl = level[p] + 1;
+    }
+    return nl;
+}
+
 // Lower adjacency of S = (A + A^T)(Q,Q) by row (cnt[n+1] offsets; the steps j < i
 // adjacent to step i) and the elimination tree of S (Liu's algorithm with
 // path compression).
@@ -597,7 +618,9 @@ void build_schedule(const Pattern &P, const Structure &S, double alpha,
     std::thread level_thread([&]() {
         // columns of the dense tail wait only for their dependencies before it
         std::vector<int32_t> level;
-        W.n_levels = levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level, W.dense_p);
+        W.n_levels = S.symmetric && W.dense_p >= n ? tree_levels(S, level)
+                                                   : levels_of(n, S.LUp.data(), S.LUi.data(), S.nU.data(), level,
+                                                               W.dense_p);
         W.level_ptr.assign(W.n_levels + 1, 0);
         for (int32_t k = 0; k < n; k++) W.level_ptr[level[k] + 1]++;
         for (int32_t l = 0; l < W.n_levels; l++) W.level_ptr[l + 1] += W.level_ptr[l];
@@ -848,6 +871,7 @@ void symmetric_structure(const Pattern &P, Structure &S, const std::vector<int32
         S.piv = P.Q;
         S.pinv = P.qinv;
     }
+    S.symmetric = true;
 }
 
 }  // namespace gblu

@@ -354,6 +354,35 @@ def test_predicted_structure_for_given_rows():
         gblu.predicted_structure(3, np.array([0, 1, 2, 3]), np.array([0, 1, 2]), np.arange(3), np.array([0, 0, 1]))
 
 
+def test_levels_of_predicted_structures_are_tree_heights():
+    """On a Cholesky-pattern structure (gblu_predicted_structure, with or
+    without pivot exchanges) the EGraph level of a column (gblu_levels over
+    its U rows) is its height in the elimination tree, the tree's parent of
+    j being the first L row of column j: the schedule computes the levels of
+    predicted structures that way."""
+    rng = np.random.default_rng(41)
+    for trial in range(40):
+        n = int(rng.integers(1, 120))
+        _, Ap, Ai, _ = inputs.random_sparse(n, rng.uniform(0.01, 0.2), rng)
+        Q = rng.permutation(n).astype(np.int32)
+        piv = None
+        if trial % 2:
+            piv = Q.copy()
+            a, b = rng.choice(n, 2) if n > 1 else (0, 0)
+            piv[a], piv[b] = piv[b], piv[a]
+        LUp, LUi, nU = gblu.predicted_structure(n, Ap, Ai, Q, piv)
+        Up = np.zeros(n + 1, np.int64)
+        Up[1:] = np.cumsum(nU)
+        Ui = np.concatenate([LUi[LUp[k]:LUp[k] + nU[k]] for k in range(n)]).astype(np.int32)
+        lv, nl = gblu.levels(n, Up, Ui)
+        height = np.zeros(n, np.int64)
+        for j in range(n):
+            if LUp[j] + nU[j] < LUp[j + 1]:
+                p = LUi[LUp[j] + nU[j]]
+                height[p] = max(height[p], height[j] + 1)
+        assert np.array_equal(lv, height) and nl == height.max() + 1
+
+
 def test_constrained_minimum_degree():
     """gblu_order_cmd: one group gives plain minimum degree; with groups the
     elimination order never goes back to a lower group, and a group
