@@ -906,6 +906,14 @@ int repredict(gblu_ctx *h, const double *Ax, cudaStream_t st, const std::vector<
 {
     *solved = false;
     h->repredictions = 0;
+    // a forced failure (gblu_refactorize_forced) belongs to the first pass
+    // only; the rounds check every column as it is
+    struct ForceOff {
+        gblu_ctx *h;
+        int32_t saved;
+        ~ForceOff() { h->force_col = saved; }
+    } force_off{h, h->force_col};
+    h->force_col = -1;
     const int32_t n = h->P.n;
     const int64_t nnz_limit = h->S.nnz() + h->S.nnz() / 4 + n;
     // the failing step reported for the call is the first check's
