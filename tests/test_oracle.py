@@ -32,7 +32,7 @@ def dense_of(n, Ap, Ai, Ax):
 
 # ---------------------------------------------------------------- golden
 @pytest.mark.parametrize("name", ["mna_vsource_3x3.txt", "refactor_fail_col2_4x4.txt",
-                                  "restart_recompute_3x3.txt"])
+                                  "restart_recompute_3x3.txt", "repredict_cascade_3x3.txt"])
 def test_golden_examples(name):
     g = load(name)
     n = g["n"]

@@ -25,6 +25,7 @@ import numpy as np
 
 from oracle import oracle as O
 from paper_2411_14082_gb300 import inputs
+from tests.golden_io import load
 
 EPS = 1e-3
 
@@ -36,7 +37,7 @@ def dense(n, Ap, Ai, Ax):
     return A
 
 
-def first_failure(A, Q, pred, prefer, qinv):
+def first_failure(A, Q, pred, prefer, qinv, strict=True, eps=EPS):
     """(k, s): the first step whose check fails on B = A(pred, Q) and the
     step of the largest candidate there; (None, None) when all pass."""
     n = len(Q)
@@ -52,8 +53,8 @@ def first_failure(A, Q, pred, prefer, qinv):
         U[:k, k] = u
         d, others = x[0], np.abs(x[1:])
         m = others.max() if len(others) else 0.0
-        if pred[k] == prefer[k]:
-            ok = d != 0 and abs(d) >= EPS * m
+        if pred[k] == prefer[k] or not strict:
+            ok = d != 0 and abs(d) >= eps * m
         else:
             ok = abs(d) > m
         if not ok:
@@ -66,6 +67,37 @@ def first_failure(A, Q, pred, prefer, qinv):
         U[k, k] = d
         L[k + 1:, k] = x[1:] / d
     return None, None
+
+
+def replay(A, Q, prefer, strict=True, eps=EPS):
+    """The rounds from the preferred rows: (final rows, rounds)."""
+    n = len(Q)
+    qinv = np.empty(n, np.int64)
+    qinv[Q] = np.arange(n)
+    pred, last, rounds = list(prefer), -1, 0
+    while True:
+        k, s = first_failure(A, Q, pred, prefer, qinv, strict, eps)
+        if k is None:
+            return pred, rounds
+        assert k > last and s > k
+        pred[k], pred[s] = pred[s], pred[k]
+        last, rounds = k, rounds + 1
+        assert rounds <= n
+
+
+def test_worked_cascade():
+    """tests/golden/repredict_cascade_3x3.txt: two rounds reach the worked
+    pivots [1, 2, 0]; with the threshold rule at every step the rounds
+    would stop at [1, 0, 2] (row 0 passes 0.96 >= 0.1 * 1 at step 1)."""
+    g = load("repredict_cascade_3x3.txt")
+    n = g["n"]
+    A = dense(n, g["Ap"], g["Ai"], g["Ax"])
+    prefer = [int(v) for v in g["prefer"]]
+    pred, rounds = replay(A, g["Q"], prefer, eps=g["eps"])
+    assert pred == [int(v) for v in g["piv"]] and rounds == 2
+    assert rounds == exchange_rounds(prefer, [int(v) for v in g["piv"]])
+    pred, _ = replay(A, g["Q"], prefer, strict=False, eps=g["eps"])
+    assert pred == [1, 0, 2]
 
 
 def exchange_rounds(prefer, piv):
@@ -110,15 +142,7 @@ def test_repredicted_pivots_are_the_oracles():
         A = dense(n, Ap, Ai, Ax)
         if np.linalg.cond(A) > 1e8:
             continue
-        pred, last, rounds = list(prefer), -1, 0
-        while True:
-            k, s = first_failure(A, Q, pred, prefer, qinv)
-            if k is None:
-                break
-            assert k > last and s > k
-            pred[k], pred[s] = pred[s], pred[k]
-            last, rounds = k, rounds + 1
-            assert rounds <= n
+        pred, rounds = replay(A, Q, prefer)
         assert pred == [int(v) for v in ref.piv]
         assert rounds == exchange_rounds(prefer, [int(v) for v in ref.piv])
         done += 1
