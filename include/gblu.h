@@ -216,12 +216,17 @@ int gblu_factorize(gblu_handle h, const double *Ax_dev, void *stream);
  * Fast re-factorization with pivot check (Section IV, Algorithms 3-5):
  * recomputes the factors of new values on the previous pattern and pivot
  * order, checking every pivot.  If a pivot fails, the restart recomputes
- * with pivoting, preferring the previous pivots, in two stages: first the
- * unfinished columns on the installed structure, speculating that every
- * step keeps its preferred row, with the same check confirming each (exact
- * when all pass: the structure is then the old one); if a check fails
- * again, a pivot must move.  On a structure that was predicted (the first
- * factorization's, or a re-prediction's), the first failing step takes the
+ * with pivoting, preferring the previous pivots.  On a structure the
+ * pivoting kernel produced (and after a forced failure, see
+ * gblu_refactorize_forced) it first runs the unfinished columns again on
+ * the installed structure, speculating that every step keeps its preferred
+ * row, with the same check confirming each (exact when all pass: the
+ * structure is then the old one); if a check fails again, a pivot must
+ * move.  On a structure that was predicted (the first factorization's, or
+ * a re-prediction's), that first stage could only fail again, so the
+ * re-factorization itself runs without stopping at a failed check (later
+ * columns are recomputed anyway) and a failure goes straight to the pivot
+ * move: the first failing step takes the
  * threshold rule's row, the step that held that row takes the failing
  * step's row, the structure is predicted again for these pivot rows (the
  * Cholesky pattern of B + B^T with B = A(piv, Q), which holds the factors
